@@ -1,0 +1,991 @@
+/*
+ * orc.c -- plain single-threaded CPU oracle of the DIG-augmented DSMC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY (see orc.h).  Slow and literal on purpose: every
+ * step is written out in the order the paper states it, with no blocking,
+ * fusion or reordering.  Build: gcc -O2 -ffp-contract=off -fPIC -shared.
+ *
+ * Paper: "DIG-augmented DSMC on unstructured meshes" (arXiv 2607.08195).
+ *   Sec. 2.1  DSMC: particle state (x, v, I_r; N_eff), move, NTC pair selection,
+ *             VSS/VHS cross sections, Borgnakke-Larsen exchange (Eq. inelastic
+ *             probability), sampled moments (Eq. dsmc_temperatures).
+ *   Sec. 3.1  exponential moving average of the summation variables
+ *             (Eq. exponential_average_moments), steady cumulative average
+ *             (Eq. steady_average_moments).
+ * Where the paper names a method without giving its steps, the oracle follows
+ * the published source named at that function (Bird 1994; Salmon et al. 2011;
+ * Marsaglia 1972; Rocchini and Cignoni 2000).
+ */
+#include "orc.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define KB 1.380649e-23
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as    */
+/* easy as 1, 2, 3", SC'11): ten rounds of the 4x32 Philox S-box with the     */
+/* Weyl key schedule.                                                          */
+/* ------------------------------------------------------------------------- */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* purposes of the random streams: key = (seed_lo, seed_hi ^ purpose << 24) */
+enum { RP_INIT_POS = 1, RP_INIT_VEL = 2, RP_WALL = 3, RP_INJECT = 4, RP_COLL = 5, RP_DIR = 6,
+       RP_LB = 7, RP_RECAL = 8 };
+
+static void rng4(const orc_ctx* c, int purpose, uint32_t entity, uint32_t sub, uint32_t step,
+                 uint32_t draw, uint32_t out[4]);
+
+/* uniform in (0,1): 23 random bits, centred in their interval */
+static float u01f(uint32_t w) { return ((float)(w >> 9) + 0.5f) * 0x1p-23f; }
+/* uniform in (0,1) with 52 random bits */
+static double u01d(uint32_t w0, uint32_t w1) {
+  uint64_t k = ((uint64_t)(w0 >> 4) << 24) | (uint64_t)(w1 >> 8);
+  return ((double)k + 0.5) * 0x1p-52;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP32 logarithm and exponential from IEEE +,-,*,/ only, so that decisions   */
+/* taken on them are reproducible on any IEEE machine.                         */
+/*  ln x  = e ln 2 + 2 atanh(s),  s = (m-1)/(m+1),  m in [1/sqrt2, sqrt2)      */
+/*          (atanh series to s^11)                                             */
+/*  exp y = 2^k exp(r),  k = nearest integer to y/ln2, r = y - k ln2            */
+/*          (Taylor series to r^7)                                             */
+/*  ln 2 is split as LN2_HI + LN2_LO with LN2_HI = ln 2 truncated to 16 bits,  */
+/*  so that k LN2_HI is exact for |k| <= 255 (Cody and Waite 1980).            */
+/* ------------------------------------------------------------------------- */
+float orc_lnf(float x) {
+  uint32_t b;
+  memcpy(&b, &x, 4);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  if (e == -127) return -87.3365448f; /* zero or subnormal: ln(2^-126) */
+  uint32_t mb = (b & 0x7fffffu) | 0x3f800000u;
+  float m;
+  memcpy(&m, &mb, 4);
+  if (m > 1.41421356f) {
+    m = m * 0.5f;
+    e = e + 1;
+  }
+  float s = (m - 1.0f) / (m + 1.0f);
+  float z = s * s;
+  float p = 0.0909090909f;
+  p = p * z + 0.111111111f;
+  p = p * z + 0.142857143f;
+  p = p * z + 0.2f;
+  p = p * z + 0.333333333f;
+  p = p * z + 1.0f;
+  float lnm = (2.0f * s) * p;
+  float fe = (float)e;
+  return fe * 0.693145751953125f + (lnm + fe * 1.42860677e-6f);
+}
+
+float orc_expf(float y) {
+  if (y < -87.0f) return 0.0f;
+  if (y > 88.0f) y = 88.0f;
+  float t = y * 1.44269504f;
+  int k = (int)(t >= 0.0f ? t + 0.5f : t - 0.5f);
+  float fk = (float)k;
+  float r = (y - fk * 0.693145751953125f) - fk * 1.42860677e-6f;
+  float p = 1.98412698e-4f;
+  p = p * r + 1.38888889e-3f;
+  p = p * r + 8.33333333e-3f;
+  p = p * r + 4.16666667e-2f;
+  p = p * r + 0.166666667f;
+  p = p * r + 0.5f;
+  p = p * r + 1.0f;
+  p = p * r + 1.0f;
+  uint32_t sb = (uint32_t)(k + 127) << 23;
+  float sc;
+  memcpy(&sc, &sb, 4);
+  return p * sc;
+}
+
+float orc_powf(float x, float a) { return orc_expf(a * orc_lnf(x)); }
+
+/* ------------------------------------------------------------------------- */
+/* context                                                                     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t tet, face, bc;
+  float nrm[3], t1[3], t2[3]; /* outward unit normal and tangent basis (FP32) */
+} bface_t;
+
+#define NPHI_MAX 17
+#define NMAC 20
+
+struct orc_ctx {
+  orc_config cfg;
+  char err[256];
+  /* mesh */
+  int64_t n_tets, n_nodes;
+  int32_t* nbr;      /* [4n] >=0 neighbour tet, <0: -1 - boundary-face index */
+  int8_t* nbr_face;  /* [4n] local face index in the neighbour */
+  double* pn;        /* [12n] outward unit normals */
+  double* pd;        /* [4n]  plane offsets: n.x = d on the face */
+  double* vol;       /* [n] */
+  double* cumvol;    /* [n] running sum of volumes */
+  double* fdtv;      /* [n] F_N dt / V_c */
+  double* nodes;
+  int32_t* tets;
+  int32_t n_bf;
+  bface_t* bf;
+  double* bflux;     /* [5 n_bf]: hits, momentum in (3), energy in (sum of incident minus reflected) */
+  orc_bc* bcs;
+  int32_t n_bcs;
+  float* bc_sigma;   /* sqrt(k T / m) per bc */
+  float* bc_U;       /* [3 n_bcs] */
+  /* gas constants (FP32 where the collision arithmetic uses them) */
+  float c_vhs, one_m_omega, cmax0, p_inel, lb_exp, hmr, T_init_f, sigma_init, u0f[3];
+  int nphi;
+  /* particles (sorted by cell between steps) */
+  int64_t N, cap;
+  double* x;
+  float* v;
+  float* Ir;
+  int32_t* cell;
+  int64_t* cstart; /* [n+1] */
+  /* collision state per cell */
+  float* cmax;
+  double* rem;
+  /* sampling */
+  double* phi_inst;
+  double* phi_ewma;
+  double* phi_win;
+  double* phi_cum;
+  int64_t n_ewma, n_win, n_cum;
+  /* debug pairs */
+  int64_t n_pairs, cap_pairs;
+  int32_t* pr; /* 4 per pair: cell, k, i, j */
+  uint8_t* pacc;
+  int64_t counters[ORC_N_COUNTERS];
+  int64_t step;
+};
+
+static void rng4(const orc_ctx* c, int purpose, uint32_t entity, uint32_t sub, uint32_t step,
+                 uint32_t draw, uint32_t out[4]) {
+  uint32_t key[2] = {(uint32_t)c->cfg.seed, (uint32_t)(c->cfg.seed >> 32) ^ ((uint32_t)purpose << 24)};
+  uint32_t ctr[4] = {entity, sub, step, draw};
+  orc_philox(ctr, key, out);
+}
+
+static int fail(orc_ctx* c, int code, const char* msg) {
+  snprintf(c->err, sizeof c->err, "%s", msg);
+  return code;
+}
+
+const char* orc_last_error(orc_ctx* c) { return c->err; }
+
+orc_ctx* orc_create(const orc_config* cfg) {
+  orc_ctx* c = (orc_ctx*)calloc(1, sizeof(orc_ctx));
+  c->cfg = *cfg;
+  if (c->cfg.max_cross <= 0) c->cfg.max_cross = 4096;
+  c->nphi = cfg->rot_dof > 0 ? 17 : 13;
+  const double m = cfg->mass, w = cfg->omega, mr = 0.5 * m;
+  /* VHS: sigma_T c_r = pi d^2 (2kT_ref/(m_r c_r^2))^(w-1/2) / Gamma(5/2-w) * c_r
+   *                  = C_vhs (c_r^2)^(1-w)                          (Bird 1994, eq. 4.63) */
+  double cv = M_PI * cfg->d_ref * cfg->d_ref * pow(2.0 * KB * cfg->T_ref / mr, w - 0.5) / tgamma(2.5 - w);
+  c->c_vhs = (float)cv;
+  c->one_m_omega = (float)(1.0 - w);
+  /* initial (sigma c_r)_max at c_0 = 2.5 sqrt(2 k T_init / m) */
+  float c0sq = (float)(6.25 * 2.0 * KB * cfg->T_init / m);
+  c->cmax0 = c->c_vhs * orc_powf(c0sq, c->one_m_omega);
+  /* Borgnakke-Larsen probability, Eq. inelastic_probability */
+  double a = cfg->alpha;
+  c->p_inel = (float)(a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0) * cfg->Z_rot));
+  c->lb_exp = (float)(1.0 / (2.5 - w));
+  c->hmr = (float)(0.5 * mr / KB); /* relative translational energy in kelvin per (m/s)^2 */
+  c->T_init_f = (float)cfg->T_init;
+  c->sigma_init = (float)sqrt(KB * cfg->T_init / m);
+  for (int i = 0; i < 3; ++i) c->u0f[i] = (float)cfg->u_init[i];
+  return c;
+}
+
+static void free_mesh(orc_ctx* c) {
+  free(c->nbr); free(c->nbr_face); free(c->pn); free(c->pd); free(c->vol); free(c->cumvol);
+  free(c->fdtv); free(c->nodes); free(c->tets); free(c->bf); free(c->bflux); free(c->bcs);
+  free(c->bc_sigma); free(c->bc_U); free(c->cstart); free(c->cmax); free(c->rem);
+  free(c->phi_inst); free(c->phi_ewma); free(c->phi_win); free(c->phi_cum);
+}
+
+void orc_destroy(orc_ctx* c) {
+  if (!c) return;
+  free_mesh(c);
+  free(c->x); free(c->v); free(c->Ir); free(c->cell); free(c->pr); free(c->pacc);
+  free(c);
+}
+
+int64_t orc_step_index(orc_ctx* c) { return c->step; }
+
+/* ------------------------------------------------------------------------- */
+/* mesh: neighbour table by matching sorted vertex triples, FP64 face planes  */
+/* ------------------------------------------------------------------------- */
+typedef struct { int32_t a, b, c2; int32_t tet, face; } fkey_t;
+
+static int fkey_cmp(const void* p, const void* q) {
+  const fkey_t* x = (const fkey_t*)p;
+  const fkey_t* y = (const fkey_t*)q;
+  if (x->a != y->a) return x->a < y->a ? -1 : 1;
+  if (x->b != y->b) return x->b < y->b ? -1 : 1;
+  if (x->c2 != y->c2) return x->c2 < y->c2 ? -1 : 1;
+  if (x->tet != y->tet) return x->tet < y->tet ? -1 : 1;
+  return x->face < y->face ? -1 : (x->face > y->face);
+}
+
+static void sort3(int32_t* v) {
+  int32_t t;
+  if (v[0] > v[1]) { t = v[0]; v[0] = v[1]; v[1] = t; }
+  if (v[1] > v[2]) { t = v[1]; v[1] = v[2]; v[2] = t; }
+  if (v[0] > v[1]) { t = v[0]; v[0] = v[1]; v[1] = t; }
+}
+
+int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_t* tets,
+                  int64_t n_tets, const int32_t* face_tag, const orc_bc* bcs, int32_t n_bcs) {
+  if (n_tets <= 0 || n_nodes <= 0) return fail(c, -1, "empty mesh");
+  free_mesh(c);
+  const int64_t n = n_tets;
+  c->n_tets = n;
+  c->n_nodes = n_nodes;
+  c->nodes = (double*)malloc(sizeof(double) * 3 * n_nodes);
+  memcpy(c->nodes, nodes, sizeof(double) * 3 * n_nodes);
+  c->tets = (int32_t*)malloc(sizeof(int32_t) * 4 * n);
+  memcpy(c->tets, tets, sizeof(int32_t) * 4 * n);
+  for (int64_t i = 0; i < 4 * n; ++i)
+    if (tets[i] < 0 || tets[i] >= n_nodes) return fail(c, -2, "tet vertex index out of range");
+  c->nbr = (int32_t*)malloc(sizeof(int32_t) * 4 * n);
+  c->nbr_face = (int8_t*)malloc(4 * n);
+  c->pn = (double*)malloc(sizeof(double) * 12 * n);
+  c->pd = (double*)malloc(sizeof(double) * 4 * n);
+  c->vol = (double*)malloc(sizeof(double) * n);
+  c->cumvol = (double*)malloc(sizeof(double) * n);
+  c->fdtv = (double*)malloc(sizeof(double) * n);
+  c->n_bcs = n_bcs;
+  c->bcs = (orc_bc*)malloc(sizeof(orc_bc) * (n_bcs > 0 ? n_bcs : 1));
+  memcpy(c->bcs, bcs, sizeof(orc_bc) * n_bcs);
+  c->bc_sigma = (float*)malloc(sizeof(float) * (n_bcs > 0 ? n_bcs : 1));
+  c->bc_U = (float*)malloc(sizeof(float) * 3 * (n_bcs > 0 ? n_bcs : 1));
+  for (int b = 0; b < n_bcs; ++b) {
+    c->bc_sigma[b] = (float)sqrt(KB * bcs[b].T / c->cfg.mass);
+    for (int i = 0; i < 3; ++i) c->bc_U[3 * b + i] = (float)bcs[b].U[i];
+  }
+
+  /* volumes: V = |det(b-a, c-a, d-a)| / 6 */
+  for (int64_t t = 0; t < n; ++t) {
+    const double* A = nodes + 3 * tets[4 * t + 0];
+    const double* B = nodes + 3 * tets[4 * t + 1];
+    const double* C = nodes + 3 * tets[4 * t + 2];
+    const double* D = nodes + 3 * tets[4 * t + 3];
+    double u[3], v[3], w[3];
+    for (int i = 0; i < 3; ++i) { u[i] = B[i] - A[i]; v[i] = C[i] - A[i]; w[i] = D[i] - A[i]; }
+    double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                 u[2] * (v[0] * w[1] - v[1] * w[0]);
+    double V = fabs(det) / 6.0;
+    if (!(V > 0.0)) return fail(c, -2, "degenerate tetrahedron (zero volume)");
+    c->vol[t] = V;
+    c->cumvol[t] = (t == 0 ? 0.0 : c->cumvol[t - 1]) + V;
+    c->fdtv[t] = c->cfg.F_N * c->cfg.dt / V;
+  }
+
+  /* face planes: face f is opposite local vertex f; its vertices in increasing
+   * local order (a, b, c); n = (b-a) x (c-a), flipped to point away from the
+   * opposite vertex, normalised; d = n . a */
+  for (int64_t t = 0; t < n; ++t) {
+    for (int f = 0; f < 4; ++f) {
+      int lv[3], k = 0;
+      for (int q = 0; q < 4; ++q)
+        if (q != f) lv[k++] = q;
+      const double* A = nodes + 3 * tets[4 * t + lv[0]];
+      const double* B = nodes + 3 * tets[4 * t + lv[1]];
+      const double* C = nodes + 3 * tets[4 * t + lv[2]];
+      const double* P = nodes + 3 * tets[4 * t + f];
+      double e1[3], e2[3], nn[3];
+      for (int i = 0; i < 3; ++i) { e1[i] = B[i] - A[i]; e2[i] = C[i] - A[i]; }
+      nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+      nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+      nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+      double side = nn[0] * (P[0] - A[0]) + nn[1] * (P[1] - A[1]) + nn[2] * (P[2] - A[2]);
+      if (side > 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+      double len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+      nn[0] = nn[0] / len; nn[1] = nn[1] / len; nn[2] = nn[2] / len;
+      double* N = c->pn + 12 * t + 3 * f;
+      N[0] = nn[0]; N[1] = nn[1]; N[2] = nn[2];
+      c->pd[4 * t + f] = nn[0] * A[0] + nn[1] * A[1] + nn[2] * A[2];
+    }
+  }
+
+  /* neighbours: sort all faces by their vertex triple; equal triples pair up */
+  fkey_t* keys = (fkey_t*)malloc(sizeof(fkey_t) * 4 * n);
+  for (int64_t t = 0; t < n; ++t)
+    for (int f = 0; f < 4; ++f) {
+      int32_t v3[3], k = 0;
+      for (int q = 0; q < 4; ++q)
+        if (q != f) v3[k++] = tets[4 * t + q];
+      sort3(v3);
+      fkey_t* K = keys + 4 * t + f;
+      K->a = v3[0]; K->b = v3[1]; K->c2 = v3[2]; K->tet = (int32_t)t; K->face = f;
+    }
+  qsort(keys, (size_t)(4 * n), sizeof(fkey_t), fkey_cmp);
+  for (int64_t i = 0; i < 4 * n; ++i) c->nbr[i] = INT32_MIN;
+  int64_t nb = 0;
+  for (int64_t i = 0; i < 4 * n;) {
+    int64_t j = i + 1;
+    while (j < 4 * n && keys[j].a == keys[i].a && keys[j].b == keys[i].b && keys[j].c2 == keys[i].c2) ++j;
+    if (j - i > 2) { free(keys); return fail(c, -2, "non-manifold face (shared by more than two tets)"); }
+    if (j - i == 2) {
+      fkey_t* P = keys + i;
+      fkey_t* Q = keys + i + 1;
+      if (face_tag[4 * P->tet + P->face] >= 0 || face_tag[4 * Q->tet + Q->face] >= 0) {
+        free(keys); return fail(c, -2, "interior face carries a boundary tag");
+      }
+      c->nbr[4 * P->tet + P->face] = Q->tet; c->nbr_face[4 * P->tet + P->face] = (int8_t)Q->face;
+      c->nbr[4 * Q->tet + Q->face] = P->tet; c->nbr_face[4 * Q->tet + Q->face] = (int8_t)P->face;
+    } else {
+      int32_t tag = face_tag[4 * keys[i].tet + keys[i].face];
+      if (tag < 0 || tag >= n_bcs) { free(keys); return fail(c, -2, "boundary face without a valid tag"); }
+      ++nb;
+    }
+    i = j;
+  }
+  free(keys);
+  /* boundary faces in (tet, face) order */
+  c->n_bf = (int32_t)nb;
+  c->bf = (bface_t*)malloc(sizeof(bface_t) * (nb > 0 ? nb : 1));
+  c->bflux = (double*)calloc(5 * (nb > 0 ? nb : 1), sizeof(double));
+  int32_t ib = 0;
+  for (int64_t t = 0; t < n; ++t)
+    for (int f = 0; f < 4; ++f) {
+      if (c->nbr[4 * t + f] != INT32_MIN) continue;
+      bface_t* B = c->bf + ib;
+      B->tet = (int32_t)t; B->face = f; B->bc = face_tag[4 * t + f];
+      const double* N = c->pn + 12 * t + 3 * f;
+      /* tangent basis: t1 = normalised (a - (a.n) n) with a = e_x unless |n_x| >= 0.9
+       * (then e_y); t2 = n x t1 */
+      double a[3] = {1.0, 0.0, 0.0};
+      if (fabs(N[0]) >= 0.9) { a[0] = 0.0; a[1] = 1.0; }
+      double an = a[0] * N[0] + a[1] * N[1] + a[2] * N[2];
+      double t1[3] = {a[0] - an * N[0], a[1] - an * N[1], a[2] - an * N[2]};
+      double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+      t1[0] = t1[0] / l1; t1[1] = t1[1] / l1; t1[2] = t1[2] / l1;
+      double t2[3] = {N[1] * t1[2] - N[2] * t1[1], N[2] * t1[0] - N[0] * t1[2], N[0] * t1[1] - N[1] * t1[0]};
+      for (int i = 0; i < 3; ++i) { B->nrm[i] = (float)N[i]; B->t1[i] = (float)t1[i]; B->t2[i] = (float)t2[i]; }
+      c->nbr[4 * t + f] = -1 - ib;
+      c->nbr_face[4 * t + f] = (int8_t)f;
+      ++ib;
+    }
+
+  /* per-cell state */
+  c->cstart = (int64_t*)calloc(n + 1, sizeof(int64_t));
+  c->cmax = (float*)malloc(sizeof(float) * n);
+  c->rem = (double*)calloc(n, sizeof(double));
+  for (int64_t t = 0; t < n; ++t) c->cmax[t] = c->cmax0;
+  c->phi_inst = (double*)calloc(NPHI_MAX * n, sizeof(double));
+  c->phi_ewma = (double*)calloc(NPHI_MAX * n, sizeof(double));
+  c->phi_win = (double*)calloc(NPHI_MAX * n, sizeof(double));
+  c->phi_cum = (double*)calloc(NPHI_MAX * n, sizeof(double));
+  c->n_ewma = c->n_win = c->n_cum = 0;
+  return 0;
+}
+
+int orc_mesh_info(orc_ctx* c, int32_t* nbr, int8_t* nbr_face, double* normals, double* d, double* vol) {
+  int64_t n = c->n_tets;
+  if (nbr) memcpy(nbr, c->nbr, sizeof(int32_t) * 4 * n);
+  if (nbr_face) memcpy(nbr_face, c->nbr_face, 4 * n);
+  if (normals) memcpy(normals, c->pn, sizeof(double) * 12 * n);
+  if (d) memcpy(d, c->pd, sizeof(double) * 4 * n);
+  if (vol) memcpy(vol, c->vol, sizeof(double) * n);
+  return c->n_bf;
+}
+
+/* brute-force point location: first tet whose four plane tests pass within tol */
+int32_t orc_locate(orc_ctx* c, const double* x, double tol) {
+  for (int64_t t = 0; t < c->n_tets; ++t) {
+    int in = 1;
+    for (int f = 0; f < 4 && in; ++f) {
+      const double* N = c->pn + 12 * t + 3 * f;
+      double s = c->pd[4 * t + f] - (N[0] * x[0] + N[1] * x[1] + N[2] * x[2]);
+      if (s < -tol) in = 0;
+    }
+    if (in) return (int32_t)t;
+  }
+  return -1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* particle storage                                                            */
+/* ------------------------------------------------------------------------- */
+static void ensure_cap(orc_ctx* c, int64_t n) {
+  if (n <= c->cap) return;
+  int64_t cap = n + n / 2 + 16;
+  c->x = (double*)realloc(c->x, sizeof(double) * 3 * cap);
+  c->v = (float*)realloc(c->v, sizeof(float) * 3 * cap);
+  c->Ir = (float*)realloc(c->Ir, sizeof(float) * cap);
+  c->cell = (int32_t*)realloc(c->cell, sizeof(int32_t) * cap);
+  c->cap = cap;
+}
+
+/* Stable counting sort of the particle array by key = 2 cell + moved, so that
+ * in every cell the particles that stayed come first, in their previous
+ * order, followed by the arrivals (including newly created particles), in
+ * their previous order.  Particles with cell < 0 are removed.  The paper's
+ * per-cell particle buckets (Listing 2) are this array cut at cstart. */
+static void sort_particles(orc_ctx* c, const uint8_t* moved) {
+  const int64_t n = c->n_tets, N = c->N;
+  int64_t* cnt = (int64_t*)calloc(2 * n + 1, sizeof(int64_t));
+  for (int64_t p = 0; p < N; ++p)
+    if (c->cell[p] >= 0) cnt[2 * (int64_t)c->cell[p] + (moved ? moved[p] : 1) + 1]++;
+  for (int64_t k = 0; k < 2 * n; ++k) cnt[k + 1] += cnt[k];
+  int64_t M = cnt[2 * n];
+  double* x = (double*)malloc(sizeof(double) * 3 * (M > 0 ? M : 1));
+  float* v = (float*)malloc(sizeof(float) * 3 * (M > 0 ? M : 1));
+  float* Ir = (float*)malloc(sizeof(float) * (M > 0 ? M : 1));
+  int32_t* cl = (int32_t*)malloc(sizeof(int32_t) * (M > 0 ? M : 1));
+  for (int64_t p = 0; p < N; ++p) {
+    if (c->cell[p] < 0) continue;
+    int64_t key = 2 * (int64_t)c->cell[p] + (moved ? moved[p] : 1);
+    int64_t q = cnt[key]++;
+    memcpy(x + 3 * q, c->x + 3 * p, 3 * sizeof(double));
+    memcpy(v + 3 * q, c->v + 3 * p, 3 * sizeof(float));
+    Ir[q] = c->Ir[p];
+    cl[q] = c->cell[p];
+  }
+  memcpy(c->x, x, sizeof(double) * 3 * M);
+  memcpy(c->v, v, sizeof(float) * 3 * M);
+  memcpy(c->Ir, Ir, sizeof(float) * M);
+  memcpy(c->cell, cl, sizeof(int32_t) * M);
+  c->N = M;
+  free(x); free(v); free(Ir); free(cl); free(cnt);
+  for (int64_t t = 0; t <= n; ++t) c->cstart[t] = 0;
+  for (int64_t p = 0; p < M; ++p) c->cstart[c->cell[p] + 1]++;
+  for (int64_t t = 0; t < n; ++t) c->cstart[t + 1] += c->cstart[t];
+}
+
+/* Gaussian pair by Marsaglia's polar method; attempts use successive draws,
+ * two attempts per Philox block. */
+static uint32_t gauss2(const orc_ctx* c, int purpose, uint32_t ent, uint32_t sub, uint32_t step,
+                       uint32_t draw0, float* g1, float* g2) {
+  for (uint32_t d = draw0; d < draw0 + 32; ++d) {
+    uint32_t w[4];
+    rng4(c, purpose, ent, sub, step, d, w);
+    for (int a = 0; a < 2; ++a) {
+      float u1 = 2.0f * u01f(w[2 * a]) - 1.0f;
+      float u2 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
+      float s = u1 * u1 + u2 * u2;
+      if (s < 1.0f && s > 0.0f) {
+        float f = sqrtf(-2.0f * orc_lnf(s) / s);
+        *g1 = u1 * f;
+        *g2 = u2 * f;
+        return d + 1;
+      }
+    }
+  }
+  *g1 = 0.0f;
+  *g2 = 0.0f;
+  return draw0 + 32;
+}
+
+/* isotropic unit vector (Marsaglia 1972): (a,b) uniform in the unit disc,
+ * e = (2a sqrt(1-s), 2b sqrt(1-s), 1-2s) with s = a^2 + b^2 */
+static void unit_vector(const orc_ctx* c, int purpose, uint32_t ent, uint32_t sub, uint32_t step, float* e) {
+  for (uint32_t d = 0; d < 32; ++d) {
+    uint32_t w[4];
+    rng4(c, purpose, ent, sub, step, d, w);
+    for (int a = 0; a < 2; ++a) {
+      float a1 = 2.0f * u01f(w[2 * a]) - 1.0f;
+      float b1 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
+      float s = a1 * a1 + b1 * b1;
+      if (s < 1.0f) {
+        float r = 2.0f * sqrtf(1.0f - s);
+        e[0] = a1 * r;
+        e[1] = b1 * r;
+        e[2] = 1.0f - 2.0f * s;
+        return;
+      }
+    }
+  }
+  e[0] = 0.0f; e[1] = 0.0f; e[2] = 1.0f;
+}
+
+/* ------------------------------------------------------------------------- */
+/* S0: initial state (paper Sec. 5.1: uniform equilibrium; Alg. 1 line       */
+/* "initialise the macroscopic state and DSMC particle state")                */
+/* ------------------------------------------------------------------------- */
+int orc_particles_init(orc_ctx* c, int64_t n) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  if (n < 0) return fail(c, -1, "negative particle count");
+  ensure_cap(c, n);
+  const int64_t nt = c->n_tets;
+  const double Vtot = c->cumvol[nt - 1];
+  for (int64_t p = 0; p < n; ++p) {
+    uint32_t w[4], w2[4];
+    /* cell by inverse CDF of the cumulative volume: smallest c with cum[c] > R V */
+    rng4(c, RP_INIT_POS, (uint32_t)p, 0, 0, 0, w);
+    double target = u01d(w[0], w[1]) * Vtot;
+    int64_t lo = 0, hi = nt - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) / 2;
+      if (c->cumvol[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    int64_t t = lo;
+    /* uniform point in the tet (Rocchini and Cignoni 2000, folding the unit cube) */
+    rng4(c, RP_INIT_POS, (uint32_t)p, 1, 0, 0, w);
+    rng4(c, RP_INIT_POS, (uint32_t)p, 2, 0, 0, w2);
+    double s = u01d(w[0], w[1]), tt = u01d(w[2], w[3]), u = u01d(w2[0], w2[1]);
+    if (s + tt > 1.0) { s = 1.0 - s; tt = 1.0 - tt; }
+    if (tt + u > 1.0) {
+      double tmp = u; u = 1.0 - s - tt; tt = 1.0 - tmp;
+    } else if (s + tt + u > 1.0) {
+      double tmp = u; u = s + tt + u - 1.0; s = 1.0 - tt - tmp;
+    }
+    const double* A = c->nodes + 3 * c->tets[4 * t + 0];
+    const double* B = c->nodes + 3 * c->tets[4 * t + 1];
+    const double* C = c->nodes + 3 * c->tets[4 * t + 2];
+    const double* D = c->nodes + 3 * c->tets[4 * t + 3];
+    for (int i = 0; i < 3; ++i)
+      c->x[3 * p + i] = A[i] + s * (B[i] - A[i]) + tt * (C[i] - A[i]) + u * (D[i] - A[i]);
+    /* Maxwellian velocity at T_init around u_init; rotational energy (in kelvin)
+     * exponential with mean T_init (two rotational degrees of freedom) */
+    float g[4];
+    gauss2(c, RP_INIT_VEL, (uint32_t)p, 0, 0, 0, &g[0], &g[1]);
+    gauss2(c, RP_INIT_VEL, (uint32_t)p, 1, 0, 0, &g[2], &g[3]);
+    for (int i = 0; i < 3; ++i) c->v[3 * p + i] = c->u0f[i] + c->sigma_init * g[i];
+    rng4(c, RP_INIT_VEL, (uint32_t)p, 2, 0, 0, w);
+    c->Ir[p] = c->cfg.rot_dof > 0 ? -c->T_init_f * orc_lnf(u01f(w[0])) : 0.0f;
+    c->cell[p] = (int32_t)t;
+  }
+  c->N = n;
+  sort_particles(c, NULL);
+  return 0;
+}
+
+int orc_write_particles(orc_ctx* c, const double* x, const float* v, const float* Ir,
+                        const int32_t* cell, int64_t n) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  ensure_cap(c, n);
+  for (int64_t p = 0; p < n; ++p)
+    if (cell[p] < 0 || cell[p] >= c->n_tets) return fail(c, -1, "cell index out of range");
+  memcpy(c->x, x, sizeof(double) * 3 * n);
+  memcpy(c->v, v, sizeof(float) * 3 * n);
+  if (Ir) memcpy(c->Ir, Ir, sizeof(float) * n); else memset(c->Ir, 0, sizeof(float) * n);
+  memcpy(c->cell, cell, sizeof(int32_t) * n);
+  c->N = n;
+  sort_particles(c, NULL);
+  return 0;
+}
+
+int orc_read_particles(orc_ctx* c, double* x, float* v, float* Ir, int32_t* cell, int64_t cap, int64_t* n) {
+  *n = c->N;
+  if (cap < c->N) return fail(c, -3, "buffer too small");
+  if (x) memcpy(x, c->x, sizeof(double) * 3 * c->N);
+  if (v) memcpy(v, c->v, sizeof(float) * 3 * c->N);
+  if (Ir) memcpy(Ir, c->Ir, sizeof(float) * c->N);
+  if (cell) memcpy(cell, c->cell, sizeof(int32_t) * c->N);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* S2/S3: face-by-face tracking with wall interaction                         */
+/* (paper Sec. 4: particles traced face by face through the cells; fully      */
+/* diffuse isothermal walls, Sec. 5)                                          */
+/* ------------------------------------------------------------------------- */
+static double dot3(const double* n, const double* y) { return fma(n[2], y[2], fma(n[1], y[1], n[0] * y[0])); }
+
+/* wall interaction at boundary face ib; hit counts the hits of this particle in
+ * this step (it keys the random stream) */
+static void wall_reflect(orc_ctx* c, int32_t ib, float* v, float* Ir, uint32_t slot, uint32_t hit, uint32_t step) {
+  const bface_t* B = c->bf + ib;
+  const orc_bc* bc = c->bcs + B->bc;
+  float vin[3] = {v[0], v[1], v[2]};
+  float Iin = *Ir;
+  if (bc->kind == 1) {
+    /* specular: v <- v - 2 (v.n) n */
+    float vn = v[0] * B->nrm[0] + v[1] * B->nrm[1] + v[2] * B->nrm[2];
+    float h = 2.0f * vn;
+    for (int i = 0; i < 3; ++i) v[i] = v[i] - h * B->nrm[i];
+  } else {
+    /* diffuse at T_w: normal speed from the flux-weighted half-range Maxwellian,
+     * tangential Gaussian components, plus the wall velocity */
+    uint32_t w[4];
+    rng4(c, RP_WALL, slot, hit, step, 0, w);
+    float sg = c->bc_sigma[B->bc];
+    float vn = sg * sqrtf(-2.0f * orc_lnf(u01f(w[0])));
+    float g1, g2;
+    gauss2(c, RP_WALL, slot, hit, step, 1, &g1, &g2);
+    float a = sg * g1, b = sg * g2;
+    const float* U = c->bc_U + 3 * B->bc;
+    for (int i = 0; i < 3; ++i) v[i] = ((U[i] + B->t1[i] * a) + B->t2[i] * b) - B->nrm[i] * vn;
+    if (c->cfg.rot_dof > 0) *Ir = -(float)bc->T * orc_lnf(u01f(w[1]));
+  }
+  /* wall flux bookkeeping (incident minus reflected), per boundary face */
+  double* F = c->bflux + 5 * ib;
+  const double m = c->cfg.mass * c->cfg.F_N;
+  double ein = 0.0, eout = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    F[1 + i] += m * ((double)vin[i] - (double)v[i]);
+    ein += (double)vin[i] * vin[i];
+    eout += (double)v[i] * v[i];
+  }
+  F[0] += 1.0;
+  F[4] += 0.5 * m * (ein - eout) + c->cfg.F_N * KB * ((double)Iin - (double)*Ir);
+  c->counters[ORC_C_WALL]++;
+}
+
+/* Track one particle for one time step.  Returns the final cell, or -1 if it
+ * left through a free-stream / outflow face.  The algorithm:
+ *   repeat: x' = x + v t_rem (fma per component).  If x' passes the plane
+ *   tests d_f - n_f.x' >= 0 of every face f other than the entry face, stop at
+ *   x'.  Otherwise the exit face is the one with the smallest
+ *   t_f = max(0, (d_f - n_f.x)/(n_f.v)) among faces with n_f.v > 0 (ties: lowest
+ *   f); if none, or t_f >= t_rem, stop at x'.  Else advance to the face,
+ *   t_rem -= t_f, and enter the neighbour (entry face = its matching face), or
+ *   reflect at a wall (entry face = the wall face), or leave the domain. */
+static int32_t track(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, uint32_t slot, uint32_t step) {
+  double t = c->cfg.dt;
+  int entry = -1;
+  uint32_t hits = 0;
+  for (int32_t ncross = 0;; ++ncross) {
+    if (ncross > c->cfg.max_cross) {
+      c->counters[ORC_C_STUCK]++;
+      return cell;
+    }
+    const double vd[3] = {(double)v[0], (double)v[1], (double)v[2]};
+    double xn[3];
+    for (int i = 0; i < 3; ++i) xn[i] = fma(vd[i], t, x[i]);
+    const double* N = c->pn + 12 * (int64_t)cell;
+    const double* Dp = c->pd + 4 * (int64_t)cell;
+    int inside = 1;
+    for (int f = 0; f < 4; ++f) {
+      if (f == entry) continue;
+      if (Dp[f] - dot3(N + 3 * f, xn) < 0.0) inside = 0;
+    }
+    if (inside) {
+      x[0] = xn[0]; x[1] = xn[1]; x[2] = xn[2];
+      return cell;
+    }
+    int best = -1;
+    double tb = 0.0;
+    for (int f = 0; f < 4; ++f) {
+      if (f == entry) continue;
+      double b = dot3(N + 3 * f, vd);
+      if (!(b > 0.0)) continue;
+      double a = Dp[f] - dot3(N + 3 * f, x);
+      double tf = a / b;
+      if (tf < 0.0) tf = 0.0;
+      if (best < 0 || tf < tb) { best = f; tb = tf; }
+    }
+    if (best < 0 || tb >= t) {
+      x[0] = xn[0]; x[1] = xn[1]; x[2] = xn[2];
+      return cell;
+    }
+    for (int i = 0; i < 3; ++i) x[i] = fma(vd[i], tb, x[i]);
+    t = t - tb;
+    c->counters[ORC_C_CROSS]++;
+    int32_t nb = c->nbr[4 * (int64_t)cell + best];
+    if (nb >= 0) {
+      entry = c->nbr_face[4 * (int64_t)cell + best];
+      cell = nb;
+      continue;
+    }
+    int32_t ib = -1 - nb;
+    int kind = c->bcs[c->bf[ib].bc].kind;
+    if (kind == 0 || kind == 1) {
+      wall_reflect(c, ib, v, Ir, slot, hits, step);
+      hits++;
+      entry = best;
+      continue;
+    }
+    c->counters[ORC_C_REMOVED]++;
+    return -1;
+  }
+}
+
+int orc_track_one(orc_ctx* c, double* x, float* v, int32_t* cell, int64_t slot, int64_t step) {
+  float Ir = 0.0f;
+  *cell = track(c, x, v, &Ir, *cell, (uint32_t)slot, (uint32_t)step);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* S5/S6: NTC collisions (Bird 1994, Sec. 11.1) with VHS cross sections and   */
+/* serial Borgnakke-Larsen exchange (paper Sec. 2.1, Eq. inelastic prob.)     */
+/* ------------------------------------------------------------------------- */
+static void record_pair(orc_ctx* c, int32_t cell, int32_t k, int32_t i, int32_t j, int acc) {
+  if (c->n_pairs >= c->cap_pairs) {
+    int64_t cap = c->cap_pairs * 2 + 1024;
+    c->pr = (int32_t*)realloc(c->pr, sizeof(int32_t) * 4 * cap);
+    c->pacc = (uint8_t*)realloc(c->pacc, cap);
+    c->cap_pairs = cap;
+  }
+  int32_t* r = c->pr + 4 * c->n_pairs;
+  r[0] = cell; r[1] = k; r[2] = i; r[3] = j;
+  c->pacc[c->n_pairs] = (uint8_t)acc;
+  c->n_pairs++;
+}
+
+static void collide_cell(orc_ctx* c, int64_t cell, uint32_t step, int record) {
+  const int64_t s0 = c->cstart[cell];
+  const int64_t N = c->cstart[cell + 1] - s0;
+  if (N < 2) return;
+  /* number of candidate pairs: 1/2 N (N-1) F_N (sigma c_r)_max dt / V_c plus the
+   * carried fractional remainder of this cell */
+  double X = (double)N * (double)(N - 1) * 0.5 * (double)c->cmax[cell] * c->fdtv[cell] + c->rem[cell];
+  double fl = floor(X);
+  c->rem[cell] = X - fl;
+  int64_t ncand = (int64_t)fl;
+  float* v = c->v + 3 * s0;
+  float* I = c->Ir + s0;
+  for (int64_t k = 0; k < ncand; ++k) {
+    uint32_t w[4];
+    rng4(c, RP_COLL, (uint32_t)cell, (uint32_t)k, step, 0, w);
+    int64_t i = (int64_t)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+    int64_t j = (int64_t)(((uint64_t)w[1] * (uint64_t)(N - 1)) >> 32);
+    if (j >= i) j = j + 1;
+    float g[3];
+    for (int q = 0; q < 3; ++q) g[q] = v[3 * i + q] - v[3 * j + q];
+    float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    float sc = g2 > 0.0f ? c->c_vhs * orc_powf(g2, c->one_m_omega) : 0.0f;
+    if (sc > c->cmax[cell]) c->cmax[cell] = sc;
+    float R = u01f(w[2]);
+    int acc = sc > R * c->cmax[cell];
+    c->counters[ORC_C_CAND]++;
+    if (record) record_pair(c, (int32_t)cell, (int32_t)k, (int32_t)i, (int32_t)j, acc);
+    if (!acc) continue;
+    c->counters[ORC_C_COLL]++;
+    if (c->cfg.rot_dof > 0) {
+      /* serial Borgnakke-Larsen: molecule i then j, each with probability
+       * P_inelastic; the collision energy E_c = E_tr + I is split with
+       * I'/E_c = 1 - R^(1/(5/2 - omega)) (two rotational degrees of freedom) */
+      uint32_t u[4];
+      rng4(c, RP_LB, (uint32_t)cell, (uint32_t)k, step, 0, u);
+      float Etr = g2 * c->hmr;
+      int64_t who[2] = {i, j};
+      for (int q = 0; q < 2; ++q) {
+        if (u01f(u[2 * q]) < c->p_inel) {
+          float Ec = Etr + I[who[q]];
+          float In = Ec * (1.0f - orc_powf(u01f(u[2 * q + 1]), c->lb_exp));
+          I[who[q]] = In;
+          Etr = Ec - In;
+          c->counters[ORC_C_LB]++;
+        }
+      }
+      g2 = Etr / c->hmr;
+    }
+    float cr = sqrtf(g2);
+    float e[3];
+    unit_vector(c, RP_DIR, (uint32_t)cell, (uint32_t)k, step, e);
+    float h = 0.5f * cr;
+    for (int q = 0; q < 3; ++q) {
+      float cm = (v[3 * i + q] + v[3 * j + q]) * 0.5f;
+      v[3 * i + q] = cm + h * e[q];
+      v[3 * j + q] = cm - h * e[q];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* S7/S8: summation variables (Eq. dsmc_temperatures, as raw sums) and their */
+/* time averages (Eq. exponential_average_moments, Eq. steady_average)       */
+/* Phi = [N, sum v_i (3), sum v_i^2 (3), sum vx vy, vx vz, vy vz,             */
+/*        sum |v|^2 v_i (3), (diatomic) sum I, sum I v_i (3)]                 */
+/* ------------------------------------------------------------------------- */
+static void sample_cells(orc_ctx* c, int flags) {
+  const int64_t n = c->n_tets;
+  const int np = c->nphi;
+  for (int64_t t = 0; t < n; ++t) {
+    double ph[NPHI_MAX];
+    memset(ph, 0, sizeof ph);
+    for (int64_t p = c->cstart[t]; p < c->cstart[t + 1]; ++p) {
+      double vx = c->v[3 * p], vy = c->v[3 * p + 1], vz = c->v[3 * p + 2];
+      double vv = vx * vx + vy * vy + vz * vz;
+      ph[0] += 1.0;
+      ph[1] += vx; ph[2] += vy; ph[3] += vz;
+      ph[4] += vx * vx; ph[5] += vy * vy; ph[6] += vz * vz;
+      ph[7] += vx * vy; ph[8] += vx * vz; ph[9] += vy * vz;
+      ph[10] += vv * vx; ph[11] += vv * vy; ph[12] += vv * vz;
+      if (np == 17) {
+        double I = c->Ir[p];
+        ph[13] += I; ph[14] += I * vx; ph[15] += I * vy; ph[16] += I * vz;
+      }
+    }
+    memcpy(c->phi_inst + NPHI_MAX * t, ph, sizeof ph);
+    if (flags & ORC_EWMA) {
+      double* E = c->phi_ewma + NPHI_MAX * t;
+      const double na = (double)c->cfg.n_a;
+      const double a = (na - 1.0) / na, b = 1.0 / na;
+      for (int q = 0; q < np; ++q) E[q] = c->n_ewma == 0 ? ph[q] : a * E[q] + b * ph[q];
+    }
+    if (flags & ORC_WINDOW) {
+      double* W = c->phi_win + NPHI_MAX * t;
+      for (int q = 0; q < np; ++q) W[q] += ph[q];
+    }
+    if (flags & ORC_CUMUL) {
+      double* C = c->phi_cum + NPHI_MAX * t;
+      for (int q = 0; q < np; ++q) C[q] += ph[q];
+    }
+  }
+  if (flags & ORC_EWMA) c->n_ewma++;
+  if (flags & ORC_WINDOW) c->n_win++;
+  if (flags & ORC_CUMUL) c->n_cum++;
+}
+
+int orc_sample(orc_ctx* c, int32_t action) {
+  const int64_t m = NPHI_MAX * c->n_tets;
+  if (action & ORC_RESET_WINDOW) { memset(c->phi_win, 0, sizeof(double) * m); c->n_win = 0; }
+  if (action & ORC_RESET_CUMUL) { memset(c->phi_cum, 0, sizeof(double) * m); c->n_cum = 0; }
+  if (action & ORC_RESET_EWMA) { memset(c->phi_ewma, 0, sizeof(double) * m); c->n_ewma = 0; }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* one DSMC time step: move (with walls / outflow), sort, collide, sample     */
+/* ------------------------------------------------------------------------- */
+int orc_dsmc_step(orc_ctx* c, int32_t n_steps, int32_t flags) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  int record = (flags & ORC_RECORD_PAIRS) != 0;
+  for (int32_t s = 0; s < n_steps; ++s) {
+    c->step += 1;
+    const uint32_t step = (uint32_t)c->step;
+    c->n_pairs = 0;
+    const int64_t N = c->N;
+    uint8_t* moved = (uint8_t*)malloc(N > 0 ? N : 1);
+    for (int64_t p = 0; p < N; ++p) {
+      int32_t old = c->cell[p];
+      int32_t nc = track(c, c->x + 3 * p, c->v + 3 * p, c->Ir + p, old, (uint32_t)p, step);
+      c->cell[p] = nc;
+      moved[p] = (uint8_t)(nc != old);
+    }
+    sort_particles(c, moved);
+    free(moved);
+    for (int64_t t = 0; t < c->n_tets; ++t) collide_cell(c, t, step, record);
+    sample_cells(c, flags & (ORC_EWMA | ORC_WINDOW | ORC_CUMUL));
+    c->counters[ORC_C_STEPS]++;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* read-out: raw summation variables, or the macroscopic moments derived from */
+/* averaged sums (Eq. dsmc_temperatures, dimensional):                        */
+/* [0] mean N, [1] rho, [2..4] u, [5] T_t, [6] T_r, [7] T, [8..13] sigma      */
+/* (xx,yy,zz,xy,xz,yz), [14..16] q_t, [17..19] q_r                            */
+/* ------------------------------------------------------------------------- */
+static void derive_macro(const orc_ctx* c, const double* ph, double V, double* M) {
+  const double m = c->cfg.mass, FN = c->cfg.F_N;
+  memset(M, 0, sizeof(double) * NMAC);
+  double N = ph[0];
+  M[0] = N;
+  if (!(N > 0.0)) return;
+  double u[3] = {ph[1] / N, ph[2] / N, ph[3] / N};
+  double vv[3][3];
+  vv[0][0] = ph[4] / N; vv[1][1] = ph[5] / N; vv[2][2] = ph[6] / N;
+  vv[0][1] = vv[1][0] = ph[7] / N; vv[0][2] = vv[2][0] = ph[8] / N; vv[1][2] = vv[2][1] = ph[9] / N;
+  double cc[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) cc[i][j] = vv[i][j] - u[i] * u[j];
+  double tr = cc[0][0] + cc[1][1] + cc[2][2];
+  double v2 = vv[0][0] + vv[1][1] + vv[2][2];
+  double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  double rho = m * FN * N / V;
+  M[1] = rho;
+  M[2] = u[0]; M[3] = u[1]; M[4] = u[2];
+  double Tt = m * tr / (3.0 * KB);
+  M[5] = Tt;
+  int dr = c->cfg.rot_dof;
+  double Tr = 0.0;
+  if (dr > 0) Tr = 2.0 * (ph[13] / N) / dr;
+  M[6] = Tr;
+  M[7] = (3.0 * Tt + dr * Tr) / (3.0 + dr);
+  M[8] = rho * (cc[0][0] - tr / 3.0);
+  M[9] = rho * (cc[1][1] - tr / 3.0);
+  M[10] = rho * (cc[2][2] - tr / 3.0);
+  M[11] = rho * cc[0][1];
+  M[12] = rho * cc[0][2];
+  M[13] = rho * cc[1][2];
+  for (int i = 0; i < 3; ++i) {
+    /* <c_i c^2> = <v_i v^2> - 2 u_j <v_i v_j> - u_i <v^2> + 2 u_i |u|^2 */
+    double uj = u[0] * vv[i][0] + u[1] * vv[i][1] + u[2] * vv[i][2];
+    double c3 = ph[10 + i] / N - 2.0 * uj - u[i] * v2 + 2.0 * u[i] * uu;
+    M[14 + i] = 0.5 * rho * c3;
+    if (dr > 0) M[17 + i] = (FN * N / V) * KB * (ph[14 + i] / N - u[i] * (ph[13] / N));
+  }
+}
+
+int orc_read_moments(orc_ctx* c, int32_t which, double* out, int64_t cap) {
+  const int64_t n = c->n_tets;
+  int base = which & 15;
+  const double* src = base == ORC_PHI_INST ? c->phi_inst
+                    : base == ORC_PHI_EWMA ? c->phi_ewma
+                    : base == ORC_PHI_WINDOW ? c->phi_win : c->phi_cum;
+  if (!(which & ORC_MACRO)) {
+    if (cap < NPHI_MAX * n) return fail(c, -3, "buffer too small");
+    memcpy(out, src, sizeof(double) * NPHI_MAX * n);
+    return 0;
+  }
+  if (cap < NMAC * n) return fail(c, -3, "buffer too small");
+  double cnt = base == ORC_PHI_WINDOW ? (double)c->n_win : base == ORC_PHI_CUM ? (double)c->n_cum : 1.0;
+  for (int64_t t = 0; t < n; ++t) {
+    double ph[NPHI_MAX];
+    for (int q = 0; q < NPHI_MAX; ++q) ph[q] = cnt > 0 ? src[NPHI_MAX * t + q] / cnt : 0.0;
+    derive_macro(c, ph, c->vol[t], out + NMAC * t);
+  }
+  return 0;
+}
+
+int orc_read_pairs(orc_ctx* c, int32_t* cell, int32_t* k, int32_t* i, int32_t* j, uint8_t* acc,
+                   int64_t cap, int64_t* n) {
+  *n = c->n_pairs;
+  if (cap < c->n_pairs) return fail(c, -3, "buffer too small");
+  for (int64_t q = 0; q < c->n_pairs; ++q) {
+    cell[q] = c->pr[4 * q]; k[q] = c->pr[4 * q + 1]; i[q] = c->pr[4 * q + 2]; j[q] = c->pr[4 * q + 3];
+    acc[q] = c->pacc[q];
+  }
+  return 0;
+}
+
+int orc_read_counters(orc_ctx* c, int64_t* out, int32_t n) {
+  for (int32_t q = 0; q < n && q < ORC_N_COUNTERS; ++q) out[q] = c->counters[q];
+  return 0;
+}
+
+int orc_cell_state(orc_ctx* c, float* cmax, double* rem, int32_t write) {
+  const int64_t n = c->n_tets;
+  if (write) {
+    if (cmax) memcpy(c->cmax, cmax, sizeof(float) * n);
+    if (rem) memcpy(c->rem, rem, sizeof(double) * n);
+  } else {
+    if (cmax) memcpy(cmax, c->cmax, sizeof(float) * n);
+    if (rem) memcpy(rem, c->rem, sizeof(double) * n);
+  }
+  return 0;
+}
+
+int orc_wall_flux(orc_ctx* c, double* out, int64_t cap, int64_t* n_bfaces) {
+  *n_bfaces = c->n_bf;
+  if (cap < 5 * (int64_t)c->n_bf) return fail(c, -3, "buffer too small");
+  memcpy(out, c->bflux, sizeof(double) * 5 * c->n_bf);
+  return 0;
+}

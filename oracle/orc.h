@@ -1,0 +1,108 @@
+/*
+ * orc.h -- plain CPU oracle of the DIG-augmented DSMC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The
+ * product (paper_2607_08195_gb300, include/dig.h) never calls it and shares
+ * no code, header, table or constant generator with it.
+ *
+ * It follows the paper step by step, single threaded, in the paper's order
+ * (DSMC method, Sec. 2.1: move, then collide pairs in the same cell, then
+ * sample; statistical treatment, Sec. 3).  Positions and ray-face parameters
+ * are FP64, velocities and collision arithmetic FP32, sums FP64.  Compile with
+ * -O2 -ffp-contract=off (no -ffast-math): every floating-point decision is
+ * then a fixed sequence of IEEE operations.
+ *
+ * The interface mirrors the shape of the product's C ABI under the prefix
+ * orc_ but takes host memory.
+ */
+#ifndef ORC_H
+#define ORC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_config {
+  double mass;      /* molecular mass, kg */
+  double d_ref;     /* VHS reference diameter, m */
+  double omega;     /* viscosity index */
+  double T_ref;     /* reference temperature of d_ref, K */
+  double alpha;     /* VSS scattering parameter (1 = VHS) */
+  double Z_rot;     /* rotational collision number */
+  int32_t rot_dof;  /* 0 (monatomic) or 2 (diatomic) */
+  int32_t max_cross;/* face crossings allowed per particle per step */
+  double F_N;       /* real molecules per simulation particle */
+  double dt;        /* time step, s */
+  uint64_t seed;
+  double n_init;    /* initial number density, 1/m^3 (informative) */
+  double T_init;    /* initial temperature, K */
+  double u_init[3]; /* initial drift, m/s */
+  double mu_ref;    /* viscosity at T_ref, Pa s */
+  double Kn;        /* global Knudsen number */
+  double L_ref;     /* reference length, m */
+  int32_t n_a;      /* EWMA effective samples (Eq. exponential average) */
+  int32_t N_s;      /* DSMC steps per outer coupling cycle */
+  int32_t N_m;      /* maximum synthetic-solver iterations */
+  int32_t passes;   /* reconstruction passes for rejected cells */
+  double eps_m;     /* synthetic-solver residual tolerance */
+  double KnD_max;   /* cell Knudsen threshold of the reliability criterion */
+  int64_t capacity; /* particle capacity */
+} orc_config;
+
+typedef struct orc_bc {
+  int32_t kind;     /* 0 diffuse wall, 1 specular wall, 2 free-stream inflow, 3 outflow */
+  int32_t pad;
+  double T;         /* wall or free-stream temperature, K */
+  double U[3];      /* wall or free-stream velocity, m/s */
+  double n;         /* free-stream number density, 1/m^3 */
+} orc_bc;
+
+/* moment selectors for orc_read_moments */
+enum { ORC_PHI_INST = 0, ORC_PHI_EWMA = 1, ORC_PHI_WINDOW = 2, ORC_PHI_CUM = 3, ORC_MACRO = 16 };
+/* dsmc_step flags */
+enum { ORC_EWMA = 1, ORC_WINDOW = 2, ORC_CUMUL = 4, ORC_RECORD_PAIRS = 8 };
+/* sample() actions */
+enum { ORC_RESET_WINDOW = 1, ORC_RESET_CUMUL = 2, ORC_RESET_EWMA = 4 };
+/* counters */
+enum { ORC_C_STEPS, ORC_C_CAND, ORC_C_COLL, ORC_C_CROSS, ORC_C_WALL, ORC_C_REMOVED,
+       ORC_C_INJECTED, ORC_C_STUCK, ORC_C_LB, ORC_N_COUNTERS };
+
+typedef struct orc_ctx orc_ctx;
+
+orc_ctx* orc_create(const orc_config* cfg);
+void orc_destroy(orc_ctx* c);
+const char* orc_last_error(orc_ctx* c);
+
+int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_t* tets,
+                  int64_t n_tets, const int32_t* face_tag, const orc_bc* bcs, int32_t n_bcs);
+int orc_particles_init(orc_ctx* c, int64_t n);
+int orc_write_particles(orc_ctx* c, const double* x, const float* v, const float* Ir,
+                        const int32_t* cell, int64_t n);
+int orc_read_particles(orc_ctx* c, double* x, float* v, float* Ir, int32_t* cell, int64_t cap,
+                       int64_t* n);
+int orc_dsmc_step(orc_ctx* c, int32_t n_steps, int32_t flags);
+int orc_sample(orc_ctx* c, int32_t action);
+int orc_read_moments(orc_ctx* c, int32_t which, double* out, int64_t cap);
+int orc_read_pairs(orc_ctx* c, int32_t* cell, int32_t* k, int32_t* i, int32_t* j, uint8_t* acc,
+                   int64_t cap, int64_t* n);
+int orc_read_counters(orc_ctx* c, int64_t* out, int32_t n);
+int orc_cell_state(orc_ctx* c, float* cmax, double* rem, int32_t write);
+int orc_wall_flux(orc_ctx* c, double* out, int64_t cap, int64_t* n_bfaces);
+int64_t orc_step_index(orc_ctx* c);
+
+/* primitives exposed for the pins */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+float orc_lnf(float x);
+float orc_expf(float y);
+float orc_powf(float x, float a);
+int orc_mesh_info(orc_ctx* c, int32_t* nbr, int8_t* nbr_face, double* normals, double* d,
+                  double* vol);
+int32_t orc_locate(orc_ctx* c, const double* x, double tol);
+int orc_track_one(orc_ctx* c, double* x, float* v, int32_t* cell, int64_t slot, int64_t step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,189 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the bench.
+
+This module holds no step of the DSMC/DIG method itself: it builds the procedural
+meshes (node coordinates, tetrahedra, boundary tags) and the scenario parameters
+(gas constants, number density, time step, particle weight) that both sides take
+as inputs.  Everything is plain numpy; nothing here touches a GPU.
+
+Workloads (lid-driven cavity, paper Sec. 5.1, rescaled to a 1 mm argon cube):
+
+* ``cavity(nh)``: the cube [-L/2, L/2]^3 split into nh^3 hexahedra, each cut into
+  six Kuhn (Freudenthal) tetrahedra along its (0,0,0)-(1,1,1) diagonal, so the
+  triangulation is conforming across hexahedra.  All six walls are diffuse at
+  T_w; the wall y = +L/2 moves with velocity (U_w, 0, 0).
+* ``open_box(nh)``: the same mesh with every boundary face a free-stream inflow
+  face (used for the injection/outflow checks).
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import math
+
+import numpy as np
+
+K_B = 1.380649e-23  # J/K
+
+# boundary-condition kinds (same integer values in include/dig.h and the oracle header)
+BC_DIFFUSE, BC_SPECULAR, BC_INFLOW, BC_OUTFLOW = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Gas:
+    mass: float
+    d_ref: float
+    omega: float
+    T_ref: float
+    rot_dof: int = 0
+    Z_rot: float = 1.0
+    alpha: float = 1.0
+
+    def mu_ref(self) -> float:
+        """VHS viscosity at T_ref (Bird 1994, eq. 4.62): the scenario's mu_0."""
+        w = self.omega
+        return 15.0 * math.sqrt(math.pi * self.mass * K_B * self.T_ref) / (
+            2.0 * math.pi * self.d_ref ** 2 * (5.0 - 2.0 * w) * (7.0 - 2.0 * w))
+
+
+ARGON = Gas(mass=6.63e-26, d_ref=4.17e-10, omega=0.81, T_ref=273.0)
+NITROGEN = Gas(mass=4.65e-26, d_ref=4.17e-10, omega=0.74, T_ref=273.0, rot_dof=2, Z_rot=5.0)
+
+
+@dataclasses.dataclass
+class Mesh:
+    nodes: np.ndarray      # [n_nodes, 3] float64
+    tets: np.ndarray       # [n_tets, 4] int32
+    face_tag: np.ndarray   # [n_tets, 4] int32: -1 interior, else index into bcs; face f is opposite vertex f
+    bcs: list              # list of dicts: kind, T, U(3), n
+
+
+def kuhn_cube(nh: int, L: float):
+    """Nodes and Kuhn tetrahedra of the cube [-L/2, L/2]^3 cut into nh^3 hexahedra."""
+    g = np.linspace(-0.5 * L, 0.5 * L, nh + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    nodes = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float64)
+
+    def nid(i, j, k):
+        return (i * (nh + 1) + j) * (nh + 1) + k
+
+    i, j, k = np.meshgrid(np.arange(nh), np.arange(nh), np.arange(nh), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        # path v000 -> +e_p0 -> +e_p0+e_p1 -> v111
+        off = np.zeros((4, 3), dtype=np.int64)
+        off[1, perm[0]] = 1
+        off[2] = off[1]
+        off[2, perm[1]] = 1
+        off[3] = 1
+        tets.append(np.stack([nid(i + o[0], j + o[1], k + o[2]) for o in off], axis=1))
+    # hex-major order: the six tets of one hex are consecutive
+    tets = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return nodes, tets
+
+
+def boundary_side(nodes, tets, L):
+    """For each (tet, local face) the cube side it lies on (0..5 = -x,+x,-y,+y,-z,+z) or -1."""
+    h = 0.5 * L
+    side = np.full(tets.shape, -1, dtype=np.int32)
+    for f in range(4):
+        verts = [tets[:, v] for v in range(4) if v != f]
+        P = np.stack([nodes[v] for v in verts], axis=1)  # [n, 3 verts, 3 coords]
+        for ax in range(3):
+            for s, val in ((0, -h), (1, h)):
+                on = np.all(np.abs(P[:, :, ax] - val) <= 1e-12 * L, axis=1)
+                side[on, f] = 2 * ax + s
+    return side
+
+
+def cavity(nh: int, L: float = 1e-3, T_w: float = 273.0, U_lid: float = 50.0) -> Mesh:
+    nodes, tets = kuhn_cube(nh, L)
+    side = boundary_side(nodes, tets, L)
+    face_tag = np.where(side < 0, -1, 0).astype(np.int32)
+    face_tag[side == 3] = 1  # lid y = +L/2
+    bcs = [dict(kind=BC_DIFFUSE, T=T_w, U=(0.0, 0.0, 0.0), n=0.0),
+           dict(kind=BC_DIFFUSE, T=T_w, U=(U_lid, 0.0, 0.0), n=0.0)]
+    return Mesh(nodes, tets, face_tag, bcs)
+
+
+def closed_box(nh: int, L: float = 1e-3, kind: int = BC_SPECULAR, T_w: float = 273.0) -> Mesh:
+    nodes, tets = kuhn_cube(nh, L)
+    side = boundary_side(nodes, tets, L)
+    face_tag = np.where(side < 0, -1, 0).astype(np.int32)
+    bcs = [dict(kind=kind, T=T_w, U=(0.0, 0.0, 0.0), n=0.0)]
+    return Mesh(nodes, tets, face_tag, bcs)
+
+
+def open_box(nh: int, L: float, n_inf: float, T_inf: float, U_inf=(0.0, 0.0, 0.0)) -> Mesh:
+    nodes, tets = kuhn_cube(nh, L)
+    side = boundary_side(nodes, tets, L)
+    face_tag = np.where(side < 0, -1, 0).astype(np.int32)
+    bcs = [dict(kind=BC_INFLOW, T=T_inf, U=tuple(U_inf), n=n_inf)]
+    return Mesh(nodes, tets, face_tag, bcs)
+
+
+@dataclasses.dataclass
+class Scenario:
+    """Everything a run needs besides the mesh; the same values feed both sides."""
+    gas: Gas
+    mesh: Mesh
+    n_particles: int
+    n_init: float          # number density of the initial state, 1/m^3
+    T_init: float
+    u_init: tuple
+    F_N: float             # real molecules per simulation particle
+    dt: float              # s
+    seed: int
+    L: float
+    Kn: float
+    capacity: int = 0      # particle capacity (0: 2x n_particles)
+    name: str = ""
+
+
+def cavity_scenario(nh: int, n_particles: int, Kn: float, seed: int, L: float = 1e-3,
+                    gas: Gas = ARGON, T0: float = 273.0, U_lid: float = 50.0,
+                    dt_factor: float = 0.2, name: str = "") -> Scenario:
+    """Cavity at global Knudsen number Kn (paper eq. for Kn: mu0/(p0 L) sqrt(pi R T0 / 2)).
+
+    dt = dt_factor * mu0/p0 (the paper's mean collision time tau = mu/p_t)."""
+    mu0 = gas.mu_ref() * (T0 / gas.T_ref) ** gas.omega
+    R = K_B / gas.mass
+    p0 = mu0 / (Kn * L) * math.sqrt(math.pi * R * T0 / 2.0)
+    n0 = p0 / (K_B * T0)
+    F_N = n0 * L ** 3 / n_particles
+    dt = dt_factor * mu0 / p0
+    mesh = cavity(nh, L=L, T_w=T0, U_lid=U_lid)
+    return Scenario(gas=gas, mesh=mesh, n_particles=n_particles, n_init=n0, T_init=T0,
+                    u_init=(0.0, 0.0, 0.0), F_N=F_N, dt=dt, seed=seed, L=L, Kn=Kn,
+                    capacity=2 * n_particles, name=name or f"cavity{nh}")
+
+
+# The five configurations used by the tests and the bench.
+def config_small(seed: int = 1) -> Scenario:
+    """Argon cavity, 6^3 hexes x 6 tets = 1,296 tets, Kn = 0.1, 20,000 particles."""
+    return cavity_scenario(6, 20_000, 0.1, seed, name="cavity-6x6x6-Kn0.1-20k")
+
+
+def config_c2(seed: int = 2) -> Scenario:
+    """Argon cavity, 30^3 hexes x 6 tets = 162,000 tets, Kn = 0.01, 8M particles."""
+    return cavity_scenario(30, 8_000_000, 0.01, seed, name="cavity-30x30x30-Kn0.01-8M")
+
+
+def config_c3(seed: int = 3) -> Scenario:
+    """Argon cavity, 20^3 hexes x 6 tets = 48,000 tets, Kn = 0.001, 3M particles."""
+    return cavity_scenario(20, 3_000_000, 0.001, seed, name="cavity-20x20x20-Kn0.001-3M")
+
+
+def random_particles(rng: np.random.Generator, scen: Scenario, n: int):
+    """Arbitrary test states: uniform points inside random tets, Maxwellian velocities.
+
+    Returns (x[n,3] f64, v[n,3] f32, Ir[n] f32, cell[n] i32); order is random."""
+    m = scen.mesh
+    cell = rng.integers(0, len(m.tets), size=n).astype(np.int32)
+    w = rng.dirichlet(np.ones(4), size=n)
+    P = m.nodes[m.tets[cell]]  # [n, 4, 3]
+    x = np.einsum("nk,nkc->nc", w, P)
+    s = math.sqrt(K_B * scen.T_init / scen.gas.mass)
+    v = (rng.standard_normal((n, 3)) * s).astype(np.float32)
+    Ir = (rng.exponential(scen.T_init, size=n)).astype(np.float32)
+    return x, v, Ir, cell

@@ -1,0 +1,436 @@
+"""Pins of the CPU oracle against things fixed outside it: published known-answer
+vectors, closed forms of kinetic theory, invariants and brute force on tiny
+meshes.  No GPU needed.
+
+Each test names the property it checks and where that property comes from.
+"""
+import dataclasses
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import orc
+from paper_2607_08195_gb300 import workload as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+KB = W.K_B
+
+
+def box_scenario(nh=1, n_particles=6000, kind=W.BC_SPECULAR, gas=W.ARGON, T=273.0, n=1.677e22,
+                 dt_factor=0.2, seed=11, L=1e-3, F_N=None):
+    mesh = W.closed_box(nh, L=L, kind=kind, T_w=T)
+    mu = gas.mu_ref() * (T / gas.T_ref) ** gas.omega
+    p = n * KB * T
+    return W.Scenario(gas=gas, mesh=mesh, n_particles=n_particles, n_init=n, T_init=T,
+                      u_init=(0.0, 0.0, 0.0), F_N=F_N if F_N is not None else n * L ** 3 / n_particles,
+                      dt=dt_factor * mu / p, seed=seed, L=L, Kn=0.1, capacity=2 * n_particles)
+
+
+# --------------------------------------------------------------------------- RNG
+def test_philox_known_answers():
+    """Philox4x32-10 against the published known-answer vectors (Salmon et al. 2011)."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox_kat.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = orc.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+# ------------------------------------------------------------------- own ln / exp
+def test_own_log_exp_match_libm():
+    """The FP32 ln/exp used in collision decisions agree with the true functions
+    (closed form) to a few FP32 ulps over the ranges the collision arithmetic uses."""
+    xs = np.geomspace(1e-6, 1e12, 400)
+    for x in xs:
+        x32 = float(np.float32(x))
+        assert abs(orc.lnf(x32) - math.log(x32)) <= 2e-6 + 1e-7 * abs(math.log(x32))
+    for y in np.linspace(-30.0, 30.0, 401):
+        y32 = float(np.float32(y))
+        assert abs(orc.expf(y32) / math.exp(y32) - 1.0) <= 5e-7
+    for x in (1.0, 3.0, 1e4, 2.5e5):
+        assert abs(orc.powf(x, 0.19) / x ** 0.19 - 1.0) < 2e-6
+
+
+# ---------------------------------------------------------------------------- mesh
+def test_mesh_tables():
+    """Kuhn-split cube: volumes sum to L^3, the neighbour relation is symmetric,
+    normals are unit and point away from the tet, boundary faces = 12 nh^2."""
+    nh, L = 3, 1e-3
+    s = box_scenario(nh=nh, L=L)
+    o = orc.Oracle(s)
+    mi = o.mesh_info()
+    assert abs(mi["vol"].sum() / L ** 3 - 1.0) < 1e-12
+    assert mi["n_bfaces"] == 12 * nh * nh
+    nbr, nf = mi["nbr"], mi["nbr_face"]
+    for t in range(len(nbr)):
+        for f in range(4):
+            if nbr[t, f] >= 0:
+                assert nbr[nbr[t, f], nf[t, f]] == t
+                # the shared face's normals are opposite
+                assert np.allclose(mi["normals"][t, f], -mi["normals"][nbr[t, f], nf[t, f]], atol=1e-12)
+    assert np.allclose(np.linalg.norm(mi["normals"], axis=2), 1.0, atol=1e-14)
+    P = s.mesh.nodes[s.mesh.tets]
+    cen = P.mean(axis=1)
+    for f in range(4):
+        # centroid is strictly inside every face plane; the opposite vertex too
+        sd = mi["d"][:, f] - np.einsum("ni,ni->n", mi["normals"][:, f], cen)
+        assert np.all(sd > 0)
+        sv = mi["d"][:, f] - np.einsum("ni,ni->n", mi["normals"][:, f], P[:, f])
+        assert np.all(sv > 0)
+
+
+def test_mesh_rejects_bad_input():
+    s = box_scenario(nh=1)
+    bad = dataclasses.replace(s, mesh=dataclasses.replace(s.mesh, face_tag=np.full_like(s.mesh.face_tag, -1)))
+    with pytest.raises(RuntimeError, match="boundary face"):
+        orc.Oracle(bad)
+    nodes = s.mesh.nodes.copy()
+    tets = s.mesh.tets.copy()
+    tets[0, 3] = tets[0, 2]  # collapse a tet
+    with pytest.raises(RuntimeError, match="degenerate|non-manifold|boundary"):
+        orc.Oracle(dataclasses.replace(s, mesh=dataclasses.replace(s.mesh, nodes=nodes, tets=tets)))
+
+
+# ------------------------------------------------------------------- tracking
+def barycentric(nodes, tets, cell, x):
+    P = nodes[tets[cell]]  # [n, 4, 3]
+    T = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=2)
+    lam = np.linalg.solve(T, (x - P[:, 0])[..., None])[..., 0]
+    return np.concatenate([1.0 - lam.sum(axis=1, keepdims=True), lam], axis=1)
+
+
+def test_point_in_tet_brute_force():
+    """P7: after each step every particle lies inside the tet it was tracked to,
+    by barycentric coordinates computed from the nodes (independent of the
+    oracle's planes); diffuse walls, a moving lid and collisions on."""
+    s = W.cavity_scenario(2, 3000, 0.1, seed=5)
+    o = orc.Oracle(s)
+    o.init()
+    for _ in range(12):
+        o.step(1, orc.EWMA)
+        x, v, Ir, cell = o.read()
+        assert len(cell) == 3000
+        lam = barycentric(s.mesh.nodes, s.mesh.tets, cell, x)
+        assert lam.min() > -1e-9, lam.min()
+        assert np.all(np.diff(cell) >= 0)  # sorted by cell
+    c = o.counters()
+    assert c["cross"] > 0 and c["wall"] > 0 and c["coll"] > 0 and c["stuck"] == 0
+
+
+def test_specular_box_conserves_speed_and_free_flight():
+    """P8: specular walls on the axis-aligned cube conserve every particle's speed
+    exactly (the reflection flips one component); with collisions off the total
+    energy is conserved bit for bit; free flight with no crossing equals x + v dt
+    to 1 ulp."""
+    s = box_scenario(nh=2, n_particles=2000, F_N=1e-30)
+    o = orc.Oracle(s)
+    o.init()
+    x0, v0, _, _ = o.read()
+    sp0 = np.sort(np.linalg.norm(v0.astype(np.float64), axis=1))
+    o.step(30, 0)
+    x1, v1, _, _ = o.read()
+    assert o.counters()["coll"] == 0 and o.counters()["wall"] > 0
+    sp1 = np.sort(np.linalg.norm(v1.astype(np.float64), axis=1))
+    assert np.array_equal(sp0, sp1)
+    lam = barycentric(s.mesh.nodes, s.mesh.tets, o.read()[3], x1)
+    assert lam.min() > -1e-9
+    # free flight inside one cell
+    cen = s.mesh.nodes[s.mesh.tets[5]].mean(axis=0)
+    v = np.array([3.0, -2.0, 1.0], np.float32)
+    xn, vn, cn = o.track_one(cen, v, 5, 0, 1)
+    assert cn == 5
+    ref = cen + v.astype(np.float64) * s.dt
+    assert np.all(np.abs(xn - ref) <= np.spacing(np.abs(ref)))
+
+
+def test_diffuse_wall_distribution():
+    """Diffuse re-emission at T_w: normal speed has the flux-weighted half-range
+    Maxwellian law (mean sigma sqrt(pi/2), mean square 2 sigma^2); tangential
+    components are N(U_w, sigma^2)."""
+    s = W.cavity_scenario(1, 10, 0.1, seed=3, U_lid=100.0)
+    o = orc.Oracle(s)
+    mi = o.mesh_info()
+    # pick a tet with a lid face (+y side); the face normal is +y
+    tags = s.mesh.face_tag
+    t, f = [(t, f) for t in range(len(tags)) for f in range(4) if tags[t, f] == 1][0]
+    assert np.allclose(mi["normals"][t, f], [0, 1, 0])
+    cen = s.mesh.nodes[s.mesh.tets[t]].mean(axis=0)
+    vs = []
+    for slot in range(20000):
+        # particle shot straight at the lid with a short flight: one hit, then rebound
+        x, v, c = o.track_one(cen, np.array([0.0, 5000.0, 0.0], np.float32), t, slot, 7)
+        vs.append(v)
+    v = np.array(vs, np.float64)
+    sig = math.sqrt(KB * 273.0 / s.gas.mass)
+    vn = -v[:, 1]
+    assert np.all(vn > 0)
+    n = len(vn)
+    assert abs(vn.mean() - sig * math.sqrt(math.pi / 2)) < 4 * vn.std() / math.sqrt(n)
+    assert abs((vn ** 2).mean() - 2 * sig ** 2) < 4 * (vn ** 2).std() / math.sqrt(n)
+    assert abs(v[:, 0].mean() - 100.0) < 4 * sig / math.sqrt(n)
+    assert abs(v[:, 2].mean()) < 4 * sig / math.sqrt(n)
+    for comp in (0, 2):
+        assert abs(v[:, comp].std() / sig - 1.0) < 4 * 0.71 / math.sqrt(n)
+
+
+def test_diffuse_box_thermalises_without_collisions():
+    """P9: collisionless gas in a closed box with diffuse walls at T_w relaxes to
+    T = T_w and u = 0, whatever its initial temperature."""
+    mesh = W.closed_box(1, L=1e-3, kind=W.BC_DIFFUSE, T_w=273.0)
+    s = W.Scenario(gas=W.ARGON, mesh=mesh, n_particles=20000, n_init=1e22, T_init=500.0,
+                   u_init=(30.0, 0.0, 0.0), F_N=1e-30, dt=2e-7, seed=4, L=1e-3, Kn=1.0, capacity=40000)
+    o = orc.Oracle(s)
+    o.init()
+    o.step(300, 0)
+    o.sample(orc.RESET_CUMUL)
+    o.step(200, orc.CUMUL)
+    Phi = o.moments(orc.PHI_CUM).sum(axis=0)
+    N = Phi[0]
+    u = Phi[1:4] / N
+    cc = Phi[4:7] / N - u * u
+    T = s.gas.mass * cc.sum() / (3 * KB)
+    # particles are strongly correlated between steps; 2e4 particles x ~30
+    # independent wall-to-wall flights: tolerance 1 %
+    assert abs(T / 273.0 - 1.0) < 0.01, T
+    assert np.all(np.abs(u) < 3.0)
+
+
+# ------------------------------------------------------------------ collisions
+def test_equilibrium_collision_rate():
+    """P1: in an equilibrium VHS gas the NTC scheme collides at
+    (1/2) N (N-1)/V F_N <sigma_T c_r> per unit time, with
+    n <sigma_T c_r> = nu = 4 d^2 n sqrt(pi k T_ref/m) (T/T_ref)^(1-omega)
+    (Bird 1994 eq. 4.64)."""
+    s = box_scenario(nh=1, n_particles=6000)
+    o = orc.Oracle(s)
+    o.init()
+    o.step(20, 0)  # let (sigma c_r)_max settle
+    c0 = o.counters()["coll"]
+    expected = 0.0
+    g = s.gas
+    V = s.L ** 3 / 6
+    nsteps = 150
+    for _ in range(nsteps):
+        x, v, Ir, cell = o.read()
+        vv = v.astype(np.float64)
+        T = g.mass * ((vv - vv.mean(0)) ** 2).sum(1).mean() / (3 * KB)
+        sc = 4 * g.d_ref ** 2 * math.sqrt(math.pi * KB * g.T_ref / g.mass) * (T / g.T_ref) ** (1 - g.omega)
+        Nc = np.bincount(cell, minlength=6).astype(np.float64)
+        o.step(1, 0)
+        expected += (0.5 * Nc * (Nc - 1) * s.F_N * sc * s.dt / V).sum()
+    got = o.counters()["coll"] - c0
+    assert abs(got - expected) < 4 * math.sqrt(expected), (got, expected)
+
+
+def test_collisions_conserve_momentum_energy():
+    """P5: each collision conserves momentum and energy; with a time step so short
+    that no particle leaves its cell (F_N raised to keep the collision count), the
+    per-cell momentum and energy after a step equal those before within FP32 rounding."""
+    s = box_scenario(nh=1, n_particles=3000, dt_factor=1e-6)
+    s = dataclasses.replace(s, F_N=s.F_N * 2e5)
+    o = orc.Oracle(s)
+    o.init()
+    x0, v0, _, c0 = o.read()
+    o.step(1, orc.RECORD_PAIRS)
+    x1, v1, _, c1 = o.read()
+    assert np.array_equal(c0, c1)
+    assert o.counters()["coll"] > 200
+    for c in range(6):
+        a, b = v0[c0 == c].astype(np.float64), v1[c1 == c].astype(np.float64)
+        scale = np.abs(a).sum()
+        assert np.all(np.abs(a.sum(0) - b.sum(0)) <= 8 * 2 ** -24 * scale)
+        ea, eb = (a * a).sum(), (b * b).sum()
+        assert abs(ea - eb) <= 8 * 2 ** -24 * ea * 4
+    P = o.pairs()
+    assert len(P) == o.counters()["cand"]
+    assert np.all(P[:, 2] != P[:, 3])
+
+
+def test_bimodal_heat_bath_relaxes_to_maxwellian():
+    """P4: two counter-streaming beams relax to a Maxwellian: kurtosis
+    <c^4>/<c^2>^2 -> 5/3, energy conserved to FP32 rounding."""
+    s = box_scenario(nh=1, n_particles=12000)
+    o = orc.Oracle(s)
+    rng = np.random.default_rng(0)
+    n = 12000
+    sig = math.sqrt(KB * 273.0 / s.gas.mass)
+    U = 2.0 * sig
+    v = rng.standard_normal((n, 3)) * 0.3 * sig
+    v[: n // 2, 0] += U
+    v[n // 2:, 0] -= U
+    cell = rng.integers(0, 6, n).astype(np.int32)
+    P = s.mesh.nodes[s.mesh.tets[cell]]
+    w = rng.dirichlet(np.ones(4), n)
+    x = np.einsum("nk,nkc->nc", w, P)
+    o.write(x, v.astype(np.float32), np.zeros(n, np.float32), cell)
+    E0 = (v.astype(np.float32).astype(np.float64) ** 2).sum()
+    k0 = None
+    for _ in range(60):
+        o.step(1, 0)
+    _, v1, _, _ = o.read()
+    c = v1.astype(np.float64)
+    c = c - c.mean(0)
+    c2 = (c * c).sum(1)
+    kurt = (c2 ** 2).mean() / c2.mean() ** 2
+    assert abs(kurt - 5.0 / 3.0) < 0.05, kurt
+    E1 = (v1.astype(np.float64) ** 2).sum()
+    assert abs(E1 / E0 - 1.0) < 1e-5
+
+
+def test_maxwell_molecule_stress_relaxation():
+    """P4 (second part): for Maxwell molecules (omega = 1) an anisotropic
+    temperature relaxes exactly as exp(-p t / mu) with the VHS viscosity
+    (Bird eq. 4.62) -- checks the collision rate and isotropic scattering."""
+    gas = W.Gas(mass=6.63e-26, d_ref=4.17e-10, omega=1.0, T_ref=273.0)
+    s = box_scenario(nh=1, n_particles=24000, gas=gas, dt_factor=0.05, seed=21)
+    o = orc.Oracle(s)
+    rng = np.random.default_rng(1)
+    n = s.n_particles
+    sig = math.sqrt(KB * 273.0 / gas.mass)
+    v = rng.standard_normal((n, 3)) * sig * np.array([1.3, 0.8, 0.8])
+    cell = rng.integers(0, 6, n).astype(np.int32)
+    P = s.mesh.nodes[s.mesh.tets[cell]]
+    x = np.einsum("nk,nkc->nc", rng.dirichlet(np.ones(4), n), P)
+    o.write(x, v.astype(np.float32), np.zeros(n, np.float32), cell)
+
+    def aniso():
+        _, vv, _, _ = o.read()
+        c = vv.astype(np.float64)
+        c -= c.mean(0)
+        m2 = (c * c).mean(0)
+        return m2[0] - 0.5 * (m2[1] + m2[2]), m2.sum() / 3
+
+    a0, th = aniso()
+    T = gas.mass * th / KB
+    mu = gas.mu_ref() * (T / gas.T_ref) ** gas.omega
+    p = s.n_init * KB * T
+    for k in (10, 20, 30):
+        o.step(10, 0)
+        a, _ = aniso()
+        pred = a0 * math.exp(-p * k * s.dt / mu)
+        # statistical error of the anisotropy ~ sqrt(2/n) th
+        assert abs(a - pred) < 4 * math.sqrt(2.0 / n) * th * 1.5 + 0.03 * abs(a0), (k, a, pred)
+
+
+def test_jeans_landau_rotational_relaxation():
+    """P3: homogeneous diatomic gas with T_t != T_r follows the Jeans-Landau law
+    dT_r/dt = (T - T_r)/(Z_r tau), tau = mu(T_t)/p_t (paper Eq. jeans_landau),
+    with T = (3 T_t + 2 T_r)/5 conserved; checks the Borgnakke-Larsen reading."""
+    gas = W.NITROGEN
+    s = box_scenario(nh=1, n_particles=30000, gas=gas, dt_factor=0.1, seed=8, T=300.0)
+    o = orc.Oracle(s)
+    rng = np.random.default_rng(2)
+    n = s.n_particles
+    Tt0, Tr0 = 400.0, 150.0
+    sig = math.sqrt(KB * Tt0 / gas.mass)
+    v = rng.standard_normal((n, 3)) * sig
+    Ir = rng.exponential(Tr0, n)
+    cell = rng.integers(0, 6, n).astype(np.int32)
+    P = s.mesh.nodes[s.mesh.tets[cell]]
+    x = np.einsum("nk,nkc->nc", rng.dirichlet(np.ones(4), n), P)
+    o.write(x, v.astype(np.float32), Ir.astype(np.float32), cell)
+
+    def temps():
+        _, vv, I, _ = o.read()
+        c = vv.astype(np.float64)
+        c -= c.mean(0)
+        return gas.mass * (c * c).sum(1).mean() / (3 * KB), I.astype(np.float64).mean()
+
+    Tt, Tr = temps()
+    Teq = (3 * Tt + 2 * Tr) / 5
+    n_num = s.n_init  # number density of the box
+
+    def rhs(Tr_):
+        Tt_ = (5 * Teq - 2 * Tr_) / 3
+        mu = gas.mu_ref() * (Tt_ / gas.T_ref) ** gas.omega
+        tau = mu / (n_num * KB * Tt_)
+        return (Teq - Tr_) / (gas.Z_rot * tau)
+
+    Tr_ode = Tr
+    t_step = s.dt
+    for blk in range(6):
+        for _ in range(20):
+            # RK4 per time step
+            k1 = rhs(Tr_ode)
+            k2 = rhs(Tr_ode + 0.5 * t_step * k1)
+            k3 = rhs(Tr_ode + 0.5 * t_step * k2)
+            k4 = rhs(Tr_ode + t_step * k3)
+            Tr_ode += t_step * (k1 + 2 * k2 + 2 * k3 + k4) / 6
+        o.step(20, 0)
+        Tt, Tr = temps()
+        assert abs((3 * Tt + 2 * Tr) / 5 - Teq) < 1e-3 * Teq
+        se = Tr / math.sqrt(n)
+        assert abs(Tr - Tr_ode) < 4 * se + 0.01 * (Teq - Tr0), (blk, Tr, Tr_ode)
+
+
+# -------------------------------------------------------------------- sampling
+def test_moments_match_two_pass_central_moments():
+    """P11: moments derived from the raw summation variables equal the direct
+    two-pass central moments of the particles in each cell (Eq. dsmc_temperatures)."""
+    gas = W.NITROGEN
+    s = W.cavity_scenario(2, 4000, 0.1, seed=9, gas=gas)
+    o = orc.Oracle(s)
+    o.init()
+    o.step(3, 0)
+    M = o.moments(orc.PHI_INST | orc.MACRO)
+    x, v, Ir, cell = o.read()
+    vol = o.mesh_info()["vol"]
+    m = gas.mass
+    for c in range(0, len(vol), 7):
+        sel = cell == c
+        if sel.sum() < 2:
+            continue
+        vv = v[sel].astype(np.float64)
+        I = Ir[sel].astype(np.float64)
+        N = len(vv)
+        u = vv.mean(0)
+        cc = vv - u
+        c2 = (cc * cc).sum(1)
+        rho = m * s.F_N * N / vol[c]
+        Tt = m * c2.mean() / (3 * KB)
+        Tr = I.mean()
+        sig = rho * (np.einsum("ni,nj->ij", cc, cc) / N - np.eye(3) * c2.mean() / 3)
+        qt = 0.5 * rho * (cc * c2[:, None]).mean(0)
+        qr = s.F_N * N / vol[c] * KB * (cc * I[:, None]).mean(0)
+        ref = np.concatenate([[N, rho], u, [Tt, Tr, (3 * Tt + 2 * Tr) / 5],
+                              [sig[0, 0], sig[1, 1], sig[2, 2], sig[0, 1], sig[0, 2], sig[1, 2]], qt, qr])
+        scale = np.concatenate([[N, rho], [np.abs(vv).max()] * 3, [Tt] * 3, [rho * (vv ** 2).sum(1).mean()] * 6,
+                                [rho * np.abs(vv).max() ** 3] * 3, [s.F_N * N / vol[c] * KB * I.mean() * np.abs(vv).max()] * 3])
+        assert np.all(np.abs(M[c] - ref) <= 1e-9 * scale), c
+
+
+def test_ewma_window_cumulative_recurrences():
+    """P11: the EWMA follows Eq. exponential_average_moments (first value = first
+    sample), the window and cumulative sums are plain sums of the per-step sums."""
+    s = W.cavity_scenario(2, 3000, 0.1, seed=10)
+    o = orc.Oracle(s, n_a=7)
+    o.init()
+    ph = []
+    for k in range(9):
+        o.step(1, orc.EWMA | orc.WINDOW | (orc.CUMUL if k >= 4 else 0))
+        ph.append(o.moments(orc.PHI_INST))
+    e = ph[0].copy()
+    for p in ph[1:]:
+        e = (6.0 / 7.0) * e + p / 7.0
+    assert np.allclose(o.moments(orc.PHI_EWMA), e, rtol=1e-12, atol=0)
+    assert np.allclose(o.moments(orc.PHI_WINDOW), sum(ph), rtol=1e-12, atol=0)
+    assert np.allclose(o.moments(orc.PHI_CUM), sum(ph[4:]), rtol=1e-12, atol=0)
+    o.sample(orc.RESET_WINDOW)
+    assert np.all(o.moments(orc.PHI_WINDOW) == 0)
+
+
+def test_bookkeeping_closed_cavity():
+    """P6: in the closed cavity the particle count never changes and the array
+    stays sorted by cell, stayers before arrivals in every cell."""
+    s = W.config_small()
+    o = orc.Oracle(s)
+    o.init()
+    prev_x, _, _, prev_c = o.read()
+    o.step(1, 0)
+    x, v, Ir, cell = o.read()
+    assert len(cell) == s.n_particles
+    assert np.all(np.diff(cell) >= 0)
+    assert o.counters()["removed"] == 0
