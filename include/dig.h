@@ -1,0 +1,214 @@
+/*
+ * dig.h -- C ABI of the GB300 DSMC/DIG library (libdig.so).
+ *
+ * One simulation context runs the DSMC particle loop of the DIG method
+ * (arXiv 2607.08195) on one GPU: move particles face by face through a
+ * tetrahedral mesh, sort them by cell, collide pairs in each cell (NTC, VHS,
+ * Borgnakke-Larsen), sample cell moments and time-average them.
+ *
+ * Conventions
+ *  - Every function returns int: DIG_OK (0) or a negative DIG_ERR_* code;
+ *    dig_last_error() gives the message of the last failure.
+ *  - Host pointers are borrowed for the duration of the call only.
+ *  - Device memory belongs to the caller: dig_arena_bytes() says how many
+ *    bytes one context needs; the caller allocates them (for instance a torch
+ *    uint8 tensor), passes the device pointer to dig_bind_arena() and keeps the
+ *    allocation alive until dig_destroy().  The library allocates no device
+ *    memory of its own.
+ *  - All GPU work is queued on the stream given to dig_set_stream() (default:
+ *    the legacy default stream).  Functions that return host data wait for the
+ *    stream, polling with a time limit (dig_config.wait_timeout_s); a wait that
+ *    runs out returns DIG_ERR_TIMEOUT.
+ *  - A context is not thread safe.
+ *  - Units are SI; rotational energies I_r are stored in kelvin (I_r / k_B).
+ */
+#ifndef DIG_H
+#define DIG_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIG_OK 0
+#define DIG_ERR_ARG (-1)      /* bad argument */
+#define DIG_ERR_MESH (-2)     /* mesh rejected (degenerate, non-manifold, untagged boundary) */
+#define DIG_ERR_CAPACITY (-3) /* particle capacity or per-cell staging capacity exceeded */
+#define DIG_ERR_STUCK (-4)    /* a particle exceeded the face-crossing limit in one step */
+#define DIG_ERR_SOLVE (-5)    /* synthetic-equation solve failed (non-finite or diverged) */
+#define DIG_ERR_CUDA (-6)     /* CUDA runtime error */
+#define DIG_ERR_STATE (-7)    /* call out of order (no mesh, no arena, no particles) */
+#define DIG_ERR_TIMEOUT (-8)  /* a host wait on the stream ran out of time */
+
+/* boundary-condition kinds */
+#define DIG_BC_DIFFUSE 0
+#define DIG_BC_SPECULAR 1
+#define DIG_BC_INFLOW 2
+#define DIG_BC_OUTFLOW 3
+
+/* dsmc_step flags */
+#define DIG_EWMA 1         /* update the exponential moving average (paper Eq. exponential_average_moments) */
+#define DIG_WINDOW 2       /* add to the coupling-window sums */
+#define DIG_CUMUL 4        /* add to the cumulative sums (paper Eq. steady_average_moments) */
+#define DIG_RECORD_PAIRS 8 /* debug: record the candidate pairs of the last step */
+#define DIG_INST 16        /* keep the instantaneous sums of the last step */
+#define DIG_WALLFLUX 32    /* accumulate momentum/energy exchanged with each wall face */
+#define DIG_SYNC 64        /* wait for the steps and check the device status before returning */
+
+/* sample() actions */
+#define DIG_RESET_WINDOW 1
+#define DIG_RESET_CUMUL 2
+#define DIG_RESET_EWMA 4
+
+/* read_moments selectors: raw summation variables (17 doubles per cell) or,
+ * with DIG_MACRO added, the 20 derived moments per cell */
+#define DIG_PHI_INST 0
+#define DIG_PHI_EWMA 1
+#define DIG_PHI_WINDOW 2
+#define DIG_PHI_CUM 3
+#define DIG_MACRO 16
+#define DIG_NPHI 17
+#define DIG_NMAC 20
+
+/* counters (read_counters) */
+#define DIG_C_STEPS 0
+#define DIG_C_CAND 1
+#define DIG_C_COLL 2
+#define DIG_C_CROSS 3
+#define DIG_C_WALL 4
+#define DIG_C_REMOVED 5
+#define DIG_C_INJECTED 6
+#define DIG_C_STUCK 7
+#define DIG_C_LB 8
+#define DIG_N_COUNTERS 9
+
+typedef struct dig_config {
+  double mass;       /* molecular mass, kg */
+  double d_ref;      /* VHS reference diameter, m */
+  double omega;      /* viscosity-temperature index */
+  double T_ref;      /* reference temperature of d_ref, K */
+  double alpha;      /* VSS angular parameter in P_inelastic (1 = VHS) */
+  double Z_rot;      /* rotational collision number Z_r */
+  int32_t rot_dof;   /* rotational degrees of freedom d_r: 0 or 2 */
+  int32_t max_cross; /* face crossings allowed per particle per step (<= 0: 4096) */
+  double F_N;        /* real molecules per simulation particle (N_eff) */
+  double dt;         /* time step, s */
+  uint64_t seed;     /* key of every random stream */
+  double n_init;     /* initial number density, 1/m^3 (informative) */
+  double T_init;     /* temperature of the initial equilibrium state, K */
+  double u_init[3];  /* drift velocity of the initial state, m/s */
+  double mu_ref;     /* viscosity at T_ref, Pa s */
+  double Kn;         /* global Knudsen number (paper Eq. kn_definition) */
+  double L_ref;      /* reference length, m */
+  int32_t n_a;       /* effective samples of the moving average */
+  int32_t N_s;       /* DSMC steps per outer coupling cycle */
+  int32_t N_m;       /* maximum synthetic-solver iterations */
+  int32_t passes;    /* neighbour-reconstruction passes */
+  double eps_m;      /* synthetic-solver residual tolerance */
+  double KnD_max;    /* threshold of the cell Knudsen criterion */
+  int64_t capacity;  /* particle capacity of the arena */
+  double wait_timeout_s; /* time limit of host waits (<= 0: 600 s) */
+  int32_t stage_cap;     /* particles staged in shared memory per CTA (<= 0: 4096) */
+  int32_t tile_cells;    /* cells per CTA of the cell pass (<= 0: chosen from the load) */
+} dig_config;
+
+typedef struct dig_bc {
+  int32_t kind;  /* DIG_BC_* */
+  int32_t pad;
+  double T;      /* wall or free-stream temperature, K */
+  double U[3];   /* wall or free-stream velocity, m/s */
+  double n;      /* free-stream number density, 1/m^3 (inflow only) */
+} dig_bc;
+
+typedef struct dig_ctx dig_ctx;
+
+/* Create a context for one gas and time step.  No GPU work is done. */
+int dig_create(const dig_config* cfg, dig_ctx** out);
+/* Release the context (the caller then frees its arena). */
+int dig_destroy(dig_ctx* ctx);
+const char* dig_last_error(dig_ctx* ctx);
+/* Queue all later GPU work on this cudaStream_t (NULL = legacy default stream). */
+int dig_set_stream(dig_ctx* ctx, void* cuda_stream);
+
+/*
+ * mesh_load -- load a conforming tetrahedral mesh (host arrays, copied).
+ * nodes [n_nodes][3] (m); tets [n_tets][4] node indices; face_tag[n_tets][4]:
+ * face f of a tet is the face opposite its vertex f; -1 on interior faces,
+ * else an index into bcs[n_bcs].  Builds the neighbour table (the paper's
+ * face-based tracking, Sec. 4, local mesh package), FP64 face planes, volumes.
+ * Errors: DIG_ERR_MESH for zero-volume tets, faces shared by more than two
+ * tets, boundary faces without a tag or interior faces with one.
+ */
+int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t* tets,
+              int64_t n_tets, const int32_t* face_tag, const dig_bc* bcs, int32_t n_bcs);
+
+/* Device bytes the context needs for the loaded mesh and cfg.capacity particles. */
+int dig_arena_bytes(dig_ctx* ctx, int64_t* bytes);
+/* Bind caller-owned device memory (256-byte aligned, >= dig_arena_bytes) and
+ * upload the mesh tables.  The memory must outlive the context. */
+int dig_bind_arena(dig_ctx* ctx, void* device_ptr, int64_t bytes);
+
+/*
+ * particles_init -- n particles in the uniform equilibrium state of cfg
+ * (paper Sec. 5.1: rho, u = u_init, T_t = T_r = T_init), cell by inverse CDF of
+ * the cell volumes, uniform position in the tet, Maxwellian velocity; then the
+ * particles are sorted by cell.  DIG_ERR_CAPACITY if n > capacity.
+ */
+int particles_init(dig_ctx* ctx, int64_t n);
+
+/* write_particles / read_particles -- HOST arrays: x [n][3] f64, v [n][3] f32,
+ * Ir [n] f32 (may be NULL; ignored and read back as 0 for a monatomic gas),
+ * cell [n] i32.  write sorts by cell, keeping the
+ * given order inside each cell.  read returns the particles sorted by cell
+ * (the order the next collision step uses) and their count in *n; with
+ * cap < count nothing is copied and DIG_ERR_CAPACITY is returned. */
+int write_particles(dig_ctx* ctx, const double* x, const float* v, const float* Ir,
+                    const int32_t* cell, int64_t n);
+int read_particles(dig_ctx* ctx, double* x, float* v, float* Ir, int32_t* cell, int64_t cap,
+                   int64_t* n);
+
+/*
+ * dsmc_step -- advance n_steps DSMC time steps (paper Sec. 2.1; Alg. 1,
+ * "perform N_s standard DSMC time steps"): move with wall interaction and
+ * removal at open boundaries, sort by cell, NTC collisions, sampling; flags
+ * select which time averages are updated (DIG_EWMA, DIG_WINDOW, DIG_CUMUL,
+ * DIG_INST, DIG_WALLFLUX, DIG_RECORD_PAIRS).  Asynchronous unless DIG_SYNC is
+ * given; device-side errors (capacity, stuck particles) are then reported by
+ * the next call that waits.
+ */
+int dsmc_step(dig_ctx* ctx, int32_t n_steps, int32_t flags);
+
+/* sample -- reset time averages (DIG_RESET_WINDOW / _CUMUL / _EWMA bits). */
+int sample(dig_ctx* ctx, int32_t action);
+
+/*
+ * read_moments -- copy per-cell sums to host out[n_tets][17] (which = DIG_PHI_*)
+ * or derived moments out[n_tets][20] (which | DIG_MACRO): mean N, rho, u(3),
+ * T_t, T_r, T, sigma (xx,yy,zz,xy,xz,yz), q_t(3), q_r(3), paper
+ * Eq. dsmc_temperatures in SI units.  Window and cumulative sums are divided
+ * by their step counts before the moments are derived.
+ */
+int read_moments(dig_ctx* ctx, int32_t which, double* host_out, int64_t cap);
+
+/* debug: candidate pairs of the last step run with DIG_RECORD_PAIRS, sorted by
+ * (cell, k): cell, candidate index k, first i and second j index inside the
+ * cell (sorted order), accepted flag.  With any output pointer NULL only the
+ * count is returned in *n. */
+int read_pairs(dig_ctx* ctx, int32_t* cell, int32_t* k, int32_t* i, int32_t* j, uint8_t* acc,
+               int64_t cap, int64_t* n);
+int read_counters(dig_ctx* ctx, int64_t* out, int32_t n);
+/* per-cell collision state (sigma c_r)_max (f32) and NTC remainder (f64), host arrays */
+int dig_cell_state(dig_ctx* ctx, float* cmax, double* rem, int32_t write);
+/* per boundary face (in (tet, face) order): hits, momentum (3) and energy given
+ * to the wall, out[n_bfaces][5]; with out NULL only *n_bfaces is set. */
+int dig_wall_flux(dig_ctx* ctx, double* out, int64_t cap, int64_t* n_bfaces);
+int dig_particle_count(dig_ctx* ctx, int64_t* n);
+/* wait for all queued work; returns the first device-side error, if any */
+int dig_synchronize(dig_ctx* ctx);
+/* number of kernels the library launched since the context was created */
+int dig_launch_count(dig_ctx* ctx, int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -590,7 +590,8 @@ int orc_write_particles(orc_ctx* c, const double* x, const float* v, const float
     if (cell[p] < 0 || cell[p] >= c->n_tets) return fail(c, -1, "cell index out of range");
   memcpy(c->x, x, sizeof(double) * 3 * n);
   memcpy(c->v, v, sizeof(float) * 3 * n);
-  if (Ir) memcpy(c->Ir, Ir, sizeof(float) * n); else memset(c->Ir, 0, sizeof(float) * n);
+  /* monatomic gas carries no rotational energy: I_r is ignored and reads as 0 */
+  if (Ir && c->cfg.rot_dof > 0) memcpy(c->Ir, Ir, sizeof(float) * n); else memset(c->Ir, 0, sizeof(float) * n);
   memcpy(c->cell, cell, sizeof(int32_t) * n);
   c->N = n;
   sort_particles(c, NULL);

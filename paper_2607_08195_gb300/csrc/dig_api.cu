@@ -1,0 +1,767 @@
+// dig_api.cu -- host side of the C ABI declared in include/dig.h.
+//
+// Builds the mesh tables on the host (neighbour table, FP64 face planes,
+// volumes, boundary-face tangent bases), lays out the caller's device arena,
+// and drives the kernels of dig_kernels.cu on the caller's stream.
+#include "../../include/dig.h"
+#include "dig_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+using namespace dig;
+
+namespace {
+constexpr double KB = 1.380649e-23;
+
+// FP32 ln/exp of the collision arithmetic, host copy (used for the initial
+// (sigma c_r)_max only; the same IEEE steps as the device functions).
+float host_ln_f(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  if (e == -127) return -87.3365448f;
+  uint32_t mb = (b & 0x7fffffu) | 0x3f800000u;
+  float m;
+  std::memcpy(&m, &mb, 4);
+  if (m > 1.41421356f) {
+    m = m * 0.5f;
+    e = e + 1;
+  }
+  float s = (m - 1.0f) / (m + 1.0f);
+  float z = s * s;
+  float p = 0.0909090909f;
+  p = p * z + 0.111111111f;
+  p = p * z + 0.142857143f;
+  p = p * z + 0.2f;
+  p = p * z + 0.333333333f;
+  p = p * z + 1.0f;
+  float lnm = (2.0f * s) * p;
+  float fe = (float)e;
+  return fe * 0.693145751953125f + (lnm + fe * 1.42860677e-6f);
+}
+float host_exp_f(float y) {
+  if (y < -87.0f) return 0.0f;
+  if (y > 88.0f) y = 88.0f;
+  float t = y * 1.44269504f;
+  int k = (int)(t >= 0.0f ? t + 0.5f : t - 0.5f);
+  float fk = (float)k;
+  float r = (y - fk * 0.693145751953125f) - fk * 1.42860677e-6f;
+  float p = 1.98412698e-4f;
+  p = p * r + 1.38888889e-3f;
+  p = p * r + 8.33333333e-3f;
+  p = p * r + 4.16666667e-2f;
+  p = p * r + 0.166666667f;
+  p = p * r + 0.5f;
+  p = p * r + 1.0f;
+  p = p * r + 1.0f;
+  uint32_t sb = (uint32_t)(k + 127) << 23;
+  float sc;
+  std::memcpy(&sc, &sb, 4);
+  return p * sc;
+}
+
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+}  // namespace
+
+struct dig_ctx {
+  dig_config cfg{};
+  char err[512] = {0};
+  cudaStream_t stream = nullptr;
+  // host mesh tables
+  int64_t n_tets = 0, n_nodes = 0;
+  std::vector<double> nodes;
+  std::vector<int32_t> tets;
+  std::vector<int32_t> nbr;
+  std::vector<signed char> nbrf;
+  std::vector<Plane64> plane;
+  std::vector<float4> plane32;
+  std::vector<double> vol, cumvol, fdtv;
+  std::vector<BFaceDev> bf;
+  std::vector<BCDev> bc;
+  float margin = 0.0f;
+  bool mesh_ok = false;
+  // device
+  bool bound = false;
+  Params P{};
+  Buf buf[2]{};
+  double* dnodes = nullptr;
+  int* dtets = nullptr;
+  double* mom_out = nullptr;
+  int cur = 0;
+  int64_t N = 0;
+  bool have_particles = false;
+  int64_t step = 0;
+  int64_t n_ewma = 0, n_win = 0, n_cum = 0, host_steps = 0;
+  int tile_cells = 0, stage_cap = 4096;
+  float cmax0 = 0.0f;
+  cudaEvent_t ev = nullptr;
+};
+
+static int fail(dig_ctx* c, int code, const char* msg) {
+  if (c) std::snprintf(c->err, sizeof c->err, "%s", msg);
+  return code;
+}
+
+static int cuda_fail(dig_ctx* c, cudaError_t e, const char* where) {
+  if (c) std::snprintf(c->err, sizeof c->err, "%s: %s", where, cudaGetErrorString(e));
+  return DIG_ERR_CUDA;
+}
+
+#define CK(call)                                             \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+extern "C" {
+
+const char* dig_last_error(dig_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+int dig_create(const dig_config* cfg, dig_ctx** out) {
+  if (!cfg || !out) return DIG_ERR_ARG;
+  if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || (cfg->rot_dof != 0 && cfg->rot_dof != 2))
+    return DIG_ERR_ARG;
+  dig_ctx* c = new dig_ctx();
+  c->cfg = *cfg;
+  if (c->cfg.max_cross <= 0) c->cfg.max_cross = 4096;
+  if (!(c->cfg.wait_timeout_s > 0)) c->cfg.wait_timeout_s = 600.0;
+  if (c->cfg.stage_cap > 0) c->stage_cap = c->cfg.stage_cap;
+  if (c->cfg.n_a <= 0) c->cfg.n_a = 1000;
+  c->tile_cells = c->cfg.tile_cells;
+  *out = c;
+  return DIG_OK;
+}
+
+int dig_destroy(dig_ctx* ctx) {
+  if (!ctx) return DIG_ERR_ARG;
+  if (ctx->ev) cudaEventDestroy(ctx->ev);
+  delete ctx;
+  return DIG_OK;
+}
+
+int dig_set_stream(dig_ctx* ctx, void* s) {
+  if (!ctx) return DIG_ERR_ARG;
+  ctx->stream = (cudaStream_t)s;
+  return DIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+              const int32_t* face_tag, const dig_bc* bcs, int32_t n_bcs) {
+  if (!ctx || !nodes || !tets || !face_tag || n_nodes <= 0 || n_tets <= 0 || n_tets > (1LL << 30))
+    return fail(ctx, DIG_ERR_ARG, "mesh_load: bad arguments");
+  if (ctx->bound) return fail(ctx, DIG_ERR_STATE, "mesh_load: arena already bound");
+  const int64_t n = n_tets;
+  ctx->n_tets = n;
+  ctx->n_nodes = n_nodes;
+  ctx->nodes.assign(nodes, nodes + 3 * n_nodes);
+  ctx->tets.assign(tets, tets + 4 * n);
+  for (int64_t i = 0; i < 4 * n; ++i)
+    if (tets[i] < 0 || tets[i] >= n_nodes) return fail(ctx, DIG_ERR_MESH, "tet vertex index out of range");
+  ctx->vol.resize(n);
+  ctx->cumvol.resize(n);
+  ctx->fdtv.resize(n);
+  ctx->plane.resize(4 * n);
+  ctx->plane32.resize(4 * n);
+  ctx->nbr.assign(4 * n, INT32_MIN);
+  ctx->nbrf.assign(4 * n, 0);
+  double run = 0.0, maxd = 0.0, maxx = 0.0;
+  for (int64_t i = 0; i < 3 * n_nodes; ++i) maxx = std::max(maxx, std::fabs(nodes[i]));
+  for (int64_t t = 0; t < n; ++t) {
+    const double* A = nodes + 3 * tets[4 * t + 0];
+    const double* B = nodes + 3 * tets[4 * t + 1];
+    const double* C = nodes + 3 * tets[4 * t + 2];
+    const double* D = nodes + 3 * tets[4 * t + 3];
+    double u[3], v[3], w[3];
+    for (int i = 0; i < 3; ++i) {
+      u[i] = B[i] - A[i];
+      v[i] = C[i] - A[i];
+      w[i] = D[i] - A[i];
+    }
+    const double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                       u[2] * (v[0] * w[1] - v[1] * w[0]);
+    const double V = std::fabs(det) / 6.0;
+    if (!(V > 0.0)) return fail(ctx, DIG_ERR_MESH, "degenerate tetrahedron (zero volume)");
+    ctx->vol[t] = V;
+    run = (t == 0 ? 0.0 : run) + V;
+    ctx->cumvol[t] = run;
+    ctx->fdtv[t] = ctx->cfg.F_N * ctx->cfg.dt / V;
+    for (int f = 0; f < 4; ++f) {
+      int lv[3], k = 0;
+      for (int q = 0; q < 4; ++q)
+        if (q != f) lv[k++] = q;
+      const double* a = nodes + 3 * tets[4 * t + lv[0]];
+      const double* b = nodes + 3 * tets[4 * t + lv[1]];
+      const double* cc = nodes + 3 * tets[4 * t + lv[2]];
+      const double* p = nodes + 3 * tets[4 * t + f];
+      double e1[3], e2[3], nn[3];
+      for (int i = 0; i < 3; ++i) {
+        e1[i] = b[i] - a[i];
+        e2[i] = cc[i] - a[i];
+      }
+      nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+      nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+      nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+      const double side = nn[0] * (p[0] - a[0]) + nn[1] * (p[1] - a[1]) + nn[2] * (p[2] - a[2]);
+      if (side > 0.0) {
+        nn[0] = -nn[0];
+        nn[1] = -nn[1];
+        nn[2] = -nn[2];
+      }
+      const double len = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+      nn[0] = nn[0] / len;
+      nn[1] = nn[1] / len;
+      nn[2] = nn[2] / len;
+      const double d = nn[0] * a[0] + nn[1] * a[1] + nn[2] * a[2];
+      ctx->plane[4 * t + f] = Plane64{nn[0], nn[1], nn[2], d};
+      ctx->plane32[4 * t + f] = make_float4((float)nn[0], (float)nn[1], (float)nn[2], (float)d);
+      maxd = std::max(maxd, std::fabs(d));
+    }
+  }
+  // FP32 inside-filter margin: the FP32 plane test d - n.x differs from the
+  // exact value by at most ~6 u (|d| + |n|_1 |x|_inf), u = 2^-24; 32 u
+  // (max|d| + sqrt3 max|x|) leaves a factor > 2 for particles slightly
+  // outside the node bounding box.
+  ctx->margin = (float)(32.0 * std::ldexp(1.0, -24) * (maxd + std::sqrt(3.0) * maxx * 1.01));
+
+  // neighbours: faces keyed by their sorted vertex triple
+  struct FK {
+    int32_t a, b, c, tet, face;
+  };
+  std::vector<FK> keys(4 * n);
+  for (int64_t t = 0; t < n; ++t)
+    for (int f = 0; f < 4; ++f) {
+      int32_t v3[3], k = 0;
+      for (int q = 0; q < 4; ++q)
+        if (q != f) v3[k++] = tets[4 * t + q];
+      std::sort(v3, v3 + 3);
+      keys[4 * t + f] = FK{v3[0], v3[1], v3[2], (int32_t)t, f};
+    }
+  std::sort(keys.begin(), keys.end(), [](const FK& x, const FK& y) {
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    if (x.c != y.c) return x.c < y.c;
+    if (x.tet != y.tet) return x.tet < y.tet;
+    return x.face < y.face;
+  });
+  for (size_t i = 0; i < keys.size();) {
+    size_t j = i + 1;
+    while (j < keys.size() && keys[j].a == keys[i].a && keys[j].b == keys[i].b && keys[j].c == keys[i].c) ++j;
+    if (j - i > 2) return fail(ctx, DIG_ERR_MESH, "non-manifold face (shared by more than two tets)");
+    if (j - i == 2) {
+      const FK& P0 = keys[i];
+      const FK& Q0 = keys[i + 1];
+      if (face_tag[4 * P0.tet + P0.face] >= 0 || face_tag[4 * Q0.tet + Q0.face] >= 0)
+        return fail(ctx, DIG_ERR_MESH, "interior face carries a boundary tag");
+      ctx->nbr[4 * P0.tet + P0.face] = Q0.tet;
+      ctx->nbrf[4 * P0.tet + P0.face] = (signed char)Q0.face;
+      ctx->nbr[4 * Q0.tet + Q0.face] = P0.tet;
+      ctx->nbrf[4 * Q0.tet + Q0.face] = (signed char)P0.face;
+    } else {
+      const int32_t tag = face_tag[4 * keys[i].tet + keys[i].face];
+      if (tag < 0 || tag >= n_bcs) return fail(ctx, DIG_ERR_MESH, "boundary face without a valid tag");
+    }
+    i = j;
+  }
+  ctx->bc.resize(std::max(1, n_bcs));
+  for (int b = 0; b < n_bcs; ++b) {
+    BCDev& B = ctx->bc[b];
+    B.kind = bcs[b].kind;
+    B.sigma = (float)std::sqrt(KB * bcs[b].T / ctx->cfg.mass);
+    B.T = (float)bcs[b].T;
+    for (int i = 0; i < 3; ++i) B.U[i] = (float)bcs[b].U[i];
+  }
+  ctx->bf.clear();
+  for (int64_t t = 0; t < n; ++t)
+    for (int f = 0; f < 4; ++f) {
+      if (ctx->nbr[4 * t + f] != INT32_MIN) continue;
+      const Plane64 pl = ctx->plane[4 * t + f];
+      const double N3[3] = {pl.nx, pl.ny, pl.nz};
+      double a[3] = {1.0, 0.0, 0.0};
+      if (std::fabs(N3[0]) >= 0.9) {
+        a[0] = 0.0;
+        a[1] = 1.0;
+      }
+      const double an = a[0] * N3[0] + a[1] * N3[1] + a[2] * N3[2];
+      double t1[3] = {a[0] - an * N3[0], a[1] - an * N3[1], a[2] - an * N3[2]};
+      const double l1 = std::sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+      t1[0] = t1[0] / l1;
+      t1[1] = t1[1] / l1;
+      t1[2] = t1[2] / l1;
+      const double t2[3] = {N3[1] * t1[2] - N3[2] * t1[1], N3[2] * t1[0] - N3[0] * t1[2],
+                            N3[0] * t1[1] - N3[1] * t1[0]};
+      BFaceDev B;
+      B.bc = face_tag[4 * t + f];
+      for (int i = 0; i < 3; ++i) {
+        B.nrm[i] = (float)N3[i];
+        B.t1[i] = (float)t1[i];
+        B.t2[i] = (float)t2[i];
+      }
+      ctx->nbr[4 * t + f] = -1 - (int32_t)ctx->bf.size();
+      ctx->nbrf[4 * t + f] = (signed char)f;
+      ctx->bf.push_back(B);
+    }
+  ctx->mesh_ok = true;
+  return DIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// arena
+// ---------------------------------------------------------------------------
+static size_t layout(dig_ctx* ctx, char* base) {
+  Arena A;
+  A.base = base;
+  const size_t n = (size_t)ctx->n_tets, cap = (size_t)ctx->cfg.capacity, nb = ctx->bf.size();
+  Params& P = ctx->P;
+  P.nbr = A.take<int>(4 * n);
+  P.nbrf = A.take<signed char>(4 * n);
+  P.plane = A.take<Plane64>(4 * n);
+  P.plane32 = A.take<float4>(4 * n);
+  P.fdtv = A.take<double>(n);
+  P.vol = A.take<double>(n);
+  P.cumvol = A.take<double>(n);
+  P.bf = A.take<BFaceDev>(std::max<size_t>(nb, 1));
+  P.bc = A.take<BCDev>(ctx->bc.size());
+  P.bflux = A.take<double>(5 * std::max<size_t>(nb, 1));
+  ctx->dnodes = A.take<double>(3 * (size_t)ctx->n_nodes);
+  ctx->dtets = A.take<int>(4 * n);
+  P.nodes = ctx->dnodes;
+  P.tets = ctx->dtets;
+  for (int b = 0; b < 2; ++b) {
+    double* xs = A.take<double>(3 * cap);
+    float* vs = A.take<float>(3 * cap);
+    float* Is = A.take<float>(cap);
+    ctx->buf[b] = Buf{xs, xs ? xs + cap : nullptr, xs ? xs + 2 * cap : nullptr,
+                      vs, vs ? vs + cap : nullptr, vs ? vs + 2 * cap : nullptr, Is};
+  }
+  P.cs = A.take<int>(n + 1);
+  P.as = A.take<int>(n + 1);
+  P.nst = A.take<int>(n);
+  P.sbase = A.take<int>(n);
+  P.nmov = A.take<int>(n);
+  P.na = A.take<int>(n);
+  P.fill = A.take<int>(n);
+  P.mkey = A.take<int>(cap);
+  P.mcell = A.take<int>(cap);
+  P.aq = A.take<int>(cap);
+  P.akey = A.take<int>(cap);
+  P.cmax = A.take<float>(n);
+  P.rem = A.take<double>(n);
+  P.phi_inst = A.take<double>(NPHI * n);
+  P.phi_ewma = A.take<double>(NPHI * n);
+  P.phi_win = A.take<double>(NPHI * n);
+  P.phi_cum = A.take<double>(NPHI * n);
+  ctx->mom_out = A.take<double>(NMAC * n);
+  P.counters = A.take<unsigned long long>(16);
+  P.status = A.take<int>(4);
+  P.state = A.take<int>(8);
+  P.scan_part = A.take<int>(2 * (size_t)scan_blocks((int)n) + 2);
+  P.pair_cap = (long long)std::max<size_t>(cap, 1 << 16);
+  P.pairs = A.take<int>(4 * (size_t)P.pair_cap);
+  P.pacc = A.take<unsigned char>((size_t)P.pair_cap);
+  P.pair_count = A.take<unsigned long long>(1);
+  return A.off + 256;
+}
+
+int dig_arena_bytes(dig_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return DIG_ERR_ARG;
+  if (!ctx->mesh_ok) return fail(ctx, DIG_ERR_STATE, "dig_arena_bytes: no mesh loaded");
+  if (ctx->cfg.capacity <= 0 || ctx->cfg.capacity > (1LL << 31) - 64)
+    return fail(ctx, DIG_ERR_ARG, "capacity must be in [1, 2^31 - 64]");
+  *bytes = (int64_t)layout(ctx, nullptr);
+  return DIG_OK;
+}
+
+int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
+  if (!ctx || !dptr) return DIG_ERR_ARG;
+  if (!ctx->mesh_ok) return fail(ctx, DIG_ERR_STATE, "dig_bind_arena: no mesh loaded");
+  if (((uintptr_t)dptr & 255) != 0) return fail(ctx, DIG_ERR_ARG, "arena must be 256-byte aligned");
+  int64_t need = 0;
+  int rc = dig_arena_bytes(ctx, &need);
+  if (rc) return rc;
+  if (bytes < need) return fail(ctx, DIG_ERR_CAPACITY, "arena smaller than dig_arena_bytes()");
+  layout(ctx, (char*)dptr);
+  Params& P = ctx->P;
+  const dig_config& c = ctx->cfg;
+  const size_t n = (size_t)ctx->n_tets;
+  P.n_cells = (int)n;
+  P.n_bf = (int)ctx->bf.size();
+  P.max_cross = c.max_cross;
+  P.rot_dof = c.rot_dof;
+  P.margin = ctx->margin;
+  P.dt = c.dt;
+  P.mass_fn = c.mass * c.F_N;
+  P.fn_kb = c.F_N * KB;
+  P.seed_lo = (uint32_t)c.seed;
+  P.seed_hi = (uint32_t)(c.seed >> 32);
+  const double m = c.mass, w = c.omega, mr = 0.5 * m;
+  P.c_vhs = (float)(M_PI * c.d_ref * c.d_ref * std::pow(2.0 * KB * c.T_ref / mr, w - 0.5) / std::tgamma(2.5 - w));
+  P.one_m_omega = (float)(1.0 - w);
+  const float c0sq = (float)(6.25 * 2.0 * KB * c.T_init / m);
+  ctx->cmax0 = P.c_vhs * host_exp_f(P.one_m_omega * host_ln_f(c0sq));
+  const double a = c.alpha;
+  P.p_inel = (float)(a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0) * c.Z_rot));
+  P.lb_exp = (float)(1.0 / (2.5 - w));
+  P.hmr = (float)(0.5 * mr / KB);
+  P.T_init = (float)c.T_init;
+  P.sigma_init = (float)std::sqrt(KB * c.T_init / m);
+  for (int i = 0; i < 3; ++i) P.u0[i] = (float)c.u_init[i];
+  const double na = (double)c.n_a;
+  P.na_a = (na - 1.0) / na;
+  P.na_b = 1.0 / na;
+  P.cap = c.capacity;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync((void*)P.nbr, ctx->nbr.data(), 4 * n * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync((void*)P.nbrf, ctx->nbrf.data(), 4 * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync((void*)P.plane, ctx->plane.data(), 4 * n * sizeof(Plane64), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync((void*)P.plane32, ctx->plane32.data(), 4 * n * sizeof(float4), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync((void*)P.fdtv, ctx->fdtv.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync((void*)P.vol, ctx->vol.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync((void*)P.cumvol, ctx->cumvol.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (!ctx->bf.empty())
+    CK(cudaMemcpyAsync((void*)P.bf, ctx->bf.data(), ctx->bf.size() * sizeof(BFaceDev), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync((void*)P.bc, ctx->bc.data(), ctx->bc.size() * sizeof(BCDev), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(P.bflux, 0, 5 * std::max<size_t>(ctx->bf.size(), 1) * sizeof(double), s));
+  CK(cudaMemcpyAsync(ctx->dnodes, ctx->nodes.data(), ctx->nodes.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->dtets, ctx->tets.data(), ctx->tets.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  std::vector<float> cm(n, ctx->cmax0);
+  CK(cudaMemcpyAsync(P.cmax, cm.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(P.rem, 0, n * sizeof(double), s));
+  for (double* ph : {P.phi_inst, P.phi_ewma, P.phi_win, P.phi_cum})
+    CK(cudaMemsetAsync(ph, 0, NPHI * n * sizeof(double), s));
+  CK(cudaMemsetAsync(P.counters, 0, 16 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(P.status, 0, 4 * sizeof(int), s));
+  CK(cudaMemsetAsync(P.state, 0, 8 * sizeof(int), s));
+  CK(cudaMemsetAsync(P.cs, 0, (n + 1) * sizeof(int), s));
+  CK(cudaMemsetAsync(P.as, 0, (n + 1) * sizeof(int), s));
+  for (int* q : {P.nst, P.sbase, P.nmov, P.na, P.fill}) CK(cudaMemsetAsync(q, 0, n * sizeof(int), s));
+  CK(cudaMemsetAsync(P.pair_count, 0, sizeof(unsigned long long), s));
+  CK(cudaStreamSynchronize(s));  // host tables are freed by the caller's lifetime; keep them anyway
+  if (!ctx->ev) CK(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));
+  ctx->bound = true;
+  return DIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// waits and status
+// ---------------------------------------------------------------------------
+static int wait_stream(dig_ctx* ctx) {
+  CK(cudaEventRecord(ctx->ev, ctx->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ctx->ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "waiting for the stream");
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > ctx->cfg.wait_timeout_s) return fail(ctx, DIG_ERR_TIMEOUT, "host wait on the stream timed out");
+    std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+  }
+  return DIG_OK;
+}
+
+static int check_status(dig_ctx* ctx) {
+  int st[4] = {0, 0, 0, 0};
+  unsigned long long cnt[16];
+  CK(cudaMemcpyAsync(st, ctx->P.status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(cnt, ctx->P.counters, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  if (st[0] & ST_CAPACITY) return fail(ctx, DIG_ERR_CAPACITY, "particle count exceeded the capacity");
+  if (st[0] & ST_CELL_OVER_STAGE)
+    return fail(ctx, DIG_ERR_CAPACITY, "a cell holds more particles than the shared-memory stage (stage_cap)");
+  if (cnt[C_STUCK] > 0) return fail(ctx, DIG_ERR_STUCK, "particles exceeded the face-crossing limit");
+  return DIG_OK;
+}
+
+int dig_synchronize(dig_ctx* ctx) {
+  if (!ctx) return DIG_ERR_ARG;
+  if (!ctx->bound) return wait_stream(ctx);
+  return check_status(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// particle loop
+// ---------------------------------------------------------------------------
+static void choose_tile(dig_ctx* ctx) {
+  if (ctx->cfg.tile_cells > 0) {
+    ctx->tile_cells = ctx->cfg.tile_cells;
+    return;
+  }
+  const double mean = std::max(1.0, (double)ctx->N / (double)ctx->n_tets);
+  int tc = (int)(0.75 * ctx->stage_cap / mean);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int by_grid = (int)((ctx->n_tets + 2 * sms - 1) / (2 * sms));
+  tc = std::min(tc, std::max(1, by_grid));
+  ctx->tile_cells = std::max(1, std::min(tc, 256));
+}
+
+// one gather/collide/move pass followed by the counting-sort bookkeeping
+static void pass(dig_ctx* ctx, int pass_flags, int sflags, uint32_t step_coll, uint32_t step_move, int ewma_first) {
+  const int other = 1 - ctx->cur;
+  launch_cell_pass(ctx->P, ctx->buf[ctx->cur], ctx->buf[other], pass_flags, sflags, step_coll, step_move,
+                   ewma_first, ctx->tile_cells, ctx->stage_cap, ctx->stream);
+  ctx->cur = other;
+  launch_scan(ctx->P, ctx->stream);
+  launch_scatter(ctx->P, ctx->stream);
+}
+
+// particles just written as arrivals into buf[cur] slots [0, n): sort them
+static int settle_new_particles(dig_ctx* ctx, int64_t n) {
+  ctx->N = n;
+  choose_tile(ctx);
+  launch_scan(ctx->P, ctx->stream);
+  launch_scatter(ctx->P, ctx->stream);
+  // the first cell pass reads only arrivals (no stayers): gather into the other buffer
+  pass(ctx, 0, 0, 0, 0, 0);
+  ctx->have_particles = true;
+  return DIG_OK;
+}
+
+static int reset_grouping(dig_ctx* ctx, int64_t n) {
+  Params& P = ctx->P;
+  const size_t nc = (size_t)ctx->n_tets;
+  cudaStream_t s = ctx->stream;
+  for (int* q : {P.nst, P.sbase, P.nmov, P.na, P.fill}) CK(cudaMemsetAsync(q, 0, nc * sizeof(int), s));
+  int st[3] = {0, 0, (int)n};
+  CK(cudaMemcpyAsync(P.state, st, sizeof st, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return DIG_OK;
+}
+
+int particles_init(dig_ctx* ctx, int64_t n) {
+  if (!ctx) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "particles_init: no arena bound");
+  if (n < 0 || n > ctx->cfg.capacity) return fail(ctx, DIG_ERR_CAPACITY, "particles_init: n exceeds capacity");
+  int rc = reset_grouping(ctx, n);
+  if (rc) return rc;
+  launch_init(ctx->P, ctx->buf[ctx->cur], (int)n, ctx->stream);
+  return settle_new_particles(ctx, n);
+}
+
+int write_particles(dig_ctx* ctx, const double* x, const float* v, const float* Ir, const int32_t* cell,
+                    int64_t n) {
+  if (!ctx || (n > 0 && (!x || !v || !cell))) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "write_particles: no arena bound");
+  if (n < 0 || n > ctx->cfg.capacity) return fail(ctx, DIG_ERR_CAPACITY, "write_particles: n exceeds capacity");
+  for (int64_t p = 0; p < n; ++p)
+    if (cell[p] < 0 || cell[p] >= ctx->n_tets) return fail(ctx, DIG_ERR_ARG, "write_particles: cell out of range");
+  int rc = reset_grouping(ctx, n);
+  if (rc) return rc;
+  const Buf& st = ctx->buf[1 - ctx->cur];  // staging in the other buffer
+  cudaStream_t s = ctx->stream;
+  if (n > 0) {
+    CK(cudaMemcpyAsync(st.x, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(st.vx, v, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (Ir) CK(cudaMemcpyAsync(st.Ir, Ir, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->P.aq, cell, n * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  launch_write(ctx->P, ctx->buf[ctx->cur], st.x, st.vx, Ir ? st.Ir : nullptr, ctx->P.aq, (int)n, s);
+  return settle_new_particles(ctx, n);
+}
+
+int read_particles(dig_ctx* ctx, double* x, float* v, float* Ir, int32_t* cell, int64_t cap, int64_t* n) {
+  if (!ctx || !n) return DIG_ERR_ARG;
+  if (!ctx->have_particles) {
+    *n = 0;
+    return DIG_OK;
+  }
+  int N = 0;
+  CK(cudaMemcpyAsync(&N, ctx->P.state, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  *n = N;
+  ctx->N = N;
+  if (cap < N) return fail(ctx, DIG_ERR_CAPACITY, "read_particles: buffer too small");
+  const Buf& st = ctx->buf[1 - ctx->cur];
+  cudaStream_t s = ctx->stream;
+  launch_read(ctx->P, ctx->buf[ctx->cur], st.x, st.vx, st.Ir, ctx->P.aq, N, s);
+  if (N > 0) {
+    if (x) CK(cudaMemcpyAsync(x, st.x, 3 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (v) CK(cudaMemcpyAsync(v, st.vx, 3 * (size_t)N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (Ir) CK(cudaMemcpyAsync(Ir, st.Ir, (size_t)N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (cell) CK(cudaMemcpyAsync(cell, ctx->P.aq, (size_t)N * sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  return wait_stream(ctx);
+}
+
+int dsmc_step(dig_ctx* ctx, int32_t n_steps, int32_t flags) {
+  if (!ctx || n_steps < 0) return DIG_ERR_ARG;
+  if (!ctx->have_particles) return fail(ctx, DIG_ERR_STATE, "dsmc_step: no particles");
+  if (n_steps == 0) return DIG_OK;
+  const int sflags = flags & (S_EWMA | S_WINDOW | S_CUMUL | S_INST | S_WALLFLUX);
+  const uint32_t t0 = (uint32_t)ctx->step;
+  for (int s = 0; s <= n_steps; ++s) {
+    int pf = 0, sf = 0, first = 0;
+    if (s > 0) {
+      pf |= PASS_COLLIDE;
+      sf = sflags & ~S_WALLFLUX;
+      if ((flags & DIG_RECORD_PAIRS) && s == n_steps) {
+        CK(cudaMemsetAsync(ctx->P.pair_count, 0, sizeof(unsigned long long), ctx->stream));
+        sf |= S_PAIRS;
+      }
+      if (sflags & S_EWMA) first = ctx->n_ewma == 0;
+    }
+    if (s < n_steps) {
+      pf |= PASS_MOVE;
+      sf |= sflags & S_WALLFLUX;
+    }
+    pass(ctx, pf, sf, t0 + (uint32_t)s, t0 + (uint32_t)s + 1, first);
+    if (s > 0) {
+      if (sflags & S_EWMA) ctx->n_ewma++;
+      if (sflags & S_WINDOW) ctx->n_win++;
+      if (sflags & S_CUMUL) ctx->n_cum++;
+    }
+  }
+  ctx->step += n_steps;
+  ctx->host_steps += n_steps;
+  if (flags & DIG_SYNC) return check_status(ctx);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "dsmc_step launch");
+  return DIG_OK;
+}
+
+int sample(dig_ctx* ctx, int32_t action) {
+  if (!ctx || !ctx->bound) return DIG_ERR_STATE;
+  const size_t m = NPHI * (size_t)ctx->n_tets * sizeof(double);
+  if (action & DIG_RESET_WINDOW) {
+    CK(cudaMemsetAsync(ctx->P.phi_win, 0, m, ctx->stream));
+    ctx->n_win = 0;
+  }
+  if (action & DIG_RESET_CUMUL) {
+    CK(cudaMemsetAsync(ctx->P.phi_cum, 0, m, ctx->stream));
+    ctx->n_cum = 0;
+  }
+  if (action & DIG_RESET_EWMA) {
+    CK(cudaMemsetAsync(ctx->P.phi_ewma, 0, m, ctx->stream));
+    ctx->n_ewma = 0;
+  }
+  return DIG_OK;
+}
+
+int read_moments(dig_ctx* ctx, int32_t which, double* out, int64_t cap) {
+  if (!ctx || !out) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "read_moments: no arena");
+  const int base = which & 15, macro = (which & DIG_MACRO) != 0;
+  const int64_t need = (macro ? NMAC : NPHI) * ctx->n_tets;
+  if (cap < need) return fail(ctx, DIG_ERR_CAPACITY, "read_moments: buffer too small");
+  const double* src = base == DIG_PHI_INST ? ctx->P.phi_inst
+                    : base == DIG_PHI_EWMA ? ctx->P.phi_ewma
+                    : base == DIG_PHI_WINDOW ? ctx->P.phi_win : ctx->P.phi_cum;
+  double cnt = base == DIG_PHI_WINDOW ? (double)ctx->n_win : base == DIG_PHI_CUM ? (double)ctx->n_cum : 1.0;
+  const double scale = (macro && cnt > 0) ? 1.0 / cnt : (macro ? 0.0 : 1.0);
+  launch_moments_ex(ctx->P, src, scale, macro, ctx->mom_out, ctx->cfg.mass, ctx->cfg.F_N, KB, ctx->stream);
+  CK(cudaMemcpyAsync(out, ctx->mom_out, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return wait_stream(ctx);
+}
+
+int read_pairs(dig_ctx* ctx, int32_t* cell, int32_t* k, int32_t* i, int32_t* j, uint8_t* acc, int64_t cap,
+               int64_t* n) {
+  if (!ctx || !n) return DIG_ERR_ARG;
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, ctx->P.pair_count, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  *n = (int64_t)cnt;
+  if (cnt > (unsigned long long)ctx->P.pair_cap) return fail(ctx, DIG_ERR_CAPACITY, "pair record overflowed");
+  if (!cell || !k || !i || !j || !acc) return DIG_OK;  // size query
+  if (cap < (int64_t)cnt) return fail(ctx, DIG_ERR_CAPACITY, "read_pairs: buffer too small");
+  std::vector<int32_t> r(4 * cnt);
+  std::vector<uint8_t> a(cnt);
+  if (cnt) {
+    CK(cudaMemcpyAsync(r.data(), ctx->P.pairs, 4 * cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(a.data(), ctx->P.pacc, cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  rc = wait_stream(ctx);
+  if (rc) return rc;
+  std::vector<int64_t> ord(cnt);
+  for (size_t q = 0; q < cnt; ++q) ord[q] = (int64_t)q;
+  std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
+    if (r[4 * x] != r[4 * y]) return r[4 * x] < r[4 * y];
+    return r[4 * x + 1] < r[4 * y + 1];
+  });
+  for (size_t q = 0; q < cnt; ++q) {
+    const int64_t o = ord[q];
+    cell[q] = r[4 * o];
+    k[q] = r[4 * o + 1];
+    i[q] = r[4 * o + 2];
+    j[q] = r[4 * o + 3];
+    acc[q] = a[o];
+  }
+  return DIG_OK;
+}
+
+int read_counters(dig_ctx* ctx, int64_t* out, int32_t n) {
+  if (!ctx || !out) return DIG_ERR_ARG;
+  unsigned long long cnt[16];
+  CK(cudaMemcpyAsync(cnt, ctx->P.counters, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  cnt[C_STEPS] = (unsigned long long)ctx->host_steps;
+  for (int q = 0; q < n && q < N_COUNTERS; ++q) out[q] = (int64_t)cnt[q];
+  return DIG_OK;
+}
+
+int dig_cell_state(dig_ctx* ctx, float* cmax, double* rem, int32_t write) {
+  if (!ctx || !ctx->bound) return DIG_ERR_STATE;
+  const size_t n = (size_t)ctx->n_tets;
+  cudaStream_t s = ctx->stream;
+  if (write) {
+    if (cmax) CK(cudaMemcpyAsync(ctx->P.cmax, cmax, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (rem) CK(cudaMemcpyAsync(ctx->P.rem, rem, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  } else {
+    if (cmax) CK(cudaMemcpyAsync(cmax, ctx->P.cmax, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (rem) CK(cudaMemcpyAsync(rem, ctx->P.rem, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  return wait_stream(ctx);
+}
+
+int dig_wall_flux(dig_ctx* ctx, double* out, int64_t cap, int64_t* n_bfaces) {
+  if (!ctx || !n_bfaces) return DIG_ERR_ARG;
+  *n_bfaces = (int64_t)ctx->bf.size();
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "no arena");
+  if (!out) return DIG_OK;  // size query
+  if (cap < 5 * *n_bfaces) return fail(ctx, DIG_ERR_CAPACITY, "dig_wall_flux: buffer too small");
+  CK(cudaMemcpyAsync(out, ctx->P.bflux, 5 * ctx->bf.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return wait_stream(ctx);
+}
+
+int dig_particle_count(dig_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return DIG_ERR_ARG;
+  if (!ctx->have_particles) {
+    *n = 0;
+    return DIG_OK;
+  }
+  int N = 0;
+  CK(cudaMemcpyAsync(&N, ctx->P.state, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  *n = N;
+  return rc;
+}
+
+int dig_launch_count(dig_ctx* ctx, int64_t* n) {
+  if (!n) return DIG_ERR_ARG;
+  *n = (int64_t)g_launches;
+  return DIG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// dig_internal.h -- structures shared by the host API (dig_api.cu) and the
+// kernels (dig_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dig {
+
+constexpr int NPHI = 17;  // summation variables per cell (13 monatomic + 4 rotational)
+constexpr int NMAC = 20;  // derived moments per cell
+constexpr int N_COUNTERS = 9;
+
+// pass flags of the cell kernel
+enum : int { PASS_COLLIDE = 1, PASS_MOVE = 2 };
+// sampling flags (same bits as the public DIG_* flags)
+enum : int { S_EWMA = 1, S_WINDOW = 2, S_CUMUL = 4, S_PAIRS = 8, S_INST = 16, S_WALLFLUX = 32 };
+// device status bits
+enum : int { ST_CELL_OVER_STAGE = 1, ST_CAPACITY = 2, ST_PAIRS_FULL = 4 };
+// counters
+enum : int { C_STEPS, C_CAND, C_COLL, C_CROSS, C_WALL, C_REMOVED, C_INJECTED, C_STUCK, C_LB };
+// random-stream purposes: key = (seed_lo, seed_hi ^ purpose << 24)
+enum : uint32_t { RP_INIT_POS = 1, RP_INIT_VEL = 2, RP_WALL = 3, RP_INJECT = 4, RP_COLL = 5,
+                  RP_DIR = 6, RP_LB = 7, RP_RECAL = 8 };
+
+// FP64 face plane: outward unit normal (nx, ny, nz) and offset d, n.x = d on the face
+struct __align__(32) Plane64 {
+  double nx, ny, nz, d;
+};
+
+struct BCDev {
+  int kind;
+  float sigma;  // sqrt(k T / m)
+  float T;
+  float U[3];
+};
+
+struct BFaceDev {
+  int bc;
+  float nrm[3], t1[3], t2[3];
+};
+
+// one particle buffer, structure of arrays; x,y,z and vx,vy,vz are contiguous
+// blocks of `cap` elements each
+struct Buf {
+  double *x, *y, *z;
+  float *vx, *vy, *vz, *Ir;
+};
+
+struct Params {
+  // mesh
+  int n_cells, n_bf, max_cross, rot_dof;
+  const int* nbr;           // [4n]: >= 0 neighbour, < 0: -1 - boundary face
+  const signed char* nbrf;  // [4n] matching face in the neighbour
+  const Plane64* plane;     // [4n]
+  const float4* plane32;    // FP32 copy used by the inside filter
+  const double* fdtv;       // [n] F_N dt / V
+  const double* vol;        // [n]
+  const double* cumvol;     // [n] running sum of volumes
+  const double* nodes;      // [n_nodes][3] (initial sampling only)
+  const int* tets;          // [n][4]
+  const BFaceDev* bf;
+  const BCDev* bc;
+  double* bflux;            // [5 n_bf]
+  float margin;             // FP32 filter margin (see track())
+  double dt;
+  double mass_fn;           // m F_N (wall flux bookkeeping)
+  double fn_kb;             // F_N k_B
+  // gas constants in FP32
+  uint32_t seed_lo, seed_hi;
+  float c_vhs, one_m_omega, p_inel, lb_exp, hmr;
+  float T_init, sigma_init, u0[3];
+  double na_a, na_b;        // EWMA weights (n_a-1)/n_a and 1/n_a
+  // per-cell grouping and sort state
+  int* cs;      // [n+1] start of each cell in the current grouping
+  int* as;      // [n+1] start of each cell's arrivals in aq/akey
+  int* nst;     // [n] stayers count
+  int* sbase;   // [n] buffer slot of the first stayer
+  int* nmov;    // [n] movers written at the back of the cell's range
+  int* na;      // [n] arrivals counted for the next grouping
+  int* fill;    // [n] scatter cursor
+  int* mkey;    // [cap] canonical key of the mover at this slot
+  int* mcell;   // [cap] destination cell of the mover at this slot (-1: removed)
+  int* aq;      // [cap] arrival: buffer slot
+  int* akey;    // [cap] arrival: canonical key
+  float* cmax;  // [n] (sigma c_r)_max
+  double* rem;  // [n] NTC remainder
+  double* phi_inst;  // [NPHI][n]
+  double* phi_ewma;
+  double* phi_win;
+  double* phi_cum;
+  unsigned long long* counters;  // [16]
+  int* status;
+  int* state;   // [0] N, [1] extra_lo, [2] extra_hi
+  int* scan_part;
+  int* pairs;   // [4 * pair_cap]
+  unsigned char* pacc;
+  unsigned long long* pair_count;
+  long long pair_cap;
+  long long cap;
+};
+
+// launchers (dig_kernels.cu)
+void launch_init(const Params& P, const Buf& out, int n, cudaStream_t s);
+void launch_write(const Params& P, const Buf& out, const double* xs, const float* vs, const float* Is,
+                  const int* cells, int n, cudaStream_t s);
+void launch_scan(const Params& P, cudaStream_t s);
+void launch_scatter(const Params& P, cudaStream_t s);
+void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags,
+                      uint32_t step_coll, uint32_t step_move, int ewma_first, int tile_cells,
+                      int stage_cap, cudaStream_t s);
+void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* Is, int* cells,
+                 int n, cudaStream_t s);
+void launch_moments_ex(const Params& P, const double* phi, double scale, int macro, double* out, double mass,
+                       double FN, double kB, cudaStream_t s);
+size_t cell_pass_smem(int tile_cells, int stage_cap, bool diatomic);
+int scan_blocks(int n_cells);
+extern long long g_launches;
+
+}  // namespace dig

@@ -1,0 +1,993 @@
+// dig_kernels.cu -- sm_103a kernels of the DSMC particle loop.
+//
+// Compiled with -fmad=false: every floating-point expression is evaluated as
+// written (no contraction), and explicit __fma_rn is used where the method
+// states a fused multiply-add.  Together with the IEEE-rounded division and
+// square root and the FP32 ln/exp below (built from +,-,*,/ only), every
+// decision the particle loop takes (cell of a particle, pair indices,
+// acceptance, wall re-emission) is a fixed sequence of IEEE operations.
+//
+// Step structure on the GPU (paper Sec. 2.1: move, then collide pairs of the
+// same cell, then sample; Sec. 4 keeps per-cell particle buckets):
+//   k_cell_pass  one CTA per tile of cells.  Gathers the tile's particles in
+//                the canonical order (stayers, then arrivals ranked by their
+//                previous canonical position) into shared memory, runs the NTC
+//                collisions one thread per cell, samples the moments, then
+//                moves every particle (face-by-face tracking, walls) and writes
+//                it back: stayers at the front of the cell's range, movers at
+//                the back with their destination cell.
+//   k_scan_*     exclusive scans of (stayers + arrivals) and arrivals per cell.
+//   k_scatter    appends each mover to its destination cell's arrival list.
+// The next k_cell_pass then sees every cell's particles: the counting sort of
+// the particle loop costs one extra pass over the movers only.
+#include "dig_internal.h"
+
+#include <cstdio>
+
+namespace dig {
+
+long long g_launches = 0;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                       uint32_t k1, uint32_t (&w)[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  w[0] = c0;
+  w[1] = c1;
+  w[2] = c2;
+  w[3] = c3;
+}
+
+__device__ __forceinline__ void rng(const Params& P, uint32_t purpose, uint32_t ent, uint32_t sub,
+                                    uint32_t step, uint32_t draw, uint32_t (&w)[4]) {
+  philox(ent, sub, step, draw, P.seed_lo, P.seed_hi ^ (purpose << 24), w);
+}
+
+// uniform (0,1) from 23 bits; uniform (0,1) from 52 bits
+__device__ __forceinline__ float u01f(uint32_t w) {
+  return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+__device__ __forceinline__ double u01d(uint32_t w0, uint32_t w1) {
+  const unsigned long long k = ((unsigned long long)(w0 >> 4) << 24) | (unsigned long long)(w1 >> 8);
+  return ((double)k + 0.5) * 2.220446049250313080847e-16;
+}
+
+// FP32 ln: exponent split plus 2 atanh(s), s = (m-1)/(m+1), series to s^11.
+__device__ __forceinline__ float ln_f(float x) {
+  const uint32_t b = __float_as_uint(x);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  if (e == -127) return -87.3365448f;
+  float m = __uint_as_float((b & 0x7fffffu) | 0x3f800000u);
+  if (m > 1.41421356f) {
+    m = m * 0.5f;
+    e = e + 1;
+  }
+  const float s = (m - 1.0f) / (m + 1.0f);
+  const float z = s * s;
+  float p = 0.0909090909f;
+  p = p * z + 0.111111111f;
+  p = p * z + 0.142857143f;
+  p = p * z + 0.2f;
+  p = p * z + 0.333333333f;
+  p = p * z + 1.0f;
+  const float lnm = (2.0f * s) * p;
+  const float fe = (float)e;
+  return fe * 0.693145751953125f + (lnm + fe * 1.42860677e-6f);
+}
+
+// FP32 exp: 2^k exp(r), Taylor series of exp(r) to r^7, ln 2 split in two parts.
+__device__ __forceinline__ float exp_f(float y) {
+  if (y < -87.0f) return 0.0f;
+  if (y > 88.0f) y = 88.0f;
+  const float t = y * 1.44269504f;
+  const int k = (int)(t >= 0.0f ? t + 0.5f : t - 0.5f);
+  const float fk = (float)k;
+  const float r = (y - fk * 0.693145751953125f) - fk * 1.42860677e-6f;
+  float p = 1.98412698e-4f;
+  p = p * r + 1.38888889e-3f;
+  p = p * r + 8.33333333e-3f;
+  p = p * r + 4.16666667e-2f;
+  p = p * r + 0.166666667f;
+  p = p * r + 0.5f;
+  p = p * r + 1.0f;
+  p = p * r + 1.0f;
+  return p * __uint_as_float((uint32_t)(k + 127) << 23);
+}
+
+__device__ __forceinline__ float pow_f(float x, float a) { return exp_f(a * ln_f(x)); }
+
+// Gaussian pair, Marsaglia's polar method; two attempts per Philox block.
+__device__ void gauss2(const Params& P, uint32_t purpose, uint32_t ent, uint32_t sub, uint32_t step,
+                       uint32_t draw0, float& g1, float& g2) {
+  for (uint32_t d = draw0; d < draw0 + 32; ++d) {
+    uint32_t w[4];
+    rng(P, purpose, ent, sub, step, d, w);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const float u1 = 2.0f * u01f(w[2 * a]) - 1.0f;
+      const float u2 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
+      const float s = u1 * u1 + u2 * u2;
+      if (s < 1.0f && s > 0.0f) {
+        const float f = sqrtf(-2.0f * ln_f(s) / s);
+        g1 = u1 * f;
+        g2 = u2 * f;
+        return;
+      }
+    }
+  }
+  g1 = 0.0f;
+  g2 = 0.0f;
+}
+
+// isotropic unit vector (Marsaglia 1972)
+__device__ void unit_vec(const Params& P, uint32_t ent, uint32_t sub, uint32_t step, float& ex, float& ey,
+                         float& ez) {
+  for (uint32_t d = 0; d < 32; ++d) {
+    uint32_t w[4];
+    rng(P, RP_DIR, ent, sub, step, d, w);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const float a1 = 2.0f * u01f(w[2 * a]) - 1.0f;
+      const float b1 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
+      const float s = a1 * a1 + b1 * b1;
+      if (s < 1.0f) {
+        const float r = 2.0f * sqrtf(1.0f - s);
+        ex = a1 * r;
+        ey = b1 * r;
+        ez = 1.0f - 2.0f * s;
+        return;
+      }
+    }
+  }
+  ex = 0.0f;
+  ey = 0.0f;
+  ez = 1.0f;
+}
+
+struct Cnt {
+  unsigned cand = 0, coll = 0, lb = 0, cross = 0, wall = 0, removed = 0, stuck = 0;
+};
+
+// ---------------------------------------------------------------------------
+// wall interaction (diffuse at T_w with wall velocity, or specular)
+// ---------------------------------------------------------------------------
+template <bool DIAT>
+__device__ void wall_reflect(const Params& P, int ib, float& vx, float& vy, float& vz, float& I, uint32_t slot,
+                             uint32_t hit, uint32_t step, bool flux) {
+  const BFaceDev B = P.bf[ib];
+  const BCDev bc = P.bc[B.bc];
+  const float ix = vx, iy = vy, iz = vz, iI = I;
+  if (bc.kind == 1) {
+    const float vn = vx * B.nrm[0] + vy * B.nrm[1] + vz * B.nrm[2];
+    const float h = 2.0f * vn;
+    vx = vx - h * B.nrm[0];
+    vy = vy - h * B.nrm[1];
+    vz = vz - h * B.nrm[2];
+  } else {
+    uint32_t w[4];
+    rng(P, RP_WALL, slot, hit, step, 0, w);
+    const float sg = bc.sigma;
+    const float vn = sg * sqrtf(-2.0f * ln_f(u01f(w[0])));
+    float g1, g2;
+    gauss2(P, RP_WALL, slot, hit, step, 1, g1, g2);
+    const float a = sg * g1, b = sg * g2;
+    vx = ((bc.U[0] + B.t1[0] * a) + B.t2[0] * b) - B.nrm[0] * vn;
+    vy = ((bc.U[1] + B.t1[1] * a) + B.t2[1] * b) - B.nrm[1] * vn;
+    vz = ((bc.U[2] + B.t1[2] * a) + B.t2[2] * b) - B.nrm[2] * vn;
+    if (DIAT) I = -bc.T * ln_f(u01f(w[1]));
+  }
+  if (flux) {
+    double* F = P.bflux + 5 * (size_t)ib;
+    const double m = P.mass_fn;
+    atomicAdd(F + 0, 1.0);
+    atomicAdd(F + 1, m * ((double)ix - (double)vx));
+    atomicAdd(F + 2, m * ((double)iy - (double)vy));
+    atomicAdd(F + 3, m * ((double)iz - (double)vz));
+    const double ein = (double)ix * ix + (double)iy * iy + (double)iz * iz;
+    const double eout = (double)vx * vx + (double)vy * vy + (double)vz * vz;
+    atomicAdd(F + 4, 0.5 * m * (ein - eout) + P.fn_kb * ((double)iI - (double)I));
+  }
+}
+
+__device__ __forceinline__ double dot3(const Plane64& n, double x, double y, double z) {
+  return __fma_rn(n.nz, z, __fma_rn(n.ny, y, __dmul_rn(n.nx, x)));
+}
+
+// Face-by-face tracking of one particle for one time step.  Returns the final
+// cell or -1 when the particle leaves through an open boundary.
+//   x' = x + v t_rem; inside if d_f - n_f.x' >= 0 for every face but the entry
+//   face; else exit face = argmin over faces with n_f.v > 0 of
+//   max(0, (d_f - n_f.x)/(n_f.v)) (ties: lowest f); stop at x' if none or if
+//   t_f >= t_rem; else advance, t_rem -= t_f, cross / reflect / leave.
+// The FP32 plane test is only a filter: it accepts "inside" only when every
+// plane clears `margin`, a bound on the FP32 rounding error of the test, so the
+// FP64 test would give the same answer; anything closer runs the FP64 test.
+template <bool DIAT>
+__device__ int track(const Params& P, double& x, double& y, double& z, float& vx, float& vy, float& vz, float& I,
+                     int cell, uint32_t slot, uint32_t step, bool flux, Cnt& cnt) {
+  double t = P.dt;
+  int entry = -1;
+  uint32_t hits = 0;
+  for (int ncross = 0;; ++ncross) {
+    if (ncross > P.max_cross) {
+      cnt.stuck++;
+      return cell;
+    }
+    const double vdx = (double)vx, vdy = (double)vy, vdz = (double)vz;
+    const double xn = __fma_rn(vdx, t, x), yn = __fma_rn(vdy, t, y), zn = __fma_rn(vdz, t, z);
+    const Plane64* pl = P.plane + 4 * (size_t)cell;
+    bool inside = true;
+    {
+      const float4* pf = P.plane32 + 4 * (size_t)cell;
+      const float fx = (float)xn, fy = (float)yn, fz = (float)zn;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        if (f == entry) continue;
+        const float4 q = __ldg(pf + f);
+        const float s = q.w - __fmaf_rn(q.z, fz, __fmaf_rn(q.y, fy, q.x * fx));
+        if (!(s > P.margin)) inside = false;
+      }
+    }
+    if (!inside) {
+      inside = true;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        if (f == entry) continue;
+        const Plane64 q = pl[f];
+        if (__dsub_rn(q.d, dot3(q, xn, yn, zn)) < 0.0) inside = false;
+      }
+    }
+    if (inside) {
+      x = xn;
+      y = yn;
+      z = zn;
+      return cell;
+    }
+    int best = -1;
+    double tb = 0.0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (f == entry) continue;
+      const Plane64 q = pl[f];
+      const double b = dot3(q, vdx, vdy, vdz);
+      if (!(b > 0.0)) continue;
+      const double a = __dsub_rn(q.d, dot3(q, x, y, z));
+      double tf = __ddiv_rn(a, b);
+      if (tf < 0.0) tf = 0.0;
+      if (best < 0 || tf < tb) {
+        best = f;
+        tb = tf;
+      }
+    }
+    if (best < 0 || tb >= t) {
+      x = xn;
+      y = yn;
+      z = zn;
+      return cell;
+    }
+    x = __fma_rn(vdx, tb, x);
+    y = __fma_rn(vdy, tb, y);
+    z = __fma_rn(vdz, tb, z);
+    t = __dsub_rn(t, tb);
+    cnt.cross++;
+    const int nb = __ldg(P.nbr + 4 * (size_t)cell + best);
+    if (nb >= 0) {
+      entry = __ldg(P.nbrf + 4 * (size_t)cell + best);
+      cell = nb;
+      continue;
+    }
+    const int ib = -1 - nb;
+    const int kind = P.bc[P.bf[ib].bc].kind;
+    if (kind <= 1) {
+      wall_reflect<DIAT>(P, ib, vx, vy, vz, I, slot, hits, step, flux);
+      hits++;
+      cnt.wall++;
+      entry = best;
+      continue;
+    }
+    cnt.removed++;
+    return -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// NTC collisions of one cell (Bird 1994 Sec. 11.1), VHS, serial
+// Borgnakke-Larsen exchange (paper Eq. inelastic_probability).  Candidates are
+// processed in order k = 0, 1, ... on the cell's shared-memory velocities.
+// ---------------------------------------------------------------------------
+template <bool DIAT>
+__device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, float* vz, float* I, int N,
+                             uint32_t step, bool record, Cnt& cnt) {
+  if (N < 2) return;
+  float cmax = P.cmax[cell];
+  const double X = (double)N * (double)(N - 1) * 0.5 * (double)cmax * P.fdtv[cell] + P.rem[cell];
+  const double fl = floor(X);
+  P.rem[cell] = X - fl;
+  const long long ncand = (long long)fl;
+  long long pbase = 0;
+  if (record) pbase = (long long)atomicAdd(P.pair_count, (unsigned long long)ncand);
+  for (long long k = 0; k < ncand; ++k) {
+    uint32_t w[4];
+    rng(P, RP_COLL, (uint32_t)cell, (uint32_t)k, step, 0, w);
+    const int i = (int)(((unsigned long long)w[0] * (unsigned long long)N) >> 32);
+    int j = (int)(((unsigned long long)w[1] * (unsigned long long)(N - 1)) >> 32);
+    if (j >= i) j = j + 1;
+    const float gx = vx[i] - vx[j], gy = vy[i] - vy[j], gz = vz[i] - vz[j];
+    float g2 = gx * gx + gy * gy + gz * gz;
+    const float sc = g2 > 0.0f ? P.c_vhs * pow_f(g2, P.one_m_omega) : 0.0f;
+    if (sc > cmax) cmax = sc;
+    const float R = u01f(w[2]);
+    const bool acc = sc > R * cmax;
+    cnt.cand++;
+    if (record && pbase + k < P.pair_cap) {
+      int* r = P.pairs + 4 * (pbase + k);
+      r[0] = cell;
+      r[1] = (int)k;
+      r[2] = i;
+      r[3] = j;
+      P.pacc[pbase + k] = acc ? 1 : 0;
+    }
+    if (!acc) continue;
+    cnt.coll++;
+    if (DIAT) {
+      uint32_t u[4];
+      rng(P, RP_LB, (uint32_t)cell, (uint32_t)k, step, 0, u);
+      float Etr = g2 * P.hmr;
+      if (u01f(u[0]) < P.p_inel) {
+        const float Ec = Etr + I[i];
+        const float In = Ec * (1.0f - pow_f(u01f(u[1]), P.lb_exp));
+        I[i] = In;
+        Etr = Ec - In;
+        cnt.lb++;
+      }
+      if (u01f(u[2]) < P.p_inel) {
+        const float Ec = Etr + I[j];
+        const float In = Ec * (1.0f - pow_f(u01f(u[3]), P.lb_exp));
+        I[j] = In;
+        Etr = Ec - In;
+        cnt.lb++;
+      }
+      g2 = Etr / P.hmr;
+    }
+    const float cr = sqrtf(g2);
+    float ex, ey, ez;
+    unit_vec(P, (uint32_t)cell, (uint32_t)k, step, ex, ey, ez);
+    const float h = 0.5f * cr;
+    float cm;
+    cm = (vx[i] + vx[j]) * 0.5f;
+    vx[i] = cm + h * ex;
+    vx[j] = cm - h * ex;
+    cm = (vy[i] + vy[j]) * 0.5f;
+    vy[i] = cm + h * ey;
+    vy[j] = cm - h * ey;
+    cm = (vz[i] + vz[j]) * 0.5f;
+    vz[i] = cm + h * ez;
+    vz[j] = cm - h * ez;
+  }
+  P.cmax[cell] = cmax;
+}
+
+// per-cell summation variables (FP32 within the step, FP64 across steps)
+template <bool DIAT>
+__device__ void sample_cell(const Params& P, int cell, const float* vx, const float* vy, const float* vz,
+                            const float* I, int N, int sflags, int ewma_first) {
+  float s[NPHI];
+#pragma unroll
+  for (int q = 0; q < NPHI; ++q) s[q] = 0.0f;
+  for (int k = 0; k < N; ++k) {
+    const float x = vx[k], y = vy[k], z = vz[k];
+    const float vv = x * x + y * y + z * z;
+    s[1] += x;
+    s[2] += y;
+    s[3] += z;
+    s[4] += x * x;
+    s[5] += y * y;
+    s[6] += z * z;
+    s[7] += x * y;
+    s[8] += x * z;
+    s[9] += y * z;
+    s[10] += vv * x;
+    s[11] += vv * y;
+    s[12] += vv * z;
+    if (DIAT) {
+      const float e = I[k];
+      s[13] += e;
+      s[14] += e * x;
+      s[15] += e * y;
+      s[16] += e * z;
+    }
+  }
+  const size_t n = (size_t)P.n_cells;
+  const int np = DIAT ? 17 : 13;
+  for (int q = 0; q < np; ++q) {
+    const double ph = q == 0 ? (double)N : (double)s[q];
+    const size_t o = (size_t)q * n + cell;
+    if (sflags & S_INST) P.phi_inst[o] = ph;
+    if (sflags & S_EWMA) P.phi_ewma[o] = ewma_first ? ph : P.na_a * P.phi_ewma[o] + P.na_b * ph;
+    if (sflags & S_WINDOW) P.phi_win[o] += ph;
+    if (sflags & S_CUMUL) P.phi_cum[o] += ph;
+  }
+}
+
+__device__ __forceinline__ void flush_counters(const Params& P, const Cnt& c) {
+  unsigned v[7] = {c.cand, c.coll, c.lb, c.cross, c.wall, c.removed, c.stuck};
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if ((threadIdx.x & 31) == 0) {
+    const int idx[7] = {C_CAND, C_COLL, C_LB, C_CROSS, C_WALL, C_REMOVED, C_STUCK};
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+      if (v[q]) atomicAdd(P.counters + idx[q], (unsigned long long)v[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the cell pass
+// ---------------------------------------------------------------------------
+constexpr int CP_THREADS = 256;
+
+size_t cell_pass_smem(int TC, int CAP, bool diat) {
+  return sizeof(int) * (size_t)(4 * TC + 4) + (size_t)CAP * (sizeof(int) + 3 * sizeof(float)) +
+         (diat ? (size_t)CAP * sizeof(float) : 0);
+}
+
+template <bool DIAT>
+__global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf OUT, int pass, int sflags,
+                                                          uint32_t step_coll, uint32_t step_move,
+                                                          int ewma_first, int TC, int CAP) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_cs = (int*)smem;       // TC+1 global canonical starts
+  int* s_as = s_cs + TC + 1;    // TC+1 arrival starts
+  int* s_nst = s_as + TC + 1;   // TC
+  int* s_sb = s_nst + TC;       // TC
+  int* s_src = s_sb + TC;       // CAP: buffer slot of each staged particle
+  float* s_vx = (float*)(s_src + CAP);
+  float* s_vy = s_vx + CAP;
+  float* s_vz = s_vy + CAP;
+  float* s_I = DIAT ? s_vz + CAP : nullptr;
+  __shared__ int s_g1;
+
+  const int c0 = blockIdx.x * TC;
+  if (c0 >= P.n_cells) return;
+  const int nc = min(TC, P.n_cells - c0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = CP_THREADS / 32;
+  const bool do_coll = (pass & PASS_COLLIDE) != 0, do_move = (pass & PASS_MOVE) != 0;
+  const bool flux = (sflags & S_WALLFLUX) != 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.state[1] = 0;
+    P.state[2] = 0;
+  }
+  for (int i = threadIdx.x; i <= nc; i += CP_THREADS) {
+    s_cs[i] = P.cs[c0 + i];
+    s_as[i] = P.as[c0 + i];
+    if (i < nc) {
+      s_nst[i] = P.nst[c0 + i];
+      s_sb[i] = P.sbase[c0 + i];
+    }
+  }
+  __syncthreads();
+  Cnt cnt;
+  int g0 = 0;
+  while (g0 < nc) {
+    if (threadIdx.x == 0) {
+      int g1 = g0 + 1;
+      while (g1 < nc && s_cs[g1 + 1] - s_cs[g0] <= CAP) ++g1;
+      s_g1 = g1;
+    }
+    __syncthreads();
+    const int g1 = s_g1;
+    const int gbase = s_cs[g0];
+    const int gN = s_cs[g1] - gbase;
+    if (gN > CAP) {  // one cell holds more particles than the stage
+      if (threadIdx.x == 0) atomicOr(P.status, ST_CELL_OVER_STAGE);
+      g0 = g1;
+      __syncthreads();
+      continue;
+    }
+    // 1. canonical order: stayers (contiguous in IN), then arrivals ranked by key
+    for (int c = g0 + warp; c < g1; c += nwarps) {
+      const int cb = s_cs[c] - gbase, ns = s_nst[c], sb = s_sb[c];
+      for (int k = lane; k < ns; k += 32) s_src[cb + k] = sb + k;
+      const int a0 = s_as[c], na = s_as[c + 1] - a0;
+      if (na <= 32) {
+        const int key = lane < na ? P.akey[a0 + lane] : 0x7fffffff;
+        const int q = lane < na ? P.aq[a0 + lane] : 0;
+        int rank = 0;
+        for (int r = 0; r < na; ++r) rank += (__shfl_sync(0xffffffffu, key, r) < key) ? 1 : 0;
+        if (lane < na) s_src[cb + ns + rank] = q;
+      } else {
+        for (int r = lane; r < na; r += 32) {
+          const int key = P.akey[a0 + r];
+          int rank = 0;
+          for (int r2 = 0; r2 < na; ++r2) rank += (P.akey[a0 + r2] < key) ? 1 : 0;
+          s_src[cb + ns + rank] = P.aq[a0 + r];
+        }
+      }
+    }
+    __syncthreads();
+    // 2. gather velocities (and rotational energies)
+    for (int k = threadIdx.x; k < gN; k += CP_THREADS) {
+      const int s = s_src[k];
+      s_vx[k] = IN.vx[s];
+      s_vy[k] = IN.vy[s];
+      s_vz[k] = IN.vz[s];
+      if (DIAT) s_I[k] = IN.Ir[s];
+    }
+    __syncthreads();
+    // 3. collisions and sampling, one thread per cell
+    if (do_coll) {
+      const bool rec = (sflags & S_PAIRS) != 0;
+      for (int c = g0 + threadIdx.x; c < g1; c += CP_THREADS) {
+        const int cb = s_cs[c] - gbase, N = s_cs[c + 1] - s_cs[c];
+        collide_cell<DIAT>(P, c0 + c, s_vx + cb, s_vy + cb, s_vz + cb, DIAT ? s_I + cb : nullptr, N, step_coll,
+                           rec, cnt);
+        sample_cell<DIAT>(P, c0 + c, s_vx + cb, s_vy + cb, s_vz + cb, DIAT ? s_I + cb : nullptr, N, sflags,
+                          ewma_first);
+      }
+      __syncthreads();
+    }
+    // 4. move and write back, one warp per cell
+    for (int c = g0 + warp; c < g1; c += nwarps) {
+      const int cb = s_cs[c] - gbase, Nc = s_cs[c + 1] - s_cs[c], cell = c0 + c, gcb = s_cs[c];
+      int stay = 0, mov = 0;
+      for (int k0 = 0; k0 < Nc; k0 += 32) {
+        const int k = k0 + lane;
+        const bool act = k < Nc;
+        double x = 0, y = 0, z = 0;
+        float vx = 0, vy = 0, vz = 0, I = 0;
+        int dst = cell;
+        if (act) {
+          const int s = s_src[cb + k];
+          x = IN.x[s];
+          y = IN.y[s];
+          z = IN.z[s];
+          vx = s_vx[cb + k];
+          vy = s_vy[cb + k];
+          vz = s_vz[cb + k];
+          if (DIAT) I = s_I[cb + k];
+          if (do_move) dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)(gcb + k), step_move, flux, cnt);
+        }
+        const bool st = act && dst == cell, mv = act && dst != cell;
+        const unsigned bs = __ballot_sync(0xffffffffu, st), bm = __ballot_sync(0xffffffffu, mv);
+        const unsigned lt = (1u << lane) - 1u;
+        int slot = 0;
+        if (st) slot = gcb + stay + __popc(bs & lt);
+        if (mv) slot = gcb + Nc - 1 - (mov + __popc(bm & lt));
+        if (act) {
+          OUT.x[slot] = x;
+          OUT.y[slot] = y;
+          OUT.z[slot] = z;
+          OUT.vx[slot] = vx;
+          OUT.vy[slot] = vy;
+          OUT.vz[slot] = vz;
+          if (DIAT) OUT.Ir[slot] = I;
+        }
+        if (mv) {
+          P.mkey[slot] = gcb + k;
+          P.mcell[slot] = dst;
+          if (dst >= 0) atomicAdd(P.na + dst, 1);
+        }
+        stay += __popc(bs);
+        mov += __popc(bm);
+      }
+      if (lane == 0) {
+        P.nst[cell] = stay;
+        P.sbase[cell] = gcb;
+        P.nmov[cell] = mov;
+      }
+    }
+    __syncthreads();
+    g0 = g1;
+  }
+  flush_counters(P, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// scans: cs = exclusive scan(nst + na), as = exclusive scan(na); zero na, fill
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 1024, SCAN_ITEMS = 4;
+constexpr int SCAN_CHUNK = SCAN_T * SCAN_ITEMS;
+
+int scan_blocks(int n) { return (n + SCAN_CHUNK - 1) / SCAN_CHUNK; }
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(Params P) {
+  const int n = P.n_cells;
+  const int base = blockIdx.x * SCAN_CHUNK;
+  int tot = 0, arr = 0;
+  for (int i = threadIdx.x; i < SCAN_CHUNK; i += SCAN_T) {
+    const int c = base + i;
+    if (c < n) {
+      const int a = P.na[c];
+      tot += P.nst[c] + a;
+      arr += a;
+    }
+  }
+  __shared__ int sh[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    arr += __shfl_xor_sync(0xffffffffu, arr, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = tot;
+    sh[1][threadIdx.x >> 5] = arr;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tot = sh[0][threadIdx.x];
+    arr = sh[1][threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) {
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      arr += __shfl_xor_sync(0xffffffffu, arr, o);
+    }
+    if (threadIdx.x == 0) {
+      P.scan_part[2 * blockIdx.x] = tot;
+      P.scan_part[2 * blockIdx.x + 1] = arr;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_final(Params P) {
+  const int n = P.n_cells;
+  const int base = blockIdx.x * SCAN_CHUNK;
+  __shared__ int sh[2][32];
+  __shared__ int s_off[2];
+  // offset of this block: sum of the partials of the blocks before it
+  int pt = 0, pa = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_T) {
+    pt += P.scan_part[2 * b];
+    pa += P.scan_part[2 * b + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    pt += __shfl_xor_sync(0xffffffffu, pt, o);
+    pa += __shfl_xor_sync(0xffffffffu, pa, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = pt;
+    sh[1][threadIdx.x >> 5] = pa;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0;
+    for (int w = 0; w < SCAN_T / 32; ++w) {
+      a += sh[0][w];
+      b += sh[1][w];
+    }
+    s_off[0] = a;
+    s_off[1] = b;
+  }
+  __syncthreads();
+  // each thread: SCAN_ITEMS consecutive cells
+  int vt[SCAN_ITEMS], va[SCAN_ITEMS];
+  int lt = 0, la = 0;
+  const int c0 = base + threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int c = c0 + i;
+    int a = 0, t = 0;
+    if (c < n) {
+      a = P.na[c];
+      t = P.nst[c] + a;
+    }
+    vt[i] = t;
+    va[i] = a;
+    lt += t;
+    la += a;
+  }
+  // block exclusive scan of (lt, la)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int it = lt, ia = la;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int yt = __shfl_up_sync(0xffffffffu, it, o), ya = __shfl_up_sync(0xffffffffu, ia, o);
+    if (lane >= o) {
+      it += yt;
+      ia += ya;
+    }
+  }
+  __syncthreads();
+  if (lane == 31) {
+    sh[0][warp] = it;
+    sh[1][warp] = ia;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int wt = sh[0][lane], wa = sh[1][lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int yt = __shfl_up_sync(0xffffffffu, wt, o), ya = __shfl_up_sync(0xffffffffu, wa, o);
+      if (lane >= o) {
+        wt += yt;
+        wa += ya;
+      }
+    }
+    sh[0][lane] = wt;
+    sh[1][lane] = wa;
+  }
+  __syncthreads();
+  int et = s_off[0] + it - lt + (warp > 0 ? sh[0][warp - 1] : 0);
+  int ea = s_off[1] + ia - la + (warp > 0 ? sh[1][warp - 1] : 0);
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int c = c0 + i;
+    if (c < n) {
+      P.cs[c] = et;
+      P.as[c] = ea;
+      P.na[c] = 0;
+      P.fill[c] = 0;
+    }
+    et += vt[i];
+    ea += va[i];
+    if (c == n - 1) {
+      P.cs[n] = et;
+      P.as[n] = ea;
+      P.state[0] = et;
+      if ((long long)et > P.cap) atomicOr(P.status, ST_CAPACITY);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// scatter movers into their destination cells' arrival lists
+// ---------------------------------------------------------------------------
+__global__ void k_scatter(Params P) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = gw; c < P.n_cells; c += nw) {
+    const int lo = P.sbase[c] + P.nst[c], hi = lo + P.nmov[c];
+    for (int q = lo + lane; q < hi; q += 32) {
+      const int d = P.mcell[q];
+      if (d >= 0) {
+        const int pos = P.as[d] + atomicAdd(P.fill + d, 1);
+        P.aq[pos] = q;
+        P.akey[pos] = P.mkey[q];
+      }
+    }
+  }
+  const int lo = P.state[1], hi = P.state[2];
+  for (int q = lo + blockIdx.x * blockDim.x + threadIdx.x; q < hi; q += gridDim.x * blockDim.x) {
+    const int d = P.mcell[q];
+    if (d >= 0) {
+      const int pos = P.as[d] + atomicAdd(P.fill + d, 1);
+      P.aq[pos] = q;
+      P.akey[pos] = P.mkey[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// initial state: paper Sec. 5.1 uniform equilibrium; new particles become
+// arrivals (keys = their index) of the next cell pass
+// ---------------------------------------------------------------------------
+template <bool DIAT>
+__global__ void k_init(Params P, Buf OUT, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint32_t w[4], w2[4];
+  const int nt = P.n_cells;
+  rng(P, RP_INIT_POS, (uint32_t)p, 0, 0, 0, w);
+  const double target = u01d(w[0], w[1]) * P.cumvol[nt - 1];
+  int lo = 0, hi = nt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (P.cumvol[mid] > target)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  const int t = lo;
+  rng(P, RP_INIT_POS, (uint32_t)p, 1, 0, 0, w);
+  rng(P, RP_INIT_POS, (uint32_t)p, 2, 0, 0, w2);
+  double s = u01d(w[0], w[1]), tt = u01d(w[2], w[3]), u = u01d(w2[0], w2[1]);
+  if (s + tt > 1.0) {
+    s = 1.0 - s;
+    tt = 1.0 - tt;
+  }
+  if (tt + u > 1.0) {
+    const double tmp = u;
+    u = 1.0 - s - tt;
+    tt = 1.0 - tmp;
+  } else if (s + tt + u > 1.0) {
+    const double tmp = u;
+    u = s + tt + u - 1.0;
+    s = 1.0 - tt - tmp;
+  }
+  const int* tv = P.tets + 4 * (size_t)t;
+  const double* A = P.nodes + 3 * (size_t)tv[0];
+  const double* B = P.nodes + 3 * (size_t)tv[1];
+  const double* C = P.nodes + 3 * (size_t)tv[2];
+  const double* D = P.nodes + 3 * (size_t)tv[3];
+  double xs[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) xs[i] = A[i] + s * (B[i] - A[i]) + tt * (C[i] - A[i]) + u * (D[i] - A[i]);
+  float g[4];
+  gauss2(P, RP_INIT_VEL, (uint32_t)p, 0, 0, 0, g[0], g[1]);
+  gauss2(P, RP_INIT_VEL, (uint32_t)p, 1, 0, 0, g[2], g[3]);
+  OUT.x[p] = xs[0];
+  OUT.y[p] = xs[1];
+  OUT.z[p] = xs[2];
+  OUT.vx[p] = P.u0[0] + P.sigma_init * g[0];
+  OUT.vy[p] = P.u0[1] + P.sigma_init * g[1];
+  OUT.vz[p] = P.u0[2] + P.sigma_init * g[2];
+  if (DIAT) {
+    rng(P, RP_INIT_VEL, (uint32_t)p, 2, 0, 0, w);
+    OUT.Ir[p] = -P.T_init * ln_f(u01f(w[0]));
+  }
+  P.mkey[p] = p;
+  P.mcell[p] = t;
+  atomicAdd(P.na + t, 1);
+}
+
+// host-supplied particles (interleaved staging) -> buffer + arrivals
+__global__ void k_write(Params P, Buf OUT, const double* xs, const float* vs, const float* Is, const int* cells,
+                        int n, int diat) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  OUT.x[p] = xs[3 * (size_t)p];
+  OUT.y[p] = xs[3 * (size_t)p + 1];
+  OUT.z[p] = xs[3 * (size_t)p + 2];
+  OUT.vx[p] = vs[3 * (size_t)p];
+  OUT.vy[p] = vs[3 * (size_t)p + 1];
+  OUT.vz[p] = vs[3 * (size_t)p + 2];
+  if (diat) OUT.Ir[p] = Is ? Is[p] : 0.0f;
+  const int c = cells[p];
+  P.mkey[p] = p;
+  P.mcell[p] = c;
+  atomicAdd(P.na + c, 1);
+}
+
+// current sorted buffer -> interleaved staging + cell of each slot
+__global__ void k_read(Params P, Buf CUR, double* xs, float* vs, float* Is, int* cells, int n, int diat) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int p = gt; p < n; p += nt) {
+    xs[3 * (size_t)p] = CUR.x[p];
+    xs[3 * (size_t)p + 1] = CUR.y[p];
+    xs[3 * (size_t)p + 2] = CUR.z[p];
+    vs[3 * (size_t)p] = CUR.vx[p];
+    vs[3 * (size_t)p + 1] = CUR.vy[p];
+    vs[3 * (size_t)p + 2] = CUR.vz[p];
+    Is[p] = diat ? CUR.Ir[p] : 0.0f;
+  }
+  for (int c = gt; c < P.n_cells; c += nt)
+    for (int p = P.cs[c]; p < P.cs[c + 1]; ++p) cells[p] = c;
+}
+
+// summation variables [NPHI][n] * scale -> [n][NPHI] or derived moments [n][NMAC]
+// (paper Eq. dsmc_temperatures from averaged raw sums, SI units)
+__global__ void k_moments(Params P, const double* phi, double scale, int macro, double* out, double mass,
+                          double FN, double kB) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  double ph[NPHI];
+#pragma unroll
+  for (int q = 0; q < NPHI; ++q) ph[q] = phi[(size_t)q * n + c] * scale;
+  if (!macro) {
+#pragma unroll
+    for (int q = 0; q < NPHI; ++q) out[(size_t)c * NPHI + q] = ph[q];
+    return;
+  }
+  double* M = out + (size_t)c * NMAC;
+#pragma unroll
+  for (int q = 0; q < NMAC; ++q) M[q] = 0.0;
+  const double N = ph[0];
+  M[0] = N;
+  if (!(N > 0.0)) return;
+  const double V = P.vol[c];
+  const double u0 = ph[1] / N, u1 = ph[2] / N, u2 = ph[3] / N;
+  const double m00 = ph[4] / N, m11 = ph[5] / N, m22 = ph[6] / N, m01 = ph[7] / N, m02 = ph[8] / N,
+               m12 = ph[9] / N;
+  const double c00 = m00 - u0 * u0, c11 = m11 - u1 * u1, c22 = m22 - u2 * u2;
+  const double c01 = m01 - u0 * u1, c02 = m02 - u0 * u2, c12 = m12 - u1 * u2;
+  const double tr = c00 + c11 + c22, v2 = m00 + m11 + m22, uu = u0 * u0 + u1 * u1 + u2 * u2;
+  const double rho = mass * FN * N / V;
+  M[1] = rho;
+  M[2] = u0;
+  M[3] = u1;
+  M[4] = u2;
+  const double Tt = mass * tr / (3.0 * kB);
+  M[5] = Tt;
+  const int dr = P.rot_dof;
+  const double Tr = dr > 0 ? 2.0 * (ph[13] / N) / dr : 0.0;
+  M[6] = Tr;
+  M[7] = (3.0 * Tt + dr * Tr) / (3.0 + dr);
+  M[8] = rho * (c00 - tr / 3.0);
+  M[9] = rho * (c11 - tr / 3.0);
+  M[10] = rho * (c22 - tr / 3.0);
+  M[11] = rho * c01;
+  M[12] = rho * c02;
+  M[13] = rho * c12;
+  const double mv[3][3] = {{m00, m01, m02}, {m01, m11, m12}, {m02, m12, m22}};
+  const double u[3] = {u0, u1, u2};
+  for (int i = 0; i < 3; ++i) {
+    const double uj = u[0] * mv[i][0] + u[1] * mv[i][1] + u[2] * mv[i][2];
+    const double c3 = ph[10 + i] / N - 2.0 * uj - u[i] * v2 + 2.0 * u[i] * uu;
+    M[14 + i] = 0.5 * rho * c3;
+    if (dr > 0) M[17 + i] = (FN * N / V) * kB * (ph[14 + i] / N - u[i] * (ph[13] / N));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+void launch_init(const Params& P, const Buf& out, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  if (P.rot_dof > 0)
+    k_init<true><<<blocks_for(n, 256), 256, 0, s>>>(P, out, n);
+  else
+    k_init<false><<<blocks_for(n, 256), 256, 0, s>>>(P, out, n);
+  ++g_launches;
+}
+
+void launch_write(const Params& P, const Buf& out, const double* xs, const float* vs, const float* Is,
+                  const int* cells, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_write<<<blocks_for(n, 256), 256, 0, s>>>(P, out, xs, vs, Is, cells, n, P.rot_dof > 0);
+  ++g_launches;
+}
+
+void launch_scan(const Params& P, cudaStream_t s) {
+  const int nb = scan_blocks(P.n_cells);
+  k_scan_reduce<<<nb, SCAN_T, 0, s>>>(P);
+  k_scan_final<<<nb, SCAN_T, 0, s>>>(P);
+  g_launches += 2;
+}
+
+void launch_scatter(const Params& P, cudaStream_t s) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  k_scatter<<<sms * 8, 256, 0, s>>>(P);
+  ++g_launches;
+}
+
+void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_coll,
+                      uint32_t step_move, int ewma_first, int TC, int CAP, cudaStream_t s) {
+  const bool diat = P.rot_dof > 0;
+  const size_t sm = cell_pass_smem(TC, CAP, diat);
+  const int nb = blocks_for(P.n_cells, TC);
+  if (diat) {
+    cudaFuncSetAttribute(k_cell_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_cell_pass<true><<<nb, CP_THREADS, sm, s>>>(P, in, out, pass, sflags, step_coll, step_move, ewma_first, TC,
+                                                  CAP);
+  } else {
+    cudaFuncSetAttribute(k_cell_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_cell_pass<false><<<nb, CP_THREADS, sm, s>>>(P, in, out, pass, sflags, step_coll, step_move, ewma_first,
+                                                   TC, CAP);
+  }
+  ++g_launches;
+}
+
+void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* Is, int* cells, int n,
+                 cudaStream_t s) {
+  k_read<<<256, 256, 0, s>>>(P, cur, xs, vs, Is, cells, n, P.rot_dof > 0);
+  ++g_launches;
+}
+
+void launch_moments_ex(const Params& P, const double* phi, double scale, int macro, double* out, double mass,
+                       double FN, double kB, cudaStream_t s) {
+  k_moments<<<blocks_for(P.n_cells, 128), 128, 0, s>>>(P, phi, scale, macro, out, mass, FN, kB);
+  ++g_launches;
+}
+
+}  // namespace dig

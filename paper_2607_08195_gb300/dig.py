@@ -1,0 +1,247 @@
+"""Thin Python binding of libdig.so (include/dig.h).
+
+Argument marshalling only: every step of the particle loop runs in the CUDA
+kernels of libdig.so.  PyTorch supplies the device memory (one uint8 tensor,
+the arena) and the stream.  There is no CPU fallback: without the compiled
+library or a CUDA device the constructor raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdig.so")
+
+EWMA, WINDOW, CUMUL, RECORD_PAIRS, INST, WALLFLUX, SYNC = 1, 2, 4, 8, 16, 32, 64
+RESET_WINDOW, RESET_CUMUL, RESET_EWMA = 1, 2, 4
+PHI_INST, PHI_EWMA, PHI_WINDOW, PHI_CUM, MACRO = 0, 1, 2, 3, 16
+NPHI, NMAC = 17, 20
+COUNTERS = ["steps", "cand", "coll", "cross", "wall", "removed", "injected", "stuck", "lb"]
+ERRORS = {-1: "DIG_ERR_ARG", -2: "DIG_ERR_MESH", -3: "DIG_ERR_CAPACITY", -4: "DIG_ERR_STUCK",
+          -5: "DIG_ERR_SOLVE", -6: "DIG_ERR_CUDA", -7: "DIG_ERR_STATE", -8: "DIG_ERR_TIMEOUT"}
+
+
+class DigError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class DigConfig(C.Structure):
+    _fields_ = [
+        ("mass", C.c_double), ("d_ref", C.c_double), ("omega", C.c_double), ("T_ref", C.c_double),
+        ("alpha", C.c_double), ("Z_rot", C.c_double), ("rot_dof", C.c_int32), ("max_cross", C.c_int32),
+        ("F_N", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64), ("n_init", C.c_double),
+        ("T_init", C.c_double), ("u_init", C.c_double * 3), ("mu_ref", C.c_double), ("Kn", C.c_double),
+        ("L_ref", C.c_double), ("n_a", C.c_int32), ("N_s", C.c_int32), ("N_m", C.c_int32),
+        ("passes", C.c_int32), ("eps_m", C.c_double), ("KnD_max", C.c_double), ("capacity", C.c_int64),
+        ("wait_timeout_s", C.c_double), ("stage_cap", C.c_int32), ("tile_cells", C.c_int32),
+    ]
+
+
+class DigBC(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("T", C.c_double), ("U", C.c_double * 3),
+                ("n", C.c_double)]
+
+
+# every symbol include/dig.h declares
+EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mesh_load", "dig_arena_bytes",
+           "dig_bind_arena", "particles_init", "write_particles", "read_particles", "dsmc_step", "sample",
+           "read_moments", "read_pairs", "read_counters", "dig_cell_state", "dig_wall_flux",
+           "dig_particle_count", "dig_synchronize", "dig_launch_count"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdig.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not built: run paper_2607_08195_gb300.build.build() (needs nvcc)")
+    L = C.CDLL(path)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "dig_create": [P, P], "dig_destroy": [P], "dig_set_stream": [P, P],
+        "mesh_load": [P, P, I64, P, I64, P, P, I32], "dig_arena_bytes": [P, P],
+        "dig_bind_arena": [P, P, I64], "particles_init": [P, I64],
+        "write_particles": [P, P, P, P, P, I64], "read_particles": [P, P, P, P, P, I64, P],
+        "dsmc_step": [P, I32, I32], "sample": [P, I32], "read_moments": [P, I32, P, I64],
+        "read_pairs": [P, P, P, P, P, P, I64, P], "read_counters": [P, P, I32],
+        "dig_cell_state": [P, P, P, I32], "dig_wall_flux": [P, P, I64, P], "dig_particle_count": [P, P],
+        "dig_synchronize": [P], "dig_launch_count": [P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.dig_last_error.argtypes = [P]
+    L.dig_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def make_config(scen, **over) -> DigConfig:
+    g = scen.gas
+    cfg = DigConfig()
+    cfg.mass, cfg.d_ref, cfg.omega, cfg.T_ref = g.mass, g.d_ref, g.omega, g.T_ref
+    cfg.alpha, cfg.Z_rot, cfg.rot_dof = g.alpha, g.Z_rot, g.rot_dof
+    cfg.max_cross = 4096
+    cfg.F_N, cfg.dt, cfg.seed = scen.F_N, scen.dt, scen.seed
+    cfg.n_init, cfg.T_init = scen.n_init, scen.T_init
+    for i in range(3):
+        cfg.u_init[i] = scen.u_init[i]
+    cfg.mu_ref = g.mu_ref()
+    cfg.Kn, cfg.L_ref = scen.Kn, scen.L
+    cfg.n_a, cfg.N_s, cfg.N_m, cfg.passes = 1000, 100, 500, 3
+    cfg.eps_m, cfg.KnD_max = 1e-6, 1.0
+    cfg.capacity = scen.capacity or 2 * scen.n_particles
+    cfg.wait_timeout_s = 600.0
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Solver:
+    """One DSMC context on one CUDA device (the C ABI, with torch-owned memory)."""
+
+    def __init__(self, scen, device: str = "cuda:0", stream=None, **over):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2607_08195_gb300.Solver needs a CUDA device (no CPU fallback)")
+        self.L = load_library()
+        self.scen = scen
+        self.device = torch.device(device)
+        self.cfg = make_config(scen, **over)
+        h = C.c_void_p()
+        self._check(self.L.dig_create(C.byref(self.cfg), C.byref(h)), None)
+        self.h = h
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._check(self.L.dig_set_stream(self.h, C.c_void_p(self.stream.cuda_stream)))
+        m = scen.mesh
+        self.n_tets = len(m.tets)
+        bcs = (DigBC * max(1, len(m.bcs)))()
+        for i, b in enumerate(m.bcs):
+            bcs[i].kind, bcs[i].T, bcs[i].n = b["kind"], b["T"], b["n"]
+            for q in range(3):
+                bcs[i].U[q] = b["U"][q]
+        nodes = np.ascontiguousarray(m.nodes, np.float64)
+        tets = np.ascontiguousarray(m.tets, np.int32)
+        tag = np.ascontiguousarray(m.face_tag, np.int32)
+        self._check(self.L.mesh_load(self.h, _p(nodes), len(nodes), _p(tets), len(tets), _p(tag),
+                                     C.cast(bcs, C.c_void_p), len(m.bcs)))
+        nb = C.c_int64(0)
+        self._check(self.L.dig_arena_bytes(self.h, C.byref(nb)))
+        self.arena_bytes = nb.value
+        self.arena = torch.empty(self.arena_bytes + 256, dtype=torch.uint8, device=self.device)
+        ptr = self.arena.data_ptr()
+        ptr = (ptr + 255) & ~255
+        self._check(self.L.dig_bind_arena(self.h, C.c_void_p(ptr), self.arena_bytes))
+
+    # ---------------------------------------------------------------- basics
+    def _check(self, rc, h=-1):
+        if rc != 0:
+            hh = self.h if h == -1 else h
+            msg = self.L.dig_last_error(hh).decode() if hh else ""
+            raise DigError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.dig_synchronize(self.h)
+            self.L.dig_destroy(self.h)
+            self.h = None
+            self.arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- particles
+    def init(self, n=None):
+        self._check(self.L.particles_init(self.h, self.scen.n_particles if n is None else n))
+
+    def write(self, x, v, Ir, cell):
+        x = np.ascontiguousarray(x, np.float64)
+        v = np.ascontiguousarray(v, np.float32)
+        Ir = None if Ir is None else np.ascontiguousarray(Ir, np.float32)
+        cell = np.ascontiguousarray(cell, np.int32)
+        self._check(self.L.write_particles(self.h, _p(x), _p(v), _p(Ir), _p(cell), len(cell)))
+
+    def count(self):
+        n = C.c_int64(0)
+        self._check(self.L.dig_particle_count(self.h, C.byref(n)))
+        return n.value
+
+    def read(self):
+        N = self.count()
+        x = np.zeros((N, 3), np.float64)
+        v = np.zeros((N, 3), np.float32)
+        Ir = np.zeros(N, np.float32)
+        cell = np.zeros(N, np.int32)
+        n = C.c_int64(0)
+        self._check(self.L.read_particles(self.h, _p(x), _p(v), _p(Ir), _p(cell), N, C.byref(n)))
+        return x, v, Ir, cell
+
+    def step(self, n=1, flags=EWMA):
+        self._check(self.L.dsmc_step(self.h, n, flags))
+
+    def sample(self, action):
+        self._check(self.L.sample(self.h, action))
+
+    def synchronize(self):
+        self._check(self.L.dig_synchronize(self.h))
+
+    def moments(self, which, out=None):
+        k = NMAC if which & MACRO else NPHI
+        if out is None:
+            out = np.zeros((self.n_tets, k), np.float64)
+        self._check(self.L.read_moments(self.h, which, _p(out), out.size))
+        return out
+
+    def pairs(self):
+        n = C.c_int64(0)
+        self._check(self.L.read_pairs(self.h, None, None, None, None, None, 0, C.byref(n)))
+        N = n.value
+        a = [np.zeros(N, np.int32) for _ in range(4)]
+        acc = np.zeros(N, np.uint8)
+        self._check(self.L.read_pairs(self.h, *[_p(x) for x in a], _p(acc), N, C.byref(n)))
+        return np.stack(a + [acc.astype(np.int32)], axis=1)
+
+    def counters(self):
+        out = np.zeros(len(COUNTERS), np.int64)
+        self._check(self.L.read_counters(self.h, _p(out), len(COUNTERS)))
+        return dict(zip(COUNTERS, out.tolist()))
+
+    def cell_state(self, cmax=None, rem=None):
+        if cmax is None:
+            cm = np.zeros(self.n_tets, np.float32)
+            rm = np.zeros(self.n_tets, np.float64)
+            self._check(self.L.dig_cell_state(self.h, _p(cm), _p(rm), 0))
+            return cm, rm
+        cm = np.ascontiguousarray(cmax, np.float32)
+        rm = np.ascontiguousarray(rem, np.float64)
+        self._check(self.L.dig_cell_state(self.h, _p(cm), _p(rm), 1))
+
+    def wall_flux(self):
+        n = C.c_int64(0)
+        self.L.dig_wall_flux(self.h, None, 0, C.byref(n))
+        out = np.zeros((n.value, 5), np.float64)
+        self._check(self.L.dig_wall_flux(self.h, _p(out), out.size, C.byref(n)))
+        return out
+
+    def launches(self):
+        n = C.c_int64(0)
+        self._check(self.L.dig_launch_count(self.h, C.byref(n)))
+        return n.value

@@ -1,0 +1,81 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol that
+include/dig.h declares; the binding's structs match the header's layout.
+No compute calls (no GPU here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_2607_08195_gb300 import dig
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dig.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2607_08195_gb300 import build
+
+    build.build()
+    return dig.load_library()
+
+
+def test_header_lists_match_binding():
+    assert declared_functions() == sorted(dig.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_config_struct_layout():
+    # field order and sizes of dig_config as in include/dig.h (no padding surprises)
+    assert ctypes.sizeof(dig.DigConfig) == 8 * 6 + 4 * 2 + 8 * 3 + 8 + 8 + 8 * 3 + 8 * 3 + 4 * 4 + 8 * 2 + 8 + 8 + 4 * 2
+    assert ctypes.sizeof(dig.DigBC) == 48
+
+
+def test_create_rejects_bad_config(lib):
+    cfg = dig.DigConfig()
+    h = ctypes.c_void_p()
+    assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == -1  # zero mass / dt
+
+
+def test_mesh_load_host_validation(lib):
+    """mesh_load runs on the host: bad meshes are rejected without a GPU."""
+    import numpy as np
+
+    from paper_2607_08195_gb300 import workload as W
+
+    s = W.config_small()
+    cfg = dig.make_config(s)
+    h = ctypes.c_void_p()
+    assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    m = s.mesh
+    bcs = (dig.DigBC * 2)()
+    tag = np.full_like(m.face_tag, -1)
+    nodes = np.ascontiguousarray(m.nodes)
+    tets = np.ascontiguousarray(m.tets)
+    rc = lib.mesh_load(h, nodes.ctypes.data, len(nodes), tets.ctypes.data, len(tets), tag.ctypes.data,
+                       ctypes.cast(bcs, ctypes.c_void_p), 2)
+    assert rc == -2
+    assert b"boundary face" in lib.dig_last_error(h)
+    tag = np.ascontiguousarray(m.face_tag)
+    rc = lib.mesh_load(h, nodes.ctypes.data, len(nodes), tets.ctypes.data, len(tets), tag.ctypes.data,
+                       ctypes.cast(bcs, ctypes.c_void_p), 2)
+    assert rc == 0
+    nb = ctypes.c_int64(0)
+    assert lib.dig_arena_bytes(h, ctypes.byref(nb)) == 0
+    assert nb.value > 40 * cfg.capacity * 2
+    lib.dig_destroy(h)

@@ -1,0 +1,203 @@
+"""GPU (CUDA path through the C ABI) against the CPU oracle, element by element.
+
+The particle loop is specified as a fixed sequence of IEEE operations (no
+contraction, own FP32 ln/exp, counter-based Philox streams), so cell ids,
+order, positions, velocities, rotational energies and candidate-pair lists
+are compared bit for bit.  The per-step cell sums are accumulated in FP32 on
+the GPU and in FP64 by the oracle: they are compared within the FP32
+summation bound (see tol_phi).
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from oracle import orc
+from paper_2607_08195_gb300 import workload as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2607_08195_gb300 import dig  # noqa: E402
+
+
+GPU_ONLY = ("tile_cells", "stage_cap", "wait_timeout_s")
+
+
+def pair(scen, **over):
+    """A GPU solver and an oracle on the same scenario and overrides."""
+    oo = {k: v for k, v in over.items() if k not in GPU_ONLY}
+    return dig.Solver(scen, "cuda:0", **over), orc.Oracle(scen, **oo)
+
+
+def assert_same_particles(g, o):
+    xg, vg, Ig, cg = g.read()
+    xo, vo, Io, co = o.read()
+    assert len(cg) == len(co)
+    assert np.array_equal(cg, co), f"cells differ at {np.flatnonzero(cg != co)[:10]}"
+    bad = np.flatnonzero(np.any(xg != xo, axis=1))
+    assert len(bad) == 0, f"positions differ at {bad[:10]}: {xg[bad[:3]]} vs {xo[bad[:3]]}"
+    badv = np.flatnonzero(np.any(vg != vo, axis=1))
+    assert len(badv) == 0, f"velocities differ at {badv[:10]}: {vg[badv[:3]]} vs {vo[badv[:3]]}"
+    assert np.array_equal(Ig, Io)
+    return xg, vg, Ig, cg
+
+
+def tol_phi(mo, nmax):
+    """FP32 sums of <= nmax terms: |error| <= nmax * 2^-24 * sum|terms| per
+    component; bounded here by the oracle's magnitude scale per component."""
+    scale = np.abs(mo).max(axis=0)
+    return 4 * nmax * 2.0 ** -24 * np.maximum(scale, 1e-30)
+
+
+def test_init_bit_exact():
+    s = W.config_small()
+    g, o = pair(s)
+    g.init()
+    o.init()
+    assert_same_particles(g, o)
+
+
+def test_single_step_from_written_state():
+    """One step from an identical serialised state: cells, order, positions,
+    velocities and every candidate pair (i, j, accept) are bit-identical."""
+    s = W.config_small(seed=11)
+    rng = np.random.default_rng(3)
+    x, v, Ir, cell = W.random_particles(rng, s, 20_000)
+    g, o = pair(s)
+    g.write(x, v, Ir, cell)
+    o.write(x, v, Ir, cell)
+    assert_same_particles(g, o)
+    g.step(1, dig.EWMA | dig.INST | dig.RECORD_PAIRS | dig.SYNC)
+    o.step(1, orc.EWMA | orc.RECORD_PAIRS)
+    assert_same_particles(g, o)
+    pg, po = g.pairs(), o.pairs()
+    assert len(pg) == len(po) > 1000
+    assert np.array_equal(pg, po)
+    mg, mo = g.moments(dig.PHI_INST), o.moments(orc.PHI_INST)
+    nmax = np.bincount(o.read()[3]).max()
+    assert np.all(np.abs(mg - mo) <= tol_phi(mo, nmax))
+    cg, co = g.cell_state(), o.cell_state()
+    assert np.array_equal(cg[0], co[0])
+    assert np.array_equal(cg[1], co[1])
+
+
+def test_multi_step_bit_exact_and_averages():
+    """30 steps from the initial state: the whole particle state stays
+    bit-identical; counters equal; time averages within FP32-sum tolerance."""
+    s = W.config_small(seed=1)
+    g, o = pair(s, n_a=50)
+    g.init()
+    o.init()
+    fl = dig.EWMA | dig.WINDOW | dig.CUMUL | dig.INST | dig.WALLFLUX
+    g.step(30, fl | dig.SYNC)
+    o.step(30, orc.EWMA | orc.WINDOW | orc.CUMUL)
+    assert_same_particles(g, o)
+    cg, co = g.counters(), o.counters()
+    for k in ("steps", "cand", "coll", "cross", "wall", "removed", "stuck"):
+        assert cg[k] == co[k], (k, cg[k], co[k])
+    nmax = 80
+    for w in (dig.PHI_EWMA, dig.PHI_WINDOW, dig.PHI_CUM):
+        mg, mo = g.moments(w), o.moments(w)
+        assert np.all(np.abs(mg - mo) <= 30 * tol_phi(mo, nmax)), w
+        Mg, Mo = g.moments(w | dig.MACRO), o.moments(w | dig.MACRO)
+        # rho, u, T: relative 1e-5 of their natural scales
+        assert np.allclose(Mg[:, 1], Mo[:, 1], rtol=1e-12)
+        assert np.all(np.abs(Mg[:, 2:5] - Mo[:, 2:5]) <= 1e-3)  # m/s
+        assert np.allclose(Mg[:, 5], Mo[:, 5], rtol=1e-5)
+    fg, fo = g.wall_flux(), o.wall_flux()
+    assert np.array_equal(fg[:, 0], fo[:, 0])
+    assert np.allclose(fg, fo, rtol=1e-9, atol=1e-9 * np.abs(fo).max())
+
+
+def test_diatomic_bit_exact():
+    """Nitrogen with Borgnakke-Larsen exchange: rotational energies bit-exact."""
+    s = W.cavity_scenario(4, 12_000, 0.05, seed=4, gas=W.NITROGEN)
+    g, o = pair(s)
+    g.init()
+    o.init()
+    g.step(12, dig.EWMA | dig.SYNC)
+    o.step(12, orc.EWMA)
+    assert_same_particles(g, o)
+    assert g.counters()["lb"] == o.counters()["lb"] > 0
+
+
+@pytest.mark.parametrize("tile_cells,stage_cap", [(1, 4096), (7, 512), (256, 8192)])
+def test_tiling_does_not_change_results(tile_cells, stage_cap):
+    """Ragged tiles (cells not a multiple of the tile) and small shared-memory
+    stages (cells grouped several times per CTA) give identical results."""
+    s = W.cavity_scenario(5, 15_000, 0.1, seed=6)
+    g, o = pair(s, tile_cells=tile_cells, stage_cap=stage_cap)
+    g.init()
+    o.init()
+    g.step(4, dig.EWMA | dig.SYNC)
+    o.step(4, orc.EWMA)
+    assert_same_particles(g, o)
+
+
+def test_edge_cases():
+    s = W.config_small(seed=5)
+    # no particles at all
+    g = dig.Solver(s, "cuda:0")
+    g.write(np.zeros((0, 3)), np.zeros((0, 3), np.float32), np.zeros(0, np.float32), np.zeros(0, np.int32))
+    g.step(3, dig.EWMA | dig.SYNC)
+    assert g.count() == 0
+    # one particle; two particles in one cell
+    g2, o2 = pair(s)
+    cen = s.mesh.nodes[s.mesh.tets[17]].mean(axis=0)
+    x = np.array([cen, cen + 1e-9])
+    v = np.array([[300.0, -50.0, 20.0], [-100.0, 10.0, 0.0]], np.float32)
+    for n in (1, 2):
+        g2.write(x[:n], v[:n], np.zeros(n, np.float32), np.full(n, 17, np.int32))
+        o2.write(x[:n], v[:n], np.zeros(n, np.float32), np.full(n, 17, np.int32))
+        g2.step(5, dig.EWMA | dig.SYNC)
+        o2.step(5, orc.EWMA)
+        assert_same_particles(g2, o2)
+
+
+def test_all_particles_in_one_cell_overflow_is_reported():
+    """A cell holding more particles than the shared-memory stage is reported
+    as DIG_ERR_CAPACITY (host check of a device status bit), not silently run."""
+    s = W.config_small(seed=2)
+    g = dig.Solver(s, "cuda:0", stage_cap=256)
+    n = 600
+    cen = s.mesh.nodes[s.mesh.tets[40]].mean(axis=0)
+    x = np.repeat(cen[None], n, axis=0)
+    v = np.zeros((n, 3), np.float32)
+    with pytest.raises(dig.DigError, match="CAPACITY"):
+        g.write(x, v, np.zeros(n, np.float32), np.full(n, 40, np.int32))
+        g.step(1, dig.SYNC)
+
+
+def test_crossing_limit_matches_oracle():
+    """With a crossing cap of 1 per step the truncated tracks are identical on
+    both sides and the GPU reports DIG_ERR_STUCK."""
+    s = W.config_small(seed=8)
+    g, o = dig.Solver(s, "cuda:0", max_cross=1), orc.Oracle(s, max_cross=1)
+    g.init()
+    o.init()
+    with pytest.raises(dig.DigError, match="STUCK"):
+        g.step(1, dig.SYNC)
+    o.step(1, 0)
+    assert g.counters()["stuck"] == o.counters()["stuck"] > 0
+    assert_same_particles(g, o)
+
+
+def test_full_size_workload_one_step():
+    """The 8M-particle, 162,000-tet cavity (the benchmarked workload, same
+    launch configuration as bench.py): one step from the initial state,
+    bit-identical to the oracle over every particle."""
+    s = W.config_c2()
+    g, o = pair(s)
+    g.init()
+    o.init()
+    g.step(1, dig.EWMA | dig.SYNC)
+    o.step(1, orc.EWMA)
+    xg, vg, Ig, cg = assert_same_particles(g, o)
+    assert len(cg) == s.n_particles
+    cg_, co_ = g.counters(), o.counters()
+    assert cg_["coll"] == co_["coll"] and cg_["cross"] == co_["cross"]
