@@ -54,6 +54,7 @@ extern "C" {
 #define DIG_INST 16        /* keep the instantaneous sums of the last step */
 #define DIG_WALLFLUX 32    /* accumulate momentum/energy exchanged with each wall face */
 #define DIG_SYNC 64        /* wait for the steps and check the device status before returning */
+#define DIG_TIMING 128     /* record CUDA events around every cell-pass launch (see dig_kernel_time) */
 
 /* sample() actions */
 #define DIG_RESET_WINDOW 1
@@ -108,7 +109,7 @@ typedef struct dig_config {
   double KnD_max;    /* threshold of the cell Knudsen criterion */
   int64_t capacity;  /* particle capacity of the arena */
   double wait_timeout_s; /* time limit of host waits (<= 0: 600 s) */
-  int32_t stage_cap;     /* particles staged in shared memory per CTA (<= 0: 4096) */
+  int32_t stage_cap;     /* particles staged in shared memory per CTA (<= 0: 3072) */
   int32_t tile_cells;    /* cells per CTA of the cell pass (<= 0: chosen from the load) */
 } dig_config;
 
@@ -205,8 +206,12 @@ int dig_wall_flux(dig_ctx* ctx, double* out, int64_t cap, int64_t* n_bfaces);
 int dig_particle_count(dig_ctx* ctx, int64_t* n);
 /* wait for all queued work; returns the first device-side error, if any */
 int dig_synchronize(dig_ctx* ctx);
-/* number of kernels the library launched since the context was created */
+/* number of kernels the library launched (all contexts of the process) */
 int dig_launch_count(dig_ctx* ctx, int64_t* n);
+/* Sum of the device times of the cell-pass launches recorded with DIG_TIMING
+ * since the last call (CUDA events on the context's stream; waits for them),
+ * and how many launches they were.  Resets the record. */
+int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

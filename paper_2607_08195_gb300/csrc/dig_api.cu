@@ -108,9 +108,12 @@ struct dig_ctx {
   bool have_particles = false;
   int64_t step = 0;
   int64_t n_ewma = 0, n_win = 0, n_cum = 0, host_steps = 0;
-  int tile_cells = 0, stage_cap = 4096;
+  int tile_cells = 0, stage_cap = 3072;
   float cmax0 = 0.0f;
   cudaEvent_t ev = nullptr;
+  std::vector<cudaEvent_t> tev;  // event pairs around timed cell passes
+  size_t tev_used = 0;
+  bool timing = false;
 };
 
 static int fail(dig_ctx* c, int code, const char* msg) {
@@ -151,6 +154,7 @@ int dig_create(const dig_config* cfg, dig_ctx** out) {
 int dig_destroy(dig_ctx* ctx) {
   if (!ctx) return DIG_ERR_ARG;
   if (ctx->ev) cudaEventDestroy(ctx->ev);
+  for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   delete ctx;
   return DIG_OK;
 }
@@ -349,20 +353,18 @@ static size_t layout(dig_ctx* ctx, char* base) {
     double* xs = A.take<double>(3 * cap);
     float* vs = A.take<float>(3 * cap);
     float* Is = A.take<float>(cap);
+    int* mc = A.take<int>(cap);
     ctx->buf[b] = Buf{xs, xs ? xs + cap : nullptr, xs ? xs + 2 * cap : nullptr,
-                      vs, vs ? vs + cap : nullptr, vs ? vs + 2 * cap : nullptr, Is};
+                      vs, vs ? vs + cap : nullptr, vs ? vs + 2 * cap : nullptr, Is, mc};
   }
   P.cs = A.take<int>(n + 1);
   P.as = A.take<int>(n + 1);
   P.nst = A.take<int>(n);
   P.sbase = A.take<int>(n);
-  P.nmov = A.take<int>(n);
+  P.nold = A.take<int>(n);
   P.na = A.take<int>(n);
   P.fill = A.take<int>(n);
-  P.mkey = A.take<int>(cap);
-  P.mcell = A.take<int>(cap);
   P.aq = A.take<int>(cap);
-  P.akey = A.take<int>(cap);
   P.cmax = A.take<float>(n);
   P.rem = A.take<double>(n);
   P.phi_inst = A.take<double>(NPHI * n);
@@ -452,7 +454,7 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   CK(cudaMemsetAsync(P.state, 0, 8 * sizeof(int), s));
   CK(cudaMemsetAsync(P.cs, 0, (n + 1) * sizeof(int), s));
   CK(cudaMemsetAsync(P.as, 0, (n + 1) * sizeof(int), s));
-  for (int* q : {P.nst, P.sbase, P.nmov, P.na, P.fill}) CK(cudaMemsetAsync(q, 0, n * sizeof(int), s));
+  for (int* q : {P.nst, P.sbase, P.nold, P.na, P.fill}) CK(cudaMemsetAsync(q, 0, n * sizeof(int), s));
   CK(cudaMemsetAsync(P.pair_count, 0, sizeof(unsigned long long), s));
   CK(cudaStreamSynchronize(s));  // host tables are freed by the caller's lifetime; keep them anyway
   if (!ctx->ev) CK(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));
@@ -516,13 +518,24 @@ static void choose_tile(dig_ctx* ctx) {
 }
 
 // one gather/collide/move pass followed by the counting-sort bookkeeping
+static cudaEvent_t timing_event(dig_ctx* ctx) {
+  if (ctx->tev_used == ctx->tev.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    ctx->tev.push_back(e);
+  }
+  return ctx->tev[ctx->tev_used++];
+}
+
 static void pass(dig_ctx* ctx, int pass_flags, int sflags, uint32_t step_coll, uint32_t step_move, int ewma_first) {
   const int other = 1 - ctx->cur;
+  if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
   launch_cell_pass(ctx->P, ctx->buf[ctx->cur], ctx->buf[other], pass_flags, sflags, step_coll, step_move,
                    ewma_first, ctx->tile_cells, ctx->stage_cap, ctx->stream);
+  if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
   ctx->cur = other;
   launch_scan(ctx->P, ctx->stream);
-  launch_scatter(ctx->P, ctx->stream);
+  launch_scatter(ctx->P, ctx->buf[ctx->cur].mc, ctx->stream);
 }
 
 // particles just written as arrivals into buf[cur] slots [0, n): sort them
@@ -530,7 +543,7 @@ static int settle_new_particles(dig_ctx* ctx, int64_t n) {
   ctx->N = n;
   choose_tile(ctx);
   launch_scan(ctx->P, ctx->stream);
-  launch_scatter(ctx->P, ctx->stream);
+  launch_scatter(ctx->P, ctx->buf[ctx->cur].mc, ctx->stream);
   // the first cell pass reads only arrivals (no stayers): gather into the other buffer
   pass(ctx, 0, 0, 0, 0, 0);
   ctx->have_particles = true;
@@ -541,7 +554,7 @@ static int reset_grouping(dig_ctx* ctx, int64_t n) {
   Params& P = ctx->P;
   const size_t nc = (size_t)ctx->n_tets;
   cudaStream_t s = ctx->stream;
-  for (int* q : {P.nst, P.sbase, P.nmov, P.na, P.fill}) CK(cudaMemsetAsync(q, 0, nc * sizeof(int), s));
+  for (int* q : {P.nst, P.sbase, P.nold, P.na, P.fill}) CK(cudaMemsetAsync(q, 0, nc * sizeof(int), s));
   int st[3] = {0, 0, (int)n};
   CK(cudaMemcpyAsync(P.state, st, sizeof st, cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
@@ -610,6 +623,7 @@ int dsmc_step(dig_ctx* ctx, int32_t n_steps, int32_t flags) {
   if (n_steps == 0) return DIG_OK;
   const int sflags = flags & (S_EWMA | S_WINDOW | S_CUMUL | S_INST | S_WALLFLUX);
   const uint32_t t0 = (uint32_t)ctx->step;
+  ctx->timing = (flags & DIG_TIMING) != 0;
   for (int s = 0; s <= n_steps; ++s) {
     int pf = 0, sf = 0, first = 0;
     if (s > 0) {
@@ -632,6 +646,7 @@ int dsmc_step(dig_ctx* ctx, int32_t n_steps, int32_t flags) {
       if (sflags & S_CUMUL) ctx->n_cum++;
     }
   }
+  ctx->timing = false;
   ctx->step += n_steps;
   ctx->host_steps += n_steps;
   if (flags & DIG_SYNC) return check_status(ctx);
@@ -756,6 +771,22 @@ int dig_particle_count(dig_ctx* ctx, int64_t* n) {
   int rc = wait_stream(ctx);
   *n = N;
   return rc;
+}
+
+int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches) {
+  if (!ctx || !total_ms || !launches) return DIG_ERR_ARG;
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < ctx->tev_used; i += 2) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, ctx->tev[i], ctx->tev[i + 1]));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = (int64_t)(ctx->tev_used / 2);
+  ctx->tev_used = 0;
+  return DIG_OK;
 }
 
 int dig_launch_count(dig_ctx* ctx, int64_t* n) {

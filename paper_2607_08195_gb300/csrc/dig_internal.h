@@ -44,6 +44,7 @@ struct BFaceDev {
 struct Buf {
   double *x, *y, *z;
   float *vx, *vy, *vz, *Ir;
+  int* mc;  // cell of the particle at each slot after the move that wrote it (-1: removed)
 };
 
 struct Params {
@@ -72,16 +73,13 @@ struct Params {
   double na_a, na_b;        // EWMA weights (n_a-1)/n_a and 1/n_a
   // per-cell grouping and sort state
   int* cs;      // [n+1] start of each cell in the current grouping
-  int* as;      // [n+1] start of each cell's arrivals in aq/akey
+  int* as;      // [n+1] start of each cell's arrivals in aq
   int* nst;     // [n] stayers count
-  int* sbase;   // [n] buffer slot of the first stayer
-  int* nmov;    // [n] movers written at the back of the cell's range
+  int* sbase;   // [n] first slot of the cell's range in the last written buffer
+  int* nold;    // [n] particles of the cell in the last written buffer
   int* na;      // [n] arrivals counted for the next grouping
   int* fill;    // [n] scatter cursor
-  int* mkey;    // [cap] canonical key of the mover at this slot
-  int* mcell;   // [cap] destination cell of the mover at this slot (-1: removed)
-  int* aq;      // [cap] arrival: buffer slot
-  int* akey;    // [cap] arrival: canonical key
+  int* aq;      // [cap] arrival lists: buffer slot of each arrival
   float* cmax;  // [n] (sigma c_r)_max
   double* rem;  // [n] NTC remainder
   double* phi_inst;  // [NPHI][n]
@@ -104,7 +102,7 @@ void launch_init(const Params& P, const Buf& out, int n, cudaStream_t s);
 void launch_write(const Params& P, const Buf& out, const double* xs, const float* vs, const float* Is,
                   const int* cells, int n, cudaStream_t s);
 void launch_scan(const Params& P, cudaStream_t s);
-void launch_scatter(const Params& P, cudaStream_t s);
+void launch_scatter(const Params& P, const int* mc, cudaStream_t s);
 void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags,
                       uint32_t step_coll, uint32_t step_move, int ewma_first, int tile_cells,
                       int stage_cap, cudaStream_t s);

@@ -11,15 +11,18 @@
 // same cell, then sample; Sec. 4 keeps per-cell particle buckets):
 //   k_cell_pass  one CTA per tile of cells.  Gathers the tile's particles in
 //                the canonical order (stayers, then arrivals ranked by their
-//                previous canonical position) into shared memory, runs the NTC
-//                collisions one thread per cell, samples the moments, then
-//                moves every particle (face-by-face tracking, walls) and writes
-//                it back: stayers at the front of the cell's range, movers at
-//                the back with their destination cell.
+//                previous slot) into shared memory, runs the NTC collisions
+//                one thread per cell, samples the moments, then moves every
+//                particle and writes it back to its canonical slot with the
+//                cell it ended in.  The move runs in two passes: all particles
+//                take the cheap path (x + v dt, FP32-proven inside test); the
+//                few that fail it are queued and tracked face by face, densely
+//                packed, so the FP64 work of crossings is not diluted by
+//                divergence (FP64 issues at 1/64 of the FP32 rate here).
 //   k_scan_*     exclusive scans of (stayers + arrivals) and arrivals per cell.
 //   k_scatter    appends each mover to its destination cell's arrival list.
-// The next k_cell_pass then sees every cell's particles: the counting sort of
-// the particle loop costs one extra pass over the movers only.
+// The counting sort of the particle loop therefore costs one 4-byte read of
+// the destination cells plus the arrival lists of the movers.
 #include "dig_internal.h"
 
 #include <cstdio>
@@ -208,15 +211,114 @@ __device__ __forceinline__ double dot3(const Plane64& n, double x, double y, dou
   return __fma_rn(n.nz, z, __fma_rn(n.ny, y, __dmul_rn(n.nx, x)));
 }
 
+// FP64 -> FP32 by truncation with integer operations only (no FP64 pipe):
+// |result - x| <= 2^-23 |x|; values below 2^-126 in magnitude become 0.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int e = (hi >> 20) & 0x7ff;
+  const unsigned m = ((unsigned)(hi & 0xfffff) << 3) | (lo >> 29);
+  const unsigned s = (unsigned)hi & 0x80000000u;
+  return e > 896 ? __uint_as_float(s | ((unsigned)(e - 896) << 23) | m) : 0.0f;
+}
+
+// FP32 plane test d - n.x of a truncated position.  Its error against the
+// exact value is below P.margin / 4 (see the margin in dig_api.cu), so
+// s > margin proves that the FP64 test d - n.x >= 0 passes and s < -margin
+// proves that it fails.
+__device__ __forceinline__ float plane_test32(const float4 q, float fx, float fy, float fz) {
+  return q.w - __fmaf_rn(q.z, fz, __fmaf_rn(q.y, fy, q.x * fx));
+}
+
+// Exit face of the ray x + v s from `cell`, exactly as the FP64 rule
+//   argmin over f != entry with b_f = n_f.v > 0 of t_f = max(0, (d_f - n_f.x)/b_f)
+// (ties: lowest f) would choose it.  FP32 interval estimates decide the face
+// when they separate it from the others; only that face's t is then computed
+// in FP64.  Otherwise everything is computed in FP64.  Returns -1 if no face
+// has b_f > 0; *tb receives t of the chosen face.
+__device__ __forceinline__ int exit_face(const Params& P, const Plane64* pl, const float4* pf, int entry,
+                                         double x, double y, double z, double vdx, double vdy, double vdz,
+                                         float vx, float vy, float vz, double* tb) {
+  const float fx = d2f_trunc(x), fy = d2f_trunc(y), fz = d2f_trunc(z);
+  const float eb = 8.0f * 5.9604645e-08f * (fabsf(vx) + fabsf(vy) + fabsf(vz)) + 1e-30f;
+  const float ea = 0.5f * P.margin;
+  float lo[4], hi[4];
+  bool cand[4];
+  bool decided = true;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    cand[f] = false;
+    lo[f] = 0.0f;
+    hi[f] = 0.0f;
+    if (f == entry) continue;
+    const float4 q = pf[f];
+    const float b = __fmaf_rn(q.z, vz, __fmaf_rn(q.y, vy, q.x * vx));
+    if (b < -eb) continue;
+    if (!(b > eb)) {
+      decided = false;
+      continue;
+    }
+    cand[f] = true;
+    const float a = plane_test32(q, fx, fy, fz);
+    const float al = a - ea, ah = a + ea;
+    float tl = al >= 0.0f ? al / (b + eb) : al / (b - eb);
+    float th = ah >= 0.0f ? ah / (b - eb) : ah / (b + eb);
+    tl = fmaxf(tl, 0.0f);
+    th = fmaxf(th, 0.0f);
+    lo[f] = tl - tl * 9.5367432e-07f;
+    hi[f] = th + th * 9.5367432e-07f + 1e-30f;
+  }
+  int best = -1;
+  if (decided) {
+    float H = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (cand[f] && (best < 0 || hi[f] < H)) {
+        best = f;
+        H = hi[f];
+      }
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (cand[f] && f != best && !(lo[f] > H)) decided = false;
+  }
+  if (decided) {
+    if (best < 0) return -1;
+    const Plane64 q = pl[best];
+    const double b = dot3(q, vdx, vdy, vdz);
+    const double a = __dsub_rn(q.d, dot3(q, x, y, z));
+    double tf = __ddiv_rn(a, b);
+    if (tf < 0.0) tf = 0.0;
+    *tb = tf;
+    return best;
+  }
+  best = -1;
+  double t = 0.0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (f == entry) continue;
+    const Plane64 q = pl[f];
+    const double b = dot3(q, vdx, vdy, vdz);
+    if (!(b > 0.0)) continue;
+    const double a = __dsub_rn(q.d, dot3(q, x, y, z));
+    double tf = __ddiv_rn(a, b);
+    if (tf < 0.0) tf = 0.0;
+    if (best < 0 || tf < t) {
+      best = f;
+      t = tf;
+    }
+  }
+  *tb = t;
+  return best;
+}
+
 // Face-by-face tracking of one particle for one time step.  Returns the final
 // cell or -1 when the particle leaves through an open boundary.
 //   x' = x + v t_rem; inside if d_f - n_f.x' >= 0 for every face but the entry
 //   face; else exit face = argmin over faces with n_f.v > 0 of
 //   max(0, (d_f - n_f.x)/(n_f.v)) (ties: lowest f); stop at x' if none or if
 //   t_f >= t_rem; else advance, t_rem -= t_f, cross / reflect / leave.
-// The FP32 plane test is only a filter: it accepts "inside" only when every
-// plane clears `margin`, a bound on the FP32 rounding error of the test, so the
-// FP64 test would give the same answer; anything closer runs the FP64 test.
+// FP32 tests only shortcut decisions they can prove (see plane_test32 and
+// exit_face); every value that is kept is computed in FP64 as stated.
 template <bool DIAT>
 __device__ int track(const Params& P, double& x, double& y, double& z, float& vx, float& vy, float& vz, float& I,
                      int cell, uint32_t slot, uint32_t step, bool flux, Cnt& cnt) {
@@ -231,19 +333,20 @@ __device__ int track(const Params& P, double& x, double& y, double& z, float& vx
     const double vdx = (double)vx, vdy = (double)vy, vdz = (double)vz;
     const double xn = __fma_rn(vdx, t, x), yn = __fma_rn(vdy, t, y), zn = __fma_rn(vdz, t, z);
     const Plane64* pl = P.plane + 4 * (size_t)cell;
-    bool inside = true;
+    const float4* pf = P.plane32 + 4 * (size_t)cell;
+    bool all_in = true, some_out = false;
     {
-      const float4* pf = P.plane32 + 4 * (size_t)cell;
-      const float fx = (float)xn, fy = (float)yn, fz = (float)zn;
+      const float fx = d2f_trunc(xn), fy = d2f_trunc(yn), fz = d2f_trunc(zn);
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         if (f == entry) continue;
-        const float4 q = __ldg(pf + f);
-        const float s = q.w - __fmaf_rn(q.z, fz, __fmaf_rn(q.y, fy, q.x * fx));
-        if (!(s > P.margin)) inside = false;
+        const float s = plane_test32(pf[f], fx, fy, fz);
+        if (!(s > P.margin)) all_in = false;
+        if (s < -P.margin) some_out = true;
       }
     }
-    if (!inside) {
+    bool inside = all_in;
+    if (!all_in && !some_out) {
       inside = true;
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
@@ -258,22 +361,8 @@ __device__ int track(const Params& P, double& x, double& y, double& z, float& vx
       z = zn;
       return cell;
     }
-    int best = -1;
     double tb = 0.0;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      if (f == entry) continue;
-      const Plane64 q = pl[f];
-      const double b = dot3(q, vdx, vdy, vdz);
-      if (!(b > 0.0)) continue;
-      const double a = __dsub_rn(q.d, dot3(q, x, y, z));
-      double tf = __ddiv_rn(a, b);
-      if (tf < 0.0) tf = 0.0;
-      if (best < 0 || tf < tb) {
-        best = f;
-        tb = tf;
-      }
-    }
+    const int best = exit_face(P, pl, pf, entry, x, y, z, vdx, vdy, vdz, vx, vy, vz, &tb);
     if (best < 0 || tb >= t) {
       x = xn;
       y = yn;
@@ -413,7 +502,8 @@ __device__ void sample_cell(const Params& P, int cell, const float* vx, const fl
     }
   }
   const size_t n = (size_t)P.n_cells;
-  const int np = DIAT ? 17 : 13;
+  constexpr int np = DIAT ? 17 : 13;
+#pragma unroll
   for (int q = 0; q < np; ++q) {
     const double ph = q == 0 ? (double)N : (double)s[q];
     const size_t o = (size_t)q * n + cell;
@@ -443,25 +533,35 @@ __device__ __forceinline__ void flush_counters(const Params& P, const Cnt& c) {
 constexpr int CP_THREADS = 256;
 
 size_t cell_pass_smem(int TC, int CAP, bool diat) {
-  return sizeof(int) * (size_t)(4 * TC + 4) + (size_t)CAP * (sizeof(int) + 3 * sizeof(float)) +
-         (diat ? (size_t)CAP * sizeof(float) : 0);
+  return sizeof(int) * (size_t)(5 * TC + 8) + (size_t)CAP * (2 * sizeof(int) + 3 * sizeof(float) + 1) +
+         (diat ? (size_t)CAP * sizeof(float) : 0) + 16;
 }
 
+// Layout of a particle buffer: the particles of cell c occupy slots
+// [cs[c], cs[c+1]) in canonical order (stayers of the last move first, in
+// their previous order, then arrivals in the order of their previous slot).
+// The pass writes every particle back to its canonical slot with mc[slot]
+// = the cell it is in after the move (-1: left the domain); the next pass
+// finds the stayers of cell c by mc == c over c's old range and the
+// arrivals from the lists built by k_scatter.
 template <bool DIAT>
 __global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf OUT, int pass, int sflags,
                                                           uint32_t step_coll, uint32_t step_move,
                                                           int ewma_first, int TC, int CAP) {
   extern __shared__ __align__(16) unsigned char smem[];
-  int* s_cs = (int*)smem;       // TC+1 global canonical starts
+  int* s_cs = (int*)smem;       // TC+1 canonical starts (global slots)
   int* s_as = s_cs + TC + 1;    // TC+1 arrival starts
-  int* s_nst = s_as + TC + 1;   // TC
-  int* s_sb = s_nst + TC;       // TC
-  int* s_src = s_sb + TC;       // CAP: buffer slot of each staged particle
-  float* s_vx = (float*)(s_src + CAP);
+  int* s_sb = s_as + TC + 1;    // TC old slot range start of each cell
+  int* s_no = s_sb + TC;        // TC old particle count of each cell
+  int* s_nst = s_no + TC;       // TC stayers counted in this pass
+  int* s_src = s_nst + TC;      // CAP: IN slot of each staged particle
+  int* s_q = s_src + CAP;       // CAP: slow-path queue
+  float* s_vx = (float*)(s_q + CAP);
   float* s_vy = s_vx + CAP;
   float* s_vz = s_vy + CAP;
-  float* s_I = DIAT ? s_vz + CAP : nullptr;
-  __shared__ int s_g1;
+  float* s_I = s_vz + CAP;      // CAP if DIAT
+  unsigned char* s_cl = (unsigned char*)(DIAT ? s_I + CAP : s_I);  // local cell of each staged particle
+  __shared__ int s_g1, s_qn;
 
   const int c0 = blockIdx.x * TC;
   if (c0 >= P.n_cells) return;
@@ -477,8 +577,9 @@ __global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf 
     s_cs[i] = P.cs[c0 + i];
     s_as[i] = P.as[c0 + i];
     if (i < nc) {
-      s_nst[i] = P.nst[c0 + i];
       s_sb[i] = P.sbase[c0 + i];
+      s_no[i] = P.nold[c0 + i];
+      s_nst[i] = 0;
     }
   }
   __syncthreads();
@@ -489,6 +590,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf 
       int g1 = g0 + 1;
       while (g1 < nc && s_cs[g1 + 1] - s_cs[g0] <= CAP) ++g1;
       s_g1 = g1;
+      s_qn = 0;
     }
     __syncthreads();
     const int g1 = s_g1;
@@ -500,25 +602,34 @@ __global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf 
       __syncthreads();
       continue;
     }
-    // 1. canonical order: stayers (contiguous in IN), then arrivals ranked by key
+    // 1. canonical order, one warp per cell: stayers found by ballot over the
+    //    cell's old range, then arrivals ranked by their previous slot
     for (int c = g0 + warp; c < g1; c += nwarps) {
-      const int cb = s_cs[c] - gbase, ns = s_nst[c], sb = s_sb[c];
-      for (int k = lane; k < ns; k += 32) s_src[cb + k] = sb + k;
+      const int cell = c0 + c, cb = s_cs[c] - gbase, Nc = s_cs[c + 1] - s_cs[c];
+      const int sb = s_sb[c], no = s_no[c];
+      int ns = 0;
+      for (int k0 = 0; k0 < no; k0 += 32) {
+        const int k = k0 + lane;
+        const bool st = k < no && IN.mc[sb + k] == cell;
+        const unsigned bs = __ballot_sync(0xffffffffu, st);
+        if (st) s_src[cb + ns + __popc(bs & ((1u << lane) - 1u))] = sb + k;
+        ns += __popc(bs);
+      }
       const int a0 = s_as[c], na = s_as[c + 1] - a0;
       if (na <= 32) {
-        const int key = lane < na ? P.akey[a0 + lane] : 0x7fffffff;
-        const int q = lane < na ? P.aq[a0 + lane] : 0;
+        const int key = lane < na ? P.aq[a0 + lane] : 0x7fffffff;
         int rank = 0;
         for (int r = 0; r < na; ++r) rank += (__shfl_sync(0xffffffffu, key, r) < key) ? 1 : 0;
-        if (lane < na) s_src[cb + ns + rank] = q;
+        if (lane < na) s_src[cb + ns + rank] = key;
       } else {
         for (int r = lane; r < na; r += 32) {
-          const int key = P.akey[a0 + r];
+          const int key = P.aq[a0 + r];
           int rank = 0;
-          for (int r2 = 0; r2 < na; ++r2) rank += (P.akey[a0 + r2] < key) ? 1 : 0;
-          s_src[cb + ns + rank] = P.aq[a0 + r];
+          for (int r2 = 0; r2 < na; ++r2) rank += (P.aq[a0 + r2] < key) ? 1 : 0;
+          s_src[cb + ns + rank] = key;
         }
       }
+      for (int k = lane; k < Nc; k += 32) s_cl[cb + k] = (unsigned char)(c - g0);
     }
     __syncthreads();
     // 2. gather velocities (and rotational energies)
@@ -542,58 +653,69 @@ __global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf 
       }
       __syncthreads();
     }
-    // 4. move and write back, one warp per cell
-    for (int c = g0 + warp; c < g1; c += nwarps) {
-      const int cb = s_cs[c] - gbase, Nc = s_cs[c + 1] - s_cs[c], cell = c0 + c, gcb = s_cs[c];
-      int stay = 0, mov = 0;
-      for (int k0 = 0; k0 < Nc; k0 += 32) {
-        const int k = k0 + lane;
-        const bool act = k < Nc;
-        double x = 0, y = 0, z = 0;
-        float vx = 0, vy = 0, vz = 0, I = 0;
-        int dst = cell;
-        if (act) {
-          const int s = s_src[cb + k];
-          x = IN.x[s];
-          y = IN.y[s];
-          z = IN.z[s];
-          vx = s_vx[cb + k];
-          vy = s_vy[cb + k];
-          vz = s_vz[cb + k];
-          if (DIAT) I = s_I[cb + k];
-          if (do_move) dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)(gcb + k), step_move, flux, cnt);
-        }
-        const bool st = act && dst == cell, mv = act && dst != cell;
-        const unsigned bs = __ballot_sync(0xffffffffu, st), bm = __ballot_sync(0xffffffffu, mv);
-        const unsigned lt = (1u << lane) - 1u;
-        int slot = 0;
-        if (st) slot = gcb + stay + __popc(bs & lt);
-        if (mv) slot = gcb + Nc - 1 - (mov + __popc(bm & lt));
-        if (act) {
-          OUT.x[slot] = x;
-          OUT.y[slot] = y;
-          OUT.z[slot] = z;
-          OUT.vx[slot] = vx;
-          OUT.vy[slot] = vy;
-          OUT.vz[slot] = vz;
-          if (DIAT) OUT.Ir[slot] = I;
-        }
-        if (mv) {
-          P.mkey[slot] = gcb + k;
-          P.mcell[slot] = dst;
-          if (dst >= 0) atomicAdd(P.na + dst, 1);
-        }
-        stay += __popc(bs);
-        mov += __popc(bm);
+    // 4a. move, fast path for every particle: x' = x + v dt, proven inside by
+    //     the FP32 plane test; the others go to the queue
+    for (int k = threadIdx.x; k < gN; k += CP_THREADS) {
+      const int s = s_src[k], lc = s_cl[k], cell = c0 + g0 + lc, slot = gbase + k;
+      double x = IN.x[s], y = IN.y[s], z = IN.z[s];
+      const float vx = s_vx[k], vy = s_vy[k], vz = s_vz[k];
+      bool done = true;
+      if (do_move) {
+        const double xn = __fma_rn((double)vx, P.dt, x), yn = __fma_rn((double)vy, P.dt, y),
+                     zn = __fma_rn((double)vz, P.dt, z);
+        const float4* pf = P.plane32 + 4 * (size_t)cell;
+        const float fx = d2f_trunc(xn), fy = d2f_trunc(yn), fz = d2f_trunc(zn);
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          if (!(plane_test32(pf[f], fx, fy, fz) > P.margin)) done = false;
+        x = xn;
+        y = yn;
+        z = zn;
       }
-      if (lane == 0) {
-        P.nst[cell] = stay;
-        P.sbase[cell] = gcb;
-        P.nmov[cell] = mov;
+      if (done) {
+        OUT.x[slot] = x;
+        OUT.y[slot] = y;
+        OUT.z[slot] = z;
+        OUT.vx[slot] = vx;
+        OUT.vy[slot] = vy;
+        OUT.vz[slot] = vz;
+        if (DIAT) OUT.Ir[slot] = s_I[k];
+        OUT.mc[slot] = cell;
+        atomicAdd(s_nst + g0 + lc, 1);
+      } else {
+        s_q[atomicAdd(&s_qn, 1)] = k;
       }
     }
     __syncthreads();
+    // 4b. queued particles: full face-by-face tracking, densely packed
+    const int qn = s_qn;
+    for (int qi = threadIdx.x; qi < qn; qi += CP_THREADS) {
+      const int k = s_q[qi];
+      const int s = s_src[k], lc = s_cl[k], cell = c0 + g0 + lc, slot = gbase + k;
+      double x = IN.x[s], y = IN.y[s], z = IN.z[s];
+      float vx = s_vx[k], vy = s_vy[k], vz = s_vz[k], I = DIAT ? s_I[k] : 0.0f;
+      const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)slot, step_move, flux, cnt);
+      OUT.x[slot] = x;
+      OUT.y[slot] = y;
+      OUT.z[slot] = z;
+      OUT.vx[slot] = vx;
+      OUT.vy[slot] = vy;
+      OUT.vz[slot] = vz;
+      if (DIAT) OUT.Ir[slot] = I;
+      OUT.mc[slot] = dst;
+      if (dst == cell)
+        atomicAdd(s_nst + g0 + lc, 1);
+      else if (dst >= 0)
+        atomicAdd(P.na + dst, 1);
+    }
+    __syncthreads();
     g0 = g1;
+  }
+  // new grouping bookkeeping of this tile's cells
+  for (int c = threadIdx.x; c < nc; c += CP_THREADS) {
+    P.nst[c0 + c] = s_nst[c];
+    P.sbase[c0 + c] = s_cs[c];
+    P.nold[c0 + c] = s_cs[c + 1] - s_cs[c];
   }
   flush_counters(P, cnt);
 }
@@ -741,30 +863,30 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_final(Params P) {
 }
 
 // ---------------------------------------------------------------------------
-// scatter movers into their destination cells' arrival lists
+// scatter movers into their destination cells' arrival lists: a particle at
+// slot q of cell c's range moved if mc[q] != c; new particles (initial
+// state, host-written, injected) occupy the extra slot range
 // ---------------------------------------------------------------------------
-__global__ void k_scatter(Params P) {
+__global__ void k_scatter(Params P, const int* __restrict__ mc) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int c = gw; c < P.n_cells; c += nw) {
-    const int lo = P.sbase[c] + P.nst[c], hi = lo + P.nmov[c];
+    const int lo = P.sbase[c], hi = lo + P.nold[c];
     for (int q = lo + lane; q < hi; q += 32) {
-      const int d = P.mcell[q];
-      if (d >= 0) {
+      const int d = mc[q];
+      if (d != c && d >= 0) {
         const int pos = P.as[d] + atomicAdd(P.fill + d, 1);
         P.aq[pos] = q;
-        P.akey[pos] = P.mkey[q];
       }
     }
   }
   const int lo = P.state[1], hi = P.state[2];
   for (int q = lo + blockIdx.x * blockDim.x + threadIdx.x; q < hi; q += gridDim.x * blockDim.x) {
-    const int d = P.mcell[q];
+    const int d = mc[q];
     if (d >= 0) {
       const int pos = P.as[d] + atomicAdd(P.fill + d, 1);
       P.aq[pos] = q;
-      P.akey[pos] = P.mkey[q];
     }
   }
 }
@@ -827,8 +949,7 @@ __global__ void k_init(Params P, Buf OUT, int n) {
     rng(P, RP_INIT_VEL, (uint32_t)p, 2, 0, 0, w);
     OUT.Ir[p] = -P.T_init * ln_f(u01f(w[0]));
   }
-  P.mkey[p] = p;
-  P.mcell[p] = t;
+  OUT.mc[p] = t;
   atomicAdd(P.na + t, 1);
 }
 
@@ -845,8 +966,7 @@ __global__ void k_write(Params P, Buf OUT, const double* xs, const float* vs, co
   OUT.vz[p] = vs[3 * (size_t)p + 2];
   if (diat) OUT.Ir[p] = Is ? Is[p] : 0.0f;
   const int c = cells[p];
-  P.mkey[p] = p;
-  P.mcell[p] = c;
+  OUT.mc[p] = c;
   atomicAdd(P.na + c, 1);
 }
 
@@ -949,7 +1069,7 @@ void launch_scan(const Params& P, cudaStream_t s) {
   g_launches += 2;
 }
 
-void launch_scatter(const Params& P, cudaStream_t s) {
+void launch_scatter(const Params& P, const int* mc, cudaStream_t s) {
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -957,7 +1077,7 @@ void launch_scatter(const Params& P, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 152;
   }
-  k_scatter<<<sms * 8, 256, 0, s>>>(P);
+  k_scatter<<<sms * 8, 256, 0, s>>>(P, mc);
   ++g_launches;
 }
 

@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdig.so")
 
-EWMA, WINDOW, CUMUL, RECORD_PAIRS, INST, WALLFLUX, SYNC = 1, 2, 4, 8, 16, 32, 64
+EWMA, WINDOW, CUMUL, RECORD_PAIRS, INST, WALLFLUX, SYNC, TIMING = 1, 2, 4, 8, 16, 32, 64, 128
 RESET_WINDOW, RESET_CUMUL, RESET_EWMA = 1, 2, 4
 PHI_INST, PHI_EWMA, PHI_WINDOW, PHI_CUM, MACRO = 0, 1, 2, 3, 16
 NPHI, NMAC = 17, 20
@@ -51,7 +51,7 @@ class DigBC(C.Structure):
 EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mesh_load", "dig_arena_bytes",
            "dig_bind_arena", "particles_init", "write_particles", "read_particles", "dsmc_step", "sample",
            "read_moments", "read_pairs", "read_counters", "dig_cell_state", "dig_wall_flux",
-           "dig_particle_count", "dig_synchronize", "dig_launch_count"]
+           "dig_particle_count", "dig_synchronize", "dig_launch_count", "dig_kernel_time"]
 
 _lib = None
 
@@ -73,7 +73,7 @@ def load_library(path: str = LIB_PATH):
         "dsmc_step": [P, I32, I32], "sample": [P, I32], "read_moments": [P, I32, P, I64],
         "read_pairs": [P, P, P, P, P, P, I64, P], "read_counters": [P, P, I32],
         "dig_cell_state": [P, P, P, I32], "dig_wall_flux": [P, P, I64, P], "dig_particle_count": [P, P],
-        "dig_synchronize": [P], "dig_launch_count": [P, P],
+        "dig_synchronize": [P], "dig_launch_count": [P, P], "dig_kernel_time": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -240,6 +240,11 @@ class Solver:
         out = np.zeros((n.value, 5), np.float64)
         self._check(self.L.dig_wall_flux(self.h, _p(out), out.size, C.byref(n)))
         return out
+
+    def kernel_time(self):
+        ms, n = C.c_double(0), C.c_int64(0)
+        self._check(self.L.dig_kernel_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def launches(self):
         n = C.c_int64(0)
