@@ -127,6 +127,8 @@ typedef struct dig_ctx dig_ctx;
 int dig_create(const dig_config* cfg, dig_ctx** out);
 /* Release the context (the caller then frees its arena). */
 int dig_destroy(dig_ctx* ctx);
+/* message of the last failure of ctx; with ctx NULL, of the calling thread's
+ * last failed context-free call */
 const char* dig_last_error(dig_ctx* ctx);
 /* Queue all later GPU work on this cudaStream_t (NULL = legacy default stream). */
 int dig_set_stream(dig_ctx* ctx, void* cuda_stream);
@@ -212,6 +214,28 @@ int dig_launch_count(dig_ctx* ctx, int64_t* n);
  * since the last call (CUDA events on the context's stream; waits for them),
  * and how many launches they were.  Resets the record. */
 int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches);
+
+/*
+ * dig_sort_by_cell -- stable counting sort by cell, the paper's per-cell
+ * particle buckets (Sec. 4, Listing 2: one particle bucket per owned cell) as
+ * a standalone op on DEVICE arrays, queued on `stream` (a cudaStream_t; NULL =
+ * legacy default stream) and asynchronous.
+ *   cell[n]       (device, int32) cell of each element; entries outside
+ *                 [0, n_cells) are dropped (-1 marks a removed particle)
+ *   cell_start    (device, int32 [n_cells+1]) output: start of each cell's
+ *                 segment in order[], cell_start[n_cells] = kept count
+ *   order         (device, int32 [n]) output: indices of the kept elements,
+ *                 sorted by cell, ties by index
+ *   scratch       (device, 256-byte aligned, >= dig_sort_scratch_bytes(n,
+ *                 n_cells) bytes) caller-owned working memory; its contents
+ *                 on entry do not matter
+ * Errors (host checks only, nothing launched): DIG_ERR_ARG for bad sizes or
+ * pointers, DIG_ERR_CAPACITY for a too small scratch; the message is
+ * dig_last_error(NULL) of the calling thread.  n < 2^31.
+ */
+int dig_sort_scratch_bytes(int64_t n, int32_t n_cells, int64_t* bytes);
+int dig_sort_by_cell(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* cell_start, int32_t* order,
+                     void* scratch, int64_t scratch_bytes, void* stream);
 
 #ifdef __cplusplus
 }

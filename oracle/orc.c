@@ -990,3 +990,22 @@ int orc_wall_flux(orc_ctx* c, double* out, int64_t cap, int64_t* n_bfaces) {
   memcpy(out, c->bflux, sizeof(double) * 5 * c->n_bf);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* standalone stable counting sort by cell                                     */
+/* ------------------------------------------------------------------------- */
+int orc_sort_by_cell(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* cell_start, int32_t* order) {
+  if (n < 0 || n_cells <= 0) return -1;
+  for (int32_t c = 0; c <= n_cells; ++c) cell_start[c] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (cell[i] < -1 || cell[i] >= n_cells) return -1;
+    if (cell[i] >= 0) cell_start[cell[i] + 1]++;
+  }
+  for (int32_t c = 0; c < n_cells; ++c) cell_start[c + 1] += cell_start[c];
+  int32_t* cur = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_cells);
+  for (int32_t c = 0; c < n_cells; ++c) cur[c] = cell_start[c];
+  for (int64_t i = 0; i < n; ++i)
+    if (cell[i] >= 0) order[cur[cell[i]]++] = (int32_t)i;
+  free(cur);
+  return 0;
+}

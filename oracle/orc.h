@@ -92,6 +92,11 @@ int orc_cell_state(orc_ctx* c, float* cmax, double* rem, int32_t write);
 int orc_wall_flux(orc_ctx* c, double* out, int64_t cap, int64_t* n_bfaces);
 int64_t orc_step_index(orc_ctx* c);
 
+/* stable counting sort by cell (the paper's per-cell particle buckets):
+ * cell[n] in [0, n_cells) or -1 (dropped); writes cell_start[n_cells+1] and
+ * order[] = indices of the kept elements sorted by cell, ties by index. */
+int orc_sort_by_cell(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* cell_start, int32_t* order);
+
 /* primitives exposed for the pins */
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 float orc_lnf(float x);

@@ -86,6 +86,7 @@ def lib():
         L.orc_locate.restype = C.c_int32
         L.orc_locate.argtypes = [P, P, C.c_double]
         L.orc_track_one.argtypes = [P, P, P, P, C.c_int64, C.c_int64]
+        L.orc_sort_by_cell.argtypes = [P, C.c_int64, C.c_int32, P, P]
         _lib = L
     return _lib
 
@@ -258,3 +259,14 @@ def expf(x):
 
 def powf(x, a):
     return lib().orc_powf(float(x), float(a))
+
+
+def sort_by_cell(cell, n_cells):
+    """Stable counting sort by cell; -1 entries are dropped."""
+    cell = np.ascontiguousarray(cell, np.int32)
+    cs = np.zeros(n_cells + 1, np.int32)
+    order = np.zeros(max(1, int((cell >= 0).sum())), np.int32)
+    rc = lib().orc_sort_by_cell(_p(cell), len(cell), n_cells, _p(cs), _p(order))
+    if rc != 0:
+        raise ValueError("orc_sort_by_cell: bad input")
+    return cs, order[: cs[-1]]

@@ -22,6 +22,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompi
 UNITS = [
     ("dig_kernels.cu", ["-fmad=false"]),
     ("dig_api.cu", ["-fmad=false"]),
+    ("dig_sort.cu", []),
 ]
 
 

@@ -132,9 +132,17 @@ static int cuda_fail(dig_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
+// message of the last failed call made without a context (dig_sort_by_cell)
+static thread_local char g_err[256] = {0};
+
+static int fail0(int code, const char* msg) {
+  std::snprintf(g_err, sizeof g_err, "%s", msg);
+  return code;
+}
+
 extern "C" {
 
-const char* dig_last_error(dig_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+const char* dig_last_error(dig_ctx* ctx) { return ctx ? ctx->err : g_err; }
 
 int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (!cfg || !out) return DIG_ERR_ARG;
@@ -786,6 +794,28 @@ int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches) {
   *total_ms = tot;
   *launches = (int64_t)(ctx->tev_used / 2);
   ctx->tev_used = 0;
+  return DIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// standalone bucket sort
+// ---------------------------------------------------------------------------
+int dig_sort_scratch_bytes(int64_t n, int32_t n_cells, int64_t* bytes) {
+  if (!bytes || n < 0 || n > INT32_MAX || n_cells <= 0) return fail0(DIG_ERR_ARG, "dig_sort_scratch_bytes: bad sizes");
+  *bytes = (int64_t)sort_scratch_bytes(n, n_cells);
+  return DIG_OK;
+}
+
+int dig_sort_by_cell(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* cell_start, int32_t* order,
+                     void* scratch, int64_t scratch_bytes, void* stream) {
+  if (n < 0 || n > INT32_MAX || n_cells <= 0 || !cell_start || !scratch || (n > 0 && (!cell || !order)))
+    return fail0(DIG_ERR_ARG, "dig_sort_by_cell: bad arguments");
+  if (((uintptr_t)scratch & 255) != 0) return fail0(DIG_ERR_ARG, "dig_sort_by_cell: scratch must be 256-byte aligned");
+  if (scratch_bytes < (int64_t)sort_scratch_bytes(n, n_cells))
+    return fail0(DIG_ERR_CAPACITY, "dig_sort_by_cell: scratch smaller than dig_sort_scratch_bytes()");
+  launch_sort_by_cell(cell, n, n_cells, cell_start, order, (char*)scratch, (cudaStream_t)stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail0(DIG_ERR_CUDA, cudaGetErrorString(e));
   return DIG_OK;
 }
 

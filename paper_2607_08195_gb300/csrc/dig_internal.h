@@ -111,6 +111,9 @@ void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* 
 void launch_moments_ex(const Params& P, const double* phi, double scale, int macro, double* out, double mass,
                        double FN, double kB, cudaStream_t s);
 size_t cell_pass_smem(int tile_cells, int stage_cap, bool diatomic);
+size_t sort_scratch_bytes(long long n, int n_cells);
+void launch_sort_by_cell(const int* cell, long long n, int n_cells, int* cell_start, int* order, char* scratch,
+                         cudaStream_t s);
 int scan_blocks(int n_cells);
 extern long long g_launches;
 

@@ -51,7 +51,8 @@ class DigBC(C.Structure):
 EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mesh_load", "dig_arena_bytes",
            "dig_bind_arena", "particles_init", "write_particles", "read_particles", "dsmc_step", "sample",
            "read_moments", "read_pairs", "read_counters", "dig_cell_state", "dig_wall_flux",
-           "dig_particle_count", "dig_synchronize", "dig_launch_count", "dig_kernel_time"]
+           "dig_particle_count", "dig_synchronize", "dig_launch_count", "dig_kernel_time",
+           "dig_sort_scratch_bytes", "dig_sort_by_cell"]
 
 _lib = None
 
@@ -74,6 +75,7 @@ def load_library(path: str = LIB_PATH):
         "read_pairs": [P, P, P, P, P, P, I64, P], "read_counters": [P, P, I32],
         "dig_cell_state": [P, P, P, I32], "dig_wall_flux": [P, P, I64, P], "dig_particle_count": [P, P],
         "dig_synchronize": [P], "dig_launch_count": [P, P], "dig_kernel_time": [P, P, P],
+        "dig_sort_scratch_bytes": [I64, I32, P], "dig_sort_by_cell": [P, I64, I32, P, P, P, I64, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -250,3 +252,29 @@ class Solver:
         n = C.c_int64(0)
         self._check(self.L.dig_launch_count(self.h, C.byref(n)))
         return n.value
+
+
+def sort_by_cell(cell, n_cells: int, stream=None):
+    """Stable counting sort of a device int32 tensor of cell ids (C ABI
+    dig_sort_by_cell); returns (cell_start, order) device tensors.  Scratch is
+    a torch allocation on the same device."""
+    import torch
+
+    L = load_library()
+    assert cell.dtype == torch.int32 and cell.is_cuda and cell.is_contiguous()
+    n = cell.numel()
+    nb = C.c_int64(0)
+    rc = L.dig_sort_scratch_bytes(n, n_cells, C.byref(nb))
+    if rc:
+        raise DigError(rc, L.dig_last_error(None).decode())
+    scratch = torch.empty(nb.value + 256, dtype=torch.uint8, device=cell.device)
+    sp = (scratch.data_ptr() + 255) & ~255
+    cs = torch.empty(n_cells + 1, dtype=torch.int32, device=cell.device)
+    order = torch.empty(max(n, 1), dtype=torch.int32, device=cell.device)
+    s = stream if stream is not None else torch.cuda.current_stream(cell.device)
+    rc = L.dig_sort_by_cell(C.c_void_p(cell.data_ptr()), n, n_cells, C.c_void_p(cs.data_ptr()),
+                            C.c_void_p(order.data_ptr()), C.c_void_p(sp), nb.value, C.c_void_p(s.cuda_stream))
+    if rc:
+        raise DigError(rc, L.dig_last_error(None).decode())
+    s.synchronize()
+    return cs, order[: int(cs[-1].item())]

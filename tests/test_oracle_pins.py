@@ -434,3 +434,16 @@ def test_bookkeeping_closed_cavity():
     assert len(cell) == s.n_particles
     assert np.all(np.diff(cell) >= 0)
     assert o.counters()["removed"] == 0
+
+
+def test_sort_by_cell_matches_stable_argsort():
+    """The standalone bucket sort equals numpy's stable argsort of the cell ids
+    (a library routine with the same definition), with -1 entries dropped."""
+    rng = np.random.default_rng(4)
+    for n, nc in ((0, 5), (1, 1), (1000, 37), (20000, 1296), (5000, 5)):
+        cell = rng.integers(-1, nc, size=n).astype(np.int32)
+        cs, order = orc.sort_by_cell(cell, nc)
+        keep = np.flatnonzero(cell >= 0)
+        ref = keep[np.argsort(cell[keep], kind="stable")]
+        assert np.array_equal(order, ref)
+        assert np.array_equal(cs, np.concatenate([[0], np.cumsum(np.bincount(cell[keep], minlength=nc))]))
