@@ -237,6 +237,29 @@ int dig_sort_scratch_bytes(int64_t n, int32_t n_cells, int64_t* bytes);
 int dig_sort_by_cell(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* cell_start, int32_t* order,
                      void* scratch, int64_t scratch_bytes, void* stream);
 
+/*
+ * dig_sort_by_cell_noalloc -- the same sort as dig_sort_by_cell, for callers
+ * that cannot allocate device memory (their device memory is owned and
+ * planned by a host framework or a fixed budget, or cudaMalloc's implicit
+ * synchronisation is not allowed where they run).  The paper has no
+ * counterpart: this is a deployment variant of the bucket sort.
+ * The caller still passes the device inputs and outputs (as for
+ * dig_sort_by_cell); the working memory is a fixed array of
+ * DIG_NOALLOC_SCRATCH_BYTES inside the library, present on every GPU that
+ * loads the library until the process exits.  Limits: n <= DIG_NOALLOC_MAX_N,
+ * n_cells <= DIG_NOALLOC_MAX_CELLS; larger sizes return DIG_ERR_CAPACITY
+ * (message in dig_last_error(NULL)) without launching anything.  The call
+ * allocates nothing.  All calls share the array: calls whose GPU work overlaps
+ * (other streams, other threads) race and give wrong results.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make it before capturing any stream on that device.
+ */
+#define DIG_NOALLOC_MAX_N 4194304
+#define DIG_NOALLOC_MAX_CELLS 1048576
+#define DIG_NOALLOC_SCRATCH_BYTES 25167104
+int dig_sort_by_cell_noalloc(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* cell_start, int32_t* order,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

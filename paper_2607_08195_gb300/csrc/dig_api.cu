@@ -140,6 +140,10 @@ static int fail0(int code, const char* msg) {
   return code;
 }
 
+namespace dig {
+void set_thread_error(const char* msg) { std::snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace dig
+
 extern "C" {
 
 const char* dig_last_error(dig_ctx* ctx) { return ctx ? ctx->err : g_err; }

@@ -115,6 +115,8 @@ size_t sort_scratch_bytes(long long n, int n_cells);
 void launch_sort_by_cell(const int* cell, long long n, int n_cells, int* cell_start, int* order, char* scratch,
                          cudaStream_t s);
 int scan_blocks(int n_cells);
+// sets the calling thread's message returned by dig_last_error(NULL)
+void set_thread_error(const char* msg);
 extern long long g_launches;
 
 }  // namespace dig

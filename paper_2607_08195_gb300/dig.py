@@ -52,7 +52,7 @@ EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mes
            "dig_bind_arena", "particles_init", "write_particles", "read_particles", "dsmc_step", "sample",
            "read_moments", "read_pairs", "read_counters", "dig_cell_state", "dig_wall_flux",
            "dig_particle_count", "dig_synchronize", "dig_launch_count", "dig_kernel_time",
-           "dig_sort_scratch_bytes", "dig_sort_by_cell"]
+           "dig_sort_scratch_bytes", "dig_sort_by_cell", "dig_sort_by_cell_noalloc"]
 
 _lib = None
 
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "dig_cell_state": [P, P, P, I32], "dig_wall_flux": [P, P, I64, P], "dig_particle_count": [P, P],
         "dig_synchronize": [P], "dig_launch_count": [P, P], "dig_kernel_time": [P, P, P],
         "dig_sort_scratch_bytes": [I64, I32, P], "dig_sort_by_cell": [P, I64, I32, P, P, P, I64, P],
+        "dig_sort_by_cell_noalloc": [P, I64, I32, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
