@@ -656,54 +656,59 @@ static void wall_reflect(orc_ctx* c, int32_t ib, float* v, float* Ir, uint32_t s
 }
 
 /* Track one particle for one time step.  Returns the final cell, or -1 if it
- * left through a free-stream / outflow face.  The algorithm:
- *   repeat: x' = x + v t_rem (fma per component).  If x' passes the plane
- *   tests d_f - n_f.x' >= 0 of every face f other than the entry face, stop at
- *   x'.  Otherwise the exit face is the one with the smallest
- *   t_f = max(0, (d_f - n_f.x)/(n_f.v)) among faces with n_f.v > 0 (ties: lowest
- *   f); if none, or t_f >= t_rem, stop at x'.  Else advance to the face,
- *   t_rem -= t_f, and enter the neighbour (entry face = its matching face), or
- *   reflect at a wall (entry face = the wall face), or leave the domain. */
+ * left through a free-stream / outflow face.  The algorithm (the paper gives
+ * face-by-face tracking without its steps; this is the reading taken):
+ *   the step's ray starts at the origin o = x with remaining time t_rem = dt
+ *   and ends at e = o + v t_rem (fma per component).  Repeat: if e passes the
+ *   plane tests d_f - n_f.e >= 0 of every face f other than the entry face, the
+ *   particle stops at e.  Otherwise the exit face is the face f != entry with
+ *   b_f = n_f.v > 0 whose hit time a_f / b_f, a_f = max(0, d_f - n_f.o), is
+ *   smallest, compared without division: f precedes g iff a_f b_g < a_g b_f
+ *   (ties: lowest f).  If there is none, or a_f >= t_rem b_f (the face is
+ *   reached only after the step), stop at e.  Else cross: into the neighbour
+ *   (entry face = its matching face; o and e unchanged), or reflect at a wall:
+ *   hit time t_h = a_f / b_f, o <- o + v t_h, t_rem <- t_rem - t_h, new
+ *   velocity, e <- o + v t_rem, entry face = the wall face; or leave the domain.
+ * All dot products are fma(n2, y2, fma(n1, y1, n0 y0)) in FP64. */
 static int32_t track(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, uint32_t slot, uint32_t step) {
-  double t = c->cfg.dt;
+  double trem = c->cfg.dt;
   int entry = -1;
   uint32_t hits = 0;
+  double o[3] = {x[0], x[1], x[2]};
+  double vd[3] = {(double)v[0], (double)v[1], (double)v[2]};
+  double e[3];
+  for (int i = 0; i < 3; ++i) e[i] = fma(vd[i], trem, o[i]);
   for (int32_t ncross = 0;; ++ncross) {
     if (ncross > c->cfg.max_cross) {
       c->counters[ORC_C_STUCK]++;
+      x[0] = o[0]; x[1] = o[1]; x[2] = o[2];
       return cell;
     }
-    const double vd[3] = {(double)v[0], (double)v[1], (double)v[2]};
-    double xn[3];
-    for (int i = 0; i < 3; ++i) xn[i] = fma(vd[i], t, x[i]);
     const double* N = c->pn + 12 * (int64_t)cell;
     const double* Dp = c->pd + 4 * (int64_t)cell;
     int inside = 1;
     for (int f = 0; f < 4; ++f) {
       if (f == entry) continue;
-      if (Dp[f] - dot3(N + 3 * f, xn) < 0.0) inside = 0;
+      if (Dp[f] - dot3(N + 3 * f, e) < 0.0) inside = 0;
     }
     if (inside) {
-      x[0] = xn[0]; x[1] = xn[1]; x[2] = xn[2];
+      x[0] = e[0]; x[1] = e[1]; x[2] = e[2];
       return cell;
     }
     int best = -1;
-    double tb = 0.0;
+    double ab = 0.0, bb = 1.0;
     for (int f = 0; f < 4; ++f) {
       if (f == entry) continue;
       double b = dot3(N + 3 * f, vd);
       if (!(b > 0.0)) continue;
-      double a = Dp[f] - dot3(N + 3 * f, x);
-      double tf = a / b;
-      if (tf < 0.0) tf = 0.0;
-      if (best < 0 || tf < tb) { best = f; tb = tf; }
+      double a = Dp[f] - dot3(N + 3 * f, o);
+      if (a < 0.0) a = 0.0;
+      if (best < 0 || a * bb < ab * b) { best = f; ab = a; bb = b; }
     }
-    if (best < 0 || tb >= t) {
-      x[0] = xn[0]; x[1] = xn[1]; x[2] = xn[2];
+    if (best < 0 || ab >= trem * bb) {
+      x[0] = e[0]; x[1] = e[1]; x[2] = e[2];
       return cell;
     }
-    for (int i = 0; i < 3; ++i) x[i] = fma(vd[i], tb, x[i]);
-    t = t - tb;
     c->counters[ORC_C_CROSS]++;
     int32_t nb = c->nbr[4 * (int64_t)cell + best];
     if (nb >= 0) {
@@ -714,8 +719,13 @@ static int32_t track(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, u
     int32_t ib = -1 - nb;
     int kind = c->bcs[c->bf[ib].bc].kind;
     if (kind == 0 || kind == 1) {
+      double th = ab / bb;
+      for (int i = 0; i < 3; ++i) o[i] = fma(vd[i], th, o[i]);
+      trem = trem - th;
       wall_reflect(c, ib, v, Ir, slot, hits, step);
       hits++;
+      vd[0] = (double)v[0]; vd[1] = (double)v[1]; vd[2] = (double)v[2];
+      for (int i = 0; i < 3; ++i) e[i] = fma(vd[i], trem, o[i]);
       entry = best;
       continue;
     }
