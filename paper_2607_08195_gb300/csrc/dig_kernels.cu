@@ -114,6 +114,17 @@ __device__ __forceinline__ float exp_f(float y) {
 
 __device__ __forceinline__ float pow_f(float x, float a) { return exp_f(a * ln_f(x)); }
 
+// Exact FP32 -> FP64 conversion with integer operations (keeps the FP64 pipe,
+// which issues at 1/64 of the FP32 rate, free for arithmetic).  Zero,
+// subnormal, infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (double)f;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // Gaussian pair, Marsaglia's polar method; two attempts per Philox block.
 __device__ void gauss2(const Params& P, uint32_t purpose, uint32_t ent, uint32_t sub, uint32_t step,
                        uint32_t draw0, float& g1, float& g2) {
@@ -137,10 +148,26 @@ __device__ void gauss2(const Params& P, uint32_t purpose, uint32_t ent, uint32_t
   g2 = 0.0f;
 }
 
-// isotropic unit vector (Marsaglia 1972)
-__device__ void unit_vec(const Params& P, uint32_t ent, uint32_t sub, uint32_t step, float& ex, float& ey,
-                         float& ez) {
-  for (uint32_t d = 0; d < 32; ++d) {
+// isotropic unit vector (Marsaglia 1972): (a, b) uniform in the unit disc,
+// e = (2a sqrt(1-s), 2b sqrt(1-s), 1-2s), s = a^2 + b^2
+// isotropic unit vector with the words of the first draw already at hand;
+// further draws (rare: both attempts of the first draw rejected) follow
+__device__ __forceinline__ void unit_vec_from(const Params& P, const uint32_t (&w0)[4], uint32_t ent, uint32_t sub,
+                                              uint32_t step, float& ex, float& ey, float& ez) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const float a1 = 2.0f * u01f(w0[2 * a]) - 1.0f;
+    const float b1 = 2.0f * u01f(w0[2 * a + 1]) - 1.0f;
+    const float s = a1 * a1 + b1 * b1;
+    if (s < 1.0f) {
+      const float r = 2.0f * sqrtf(1.0f - s);
+      ex = a1 * r;
+      ey = b1 * r;
+      ez = 1.0f - 2.0f * s;
+      return;
+    }
+  }
+  for (uint32_t d = 1; d < 32; ++d) {
     uint32_t w[4];
     rng(P, RP_DIR, ent, sub, step, d, w);
 #pragma unroll
@@ -230,16 +257,47 @@ __device__ __forceinline__ float plane_test32(const float4 q, float fx, float fy
   return q.w - __fmaf_rn(q.z, fz, __fmaf_rn(q.y, fy, q.x * fx));
 }
 
-// Exit face of the ray x + v s from `cell`, exactly as the FP64 rule
-//   argmin over f != entry with b_f = n_f.v > 0 of t_f = max(0, (d_f - n_f.x)/b_f)
-// (ties: lowest f) would choose it.  FP32 interval estimates decide the face
-// when they separate it from the others; only that face's t is then computed
-// in FP64.  Otherwise everything is computed in FP64.  Returns -1 if no face
-// has b_f > 0; *tb receives t of the chosen face.
-__device__ __forceinline__ int exit_face(const Params& P, const Plane64* pl, const float4* pf, int entry,
-                                         double x, double y, double z, double vdx, double vdy, double vdz,
-                                         float vx, float vy, float vz, double* tb) {
-  const float fx = d2f_trunc(x), fy = d2f_trunc(y), fz = d2f_trunc(z);
+// Exit face of the step's ray from `cell`, decided as the FP64 rule decides it:
+//   among faces f != entry with b_f = n_f.v > 0, the smallest hit time
+//   a_f / b_f with a_f = max(0, d_f - n_f.o) (o: the ray origin), comparing
+//   f before g iff a_f b_g < a_g b_f (ties: lowest f); the face is crossed
+//   within the step iff !(a_f >= t_rem b_f).
+// FP32 interval estimates of b_f and of the hit times decide both answers
+// when they separate them; otherwise everything is evaluated in FP64 exactly
+// as stated.  Returns the face (-1: none) and sets *cross.
+struct Exit {
+  int face;
+  bool cross;
+};
+
+__device__ __forceinline__ Exit exit_face_fp64(const Plane64* pl, int entry, double ox, double oy, double oz,
+                                               double vdx, double vdy, double vdz, double trem) {
+  int best = -1;
+  double ab = 0.0, bb = 1.0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (f == entry) continue;
+    const Plane64 q = pl[f];
+    const double b = dot3(q, vdx, vdy, vdz);
+    if (!(b > 0.0)) continue;
+    double a = __dsub_rn(q.d, dot3(q, ox, oy, oz));
+    if (a < 0.0) a = 0.0;
+    if (best < 0 || __dmul_rn(a, bb) < __dmul_rn(ab, b)) {
+      best = f;
+      ab = a;
+      bb = b;
+    }
+  }
+  Exit r;
+  r.face = best;
+  r.cross = best >= 0 && !(ab >= __dmul_rn(trem, bb));
+  return r;
+}
+
+__device__ __forceinline__ Exit exit_face(const Params& P, const Plane64* pl, const float4* pf, int entry,
+                                          double ox, double oy, double oz, float fox, float foy, float foz,
+                                          double vdx, double vdy, double vdz, float vx, float vy, float vz,
+                                          double trem) {
   const float eb = 8.0f * 5.9604645e-08f * (fabsf(vx) + fabsf(vy) + fabsf(vz)) + 1e-30f;
   const float ea = 0.5f * P.margin;
   float lo[4], hi[4];
@@ -259,91 +317,75 @@ __device__ __forceinline__ int exit_face(const Params& P, const Plane64* pl, con
       continue;
     }
     cand[f] = true;
-    const float a = plane_test32(q, fx, fy, fz);
-    const float al = a - ea, ah = a + ea;
-    float tl = al >= 0.0f ? al / (b + eb) : al / (b - eb);
-    float th = ah >= 0.0f ? ah / (b - eb) : ah / (b + eb);
-    tl = fmaxf(tl, 0.0f);
-    th = fmaxf(th, 0.0f);
+    const float a = plane_test32(q, fox, foy, foz);
+    const float al = fmaxf(a - ea, 0.0f), ah = fmaxf(a + ea, 0.0f);
+    const float tl = __fdividef(al, b + eb), th = __fdividef(ah, b - eb);
     lo[f] = tl - tl * 9.5367432e-07f;
     hi[f] = th + th * 9.5367432e-07f + 1e-30f;
   }
-  int best = -1;
+  Exit r;
+  r.face = -1;
+  r.cross = false;
   if (decided) {
     float H = 0.0f;
 #pragma unroll
     for (int f = 0; f < 4; ++f)
-      if (cand[f] && (best < 0 || hi[f] < H)) {
-        best = f;
+      if (cand[f] && (r.face < 0 || hi[f] < H)) {
+        r.face = f;
         H = hi[f];
       }
 #pragma unroll
     for (int f = 0; f < 4; ++f)
-      if (cand[f] && f != best && !(lo[f] > H)) decided = false;
-  }
-  if (decided) {
-    if (best < 0) return -1;
-    const Plane64 q = pl[best];
-    const double b = dot3(q, vdx, vdy, vdz);
-    const double a = __dsub_rn(q.d, dot3(q, x, y, z));
-    double tf = __ddiv_rn(a, b);
-    if (tf < 0.0) tf = 0.0;
-    *tb = tf;
-    return best;
-  }
-  best = -1;
-  double t = 0.0;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    if (f == entry) continue;
-    const Plane64 q = pl[f];
-    const double b = dot3(q, vdx, vdy, vdz);
-    if (!(b > 0.0)) continue;
-    const double a = __dsub_rn(q.d, dot3(q, x, y, z));
-    double tf = __ddiv_rn(a, b);
-    if (tf < 0.0) tf = 0.0;
-    if (best < 0 || tf < t) {
-      best = f;
-      t = tf;
+      if (cand[f] && f != r.face && !(lo[f] > H)) decided = false;
+    if (decided && r.face >= 0) {
+      const float T = (float)trem;
+      if (H < T * 0.99999f)
+        r.cross = true;
+      else if (lo[r.face] > T * 1.00001f)
+        r.cross = false;
+      else
+        decided = false;
     }
   }
-  *tb = t;
-  return best;
+  if (decided) return r;
+  return exit_face_fp64(pl, entry, ox, oy, oz, vdx, vdy, vdz, trem);
 }
 
-// Face-by-face tracking of one particle for one time step.  Returns the final
-// cell or -1 when the particle leaves through an open boundary.
-//   x' = x + v t_rem; inside if d_f - n_f.x' >= 0 for every face but the entry
-//   face; else exit face = argmin over faces with n_f.v > 0 of
-//   max(0, (d_f - n_f.x)/(n_f.v)) (ties: lowest f); stop at x' if none or if
-//   t_f >= t_rem; else advance, t_rem -= t_f, cross / reflect / leave.
-// FP32 tests only shortcut decisions they can prove (see plane_test32 and
-// exit_face); every value that is kept is computed in FP64 as stated.
+// Face-by-face tracking of one particle for one time step (the same rule as
+// the oracle): ray from o = x to e = o + v t_rem; while e is outside the
+// current cell, cross the exit face (exit_face); at a wall the hit time
+// a_f / b_f is computed in FP64, o moves to the hit point, the particle is
+// re-emitted and e is recomputed.  Returns the final cell or -1 when the
+// particle leaves through an open boundary.  FP32 tests only shortcut
+// decisions they prove (plane_test32, exit_face).
 template <bool DIAT>
 __device__ int track(const Params& P, double& x, double& y, double& z, float& vx, float& vy, float& vz, float& I,
                      int cell, uint32_t slot, uint32_t step, bool flux, Cnt& cnt) {
-  double t = P.dt;
+  double trem = P.dt;
   int entry = -1;
   uint32_t hits = 0;
+  double ox = x, oy = y, oz = z;
+  double vdx = f2d(vx), vdy = f2d(vy), vdz = f2d(vz);
+  double ex = __fma_rn(vdx, trem, ox), ey = __fma_rn(vdy, trem, oy), ez = __fma_rn(vdz, trem, oz);
+  float fox = d2f_trunc(ox), foy = d2f_trunc(oy), foz = d2f_trunc(oz);
+  float fex = d2f_trunc(ex), fey = d2f_trunc(ey), fez = d2f_trunc(ez);
   for (int ncross = 0;; ++ncross) {
     if (ncross > P.max_cross) {
       cnt.stuck++;
+      x = ox;
+      y = oy;
+      z = oz;
       return cell;
     }
-    const double vdx = (double)vx, vdy = (double)vy, vdz = (double)vz;
-    const double xn = __fma_rn(vdx, t, x), yn = __fma_rn(vdy, t, y), zn = __fma_rn(vdz, t, z);
     const Plane64* pl = P.plane + 4 * (size_t)cell;
     const float4* pf = P.plane32 + 4 * (size_t)cell;
     bool all_in = true, some_out = false;
-    {
-      const float fx = d2f_trunc(xn), fy = d2f_trunc(yn), fz = d2f_trunc(zn);
 #pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        if (f == entry) continue;
-        const float s = plane_test32(pf[f], fx, fy, fz);
-        if (!(s > P.margin)) all_in = false;
-        if (s < -P.margin) some_out = true;
-      }
+    for (int f = 0; f < 4; ++f) {
+      if (f == entry) continue;
+      const float s = plane_test32(pf[f], fex, fey, fez);
+      if (!(s > P.margin)) all_in = false;
+      if (s < -P.margin) some_out = true;
     }
     bool inside = all_in;
     if (!all_in && !some_out) {
@@ -352,27 +394,23 @@ __device__ int track(const Params& P, double& x, double& y, double& z, float& vx
       for (int f = 0; f < 4; ++f) {
         if (f == entry) continue;
         const Plane64 q = pl[f];
-        if (__dsub_rn(q.d, dot3(q, xn, yn, zn)) < 0.0) inside = false;
+        if (__dsub_rn(q.d, dot3(q, ex, ey, ez)) < 0.0) inside = false;
       }
     }
     if (inside) {
-      x = xn;
-      y = yn;
-      z = zn;
+      x = ex;
+      y = ey;
+      z = ez;
       return cell;
     }
-    double tb = 0.0;
-    const int best = exit_face(P, pl, pf, entry, x, y, z, vdx, vdy, vdz, vx, vy, vz, &tb);
-    if (best < 0 || tb >= t) {
-      x = xn;
-      y = yn;
-      z = zn;
+    const Exit X = exit_face(P, pl, pf, entry, ox, oy, oz, fox, foy, foz, vdx, vdy, vdz, vx, vy, vz, trem);
+    if (!X.cross) {
+      x = ex;
+      y = ey;
+      z = ez;
       return cell;
     }
-    x = __fma_rn(vdx, tb, x);
-    y = __fma_rn(vdy, tb, y);
-    z = __fma_rn(vdz, tb, z);
-    t = __dsub_rn(t, tb);
+    const int best = X.face;
     cnt.cross++;
     const int nb = __ldg(P.nbr + 4 * (size_t)cell + best);
     if (nb >= 0) {
@@ -383,9 +421,30 @@ __device__ int track(const Params& P, double& x, double& y, double& z, float& vx
     const int ib = -1 - nb;
     const int kind = P.bc[P.bf[ib].bc].kind;
     if (kind <= 1) {
+      const Plane64 q = pl[best];
+      const double b = dot3(q, vdx, vdy, vdz);
+      double a = __dsub_rn(q.d, dot3(q, ox, oy, oz));
+      if (a < 0.0) a = 0.0;
+      const double th = __ddiv_rn(a, b);
+      ox = __fma_rn(vdx, th, ox);
+      oy = __fma_rn(vdy, th, oy);
+      oz = __fma_rn(vdz, th, oz);
+      trem = __dsub_rn(trem, th);
       wall_reflect<DIAT>(P, ib, vx, vy, vz, I, slot, hits, step, flux);
       hits++;
       cnt.wall++;
+      vdx = f2d(vx);
+      vdy = f2d(vy);
+      vdz = f2d(vz);
+      ex = __fma_rn(vdx, trem, ox);
+      ey = __fma_rn(vdy, trem, oy);
+      ez = __fma_rn(vdz, trem, oz);
+      fox = d2f_trunc(ox);
+      foy = d2f_trunc(oy);
+      foz = d2f_trunc(oz);
+      fex = d2f_trunc(ex);
+      fey = d2f_trunc(ey);
+      fez = d2f_trunc(ez);
       entry = best;
       continue;
     }
@@ -410,9 +469,15 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
   const long long ncand = (long long)fl;
   long long pbase = 0;
   if (record) pbase = (long long)atomicAdd(P.pair_count, (unsigned long long)ncand);
+  uint32_t w[4];
+  if (ncand > 0) rng(P, RP_COLL, (uint32_t)cell, 0u, step, 0, w);
   for (long long k = 0; k < ncand; ++k) {
-    uint32_t w[4];
-    rng(P, RP_COLL, (uint32_t)cell, (uint32_t)k, step, 0, w);
+    // random words of the next candidate and of this candidate's first
+    // direction draw: independent of this candidate's arithmetic, so they
+    // overlap with its dependent FP32 chain
+    uint32_t wn[4], wd[4];
+    if (k + 1 < ncand) rng(P, RP_COLL, (uint32_t)cell, (uint32_t)(k + 1), step, 0, wn);
+    rng(P, RP_DIR, (uint32_t)cell, (uint32_t)k, step, 0, wd);
     const int i = (int)(((unsigned long long)w[0] * (unsigned long long)N) >> 32);
     int j = (int)(((unsigned long long)w[1] * (unsigned long long)(N - 1)) >> 32);
     if (j >= i) j = j + 1;
@@ -431,7 +496,11 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
       r[3] = j;
       P.pacc[pbase + k] = acc ? 1 : 0;
     }
-    if (!acc) continue;
+    if (!acc) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] = wn[q];
+      continue;
+    }
     cnt.coll++;
     if (DIAT) {
       uint32_t u[4];
@@ -455,7 +524,9 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
     }
     const float cr = sqrtf(g2);
     float ex, ey, ez;
-    unit_vec(P, (uint32_t)cell, (uint32_t)k, step, ex, ey, ez);
+    unit_vec_from(P, wd, (uint32_t)cell, (uint32_t)k, step, ex, ey, ez);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = wn[q];
     const float h = 0.5f * cr;
     float cm;
     cm = (vx[i] + vx[j]) * 0.5f;
@@ -471,14 +542,17 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
   P.cmax[cell] = cmax;
 }
 
-// per-cell summation variables (FP32 within the step, FP64 across steps)
+// per-cell summation variables, one warp per cell: FP32 partial sums per lane
+// (strided over the cell's particles) reduced across the warp, then FP64
+// across steps; lane q updates component q
 template <bool DIAT>
-__device__ void sample_cell(const Params& P, int cell, const float* vx, const float* vy, const float* vz,
-                            const float* I, int N, int sflags, int ewma_first) {
-  float s[NPHI];
+__device__ void sample_cell_warp(const Params& P, int cell, const float* vx, const float* vy, const float* vz,
+                                 const float* I, int N, int sflags, int ewma_first, int lane) {
+  constexpr int np = DIAT ? 17 : 13;
+  float s[np];
 #pragma unroll
-  for (int q = 0; q < NPHI; ++q) s[q] = 0.0f;
-  for (int k = 0; k < N; ++k) {
+  for (int q = 0; q < np; ++q) s[q] = 0.0f;
+  for (int k = lane; k < N; k += 32) {
     const float x = vx[k], y = vy[k], z = vz[k];
     const float vv = x * x + y * y + z * z;
     s[1] += x;
@@ -501,12 +575,17 @@ __device__ void sample_cell(const Params& P, int cell, const float* vx, const fl
       s[16] += e * z;
     }
   }
-  const size_t n = (size_t)P.n_cells;
-  constexpr int np = DIAT ? 17 : 13;
+  float mine = 0.0f;
 #pragma unroll
-  for (int q = 0; q < np; ++q) {
-    const double ph = q == 0 ? (double)N : (double)s[q];
-    const size_t o = (size_t)q * n + cell;
+  for (int q = 1; q < np; ++q) {
+    float v = s[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == q) mine = v;
+  }
+  if (lane < np) {
+    const size_t o = (size_t)lane * (size_t)P.n_cells + cell;
+    const double ph = lane == 0 ? (double)N : f2d(mine);
     if (sflags & S_INST) P.phi_inst[o] = ph;
     if (sflags & S_EWMA) P.phi_ewma[o] = ewma_first ? ph : P.na_a * P.phi_ewma[o] + P.na_b * ph;
     if (sflags & S_WINDOW) P.phi_win[o] += ph;
@@ -545,7 +624,7 @@ size_t cell_pass_smem(int TC, int CAP, bool diat) {
 // finds the stayers of cell c by mc == c over c's old range and the
 // arrivals from the lists built by k_scatter.
 template <bool DIAT>
-__global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf OUT, int pass, int sflags,
+__global__ void __launch_bounds__(CP_THREADS, 3) k_cell_pass(Params P, Buf IN, Buf OUT, int pass, int sflags,
                                                           uint32_t step_coll, uint32_t step_move,
                                                           int ewma_first, int TC, int CAP) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -648,8 +727,12 @@ __global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf 
         const int cb = s_cs[c] - gbase, N = s_cs[c + 1] - s_cs[c];
         collide_cell<DIAT>(P, c0 + c, s_vx + cb, s_vy + cb, s_vz + cb, DIAT ? s_I + cb : nullptr, N, step_coll,
                            rec, cnt);
-        sample_cell<DIAT>(P, c0 + c, s_vx + cb, s_vy + cb, s_vz + cb, DIAT ? s_I + cb : nullptr, N, sflags,
-                          ewma_first);
+      }
+      __syncthreads();
+      for (int c = g0 + warp; c < g1; c += nwarps) {
+        const int cb = s_cs[c] - gbase, N = s_cs[c + 1] - s_cs[c];
+        sample_cell_warp<DIAT>(P, c0 + c, s_vx + cb, s_vy + cb, s_vz + cb, DIAT ? s_I + cb : nullptr, N, sflags,
+                               ewma_first, lane);
       }
       __syncthreads();
     }
@@ -661,8 +744,8 @@ __global__ void __launch_bounds__(CP_THREADS) k_cell_pass(Params P, Buf IN, Buf 
       const float vx = s_vx[k], vy = s_vy[k], vz = s_vz[k];
       bool done = true;
       if (do_move) {
-        const double xn = __fma_rn((double)vx, P.dt, x), yn = __fma_rn((double)vy, P.dt, y),
-                     zn = __fma_rn((double)vz, P.dt, z);
+        const double xn = __fma_rn(f2d(vx), P.dt, x), yn = __fma_rn(f2d(vy), P.dt, y),
+                     zn = __fma_rn(f2d(vz), P.dt, z);
         const float4* pf = P.plane32 + 4 * (size_t)cell;
         const float fx = d2f_trunc(xn), fy = d2f_trunc(yn), fz = d2f_trunc(zn);
 #pragma unroll
