@@ -111,6 +111,8 @@ typedef struct dig_config {
   double wait_timeout_s; /* time limit of host waits (<= 0: 600 s) */
   int32_t stage_cap;     /* particles staged in shared memory per CTA (<= 0: 3072) */
   int32_t tile_cells;    /* cells per CTA of the cell pass (<= 0: chosen from the load) */
+  int32_t cta_threads;   /* threads per CTA of the cell pass: 64, 128 or 256 (<= 0: 256) */
+  int32_t pad1;
 } dig_config;
 
 typedef struct dig_bc {

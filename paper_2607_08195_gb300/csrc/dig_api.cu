@@ -108,7 +108,7 @@ struct dig_ctx {
   bool have_particles = false;
   int64_t step = 0;
   int64_t n_ewma = 0, n_win = 0, n_cum = 0, host_steps = 0;
-  int tile_cells = 0, stage_cap = 3072;
+  int tile_cells = 0, stage_cap = 3072, cta_threads = 256;
   float cmax0 = 0.0f;
   cudaEvent_t ev = nullptr;
   std::vector<cudaEvent_t> tev;  // event pairs around timed cell passes
@@ -157,6 +157,7 @@ int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (c->cfg.max_cross <= 0) c->cfg.max_cross = 4096;
   if (!(c->cfg.wait_timeout_s > 0)) c->cfg.wait_timeout_s = 600.0;
   if (c->cfg.stage_cap > 0) c->stage_cap = c->cfg.stage_cap;
+  if (c->cfg.cta_threads > 0) c->cta_threads = c->cfg.cta_threads <= 64 ? 64 : c->cfg.cta_threads <= 128 ? 128 : 256;
   if (c->cfg.n_a <= 0) c->cfg.n_a = 1000;
   c->tile_cells = c->cfg.tile_cells;
   *out = c;
@@ -543,7 +544,7 @@ static void pass(dig_ctx* ctx, int pass_flags, int sflags, uint32_t step_coll, u
   const int other = 1 - ctx->cur;
   if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
   launch_cell_pass(ctx->P, ctx->buf[ctx->cur], ctx->buf[other], pass_flags, sflags, step_coll, step_move,
-                   ewma_first, ctx->tile_cells, ctx->stage_cap, ctx->stream);
+                   ewma_first, ctx->tile_cells, ctx->stage_cap, ctx->cta_threads, ctx->stream);
   if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
   ctx->cur = other;
   launch_scan(ctx->P, ctx->stream);

@@ -105,7 +105,7 @@ void launch_scan(const Params& P, cudaStream_t s);
 void launch_scatter(const Params& P, const int* mc, cudaStream_t s);
 void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags,
                       uint32_t step_coll, uint32_t step_move, int ewma_first, int tile_cells,
-                      int stage_cap, cudaStream_t s);
+                      int stage_cap, int threads, cudaStream_t s);
 void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* Is, int* cells,
                  int n, cudaStream_t s);
 void launch_moments_ex(const Params& P, const double* phi, double scale, int macro, double* out, double mass,

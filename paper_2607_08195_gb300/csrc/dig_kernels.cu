@@ -587,7 +587,7 @@ __device__ void sample_cell_warp(const Params& P, int cell, const float* vx, con
     const size_t o = (size_t)lane * (size_t)P.n_cells + cell;
     const double ph = lane == 0 ? (double)N : f2d(mine);
     if (sflags & S_INST) P.phi_inst[o] = ph;
-    if (sflags & S_EWMA) P.phi_ewma[o] = ewma_first ? ph : P.na_a * P.phi_ewma[o] + P.na_b * ph;
+    if (sflags & S_EWMA) P.phi_ewma[o] = ewma_first ? ph : __fma_rn(P.na_a, P.phi_ewma[o], P.na_b * ph);
     if (sflags & S_WINDOW) P.phi_win[o] += ph;
     if (sflags & S_CUMUL) P.phi_cum[o] += ph;
   }
@@ -609,7 +609,6 @@ __device__ __forceinline__ void flush_counters(const Params& P, const Cnt& c) {
 // ---------------------------------------------------------------------------
 // the cell pass
 // ---------------------------------------------------------------------------
-constexpr int CP_THREADS = 256;
 
 size_t cell_pass_smem(int TC, int CAP, bool diat) {
   return sizeof(int) * (size_t)(5 * TC + 8) + (size_t)CAP * (2 * sizeof(int) + 3 * sizeof(float) + 1) +
@@ -623,8 +622,13 @@ size_t cell_pass_smem(int TC, int CAP, bool diat) {
 // = the cell it is in after the move (-1: left the domain); the next pass
 // finds the stayers of cell c by mc == c over c's old range and the
 // arrivals from the lists built by k_scatter.
-template <bool DIAT>
-__global__ void __launch_bounds__(CP_THREADS, 3) k_cell_pass(Params P, Buf IN, Buf OUT, int pass, int sflags,
+// resident threads per SM the register budget of the cell pass is sized for
+#ifndef DIG_CP_RESIDENT
+#define DIG_CP_RESIDENT 768
+#endif
+
+template <bool DIAT, int CP_THREADS>
+__global__ void __launch_bounds__(CP_THREADS, DIG_CP_RESIDENT / CP_THREADS) k_cell_pass(Params P, Buf IN, Buf OUT, int pass, int sflags,
                                                           uint32_t step_coll, uint32_t step_move,
                                                           int ewma_first, int TC, int CAP) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -681,43 +685,87 @@ __global__ void __launch_bounds__(CP_THREADS, 3) k_cell_pass(Params P, Buf IN, B
       __syncthreads();
       continue;
     }
-    // 1. canonical order, one warp per cell: stayers found by ballot over the
-    //    cell's old range, then arrivals ranked by their previous slot
-    for (int c = g0 + warp; c < g1; c += nwarps) {
-      const int cell = c0 + c, cb = s_cs[c] - gbase, Nc = s_cs[c + 1] - s_cs[c];
-      const int sb = s_sb[c], no = s_no[c];
-      int ns = 0;
-      for (int k0 = 0; k0 < no; k0 += 32) {
-        const int k = k0 + lane;
-        const bool st = k < no && IN.mc[sb + k] == cell;
-        const unsigned bs = __ballot_sync(0xffffffffu, st);
-        if (st) s_src[cb + ns + __popc(bs & ((1u << lane) - 1u))] = sb + k;
-        ns += __popc(bs);
-      }
-      const int a0 = s_as[c], na = s_as[c + 1] - a0;
-      if (na <= 32) {
-        const int key = lane < na ? P.aq[a0 + lane] : 0x7fffffff;
-        int rank = 0;
-        for (int r = 0; r < na; ++r) rank += (__shfl_sync(0xffffffffu, key, r) < key) ? 1 : 0;
-        if (lane < na) s_src[cb + ns + rank] = key;
-      } else {
-        for (int r = lane; r < na; r += 32) {
-          const int key = P.aq[a0 + r];
-          int rank = 0;
-          for (int r2 = 0; r2 < na; ++r2) rank += (P.aq[a0 + r2] < key) ? 1 : 0;
-          s_src[cb + ns + rank] = key;
+    // 1. canonical order.  First stage, with coalesced loads by all threads, the
+    //    cell ids of the group's old slot range (contiguous: the cells' old
+    //    ranges are adjacent) and the group's arrival lists; then one warp per
+    //    cell finds the stayers by ballot and ranks the arrivals by slot.
+    {
+      const int olo = s_sb[g0], nO = s_sb[g1 - 1] + s_no[g1 - 1] - olo;
+      const bool stage_old = nO <= CAP;
+      int* s_mc = s_q;
+      int* s_aq = reinterpret_cast<int*>(s_vx);
+      const int alo = s_as[g0], nA = s_as[g1] - alo;
+      if (stage_old) {
+        for (int i0 = threadIdx.x; i0 < nO; i0 += 4 * CP_THREADS) {
+          int t[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) t[u] = i0 + u * CP_THREADS < nO ? IN.mc[olo + i0 + u * CP_THREADS] : 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i0 + u * CP_THREADS < nO) s_mc[i0 + u * CP_THREADS] = t[u];
         }
       }
-      for (int k = lane; k < Nc; k += 32) s_cl[cb + k] = (unsigned char)(c - g0);
+      for (int i0 = threadIdx.x; i0 < nA; i0 += 4 * CP_THREADS) {
+        int t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = i0 + u * CP_THREADS < nA ? P.aq[alo + i0 + u * CP_THREADS] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i0 + u * CP_THREADS < nA) s_aq[i0 + u * CP_THREADS] = t[u];
+      }
+      __syncthreads();
+      for (int c = g0 + warp; c < g1; c += nwarps) {
+        const int cell = c0 + c, cb = s_cs[c] - gbase, Nc = s_cs[c + 1] - s_cs[c];
+        const int sb = s_sb[c], no = s_no[c];
+        int ns = 0;
+        for (int k0 = 0; k0 < no; k0 += 32) {
+          const int k = k0 + lane;
+          const bool st = k < no && (stage_old ? s_mc[sb - olo + k] : IN.mc[sb + k]) == cell;
+          const unsigned bs = __ballot_sync(0xffffffffu, st);
+          if (st) s_src[cb + ns + __popc(bs & ((1u << lane) - 1u))] = sb + k;
+          ns += __popc(bs);
+        }
+        const int a0 = s_as[c] - alo, na = s_as[c + 1] - s_as[c];
+        if (na <= 32) {
+          const int key = lane < na ? s_aq[a0 + lane] : 0x7fffffff;
+          int rank = 0;
+          for (int r = 0; r < na; ++r) rank += (__shfl_sync(0xffffffffu, key, r) < key) ? 1 : 0;
+          if (lane < na) s_src[cb + ns + rank] = key;
+        } else {
+          for (int r = lane; r < na; r += 32) {
+            const int key = s_aq[a0 + r];
+            int rank = 0;
+            for (int r2 = 0; r2 < na; ++r2) rank += (s_aq[a0 + r2] < key) ? 1 : 0;
+            s_src[cb + ns + rank] = key;
+          }
+        }
+        for (int kk = lane; kk < Nc; kk += 32) s_cl[cb + kk] = (unsigned char)(c - g0);
+      }
     }
     __syncthreads();
     // 2. gather velocities (and rotational energies)
-    for (int k = threadIdx.x; k < gN; k += CP_THREADS) {
-      const int s = s_src[k];
-      s_vx[k] = IN.vx[s];
-      s_vy[k] = IN.vy[s];
-      s_vz[k] = IN.vz[s];
-      if (DIAT) s_I[k] = IN.Ir[s];
+    for (int k0 = threadIdx.x; k0 < gN; k0 += 4 * CP_THREADS) {
+      int sidx[4];
+      float ga[4], gb[4], gc[4], gd[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sidx[u] = k0 + u * CP_THREADS < gN ? s_src[k0 + u * CP_THREADS] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (sidx[u] >= 0) {
+          ga[u] = IN.vx[sidx[u]];
+          gb[u] = IN.vy[sidx[u]];
+          gc[u] = IN.vz[sidx[u]];
+          if (DIAT) gd[u] = IN.Ir[sidx[u]];
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (sidx[u] >= 0) {
+          const int k = k0 + u * CP_THREADS;
+          s_vx[k] = ga[u];
+          s_vy[k] = gb[u];
+          s_vz[k] = gc[u];
+          if (DIAT) s_I[k] = gd[u];
+        }
     }
     __syncthreads();
     // 3. collisions and sampling, one thread per cell
@@ -738,35 +786,52 @@ __global__ void __launch_bounds__(CP_THREADS, 3) k_cell_pass(Params P, Buf IN, B
     }
     // 4a. move, fast path for every particle: x' = x + v dt, proven inside by
     //     the FP32 plane test; the others go to the queue
-    for (int k = threadIdx.x; k < gN; k += CP_THREADS) {
-      const int s = s_src[k], lc = s_cl[k], cell = c0 + g0 + lc, slot = gbase + k;
-      double x = IN.x[s], y = IN.y[s], z = IN.z[s];
-      const float vx = s_vx[k], vy = s_vy[k], vz = s_vz[k];
-      bool done = true;
-      if (do_move) {
-        const double xn = __fma_rn(f2d(vx), P.dt, x), yn = __fma_rn(f2d(vy), P.dt, y),
-                     zn = __fma_rn(f2d(vz), P.dt, z);
-        const float4* pf = P.plane32 + 4 * (size_t)cell;
-        const float fx = d2f_trunc(xn), fy = d2f_trunc(yn), fz = d2f_trunc(zn);
+    for (int k0 = threadIdx.x; k0 < gN; k0 += 4 * CP_THREADS) {
+      // positions of four particles in flight at once
+      double X[4], Y[4], Z[4];
 #pragma unroll
-        for (int f = 0; f < 4; ++f)
-          if (!(plane_test32(pf[f], fx, fy, fz) > P.margin)) done = false;
-        x = xn;
-        y = yn;
-        z = zn;
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u * CP_THREADS;
+        if (k < gN) {
+          const int s = s_src[k];
+          X[u] = IN.x[s];
+          Y[u] = IN.y[s];
+          Z[u] = IN.z[s];
+        }
       }
-      if (done) {
-        OUT.x[slot] = x;
-        OUT.y[slot] = y;
-        OUT.z[slot] = z;
-        OUT.vx[slot] = vx;
-        OUT.vy[slot] = vy;
-        OUT.vz[slot] = vz;
-        if (DIAT) OUT.Ir[slot] = s_I[k];
-        OUT.mc[slot] = cell;
-        atomicAdd(s_nst + g0 + lc, 1);
-      } else {
-        s_q[atomicAdd(&s_qn, 1)] = k;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u * CP_THREADS;
+        if (k >= gN) continue;
+        const int lc = s_cl[k], cell = c0 + g0 + lc, slot = gbase + k;
+        double x = X[u], y = Y[u], z = Z[u];
+        const float vx = s_vx[k], vy = s_vy[k], vz = s_vz[k];
+        bool done = true;
+        if (do_move) {
+          const double xn = __fma_rn(f2d(vx), P.dt, x), yn = __fma_rn(f2d(vy), P.dt, y),
+                       zn = __fma_rn(f2d(vz), P.dt, z);
+          const float4* pf = P.plane32 + 4 * (size_t)cell;
+          const float fx = d2f_trunc(xn), fy = d2f_trunc(yn), fz = d2f_trunc(zn);
+#pragma unroll
+          for (int f = 0; f < 4; ++f)
+            if (!(plane_test32(pf[f], fx, fy, fz) > P.margin)) done = false;
+          x = xn;
+          y = yn;
+          z = zn;
+        }
+        if (done) {
+          OUT.x[slot] = x;
+          OUT.y[slot] = y;
+          OUT.z[slot] = z;
+          OUT.vx[slot] = vx;
+          OUT.vy[slot] = vy;
+          OUT.vz[slot] = vz;
+          if (DIAT) OUT.Ir[slot] = s_I[k];
+          OUT.mc[slot] = cell;
+          atomicAdd(s_nst + g0 + lc, 1);
+        } else {
+          s_q[atomicAdd(&s_qn, 1)] = k;
+        }
       }
     }
     __syncthreads();
@@ -1164,20 +1229,27 @@ void launch_scatter(const Params& P, const int* mc, cudaStream_t s) {
   ++g_launches;
 }
 
-void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_coll,
+template <bool DIAT, int NT>
+static void launch_cp(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_coll,
                       uint32_t step_move, int ewma_first, int TC, int CAP, cudaStream_t s) {
-  const bool diat = P.rot_dof > 0;
-  const size_t sm = cell_pass_smem(TC, CAP, diat);
+  const size_t sm = cell_pass_smem(TC, CAP, DIAT);
   const int nb = blocks_for(P.n_cells, TC);
-  if (diat) {
-    cudaFuncSetAttribute(k_cell_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cell_pass<true><<<nb, CP_THREADS, sm, s>>>(P, in, out, pass, sflags, step_coll, step_move, ewma_first, TC,
-                                                  CAP);
+  cudaFuncSetAttribute(k_cell_pass<DIAT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_cell_pass<DIAT, NT><<<nb, NT, sm, s>>>(P, in, out, pass, sflags, step_coll, step_move, ewma_first, TC, CAP);
+}
+
+void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_coll,
+                      uint32_t step_move, int ewma_first, int TC, int CAP, int threads, cudaStream_t s) {
+  const bool diat = P.rot_dof > 0;
+#define DIG_CP(D, T) launch_cp<D, T>(P, in, out, pass, sflags, step_coll, step_move, ewma_first, TC, CAP, s)
+  if (threads <= 64) {
+    if (diat) DIG_CP(true, 64); else DIG_CP(false, 64);
+  } else if (threads <= 128) {
+    if (diat) DIG_CP(true, 128); else DIG_CP(false, 128);
   } else {
-    cudaFuncSetAttribute(k_cell_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cell_pass<false><<<nb, CP_THREADS, sm, s>>>(P, in, out, pass, sflags, step_coll, step_move, ewma_first,
-                                                   TC, CAP);
+    if (diat) DIG_CP(true, 256); else DIG_CP(false, 256);
   }
+#undef DIG_CP
   ++g_launches;
 }
 

@@ -25,7 +25,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2607_08195_gb300 import dig  # noqa: E402
 
 
-GPU_ONLY = ("tile_cells", "stage_cap", "wait_timeout_s")
+GPU_ONLY = ("tile_cells", "stage_cap", "wait_timeout_s", "cta_threads")
 
 
 def pair(scen, **over):
@@ -126,12 +126,13 @@ def test_diatomic_bit_exact():
     assert g.counters()["lb"] == o.counters()["lb"] > 0
 
 
-@pytest.mark.parametrize("tile_cells,stage_cap", [(1, 4096), (7, 512), (256, 8192)])
-def test_tiling_does_not_change_results(tile_cells, stage_cap):
+@pytest.mark.parametrize("tile_cells,stage_cap,threads", [(1, 4096, 256), (7, 512, 256), (256, 8192, 256),
+                                                          (0, 1024, 64), (5, 1536, 128)])
+def test_tiling_does_not_change_results(tile_cells, stage_cap, threads):
     """Ragged tiles (cells not a multiple of the tile) and small shared-memory
     stages (cells grouped several times per CTA) give identical results."""
     s = W.cavity_scenario(5, 15_000, 0.1, seed=6)
-    g, o = pair(s, tile_cells=tile_cells, stage_cap=stage_cap)
+    g, o = pair(s, tile_cells=tile_cells, stage_cap=stage_cap, cta_threads=threads)
     g.init()
     o.init()
     g.step(4, dig.EWMA | dig.SYNC)
