@@ -31,6 +31,23 @@ sys.path.insert(0, ROOT)
 N_S = 200  # DSMC steps per bench step (one coupling window of the benchmarked cavity)
 
 
+def read_traffic():
+    """DRAM bytes per cell-pass launch from the committed ncu summary, if the
+    kernel source is still the one that was profiled (else None)."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2607_08195_gb300", "csrc", "dig_kernels.cu")
+    prof = os.path.join(ROOT, "profiles", "k_cell_pass-cavity30-Kn0.01-8M.md")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = dict(l.split(":", 1) for l in open(prof) if l.startswith(("kernel_source_sha256_16:", "dram_bytes")))
+        if fields["kernel_source_sha256_16"].strip() == h:
+            return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -232,7 +249,7 @@ def main():
     psteps_per_launch = psteps / max(k_n, 1)
     achieved = alg_bytes_per_pstep * psteps_per_launch / (cp_launch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_cell_pass", "peak_kind": peak_kind,
+                "traffic": read_traffic(), "kernel": "k_cell_pass", "peak_kind": peak_kind,
                 "kernel_ms_per_launch": cp_launch_ms, "kernel_share_of_step": k_ms / ms}
 
     # end to end through the C ABI with host buffers: pinned host particle
