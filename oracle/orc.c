@@ -134,6 +134,10 @@ float orc_powf(float x, float a) { return orc_expf(a * orc_lnf(x)); }
 typedef struct {
   int32_t tet, face, bc;
   float nrm[3], t1[3], t2[3]; /* outward unit normal and tangent basis (FP32) */
+  /* free-stream inflow faces only */
+  int32_t vtx[3];             /* the face's nodes (local order of the face) */
+  double expn;                /* expected injections per step: F A dt / F_N */
+  float s, p1, invb, sig, ut1, ut2; /* speed ratio, mixture weight, 1/beta, sqrt(kT/m), U.t1, U.t2 */
 } bface_t;
 
 #define NPHI_MAX 17
@@ -156,6 +160,7 @@ struct orc_ctx {
   int32_t n_bf;
   bface_t* bf;
   double* bflux;     /* [5 n_bf]: hits, momentum in (3), energy in (sum of incident minus reflected) */
+  double* inj_rem;   /* [n_bf] carried fractional injection count of each inflow face */
   orc_bc* bcs;
   int32_t n_bcs;
   float* bc_sigma;   /* sqrt(k T / m) per bc */
@@ -228,7 +233,7 @@ orc_ctx* orc_create(const orc_config* cfg) {
 
 static void free_mesh(orc_ctx* c) {
   free(c->nbr); free(c->nbr_face); free(c->pn); free(c->pd); free(c->vol); free(c->cumvol);
-  free(c->fdtv); free(c->nodes); free(c->tets); free(c->bf); free(c->bflux); free(c->bcs);
+  free(c->fdtv); free(c->nodes); free(c->tets); free(c->bf); free(c->bflux); free(c->inj_rem); free(c->bcs);
   free(c->bc_sigma); free(c->bc_U); free(c->cstart); free(c->cmax); free(c->rem);
   free(c->phi_inst); free(c->phi_ewma); free(c->phi_win); free(c->phi_cum);
 }
@@ -376,6 +381,7 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
   c->n_bf = (int32_t)nb;
   c->bf = (bface_t*)malloc(sizeof(bface_t) * (nb > 0 ? nb : 1));
   c->bflux = (double*)calloc(5 * (nb > 0 ? nb : 1), sizeof(double));
+  c->inj_rem = (double*)calloc(nb > 0 ? nb : 1, sizeof(double));
   int32_t ib = 0;
   for (int64_t t = 0; t < n; ++t)
     for (int f = 0; f < 4; ++f) {
@@ -395,6 +401,37 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
       for (int i = 0; i < 3; ++i) { B->nrm[i] = (float)N[i]; B->t1[i] = (float)t1[i]; B->t2[i] = (float)t2[i]; }
       c->nbr[4 * t + f] = -1 - ib;
       c->nbr_face[4 * t + f] = (int8_t)f;
+      memset(B->vtx, 0, sizeof B->vtx);
+      B->expn = 0.0;
+      B->s = B->p1 = B->invb = B->sig = B->ut1 = B->ut2 = 0.0f;
+      const orc_bc* bc = bcs + B->bc;
+      if (bc->kind == 2) {
+        /* Bird (1994) eq. 4.22: one-sided number flux of a drifting Maxwellian
+         * through a face with inward normal n_in = -n: F = n/(2 sqrt(pi) beta)
+         * [exp(-s^2) + sqrt(pi) s (1 + erf s)], beta = sqrt(m/2kT), s = beta U.n_in */
+        int k = 0;
+        for (int q = 0; q < 4; ++q)
+          if (q != f) B->vtx[k++] = tets[4 * t + q];
+        const double* P0 = nodes + 3 * B->vtx[0];
+        const double* P1 = nodes + 3 * B->vtx[1];
+        const double* P2 = nodes + 3 * B->vtx[2];
+        double e1[3], e2[3];
+        for (int i = 0; i < 3; ++i) { e1[i] = P1[i] - P0[i]; e2[i] = P2[i] - P0[i]; }
+        const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                     cz = e1[0] * e2[1] - e1[1] * e2[0];
+        const double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+        const double beta = sqrt(c->cfg.mass / (2.0 * KB * bc->T));
+        const double sn = -beta * (bc->U[0] * N[0] + bc->U[1] * N[1] + bc->U[2] * N[2]);
+        const double flux = bc->n / (2.0 * sqrt(M_PI) * beta) * (exp(-sn * sn) + sqrt(M_PI) * sn * (1.0 + erf(sn)));
+        B->expn = flux * area * c->cfg.dt / c->cfg.F_N;
+        B->s = (float)sn;
+        const double m1 = 0.5, m2 = sn > 0.0 ? sn * sqrt(M_PI) : 0.0;
+        B->p1 = (float)(m1 / (m1 + m2));
+        B->invb = (float)(1.0 / beta);
+        B->sig = (float)sqrt(KB * bc->T / c->cfg.mass);
+        B->ut1 = (float)(bc->U[0] * t1[0] + bc->U[1] * t1[1] + bc->U[2] * t1[2]);
+        B->ut2 = (float)(bc->U[0] * t2[0] + bc->U[1] * t2[1] + bc->U[2] * t2[2]);
+      }
       ++ib;
     }
 
@@ -670,9 +707,10 @@ static void wall_reflect(orc_ctx* c, int32_t ib, float* v, float* Ir, uint32_t s
  *   hit time t_h = a_f / b_f, o <- o + v t_h, t_rem <- t_rem - t_h, new
  *   velocity, e <- o + v t_rem, entry face = the wall face; or leave the domain.
  * All dot products are fma(n2, y2, fma(n1, y1, n0 y0)) in FP64. */
-static int32_t track(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, uint32_t slot, uint32_t step) {
-  double trem = c->cfg.dt;
-  int entry = -1;
+static int32_t track_ex(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, uint32_t slot, uint32_t step,
+                        double t_move, int entry0) {
+  double trem = t_move;
+  int entry = entry0;
   uint32_t hits = 0;
   double o[3] = {x[0], x[1], x[2]};
   double vd[3] = {(double)v[0], (double)v[1], (double)v[2]};
@@ -732,6 +770,10 @@ static int32_t track(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, u
     c->counters[ORC_C_REMOVED]++;
     return -1;
   }
+}
+
+static int32_t track(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, uint32_t slot, uint32_t step) {
+  return track_ex(c, x, v, Ir, cell, slot, step, c->cfg.dt, -1);
 }
 
 int orc_track_one(orc_ctx* c, double* x, float* v, int32_t* cell, int64_t slot, int64_t step) {
@@ -872,6 +914,91 @@ int orc_sample(orc_ctx* c, int32_t action) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* S4: free-stream injection.  Per inflow face and step: N = floor(E + r),    */
+/* r <- E + r - N (E = F A dt / F_N).  Each new particle: uniform point on    */
+/* the face; tangential velocity U_t + N(0, kT/m); inward normal speed from    */
+/* the drifting flux distribution g(z) ~ z exp(-(z-s)^2), z > 0 (z = beta v_n)*/
+/* sampled by acceptance-rejection (below); then it moves for a uniform       */
+/* fraction of dt from the face into the domain.                               */
+/*   s <= 0: z = sqrt(-ln R) (density z exp(-z^2)), accept with exp(2 s z).   */
+/*   s > 0:  dominating function (z-s)^+ e^{-(z-s)^2} + s e^{-(z-s)^2} on all */
+/*           z, component masses 1/2 and s sqrt(pi): z = s + sqrt(-ln R) from */
+/*           the first (always accepted), or z = s + N(0,1/2) from the second,*/
+/*           rejected if z <= 0 and accepted with z/s if z < s -- the ratio   */
+/*           g / dominating function (g = 0 for z <= 0).                      */
+/* Random stream: entity = boundary face, sub = k, draw 0 position, draw 1    */
+/* fraction of dt, draws 2.. tangential Gaussian pair, then normal speed      */
+/* attempts, then (diatomic) the rotational energy.                            */
+/* ------------------------------------------------------------------------- */
+static float inflow_normal_speed(const orc_ctx* c, const bface_t* B, uint32_t ib, uint32_t k, uint32_t step,
+                                 uint32_t* draw) {
+  const float s = B->s;
+  for (int att = 0; att < 64; ++att) {
+    uint32_t w[4];
+    rng4(c, RP_INJECT, ib, k, step, (*draw)++, w);
+    if (s <= 0.0f) {
+      float z = sqrtf(-orc_lnf(u01f(w[0])));
+      if (u01f(w[1]) < orc_expf(2.0f * s * z)) return z;
+    } else if (u01f(w[0]) < B->p1) {
+      return s + sqrtf(-orc_lnf(u01f(w[1])));
+    } else {
+      /* the second component's Gaussian is drawn to completion (polar method
+       * over the following draws) before the acceptance test */
+      float g1, g2;
+      *draw = gauss2(c, RP_INJECT, ib, k, step, *draw, &g1, &g2);
+      float z = s + g1 * 0.707106781f;
+      if (z > 0.0f && (z >= s || u01f(w[3]) * s < z)) return z;
+    }
+  }
+  return s > 0.0f ? s : 0.5f;
+}
+
+static void inject(orc_ctx* c, uint32_t step, uint8_t** moved, int64_t* cap_moved) {
+  for (int32_t ib = 0; ib < c->n_bf; ++ib) {
+    const bface_t* B = c->bf + ib;
+    if (c->bcs[B->bc].kind != 2) continue;
+    double X = B->expn + c->inj_rem[ib];
+    double fl = floor(X);
+    c->inj_rem[ib] = X - fl;
+    const int64_t n = (int64_t)fl;
+    for (int64_t k = 0; k < n; ++k) {
+      const int64_t p = c->N;
+      ensure_cap(c, p + 1);
+      if (p + 1 > *cap_moved) {
+        *cap_moved = 2 * (p + 1);
+        *moved = (uint8_t*)realloc(*moved, (size_t)*cap_moved);
+      }
+      uint32_t w[4];
+      rng4(c, RP_INJECT, (uint32_t)ib, (uint32_t)k, step, 0, w);
+      double r1 = u01d(w[0], w[1]), r2 = u01d(w[2], w[3]);
+      if (r1 + r2 > 1.0) { r1 = 1.0 - r1; r2 = 1.0 - r2; }
+      const double* A = c->nodes + 3 * B->vtx[0];
+      const double* P1 = c->nodes + 3 * B->vtx[1];
+      const double* P2 = c->nodes + 3 * B->vtx[2];
+      double* x = c->x + 3 * p;
+      for (int i = 0; i < 3; ++i) x[i] = A[i] + r1 * (P1[i] - A[i]) + r2 * (P2[i] - A[i]);
+      rng4(c, RP_INJECT, (uint32_t)ib, (uint32_t)k, step, 1, w);
+      const double tfrac = u01d(w[0], w[1]);
+      float g1, g2;
+      uint32_t draw = gauss2(c, RP_INJECT, (uint32_t)ib, (uint32_t)k, step, 2, &g1, &g2);
+      const float vn = inflow_normal_speed(c, B, (uint32_t)ib, (uint32_t)k, step, &draw) * B->invb;
+      const float a = B->ut1 + B->sig * g1, b = B->ut2 + B->sig * g2;
+      float* v = c->v + 3 * p;
+      for (int i = 0; i < 3; ++i) v[i] = (B->t1[i] * a + B->t2[i] * b) - B->nrm[i] * vn;
+      c->Ir[p] = 0.0f;
+      if (c->cfg.rot_dof > 0) {
+        rng4(c, RP_INJECT, (uint32_t)ib, (uint32_t)k, step, draw, w);
+        c->Ir[p] = -(float)c->bcs[B->bc].T * orc_lnf(u01f(w[0]));
+      }
+      c->N = p + 1;
+      c->counters[ORC_C_INJECTED]++;
+      c->cell[p] = track_ex(c, x, v, c->Ir + p, B->tet, (uint32_t)p, step, tfrac * c->cfg.dt, B->face);
+      (*moved)[p] = 1;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
 /* one DSMC time step: move (with walls / outflow), sort, collide, sample     */
 /* ------------------------------------------------------------------------- */
 int orc_dsmc_step(orc_ctx* c, int32_t n_steps, int32_t flags) {
@@ -882,13 +1009,15 @@ int orc_dsmc_step(orc_ctx* c, int32_t n_steps, int32_t flags) {
     const uint32_t step = (uint32_t)c->step;
     c->n_pairs = 0;
     const int64_t N = c->N;
-    uint8_t* moved = (uint8_t*)malloc(N > 0 ? N : 1);
+    int64_t cap_moved = N + 1024;
+    uint8_t* moved = (uint8_t*)malloc((size_t)cap_moved);
     for (int64_t p = 0; p < N; ++p) {
       int32_t old = c->cell[p];
       int32_t nc = track(c, c->x + 3 * p, c->v + 3 * p, c->Ir + p, old, (uint32_t)p, step);
       c->cell[p] = nc;
       moved[p] = (uint8_t)(nc != old);
     }
+    inject(c, step, &moved, &cap_moved);
     sort_particles(c, moved);
     free(moved);
     for (int64_t t = 0; t < c->n_tets; ++t) collide_cell(c, t, step, record);

@@ -122,6 +122,16 @@ def open_box(nh: int, L: float, n_inf: float, T_inf: float, U_inf=(0.0, 0.0, 0.0
     return Mesh(nodes, tets, face_tag, bcs)
 
 
+def box_sides(nh: int, L: float, side_bc, bcs) -> Mesh:
+    """Cube whose six sides (0..5 = -x,+x,-y,+y,-z,+z) carry bcs[side_bc[side]]."""
+    nodes, tets = kuhn_cube(nh, L)
+    side = boundary_side(nodes, tets, L)
+    face_tag = np.full(tets.shape, -1, dtype=np.int32)
+    for sd in range(6):
+        face_tag[side == sd] = side_bc[sd]
+    return Mesh(nodes, tets, face_tag, list(bcs))
+
+
 @dataclasses.dataclass
 class Scenario:
     """Everything a run needs besides the mesh; the same values feed both sides."""

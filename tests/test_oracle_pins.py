@@ -447,3 +447,96 @@ def test_sort_by_cell_matches_stable_argsort():
         ref = keep[np.argsort(cell[keep], kind="stable")]
         assert np.array_equal(order, ref)
         assert np.array_equal(cs, np.concatenate([[0], np.cumsum(np.bincount(cell[keep], minlength=nc))]))
+
+
+# --------------------------------------------------------------- injection (S4)
+def inflow_scenario(U, T=273.0, n=1e20, sides_inflow=(0,), dt=1e-9, F_N=None, n_particles=0, L=1e-3, seed=31):
+    """One-hex box: the listed sides are free-stream inflow, the others outflow;
+    collisions switched off (tiny molecular diameter)."""
+    gas = W.Gas(mass=6.63e-26, d_ref=1e-16, omega=0.81, T_ref=273.0)
+    bcs = [dict(kind=W.BC_INFLOW, T=T, U=tuple(U), n=n), dict(kind=W.BC_OUTFLOW, T=T, U=(0.0, 0.0, 0.0), n=0.0)]
+    side_bc = [0 if sd in sides_inflow else 1 for sd in range(6)]
+    mesh = W.box_sides(1, L, side_bc, bcs)
+    return W.Scenario(gas=gas, mesh=mesh, n_particles=n_particles, n_init=n, T_init=T, u_init=(0.0, 0.0, 0.0),
+                      F_N=F_N if F_N else n * L ** 3 / 20000, dt=dt, seed=seed, L=L, Kn=1.0, capacity=400000)
+
+
+def bird_flux(n, T, m, Un):
+    """Bird (1994) eq. 4.22, one-sided number flux of a drifting Maxwellian."""
+    from scipy.special import erf
+
+    beta = math.sqrt(m / (2 * KB * T))
+    s = beta * Un
+    return n / (2 * math.sqrt(math.pi) * beta) * (math.exp(-s * s) + math.sqrt(math.pi) * s * (1 + erf(s)))
+
+
+def test_injection_count_follows_bird_flux():
+    """P10: particles injected per step through a face = F A dt / F_N with F
+    the one-sided flux of the drifting Maxwellian (Bird eq. 4.22), remainder
+    carried: after S steps the count is within one per face of S F A dt / F_N."""
+    for Ux in (0.0, 400.0, -250.0):
+        sc = inflow_scenario((Ux, 30.0, 0.0), F_N=1e20 * 1e-9 / 3000)
+        o = orc.Oracle(sc)
+        o.write(np.zeros((0, 3)), np.zeros((0, 3), np.float32), np.zeros(0, np.float32), np.zeros(0, np.int32))
+        S = 7
+        o.step(S, 0)
+        got = o.counters()["injected"]
+        # the -x side is split into two triangles of total area L^2; inward normal +x
+        exp_count = S * bird_flux(1e20, 273.0, sc.gas.mass, Ux) * sc.L ** 2 * sc.dt / sc.F_N
+        assert abs(got - exp_count) <= 2.0, (Ux, got, exp_count)
+
+
+@pytest.mark.parametrize("Ux", [300.0, -200.0, 0.0])
+def test_injected_velocity_distribution(Ux):
+    """Injected particles (tiny dt: none has left yet) carry the inflow law:
+    normal speed density ~ v exp(-beta^2 (v - U_n)^2) on v > 0 (moments by
+    numerical integration), tangential components N(U_t, kT/m)."""
+    from scipy.integrate import quad
+
+    T = 273.0
+    m = 6.63e-26
+    F_N = bird_flux(1e20, T, m, Ux) * 1e-6 * 1e-12 / 20000  # ~20,000 injections in one step
+    sc = inflow_scenario((Ux, 40.0, 0.0), T=T, dt=1e-12, F_N=F_N)
+    o = orc.Oracle(sc)
+    o.write(np.zeros((0, 3)), np.zeros((0, 3), np.float32), np.zeros(0, np.float32), np.zeros(0, np.int32))
+    o.step(1, 0)
+    x, v, _, cell = o.read()
+    n = len(v)
+    assert n > 15000
+    vx = v[:, 0].astype(np.float64)
+    assert np.all(vx > 0)
+    beta = math.sqrt(sc.gas.mass / (2 * KB * T))
+    g = lambda z: z * math.exp(-(z - beta * Ux) ** 2)
+    Z = quad(g, 0, np.inf)[0]
+    m1 = quad(lambda z: z * g(z), 0, np.inf)[0] / Z / beta
+    m2 = quad(lambda z: z * z * g(z), 0, np.inf)[0] / Z / beta ** 2
+    assert abs(vx.mean() - m1) < 4 * vx.std() / math.sqrt(n)
+    assert abs((vx ** 2).mean() - m2) < 4 * (vx ** 2).std() / math.sqrt(n)
+    sig = math.sqrt(KB * T / sc.gas.mass)
+    assert abs(v[:, 1].mean() - 40.0) < 4 * sig / math.sqrt(n)
+    assert abs(v[:, 2].mean()) < 4 * sig / math.sqrt(n)
+    assert abs(v[:, 1].astype(np.float64).std() / sig - 1) < 4 * 0.71 / math.sqrt(n)
+    # positions: on or just inside the inflow side x = -L/2
+    assert np.all(x[:, 0] >= -0.5 * sc.L - 1e-15) and np.all(x[:, 0] < -0.5 * sc.L + 1e-8)
+
+
+def test_open_box_reaches_free_stream():
+    """P10: a box with free-stream inflow on all six sides and no collisions
+    fills to the free-stream state: number density n, drift U, temperature T."""
+    T, n, U = 300.0, 1e20, (150.0, -60.0, 0.0)
+    sc = inflow_scenario(U, T=T, n=n, sides_inflow=range(6), dt=5e-8, F_N=n * 1e-9 / 20000)
+    o = orc.Oracle(sc)
+    o.write(np.zeros((0, 3)), np.zeros((0, 3), np.float32), np.zeros(0, np.float32), np.zeros(0, np.int32))
+    o.step(600, 0)  # ~10 box-crossing times: slow molecules need long to fill the box
+    o.sample(orc.RESET_CUMUL)
+    o.step(400, orc.CUMUL)
+    Phi = o.moments(orc.PHI_CUM).sum(axis=0) / 400
+    N = Phi[0]
+    dens = N * sc.F_N / sc.L ** 3
+    u = Phi[1:4] / N
+    T_m = sc.gas.mass * (Phi[4:7] / N - u * u).sum() / (3 * KB)
+    assert abs(dens / n - 1) < 0.02, dens / n
+    assert np.all(np.abs(u - np.array(U)) < 6.0), u
+    assert abs(T_m / T - 1) < 0.02, T_m
+    c = o.counters()
+    assert c["injected"] > 0 and c["removed"] > 0
