@@ -94,6 +94,7 @@ struct dig_ctx {
   std::vector<double> vol, cumvol, fdtv;
   std::vector<BFaceDev> bf;
   std::vector<BCDev> bc;
+  std::vector<InflowDev> inflow;
   float margin = 0.0f;
   bool mesh_ok = false;
   // device
@@ -307,6 +308,7 @@ int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t*
     for (int i = 0; i < 3; ++i) B.U[i] = (float)bcs[b].U[i];
   }
   ctx->bf.clear();
+  ctx->inflow.clear();
   for (int64_t t = 0; t < n; ++t)
     for (int f = 0; f < 4; ++f) {
       if (ctx->nbr[4 * t + f] != INT32_MIN) continue;
@@ -331,6 +333,45 @@ int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t*
         B.nrm[i] = (float)N3[i];
         B.t1[i] = (float)t1[i];
         B.t2[i] = (float)t2[i];
+      }
+      if (bcs[B.bc].kind == DIG_BC_INFLOW) {
+        // Bird (1994) eq. 4.22: one-sided number flux of the drifting free stream
+        // through the face, inward normal -n; constants of the inflow law
+        const dig_bc& fb = bcs[B.bc];
+        InflowDev F{};
+        F.bface = (int)ctx->bf.size();
+        F.tet = (int)t;
+        F.face = f;
+        int vq[3], kq = 0;
+        for (int q = 0; q < 4; ++q)
+          if (q != f) vq[kq++] = tets[4 * t + q];
+        const double* P0 = nodes + 3 * vq[0];
+        const double* P1 = nodes + 3 * vq[1];
+        const double* P2 = nodes + 3 * vq[2];
+        double e1[3], e2[3];
+        for (int i = 0; i < 3; ++i) {
+          F.a[i] = P0[i];
+          F.b[i] = P1[i];
+          F.c[i] = P2[i];
+          e1[i] = P1[i] - P0[i];
+          e2[i] = P2[i] - P0[i];
+        }
+        const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                     cz = e1[0] * e2[1] - e1[1] * e2[0];
+        const double area = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+        const double beta = std::sqrt(ctx->cfg.mass / (2.0 * KB * fb.T));
+        const double sn = -beta * (fb.U[0] * N3[0] + fb.U[1] * N3[1] + fb.U[2] * N3[2]);
+        const double flux = fb.n / (2.0 * std::sqrt(M_PI) * beta) *
+                            (std::exp(-sn * sn) + std::sqrt(M_PI) * sn * (1.0 + std::erf(sn)));
+        F.expn = flux * area * ctx->cfg.dt / ctx->cfg.F_N;
+        F.s = (float)sn;
+        const double m1 = 0.5, m2 = sn > 0.0 ? sn * std::sqrt(M_PI) : 0.0;
+        F.p1 = (float)(m1 / (m1 + m2));
+        F.invb = (float)(1.0 / beta);
+        F.sig = (float)std::sqrt(KB * fb.T / ctx->cfg.mass);
+        F.ut1 = (float)(fb.U[0] * t1[0] + fb.U[1] * t1[1] + fb.U[2] * t1[2]);
+        F.ut2 = (float)(fb.U[0] * t2[0] + fb.U[1] * t2[1] + fb.U[2] * t2[2]);
+        ctx->inflow.push_back(F);
       }
       ctx->nbr[4 * t + f] = -1 - (int32_t)ctx->bf.size();
       ctx->nbrf[4 * t + f] = (signed char)f;
@@ -358,6 +399,11 @@ static size_t layout(dig_ctx* ctx, char* base) {
   P.bf = A.take<BFaceDev>(std::max<size_t>(nb, 1));
   P.bc = A.take<BCDev>(ctx->bc.size());
   P.bflux = A.take<double>(5 * std::max<size_t>(nb, 1));
+  const size_t ni = ctx->inflow.size();
+  P.inflow = A.take<InflowDev>(std::max<size_t>(ni, 1));
+  P.inj_rem = A.take<double>(std::max<size_t>(ni, 1));
+  P.inj_cnt = A.take<int>(std::max<size_t>(ni, 1));
+  P.inj_off = A.take<int>(ni + 1);
   ctx->dnodes = A.take<double>(3 * (size_t)ctx->n_nodes);
   ctx->dtets = A.take<int>(4 * n);
   P.nodes = ctx->dnodes;
@@ -419,6 +465,7 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   const size_t n = (size_t)ctx->n_tets;
   P.n_cells = (int)n;
   P.n_bf = (int)ctx->bf.size();
+  P.n_in = (int)ctx->inflow.size();
   P.max_cross = c.max_cross;
   P.rot_dof = c.rot_dof;
   P.margin = ctx->margin;
@@ -455,6 +502,11 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
     CK(cudaMemcpyAsync((void*)P.bf, ctx->bf.data(), ctx->bf.size() * sizeof(BFaceDev), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync((void*)P.bc, ctx->bc.data(), ctx->bc.size() * sizeof(BCDev), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(P.bflux, 0, 5 * std::max<size_t>(ctx->bf.size(), 1) * sizeof(double), s));
+  if (!ctx->inflow.empty()) {
+    CK(cudaMemcpyAsync((void*)P.inflow, ctx->inflow.data(), ctx->inflow.size() * sizeof(InflowDev),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(P.inj_rem, 0, ctx->inflow.size() * sizeof(double), s));
+  }
   CK(cudaMemcpyAsync(ctx->dnodes, ctx->nodes.data(), ctx->nodes.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ctx->dtets, ctx->tets.data(), ctx->tets.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   std::vector<float> cm(n, ctx->cmax0);
@@ -546,6 +598,8 @@ static void pass(dig_ctx* ctx, int pass_flags, int sflags, uint32_t step_coll, u
   launch_cell_pass(ctx->P, ctx->buf[ctx->cur], ctx->buf[other], pass_flags, sflags, step_coll, step_move,
                    ewma_first, ctx->tile_cells, ctx->stage_cap, ctx->cta_threads, ctx->stream);
   if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
+  if (pass_flags & PASS_MOVE)
+    launch_inject(ctx->P, ctx->buf[other], step_move, (sflags & S_WALLFLUX) != 0, ctx->stream);
   ctx->cur = other;
   launch_scan(ctx->P, ctx->stream);
   launch_scatter(ctx->P, ctx->buf[ctx->cur].mc, ctx->stream);

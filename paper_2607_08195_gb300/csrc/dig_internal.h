@@ -39,6 +39,15 @@ struct BFaceDev {
   float nrm[3], t1[3], t2[3];
 };
 
+// a free-stream inflow face: its boundary face, tet and local face, corners,
+// expected injections per step and the constants of the inflow law
+struct InflowDev {
+  int bface, tet, face, pad;
+  double a[3], b[3], c[3];
+  double expn;
+  float s, p1, invb, sig, ut1, ut2;
+};
+
 // one particle buffer, structure of arrays; x,y,z and vx,vy,vz are contiguous
 // blocks of `cap` elements each
 struct Buf {
@@ -62,6 +71,11 @@ struct Params {
   const BFaceDev* bf;
   const BCDev* bc;
   double* bflux;            // [5 n_bf]
+  int n_in;                 // inflow faces
+  const InflowDev* inflow;  // [n_in]
+  double* inj_rem;          // [n_in] carried fractional injection counts
+  int* inj_cnt;             // [n_in] injections of the current step
+  int* inj_off;             // [n_in + 1] their exclusive scan
   float margin;             // FP32 filter margin (see track())
   double dt;
   double mass_fn;           // m F_N (wall flux bookkeeping)
@@ -106,6 +120,7 @@ void launch_scatter(const Params& P, const int* mc, cudaStream_t s);
 void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags,
                       uint32_t step_coll, uint32_t step_move, int ewma_first, int tile_cells,
                       int stage_cap, int threads, cudaStream_t s);
+void launch_inject(const Params& P, const Buf& out, uint32_t step, int wallflux, cudaStream_t s);
 void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* Is, int* cells,
                  int n, cudaStream_t s);
 void launch_moments_ex(const Params& P, const double* phi, double scale, int macro, double* out, double mass,

@@ -125,6 +125,31 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double((int)hi, (int)(b << 29));
 }
 
+// Gaussian pair, Marsaglia's polar method; two attempts per Philox block;
+// returns the index of the first unused draw.
+__device__ uint32_t gauss2_next(const Params& P, uint32_t purpose, uint32_t ent, uint32_t sub, uint32_t step,
+                                uint32_t draw0, float& g1, float& g2) {
+  for (uint32_t d = draw0; d < draw0 + 32; ++d) {
+    uint32_t w[4];
+    rng(P, purpose, ent, sub, step, d, w);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const float u1 = 2.0f * u01f(w[2 * a]) - 1.0f;
+      const float u2 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
+      const float s = u1 * u1 + u2 * u2;
+      if (s < 1.0f && s > 0.0f) {
+        const float f = sqrtf(-2.0f * ln_f(s) / s);
+        g1 = u1 * f;
+        g2 = u2 * f;
+        return d + 1;
+      }
+    }
+  }
+  g1 = 0.0f;
+  g2 = 0.0f;
+  return draw0 + 32;
+}
+
 // Gaussian pair, Marsaglia's polar method; two attempts per Philox block.
 __device__ void gauss2(const Params& P, uint32_t purpose, uint32_t ent, uint32_t sub, uint32_t step,
                        uint32_t draw0, float& g1, float& g2) {
@@ -360,9 +385,7 @@ __device__ __forceinline__ Exit exit_face(const Params& P, const Plane64* pl, co
 // decisions they prove (plane_test32, exit_face).
 template <bool DIAT>
 __device__ int track(const Params& P, double& x, double& y, double& z, float& vx, float& vy, float& vz, float& I,
-                     int cell, uint32_t slot, uint32_t step, bool flux, Cnt& cnt) {
-  double trem = P.dt;
-  int entry = -1;
+                     int cell, uint32_t slot, uint32_t step, bool flux, Cnt& cnt, double trem, int entry) {
   uint32_t hits = 0;
   double ox = x, oy = y, oz = z;
   double vdx = f2d(vx), vdy = f2d(vy), vdz = f2d(vz);
@@ -842,7 +865,7 @@ __global__ void __launch_bounds__(CP_THREADS, DIG_CP_RESIDENT / CP_THREADS) k_ce
       const int s = s_src[k], lc = s_cl[k], cell = c0 + g0 + lc, slot = gbase + k;
       double x = IN.x[s], y = IN.y[s], z = IN.z[s];
       float vx = s_vx[k], vy = s_vy[k], vz = s_vz[k], I = DIAT ? s_I[k] : 0.0f;
-      const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)slot, step_move, flux, cnt);
+      const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)slot, step_move, flux, cnt, P.dt, -1);
       OUT.x[slot] = x;
       OUT.y[slot] = y;
       OUT.z[slot] = z;
@@ -865,6 +888,157 @@ __global__ void __launch_bounds__(CP_THREADS, DIG_CP_RESIDENT / CP_THREADS) k_ce
     P.sbase[c0 + c] = s_cs[c];
     P.nold[c0 + c] = s_cs[c + 1] - s_cs[c];
   }
+  flush_counters(P, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// S4: free-stream injection through inflow faces (Bird's one-sided flux, the
+// count carried as an FP64 remainder per face; the normal speed drawn from the
+// drifting flux law z exp(-(z-s)^2), z = beta v_n > 0, by acceptance-rejection:
+//   s <= 0: z = sqrt(-ln R), accepted with exp(2 s z);
+//   s > 0:  dominating function (z-s)^+ e^{-(z-s)^2} + s e^{-(z-s)^2}, masses
+//           1/2 and s sqrt(pi): z = s + sqrt(-ln R), or z = s + N(0,1/2)
+//           (Gaussian drawn to completion) rejected for z <= 0 and accepted
+//           with z/s below s.
+// New particles are appended after every existing slot, face-major in
+// boundary-face order, then move for a uniform fraction of dt.
+// ---------------------------------------------------------------------------
+__global__ void k_inj_count(Params P) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P.n_in) return;
+  const double X = P.inflow[j].expn + P.inj_rem[j];
+  const double fl = floor(X);
+  P.inj_rem[j] = X - fl;
+  P.inj_cnt[j] = (int)fl;
+}
+
+// single-CTA exclusive scan of the per-face counts (inflow faces are few
+// compared with particles; the loop walks them in chunks of the block)
+__global__ void __launch_bounds__(1024) k_inj_scan(Params P) {
+  __shared__ int sh[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < P.n_in; base += 1024) {
+    const int j = base + threadIdx.x;
+    const int v = j < P.n_in ? P.inj_cnt[j] : 0;
+    int inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      int w = sh[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      sh[lane] = w;
+    }
+    __syncthreads();
+    const int excl = carry + inc - v + (warp > 0 ? sh[warp - 1] : 0);
+    if (j < P.n_in) P.inj_off[j] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.inj_off[P.n_in] = carry;
+    const int N0 = P.cs[P.n_cells];
+    long long hi = (long long)N0 + carry;
+    if (hi > P.cap) {
+      atomicOr(P.status, ST_CAPACITY);
+      hi = P.cap;
+    }
+    P.state[1] = N0;
+    P.state[2] = (int)hi;
+  }
+}
+
+template <bool DIAT>
+__device__ float inflow_normal_speed(const Params& P, const InflowDev& F, uint32_t ib, uint32_t k, uint32_t step,
+                                     uint32_t& draw) {
+  const float s = F.s;
+  for (int att = 0; att < 64; ++att) {
+    uint32_t w[4];
+    rng(P, RP_INJECT, ib, k, step, draw++, w);
+    if (s <= 0.0f) {
+      const float z = sqrtf(-ln_f(u01f(w[0])));
+      if (u01f(w[1]) < exp_f(2.0f * s * z)) return z;
+    } else if (u01f(w[0]) < F.p1) {
+      return s + sqrtf(-ln_f(u01f(w[1])));
+    } else {
+      float g1, g2;
+      draw = gauss2_next(P, RP_INJECT, ib, k, step, draw, g1, g2);
+      const float z = s + g1 * 0.707106781f;
+      if (z > 0.0f && (z >= s || u01f(w[3]) * s < z)) return z;
+    }
+  }
+  return s > 0.0f ? s : 0.5f;
+}
+
+template <bool DIAT>
+__global__ void k_inj_gen(Params P, Buf OUT, uint32_t step, int wallflux) {
+  const int N0 = P.state[1], total = P.state[2] - N0;
+  Cnt cnt;
+  unsigned inj = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    ++inj;
+    // face of this new particle: last j with inj_off[j] <= t
+    int lo = 0, hi = P.n_in - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (P.inj_off[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const InflowDev F = P.inflow[lo];
+    const uint32_t ib = (uint32_t)F.bface, k = (uint32_t)(t - P.inj_off[lo]);
+    const int slot = N0 + t;
+    uint32_t w[4];
+    rng(P, RP_INJECT, ib, k, step, 0, w);
+    double r1 = u01d(w[0], w[1]), r2 = u01d(w[2], w[3]);
+    if (r1 + r2 > 1.0) {
+      r1 = 1.0 - r1;
+      r2 = 1.0 - r2;
+    }
+    double x = F.a[0] + r1 * (F.b[0] - F.a[0]) + r2 * (F.c[0] - F.a[0]);
+    double y = F.a[1] + r1 * (F.b[1] - F.a[1]) + r2 * (F.c[1] - F.a[1]);
+    double z = F.a[2] + r1 * (F.b[2] - F.a[2]) + r2 * (F.c[2] - F.a[2]);
+    rng(P, RP_INJECT, ib, k, step, 1, w);
+    const double tfrac = u01d(w[0], w[1]);
+    float g1, g2;
+    uint32_t draw = gauss2_next(P, RP_INJECT, ib, k, step, 2, g1, g2);
+    const float vn = inflow_normal_speed<DIAT>(P, F, ib, k, step, draw) * F.invb;
+    const BFaceDev B = P.bf[F.bface];
+    const float a = F.ut1 + F.sig * g1, b = F.ut2 + F.sig * g2;
+    float vx = (B.t1[0] * a + B.t2[0] * b) - B.nrm[0] * vn;
+    float vy = (B.t1[1] * a + B.t2[1] * b) - B.nrm[1] * vn;
+    float vz = (B.t1[2] * a + B.t2[2] * b) - B.nrm[2] * vn;
+    float I = 0.0f;
+    if (DIAT) {
+      rng(P, RP_INJECT, ib, k, step, draw, w);
+      I = -P.bc[B.bc].T * ln_f(u01f(w[0]));
+    }
+    const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, F.tet, (uint32_t)slot, step, wallflux != 0, cnt,
+                                tfrac * P.dt, F.face);
+    OUT.x[slot] = x;
+    OUT.y[slot] = y;
+    OUT.z[slot] = z;
+    OUT.vx[slot] = vx;
+    OUT.vy[slot] = vy;
+    OUT.vz[slot] = vz;
+    if (DIAT) OUT.Ir[slot] = I;
+    OUT.mc[slot] = dst;
+    if (dst >= 0) atomicAdd(P.na + dst, 1);
+  }
+  // injected count and the tracking counters of the new particles
+  for (int o = 16; o > 0; o >>= 1) inj += __shfl_xor_sync(0xffffffffu, inj, o);
+  if ((threadIdx.x & 31) == 0 && inj) atomicAdd(P.counters + C_INJECTED, (unsigned long long)inj);
   flush_counters(P, cnt);
 }
 
@@ -1251,6 +1425,24 @@ void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, 
   }
 #undef DIG_CP
   ++g_launches;
+}
+
+void launch_inject(const Params& P, const Buf& out, uint32_t step, int wallflux, cudaStream_t s) {
+  if (P.n_in <= 0) return;
+  k_inj_count<<<blocks_for(P.n_in, 256), 256, 0, s>>>(P);
+  k_inj_scan<<<1, 1024, 0, s>>>(P);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  if (P.rot_dof > 0)
+    k_inj_gen<true><<<sms * 4, 256, 0, s>>>(P, out, step, wallflux);
+  else
+    k_inj_gen<false><<<sms * 4, 256, 0, s>>>(P, out, step, wallflux);
+  g_launches += 3;
 }
 
 void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* Is, int* cells, int n,
