@@ -152,6 +152,7 @@ struct orc_ctx {
   int8_t* nbr_face;  /* [4n] local face index in the neighbour */
   double* pn;        /* [12n] outward unit normals */
   double* pd;        /* [4n]  plane offsets: n.x = d on the face */
+  double* parea;     /* [4n]  face areas */
   double* vol;       /* [n] */
   double* cumvol;    /* [n] running sum of volumes */
   double* fdtv;      /* [n] F_N dt / V_c */
@@ -190,6 +191,14 @@ struct orc_ctx {
   uint8_t* pacc;
   int64_t counters[ORC_N_COUNTERS];
   int64_t step;
+  /* DIG coupling */
+  int64_t flux_steps;  /* DSMC steps accumulated in bflux since the last coupling */
+  int64_t n_couple;    /* couplings done */
+  double* cp_half;     /* [6n] M^{k+1/2} fed to the solver: rho, u(3), T_t, T_r (nondimensional) */
+  double* cp_hot;      /* [12n] HoT: sigma (xx,yy,zz,xy,xz,yz), q_t (3), q_r (3) (nondimensional) */
+  double* cp_new;      /* [6n] M^{k+1} */
+  double* cp_own;      /* [6n] the cell's own sampled state (nondimensional) */
+  double* cp_flag;     /* [n] 1 accepted, 2 reconstructed, 0 neither */
 };
 
 static void rng4(const orc_ctx* c, int purpose, uint32_t entity, uint32_t sub, uint32_t step,
@@ -232,7 +241,8 @@ orc_ctx* orc_create(const orc_config* cfg) {
 }
 
 static void free_mesh(orc_ctx* c) {
-  free(c->nbr); free(c->nbr_face); free(c->pn); free(c->pd); free(c->vol); free(c->cumvol);
+  free(c->nbr); free(c->nbr_face); free(c->pn); free(c->pd); free(c->parea); free(c->vol); free(c->cumvol);
+  free(c->cp_half); free(c->cp_hot); free(c->cp_new); free(c->cp_flag); free(c->cp_own);
   free(c->fdtv); free(c->nodes); free(c->tets); free(c->bf); free(c->bflux); free(c->inj_rem); free(c->bcs);
   free(c->bc_sigma); free(c->bc_U); free(c->cstart); free(c->cmax); free(c->rem);
   free(c->phi_inst); free(c->phi_ewma); free(c->phi_win); free(c->phi_cum);
@@ -286,6 +296,7 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
   c->nbr_face = (int8_t*)malloc(4 * n);
   c->pn = (double*)malloc(sizeof(double) * 12 * n);
   c->pd = (double*)malloc(sizeof(double) * 4 * n);
+  c->parea = (double*)malloc(sizeof(double) * 4 * n);
   c->vol = (double*)malloc(sizeof(double) * n);
   c->cumvol = (double*)malloc(sizeof(double) * n);
   c->fdtv = (double*)malloc(sizeof(double) * n);
@@ -340,6 +351,7 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
       double* N = c->pn + 12 * t + 3 * f;
       N[0] = nn[0]; N[1] = nn[1]; N[2] = nn[2];
       c->pd[4 * t + f] = nn[0] * A[0] + nn[1] * A[1] + nn[2] * A[2];
+      c->parea[4 * t + f] = 0.5 * len;
     }
   }
 
@@ -1023,6 +1035,7 @@ int orc_dsmc_step(orc_ctx* c, int32_t n_steps, int32_t flags) {
     for (int64_t t = 0; t < c->n_tets; ++t) collide_cell(c, t, step, record);
     sample_cells(c, flags & (ORC_EWMA | ORC_WINDOW | ORC_CUMUL));
     c->counters[ORC_C_STEPS]++;
+    c->flux_steps++;
   }
   return 0;
 }
@@ -1146,5 +1159,472 @@ int orc_sort_by_cell(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* c
   for (int64_t i = 0; i < n; ++i)
     if (cell[i] >= 0) order[cur[cell[i]]++] = (int32_t)i;
   free(cur);
+  return 0;
+}
+
+/* ========================================================================= */
+/* DIG coupling (paper Sec. 3, Alg. 1): S9 HoT extraction and reliability    */
+/* filter, S10 synthetic-equation solve, S11 particle recalibration.         */
+/* Nondimensional variables (Sec. 2.2): lengths / L0, density / (m n0),      */
+/* temperature / T0, velocity / sqrt(R T0), R = k/m; then p = rho T_t,       */
+/* mu = Kn sqrt(2/pi) T_t^omega (from the paper's Kn definition), stress /   */
+/* (rho0 R T0), heat flux / (rho0 (R T0)^{3/2}).                              */
+/* ========================================================================= */
+typedef struct {
+  double L0, T0, rho0, c0, Kn, omega, gam, dr, Zr;
+} nd_t;
+
+static nd_t nondim(const orc_ctx* c) {
+  nd_t d;
+  d.L0 = c->cfg.L_ref;
+  d.T0 = c->cfg.T_init;
+  d.rho0 = c->cfg.mass * c->cfg.n_init;
+  d.c0 = sqrt(KB / c->cfg.mass * d.T0);
+  d.Kn = c->cfg.Kn;
+  d.omega = c->cfg.omega;
+  d.dr = (double)c->cfg.rot_dof;
+  d.gam = (5.0 + d.dr) / (3.0 + d.dr);
+  d.Zr = c->cfg.Z_rot;
+  return d;
+}
+
+/* viscosity and conductivities (Sec. 2.2, NSF relations; the heat-flux
+ * relaxation matrix is not given: kappa_t = 15/4 mu, kappa_r = 1.32 mu) */
+static double mu_nd(const nd_t* d, double Tt) { return d->Kn * sqrt(2.0 / M_PI) * pow(Tt > 1e-6 ? Tt : 1e-6, d->omega); }
+
+/* boundary values of u, T_t, T_r at boundary face ib (walls: wall values;
+ * open faces: free stream) */
+static void bc_values(const orc_ctx* c, const nd_t* d, int32_t ib, double* u, double* T) {
+  const orc_bc* b = c->bcs + c->bf[ib].bc;
+  for (int i = 0; i < 3; ++i) u[i] = b->U[i] / d->c0;
+  *T = b->T / d->T0;
+}
+
+/* Green-Gauss gradients of u (3) and T_t, T_r at every cell:
+ * grad phi_c = 1/V_c sum_f phi_f n_f A_f, phi_f = mean of the two cells,
+ * boundary values at boundary faces.  prim[6n]: rho, u(3), T_t, T_r. */
+static void gradients(const orc_ctx* c, const nd_t* d, const double* prim, double* grad /* [15n] */) {
+  const int64_t n = c->n_tets;
+  for (int64_t t = 0; t < n; ++t) {
+    double g[15];
+    memset(g, 0, sizeof g);
+    const double* Pc = prim + 6 * t;
+    for (int f = 0; f < 4; ++f) {
+      const double* N = c->pn + 12 * t + 3 * f;
+      const double A = c->parea[4 * t + f] / (d->L0 * d->L0);
+      const int32_t nb = c->nbr[4 * t + f];
+      double phi[5];
+      if (nb >= 0) {
+        const double* Pn = prim + 6 * (int64_t)nb;
+        for (int q = 0; q < 5; ++q) phi[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
+      } else {
+        double ub[3], Tb;
+        bc_values(c, d, -1 - nb, ub, &Tb);
+        phi[0] = ub[0]; phi[1] = ub[1]; phi[2] = ub[2]; phi[3] = Tb; phi[4] = Tb;
+      }
+      for (int q = 0; q < 5; ++q)
+        for (int i = 0; i < 3; ++i) g[3 * q + i] += phi[q] * N[i] * A;
+    }
+    const double V = c->vol[t] / (d->L0 * d->L0 * d->L0);
+    for (int q = 0; q < 15; ++q) grad[15 * t + q] = g[q] / V;
+  }
+}
+
+/* NSF stress (6) and heat fluxes (3 + 3) of one cell from its primitives and gradients */
+static void nsf(const nd_t* d, const double* P, const double* G, double* sig, double* qt, double* qr) {
+  const double mu = mu_nd(d, P[4]);
+  /* G[3q + i] = d phi_q / d x_i ; phi_0..2 = u_x,u_y,u_z */
+  const double div = G[0] + G[4] + G[8];
+  sig[0] = -mu * (2.0 * G[0] - 2.0 / 3.0 * div);
+  sig[1] = -mu * (2.0 * G[4] - 2.0 / 3.0 * div);
+  sig[2] = -mu * (2.0 * G[8] - 2.0 / 3.0 * div);
+  sig[3] = -mu * (G[1] + G[3]);
+  sig[4] = -mu * (G[2] + G[6]);
+  sig[5] = -mu * (G[5] + G[7]);
+  const double kt = 3.75 * mu, kr = 1.32 * mu;
+  for (int i = 0; i < 3; ++i) {
+    qt[i] = -kt * G[9 + i];
+    qr[i] = d->dr > 0 ? -kr * G[12 + i] : 0.0;
+  }
+}
+
+/* S9: M^{k+1/2}, HoT and the reliability filter with neighbour reconstruction */
+static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_rec) {
+  const int64_t n = c->n_tets;
+  double* mac = (double*)malloc(sizeof(double) * NMAC * n);
+  double* grad = (double*)malloc(sizeof(double) * 15 * n);
+  double* sdsmc = (double*)malloc(sizeof(double) * 12 * n);
+  for (int64_t t = 0; t < n; ++t) {
+    derive_macro(c, c->phi_ewma + NPHI_MAX * t, c->vol[t], mac + NMAC * t);
+    const double* M = mac + NMAC * t;
+    double* own = c->cp_own + 6 * t;
+    own[0] = M[1] / d->rho0;
+    own[1] = M[2] / d->c0; own[2] = M[3] / d->c0; own[3] = M[4] / d->c0;
+    own[4] = M[5] / d->T0;
+    own[5] = d->dr > 0 ? M[6] / d->T0 : own[4];
+    const double ss = d->rho0 * d->c0 * d->c0, qs = ss * d->c0;
+    for (int q = 0; q < 6; ++q) sdsmc[12 * t + q] = M[8 + q] / ss;
+    for (int q = 0; q < 3; ++q) {
+      sdsmc[12 * t + 6 + q] = M[14 + q] / qs;
+      sdsmc[12 * t + 9 + q] = M[17 + q] / qs;
+    }
+  }
+  gradients(c, d, c->cp_own, grad);
+  uint8_t* avail = (uint8_t*)calloc(n, 1);
+  *n_rej = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    const double* P = c->cp_own + 6 * t;
+    double sig[6], qt[3], qr[3];
+    nsf(d, P, grad + 15 * t, sig, qt, qr);
+    double* H = c->cp_hot + 12 * t;
+    for (int q = 0; q < 6; ++q) H[q] = sdsmc[12 * t + q] - sig[q];
+    for (int q = 0; q < 3; ++q) {
+      H[6 + q] = sdsmc[12 * t + 6 + q] - qt[q];
+      H[9 + q] = sdsmc[12 * t + 9 + q] - qr[q];
+    }
+    memcpy(c->cp_half + 6 * t, P, 6 * sizeof(double));
+    /* local cell Knudsen number (Eq. cell_kn_stability) */
+    const double V = c->vol[t] / (d->L0 * d->L0 * d->L0);
+    const double dc = 2.0 * cbrt(3.0 * V / (4.0 * M_PI));
+    int ok = mac[NMAC * t] > 0.0 && P[0] > 0.0 && P[4] > 0.0;
+    for (int q = 0; q < 6 && ok; ++q) ok = isfinite(P[q]);
+    for (int q = 0; q < 12 && ok; ++q) ok = isfinite(H[q]);
+    if (ok) {
+      const double lam = d->Kn * pow(P[4], d->omega - 0.5) / P[0];
+      ok = lam / dc <= c->cfg.KnD_max;
+    }
+    avail[t] = (uint8_t)ok;
+    c->cp_flag[t] = ok ? 1.0 : 0.0;
+    if (!ok) (*n_rej)++;
+  }
+  /* reconstruction passes: a rejected cell with available face neighbours
+   * takes their equal-weight mean (state and HoT); it becomes available for
+   * the next pass */
+  *n_rec = 0;
+  uint8_t* nxt = (uint8_t*)malloc(n);
+  for (int pass = 0; pass < c->cfg.passes; ++pass) {
+    memcpy(nxt, avail, n);
+    for (int64_t t = 0; t < n; ++t) {
+      if (avail[t]) continue;
+      double acc[18];
+      memset(acc, 0, sizeof acc);
+      int cnt = 0;
+      for (int f = 0; f < 4; ++f) {
+        const int32_t nb = c->nbr[4 * t + f];
+        if (nb < 0 || !avail[nb]) continue;
+        for (int q = 0; q < 6; ++q) acc[q] += c->cp_half[6 * (int64_t)nb + q];
+        for (int q = 0; q < 12; ++q) acc[6 + q] += c->cp_hot[12 * (int64_t)nb + q];
+        cnt++;
+      }
+      if (cnt == 0) continue;
+      for (int q = 0; q < 6; ++q) c->cp_half[6 * t + q] = acc[q] / cnt;
+      for (int q = 0; q < 12; ++q) c->cp_hot[12 * t + q] = acc[6 + q] / cnt;
+      nxt[t] = 1;
+      c->cp_flag[t] = 2.0;
+      (*n_rec)++;
+    }
+    memcpy(avail, nxt, n);
+  }
+  free(nxt); free(avail); free(mac); free(grad); free(sdsmc);
+}
+
+/* S10: steady synthetic equations (Eq. macro with the closure
+ * sigma = sigma_NSF + HoT, q = q_NSF + HoT) by explicit pseudo-time
+ * stepping with one global step (the smallest local step at CFL 0.5, so the
+ * transient stays conservative): cell-centred finite volumes,
+ * Rusanov inviscid flux, face-averaged stress and heat flux, walls closed by
+ * the DSMC-sampled wall fluxes of the coupling window, open faces by the free
+ * stream.  Stops after N_m iterations or when the residual L2 norm falls
+ * below eps_m times its first value. */
+static void prim_from_cons(const nd_t* d, const double* U, double* P) {
+  const double rho = U[0];
+  const double ux = U[1] / rho, uy = U[2] / rho, uz = U[3] / rho;
+  const double er = d->dr > 0 ? U[5] / rho : 0.0;
+  const double E = U[4] / rho;
+  P[0] = rho; P[1] = ux; P[2] = uy; P[3] = uz;
+  P[4] = (2.0 / 3.0) * (E - 0.5 * (ux * ux + uy * uy + uz * uz) - er);
+  P[5] = d->dr > 0 ? 2.0 * er / d->dr : P[4];
+}
+
+static void cons_from_prim(const nd_t* d, const double* P, double* U) {
+  const double rho = P[0], uu = P[1] * P[1] + P[2] * P[2] + P[3] * P[3];
+  const double er = d->dr > 0 ? 0.5 * d->dr * P[5] : 0.0;
+  U[0] = rho; U[1] = rho * P[1]; U[2] = rho * P[2]; U[3] = rho * P[3];
+  U[4] = rho * (1.5 * P[4] + 0.5 * uu + er);
+  U[5] = rho * er;
+}
+
+/* inviscid flux along unit normal N of primitive state P */
+static void inv_flux(const double* P, const double* U, const double* N, double* F) {
+  const double un = P[1] * N[0] + P[2] * N[1] + P[3] * N[2];
+  const double p = P[0] * P[4];
+  F[0] = U[0] * un;
+  F[1] = U[1] * un + p * N[0];
+  F[2] = U[2] * un + p * N[1];
+  F[3] = U[3] * un + p * N[2];
+  F[4] = (U[4] + p) * un;
+  F[5] = U[5] * un;
+}
+
+static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_out) {
+  const int64_t n = c->n_tets;
+  const int nv = 6;
+  double* U = (double*)malloc(sizeof(double) * nv * n);
+  double* P = (double*)calloc(6 * n, sizeof(double));
+  double* R = (double*)malloc(sizeof(double) * nv * n);
+  double* G = (double*)malloc(sizeof(double) * 15 * n);
+  double* S = (double*)malloc(sizeof(double) * 12 * n); /* total stress and heat fluxes per cell */
+  double* dtl = (double*)malloc(sizeof(double) * n);
+  for (int64_t t = 0; t < n; ++t) cons_from_prim(d, c->cp_half + 6 * t, U + nv * t);
+  const double L2 = d->L0 * d->L0, L3 = L2 * d->L0;
+  const double mflux = d->rho0 * d->c0 * d->c0, eflux = mflux * d->c0;
+  const double wall_t = c->flux_steps > 0 ? (double)c->flux_steps * c->cfg.dt : 0.0;
+  double res0 = 0.0, res = 0.0;
+  int it = 0;
+  for (it = 0; it < c->cfg.N_m; ++it) {
+    for (int64_t t = 0; t < n; ++t) prim_from_cons(d, U + nv * t, P + 6 * t);
+    gradients(c, d, P, G);
+    for (int64_t t = 0; t < n; ++t) {
+      double sig[6], qt[3], qr[3];
+      nsf(d, P + 6 * t, G + 15 * t, sig, qt, qr);
+      const double* H = c->cp_hot + 12 * t;
+      for (int q = 0; q < 6; ++q) S[12 * t + q] = sig[q] + H[q];
+      for (int q = 0; q < 3; ++q) {
+        S[12 * t + 6 + q] = qt[q] + H[6 + q];
+        S[12 * t + 9 + q] = qr[q] + H[9 + q];
+      }
+    }
+    double rsum = 0.0;
+    for (int64_t t = 0; t < n; ++t) {
+      const double* Pc = P + 6 * t;
+      const double* Uc = U + nv * t;
+      const double V = c->vol[t] / L3;
+      double acc[6] = {0, 0, 0, 0, 0, 0};
+      double lam_sum = 0.0;
+      const double cc = sqrt(d->gam * Pc[4]);
+      const double nu = 2.5 * mu_nd(d, Pc[4]) / Pc[0];
+      for (int f = 0; f < 4; ++f) {
+        const double* N = c->pn + 12 * t + 3 * f;
+        const double A = c->parea[4 * t + f] / L2;
+        const int32_t nb = c->nbr[4 * t + f];
+        double F[6];
+        if (nb >= 0 || c->bcs[c->bf[-1 - nb].bc].kind >= 2) {
+          double Pn[6], Un[6];
+          if (nb >= 0) {
+            memcpy(Pn, P + 6 * (int64_t)nb, sizeof Pn);
+            memcpy(Un, U + nv * (int64_t)nb, sizeof Un);
+          } else {
+            const orc_bc* b = c->bcs + c->bf[-1 - nb].bc;
+            Pn[0] = b->kind == 2 ? b->n * c->cfg.mass / d->rho0 : Pc[0];
+            Pn[1] = b->U[0] / d->c0; Pn[2] = b->U[1] / d->c0; Pn[3] = b->U[2] / d->c0;
+            Pn[4] = b->T / d->T0; Pn[5] = Pn[4];
+            if (b->kind == 3) memcpy(Pn, Pc, sizeof Pn);
+            cons_from_prim(d, Pn, Un);
+          }
+          double FL[6], FR[6];
+          inv_flux(Pc, Uc, N, FL);
+          inv_flux(Pn, Un, N, FR);
+          const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
+          const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
+          const double cl = sqrt(d->gam * Pc[4]), cr = sqrt(d->gam * (Pn[4] > 0 ? Pn[4] : 1e-12));
+          const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
+          for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
+          if (nb >= 0) {
+            const double* Sc = S + 12 * t;
+            const double* Sn = S + 12 * (int64_t)nb;
+            double sf[6], qtf[3], qrf[3], uf[3];
+            for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (Sc[q] + Sn[q]);
+            for (int q = 0; q < 3; ++q) {
+              qtf[q] = 0.5 * (Sc[6 + q] + Sn[6 + q]);
+              qrf[q] = 0.5 * (Sc[9 + q] + Sn[9 + q]);
+              uf[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
+            }
+            /* sigma . n with sigma = [[xx,xy,xz],[xy,yy,yz],[xz,yz,zz]] */
+            const double sn0 = sf[0] * N[0] + sf[3] * N[1] + sf[4] * N[2];
+            const double sn1 = sf[3] * N[0] + sf[1] * N[1] + sf[5] * N[2];
+            const double sn2 = sf[4] * N[0] + sf[5] * N[1] + sf[2] * N[2];
+            F[1] += sn0; F[2] += sn1; F[3] += sn2;
+            F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + (qtf[0] + qrf[0]) * N[0] + (qtf[1] + qrf[1]) * N[1] +
+                    (qtf[2] + qrf[2]) * N[2];
+            F[5] += qrf[0] * N[0] + qrf[1] * N[1] + qrf[2] * N[2];
+          }
+          lam_sum += A * (lm + 2.0 * nu * A / V);
+        } else {
+          /* wall: no mass flux; momentum and energy given to the wall per unit
+           * area and time, as sampled by DSMC over the coupling window (if
+           * none was sampled: the cell pressure only) */
+          const int32_t ib = -1 - nb;
+          const double* W = c->bflux + 5 * ib;
+          const double Ad = c->parea[4 * t + f];
+          F[0] = 0.0;
+          if (wall_t > 0.0) {
+            for (int i = 0; i < 3; ++i) F[1 + i] = W[1 + i] / (wall_t * Ad) / mflux;
+            F[4] = W[4] / (wall_t * Ad) / eflux;
+          } else {
+            const double p = Pc[0] * Pc[4];
+            for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
+            F[4] = 0.0;
+          }
+          F[5] = 0.0;
+          lam_sum += A * (cc + 2.0 * nu * A / V);
+        }
+        for (int q = 0; q < 6; ++q) acc[q] += F[q] * A;
+      }
+      double* Rc = R + nv * t;
+      for (int q = 0; q < 6; ++q) Rc[q] = -acc[q] / V;
+      if (d->dr > 0) {
+        /* rotational relaxation source (Eq. macro, last line) */
+        const double T = (3.0 * Pc[4] + d->dr * Pc[5]) / (3.0 + d->dr);
+        const double tau = mu_nd(d, Pc[4]) / (Pc[0] * Pc[4]);
+        Rc[5] += 0.5 * d->dr * Pc[0] * (T - Pc[5]) / (d->Zr * tau);
+      } else {
+        Rc[5] = 0.0;
+      }
+      dtl[t] = 0.5 * V / lam_sum;
+      for (int q = 0; q < 5; ++q) rsum += V * Rc[q] * Rc[q];
+    }
+    res = sqrt(rsum);
+    if (it == 0) res0 = res > 0 ? res : 1.0;
+    if (!isfinite(res)) break;
+    if (res <= c->cfg.eps_m * res0) break;
+    /* one global pseudo-time step (the smallest local stable step) keeps the
+     * transient conservative */
+    double dtg = dtl[0];
+    for (int64_t t = 1; t < n; ++t) dtg = dtl[t] < dtg ? dtl[t] : dtg;
+    for (int64_t t = 0; t < n; ++t)
+      for (int q = 0; q < nv; ++q) U[nv * t + q] += dtg * R[nv * t + q];
+  }
+  int ok = isfinite(res);
+  for (int64_t t = 0; t < n && ok; ++t) {
+    prim_from_cons(d, U + nv * t, c->cp_new + 6 * t);
+    ok = c->cp_new[6 * t] > 0 && c->cp_new[6 * t + 4] > 0;
+  }
+  *iters = it;
+  *res_out = res / res0;
+  free(U); free(P); free(R); free(G); free(S); free(dtl);
+  return ok ? 0 : -5;
+}
+
+/* S11: recalibrate the particles of accepted cells to M^{k+1}:
+ * v' = u_a + (v - u_b) sqrt(T_a / T_b), I' = I T_r,a / T_r,b (ratios clamped
+ * to [1/4, 4]); number ratio r = rho_a / rho_b clamped to [1/2, 2]: delete
+ * with probability 1 - r, or clone with probability r - 1 (the clone at a
+ * uniform point of the cell with the recalibrated velocity).  b = the cell's
+ * own sampled state, a = the solved state. */
+static void recalibrate(orc_ctx* c, const nd_t* d, int64_t* n_clone, int64_t* n_del) {
+  const int64_t n = c->n_tets, N = c->N;
+  *n_clone = 0;
+  *n_del = 0;
+  int64_t cap_moved = N + N / 4 + 1024;
+  uint8_t* moved = (uint8_t*)calloc((size_t)cap_moved, 1);
+  const uint32_t sub = (uint32_t)c->n_couple;
+  for (int64_t t = 0; t < n; ++t) {
+    if (c->cp_flag[t] != 1.0) continue;
+    const double* b = c->cp_own + 6 * t;
+    const double* a = c->cp_new + 6 * t;
+    double rt = a[4] / b[4];
+    rt = rt < 0.25 ? 0.25 : rt > 4.0 ? 4.0 : rt;
+    double rr = d->dr > 0 ? a[5] / b[5] : 1.0;
+    rr = rr < 0.25 ? 0.25 : rr > 4.0 ? 4.0 : rr;
+    double rn = a[0] / b[0];
+    rn = rn < 0.5 ? 0.5 : rn > 2.0 ? 2.0 : rn;
+    const float sc = (float)sqrt(rt), fr = (float)rr;
+    float ua[3], ub[3];
+    for (int i = 0; i < 3; ++i) {
+      ua[i] = (float)(a[1 + i] * d->c0);
+      ub[i] = (float)(b[1 + i] * d->c0);
+    }
+    for (int64_t p = c->cstart[t]; p < c->cstart[t + 1]; ++p) {
+      float* v = c->v + 3 * p;
+      for (int i = 0; i < 3; ++i) v[i] = ua[i] + (v[i] - ub[i]) * sc;
+      c->Ir[p] = c->Ir[p] * fr;
+      uint32_t w[4];
+      rng4(c, RP_RECAL, (uint32_t)p, sub, 0, 0, w);
+      const double R = u01d(w[0], w[1]);
+      if (rn < 1.0) {
+        if (R < 1.0 - rn) {
+          c->cell[p] = -1;
+          (*n_del)++;
+        }
+      } else if (rn > 1.0 && R < rn - 1.0) {
+        const int64_t q = c->N;
+        ensure_cap(c, q + 1);
+        if (q + 1 > cap_moved) {
+          cap_moved = 2 * (q + 1);
+          moved = (uint8_t*)realloc(moved, (size_t)cap_moved);
+        }
+        uint32_t w2[4];
+        rng4(c, RP_RECAL, (uint32_t)p, sub, 0, 1, w);
+        rng4(c, RP_RECAL, (uint32_t)p, sub, 0, 2, w2);
+        double s = u01d(w[0], w[1]), tt = u01d(w[2], w[3]), u = u01d(w2[0], w2[1]);
+        if (s + tt > 1.0) { s = 1.0 - s; tt = 1.0 - tt; }
+        if (tt + u > 1.0) {
+          double tmp = u; u = 1.0 - s - tt; tt = 1.0 - tmp;
+        } else if (s + tt + u > 1.0) {
+          double tmp = u; u = s + tt + u - 1.0; s = 1.0 - tt - tmp;
+        }
+        const double* A = c->nodes + 3 * c->tets[4 * t + 0];
+        const double* B = c->nodes + 3 * c->tets[4 * t + 1];
+        const double* C = c->nodes + 3 * c->tets[4 * t + 2];
+        const double* D = c->nodes + 3 * c->tets[4 * t + 3];
+        for (int i = 0; i < 3; ++i)
+          c->x[3 * q + i] = A[i] + s * (B[i] - A[i]) + tt * (C[i] - A[i]) + u * (D[i] - A[i]);
+        memcpy(c->v + 3 * q, c->v + 3 * p, 3 * sizeof(float));
+        c->Ir[q] = c->Ir[p];
+        c->cell[q] = (int32_t)t;
+        moved[q] = 1;
+        c->N = q + 1;
+        (*n_clone)++;
+      }
+    }
+  }
+  sort_particles(c, moved);
+  free(moved);
+}
+
+int orc_couple(orc_ctx* c, orc_couple_report* rep) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  const int64_t n = c->n_tets;
+  if (!c->cp_half) {
+    c->cp_half = (double*)calloc(6 * n, sizeof(double));
+    c->cp_hot = (double*)calloc(12 * n, sizeof(double));
+    c->cp_new = (double*)calloc(6 * n, sizeof(double));
+    c->cp_own = (double*)calloc(6 * n, sizeof(double));
+    c->cp_flag = (double*)calloc(n, sizeof(double));
+  }
+  const nd_t d = nondim(c);
+  memset(rep, 0, sizeof *rep);
+  extract_hot(c, &d, &rep->n_rejected, &rep->n_reconstructed);
+  int rc = solve_synthetic(c, &d, &rep->iters, &rep->residual);
+  c->n_couple++;
+  if (rc == 0) recalibrate(c, &d, &rep->n_cloned, &rep->n_deleted);
+  memset(c->bflux, 0, sizeof(double) * 5 * (c->n_bf > 0 ? c->n_bf : 1));
+  c->flux_steps = 0;
+  return rc == 0 ? 0 : fail(c, -5, "synthetic solve failed (non-finite or non-positive state)");
+}
+
+int orc_read_couple(orc_ctx* c, int32_t which, double* out, int64_t cap) {
+  const int64_t n = c->n_tets;
+  const double* src = which == 0 ? c->cp_half : which == 1 ? c->cp_hot : which == 2 ? c->cp_new
+                    : which == 3 ? c->cp_flag : c->cp_own;
+  const int64_t k = which == 1 ? 12 : which == 3 ? 1 : 6;
+  if (!src) return fail(c, -7, "no coupling done");
+  if (cap < k * n) return fail(c, -3, "buffer too small");
+  memcpy(out, src, sizeof(double) * k * n);
+  return 0;
+}
+
+int orc_write_moments(orc_ctx* c, int32_t which, const double* in) {
+  const int64_t n = c->n_tets;
+  double* dst = which == ORC_PHI_INST ? c->phi_inst : which == ORC_PHI_EWMA ? c->phi_ewma
+              : which == ORC_PHI_WINDOW ? c->phi_win : c->phi_cum;
+  memcpy(dst, in, sizeof(double) * NPHI_MAX * n);
+  if (which == ORC_PHI_EWMA && c->n_ewma == 0) c->n_ewma = 1;
+  return 0;
+}
+
+int orc_write_wall_flux(orc_ctx* c, const double* in, int64_t steps) {
+  memcpy(c->bflux, in, sizeof(double) * 5 * c->n_bf);
+  c->flux_steps = steps;
   return 0;
 }

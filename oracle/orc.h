@@ -92,6 +92,21 @@ int orc_cell_state(orc_ctx* c, float* cmax, double* rem, int32_t write);
 int orc_wall_flux(orc_ctx* c, double* out, int64_t cap, int64_t* n_bfaces);
 int64_t orc_step_index(orc_ctx* c);
 
+/* DIG coupling (Alg. 1: one outer step after N_s DSMC steps) */
+typedef struct orc_couple_report {
+  int32_t iters;            /* synthetic-solver iterations */
+  int32_t pad;
+  double residual;          /* final residual / first residual */
+  int64_t n_rejected;       /* cells failing the cell-Knudsen criterion */
+  int64_t n_reconstructed;  /* rejected cells rebuilt from neighbours */
+  int64_t n_cloned, n_deleted;
+} orc_couple_report;
+int orc_couple(orc_ctx* c, orc_couple_report* rep);
+/* which: 0 M^{k+1/2} [n][6], 1 HoT [n][12], 2 M^{k+1} [n][6], 3 flags [n], 4 own sampled state [n][6] */
+int orc_read_couple(orc_ctx* c, int32_t which, double* out, int64_t cap);
+int orc_write_moments(orc_ctx* c, int32_t which, const double* in);
+int orc_write_wall_flux(orc_ctx* c, const double* in, int64_t steps);
+
 /* stable counting sort by cell (the paper's per-cell particle buckets):
  * cell[n] in [0, n_cells) or -1 (dropped); writes cell_start[n_cells+1] and
  * order[] = indices of the kept elements sorted by cell, ties by index. */

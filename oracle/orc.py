@@ -32,6 +32,14 @@ class OrcConfig(C.Structure):
     ]
 
 
+class CoupleReport(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("pad", C.c_int32), ("residual", C.c_double), ("n_rejected", C.c_int64),
+                ("n_reconstructed", C.c_int64), ("n_cloned", C.c_int64), ("n_deleted", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 class OrcBC(C.Structure):
     _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("T", C.c_double), ("U", C.c_double * 3),
                 ("n", C.c_double)]
@@ -87,6 +95,10 @@ def lib():
         L.orc_locate.argtypes = [P, P, C.c_double]
         L.orc_track_one.argtypes = [P, P, P, P, C.c_int64, C.c_int64]
         L.orc_sort_by_cell.argtypes = [P, C.c_int64, C.c_int32, P, P]
+        L.orc_couple.argtypes = [P, P]
+        L.orc_read_couple.argtypes = [P, C.c_int32, P, C.c_int64]
+        L.orc_write_moments.argtypes = [P, C.c_int32, P]
+        L.orc_write_wall_flux.argtypes = [P, P, C.c_int64]
         _lib = L
     return _lib
 
@@ -243,6 +255,26 @@ class Oracle:
         c = np.array([cell], np.int32)
         self.L.orc_track_one(self.h, _p(x), _p(v), _p(c), slot, step)
         return x, v, int(c[0])
+
+    def couple(self):
+        r = CoupleReport()
+        self._check(self.L.orc_couple(self.h, C.byref(r)))
+        return r.as_dict()
+
+    def read_couple(self, which):
+        k = {0: 6, 1: 12, 2: 6, 3: 1, 4: 6}[which]
+        out = np.zeros((self.n_tets, k), np.float64)
+        self._check(self.L.orc_read_couple(self.h, which, _p(out), out.size))
+        return out
+
+    def write_moments(self, which, phi):
+        phi = np.ascontiguousarray(phi, np.float64)
+        assert phi.shape == (self.n_tets, NPHI)
+        self._check(self.L.orc_write_moments(self.h, which, _p(phi)))
+
+    def write_wall_flux(self, flux, steps):
+        flux = np.ascontiguousarray(flux, np.float64)
+        self._check(self.L.orc_write_wall_flux(self.h, _p(flux), steps))
 
     @property
     def step_index(self):
