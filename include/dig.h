@@ -218,6 +218,43 @@ int dig_launch_count(dig_ctx* ctx, int64_t* n);
 int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches);
 
 /*
+ * DIG coupling -- one outer step of the paper's Alg. 1 after N_s DSMC steps:
+ * from the moving-average sums, M^{k+1/2} and HoT = sampled stress / heat
+ * flux minus their NSF values (Sec. 3.1, Eq. hot_extraction), the cell
+ * Knudsen criterion Kn_Delta <= KnD_max (Sec. 3.2) with `passes` layers of
+ * equal-weight neighbour reconstruction, the steady synthetic equations
+ * (Eq. macro with Eq. synthetic_closure) solved for M^{k+1} (at most N_m
+ * iterations or residual below eps_m of its first value), and the particles
+ * of accepted cells recalibrated to M^{k+1} (velocities shifted and scaled,
+ * rotational energies scaled, particles cloned or deleted with the density
+ * ratio).  Walls use the momentum and energy given to each wall face during
+ * the DSMC steps run with DIG_WALLFLUX since the last coupling.  Synchronous;
+ * DIG_ERR_SOLVE if the solve produced a non-finite or non-positive state (the
+ * particles are then left unchanged).
+ */
+typedef struct dig_couple_report {
+  int32_t iters;            /* synthetic-solver iterations */
+  int32_t pad;
+  double residual;          /* final residual relative to the first one */
+  int64_t n_rejected;       /* cells failing the cell-Knudsen criterion */
+  int64_t n_reconstructed;  /* rejected cells rebuilt from their neighbours */
+  int64_t n_cloned, n_deleted;
+} dig_couple_report;
+int dig_couple(dig_ctx* ctx, dig_couple_report* out);
+/* coupling fields of the last dig_couple, host out[n_tets][k], nondimensional
+ * (density / (m n_init), velocity / sqrt(k T_init / m), temperature / T_init):
+ * which 0 = M^{k+1/2} fed to the solver (rho, u(3), T_t, T_r; k = 6),
+ * 1 = HoT (sigma xx,yy,zz,xy,xz,yz, q_t(3), q_r(3); k = 12), 2 = M^{k+1}
+ * (k = 6), 3 = cell flags (1 accepted, 2 reconstructed, 0 neither; k = 1),
+ * 4 = each cell's own sampled state (k = 6) */
+int dig_read_couple(dig_ctx* ctx, int32_t which, double* host_out, int64_t cap);
+/* overwrite summation variables (which = DIG_PHI_*) from host in[n_tets][17] */
+int dig_write_moments(dig_ctx* ctx, int32_t which, const double* host_in);
+/* overwrite the per-wall-face sums in[n_bfaces][5] (hits, momentum, energy
+ * given to the wall) and the number of DSMC steps they cover */
+int dig_write_wall_flux(dig_ctx* ctx, const double* host_in, int64_t steps);
+
+/*
  * dig_sort_by_cell -- stable counting sort by cell, the paper's per-cell
  * particle buckets (Sec. 4, Listing 2: one particle bucket per owned cell) as
  * a standalone op on DEVICE arrays, queued on `stream` (a cudaStream_t; NULL =

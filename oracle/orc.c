@@ -1596,8 +1596,9 @@ int orc_couple(orc_ctx* c, orc_couple_report* rep) {
   memset(rep, 0, sizeof *rep);
   extract_hot(c, &d, &rep->n_rejected, &rep->n_reconstructed);
   int rc = solve_synthetic(c, &d, &rep->iters, &rep->residual);
-  c->n_couple++;
+  /* the k-th coupling (k = 0, 1, ...) keys its random stream with sub = k */
   if (rc == 0) recalibrate(c, &d, &rep->n_cloned, &rep->n_deleted);
+  c->n_couple++;
   memset(c->bflux, 0, sizeof(double) * 5 * (c->n_bf > 0 ? c->n_bf : 1));
   c->flux_steps = 0;
   return rc == 0 ? 0 : fail(c, -5, "synthetic solve failed (non-finite or non-positive state)");

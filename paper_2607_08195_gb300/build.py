@@ -23,6 +23,7 @@ UNITS = [
     ("dig_kernels.cu", ["-fmad=false"]),
     ("dig_api.cu", ["-fmad=false"]),
     ("dig_sort.cu", []),
+    ("dig_couple.cu", ["-fmad=false"]),
     ("dig_noalloc.cu", []),
 ]
 

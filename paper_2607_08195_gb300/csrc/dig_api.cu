@@ -91,10 +91,11 @@ struct dig_ctx {
   std::vector<signed char> nbrf;
   std::vector<Plane64> plane;
   std::vector<float4> plane32;
-  std::vector<double> vol, cumvol, fdtv;
+  std::vector<double> vol, cumvol, fdtv, area;
   std::vector<BFaceDev> bf;
   std::vector<BCDev> bc;
   std::vector<InflowDev> inflow;
+  std::vector<dig_bc> bc_host;
   float margin = 0.0f;
   bool mesh_ok = false;
   // device
@@ -113,6 +114,9 @@ struct dig_ctx {
   float cmax0 = 0.0f;
   cudaEvent_t ev = nullptr;
   std::vector<cudaEvent_t> tev;  // event pairs around timed cell passes
+  CoupleParams C{};
+  std::vector<double> bcU, bcT, bcn;
+  int64_t flux_steps = 0, n_couple = 0;
   size_t tev_used = 0;
   bool timing = false;
 };
@@ -199,6 +203,7 @@ int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t*
   ctx->fdtv.resize(n);
   ctx->plane.resize(4 * n);
   ctx->plane32.resize(4 * n);
+  ctx->area.resize(4 * n);
   ctx->nbr.assign(4 * n, INT32_MIN);
   ctx->nbrf.assign(4 * n, 0);
   double run = 0.0, maxd = 0.0, maxx = 0.0;
@@ -245,6 +250,7 @@ int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t*
         nn[2] = -nn[2];
       }
       const double len = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+      ctx->area[4 * t + f] = 0.5 * len;
       nn[0] = nn[0] / len;
       nn[1] = nn[1] / len;
       nn[2] = nn[2] / len;
@@ -300,6 +306,8 @@ int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t*
     i = j;
   }
   ctx->bc.resize(std::max(1, n_bcs));
+  ctx->bc_host.assign(bcs, bcs + n_bcs);
+  ctx->bc_host.resize(std::max(1, n_bcs));
   for (int b = 0; b < n_bcs; ++b) {
     BCDev& B = ctx->bc[b];
     B.kind = bcs[b].kind;
@@ -439,6 +447,32 @@ static size_t layout(dig_ctx* ctx, char* base) {
   P.pairs = A.take<int>(4 * (size_t)P.pair_cap);
   P.pacc = A.take<unsigned char>((size_t)P.pair_cap);
   P.pair_count = A.take<unsigned long long>(1);
+  // DIG coupling
+  CoupleParams& C = ctx->C;
+  C.area = A.take<double>(4 * n);
+  const size_t nbc = std::max<size_t>(ctx->bc.size(), 1);
+  C.bcU = A.take<double>(3 * nbc);
+  C.bcT = A.take<double>(nbc);
+  C.bcn = A.take<double>(nbc);
+  C.own = A.take<double>(6 * n);
+  C.sd = A.take<double>(12 * n);
+  C.grad = A.take<double>(15 * n);
+  C.half = A.take<double>(6 * n);
+  C.hot = A.take<double>(12 * n);
+  C.newst = A.take<double>(6 * n);
+  C.flag = A.take<double>(n);
+  C.nbar = A.take<double>(n);
+  C.U = A.take<double>(6 * n);
+  C.prim = A.take<double>(6 * n);
+  C.S = A.take<double>(12 * n);
+  C.R = A.take<double>(6 * n);
+  C.part = A.take<double>(couple_part_count((int)n));
+  C.avail = A.take<int>(n);
+  C.avail2 = A.take<int>(n);
+  C.stats = A.take<unsigned long long>(4);
+  C.scal = A.take<CoupleScalars>(1);
+  C.rpart = A.take<int>(cap / 4096 + 2);
+  C.clone_total = A.take<int>(1);
   return A.off + 256;
 }
 
@@ -521,7 +555,39 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   CK(cudaMemsetAsync(P.as, 0, (n + 1) * sizeof(int), s));
   for (int* q : {P.nst, P.sbase, P.nold, P.na, P.fill}) CK(cudaMemsetAsync(q, 0, n * sizeof(int), s));
   CK(cudaMemsetAsync(P.pair_count, 0, sizeof(unsigned long long), s));
-  CK(cudaStreamSynchronize(s));  // host tables are freed by the caller's lifetime; keep them anyway
+  // no slot refers to a cell until a pass writes it
+  for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(ctx->buf[b].mc, 0xff, (size_t)c.capacity * sizeof(int), s));
+  {
+    CoupleParams& C = ctx->C;
+    CK(cudaMemcpyAsync((void*)C.area, ctx->area.data(), 4 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    ctx->bcU.assign(3 * ctx->bc.size(), 0.0);
+    ctx->bcT.assign(ctx->bc.size(), 0.0);
+    ctx->bcn.assign(ctx->bc.size(), 0.0);
+    for (size_t b = 0; b < ctx->bc.size(); ++b) {
+      for (int i = 0; i < 3; ++i) ctx->bcU[3 * b + i] = ctx->bc_host[b].U[i];
+      ctx->bcT[b] = ctx->bc_host[b].T;
+      ctx->bcn[b] = ctx->bc_host[b].n;
+    }
+    if (!ctx->bc.empty()) {
+      CK(cudaMemcpyAsync((void*)C.bcU, ctx->bcU.data(), ctx->bcU.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync((void*)C.bcT, ctx->bcT.data(), ctx->bcT.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync((void*)C.bcn, ctx->bcn.data(), ctx->bcn.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    C.L0 = c.L_ref;
+    C.T0 = c.T_init;
+    C.rho0 = c.mass * c.n_init;
+    C.c0 = std::sqrt(KB / c.mass * C.T0);
+    C.Kn = c.Kn;
+    C.omega = c.omega;
+    C.dr = (double)c.rot_dof;
+    C.gam = (5.0 + C.dr) / (3.0 + C.dr);
+    C.Zr = c.Z_rot;
+    C.mass = c.mass;
+    C.FN = c.F_N;
+    C.kB = KB;
+    C.KnD_max = c.KnD_max;
+  }
+  CK(cudaStreamSynchronize(s));
   if (!ctx->ev) CK(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));
   ctx->bound = true;
   return DIG_OK;
@@ -714,6 +780,7 @@ int dsmc_step(dig_ctx* ctx, int32_t n_steps, int32_t flags) {
     }
   }
   ctx->timing = false;
+  if (flags & DIG_WALLFLUX) ctx->flux_steps += n_steps;
   ctx->step += n_steps;
   ctx->host_steps += n_steps;
   if (flags & DIG_SYNC) return check_status(ctx);
@@ -854,6 +921,93 @@ int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches) {
   *launches = (int64_t)(ctx->tev_used / 2);
   ctx->tev_used = 0;
   return DIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DIG coupling (Alg. 1, one outer step)
+// ---------------------------------------------------------------------------
+int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
+  if (!ctx || !out) return DIG_ERR_ARG;
+  if (!ctx->have_particles) return fail(ctx, DIG_ERR_STATE, "dig_couple: no particles");
+  if (ctx->cfg.N_m < 0 || ctx->cfg.passes < 0) return fail(ctx, DIG_ERR_ARG, "dig_couple: bad N_m or passes");
+  std::memset(out, 0, sizeof *out);
+  cudaStream_t s = ctx->stream;
+  CoupleParams& C = ctx->C;
+  C.wall_t = ctx->flux_steps > 0 ? (double)ctx->flux_steps * ctx->cfg.dt : 0.0;
+  CK(cudaMemsetAsync(C.stats, 0, 4 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(C.scal, 0, sizeof(CoupleScalars), s));
+  CK(cudaMemsetAsync(C.clone_total, 0, sizeof(int), s));
+  launch_couple_s9(ctx->P, C, ctx->cfg.passes, s);
+  launch_couple_s10(ctx->P, C, ctx->cfg.N_m, ctx->cfg.eps_m, s);
+  CoupleScalars sc{};
+  int N = 0;
+  CK(cudaMemcpyAsync(&sc, C.scal, sizeof sc, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&N, ctx->P.cs + ctx->n_tets, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  out->iters = sc.iters;
+  out->residual = sc.res / (sc.res0 > 0 ? sc.res0 : 1.0);
+  const uint32_t sub = (uint32_t)ctx->n_couple;
+  ctx->n_couple++;
+  bool solved = !sc.bad && std::isfinite(sc.res);
+  if (solved) {
+    launch_couple_s11(ctx->P, C, ctx->buf[ctx->cur], N, sub, ctx->P.aq, s);
+    launch_scan(ctx->P, s);
+    launch_scatter(ctx->P, ctx->buf[ctx->cur].mc, s);
+    pass(ctx, 0, 0, 0, 0, 0);
+  }
+  CK(cudaMemsetAsync(ctx->P.bflux, 0, 5 * std::max<size_t>(ctx->bf.size(), 1) * sizeof(double), s));
+  ctx->flux_steps = 0;
+  unsigned long long st[4];
+  CK(cudaMemcpyAsync(st, C.stats, sizeof st, cudaMemcpyDeviceToHost, s));
+  rc = check_status(ctx);
+  out->n_rejected = (int64_t)st[0];
+  out->n_reconstructed = (int64_t)st[1];
+  out->n_cloned = (int64_t)st[2];
+  out->n_deleted = (int64_t)st[3];
+  if (rc) return rc;
+  if (!solved) return fail(ctx, DIG_ERR_SOLVE, "synthetic solve failed (non-finite or non-positive state)");
+  return DIG_OK;
+}
+
+int dig_read_couple(dig_ctx* ctx, int32_t which, double* out, int64_t cap) {
+  if (!ctx || !out || which < 0 || which > 4) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "dig_read_couple: no arena");
+  const CoupleParams& C = ctx->C;
+  const double* src = which == 0 ? C.half : which == 1 ? C.hot : which == 2 ? C.newst : which == 3 ? C.flag : C.own;
+  const int k = which == 1 ? 12 : which == 3 ? 1 : 6;
+  const int64_t n = ctx->n_tets;
+  if (cap < k * n) return fail(ctx, DIG_ERR_CAPACITY, "dig_read_couple: buffer too small");
+  std::vector<double> tmp((size_t)k * n);
+  CK(cudaMemcpyAsync(tmp.data(), src, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  for (int64_t c = 0; c < n; ++c)
+    for (int q = 0; q < k; ++q) out[c * k + q] = tmp[(size_t)q * n + c];
+  return DIG_OK;
+}
+
+int dig_write_moments(dig_ctx* ctx, int32_t which, const double* in) {
+  if (!ctx || !in || which < 0 || which > 3) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "dig_write_moments: no arena");
+  const int64_t n = ctx->n_tets;
+  double* dst = which == DIG_PHI_INST ? ctx->P.phi_inst : which == DIG_PHI_EWMA ? ctx->P.phi_ewma
+              : which == DIG_PHI_WINDOW ? ctx->P.phi_win : ctx->P.phi_cum;
+  std::vector<double> tmp((size_t)NPHI * n);
+  for (int64_t c = 0; c < n; ++c)
+    for (int q = 0; q < NPHI; ++q) tmp[(size_t)q * n + c] = in[c * NPHI + q];
+  CK(cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (which == DIG_PHI_EWMA && ctx->n_ewma == 0) ctx->n_ewma = 1;
+  return wait_stream(ctx);
+}
+
+int dig_write_wall_flux(dig_ctx* ctx, const double* in, int64_t steps) {
+  if (!ctx || !in || steps < 0) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "dig_write_wall_flux: no arena");
+  if (!ctx->bf.empty())
+    CK(cudaMemcpyAsync(ctx->P.bflux, in, 5 * ctx->bf.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->flux_steps = steps;
+  return wait_stream(ctx);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,705 @@
+// dig_couple.cu -- the intermittent DIG coupling on the GPU (paper Sec. 3,
+// Alg. 1): S9 HoT extraction with the cell-Knudsen reliability filter and
+// layered neighbour reconstruction, S10 the steady synthetic equations, S11
+// particle recalibration.  FP64 throughout, one thread per cell (the work is
+// per cell and small next to the particle loop); compiled with -fmad=false.
+//
+// Nondimensional variables (Sec. 2.2): lengths / L0, density / (m n0),
+// temperature / T0, velocity / sqrt(R T0); p = rho T_t; mu = Kn sqrt(2/pi)
+// T_t^omega (the paper's Kn definition); kappa_t = 15/4 mu, kappa_r = 1.32 mu.
+// Arrays are component-major, [component][cell].
+#include "dig_internal.h"
+
+namespace dig {
+
+namespace {
+
+__device__ __forceinline__ double mu_nd(const CoupleParams& C, double Tt) {
+  return C.Kn * sqrt(2.0 / M_PI) * pow(Tt > 1e-6 ? Tt : 1e-6, C.omega);
+}
+
+// boundary values (walls: wall velocity and temperature; open: free stream)
+__device__ __forceinline__ void bc_values(const Params& P, const CoupleParams& C, int ib, double* u, double* T) {
+  const int b = P.bf[ib].bc;
+  for (int i = 0; i < 3; ++i) u[i] = C.bcU[3 * b + i] / C.c0;
+  *T = C.bcT[b] / C.T0;
+}
+
+// S9: the cell's own state and sampled stress / heat flux from the moving
+// average of the summation variables (Eq. dsmc_temperatures, nondimensional)
+__global__ void k_cp_extract(Params P, CoupleParams C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  double ph[NPHI];
+  for (int q = 0; q < NPHI; ++q) ph[q] = P.phi_ewma[(size_t)q * n + c];
+  double M[NMAC];
+  for (int q = 0; q < NMAC; ++q) M[q] = 0.0;
+  const double N = ph[0];
+  M[0] = N;
+  if (N > 0.0) {
+    const double V = P.vol[c];
+    const double u0 = ph[1] / N, u1 = ph[2] / N, u2 = ph[3] / N;
+    const double m00 = ph[4] / N, m11 = ph[5] / N, m22 = ph[6] / N, m01 = ph[7] / N, m02 = ph[8] / N,
+                 m12 = ph[9] / N;
+    const double c00 = m00 - u0 * u0, c11 = m11 - u1 * u1, c22 = m22 - u2 * u2;
+    const double c01 = m01 - u0 * u1, c02 = m02 - u0 * u2, c12 = m12 - u1 * u2;
+    const double tr = c00 + c11 + c22, v2 = m00 + m11 + m22, uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const double rho = C.mass * C.FN * N / V;
+    M[1] = rho;
+    M[2] = u0;
+    M[3] = u1;
+    M[4] = u2;
+    M[5] = C.mass * tr / (3.0 * C.kB);
+    M[6] = C.dr > 0 ? 2.0 * (ph[13] / N) / C.dr : 0.0;
+    M[8] = rho * (c00 - tr / 3.0);
+    M[9] = rho * (c11 - tr / 3.0);
+    M[10] = rho * (c22 - tr / 3.0);
+    M[11] = rho * c01;
+    M[12] = rho * c02;
+    M[13] = rho * c12;
+    const double mv[3][3] = {{m00, m01, m02}, {m01, m11, m12}, {m02, m12, m22}};
+    const double u[3] = {u0, u1, u2};
+    for (int i = 0; i < 3; ++i) {
+      const double uj = u[0] * mv[i][0] + u[1] * mv[i][1] + u[2] * mv[i][2];
+      const double c3 = ph[10 + i] / N - 2.0 * uj - u[i] * v2 + 2.0 * u[i] * uu;
+      M[14 + i] = 0.5 * rho * c3;
+      if (C.dr > 0) M[17 + i] = (C.FN * N / V) * C.kB * (ph[14 + i] / N - u[i] * (ph[13] / N));
+    }
+  }
+  C.own[0 * (size_t)n + c] = M[1] / C.rho0;
+  C.own[1 * (size_t)n + c] = M[2] / C.c0;
+  C.own[2 * (size_t)n + c] = M[3] / C.c0;
+  C.own[3 * (size_t)n + c] = M[4] / C.c0;
+  C.own[4 * (size_t)n + c] = M[5] / C.T0;
+  C.own[5 * (size_t)n + c] = C.dr > 0 ? M[6] / C.T0 : M[5] / C.T0;
+  const double ss = C.rho0 * C.c0 * C.c0, qs = ss * C.c0;
+  for (int q = 0; q < 6; ++q) C.sd[(size_t)q * n + c] = M[8 + q] / ss;
+  for (int q = 0; q < 3; ++q) {
+    C.sd[(size_t)(6 + q) * n + c] = M[14 + q] / qs;
+    C.sd[(size_t)(9 + q) * n + c] = M[17 + q] / qs;
+  }
+  C.nbar[c] = N;
+}
+
+// Green-Gauss gradients of u (3), T_t, T_r from primitives prim[6][n]
+__global__ void k_cp_grad(Params P, CoupleParams C, const double* __restrict__ prim, double* __restrict__ grad) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  double g[15];
+  for (int q = 0; q < 15; ++q) g[q] = 0.0;
+  const double L2 = C.L0 * C.L0;
+  for (int f = 0; f < 4; ++f) {
+    const Plane64 pl = P.plane[4 * (size_t)c + f];
+    const double N3[3] = {pl.nx, pl.ny, pl.nz};
+    const double A = C.area[4 * (size_t)c + f] / L2;
+    const int nb = P.nbr[4 * (size_t)c + f];
+    double phi[5];
+    if (nb >= 0) {
+      for (int q = 0; q < 5; ++q) phi[q] = 0.5 * (prim[(size_t)(1 + q) * n + c] + prim[(size_t)(1 + q) * n + nb]);
+    } else {
+      double ub[3], Tb;
+      bc_values(P, C, -1 - nb, ub, &Tb);
+      phi[0] = ub[0];
+      phi[1] = ub[1];
+      phi[2] = ub[2];
+      phi[3] = Tb;
+      phi[4] = Tb;
+    }
+    for (int q = 0; q < 5; ++q)
+      for (int i = 0; i < 3; ++i) g[3 * q + i] += phi[q] * N3[i] * A;
+  }
+  const double V = P.vol[c] / (L2 * C.L0);
+  for (int q = 0; q < 15; ++q) grad[(size_t)q * n + c] = g[q] / V;
+}
+
+__device__ void nsf(const CoupleParams& C, double Tt, const double* G, double* sig, double* qt, double* qr) {
+  const double mu = mu_nd(C, Tt);
+  const double div = G[0] + G[4] + G[8];
+  sig[0] = -mu * (2.0 * G[0] - 2.0 / 3.0 * div);
+  sig[1] = -mu * (2.0 * G[4] - 2.0 / 3.0 * div);
+  sig[2] = -mu * (2.0 * G[8] - 2.0 / 3.0 * div);
+  sig[3] = -mu * (G[1] + G[3]);
+  sig[4] = -mu * (G[2] + G[6]);
+  sig[5] = -mu * (G[5] + G[7]);
+  const double kt = 3.75 * mu, kr = 1.32 * mu;
+  for (int i = 0; i < 3; ++i) {
+    qt[i] = -kt * G[9 + i];
+    qr[i] = C.dr > 0 ? -kr * G[12 + i] : 0.0;
+  }
+}
+
+// HoT = sampled - NSF; cell Knudsen criterion (Eq. criterion); half = own
+__global__ void k_cp_hot(Params P, CoupleParams C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  double Pc[6], G[15];
+  for (int q = 0; q < 6; ++q) Pc[q] = C.own[(size_t)q * n + c];
+  for (int q = 0; q < 15; ++q) G[q] = C.grad[(size_t)q * n + c];
+  double sig[6], qt[3], qr[3];
+  nsf(C, Pc[4], G, sig, qt, qr);
+  double H[12];
+  for (int q = 0; q < 6; ++q) H[q] = C.sd[(size_t)q * n + c] - sig[q];
+  for (int q = 0; q < 3; ++q) {
+    H[6 + q] = C.sd[(size_t)(6 + q) * n + c] - qt[q];
+    H[9 + q] = C.sd[(size_t)(9 + q) * n + c] - qr[q];
+  }
+  for (int q = 0; q < 12; ++q) C.hot[(size_t)q * n + c] = H[q];
+  for (int q = 0; q < 6; ++q) C.half[(size_t)q * n + c] = Pc[q];
+  const double V = P.vol[c] / (C.L0 * C.L0 * C.L0);
+  const double dc = 2.0 * cbrt(3.0 * V / (4.0 * M_PI));
+  bool ok = C.nbar[c] > 0.0 && Pc[0] > 0.0 && Pc[4] > 0.0;
+  for (int q = 0; q < 6 && ok; ++q) ok = isfinite(Pc[q]);
+  for (int q = 0; q < 12 && ok; ++q) ok = isfinite(H[q]);
+  if (ok) {
+    const double lam = C.Kn * pow(Pc[4], C.omega - 0.5) / Pc[0];
+    ok = lam / dc <= C.KnD_max;
+  }
+  C.avail[c] = ok ? 1 : 0;
+  C.flag[c] = ok ? 1.0 : 0.0;
+  if (!ok) atomicAdd(C.stats + 0, 1ull);
+}
+
+// one reconstruction pass: a rejected cell with available face neighbours
+// takes their equal-weight mean of state and HoT
+__global__ void k_cp_recon(Params P, CoupleParams C, const int* __restrict__ av_in, int* __restrict__ av_out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  if (av_in[c]) {
+    av_out[c] = 1;
+    return;
+  }
+  double acc[18];
+  for (int q = 0; q < 18; ++q) acc[q] = 0.0;
+  int cnt = 0;
+  for (int f = 0; f < 4; ++f) {
+    const int nb = P.nbr[4 * (size_t)c + f];
+    if (nb < 0 || !av_in[nb]) continue;
+    for (int q = 0; q < 6; ++q) acc[q] += C.half[(size_t)q * n + nb];
+    for (int q = 0; q < 12; ++q) acc[6 + q] += C.hot[(size_t)q * n + nb];
+    cnt++;
+  }
+  av_out[c] = cnt > 0 ? 1 : 0;
+  if (cnt == 0) return;
+  for (int q = 0; q < 6; ++q) C.half[(size_t)q * n + c] = acc[q] / cnt;
+  for (int q = 0; q < 12; ++q) C.hot[(size_t)q * n + c] = acc[6 + q] / cnt;
+  C.flag[c] = 2.0;
+  atomicAdd(C.stats + 1, 1ull);
+}
+
+__device__ __forceinline__ void cons_from_prim(const CoupleParams& C, const double* Pp, double* U) {
+  const double rho = Pp[0], uu = Pp[1] * Pp[1] + Pp[2] * Pp[2] + Pp[3] * Pp[3];
+  const double er = C.dr > 0 ? 0.5 * C.dr * Pp[5] : 0.0;
+  U[0] = rho;
+  U[1] = rho * Pp[1];
+  U[2] = rho * Pp[2];
+  U[3] = rho * Pp[3];
+  U[4] = rho * (1.5 * Pp[4] + 0.5 * uu + er);
+  U[5] = rho * er;
+}
+
+__device__ __forceinline__ void prim_from_cons(const CoupleParams& C, const double* U, double* Pp) {
+  const double rho = U[0];
+  const double ux = U[1] / rho, uy = U[2] / rho, uz = U[3] / rho;
+  const double er = C.dr > 0 ? U[5] / rho : 0.0;
+  const double E = U[4] / rho;
+  Pp[0] = rho;
+  Pp[1] = ux;
+  Pp[2] = uy;
+  Pp[3] = uz;
+  Pp[4] = (2.0 / 3.0) * (E - 0.5 * (ux * ux + uy * uy + uz * uz) - er);
+  Pp[5] = C.dr > 0 ? 2.0 * er / C.dr : Pp[4];
+}
+
+__global__ void k_cp_init_cons(Params P, CoupleParams C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  double Pp[6], U[6];
+  for (int q = 0; q < 6; ++q) Pp[q] = C.half[(size_t)q * n + c];
+  cons_from_prim(C, Pp, U);
+  for (int q = 0; q < 6; ++q) C.U[(size_t)q * n + c] = U[q];
+}
+
+__global__ void k_cp_prim(Params P, CoupleParams C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n || C.scal->done) return;
+  double U[6], Pp[6];
+  for (int q = 0; q < 6; ++q) U[q] = C.U[(size_t)q * n + c];
+  prim_from_cons(C, U, Pp);
+  for (int q = 0; q < 6; ++q) C.prim[(size_t)q * n + c] = Pp[q];
+}
+
+// total stress and heat fluxes per cell: NSF of the current state + HoT
+__global__ void k_cp_stress(Params P, CoupleParams C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n || C.scal->done) return;
+  double G[15];
+  for (int q = 0; q < 15; ++q) G[q] = C.grad[(size_t)q * n + c];
+  double sig[6], qt[3], qr[3];
+  nsf(C, C.prim[(size_t)4 * n + c], G, sig, qt, qr);
+  for (int q = 0; q < 6; ++q) C.S[(size_t)q * n + c] = sig[q] + C.hot[(size_t)q * n + c];
+  for (int q = 0; q < 3; ++q) {
+    C.S[(size_t)(6 + q) * n + c] = qt[q] + C.hot[(size_t)(6 + q) * n + c];
+    C.S[(size_t)(9 + q) * n + c] = qr[q] + C.hot[(size_t)(9 + q) * n + c];
+  }
+}
+
+__device__ __forceinline__ void inv_flux(const double* Pp, const double* U, const double* N, double* F) {
+  const double un = Pp[1] * N[0] + Pp[2] * N[1] + Pp[3] * N[2];
+  const double p = Pp[0] * Pp[4];
+  F[0] = U[0] * un;
+  F[1] = U[1] * un + p * N[0];
+  F[2] = U[2] * un + p * N[1];
+  F[3] = U[3] * un + p * N[2];
+  F[4] = (U[4] + p) * un;
+  F[5] = U[5] * un;
+}
+
+constexpr int CPT = 256;
+
+// face fluxes, residual and local stable step of every cell; per-block
+// partial (min step, sum of squared residuals)
+__global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (C.scal->done) return;
+  double dmin = 1e300, rs = 0.0;
+  if (c < n) {
+    double Pc[6], Uc[6];
+    for (int q = 0; q < 6; ++q) {
+      Pc[q] = C.prim[(size_t)q * n + c];
+      Uc[q] = C.U[(size_t)q * n + c];
+    }
+    const double L2 = C.L0 * C.L0, L3 = L2 * C.L0;
+    const double V = P.vol[c] / L3;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double lam_sum = 0.0;
+    const double cc = sqrt(C.gam * Pc[4]);
+    const double nu = 2.5 * mu_nd(C, Pc[4]) / Pc[0];
+    const double mflux = C.rho0 * C.c0 * C.c0, eflux = mflux * C.c0;
+    for (int f = 0; f < 4; ++f) {
+      const Plane64 pl = P.plane[4 * (size_t)c + f];
+      const double N[3] = {pl.nx, pl.ny, pl.nz};
+      const double Ad = C.area[4 * (size_t)c + f];
+      const double A = Ad / L2;
+      const int nb = P.nbr[4 * (size_t)c + f];
+      const int kind = nb >= 0 ? -1 : P.bc[P.bf[-1 - nb].bc].kind;
+      double F[6];
+      if (nb >= 0 || kind >= 2) {
+        double Pn[6], Un[6];
+        if (nb >= 0) {
+          for (int q = 0; q < 6; ++q) {
+            Pn[q] = C.prim[(size_t)q * n + nb];
+            Un[q] = C.U[(size_t)q * n + nb];
+          }
+        } else {
+          const int b = P.bf[-1 - nb].bc;
+          if (kind == 3) {
+            for (int q = 0; q < 6; ++q) Pn[q] = Pc[q];
+          } else {
+            Pn[0] = C.bcn[b] * C.mass / C.rho0;
+            Pn[1] = C.bcU[3 * b + 0] / C.c0;
+            Pn[2] = C.bcU[3 * b + 1] / C.c0;
+            Pn[3] = C.bcU[3 * b + 2] / C.c0;
+            Pn[4] = C.bcT[b] / C.T0;
+            Pn[5] = Pn[4];
+          }
+          cons_from_prim(C, Pn, Un);
+        }
+        double FL[6], FR[6];
+        inv_flux(Pc, Uc, N, FL);
+        inv_flux(Pn, Un, N, FR);
+        const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
+        const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
+        const double cl = sqrt(C.gam * Pc[4]), cr = sqrt(C.gam * (Pn[4] > 0 ? Pn[4] : 1e-12));
+        const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
+        for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
+        if (nb >= 0) {
+          double sf[6], qtf[3], qrf[3], uf[3];
+          for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (C.S[(size_t)q * n + c] + C.S[(size_t)q * n + nb]);
+          for (int q = 0; q < 3; ++q) {
+            qtf[q] = 0.5 * (C.S[(size_t)(6 + q) * n + c] + C.S[(size_t)(6 + q) * n + nb]);
+            qrf[q] = 0.5 * (C.S[(size_t)(9 + q) * n + c] + C.S[(size_t)(9 + q) * n + nb]);
+            uf[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
+          }
+          const double sn0 = sf[0] * N[0] + sf[3] * N[1] + sf[4] * N[2];
+          const double sn1 = sf[3] * N[0] + sf[1] * N[1] + sf[5] * N[2];
+          const double sn2 = sf[4] * N[0] + sf[5] * N[1] + sf[2] * N[2];
+          F[1] += sn0;
+          F[2] += sn1;
+          F[3] += sn2;
+          F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + (qtf[0] + qrf[0]) * N[0] + (qtf[1] + qrf[1]) * N[1] +
+                  (qtf[2] + qrf[2]) * N[2];
+          F[5] += qrf[0] * N[0] + qrf[1] * N[1] + qrf[2] * N[2];
+        }
+        lam_sum += A * (lm + 2.0 * nu * A / V);
+      } else {
+        const int ib = -1 - nb;
+        const double* W = P.bflux + 5 * (size_t)ib;
+        F[0] = 0.0;
+        if (C.wall_t > 0.0) {
+          for (int i = 0; i < 3; ++i) F[1 + i] = W[1 + i] / (C.wall_t * Ad) / mflux;
+          F[4] = W[4] / (C.wall_t * Ad) / eflux;
+        } else {
+          const double p = Pc[0] * Pc[4];
+          for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
+          F[4] = 0.0;
+        }
+        F[5] = 0.0;
+        lam_sum += A * (cc + 2.0 * nu * A / V);
+      }
+      for (int q = 0; q < 6; ++q) acc[q] += F[q] * A;
+    }
+    double Rc[6];
+    for (int q = 0; q < 6; ++q) Rc[q] = -acc[q] / V;
+    if (C.dr > 0) {
+      const double T = (3.0 * Pc[4] + C.dr * Pc[5]) / (3.0 + C.dr);
+      const double tau = mu_nd(C, Pc[4]) / (Pc[0] * Pc[4]);
+      Rc[5] += 0.5 * C.dr * Pc[0] * (T - Pc[5]) / (C.Zr * tau);
+    } else {
+      Rc[5] = 0.0;
+    }
+    for (int q = 0; q < 6; ++q) C.R[(size_t)q * n + c] = Rc[q];
+    dmin = 0.5 * V / lam_sum;
+    for (int q = 0; q < 5; ++q) rs += V * Rc[q] * Rc[q];
+  }
+  __shared__ double sm[CPT / 32], ss[CPT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    rs += __shfl_xor_sync(0xffffffffu, rs, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sm[threadIdx.x >> 5] = dmin;
+    ss[threadIdx.x >> 5] = rs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < CPT / 32; ++w) {
+      sm[0] = fmin(sm[0], sm[w]);
+      ss[0] += ss[w];
+    }
+    C.part[2 * blockIdx.x] = sm[0];
+    C.part[2 * blockIdx.x + 1] = ss[0];
+  }
+}
+
+// global step, residual norm and the stopping test (one block)
+__global__ void k_cp_reduce(CoupleParams C, int nblocks, int it, double eps) {
+  if (C.scal->done) return;
+  __shared__ double sm[1024], ss[1024];
+  double dmin = 1e300, rs = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    dmin = fmin(dmin, C.part[2 * b]);
+    rs += C.part[2 * b + 1];
+  }
+  sm[threadIdx.x] = dmin;
+  ss[threadIdx.x] = rs;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + s]);
+      ss[threadIdx.x] += ss[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double res = sqrt(ss[0]);
+    if (it == 0) C.scal->res0 = res > 0 ? res : 1.0;
+    C.scal->res = res;
+    C.scal->iters = it;
+    C.scal->dtg = sm[0];
+    if (!isfinite(res) || res <= eps * C.scal->res0) C.scal->done = 1;
+  }
+}
+
+__global__ void k_cp_update(Params P, CoupleParams C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n || C.scal->done) return;
+  const double dt = C.scal->dtg;
+  for (int q = 0; q < 6; ++q) C.U[(size_t)q * n + c] += dt * C.R[(size_t)q * n + c];
+}
+
+__global__ void k_cp_final(Params P, CoupleParams C, int N_m) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c == 0 && !C.scal->done) C.scal->iters = N_m;
+  if (c >= n) return;
+  double U[6], Pp[6];
+  for (int q = 0; q < 6; ++q) U[q] = C.U[(size_t)q * n + c];
+  prim_from_cons(C, U, Pp);
+  for (int q = 0; q < 6; ++q) C.newst[(size_t)q * n + c] = Pp[q];
+  if (!(Pp[0] > 0.0) || !(Pp[4] > 0.0) || !isfinite(Pp[0]) || !isfinite(Pp[4])) C.scal->bad = 1;
+}
+
+// ---------------------------------------------------------------------------
+// S11 recalibration of the particles of accepted cells
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox_c(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                         uint32_t k1, uint32_t (&w)[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  w[0] = c0;
+  w[1] = c1;
+  w[2] = c2;
+  w[3] = c3;
+}
+
+__device__ __forceinline__ double u01d_c(uint32_t w0, uint32_t w1) {
+  const unsigned long long k = ((unsigned long long)(w0 >> 4) << 24) | (unsigned long long)(w1 >> 8);
+  return ((double)k + 0.5) * 2.220446049250313080847e-16;
+}
+
+struct RecalCell {
+  float ua[3], ub[3], sc, fr;
+  double rn;
+  bool on;
+};
+
+__device__ __forceinline__ RecalCell recal_cell(const CoupleParams& C, int c, int n) {
+  RecalCell r;
+  r.on = C.flag[c] == 1.0;
+  const double b4 = C.own[(size_t)4 * n + c], a4 = C.newst[(size_t)4 * n + c];
+  double rt = a4 / b4;
+  rt = rt < 0.25 ? 0.25 : rt > 4.0 ? 4.0 : rt;
+  double rr = C.dr > 0 ? C.newst[(size_t)5 * n + c] / C.own[(size_t)5 * n + c] : 1.0;
+  rr = rr < 0.25 ? 0.25 : rr > 4.0 ? 4.0 : rr;
+  double rn = C.newst[c] / C.own[c];
+  r.rn = rn < 0.5 ? 0.5 : rn > 2.0 ? 2.0 : rn;
+  r.sc = (float)sqrt(rt);
+  r.fr = (float)rr;
+  for (int i = 0; i < 3; ++i) {
+    r.ua[i] = (float)(C.newst[(size_t)(1 + i) * n + c] * C.c0);
+    r.ub[i] = (float)(C.own[(size_t)(1 + i) * n + c] * C.c0);
+  }
+  return r;
+}
+
+// one warp per cell: rescale velocities and rotational energies in place,
+// decide deletion (mc = -1) or cloning (flag in cl[slot])
+__global__ void k_recal_decide(Params P, CoupleParams C, Buf CUR, int* __restrict__ cl, uint32_t sub) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n = P.n_cells;
+  for (int c = gw; c < n; c += nw) {
+    const int lo = P.cs[c], hi = P.cs[c + 1];
+    const RecalCell r = recal_cell(C, c, n);
+    int stay = 0;
+    for (int p = lo + lane; p < hi; p += 32) {
+      int clone = 0;
+      bool keep = true;
+      if (r.on) {
+        CUR.vx[p] = r.ua[0] + (CUR.vx[p] - r.ub[0]) * r.sc;
+        CUR.vy[p] = r.ua[1] + (CUR.vy[p] - r.ub[1]) * r.sc;
+        CUR.vz[p] = r.ua[2] + (CUR.vz[p] - r.ub[2]) * r.sc;
+        if (C.dr > 0) CUR.Ir[p] = CUR.Ir[p] * r.fr;
+        uint32_t w[4];
+        philox_c((uint32_t)p, sub, 0u, 0u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w);
+        const double R = u01d_c(w[0], w[1]);
+        if (r.rn < 1.0) {
+          if (R < 1.0 - r.rn) keep = false;
+        } else if (r.rn > 1.0 && R < r.rn - 1.0) {
+          clone = 1;
+        }
+      }
+      CUR.mc[p] = keep ? c : -1;
+      cl[p] = clone;
+      stay += keep ? 1 : 0;
+      if (!keep) atomicAdd(C.stats + 3, 1ull);
+    }
+    for (int o = 16; o > 0; o >>= 1) stay += __shfl_xor_sync(0xffffffffu, stay, o);
+    if (lane == 0) {
+      P.nst[c] = stay;
+      P.sbase[c] = lo;
+      P.nold[c] = hi - lo;
+    }
+  }
+}
+
+// exclusive scan of the clone flags over the particles (two kernels)
+constexpr int RS = 1024 * 4;
+__global__ void __launch_bounds__(1024) k_recal_reduce(const int* __restrict__ cl, int N, int* part) {
+  int t = 0;
+  for (int i = blockIdx.x * RS + threadIdx.x; i < min(N, (int)(blockIdx.x + 1) * RS); i += 1024) t += cl[i];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __shared__ int sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0;
+    for (int w = 0; w < 32; ++w) a += sh[w];
+    part[blockIdx.x] = a;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_recal_scan(int* __restrict__ cl, int N, const int* part, int nb,
+                                                     int* total) {
+  __shared__ int sh[32];
+  __shared__ int s_off;
+  int p = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += 1024) p += part[b];
+  for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = p;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0;
+    for (int w = 0; w < 32; ++w) a += sh[w];
+    s_off = a;
+  }
+  __syncthreads();
+  const int i0 = blockIdx.x * RS + threadIdx.x * 4;
+  int v[4], loc = 0;
+  for (int u = 0; u < 4; ++u) {
+    v[u] = i0 + u < N ? cl[i0 + u] : 0;
+    loc += v[u];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = sh[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  int e = s_off + inc - loc + (warp > 0 ? sh[warp - 1] : 0);
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + u;
+    if (i < N) cl[i] = v[u] ? e : -1;
+    e += v[u];
+    if (i == N - 1) *total = e;
+  }
+}
+
+// clones at slots N + (their rank), uniform point in the parent's cell
+__global__ void k_recal_clone(Params P, CoupleParams C, Buf CUR, const int* __restrict__ cl, int N, uint32_t sub) {
+  const int n = P.n_cells;
+  const int total = *C.clone_total;
+  long long hi = (long long)N + total;
+  if (hi > P.cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(P.status, ST_CAPACITY);
+    hi = P.cap;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.state[1] = N;
+    P.state[2] = (int)hi;
+  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int p = P.cs[c]; p < P.cs[c + 1]; ++p) {
+      const int r = cl[p];
+      if (r < 0) continue;
+      const long long q = (long long)N + r;
+      if (q >= hi) continue;
+      uint32_t w[4], w2[4];
+      philox_c((uint32_t)p, sub, 0u, 1u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w);
+      philox_c((uint32_t)p, sub, 0u, 2u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w2);
+      double s = u01d_c(w[0], w[1]), tt = u01d_c(w[2], w[3]), u = u01d_c(w2[0], w2[1]);
+      if (s + tt > 1.0) {
+        s = 1.0 - s;
+        tt = 1.0 - tt;
+      }
+      if (tt + u > 1.0) {
+        const double tmp = u;
+        u = 1.0 - s - tt;
+        tt = 1.0 - tmp;
+      } else if (s + tt + u > 1.0) {
+        const double tmp = u;
+        u = s + tt + u - 1.0;
+        s = 1.0 - tt - tmp;
+      }
+      const int* tv = P.tets + 4 * (size_t)c;
+      const double* A = P.nodes + 3 * (size_t)tv[0];
+      const double* B = P.nodes + 3 * (size_t)tv[1];
+      const double* Cc = P.nodes + 3 * (size_t)tv[2];
+      const double* D = P.nodes + 3 * (size_t)tv[3];
+      CUR.x[q] = A[0] + s * (B[0] - A[0]) + tt * (Cc[0] - A[0]) + u * (D[0] - A[0]);
+      CUR.y[q] = A[1] + s * (B[1] - A[1]) + tt * (Cc[1] - A[1]) + u * (D[1] - A[1]);
+      CUR.z[q] = A[2] + s * (B[2] - A[2]) + tt * (Cc[2] - A[2]) + u * (D[2] - A[2]);
+      CUR.vx[q] = CUR.vx[p];
+      CUR.vy[q] = CUR.vy[p];
+      CUR.vz[q] = CUR.vz[p];
+      if (C.dr > 0) CUR.Ir[q] = CUR.Ir[p];
+      CUR.mc[q] = c;
+      atomicAdd(P.na + c, 1);
+      atomicAdd(C.stats + 2, 1ull);
+    }
+  }
+}
+
+int nb_for(int n, int t) { return (n + t - 1) / t; }
+}  // namespace
+
+void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, cudaStream_t s) {
+  const int n = P.n_cells, nb = nb_for(n, CPT);
+  k_cp_extract<<<nb, CPT, 0, s>>>(P, C);
+  k_cp_grad<<<nb, CPT, 0, s>>>(P, C, C.own, C.grad);
+  k_cp_hot<<<nb, CPT, 0, s>>>(P, C);
+  int* a = C.avail;
+  int* b = C.avail2;
+  for (int q = 0; q < passes; ++q) {
+    k_cp_recon<<<nb, CPT, 0, s>>>(P, C, a, b);
+    int* t = a;
+    a = b;
+    b = t;
+  }
+  g_launches += 3 + passes;
+}
+
+void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double eps, cudaStream_t s) {
+  const int n = P.n_cells, nb = nb_for(n, CPT);
+  k_cp_init_cons<<<nb, CPT, 0, s>>>(P, C);
+  for (int it = 0; it < N_m; ++it) {
+    k_cp_prim<<<nb, CPT, 0, s>>>(P, C);
+    k_cp_grad<<<nb, CPT, 0, s>>>(P, C, C.prim, C.grad);
+    k_cp_stress<<<nb, CPT, 0, s>>>(P, C);
+    k_cp_flux<<<nb, CPT, 0, s>>>(P, C);
+    k_cp_reduce<<<1, 1024, 0, s>>>(C, nb, it, eps);
+    k_cp_update<<<nb, CPT, 0, s>>>(P, C);
+  }
+  k_cp_final<<<nb, CPT, 0, s>>>(P, C, N_m);
+  g_launches += 2 + 6LL * N_m;
+}
+
+void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, int N, uint32_t sub, int* cl,
+                       cudaStream_t s) {
+  const int n = P.n_cells;
+  k_recal_decide<<<nb_for(n * 32, 256), 256, 0, s>>>(P, C, cur, cl, sub);
+  const int nbr = (N + RS - 1) / RS;
+  if (N > 0) {
+    k_recal_reduce<<<nbr, 1024, 0, s>>>(cl, N, C.rpart);
+    k_recal_scan<<<nbr, 1024, 0, s>>>(cl, N, C.rpart, nbr, C.clone_total);
+  }
+  k_recal_clone<<<nb_for(n, 256), 256, 0, s>>>(P, C, cur, cl, N, sub);
+  g_launches += N > 0 ? 4 : 2;
+}
+
+size_t couple_part_count(int n_cells) { return 2 * (size_t)nb_for(n_cells, CPT) + 2; }
+
+}  // namespace dig

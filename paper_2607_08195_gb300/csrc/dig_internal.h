@@ -111,6 +111,32 @@ struct Params {
   long long cap;
 };
 
+// DIG coupling state (dig_couple.cu); arrays are [component][cell]
+struct CoupleScalars {
+  double res0, res, dtg;
+  int iters, done, bad, pad;
+};
+
+struct CoupleParams {
+  double L0, T0, rho0, c0, Kn, omega, gam, dr, Zr, mass, FN, kB, KnD_max, wall_t;
+  const double* area;  // [4n] face areas
+  const double* bcU;   // [3 n_bcs]
+  const double* bcT;   // [n_bcs]
+  const double* bcn;   // [n_bcs]
+  double *own, *sd, *grad, *half, *hot, *newst, *flag, *nbar, *U, *prim, *S, *R, *part;
+  int *avail, *avail2;
+  unsigned long long* stats;  // rejected, reconstructed, cloned, deleted
+  CoupleScalars* scal;
+  int* rpart;
+  int* clone_total;
+};
+
+void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, cudaStream_t s);
+void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double eps, cudaStream_t s);
+void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, int N, uint32_t sub, int* cl,
+                       cudaStream_t s);
+size_t couple_part_count(int n_cells);
+
 // launchers (dig_kernels.cu)
 void launch_init(const Params& P, const Buf& out, int n, cudaStream_t s);
 void launch_write(const Params& P, const Buf& out, const double* xs, const float* vs, const float* Is,

@@ -702,7 +702,10 @@ __global__ void __launch_bounds__(CP_THREADS, DIG_CP_RESIDENT / CP_THREADS) k_ce
     const int g1 = s_g1;
     const int gbase = s_cs[g0];
     const int gN = s_cs[g1] - gbase;
-    if (gN > CAP) {  // one cell holds more particles than the stage
+    if (gN > CAP) {
+      // one cell holds more particles than the stage: reported as an error;
+      // its slots are marked removed so that the buffer stays consistent
+      for (int k = threadIdx.x; k < gN; k += CP_THREADS) OUT.mc[gbase + k] = -1;
       if (threadIdx.x == 0) atomicOr(P.status, ST_CELL_OVER_STAGE);
       g0 = g1;
       __syncthreads();
@@ -1197,7 +1200,7 @@ __global__ void k_scatter(Params P, const int* __restrict__ mc) {
     const int lo = P.sbase[c], hi = lo + P.nold[c];
     for (int q = lo + lane; q < hi; q += 32) {
       const int d = mc[q];
-      if (d != c && d >= 0) {
+      if (d != c && d >= 0 && d < P.n_cells) {
         const int pos = P.as[d] + atomicAdd(P.fill + d, 1);
         P.aq[pos] = q;
       }
@@ -1206,7 +1209,7 @@ __global__ void k_scatter(Params P, const int* __restrict__ mc) {
   const int lo = P.state[1], hi = P.state[2];
   for (int q = lo + blockIdx.x * blockDim.x + threadIdx.x; q < hi; q += gridDim.x * blockDim.x) {
     const int d = mc[q];
-    if (d >= 0) {
+    if (d >= 0 && d < P.n_cells) {
       const int pos = P.as[d] + atomicAdd(P.fill + d, 1);
       P.aq[pos] = q;
     }

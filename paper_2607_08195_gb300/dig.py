@@ -43,6 +43,14 @@ class DigConfig(C.Structure):
     ]
 
 
+class CoupleReport(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("pad", C.c_int32), ("residual", C.c_double), ("n_rejected", C.c_int64),
+                ("n_reconstructed", C.c_int64), ("n_cloned", C.c_int64), ("n_deleted", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 class DigBC(C.Structure):
     _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("T", C.c_double), ("U", C.c_double * 3),
                 ("n", C.c_double)]
@@ -53,7 +61,8 @@ EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mes
            "dig_bind_arena", "particles_init", "write_particles", "read_particles", "dsmc_step", "sample",
            "read_moments", "read_pairs", "read_counters", "dig_cell_state", "dig_wall_flux",
            "dig_particle_count", "dig_synchronize", "dig_launch_count", "dig_kernel_time",
-           "dig_sort_scratch_bytes", "dig_sort_by_cell", "dig_sort_by_cell_noalloc"]
+           "dig_sort_scratch_bytes", "dig_sort_by_cell", "dig_sort_by_cell_noalloc", "dig_couple",
+           "dig_read_couple", "dig_write_moments", "dig_write_wall_flux"]
 
 _lib = None
 
@@ -78,6 +87,8 @@ def load_library(path: str = LIB_PATH):
         "dig_synchronize": [P], "dig_launch_count": [P, P], "dig_kernel_time": [P, P, P],
         "dig_sort_scratch_bytes": [I64, I32, P], "dig_sort_by_cell": [P, I64, I32, P, P, P, I64, P],
         "dig_sort_by_cell_noalloc": [P, I64, I32, P, P, P],
+        "dig_couple": [P, P], "dig_read_couple": [P, I32, P, I64], "dig_write_moments": [P, I32, P],
+        "dig_write_wall_flux": [P, P, I64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -244,6 +255,26 @@ class Solver:
         out = np.zeros((n.value, 5), np.float64)
         self._check(self.L.dig_wall_flux(self.h, _p(out), out.size, C.byref(n)))
         return out
+
+    def couple(self):
+        r = CoupleReport()
+        self._check(self.L.dig_couple(self.h, C.byref(r)))
+        return r.as_dict()
+
+    def read_couple(self, which):
+        k = {0: 6, 1: 12, 2: 6, 3: 1, 4: 6}[which]
+        out = np.zeros((self.n_tets, k), np.float64)
+        self._check(self.L.dig_read_couple(self.h, which, _p(out), out.size))
+        return out
+
+    def write_moments(self, which, phi):
+        phi = np.ascontiguousarray(phi, np.float64)
+        assert phi.shape == (self.n_tets, NPHI)
+        self._check(self.L.dig_write_moments(self.h, which, _p(phi)))
+
+    def write_wall_flux(self, flux, steps):
+        flux = np.ascontiguousarray(flux, np.float64)
+        self._check(self.L.dig_write_wall_flux(self.h, _p(flux), steps))
 
     def kernel_time(self):
         ms, n = C.c_double(0), C.c_int64(0)

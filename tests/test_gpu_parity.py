@@ -244,3 +244,76 @@ def test_injection_bit_exact(gas, U, sides):
     for k in ("injected", "removed", "cand", "coll", "cross", "lb"):
         assert cg[k] == co[k], (k, cg[k], co[k])
     assert cg["injected"] > 0 and cg["removed"] > 0
+
+
+def seeded_dig_state(scen, steps=60, **over):
+    """Oracle state after `steps` DSMC steps (moving average, wall fluxes on);
+    returns the oracle and its particles, sums and wall fluxes."""
+    o = orc.Oracle(scen, **over)
+    o.init()
+    o.step(steps, orc.EWMA)
+    return o, o.read(), o.moments(orc.PHI_EWMA), o.wall_flux()
+
+
+@pytest.mark.parametrize("nh,kn,passes,kmax", [(4, 0.1, 3, 1.0), (5, 0.05, 2, 0.4)])
+def test_couple_parity_from_written_state(nh, kn, passes, kmax):
+    """S9-S11 from an identical written state (particles, moving-average sums,
+    wall fluxes): identical filter flags, rejection/reconstruction counts,
+    clone/delete decisions and particle cells; FP64 fields within 1e-9."""
+    s = W.cavity_scenario(nh, 30 * 6 * nh ** 3, kn, seed=17)
+    over = dict(N_m=60, passes=passes, KnD_max=kmax)
+    o, (x, v, Ir, cell), phi, wf = seeded_dig_state(s, **over)
+    g = dig.Solver(s, "cuda:0", **over)
+    g.write(x, v, Ir, cell)
+    g.write_moments(dig.PHI_EWMA, phi)
+    g.write_wall_flux(wf, 60)
+    rg = g.couple()
+    ro = o.couple()
+    for k in ("iters", "n_rejected", "n_reconstructed", "n_cloned", "n_deleted"):
+        assert rg[k] == ro[k], (k, rg[k], ro[k])
+    assert ro["n_rejected"] > 0 and ro["n_cloned"] + ro["n_deleted"] > 0
+    assert np.array_equal(g.read_couple(3), o.read_couple(3))
+    for which in (4, 0, 1, 2):
+        a, b = g.read_couple(which), o.read_couple(which)
+        scale = np.abs(b).max(axis=0) + 1e-30
+        assert np.all(np.abs(a - b) <= 1e-9 * scale), (which, np.abs(a - b).max())
+    xg, vg, Ig, cg = g.read()
+    xo, vo, Io, co = o.read()
+    assert np.array_equal(cg, co)
+    assert np.array_equal(xg, xo)
+    assert np.allclose(vg, vo, rtol=1e-6, atol=1e-4)
+
+
+def test_couple_fixed_point_identity_on_gpu():
+    """Uniform equilibrium with the exact wall pressure: the GPU coupling leaves
+    the state and every particle unchanged (no clones or deletions)."""
+    s = W.Scenario(gas=W.ARGON, mesh=W.closed_box(2, 1e-3, W.BC_DIFFUSE), n_particles=4000, n_init=1.677e22,
+                   T_init=273.0, u_init=(0.0, 0.0, 0.0), F_N=1.677e22 * 1e-9 / 4000, dt=6.7e-8, seed=5, L=1e-3,
+                   Kn=0.1, capacity=8000)
+    g = dig.Solver(s, "cuda:0", N_m=40, KnD_max=1e9)
+    g.init()
+    x0, v0, I0, c0 = g.read()
+    vol = orc.Oracle(s).mesh_info()["vol"]
+    kT_m = W.K_B * s.T_init / s.gas.mass
+    N = s.n_init * vol / s.F_N
+    phi = np.zeros((len(vol), dig.NPHI))
+    phi[:, 0] = N
+    phi[:, 4:7] = (N * kT_m)[:, None]
+    g.write_moments(dig.PHI_EWMA, phi)
+    # exact pressure on every wall face
+    mi = orc.Oracle(s).mesh_info()
+    P = s.mesh.nodes[s.mesh.tets]
+    rows = []
+    p = s.n_init * W.K_B * s.T_init
+    for t in range(len(vol)):
+        for f in range(4):
+            if mi["nbr"][t, f] < 0:
+                q = [k for k in range(4) if k != f]
+                A = 0.5 * np.linalg.norm(np.cross(P[t, q[1]] - P[t, q[0]], P[t, q[2]] - P[t, q[0]]))
+                rows.append([1.0, *(p * mi["normals"][t, f] * A * 10 * s.dt), 0.0])
+    g.write_wall_flux(np.array(rows), 10)
+    r = g.couple()
+    assert r["n_cloned"] == 0 and r["n_deleted"] == 0 and r["n_rejected"] == 0
+    assert np.allclose(g.read_couple(2), g.read_couple(0), rtol=0, atol=1e-10)
+    x1, v1, I1, c1 = g.read()
+    assert np.array_equal(v0, v1) and np.array_equal(x0, x1) and np.array_equal(c0, c1)
