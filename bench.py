@@ -2,10 +2,12 @@
 
 Workload: the argon lid-driven cavity refined to 30x30x30 hexahedra (162,000
 Kuhn tets) at Kn = 0.01 with 8,000,000 particles, Maxwellian initial state,
-seed 2.  One bench step is one coupling window: N_s = 200 DSMC time steps
-(move with diffuse walls, sort by cell, NTC collisions, sampling, moving
-average).  The particle state (2 x 320 MB) is far larger than L2, so no L2
-flush is needed between steps.
+seed 2.  One bench step is one outer DIG cycle (paper Alg. 1): N_s = 200 DSMC
+time steps (move with diffuse walls, sort by cell, NTC collisions, sampling,
+moving average, wall-flux sampling) followed by one coupling (HoT extraction
+and filter, synthetic-equation solve, particle recalibration).  The particle
+state (2 x 352 MB) is far larger than L2, so no L2 flush is needed between
+steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -195,6 +197,7 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-couple", action="store_true", help="DSMC steps only (no DIG coupling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -212,10 +215,17 @@ def main():
     g = dig.Solver(scen, str(device))
     g.init()
     g.synchronize()
-    flags = dig.EWMA
+    flags = dig.EWMA | dig.WALLFLUX
+    reports = []
+
+    def cycle(timing=0):
+        g.step(N_S, flags | timing)
+        if not args.no_couple:
+            reports.append(g.couple())
+
     # warm-up steps (untimed)
     for _ in range(args.warmup):
-        g.step(N_S, flags)
+        cycle()
     g.synchronize()
     stream = g.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -226,7 +236,7 @@ def main():
         torch.cuda.synchronize(device)
         e0.record(stream)
         for _ in range(args.steps):
-            g.step(N_S, flags | dig.TIMING)
+            cycle(dig.TIMING)
         e1.record(stream)
         torch.cuda.synchronize(device)
         barrier(pg, device)
@@ -265,13 +275,13 @@ def main():
         h2d = xn.nbytes + vn.nbytes + cn.nbytes
         d2h = on.nbytes
         g.write(xn, vn, None, cn)
-        g.step(N_S, flags)
+        cycle()
         g.moments(dig.PHI_EWMA, on)
         barrier(pg, device)
         t0 = time.perf_counter()
         for _ in range(args.steps):
             g.write(xn, vn, None, cn)
-            g.step(N_S, flags)
+            cycle()
             g.moments(dig.PHI_EWMA, on)
         t1 = time.perf_counter()
         barrier(pg, device)
@@ -292,10 +302,12 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32",
             "data": "synthetic",
             "config": {"workload": scen.name, "particles": scen.n_particles, "tets": len(scen.mesh.tets),
-                       "dsmc_steps_per_step": N_S, "coupling": "none", "parallelism": f"replicas{world}",
+                       "dsmc_steps_per_step": N_S, "parallelism": f"replicas{world}",
+                       "coupling": "none" if args.no_couple else f"DIG every {N_S} steps, N_m={g.cfg.N_m}",
                        "l2": "inputs larger than L2 (2 x 320 MB particle buffers)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
+            "couple_last": reports[-1] if reports else None,
         }
         print(json.dumps(line), flush=True)
     g.close()

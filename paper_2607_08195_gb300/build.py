@@ -23,7 +23,7 @@ UNITS = [
     ("dig_kernels.cu", ["-fmad=false"]),
     ("dig_api.cu", ["-fmad=false"]),
     ("dig_sort.cu", []),
-    ("dig_couple.cu", ["-fmad=false"]),
+    ("dig_couple.cu", []),
     ("dig_noalloc.cu", []),
 ]
 

@@ -466,6 +466,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
   C.prim = A.take<double>(6 * n);
   C.S = A.take<double>(12 * n);
   C.R = A.take<double>(6 * n);
+  C.mu = A.take<double>(n);
   C.part = A.take<double>(couple_part_count((int)n));
   C.avail = A.take<int>(n);
   C.avail2 = A.take<int>(n);

@@ -2,7 +2,8 @@
 // Alg. 1): S9 HoT extraction with the cell-Knudsen reliability filter and
 // layered neighbour reconstruction, S10 the steady synthetic equations, S11
 // particle recalibration.  FP64 throughout, one thread per cell (the work is
-// per cell and small next to the particle loop); compiled with -fmad=false.
+// per cell and small next to the particle loop).  Multiply-adds may be fused
+// here: the fields are compared with the oracle within FP64 tolerances.
 //
 // Nondimensional variables (Sec. 2.2): lengths / L0, density / (m n0),
 // temperature / T0, velocity / sqrt(R T0); p = rho T_t; mu = Kn sqrt(2/pi)
@@ -114,8 +115,7 @@ __global__ void k_cp_grad(Params P, CoupleParams C, const double* __restrict__ p
   for (int q = 0; q < 15; ++q) grad[(size_t)q * n + c] = g[q] / V;
 }
 
-__device__ void nsf(const CoupleParams& C, double Tt, const double* G, double* sig, double* qt, double* qr) {
-  const double mu = mu_nd(C, Tt);
+__device__ void nsf_mu(const CoupleParams& C, double mu, const double* G, double* sig, double* qt, double* qr) {
   const double div = G[0] + G[4] + G[8];
   sig[0] = -mu * (2.0 * G[0] - 2.0 / 3.0 * div);
   sig[1] = -mu * (2.0 * G[4] - 2.0 / 3.0 * div);
@@ -128,6 +128,10 @@ __device__ void nsf(const CoupleParams& C, double Tt, const double* G, double* s
     qt[i] = -kt * G[9 + i];
     qr[i] = C.dr > 0 ? -kr * G[12 + i] : 0.0;
   }
+}
+
+__device__ void nsf(const CoupleParams& C, double Tt, const double* G, double* sig, double* qt, double* qr) {
+  nsf_mu(C, mu_nd(C, Tt), G, sig, qt, qr);
 }
 
 // HoT = sampled - NSF; cell Knudsen criterion (Eq. criterion); half = own
@@ -224,14 +228,24 @@ __global__ void k_cp_init_cons(Params P, CoupleParams C) {
   for (int q = 0; q < 6; ++q) C.U[(size_t)q * n + c] = U[q];
 }
 
-__global__ void k_cp_prim(Params P, CoupleParams C) {
+// U += dt R of the previous iteration (unless it stopped), then the
+// primitives and the viscosity of the new state
+__global__ void k_cp_prim(Params P, CoupleParams C, int apply) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
   if (c >= n || C.scal->done) return;
   double U[6], Pp[6];
-  for (int q = 0; q < 6; ++q) U[q] = C.U[(size_t)q * n + c];
+  const double dt = C.scal->dtg;
+  for (int q = 0; q < 6; ++q) {
+    U[q] = C.U[(size_t)q * n + c];
+    if (apply) {
+      U[q] += dt * C.R[(size_t)q * n + c];
+      C.U[(size_t)q * n + c] = U[q];
+    }
+  }
   prim_from_cons(C, U, Pp);
   for (int q = 0; q < 6; ++q) C.prim[(size_t)q * n + c] = Pp[q];
+  C.mu[c] = mu_nd(C, Pp[4]);
 }
 
 // total stress and heat fluxes per cell: NSF of the current state + HoT
@@ -242,7 +256,7 @@ __global__ void k_cp_stress(Params P, CoupleParams C) {
   double G[15];
   for (int q = 0; q < 15; ++q) G[q] = C.grad[(size_t)q * n + c];
   double sig[6], qt[3], qr[3];
-  nsf(C, C.prim[(size_t)4 * n + c], G, sig, qt, qr);
+  nsf_mu(C, C.mu[c], G, sig, qt, qr);
   for (int q = 0; q < 6; ++q) C.S[(size_t)q * n + c] = sig[q] + C.hot[(size_t)q * n + c];
   for (int q = 0; q < 3; ++q) {
     C.S[(size_t)(6 + q) * n + c] = qt[q] + C.hot[(size_t)(6 + q) * n + c];
@@ -281,7 +295,8 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
     double acc[6] = {0, 0, 0, 0, 0, 0};
     double lam_sum = 0.0;
     const double cc = sqrt(C.gam * Pc[4]);
-    const double nu = 2.5 * mu_nd(C, Pc[4]) / Pc[0];
+    const double muc = C.mu[c];
+    const double nu = 2.5 * muc / Pc[0];
     const double mflux = C.rho0 * C.c0 * C.c0, eflux = mflux * C.c0;
     for (int f = 0; f < 4; ++f) {
       const Plane64 pl = P.plane[4 * (size_t)c + f];
@@ -360,7 +375,7 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
     for (int q = 0; q < 6; ++q) Rc[q] = -acc[q] / V;
     if (C.dr > 0) {
       const double T = (3.0 * Pc[4] + C.dr * Pc[5]) / (3.0 + C.dr);
-      const double tau = mu_nd(C, Pc[4]) / (Pc[0] * Pc[4]);
+      const double tau = muc / (Pc[0] * Pc[4]);
       Rc[5] += 0.5 * C.dr * Pc[0] * (T - Pc[5]) / (C.Zr * tau);
     } else {
       Rc[5] = 0.0;
@@ -507,10 +522,11 @@ __global__ void k_recal_decide(Params P, CoupleParams C, Buf CUR, int* __restric
       int clone = 0;
       bool keep = true;
       if (r.on) {
-        CUR.vx[p] = r.ua[0] + (CUR.vx[p] - r.ub[0]) * r.sc;
-        CUR.vy[p] = r.ua[1] + (CUR.vy[p] - r.ub[1]) * r.sc;
-        CUR.vz[p] = r.ua[2] + (CUR.vz[p] - r.ub[2]) * r.sc;
-        if (C.dr > 0) CUR.Ir[p] = CUR.Ir[p] * r.fr;
+        // v' = u_a + (v - u_b) sc, evaluated as written (no fused multiply-add)
+        CUR.vx[p] = __fadd_rn(r.ua[0], __fmul_rn(__fsub_rn(CUR.vx[p], r.ub[0]), r.sc));
+        CUR.vy[p] = __fadd_rn(r.ua[1], __fmul_rn(__fsub_rn(CUR.vy[p], r.ub[1]), r.sc));
+        CUR.vz[p] = __fadd_rn(r.ua[2], __fmul_rn(__fsub_rn(CUR.vz[p], r.ub[2]), r.sc));
+        if (C.dr > 0) CUR.Ir[p] = __fmul_rn(CUR.Ir[p], r.fr);
         uint32_t w[4];
         philox_c((uint32_t)p, sub, 0u, 0u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w);
         const double R = u01d_c(w[0], w[1]);
@@ -639,9 +655,15 @@ __global__ void k_recal_clone(Params P, CoupleParams C, Buf CUR, const int* __re
       const double* B = P.nodes + 3 * (size_t)tv[1];
       const double* Cc = P.nodes + 3 * (size_t)tv[2];
       const double* D = P.nodes + 3 * (size_t)tv[3];
-      CUR.x[q] = A[0] + s * (B[0] - A[0]) + tt * (Cc[0] - A[0]) + u * (D[0] - A[0]);
-      CUR.y[q] = A[1] + s * (B[1] - A[1]) + tt * (Cc[1] - A[1]) + u * (D[1] - A[1]);
-      CUR.z[q] = A[2] + s * (B[2] - A[2]) + tt * (Cc[2] - A[2]) + u * (D[2] - A[2]);
+      // uniform point in the tet, evaluated as written (no fused multiply-add)
+      double xs[3];
+      for (int i = 0; i < 3; ++i)
+        xs[i] = __dadd_rn(__dadd_rn(__dadd_rn(A[i], __dmul_rn(s, __dsub_rn(B[i], A[i]))),
+                                    __dmul_rn(tt, __dsub_rn(Cc[i], A[i]))),
+                          __dmul_rn(u, __dsub_rn(D[i], A[i])));
+      CUR.x[q] = xs[0];
+      CUR.y[q] = xs[1];
+      CUR.z[q] = xs[2];
       CUR.vx[q] = CUR.vx[p];
       CUR.vy[q] = CUR.vy[p];
       CUR.vz[q] = CUR.vz[p];
@@ -676,15 +698,15 @@ void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double e
   const int n = P.n_cells, nb = nb_for(n, CPT);
   k_cp_init_cons<<<nb, CPT, 0, s>>>(P, C);
   for (int it = 0; it < N_m; ++it) {
-    k_cp_prim<<<nb, CPT, 0, s>>>(P, C);
+    k_cp_prim<<<nb, CPT, 0, s>>>(P, C, it > 0);
     k_cp_grad<<<nb, CPT, 0, s>>>(P, C, C.prim, C.grad);
     k_cp_stress<<<nb, CPT, 0, s>>>(P, C);
     k_cp_flux<<<nb, CPT, 0, s>>>(P, C);
     k_cp_reduce<<<1, 1024, 0, s>>>(C, nb, it, eps);
-    k_cp_update<<<nb, CPT, 0, s>>>(P, C);
   }
+  if (N_m > 0) k_cp_update<<<nb, CPT, 0, s>>>(P, C);
   k_cp_final<<<nb, CPT, 0, s>>>(P, C, N_m);
-  g_launches += 2 + 6LL * N_m;
+  g_launches += 3 + 5LL * N_m;
 }
 
 void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, int N, uint32_t sub, int* cl,

@@ -123,7 +123,7 @@ struct CoupleParams {
   const double* bcU;   // [3 n_bcs]
   const double* bcT;   // [n_bcs]
   const double* bcn;   // [n_bcs]
-  double *own, *sd, *grad, *half, *hot, *newst, *flag, *nbar, *U, *prim, *S, *R, *part;
+  double *own, *sd, *grad, *half, *hot, *newst, *flag, *nbar, *U, *prim, *S, *R, *part, *mu;
   int *avail, *avail2;
   unsigned long long* stats;  // rejected, reconstructed, cloned, deleted
   CoupleScalars* scal;
