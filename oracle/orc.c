@@ -1629,3 +1629,158 @@ int orc_write_wall_flux(orc_ctx* c, const double* in, int64_t steps) {
   c->flux_steps = steps;
   return 0;
 }
+
+/* ========================================================================= */
+/* S12/S13: learned per-cell closure (not in the paper): an MLP             */
+/* 13 -> 64 -> 64 -> 64 -> 8 with GELU, BF16 weights and activations,       */
+/* accumulation in FP64 here (the reference of the FP32-accumulating        */
+/* kernels).  Parameters, FP32 master copy, layout [out][in] per layer:     */
+/* W1[64][13] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[8][64] b4[8].   */
+/* ========================================================================= */
+#define MLP_NIN 13
+#define MLP_NH 64
+#define MLP_NOUT 8
+#define MLP_NPARAM (MLP_NH * MLP_NIN + MLP_NH + 2 * (MLP_NH * MLP_NH + MLP_NH) + MLP_NOUT * MLP_NH + MLP_NOUT)
+
+int32_t orc_mlp_nparam(void) { return MLP_NPARAM; }
+
+/* FP32 -> BF16 -> FP32, round to nearest even */
+double orc_bf16(double x) {
+  float f = (float)x;
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  if ((b & 0x7f800000u) == 0x7f800000u) return f; /* inf / nan unchanged */
+  b = (b + 0x7fffu + ((b >> 16) & 1u)) & 0xffff0000u;
+  memcpy(&f, &b, 4);
+  return f;
+}
+
+static double gelu(double z) { return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }
+static double gelu_d(double z) { return 0.5 * (1.0 + erf(z / sqrt(2.0))) + z * exp(-0.5 * z * z) / sqrt(2.0 * M_PI); }
+
+typedef struct {
+  const float *W[4], *b[4];
+  int nin[4], nout[4];
+} mlp_view;
+
+static mlp_view mlp_layout(const float* p) {
+  mlp_view v;
+  const int ni[4] = {MLP_NIN, MLP_NH, MLP_NH, MLP_NH}, no[4] = {MLP_NH, MLP_NH, MLP_NH, MLP_NOUT};
+  const float* q = p;
+  for (int l = 0; l < 4; ++l) {
+    v.W[l] = q;
+    q += ni[l] * no[l];
+    v.b[l] = q;
+    q += no[l];
+    v.nin[l] = ni[l];
+    v.nout[l] = no[l];
+  }
+  return v;
+}
+
+/* forward of one row; a[l] are the layer inputs (BF16-rounded when bf16 != 0),
+ * z[l] the pre-activations; returns outputs y[8] */
+static void mlp_row(const mlp_view* v, const float* x, int bf16, double a[4][MLP_NH], double z[4][MLP_NH], double* y) {
+  for (int k = 0; k < MLP_NIN; ++k) a[0][k] = bf16 ? orc_bf16(x[k]) : x[k];
+  for (int l = 0; l < 4; ++l) {
+    for (int j = 0; j < v->nout[l]; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < v->nin[l]; ++k) {
+        double w = v->W[l][j * v->nin[l] + k];
+        if (bf16) w = orc_bf16(w);
+        s += w * a[l][k];
+      }
+      s += v->b[l][j];
+      z[l][j] = s;
+      if (l < 3) a[l + 1][j] = bf16 ? orc_bf16(gelu(s)) : gelu(s);
+      else y[j] = s;
+    }
+  }
+}
+
+int orc_mlp_forward(const float* params, const float* X, int64_t n, int32_t bf16, double* Y) {
+  mlp_view v = mlp_layout(params);
+  double a[4][MLP_NH], z[4][MLP_NH];
+  for (int64_t r = 0; r < n; ++r) mlp_row(&v, X + MLP_NIN * r, bf16, a, z, Y + MLP_NOUT * r);
+  return 0;
+}
+
+/* mean-square loss L = 1/(8n) sum (y - t)^2 and its gradient with respect to
+ * every parameter (backpropagation through the same computation; the BF16
+ * roundings are passed straight through) */
+double orc_mlp_grad(const float* params, const float* X, const float* T, int64_t n, int32_t bf16, double* grad) {
+  mlp_view v = mlp_layout(params);
+  memset(grad, 0, sizeof(double) * MLP_NPARAM);
+  double* gW[4];
+  double* gb[4];
+  {
+    double* q = grad;
+    for (int l = 0; l < 4; ++l) {
+      gW[l] = q;
+      q += v.nin[l] * v.nout[l];
+      gb[l] = q;
+      q += v.nout[l];
+    }
+  }
+  double loss = 0.0;
+  double a[4][MLP_NH], z[4][MLP_NH], y[MLP_NOUT], d[MLP_NH], dn[MLP_NH];
+  for (int64_t r = 0; r < n; ++r) {
+    mlp_row(&v, X + MLP_NIN * r, bf16, a, z, y);
+    for (int j = 0; j < MLP_NOUT; ++j) {
+      const double e = y[j] - T[MLP_NOUT * r + j];
+      loss += e * e;
+      d[j] = 2.0 * e / (double)(MLP_NOUT * n);
+    }
+    for (int l = 3; l >= 0; --l) {
+      for (int j = 0; j < v.nout[l]; ++j) {
+        gb[l][j] += d[j];
+        for (int k = 0; k < v.nin[l]; ++k) gW[l][j * v.nin[l] + k] += d[j] * a[l][k];
+      }
+      if (l == 0) break;
+      for (int k = 0; k < v.nin[l]; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < v.nout[l]; ++j) {
+          double w = v.W[l][j * v.nin[l] + k];
+          if (bf16) w = orc_bf16(w);
+          s += w * d[j];
+        }
+        dn[k] = s * gelu_d(z[l - 1][k]);
+      }
+      memcpy(d, dn, sizeof(double) * v.nin[l]);
+    }
+  }
+  return loss / (double)(MLP_NOUT * n);
+}
+
+/* Adam (Kingma and Ba 2015) on the FP32 master parameters, step t >= 1 */
+void orc_adam(float* params, double* m, double* vv, const double* g, int64_t t, double lr, double b1, double b2,
+              double eps) {
+  const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+  for (int i = 0; i < MLP_NPARAM; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    vv[i] = b2 * vv[i] + (1.0 - b2) * g[i] * g[i];
+    params[i] = (float)(params[i] - lr * (m[i] / c1) / (sqrt(vv[i] / c2) + eps));
+  }
+}
+
+/* He-normal initialisation from the MLP_INIT random stream (Box-Muller free:
+ * polar Gaussian pairs), biases zero */
+void orc_mlp_init(float* params, uint64_t seed) {
+  orc_ctx tmp;
+  memset(&tmp, 0, sizeof tmp);
+  tmp.cfg.seed = seed;
+  mlp_view v = mlp_layout(params);
+  int idx = 0;
+  for (int l = 0; l < 4; ++l) {
+    const float sd = (float)sqrt(2.0 / v.nin[l]);
+    float* W = (float*)v.W[l];
+    float* b = (float*)v.b[l];
+    for (int i = 0; i < v.nin[l] * v.nout[l]; i += 2, idx += 2) {
+      float g1, g2;
+      gauss2(&tmp, 9, (uint32_t)idx, 0, 0, 0, &g1, &g2);
+      W[i] = sd * g1;
+      if (i + 1 < v.nin[l] * v.nout[l]) W[i + 1] = sd * g2;
+    }
+    for (int j = 0; j < v.nout[l]; ++j) b[j] = 0.0f;
+  }
+}

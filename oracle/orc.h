@@ -107,6 +107,15 @@ int orc_read_couple(orc_ctx* c, int32_t which, double* out, int64_t cap);
 int orc_write_moments(orc_ctx* c, int32_t which, const double* in);
 int orc_write_wall_flux(orc_ctx* c, const double* in, int64_t steps);
 
+/* learned closure (S12/S13): MLP 13 -> 64 -> 64 -> 64 -> 8, GELU */
+int32_t orc_mlp_nparam(void);
+double orc_bf16(double x);
+void orc_mlp_init(float* params, uint64_t seed);
+int orc_mlp_forward(const float* params, const float* X, int64_t n, int32_t bf16, double* Y);
+double orc_mlp_grad(const float* params, const float* X, const float* T, int64_t n, int32_t bf16, double* grad);
+void orc_adam(float* params, double* m, double* v, const double* g, int64_t t, double lr, double b1, double b2,
+              double eps);
+
 /* stable counting sort by cell (the paper's per-cell particle buckets):
  * cell[n] in [0, n_cells) or -1 (dropped); writes cell_start[n_cells+1] and
  * order[] = indices of the kept elements sorted by cell, ties by index. */

@@ -96,6 +96,14 @@ def lib():
         L.orc_track_one.argtypes = [P, P, P, P, C.c_int64, C.c_int64]
         L.orc_sort_by_cell.argtypes = [P, C.c_int64, C.c_int32, P, P]
         L.orc_couple.argtypes = [P, P]
+        L.orc_mlp_nparam.restype = C.c_int32
+        L.orc_bf16.restype = C.c_double
+        L.orc_bf16.argtypes = [C.c_double]
+        L.orc_mlp_init.argtypes = [P, C.c_uint64]
+        L.orc_mlp_forward.argtypes = [P, P, C.c_int64, C.c_int32, P]
+        L.orc_mlp_grad.restype = C.c_double
+        L.orc_mlp_grad.argtypes = [P, P, P, C.c_int64, C.c_int32, P]
+        L.orc_adam.argtypes = [P, P, P, P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_read_couple.argtypes = [P, C.c_int32, P, C.c_int64]
         L.orc_write_moments.argtypes = [P, C.c_int32, P]
         L.orc_write_wall_flux.argtypes = [P, P, C.c_int64]
@@ -302,3 +310,39 @@ def sort_by_cell(cell, n_cells):
     if rc != 0:
         raise ValueError("orc_sort_by_cell: bad input")
     return cs, order[: cs[-1]]
+
+
+# ------------------------------------------------------------- learned closure
+def mlp_nparam():
+    return lib().orc_mlp_nparam()
+
+
+def mlp_init(seed):
+    p = np.zeros(mlp_nparam(), np.float32)
+    lib().orc_mlp_init(_p(p), seed)
+    return p
+
+
+def mlp_forward(params, X, bf16=True):
+    params = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    Y = np.zeros((len(X), 8), np.float64)
+    lib().orc_mlp_forward(_p(params), _p(X), len(X), int(bf16), _p(Y))
+    return Y
+
+
+def mlp_grad(params, X, T, bf16=True):
+    params = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    g = np.zeros(mlp_nparam(), np.float64)
+    loss = lib().orc_mlp_grad(_p(params), _p(X), _p(T), len(X), int(bf16), _p(g))
+    return loss, g
+
+
+def adam(params, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    lib().orc_adam(_p(params), _p(m), _p(v), _p(np.ascontiguousarray(g, np.float64)), t, lr, b1, b2, eps)
+
+
+def bf16(x):
+    return lib().orc_bf16(float(x))

@@ -674,3 +674,73 @@ def test_recalibration_number_statistics():
     got = r["n_cloned"] - r["n_deleted"]
     assert abs(got - exp) < 4 * math.sqrt(var) + 1, (got, exp, var)
     assert len(o.read()[3]) == N0.sum() + r["n_cloned"] - r["n_deleted"]
+
+
+# ----------------------------------------------------------- learned closure (S12/S13)
+def test_bf16_round_to_nearest_even():
+    """BF16 = FP32 with 8 significant bits, round to nearest, ties to even."""
+    assert orc.bf16(1.0 + 2 ** -8) == 1.0  # tie between 1 and 1+2^-7: even
+    assert orc.bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6  # tie: even mantissa
+    assert orc.bf16(1.0 + 2 ** -8 + 2 ** -12) == 1.0 + 2 ** -7
+    assert orc.bf16(-3.0) == -3.0 and orc.bf16(0.0) == 0.0
+
+
+def test_mlp_forward_composes_gelu():
+    """A network that routes one input through one unit per layer computes
+    GELU(GELU(GELU(x))) with GELU(z) = z (1 + erf(z/sqrt2))/2 (closed form)."""
+    from scipy.special import erf
+
+    p = np.zeros(orc.mlp_nparam(), np.float32)
+    o = 0
+    p[o + 0] = 1.0  # W1[0][0]
+    o += 64 * 13 + 64
+    p[o + 0] = 1.0  # W2[0][0]
+    o += 64 * 64 + 64
+    p[o + 0] = 1.0  # W3[0][0]
+    o += 64 * 64 + 64
+    p[o + 0] = 1.0  # W4[0][0]
+    g = lambda z: 0.5 * z * (1 + erf(z / math.sqrt(2)))
+    X = np.zeros((5, 13), np.float32)
+    X[:, 0] = [-2.0, -0.5, 0.0, 0.7, 3.0]
+    Y = orc.mlp_forward(p, X, bf16=False)
+    assert np.allclose(Y[:, 0], g(g(g(X[:, 0].astype(np.float64)))), rtol=1e-12, atol=1e-15)
+    assert np.all(Y[:, 1:] == 0)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    """P14: backpropagated gradient of the mean-square loss equals central
+    finite differences of the FP64 network (no BF16 rounding) to 1e-6."""
+    rng = np.random.default_rng(5)
+    p = orc.mlp_init(7)
+    p += (0.05 * rng.standard_normal(len(p))).astype(np.float32)  # nonzero biases too
+    X = rng.standard_normal((12, 13)).astype(np.float32)
+    T = rng.standard_normal((12, 8)).astype(np.float32)
+    loss, g = orc.mlp_grad(p, X, T, bf16=False)
+    idx = list(rng.choice(len(p), 40, replace=False)) + [len(p) - 1, len(p) - 9, 64 * 13 + 3]
+    for i in idx:
+        h = 3e-5 * max(1.0, abs(float(p[i])))
+        pp = p.astype(np.float64)
+
+        def L(delta):
+            q = p.copy()
+            q[i] = np.float32(pp[i] + delta)
+            d = float(q[i]) - pp[i]
+            return orc.mlp_grad(q, X, T, bf16=False)[0], d
+
+        lp, dp = L(h)
+        lm, dm = L(-h)
+        fd = (lp - lm) / (dp - dm)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-10, (i, fd, g[i])
+
+
+def test_adam_first_step_closed_form():
+    """Adam's first step moves every parameter by lr * g / (|g| + eps) (the
+    bias-corrected moments equal g and g^2), i.e. lr * sign(g)."""
+    p = np.ones(orc.mlp_nparam(), np.float32)
+    g = np.linspace(-2, 3, len(p))
+    g[len(g) // 2] = 0.5
+    m = np.zeros(len(p))
+    v = np.zeros(len(p))
+    orc.adam(p, m, v, g, 1, lr=1e-3)
+    exp = 1.0 - 1e-3 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(p, exp.astype(np.float32), rtol=0, atol=2e-7)
