@@ -198,6 +198,7 @@ struct orc_ctx {
   double* cp_hot;      /* [12n] HoT: sigma (xx,yy,zz,xy,xz,yz), q_t (3), q_r (3) (nondimensional) */
   double* cp_new;      /* [6n] M^{k+1} */
   double* cp_own;      /* [6n] the cell's own sampled state (nondimensional) */
+  float* cl_params;    /* learned-closure parameters (S12), NULL until set */
   double* cp_flag;     /* [n] 1 accepted, 2 reconstructed, 0 neither */
 };
 
@@ -243,6 +244,7 @@ orc_ctx* orc_create(const orc_config* cfg) {
 static void free_mesh(orc_ctx* c) {
   free(c->nbr); free(c->nbr_face); free(c->pn); free(c->pd); free(c->parea); free(c->vol); free(c->cumvol);
   free(c->cp_half); free(c->cp_hot); free(c->cp_new); free(c->cp_flag); free(c->cp_own);
+  free(c->cl_params);
   free(c->fdtv); free(c->nodes); free(c->tets); free(c->bf); free(c->bflux); free(c->inj_rem); free(c->bcs);
   free(c->bc_sigma); free(c->bc_U); free(c->cstart); free(c->cmax); free(c->rem);
   free(c->phi_inst); free(c->phi_ewma); free(c->phi_win); free(c->phi_cum);
@@ -1248,20 +1250,27 @@ static void nsf(const nd_t* d, const double* P, const double* G, double* sig, do
   }
 }
 
-/* S9: M^{k+1/2}, HoT and the reliability filter with neighbour reconstruction */
-static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_rec) {
+/* S9 first half: from summation variables phi (sums over cnt steps; cnt = 1
+ * for the moving average) the cell's own nondimensional state own[6n] (rho,
+ * u(3), T_t, T_r), its mean particle count nbar[n] and HoT[12n] = sampled
+ * stress / heat flux minus their NSF values at the gradients of that state
+ * (Sec. 3.1, Eq. hot_extraction) */
+static void sampled_hot(orc_ctx* c, const nd_t* d, const double* phi, double cnt, double* own, double* H,
+                        double* nbar) {
   const int64_t n = c->n_tets;
-  double* mac = (double*)malloc(sizeof(double) * NMAC * n);
   double* grad = (double*)malloc(sizeof(double) * 15 * n);
   double* sdsmc = (double*)malloc(sizeof(double) * 12 * n);
   for (int64_t t = 0; t < n; ++t) {
-    derive_macro(c, c->phi_ewma + NPHI_MAX * t, c->vol[t], mac + NMAC * t);
-    const double* M = mac + NMAC * t;
-    double* own = c->cp_own + 6 * t;
-    own[0] = M[1] / d->rho0;
-    own[1] = M[2] / d->c0; own[2] = M[3] / d->c0; own[3] = M[4] / d->c0;
-    own[4] = M[5] / d->T0;
-    own[5] = d->dr > 0 ? M[6] / d->T0 : own[4];
+    double ph[NPHI_MAX], M[NMAC];
+    for (int q = 0; q < NPHI_MAX; ++q)
+      ph[q] = cnt == 1.0 ? phi[NPHI_MAX * t + q] : cnt > 0 ? phi[NPHI_MAX * t + q] / cnt : 0.0;
+    derive_macro(c, ph, c->vol[t], M);
+    nbar[t] = M[0];
+    double* o = own + 6 * t;
+    o[0] = M[1] / d->rho0;
+    o[1] = M[2] / d->c0; o[2] = M[3] / d->c0; o[3] = M[4] / d->c0;
+    o[4] = M[5] / d->T0;
+    o[5] = d->dr > 0 ? M[6] / d->T0 : o[4];
     const double ss = d->rho0 * d->c0 * d->c0, qs = ss * d->c0;
     for (int q = 0; q < 6; ++q) sdsmc[12 * t + q] = M[8 + q] / ss;
     for (int q = 0; q < 3; ++q) {
@@ -1269,24 +1278,106 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
       sdsmc[12 * t + 9 + q] = M[17 + q] / qs;
     }
   }
-  gradients(c, d, c->cp_own, grad);
+  gradients(c, d, own, grad);
+  for (int64_t t = 0; t < n; ++t) {
+    double sig[6], qt[3], qr[3];
+    nsf(d, own + 6 * t, grad + 15 * t, sig, qt, qr);
+    double* h = H + 12 * t;
+    for (int q = 0; q < 6; ++q) h[q] = sdsmc[12 * t + q] - sig[q];
+    for (int q = 0; q < 3; ++q) {
+      h[6 + q] = sdsmc[12 * t + 6 + q] - qt[q];
+      h[9 + q] = sdsmc[12 * t + 9 + q] - qr[q];
+    }
+  }
+  free(grad); free(sdsmc);
+}
+
+/* S12 inputs: 13 features per cell from summation variables phi over cnt
+ * steps -- rho, u(3), T_t (nondimensional) and the traceless HoT stress
+ * (xx, yy, xy, xz, yz) over rho T_t and translational HoT heat flux over
+ * rho T_t^{3/2} (i.e. sigma / (rho k T / m), q / (rho (k T / m)^{3/2}) in SI).
+ * A cell without particles, or with a non-positive or non-finite state, gets
+ * a zero row and valid[t] = 0.  own[6n] receives the cells' states. */
+static void closure_inputs(orc_ctx* c, const nd_t* d, const double* phi, double cnt, float* X, double* own,
+                           uint8_t* valid) {
+  const int64_t n = c->n_tets;
+  double* H = (double*)malloc(sizeof(double) * 12 * n);
+  double* nbar = (double*)malloc(sizeof(double) * n);
+  sampled_hot(c, d, phi, cnt, own, H, nbar);
+  for (int64_t t = 0; t < n; ++t) {
+    const double* o = own + 6 * t;
+    const double* h = H + 12 * t;
+    int ok = cnt > 0 && nbar[t] > 0.0 && o[0] > 0.0 && o[4] > 0.0;
+    double f[13];
+    if (ok) {
+      const double s = o[0] * o[4], qn = s * sqrt(o[4]);
+      f[0] = o[0]; f[1] = o[1]; f[2] = o[2]; f[3] = o[3]; f[4] = o[4];
+      f[5] = h[0] / s; f[6] = h[1] / s; f[7] = h[3] / s; f[8] = h[4] / s; f[9] = h[5] / s;
+      f[10] = h[6] / qn; f[11] = h[7] / qn; f[12] = h[8] / qn;
+      for (int k = 0; k < 13 && ok; ++k) ok = isfinite(f[k]) && isfinite((float)f[k]);
+    }
+    for (int k = 0; k < 13; ++k) X[13 * t + k] = ok ? (float)f[k] : 0.0f;
+    if (valid) valid[t] = (uint8_t)ok;
+  }
+  free(H); free(nbar);
+}
+
+static const double* phi_select(const orc_ctx* c, int32_t which, double* cnt) {
+  *cnt = which == ORC_PHI_WINDOW ? (double)c->n_win : which == ORC_PHI_CUM ? (double)c->n_cum : 1.0;
+  return which == ORC_PHI_INST ? c->phi_inst : which == ORC_PHI_EWMA ? c->phi_ewma
+       : which == ORC_PHI_WINDOW ? c->phi_win : c->phi_cum;
+}
+
+/* S12 in the coupling: the learned closure evaluated on the coupling
+ * window's features replaces the translational HoT (sigma, q_t) of every cell
+ * whose features are valid and whose prediction is finite and within
+ * ORC_CLOSURE_YMAX; the other cells keep the sampled HoT (the fallback).
+ * sigma_zz = -(sigma_xx + sigma_yy); q_r keeps its sampled value. */
+static int64_t closure_apply(orc_ctx* c, const nd_t* d) {
+  const int64_t n = c->n_tets;
+  float* X = (float*)malloc(sizeof(float) * 13 * n);
+  double* Y = (double*)malloc(sizeof(double) * 8 * n);
+  double* own = (double*)malloc(sizeof(double) * 6 * n);
+  uint8_t* valid = (uint8_t*)malloc(n);
+  closure_inputs(c, d, c->phi_win, (double)c->n_win, X, own, valid);
+  orc_mlp_forward(c->cl_params, X, n, 1, Y);
+  int64_t used = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    const double* y = Y + 8 * t;
+    int ok = valid[t];
+    for (int k = 0; k < 8 && ok; ++k) ok = isfinite(y[k]) && fabs(y[k]) <= ORC_CLOSURE_YMAX;
+    if (!ok) continue;
+    const double rho = own[6 * t], T = own[6 * t + 4];
+    const double s = rho * T, qn = s * sqrt(T);
+    double* h = c->cp_hot + 12 * t;
+    h[0] = y[0] * s;
+    h[1] = y[1] * s;
+    h[2] = -(h[0] + h[1]);
+    h[3] = y[2] * s;
+    h[4] = y[3] * s;
+    h[5] = y[4] * s;
+    for (int q = 0; q < 3; ++q) h[6 + q] = y[5 + q] * qn;
+    used++;
+  }
+  free(X); free(Y); free(own); free(valid);
+  return used;
+}
+
+/* S9: M^{k+1/2}, HoT and the reliability filter with neighbour reconstruction */
+static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_rec, int64_t* n_learned) {
+  const int64_t n = c->n_tets;
+  double* nbar = (double*)malloc(sizeof(double) * n);
+  sampled_hot(c, d, c->phi_ewma, 1.0, c->cp_own, c->cp_hot, nbar);
   uint8_t* avail = (uint8_t*)calloc(n, 1);
   *n_rej = 0;
   for (int64_t t = 0; t < n; ++t) {
     const double* P = c->cp_own + 6 * t;
-    double sig[6], qt[3], qr[3];
-    nsf(d, P, grad + 15 * t, sig, qt, qr);
-    double* H = c->cp_hot + 12 * t;
-    for (int q = 0; q < 6; ++q) H[q] = sdsmc[12 * t + q] - sig[q];
-    for (int q = 0; q < 3; ++q) {
-      H[6 + q] = sdsmc[12 * t + 6 + q] - qt[q];
-      H[9 + q] = sdsmc[12 * t + 9 + q] - qr[q];
-    }
+    const double* H = c->cp_hot + 12 * t;
     memcpy(c->cp_half + 6 * t, P, 6 * sizeof(double));
     /* local cell Knudsen number (Eq. cell_kn_stability) */
     const double V = c->vol[t] / (d->L0 * d->L0 * d->L0);
     const double dc = 2.0 * cbrt(3.0 * V / (4.0 * M_PI));
-    int ok = mac[NMAC * t] > 0.0 && P[0] > 0.0 && P[4] > 0.0;
+    int ok = nbar[t] > 0.0 && P[0] > 0.0 && P[4] > 0.0;
     for (int q = 0; q < 6 && ok; ++q) ok = isfinite(P[q]);
     for (int q = 0; q < 12 && ok; ++q) ok = isfinite(H[q]);
     if (ok) {
@@ -1297,6 +1388,7 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
     c->cp_flag[t] = ok ? 1.0 : 0.0;
     if (!ok) (*n_rej)++;
   }
+  *n_learned = c->cfg.closure && c->cl_params ? closure_apply(c, d) : 0;
   /* reconstruction passes: a rejected cell with available face neighbours
    * takes their equal-weight mean (state and HoT); it becomes available for
    * the next pass */
@@ -1325,7 +1417,7 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
     }
     memcpy(avail, nxt, n);
   }
-  free(nxt); free(avail); free(mac); free(grad); free(sdsmc);
+  free(nxt); free(avail); free(nbar);
 }
 
 /* S10: steady synthetic equations (Eq. macro with the closure
@@ -1594,7 +1686,9 @@ int orc_couple(orc_ctx* c, orc_couple_report* rep) {
   }
   const nd_t d = nondim(c);
   memset(rep, 0, sizeof *rep);
-  extract_hot(c, &d, &rep->n_rejected, &rep->n_reconstructed);
+  int64_t n_learned = 0;
+  extract_hot(c, &d, &rep->n_rejected, &rep->n_reconstructed, &n_learned);
+  rep->n_learned = (int32_t)n_learned;
   int rc = solve_synthetic(c, &d, &rep->iters, &rep->residual);
   /* the k-th coupling (k = 0, 1, ...) keys its random stream with sub = k */
   if (rc == 0) recalibrate(c, &d, &rep->n_cloned, &rep->n_deleted);
@@ -1783,4 +1877,55 @@ void orc_mlp_init(float* params, uint64_t seed) {
     }
     for (int j = 0; j < v.nout[l]; ++j) b[j] = 0.0f;
   }
+}
+
+int orc_closure_set(orc_ctx* c, const float* params) {
+  if (!c->cl_params) c->cl_params = (float*)malloc(sizeof(float) * MLP_NPARAM);
+  memcpy(c->cl_params, params, sizeof(float) * MLP_NPARAM);
+  return 0;
+}
+
+/* X[n][13]: the closure inputs of every cell from moments `which` */
+int orc_closure_features(orc_ctx* c, int32_t which, float* X) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  const nd_t d = nondim(c);
+  double cnt;
+  const double* phi = phi_select(c, which, &cnt);
+  double* own = (double*)malloc(sizeof(double) * 6 * c->n_tets);
+  closure_inputs(c, &d, phi, cnt, X, own, NULL);
+  free(own);
+  return 0;
+}
+
+/* S13 targets: Y[r][8] = HoT of moments `which` (the long-time average) of
+ * cell r mod n, normalised like the inputs by the density X[r][0] and
+ * temperature X[r][4] of input row r: sigma (xx, yy, xy, xz, yz) / (rho T),
+ * q_t / (rho T^{3/2}).  Rows whose input is invalid (zero density or
+ * temperature) or whose cell has no particles in `which` are zero. */
+int orc_closure_targets(orc_ctx* c, int32_t which, const float* X, int64_t n_rows, float* Y) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  const int64_t n = c->n_tets;
+  const nd_t d = nondim(c);
+  double cnt;
+  const double* phi = phi_select(c, which, &cnt);
+  double* own = (double*)malloc(sizeof(double) * 6 * n);
+  double* H = (double*)malloc(sizeof(double) * 12 * n);
+  double* nbar = (double*)malloc(sizeof(double) * n);
+  sampled_hot(c, &d, phi, cnt, own, H, nbar);
+  for (int64_t r = 0; r < n_rows; ++r) {
+    const int64_t t = r % n;
+    const double x0 = X[13 * r], x4 = X[13 * r + 4];
+    const double* h = H + 12 * t;
+    int ok = cnt > 0 && nbar[t] > 0.0 && x0 > 0.0 && x4 > 0.0;
+    double y[8];
+    if (ok) {
+      const double s = x0 * x4, qn = s * sqrt(x4);
+      y[0] = h[0] / s; y[1] = h[1] / s; y[2] = h[3] / s; y[3] = h[4] / s; y[4] = h[5] / s;
+      y[5] = h[6] / qn; y[6] = h[7] / qn; y[7] = h[8] / qn;
+      for (int k = 0; k < 8 && ok; ++k) ok = isfinite(y[k]) && isfinite((float)y[k]);
+    }
+    for (int k = 0; k < 8; ++k) Y[8 * r + k] = ok ? (float)y[k] : 0.0f;
+  }
+  free(own); free(H); free(nbar);
+  return 0;
 }

@@ -49,6 +49,8 @@ typedef struct orc_config {
   double eps_m;     /* synthetic-solver residual tolerance */
   double KnD_max;   /* cell Knudsen threshold of the reliability criterion */
   int64_t capacity; /* particle capacity */
+  int32_t closure;  /* 1: the learned closure supplies the HoT of the coupling (S12) */
+  int32_t pad;
 } orc_config;
 
 typedef struct orc_bc {
@@ -95,7 +97,7 @@ int64_t orc_step_index(orc_ctx* c);
 /* DIG coupling (Alg. 1: one outer step after N_s DSMC steps) */
 typedef struct orc_couple_report {
   int32_t iters;            /* synthetic-solver iterations */
-  int32_t pad;
+  int32_t n_learned;        /* cells whose HoT came from the learned closure */
   double residual;          /* final residual / first residual */
   int64_t n_rejected;       /* cells failing the cell-Knudsen criterion */
   int64_t n_reconstructed;  /* rejected cells rebuilt from neighbours */
@@ -115,6 +117,12 @@ int orc_mlp_forward(const float* params, const float* X, int64_t n, int32_t bf16
 double orc_mlp_grad(const float* params, const float* X, const float* T, int64_t n, int32_t bf16, double* grad);
 void orc_adam(float* params, double* m, double* v, const double* g, int64_t t, double lr, double b1, double b2,
               double eps);
+/* closure inputs and targets; a prediction with a component beyond
+ * ORC_CLOSURE_YMAX in magnitude (or non-finite) falls back to the sampled HoT */
+#define ORC_CLOSURE_YMAX 4.0
+int orc_closure_set(orc_ctx* c, const float* params);
+int orc_closure_features(orc_ctx* c, int32_t which, float* X);
+int orc_closure_targets(orc_ctx* c, int32_t which, const float* X, int64_t n_rows, float* Y);
 
 /* stable counting sort by cell (the paper's per-cell particle buckets):
  * cell[n] in [0, n_cells) or -1 (dropped); writes cell_start[n_cells+1] and

@@ -29,15 +29,16 @@ class OrcConfig(C.Structure):
         ("T_init", C.c_double), ("u_init", C.c_double * 3), ("mu_ref", C.c_double), ("Kn", C.c_double),
         ("L_ref", C.c_double), ("n_a", C.c_int32), ("N_s", C.c_int32), ("N_m", C.c_int32),
         ("passes", C.c_int32), ("eps_m", C.c_double), ("KnD_max", C.c_double), ("capacity", C.c_int64),
+        ("closure", C.c_int32), ("pad", C.c_int32),
     ]
 
 
 class CoupleReport(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("pad", C.c_int32), ("residual", C.c_double), ("n_rejected", C.c_int64),
+    _fields_ = [("iters", C.c_int32), ("n_learned", C.c_int32), ("residual", C.c_double), ("n_rejected", C.c_int64),
                 ("n_reconstructed", C.c_int64), ("n_cloned", C.c_int64), ("n_deleted", C.c_int64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class OrcBC(C.Structure):
@@ -107,6 +108,9 @@ def lib():
         L.orc_read_couple.argtypes = [P, C.c_int32, P, C.c_int64]
         L.orc_write_moments.argtypes = [P, C.c_int32, P]
         L.orc_write_wall_flux.argtypes = [P, P, C.c_int64]
+        L.orc_closure_set.argtypes = [P, P]
+        L.orc_closure_features.argtypes = [P, C.c_int32, P]
+        L.orc_closure_targets.argtypes = [P, C.c_int32, P, C.c_int64, P]
         _lib = L
     return _lib
 
@@ -283,6 +287,22 @@ class Oracle:
     def write_wall_flux(self, flux, steps):
         flux = np.ascontiguousarray(flux, np.float64)
         self._check(self.L.orc_write_wall_flux(self.h, _p(flux), steps))
+
+    def closure_set(self, params):
+        params = np.ascontiguousarray(params, np.float32)
+        assert params.size == mlp_nparam()
+        self._check(self.L.orc_closure_set(self.h, _p(params)))
+
+    def closure_features(self, which):
+        X = np.zeros((self.n_tets, 13), np.float32)
+        self._check(self.L.orc_closure_features(self.h, which, _p(X)))
+        return X
+
+    def closure_targets(self, which, X):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.zeros((len(X), 8), np.float32)
+        self._check(self.L.orc_closure_targets(self.h, which, _p(X), len(X), _p(Y)))
+        return Y
 
     @property
     def step_index(self):

@@ -744,3 +744,132 @@ def test_adam_first_step_closed_form():
     orc.adam(p, m, v, g, 1, lr=1e-3)
     exp = 1.0 - 1e-3 * g / (np.abs(g) + 1e-8)
     assert np.allclose(p, exp.astype(np.float32), rtol=0, atol=2e-7)
+
+
+# ------------------------------------------------------- learned closure inputs
+def stressed_phi(o, scen, sigma, q, rho_scale=1.0, T=None):
+    """Exact per-step summation variables of a state at rest with density
+    rho_scale * m n_init, temperature T, traceless stress sigma (xx, yy, zz,
+    xy, xz, yz) and heat flux q: <c_i c_j> = (kT/m) delta_ij + sigma_ij / rho,
+    <c_i c^2> = 2 q_i / rho."""
+    vol = o.mesh_info()["vol"]
+    T = scen.T_init if T is None else T
+    m = scen.gas.mass
+    rho = rho_scale * m * scen.n_init
+    N = scen.n_init * rho_scale * vol / scen.F_N
+    phi = np.zeros((len(vol), orc.NPHI))
+    phi[:, 0] = N
+    for k, s in enumerate(sigma):
+        phi[:, 4 + k] = N * ((KB * T / m if k < 3 else 0.0) + s / rho)
+    for i in range(3):
+        phi[:, 10 + i] = N * 2.0 * q[i] / rho
+    return phi
+
+
+SIG = np.array([0.04, -0.015, -0.025, 0.01, -0.02, 0.03])  # / p
+QF = np.array([0.02, -0.01, 0.005])  # / (rho (kT/m)^{3/2})
+
+
+def test_closure_features_closed_form():
+    """S12 inputs of a uniform state at rest in a box whose diffuse walls are
+    at the gas temperature (all gradients vanish, so the HoT is the sampled
+    stress and heat flux): rho / (m n0), u / c0, T / T0, the traceless stress
+    (xx, yy, xy, xz, yz) over p = rho k T / m and the heat flux over
+    rho (k T / m)^{3/2}; an empty cell gives a zero row."""
+    s = box_scenario(nh=2, n_particles=3000, kind=W.BC_DIFFUSE)
+    o = orc.Oracle(s)
+    o.init()
+    o.step(1, orc.WINDOW)
+    rs = 1.3
+    p = rs * s.n_init * KB * s.T_init
+    rho = rs * s.gas.mass * s.n_init
+    kTm = KB * s.T_init / s.gas.mass
+    phi = stressed_phi(o, s, SIG * p, QF * rho * kTm ** 1.5, rho_scale=rs)
+    phi[3] = 0.0  # an empty cell
+    o.write_moments(orc.PHI_WINDOW, phi)
+    X = o.closure_features(orc.PHI_WINDOW).astype(np.float64)
+    exp = np.concatenate([[rs, 0, 0, 0, 1.0], SIG[[0, 1, 3, 4, 5]], QF])
+    # the empty cell's zero temperature enters its face neighbours' gradients
+    nbr = o.mesh_info()["nbr"]
+    ok = np.all(nbr != 3, axis=1) & (np.arange(len(X)) != 3)
+    assert ok.sum() >= len(X) - 5
+    assert np.all(X[3] == 0)
+    assert np.allclose(X[ok], exp[None, :], rtol=2e-6, atol=1e-7), np.abs(X[ok] - exp).max(axis=0)
+
+
+def test_closure_targets_normalised_by_input_row():
+    """S13 targets: the HoT of the long-time (cumulative) average of cell
+    r mod n divided by rho T (stress) and rho T^{3/2} (heat flux) of input row
+    r, for a stack of input rows spanning several windows; rows with zero
+    density or temperature are zero."""
+    s = box_scenario(nh=1, n_particles=2000, kind=W.BC_DIFFUSE)
+    o = orc.Oracle(s)
+    o.init()
+    o.step(1, orc.WINDOW | orc.CUMUL)
+    p = s.n_init * KB * s.T_init
+    rho = s.gas.mass * s.n_init
+    kTm = KB * s.T_init / s.gas.mass
+    o.write_moments(orc.PHI_CUM, stressed_phi(o, s, SIG * p, QF * rho * kTm ** 1.5))
+    n = o.n_tets
+    rng = np.random.default_rng(3)
+    X = rng.uniform(0.5, 2.0, (3 * n, 13)).astype(np.float32)
+    X[n + 2, 0] = 0.0
+    X[2 * n + 1, 4] = 0.0
+    Y = o.closure_targets(orc.PHI_CUM, X).astype(np.float64)
+    x0, x4 = X[:, 0].astype(np.float64), X[:, 4].astype(np.float64)
+    with np.errstate(divide="ignore"):
+        exp = np.concatenate([np.outer(1 / (x0 * x4), SIG[[0, 1, 3, 4, 5]]), np.outer(1 / (x0 * x4 ** 1.5), QF)],
+                             axis=1)
+    bad = np.zeros(3 * n, bool)
+    bad[[n + 2, 2 * n + 1]] = True
+    exp[bad] = 0.0
+    assert np.allclose(Y, exp, rtol=2e-6, atol=1e-8), np.abs(Y - exp).max()
+
+
+def constant_net(y):
+    """Parameters of the network whose output is the constant y: zero weights,
+    zero hidden biases, output bias y (GELU(0) = 0)."""
+    p = np.zeros(orc.mlp_nparam(), np.float32)
+    p[-8:] = y
+    return p
+
+
+def closure_case(closure, y, empty=()):
+    s = box_scenario(nh=2, n_particles=3000, kind=W.BC_DIFFUSE)
+    o = orc.Oracle(s, N_m=5, KnD_max=1e9, closure=closure)
+    o.init()
+    o.step(1, orc.WINDOW)
+    phi_w = stressed_phi(o, s, 0 * SIG, 0 * QF, rho_scale=1.3, T=1.2 * s.T_init)
+    phi_w[list(empty)] = 0.0
+    o.write_moments(orc.PHI_WINDOW, phi_w)
+    p = s.n_init * KB * s.T_init
+    o.write_moments(orc.PHI_EWMA, stressed_phi(o, s, 0.5 * SIG * p, 0 * QF))
+    o.write_wall_flux(wall_pressure_flux(o, s, 10), 10)
+    o.closure_set(constant_net(y))
+    r = o.couple()
+    return r, o.read_couple(1)
+
+
+def test_closure_replaces_hot_in_coupling():
+    """S12 in the coupling: with a network that outputs the constant y the HoT
+    of each cell is y de-normalised by the window's density and temperature
+    (sigma_zz = -(sigma_xx + sigma_yy)); cells with an empty window, and every
+    cell when a component of y exceeds the limit, keep the sampled HoT."""
+    y = np.array([0.05, -0.02, 0.01, 0.03, -0.04, 0.02, 0.01, -0.03], np.float32)
+    r0, H0 = closure_case(0, y, empty=(0, 5))
+    r1, H1 = closure_case(1, y, empty=(0, 5))
+    n = len(H1)
+    assert r0["n_learned"] == 0 and r1["n_learned"] == n - 2
+    rho, T = 1.3, 1.2
+    yd = y.astype(np.float64)
+    s, qn = rho * T, rho * T * math.sqrt(T)
+    exp = np.array([yd[0] * s, yd[1] * s, 0.0, yd[2] * s, yd[3] * s, yd[4] * s, *(yd[5:] * qn), 0, 0, 0])
+    exp[2] = -(exp[0] + exp[1])
+    learned = np.ones(n, bool)
+    learned[[0, 5]] = False
+    assert np.allclose(H1[learned], exp[None, :], rtol=1e-12, atol=1e-15)
+    assert np.array_equal(H1[~learned], H0[~learned])
+    y_bad = y.copy()
+    y_bad[3] = 4.5  # beyond the plausibility limit
+    r2, H2 = closure_case(1, y_bad)
+    assert r2["n_learned"] == 0 and np.array_equal(H2, closure_case(0, y_bad)[1])
