@@ -112,7 +112,7 @@ typedef struct dig_config {
   int32_t stage_cap;     /* particles staged in shared memory per CTA (<= 0: 3072) */
   int32_t tile_cells;    /* cells per CTA of the cell pass (<= 0: chosen from the load) */
   int32_t cta_threads;   /* threads per CTA of the cell pass: 64, 128 or 256 (<= 0: 256) */
-  int32_t pad1;
+  int32_t closure;       /* 1: dig_couple takes the HoT from the learned closure (see closure_*) */
 } dig_config;
 
 typedef struct dig_bc {
@@ -228,13 +228,18 @@ int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches);
  * of accepted cells recalibrated to M^{k+1} (velocities shifted and scaled,
  * rotational energies scaled, particles cloned or deleted with the density
  * ratio).  Walls use the momentum and energy given to each wall face during
- * the DSMC steps run with DIG_WALLFLUX since the last coupling.  Synchronous;
+ * the DSMC steps run with DIG_WALLFLUX since the last coupling.  With
+ * cfg.closure = 1 and closure parameters set, the translational HoT (sigma,
+ * q_t) of each cell comes from the learned closure evaluated on the coupling
+ * window's sums (DIG_WINDOW; see closure_features), except for cells whose
+ * window is empty or whose prediction is non-finite or has a component beyond
+ * DIG_CLOSURE_YMAX: they keep the sampled HoT.  Synchronous;
  * DIG_ERR_SOLVE if the solve produced a non-finite or non-positive state (the
  * particles are then left unchanged).
  */
 typedef struct dig_couple_report {
   int32_t iters;            /* synthetic-solver iterations */
-  int32_t pad;
+  int32_t n_learned;        /* cells whose HoT came from the learned closure */
   double residual;          /* final residual relative to the first one */
   int64_t n_rejected;       /* cells failing the cell-Knudsen criterion */
   int64_t n_reconstructed;  /* rejected cells rebuilt from their neighbours */
@@ -253,6 +258,66 @@ int dig_write_moments(dig_ctx* ctx, int32_t which, const double* host_in);
 /* overwrite the per-wall-face sums in[n_bfaces][5] (hits, momentum, energy
  * given to the wall) and the number of DSMC steps they cover */
 int dig_write_wall_flux(dig_ctx* ctx, const double* host_in, int64_t steps);
+
+/*
+ * Learned closure (not in the paper; the DIG HoT from a per-cell network):
+ * an MLP 13 -> 64 -> 64 -> 64 -> 8 with GELU (z/2 (1 + erf(z / sqrt 2))) on
+ * the hidden layers, BF16 weights and activations, FP32 accumulation on the
+ * tensor cores.  Parameters (FP32 master copy, [out][in] per layer):
+ * W1[64][13] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[8][64] b4[8],
+ * DIG_MLP_NPARAM floats; the biases are not rounded to BF16.
+ * Inputs (closure_features), per cell, nondimensional as in dig_read_couple:
+ * rho, u(3), T_t, the traceless HoT stress (xx, yy, xy, xz, yz) / (rho T_t)
+ * and translational HoT heat flux (3) / (rho T_t^{3/2}) -- in SI, sigma over
+ * rho k T / m and q over rho (k T / m)^{3/2}.  Outputs: the same eight HoT
+ * components, normalised the same way by the input's rho and T_t.
+ * Device arrays (X, Y, perm) are the caller's, read or written on the
+ * context's stream; rows are contiguous (X [n][13], Y [n][8], f32).
+ */
+#define DIG_MLP_NIN 13
+#define DIG_MLP_NOUT 8
+#define DIG_MLP_NPARAM 9736
+#define DIG_CLOSURE_YMAX 4.0
+/* He-normal weights (std sqrt(2 / fan_in)) from the seed's MLP_INIT random
+ * stream, zero biases; resets the Adam state.  Needs a bound arena. */
+int closure_init(dig_ctx* ctx, uint64_t seed);
+/* copy parameters from / to HOST params[n], n = DIG_MLP_NPARAM (else
+ * DIG_ERR_ARG); set resets the Adam state */
+int closure_set(dig_ctx* ctx, const float* params, int64_t n);
+int closure_get(dig_ctx* ctx, float* params, int64_t n);
+/* X[n_tets][13] (DEVICE): the inputs of every cell from the sums `which`
+ * (DIG_PHI_*; window and cumulative sums are averaged over their steps); a
+ * cell without particles gets a zero row.  Asynchronous. */
+int closure_features(dig_ctx* ctx, int32_t which, float* X);
+/* training targets Y[n_rows][8] (DEVICE): the HoT of the sums `which` (the
+ * long-time average) of cell r mod n_tets, normalised by the density X[r][0]
+ * and temperature X[r][4] of input row r (X: n_rows stacked closure_features
+ * outputs); zero for rows with zero density or temperature or an empty cell.
+ * Asynchronous. */
+int closure_targets(dig_ctx* ctx, int32_t which, const float* X, int64_t n_rows, float* Y);
+/* Y[n][8] = network(X[n][13]) (DEVICE).  Asynchronous. */
+int closure_forward(dig_ctx* ctx, const float* X, int64_t n, float* Y);
+/* mean-square error L = 1/(8 n) sum (pred - Y)^2 over n rows (DEVICE X, Y):
+ * pred = network(X), or with identity = 1 the inputs' own HoT X[:, 5:13]
+ * (the closure without the network).  Synchronous. */
+int closure_loss(dig_ctx* ctx, const float* X, const float* Y, int64_t n, int32_t identity, double* loss);
+/* gradient of L over all n rows with respect to every parameter, to HOST
+ * grad[DIG_MLP_NPARAM] (FP32); *loss = L.  No update.  Synchronous. */
+int closure_grad(dig_ctx* ctx, const float* X, const float* Y, int64_t n, float* grad, double* loss);
+typedef struct dig_train_cfg {
+  int32_t epochs;        /* passes over the rows (>= 1) */
+  int32_t batch;         /* rows per Adam step (>= 1) */
+  double lr, beta1, beta2, eps; /* Adam (Kingma and Ba 2015) */
+  const int32_t* perm;   /* DEVICE [epochs][n]: row order of each epoch, a
+                            permutation of 0..n-1; NULL: rows in order */
+} dig_train_cfg;
+/* Adam on the mean-square error over mini-batches of the rows X[n][13] ->
+ * Y[n][8] (DEVICE); loss[epochs] (HOST) receives each epoch's mean training
+ * loss.  The Adam step count carries over between calls.  DIG_ERR_ARG for a
+ * bad cfg or a perm entry outside [0, n) (found on the device: the epoch's
+ * rows with such entries are skipped).  Synchronous. */
+int closure_train(dig_ctx* ctx, const dig_train_cfg* cfg, const float* X, const float* Y, int64_t n,
+                  double* loss);
 
 /*
  * dig_sort_by_cell -- stable counting sort by cell, the paper's per-cell

@@ -25,6 +25,7 @@ UNITS = [
     ("dig_sort.cu", []),
     ("dig_couple.cu", []),
     ("dig_noalloc.cu", []),
+    ("dig_mlp.cu", []),
 ]
 
 

@@ -119,6 +119,12 @@ struct dig_ctx {
   int64_t flux_steps = 0, n_couple = 0;
   size_t tev_used = 0;
   bool timing = false;
+  // learned closure: FP32 master parameters, Adam moments, gradient
+  float *cl_p = nullptr, *cl_m = nullptr, *cl_v = nullptr, *cl_g = nullptr;
+  double* cl_acc = nullptr;  // [2] loss accumulators
+  int* cl_status = nullptr;
+  bool cl_set = false;
+  int64_t adam_t = 0;
 };
 
 static int fail(dig_ctx* c, int code, const char* msg) {
@@ -470,7 +476,16 @@ static size_t layout(dig_ctx* ctx, char* base) {
   C.part = A.take<double>(couple_part_count((int)n));
   C.avail = A.take<int>(n);
   C.avail2 = A.take<int>(n);
-  C.stats = A.take<unsigned long long>(4);
+  C.feat = A.take<float>((size_t)MLP_NIN * n);
+  C.ypred = A.take<float>((size_t)MLP_NOUT * n);
+  C.wnorm = A.take<double>(2 * n);
+  C.stats = A.take<unsigned long long>(8);
+  ctx->cl_p = A.take<float>(MLP_NPARAM);
+  ctx->cl_m = A.take<float>(MLP_NPARAM);
+  ctx->cl_v = A.take<float>(MLP_NPARAM);
+  ctx->cl_g = A.take<float>(MLP_NPARAM);
+  ctx->cl_acc = A.take<double>(2);
+  ctx->cl_status = A.take<int>(2);
   C.scal = A.take<CoupleScalars>(1);
   C.rpart = A.take<int>(cap / 4096 + 2);
   C.clone_total = A.take<int>(1);
@@ -935,10 +950,16 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
   cudaStream_t s = ctx->stream;
   CoupleParams& C = ctx->C;
   C.wall_t = ctx->flux_steps > 0 ? (double)ctx->flux_steps * ctx->cfg.dt : 0.0;
-  CK(cudaMemsetAsync(C.stats, 0, 4 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(C.stats, 0, 5 * sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(C.scal, 0, sizeof(CoupleScalars), s));
   CK(cudaMemsetAsync(C.clone_total, 0, sizeof(int), s));
-  launch_couple_s9(ctx->P, C, ctx->cfg.passes, s);
+  const bool learned = ctx->cfg.closure == 1 && ctx->cl_set;
+  if (learned) {
+    // S12: the closure's inputs from the coupling window, then its outputs
+    launch_closure_features(ctx->P, C, ctx->P.phi_win, (double)ctx->n_win, C.feat, s);
+    launch_mlp_forward(ctx->cl_p, C.feat, ctx->n_tets, C.ypred, s);
+  }
+  launch_couple_s9(ctx->P, C, ctx->cfg.passes, learned ? C.ypred : nullptr, s);
   launch_couple_s10(ctx->P, C, ctx->cfg.N_m, ctx->cfg.eps_m, s);
   CoupleScalars sc{};
   int N = 0;
@@ -959,9 +980,10 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
   }
   CK(cudaMemsetAsync(ctx->P.bflux, 0, 5 * std::max<size_t>(ctx->bf.size(), 1) * sizeof(double), s));
   ctx->flux_steps = 0;
-  unsigned long long st[4];
+  unsigned long long st[5];
   CK(cudaMemcpyAsync(st, C.stats, sizeof st, cudaMemcpyDeviceToHost, s));
   rc = check_status(ctx);
+  out->n_learned = (int32_t)st[4];
   out->n_rejected = (int64_t)st[0];
   out->n_reconstructed = (int64_t)st[1];
   out->n_cloned = (int64_t)st[2];
@@ -1040,3 +1062,142 @@ int dig_launch_count(dig_ctx* ctx, int64_t* n) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// learned closure (S12/S13)
+// ---------------------------------------------------------------------------
+static int closure_reset_adam(dig_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->cl_m, 0, MLP_NPARAM * sizeof(float), s));
+  CK(cudaMemsetAsync(ctx->cl_v, 0, MLP_NPARAM * sizeof(float), s));
+  CK(cudaMemsetAsync(ctx->cl_g, 0, MLP_NPARAM * sizeof(float), s));
+  ctx->adam_t = 0;
+  ctx->cl_set = true;
+  return DIG_OK;
+}
+
+int closure_init(dig_ctx* ctx, uint64_t seed) {
+  if (!ctx) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "closure_init: no arena");
+  launch_mlp_init(ctx->P, seed, ctx->cl_p, ctx->stream);
+  CK(cudaGetLastError());
+  return closure_reset_adam(ctx);
+}
+
+int closure_set(dig_ctx* ctx, const float* params, int64_t n) {
+  if (!ctx || !params) return DIG_ERR_ARG;
+  if (n != MLP_NPARAM) return fail(ctx, DIG_ERR_ARG, "closure_set: n must be DIG_MLP_NPARAM");
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "closure_set: no arena");
+  CK(cudaMemcpyAsync(ctx->cl_p, params, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  int rc = closure_reset_adam(ctx);
+  if (rc) return rc;
+  return wait_stream(ctx);
+}
+
+int closure_get(dig_ctx* ctx, float* params, int64_t n) {
+  if (!ctx || !params) return DIG_ERR_ARG;
+  if (n != MLP_NPARAM) return fail(ctx, DIG_ERR_ARG, "closure_get: n must be DIG_MLP_NPARAM");
+  if (!ctx->cl_set) return fail(ctx, DIG_ERR_STATE, "closure_get: no parameters set");
+  CK(cudaMemcpyAsync(params, ctx->cl_p, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  return wait_stream(ctx);
+}
+
+static const double* phi_of(dig_ctx* ctx, int which, double* cnt) {
+  *cnt = which == DIG_PHI_WINDOW ? (double)ctx->n_win : which == DIG_PHI_CUM ? (double)ctx->n_cum : 1.0;
+  return which == DIG_PHI_INST ? ctx->P.phi_inst : which == DIG_PHI_EWMA ? ctx->P.phi_ewma
+       : which == DIG_PHI_WINDOW ? ctx->P.phi_win : ctx->P.phi_cum;
+}
+
+int closure_features(dig_ctx* ctx, int32_t which, float* X) {
+  if (!ctx || !X || which < 0 || which > 3) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "closure_features: no arena");
+  double cnt;
+  const double* phi = phi_of(ctx, which, &cnt);
+  launch_closure_features(ctx->P, ctx->C, phi, cnt, X, ctx->stream);
+  CK(cudaGetLastError());
+  return DIG_OK;
+}
+
+int closure_targets(dig_ctx* ctx, int32_t which, const float* X, int64_t n_rows, float* Y) {
+  if (!ctx || which < 0 || which > 3 || n_rows < 0 || (n_rows > 0 && (!X || !Y))) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "closure_targets: no arena");
+  double cnt;
+  const double* phi = phi_of(ctx, which, &cnt);
+  launch_closure_targets(ctx->P, ctx->C, phi, cnt, X, n_rows, Y, ctx->stream);
+  CK(cudaGetLastError());
+  return DIG_OK;
+}
+
+int closure_forward(dig_ctx* ctx, const float* X, int64_t n, float* Y) {
+  if (!ctx || n < 0 || (n > 0 && (!X || !Y))) return DIG_ERR_ARG;
+  if (!ctx->cl_set) return fail(ctx, DIG_ERR_STATE, "closure_forward: no parameters set");
+  launch_mlp_forward(ctx->cl_p, X, n, Y, ctx->stream);
+  CK(cudaGetLastError());
+  return DIG_OK;
+}
+
+int closure_loss(dig_ctx* ctx, const float* X, const float* Y, int64_t n, int32_t identity, double* loss) {
+  if (!ctx || !loss || n <= 0 || !X || !Y) return DIG_ERR_ARG;
+  if (!identity && !ctx->cl_set) return fail(ctx, DIG_ERR_STATE, "closure_loss: no parameters set");
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->cl_acc, 0, 2 * sizeof(double), s));
+  launch_mlp_loss(ctx->cl_p, X, Y, n, identity ? 1 : 0, ctx->cl_acc, s);
+  CK(cudaGetLastError());
+  double acc = 0.0;
+  CK(cudaMemcpyAsync(&acc, ctx->cl_acc, sizeof acc, cudaMemcpyDeviceToHost, s));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  *loss = acc / (double)(MLP_NOUT * n);
+  return DIG_OK;
+}
+
+int closure_grad(dig_ctx* ctx, const float* X, const float* Y, int64_t n, float* grad, double* loss) {
+  if (!ctx || !grad || !loss || n <= 0 || !X || !Y) return DIG_ERR_ARG;
+  if (!ctx->cl_set) return fail(ctx, DIG_ERR_STATE, "closure_grad: no parameters set");
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->cl_g, 0, MLP_NPARAM * sizeof(float), s));
+  CK(cudaMemsetAsync(ctx->cl_acc, 0, 2 * sizeof(double), s));
+  CK(cudaMemsetAsync(ctx->cl_status, 0, 2 * sizeof(int), s));
+  launch_mlp_train_step(ctx->cl_p, X, Y, nullptr, n, 0, n, ctx->cl_g, ctx->cl_acc, ctx->cl_status, s);
+  CK(cudaGetLastError());
+  double acc = 0.0;
+  CK(cudaMemcpyAsync(grad, ctx->cl_g, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&acc, ctx->cl_acc, sizeof acc, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemsetAsync(ctx->cl_g, 0, MLP_NPARAM * sizeof(float), s));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  *loss = acc / (double)(MLP_NOUT * n);
+  return DIG_OK;
+}
+
+int closure_train(dig_ctx* ctx, const dig_train_cfg* cfg, const float* X, const float* Y, int64_t n,
+                  double* loss) {
+  if (!ctx || !cfg || !loss || n <= 0 || !X || !Y) return DIG_ERR_ARG;
+  if (cfg->epochs < 1 || cfg->batch < 1 || !(cfg->lr > 0.0) || !(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0) ||
+      !(cfg->beta2 >= 0.0 && cfg->beta2 < 1.0) || !(cfg->eps > 0.0))
+    return fail(ctx, DIG_ERR_ARG, "closure_train: bad epochs, batch or Adam constants");
+  if (n >= (1LL << 31)) return fail(ctx, DIG_ERR_ARG, "closure_train: n must be < 2^31");
+  if (!ctx->cl_set) return fail(ctx, DIG_ERR_STATE, "closure_train: no parameters set");
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->cl_status, 0, 2 * sizeof(int), s));
+  for (int e = 0; e < cfg->epochs; ++e) {
+    CK(cudaMemsetAsync(ctx->cl_acc, 0, 2 * sizeof(double), s));
+    const int32_t* perm = cfg->perm ? cfg->perm + (size_t)e * (size_t)n : nullptr;
+    for (int64_t b0 = 0; b0 < n; b0 += cfg->batch) {
+      const int64_t nb = std::min<int64_t>(cfg->batch, n - b0);
+      launch_mlp_train_step(ctx->cl_p, X, Y, perm, n, b0, nb, ctx->cl_g, ctx->cl_acc, ctx->cl_status, s);
+      launch_adam(ctx->cl_p, ctx->cl_m, ctx->cl_v, ctx->cl_g, ++ctx->adam_t, (float)cfg->lr, (float)cfg->beta1,
+                  (float)cfg->beta2, (float)cfg->eps, s);
+    }
+    CK(cudaGetLastError());
+    double acc = 0.0;
+    int st = 0;
+    CK(cudaMemcpyAsync(&acc, ctx->cl_acc, sizeof acc, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&st, ctx->cl_status, sizeof st, cudaMemcpyDeviceToHost, s));
+    int rc = wait_stream(ctx);
+    if (rc) return rc;
+    if (st) return fail(ctx, DIG_ERR_ARG, "closure_train: a perm entry is outside [0, n)");
+    loss[e] = acc / (double)(MLP_NOUT * n);
+  }
+  return DIG_OK;
+}

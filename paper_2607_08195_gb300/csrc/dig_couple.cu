@@ -26,14 +26,18 @@ __device__ __forceinline__ void bc_values(const Params& P, const CoupleParams& C
   *T = C.bcT[b] / C.T0;
 }
 
-// S9: the cell's own state and sampled stress / heat flux from the moving
-// average of the summation variables (Eq. dsmc_temperatures, nondimensional)
-__global__ void k_cp_extract(Params P, CoupleParams C) {
+// S9: the cell's own state and sampled stress / heat flux from summation
+// variables phi summed over cnt steps (cnt = 1: the moving average)
+// (Eq. dsmc_temperatures, nondimensional)
+__global__ void k_cp_extract(Params P, CoupleParams C, const double* __restrict__ phi, double cnt) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
   if (c >= n) return;
   double ph[NPHI];
-  for (int q = 0; q < NPHI; ++q) ph[q] = P.phi_ewma[(size_t)q * n + c];
+  for (int q = 0; q < NPHI; ++q) {
+    const double v = phi[(size_t)q * n + c];
+    ph[q] = cnt == 1.0 ? v : cnt > 0.0 ? v / cnt : 0.0;
+  }
   double M[NMAC];
   for (int q = 0; q < NMAC; ++q) M[q] = 0.0;
   const double N = ph[0];
@@ -134,22 +138,28 @@ __device__ void nsf(const CoupleParams& C, double Tt, const double* G, double* s
   nsf_mu(C, mu_nd(C, Tt), G, sig, qt, qr);
 }
 
-// HoT = sampled - NSF; cell Knudsen criterion (Eq. criterion); half = own
-__global__ void k_cp_hot(Params P, CoupleParams C) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// HoT = sampled - NSF of cell c (Eq. hot_extraction) from C.own, C.sd, C.grad
+__device__ void hot_cell(const Params& P, const CoupleParams& C, int c, double* Pc, double* H) {
   const int n = P.n_cells;
-  if (c >= n) return;
-  double Pc[6], G[15];
+  double G[15];
   for (int q = 0; q < 6; ++q) Pc[q] = C.own[(size_t)q * n + c];
   for (int q = 0; q < 15; ++q) G[q] = C.grad[(size_t)q * n + c];
   double sig[6], qt[3], qr[3];
   nsf(C, Pc[4], G, sig, qt, qr);
-  double H[12];
   for (int q = 0; q < 6; ++q) H[q] = C.sd[(size_t)q * n + c] - sig[q];
   for (int q = 0; q < 3; ++q) {
     H[6 + q] = C.sd[(size_t)(6 + q) * n + c] - qt[q];
     H[9 + q] = C.sd[(size_t)(9 + q) * n + c] - qr[q];
   }
+}
+
+// HoT; cell Knudsen criterion (Eq. criterion); half = own
+__global__ void k_cp_hot(Params P, CoupleParams C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  double Pc[6], H[12];
+  hot_cell(P, C, c, Pc, H);
   for (int q = 0; q < 12; ++q) C.hot[(size_t)q * n + c] = H[q];
   for (int q = 0; q < 6; ++q) C.half[(size_t)q * n + c] = Pc[q];
   const double V = P.vol[c] / (C.L0 * C.L0 * C.L0);
@@ -164,6 +174,94 @@ __global__ void k_cp_hot(Params P, CoupleParams C) {
   C.avail[c] = ok ? 1 : 0;
   C.flag[c] = ok ? 1.0 : 0.0;
   if (!ok) atomicAdd(C.stats + 0, 1ull);
+}
+
+// S12 inputs of every cell (see closure_features in dig.h): rho, u(3), T_t,
+// traceless HoT stress (xx, yy, xy, xz, yz) / (rho T_t), HoT q_t / (rho
+// T_t^{3/2}); zero rows for empty cells.  wnorm keeps rho and T_t (0 when
+// the row is invalid).
+__global__ void k_cl_features(Params P, CoupleParams C, float* __restrict__ X) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  double o[6], H[12], f[MLP_NIN];
+  hot_cell(P, C, c, o, H);
+  bool ok = C.nbar[c] > 0.0 && o[0] > 0.0 && o[4] > 0.0;
+  if (ok) {
+    const double s = o[0] * o[4], qn = s * sqrt(o[4]);
+    f[0] = o[0];
+    f[1] = o[1];
+    f[2] = o[2];
+    f[3] = o[3];
+    f[4] = o[4];
+    f[5] = H[0] / s;
+    f[6] = H[1] / s;
+    f[7] = H[3] / s;
+    f[8] = H[4] / s;
+    f[9] = H[5] / s;
+    f[10] = H[6] / qn;
+    f[11] = H[7] / qn;
+    f[12] = H[8] / qn;
+    for (int k = 0; k < MLP_NIN && ok; ++k) ok = isfinite(f[k]) && isfinite((float)f[k]);
+  }
+  for (int k = 0; k < MLP_NIN; ++k) X[(size_t)c * MLP_NIN + k] = ok ? (float)f[k] : 0.0f;
+  C.wnorm[c] = ok ? o[0] : 0.0;
+  C.wnorm[(size_t)n + c] = ok ? o[4] : 0.0;
+}
+
+// S13 targets: HoT of cell r mod n normalised by input row r's rho and T_t
+__global__ void k_cl_targets(Params P, CoupleParams C, const float* __restrict__ X, long long n_rows,
+                             float* __restrict__ Y) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const int n = P.n_cells;
+  const int c = (int)(r % n);
+  const double x0 = X[r * MLP_NIN], x4 = X[r * MLP_NIN + 4];
+  bool ok = C.nbar[c] > 0.0 && x0 > 0.0 && x4 > 0.0;
+  double y[MLP_NOUT];
+  if (ok) {
+    double o[6], H[12];
+    hot_cell(P, C, c, o, H);
+    const double s = x0 * x4, qn = s * sqrt(x4);
+    y[0] = H[0] / s;
+    y[1] = H[1] / s;
+    y[2] = H[3] / s;
+    y[3] = H[4] / s;
+    y[4] = H[5] / s;
+    y[5] = H[6] / qn;
+    y[6] = H[7] / qn;
+    y[7] = H[8] / qn;
+    for (int k = 0; k < MLP_NOUT && ok; ++k) ok = isfinite(y[k]) && isfinite((float)y[k]);
+  }
+  for (int k = 0; k < MLP_NOUT; ++k) Y[r * MLP_NOUT + k] = ok ? (float)y[k] : 0.0f;
+}
+
+// S12 in the coupling: a cell with a valid window and a finite prediction
+// within CLOSURE_YMAX takes the de-normalised prediction as its translational
+// HoT; sigma_zz = -(sigma_xx + sigma_yy); q_r keeps the sampled value
+__global__ void k_cl_apply(Params P, CoupleParams C, const float* __restrict__ Y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  const double rho = C.wnorm[c], T = C.wnorm[(size_t)n + c];
+  bool ok = rho > 0.0 && T > 0.0;
+  double y[MLP_NOUT];
+  for (int k = 0; k < MLP_NOUT; ++k) {
+    y[k] = Y[(size_t)c * MLP_NOUT + k];
+    ok = ok && isfinite(y[k]) && fabs(y[k]) <= CLOSURE_YMAX;
+  }
+  if (!ok) return;
+  const double s = rho * T, qn = s * sqrt(T);
+  double h[9];
+  h[0] = __dmul_rn(y[0], s);
+  h[1] = __dmul_rn(y[1], s);
+  h[2] = -__dadd_rn(h[0], h[1]);
+  h[3] = __dmul_rn(y[2], s);
+  h[4] = __dmul_rn(y[3], s);
+  h[5] = __dmul_rn(y[4], s);
+  for (int q = 0; q < 3; ++q) h[6 + q] = __dmul_rn(y[5 + q], qn);
+  for (int q = 0; q < 9; ++q) C.hot[(size_t)q * n + c] = h[q];
+  atomicAdd(C.stats + 4, 1ull);
 }
 
 // one reconstruction pass: a rejected cell with available face neighbours
@@ -678,11 +776,15 @@ __global__ void k_recal_clone(Params P, CoupleParams C, Buf CUR, const int* __re
 int nb_for(int n, int t) { return (n + t - 1) / t; }
 }  // namespace
 
-void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, cudaStream_t s) {
+void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const float* ypred, cudaStream_t s) {
   const int n = P.n_cells, nb = nb_for(n, CPT);
-  k_cp_extract<<<nb, CPT, 0, s>>>(P, C);
+  k_cp_extract<<<nb, CPT, 0, s>>>(P, C, P.phi_ewma, 1.0);
   k_cp_grad<<<nb, CPT, 0, s>>>(P, C, C.own, C.grad);
   k_cp_hot<<<nb, CPT, 0, s>>>(P, C);
+  if (ypred) {
+    k_cl_apply<<<nb, CPT, 0, s>>>(P, C, ypred);
+    ++g_launches;
+  }
   int* a = C.avail;
   int* b = C.avail2;
   for (int q = 0; q < passes; ++q) {
@@ -720,6 +822,27 @@ void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, i
   }
   k_recal_clone<<<nb_for(n, 256), 256, 0, s>>>(P, C, cur, cl, N, sub);
   g_launches += N > 0 ? 4 : 2;
+}
+
+void launch_closure_features(const Params& P, const CoupleParams& C, const double* phi, double cnt, float* X,
+                             cudaStream_t s) {
+  const int n = P.n_cells, nb = nb_for(n, CPT);
+  k_cp_extract<<<nb, CPT, 0, s>>>(P, C, phi, cnt);
+  k_cp_grad<<<nb, CPT, 0, s>>>(P, C, C.own, C.grad);
+  k_cl_features<<<nb, CPT, 0, s>>>(P, C, X);
+  g_launches += 3;
+}
+
+void launch_closure_targets(const Params& P, const CoupleParams& C, const double* phi, double cnt, const float* X,
+                            long long n_rows, float* Y, cudaStream_t s) {
+  const int n = P.n_cells, nb = nb_for(n, CPT);
+  k_cp_extract<<<nb, CPT, 0, s>>>(P, C, phi, cnt);
+  k_cp_grad<<<nb, CPT, 0, s>>>(P, C, C.own, C.grad);
+  g_launches += 2;
+  if (n_rows > 0) {
+    k_cl_targets<<<(unsigned)((n_rows + 255) / 256), 256, 0, s>>>(P, C, X, n_rows, Y);
+    ++g_launches;
+  }
 }
 
 size_t couple_part_count(int n_cells) { return 2 * (size_t)nb_for(n_cells, CPT) + 2; }

@@ -20,7 +20,10 @@ enum : int { ST_CELL_OVER_STAGE = 1, ST_CAPACITY = 2, ST_PAIRS_FULL = 4 };
 enum : int { C_STEPS, C_CAND, C_COLL, C_CROSS, C_WALL, C_REMOVED, C_INJECTED, C_STUCK, C_LB };
 // random-stream purposes: key = (seed_lo, seed_hi ^ purpose << 24)
 enum : uint32_t { RP_INIT_POS = 1, RP_INIT_VEL = 2, RP_WALL = 3, RP_INJECT = 4, RP_COLL = 5,
-                  RP_DIR = 6, RP_LB = 7, RP_RECAL = 8 };
+                  RP_DIR = 6, RP_LB = 7, RP_RECAL = 8, RP_MLP_INIT = 9 };
+// learned closure
+constexpr int MLP_NIN = 13, MLP_NOUT = 8, MLP_NPARAM = 9736;
+constexpr double CLOSURE_YMAX = 4.0;
 
 // FP64 face plane: outward unit normal (nx, ny, nz) and offset d, n.x = d on the face
 struct __align__(32) Plane64 {
@@ -125,13 +128,32 @@ struct CoupleParams {
   const double* bcn;   // [n_bcs]
   double *own, *sd, *grad, *half, *hot, *newst, *flag, *nbar, *U, *prim, *S, *R, *part, *mu;
   int *avail, *avail2;
-  unsigned long long* stats;  // rejected, reconstructed, cloned, deleted
+  float* feat;    // [n][13] closure inputs of the coupling window
+  float* ypred;   // [n][8] closure outputs
+  double* wnorm;  // [2][n] window density and temperature (0: invalid row)
+  unsigned long long* stats;  // rejected, reconstructed, cloned, deleted, learned
   CoupleScalars* scal;
   int* rpart;
   int* clone_total;
 };
 
-void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, cudaStream_t s);
+// S9; with ypred non-null the learned closure's outputs replace the HoT
+void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const float* ypred, cudaStream_t s);
+// closure inputs X[n][13] from sums phi over cnt steps (also fills C.wnorm)
+void launch_closure_features(const Params& P, const CoupleParams& C, const double* phi, double cnt, float* X,
+                             cudaStream_t s);
+// closure targets Y[n_rows][8] from sums phi over cnt steps and input rows X
+void launch_closure_targets(const Params& P, const CoupleParams& C, const double* phi, double cnt, const float* X,
+                            long long n_rows, float* Y, cudaStream_t s);
+// learned closure (dig_mlp.cu); params are the FP32 master parameters
+void launch_mlp_forward(const float* params, const float* X, long long n, float* Y, cudaStream_t s);
+void launch_mlp_train_step(const float* params, const float* X, const float* T, const int* perm, long long n_total,
+                           long long b0, long long nb, float* grad, double* loss, int* status, cudaStream_t s);
+void launch_mlp_loss(const float* params, const float* X, const float* T, long long n, int identity, double* acc,
+                     cudaStream_t s);
+void launch_adam(float* p, float* m, float* v, float* g, long long t, float lr, float b1, float b2, float eps,
+                 cudaStream_t s);
+void launch_mlp_init(const Params& P, uint64_t seed, float* params, cudaStream_t s);
 void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double eps, cudaStream_t s);
 void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, int N, uint32_t sub, int* cl,
                        cudaStream_t s);

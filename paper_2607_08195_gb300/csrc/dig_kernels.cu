@@ -25,6 +25,7 @@
 // the destination cells plus the arrival lists of the movers.
 #include "dig_internal.h"
 
+#include <cmath>
 #include <cstdio>
 
 namespace dig {
@@ -1446,6 +1447,56 @@ void launch_inject(const Params& P, const Buf& out, uint32_t step, int wallflux,
   else
     k_inj_gen<false><<<sms * 4, 256, 0, s>>>(P, out, step, wallflux);
   g_launches += 3;
+}
+
+namespace {
+// He-normal initialisation of the learned closure: weight k of the network
+// (layers in order, biases skipped) is the k-th value of the Gaussian pairs
+// drawn from the MLP_INIT stream with entity = the pair's first index;
+// std sqrt(2 / fan_in) per layer; biases zero
+__global__ void k_mlp_init(Params P, float* __restrict__ params, float sd_in, float sd_hid) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // pair index
+  constexpr int nW[4] = {64 * MLP_NIN, 64 * 64, 64 * 64, MLP_NOUT * 64};
+  constexpr int nb[4] = {64, 64, 64, MLP_NOUT};
+  const int idx = 2 * k;
+  int base = 0, poff = 0, l = 0;
+  for (; l < 4; ++l) {
+    if (idx < base + nW[l]) break;
+    base += nW[l];
+    poff += nW[l] + nb[l];
+  }
+  if (l < 4) {
+    float g1, g2;
+    gauss2(P, RP_MLP_INIT, (uint32_t)idx, 0, 0, 0, g1, g2);
+    const float sd = l == 0 ? sd_in : sd_hid;
+    const int i = idx - base;
+    params[poff + i] = sd * g1;
+    if (i + 1 < nW[l]) params[poff + i + 1] = sd * g2;
+  }
+  // biases
+  if (k < 64 * 3 + MLP_NOUT) {
+    int o = 0, j = k;
+    for (int q = 0; q < 4; ++q) {
+      o += nW[q];
+      if (j < nb[q]) {
+        params[o + j] = 0.0f;
+        break;
+      }
+      j -= nb[q];
+      o += nb[q];
+    }
+  }
+}
+}  // namespace
+
+void launch_mlp_init(const Params& P0, uint64_t seed, float* params, cudaStream_t s) {
+  Params P = P0;
+  P.seed_lo = (uint32_t)seed;
+  P.seed_hi = (uint32_t)(seed >> 32);
+  const float sd_in = (float)std::sqrt(2.0 / MLP_NIN), sd_hid = (float)std::sqrt(2.0 / 64);
+  const int pairs = (64 * MLP_NIN + 2 * 64 * 64 + MLP_NOUT * 64) / 2;
+  k_mlp_init<<<(pairs + 255) / 256, 256, 0, s>>>(P, params, sd_in, sd_hid);
+  ++g_launches;
 }
 
 void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* Is, int* cells, int n,

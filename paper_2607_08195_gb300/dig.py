@@ -39,16 +39,25 @@ class DigConfig(C.Structure):
         ("L_ref", C.c_double), ("n_a", C.c_int32), ("N_s", C.c_int32), ("N_m", C.c_int32),
         ("passes", C.c_int32), ("eps_m", C.c_double), ("KnD_max", C.c_double), ("capacity", C.c_int64),
         ("wait_timeout_s", C.c_double), ("stage_cap", C.c_int32), ("tile_cells", C.c_int32),
-        ("cta_threads", C.c_int32), ("pad1", C.c_int32),
+        ("cta_threads", C.c_int32), ("closure", C.c_int32),
     ]
 
 
 class CoupleReport(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("pad", C.c_int32), ("residual", C.c_double), ("n_rejected", C.c_int64),
+    _fields_ = [("iters", C.c_int32), ("n_learned", C.c_int32), ("residual", C.c_double), ("n_rejected", C.c_int64),
                 ("n_reconstructed", C.c_int64), ("n_cloned", C.c_int64), ("n_deleted", C.c_int64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TrainConfig(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("perm", C.c_void_p)]
+
+
+MLP_NIN, MLP_NOUT, MLP_NPARAM = 13, 8, 9736
+CLOSURE_YMAX = 4.0
 
 
 class DigBC(C.Structure):
@@ -62,7 +71,9 @@ EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mes
            "read_moments", "read_pairs", "read_counters", "dig_cell_state", "dig_wall_flux",
            "dig_particle_count", "dig_synchronize", "dig_launch_count", "dig_kernel_time",
            "dig_sort_scratch_bytes", "dig_sort_by_cell", "dig_sort_by_cell_noalloc", "dig_couple",
-           "dig_read_couple", "dig_write_moments", "dig_write_wall_flux"]
+           "dig_read_couple", "dig_write_moments", "dig_write_wall_flux", "closure_init", "closure_set",
+           "closure_get", "closure_features", "closure_targets", "closure_forward", "closure_loss", "closure_grad",
+           "closure_train"]
 
 _lib = None
 
@@ -89,6 +100,10 @@ def load_library(path: str = LIB_PATH):
         "dig_sort_by_cell_noalloc": [P, I64, I32, P, P, P],
         "dig_couple": [P, P], "dig_read_couple": [P, I32, P, I64], "dig_write_moments": [P, I32, P],
         "dig_write_wall_flux": [P, P, I64],
+        "closure_init": [P, C.c_uint64], "closure_set": [P, P, I64], "closure_get": [P, P, I64],
+        "closure_features": [P, I32, P], "closure_targets": [P, I32, P, I64, P], "closure_forward": [P, P, I64, P],
+        "closure_loss": [P, P, P, I64, I32, P], "closure_grad": [P, P, P, I64, P, P],
+        "closure_train": [P, P, P, P, I64, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -285,6 +300,90 @@ class Solver:
         n = C.c_int64(0)
         self._check(self.L.dig_launch_count(self.h, C.byref(n)))
         return n.value
+
+    # ---------------------------------------------------------------- learned closure
+    def _dev(self, t, dtype, cols=None):
+        import torch
+
+        assert t.is_cuda and t.dtype == dtype and t.is_contiguous(), "expected a contiguous device tensor"
+        if cols is not None:
+            assert t.dim() == 2 and t.shape[1] == cols
+        return C.c_void_p(t.data_ptr())
+
+    def closure_init(self, seed):
+        self._check(self.L.closure_init(self.h, seed))
+
+    def closure_set(self, params):
+        params = np.ascontiguousarray(params, np.float32)
+        self._check(self.L.closure_set(self.h, _p(params), params.size))
+
+    def closure_get(self):
+        p = np.zeros(MLP_NPARAM, np.float32)
+        self._check(self.L.closure_get(self.h, _p(p), p.size))
+        return p
+
+    def closure_features(self, which, X=None):
+        """X[n_tets][13] (device tensor, filled) from the sums `which`."""
+        import torch
+
+        if X is None:
+            X = torch.empty((self.n_tets, MLP_NIN), dtype=torch.float32, device=self.device)
+        assert X.shape[0] == self.n_tets
+        self._check(self.L.closure_features(self.h, which, self._dev(X, torch.float32, MLP_NIN)))
+        return X
+
+    def closure_targets(self, which, X, Y=None):
+        import torch
+
+        if Y is None:
+            Y = torch.empty((X.shape[0], MLP_NOUT), dtype=torch.float32, device=self.device)
+        self._check(self.L.closure_targets(self.h, which, self._dev(X, torch.float32, MLP_NIN), X.shape[0],
+                                           self._dev(Y, torch.float32, MLP_NOUT)))
+        return Y
+
+    def closure_forward(self, X, Y=None):
+        import torch
+
+        if Y is None:
+            Y = torch.empty((X.shape[0], MLP_NOUT), dtype=torch.float32, device=self.device)
+        self._check(self.L.closure_forward(self.h, self._dev(X, torch.float32, MLP_NIN), X.shape[0],
+                                           self._dev(Y, torch.float32, MLP_NOUT)))
+        return Y
+
+    def closure_loss(self, X, Y, identity=False):
+        import torch
+
+        loss = C.c_double(0)
+        self._check(self.L.closure_loss(self.h, self._dev(X, torch.float32, MLP_NIN),
+                                        self._dev(Y, torch.float32, MLP_NOUT), X.shape[0], int(identity),
+                                        C.byref(loss)))
+        return loss.value
+
+    def closure_grad(self, X, Y):
+        import torch
+
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = C.c_double(0)
+        self._check(self.L.closure_grad(self.h, self._dev(X, torch.float32, MLP_NIN),
+                                        self._dev(Y, torch.float32, MLP_NOUT), X.shape[0], _p(g),
+                                        C.byref(loss)))
+        return loss.value, g
+
+    def closure_train(self, X, Y, epochs, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, perm=None):
+        """Adam over mini-batches; perm: device int32 [epochs][n] row orders
+        (None: rows in order).  Returns the per-epoch training losses."""
+        import torch
+
+        n = X.shape[0]
+        cfg = TrainConfig()
+        cfg.epochs, cfg.batch, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps = epochs, batch, lr, beta1, beta2, eps
+        if perm is not None:
+            assert perm.shape == (epochs, n)
+            cfg.perm = self._dev(perm, torch.int32).value
+        loss = np.zeros(epochs, np.float64)
+        self._check(self.L.closure_train(self.h, C.byref(cfg), self._dev(X, torch.float32, MLP_NIN),
+                                         self._dev(Y, torch.float32, MLP_NOUT), n, _p(loss)))
+        return loss
 
 
 def sort_by_cell(cell, n_cells: int, stream=None):

@@ -79,3 +79,35 @@ def test_mesh_load_host_validation(lib):
     assert lib.dig_arena_bytes(h, ctypes.byref(nb)) == 0
     assert nb.value > 40 * cfg.capacity * 2
     lib.dig_destroy(h)
+
+
+def test_closure_structs_layout():
+    assert ctypes.sizeof(dig.TrainConfig) == 4 * 2 + 8 * 4 + 8
+    assert ctypes.sizeof(dig.CoupleReport) == 4 * 2 + 8 + 8 * 4
+
+
+def test_closure_host_validation(lib):
+    """The closure entry points validate their arguments on the host: a wrong
+    parameter count or training constants are rejected before any GPU work,
+    and calls before an arena is bound report DIG_ERR_STATE."""
+    import numpy as np
+
+    from paper_2607_08195_gb300 import workload as W
+
+    s = W.config_small()
+    cfg = dig.make_config(s)
+    h = ctypes.c_void_p()
+    assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    p = np.zeros(dig.MLP_NPARAM, np.float32)
+    assert lib.closure_set(h, p.ctypes.data, dig.MLP_NPARAM - 1) == -1
+    assert lib.closure_set(h, p.ctypes.data, dig.MLP_NPARAM) == -7
+    assert lib.closure_init(h, 3) == -7
+    tc = dig.TrainConfig()
+    tc.epochs, tc.batch, tc.lr, tc.beta1, tc.beta2, tc.eps = 0, 16, 1e-3, 0.9, 0.999, 1e-8
+    loss = np.zeros(1)
+    fake = ctypes.c_void_p(256)  # never dereferenced: the call fails validation first
+    assert lib.closure_train(h, ctypes.byref(tc), fake, fake, 10, loss.ctypes.data) == -1
+    tc.epochs, tc.beta1 = 1, 1.0
+    assert lib.closure_train(h, ctypes.byref(tc), fake, fake, 10, loss.ctypes.data) == -1
+    assert lib.closure_features(h, 7, fake) == -1
+    assert lib.dig_destroy(h) == 0

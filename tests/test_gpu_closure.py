@@ -1,0 +1,246 @@
+"""Learned closure (S12/S13) on the GPU through the C ABI, against the oracle.
+
+The network runs in BF16 with FP32 accumulation on the tensor cores; the
+oracle rounds weights and activations to BF16 the same way but accumulates in
+FP64, so outputs and gradients are compared within 1e-2 relative (a BF16
+activation that rounds the other way moves an output by about 2^-9 of its
+scale).  Inputs, targets and the coupling fields are FP64 arithmetic on both
+sides and are compared within FP32 / FP64 tolerances.
+"""
+import numpy as np
+import pytest
+
+from oracle import orc
+from paper_2607_08195_gb300 import workload as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2607_08195_gb300 import dig  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def solver():
+    s = W.config_small(seed=41)
+    g = dig.Solver(s, DEV)
+    yield g
+    g.close()
+
+
+def random_net(seed, bias=0.05, scale=1.0):
+    rng = np.random.default_rng(seed)
+    p = orc.mlp_init(seed) * np.float32(scale)
+    p += (bias * rng.standard_normal(len(p))).astype(np.float32)
+    return p
+
+
+def test_init_is_bit_exact(solver):
+    """He-normal initialisation from the MLP_INIT stream: identical parameters."""
+    for seed in (3, 2 ** 40 + 7):
+        solver.closure_init(seed)
+        assert np.array_equal(solver.closure_get(), orc.mlp_init(seed))
+
+
+@pytest.mark.parametrize("n", [1, 64, 1000, 4096 + 37])
+def test_forward_parity(solver, n):
+    """Forward pass on rows spanning several 64-row tiles and a ragged tail."""
+    p = random_net(n)
+    solver.closure_set(p)
+    rng = np.random.default_rng(n + 1)
+    X = rng.standard_normal((n, 13)).astype(np.float32)
+    Yg = solver.closure_forward(torch.from_numpy(X).to(DEV)).cpu().numpy().astype(np.float64)
+    Yo = orc.mlp_forward(p, X, bf16=True)
+    scale = np.abs(Yo).max()
+    assert np.abs(Yg - Yo).max() <= 1e-2 * scale, np.abs(Yg - Yo).max() / scale
+    assert np.abs(Yg - Yo).mean() <= 2e-3 * scale
+    # the FP64 network without BF16 is farther away than the BF16 oracle
+    Y64 = orc.mlp_forward(p, X, bf16=False)
+    assert np.abs(Yg - Yo).mean() < np.abs(Yg - Y64).mean()
+
+
+def test_gradient_parity(solver):
+    """Backward pass: gradient of the mean-square loss over 777 rows, layer by
+    layer within 1e-2 relative L2; the loss within 1e-3."""
+    p = random_net(9)
+    solver.closure_set(p)
+    rng = np.random.default_rng(10)
+    X = rng.standard_normal((777, 13)).astype(np.float32)
+    T = (0.5 * rng.standard_normal((777, 8))).astype(np.float32)
+    lg, gg = solver.closure_grad(torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV))
+    lo, go = orc.mlp_grad(p, X, T, bf16=True)
+    assert abs(lg - lo) <= 1e-3 * lo
+    off = 0
+    for nin, nout in ((13, 64), (64, 64), (64, 64), (64, 8)):
+        for size in (nin * nout, nout):
+            a, b = gg[off:off + size].astype(np.float64), go[off:off + size]
+            assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b), (off, np.linalg.norm(a - b) / np.linalg.norm(b))
+            off += size
+    assert off == dig.MLP_NPARAM
+    # the gradient buffer is cleared afterwards: a second call gives the same
+    lg2, gg2 = solver.closure_grad(torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV))
+    assert np.array_equal(gg, gg2) or np.abs(gg - gg2).max() <= 1e-6 * np.abs(gg).max()
+
+
+def test_adam_training_follows_oracle(solver):
+    """Five Adam steps on mini-batches in a given row order: the per-epoch loss
+    and the parameters track the oracle (FP64 Adam on its own gradients)."""
+    p = random_net(12, scale=0.5)
+    rng = np.random.default_rng(13)
+    n, batch = 640, 128
+    X = rng.standard_normal((n, 13)).astype(np.float32)
+    T = (0.3 * rng.standard_normal((n, 8))).astype(np.float32)
+    perm = rng.permutation(n).astype(np.int32)
+    solver.closure_set(p)
+    lr = 1e-3
+    loss = solver.closure_train(torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV), epochs=1, batch=batch,
+                                lr=lr, perm=torch.from_numpy(perm[None, :]).to(DEV))
+    q = p.copy()
+    m = np.zeros(len(q))
+    v = np.zeros(len(q))
+    sse = 0.0
+    for k, b0 in enumerate(range(0, n, batch)):
+        rows = perm[b0:b0 + batch]
+        l, g = orc.mlp_grad(q, X[rows], T[rows], bf16=True)
+        sse += l * len(rows)
+        orc.adam(q, m, v, g, k + 1, lr=lr)
+    assert abs(loss[0] - sse / n) <= 2e-3 * (sse / n)
+    pg = solver.closure_get()
+    step = np.abs(q.astype(np.float64) - p)
+    diff = np.abs(pg.astype(np.float64) - q)
+    # Adam moves each parameter by about lr per step; BF16 noise in tiny
+    # gradients can change the direction of a few of them
+    assert np.mean(diff <= 0.1 * 5 * lr) > 0.97, np.mean(diff <= 0.1 * 5 * lr)
+    assert np.median(step) > 0.5 * lr
+
+
+def test_train_rejects_bad_perm(solver):
+    """A perm entry outside [0, n) is caught on the device: DIG_ERR_ARG."""
+    solver.closure_init(1)
+    X = torch.zeros((100, 13), device=DEV)
+    T = torch.zeros((100, 8), device=DEV)
+    perm = torch.arange(100, dtype=torch.int32, device=DEV)[None, :].clone()
+    perm[0, 17] = 100
+    with pytest.raises(dig.DigError) as e:
+        solver.closure_train(X, T, epochs=1, batch=32, perm=perm)
+    assert e.value.code == -1
+
+
+def test_loss_matches_oracle(solver):
+    p = random_net(21)
+    solver.closure_set(p)
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((1500, 13)).astype(np.float32)
+    T = rng.standard_normal((1500, 8)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV)
+    lo = orc.mlp_grad(p, X, T, bf16=True)[0]
+    assert abs(solver.closure_loss(Xd, Td) - lo) <= 1e-3 * lo
+    li = ((X[:, 5:13].astype(np.float64) - T) ** 2).mean()
+    assert abs(solver.closure_loss(Xd, Td, identity=True) - li) <= 1e-12 * li
+
+
+def window_state(scen, steps, **over):
+    """Oracle after `steps` steps with moving average, window and cumulative
+    sums; returns it with its particles, sums and wall fluxes."""
+    o = orc.Oracle(scen, **over)
+    o.init()
+    o.step(steps, orc.EWMA | orc.WINDOW | orc.CUMUL)
+    return o, o.read(), {w: o.moments(w) for w in (orc.PHI_EWMA, orc.PHI_WINDOW, orc.PHI_CUM)}, o.wall_flux()
+
+
+def gpu_with_state(scen, steps, parts, phis, wf, **over):
+    g = dig.Solver(scen, DEV, **over)
+    g.init()
+    g.step(steps, dig.WINDOW | dig.CUMUL | dig.SYNC)  # window / cumulative step counts as the oracle's
+    g.write(*parts)
+    for w, ph in phis.items():
+        g.write_moments(w, ph)
+    g.write_wall_flux(wf, steps)
+    return g
+
+
+def test_features_and_targets_parity():
+    """S12 inputs from the window sums and S13 targets from the cumulative sums
+    of an identical state, over stacked rows with invalid ones."""
+    s = W.cavity_scenario(4, 24_000, 0.1, seed=19)
+    o, parts, phis, wf = window_state(s, 30)
+    g = gpu_with_state(s, 30, parts, phis, wf)
+    Xg = g.closure_features(dig.PHI_WINDOW).cpu().numpy()
+    Xo = o.closure_features(orc.PHI_WINDOW)
+    assert np.all(np.abs(Xg - Xo) <= 1e-5 * np.abs(Xo).max(axis=0) + 1e-7), np.abs(Xg - Xo).max(axis=0)
+    assert np.all(Xo[:, 0] > 0)
+    Xs = np.concatenate([Xo, 1.1 * Xo, Xo])
+    Xs[len(Xo) + 3] = 0.0
+    Yg = g.closure_targets(dig.PHI_CUM, torch.from_numpy(Xs).to(DEV)).cpu().numpy()
+    Yo = o.closure_targets(orc.PHI_CUM, Xs)
+    assert np.all(Yg[len(Xo) + 3] == 0)
+    assert np.all(np.abs(Yg - Yo) <= 1e-5 * np.abs(Yo).max(axis=0) + 1e-7), np.abs(Yg - Yo).max(axis=0)
+
+
+def test_coupling_with_learned_closure_parity():
+    """dig_couple with the learned closure: the same cells take the network's
+    HoT (the rest fall back to the sampled HoT), HoT and M^{k+1} agree within
+    the BF16 tolerance."""
+    s = W.cavity_scenario(4, 24_000, 0.1, seed=23)
+    over = dict(N_m=60, passes=2, KnD_max=1.0, closure=1)
+    o, parts, phis, wf = window_state(s, 40, **over)
+    g = gpu_with_state(s, 40, parts, phis, wf, **over)
+    p = random_net(31, scale=0.2, bias=0.01)
+    o.closure_set(p)
+    g.closure_set(p)
+    rg, ro = g.couple(), o.couple()
+    assert ro["n_learned"] > 0.9 * o.n_tets
+    assert abs(rg["n_learned"] - ro["n_learned"]) <= 2
+    assert rg["n_rejected"] == ro["n_rejected"] and rg["iters"] == ro["iters"]
+    Hg, Ho = g.read_couple(1), o.read_couple(1)
+    sc = np.abs(Ho).max(axis=0) + 1e-30
+    assert np.all(np.abs(Hg - Ho) <= 2e-2 * sc), (np.abs(Hg - Ho) / sc).max(axis=0)
+    Mg, Mo = g.read_couple(2), o.read_couple(2)
+    assert np.all(np.abs(Mg - Mo) <= 2e-3 * (np.abs(Mo).max(axis=0) + 1e-3)), np.abs(Mg - Mo).max(axis=0)
+    # without the network the coupling is the plain DIG coupling
+    g2 = gpu_with_state(s, 40, parts, phis, wf, **dict(over, closure=0))
+    g2.closure_set(p)
+    assert g2.couple()["n_learned"] == 0
+
+
+def test_trained_closure_beats_window_average():
+    """S13 end to end on the GPU: cell data generated by the solver (50-step
+    windows as inputs, the long-time average as target), trained with the
+    library's own kernels, reduces the error of the HoT against the long-time
+    average on held-out windows well below that of the window HoT itself (the
+    method without the network); the coupling then uses it."""
+    s = W.cavity_scenario(6, 130_000, 0.1, seed=29)
+    g = dig.Solver(s, DEV, N_m=100, closure=1)
+    g.init()
+    g.step(600, dig.EWMA)
+    g.sample(dig.RESET_CUMUL)
+    n, nwin, wsteps = g.n_tets, 100, 25
+    X = torch.empty((nwin * n, 13), dtype=torch.float32, device=DEV)
+    for w in range(nwin):
+        g.sample(dig.RESET_WINDOW)
+        g.step(wsteps, dig.EWMA | dig.WINDOW | dig.CUMUL)
+        g.closure_features(dig.PHI_WINDOW, X[w * n:(w + 1) * n])
+    Y = g.closure_targets(dig.PHI_CUM, X)
+    ntr = 80 * n
+    Xtr, Ytr, Xva, Yva = X[:ntr].contiguous(), Y[:ntr].contiguous(), X[ntr:].contiguous(), Y[ntr:].contiguous()
+    assert torch.all(Xva[:, 0] > 0)
+    g.closure_init(5)
+    epochs = 8
+    rng = np.random.default_rng(6)
+    perm = torch.from_numpy(np.stack([rng.permutation(ntr) for _ in range(epochs)]).astype(np.int32)).to(DEV)
+    loss = g.closure_train(Xtr, Ytr, epochs=epochs, batch=512, lr=2e-3, perm=perm)
+    assert loss[-1] < 0.5 * loss[0], loss
+    net = g.closure_loss(Xva, Yva)
+    raw = g.closure_loss(Xva, Yva, identity=True)
+    print(f"closure gain: train loss {loss[0]:.3e} -> {loss[-1]:.3e}; held-out MSE net {net:.3e} "
+          f"vs window HoT {raw:.3e} (ratio {net / raw:.3f})")
+    assert net < 0.6 * raw, (net, raw)
+    # the coupling takes the trained closure's HoT
+    g.sample(dig.RESET_WINDOW)
+    g.step(wsteps, dig.EWMA | dig.WINDOW | dig.WALLFLUX)
+    r = g.couple()
+    assert r["n_learned"] > 0.9 * n and r["iters"] > 0
