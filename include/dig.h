@@ -109,9 +109,10 @@ typedef struct dig_config {
   double KnD_max;    /* threshold of the cell Knudsen criterion */
   int64_t capacity;  /* particle capacity of the arena */
   double wait_timeout_s; /* time limit of host waits (<= 0: 600 s) */
-  int32_t stage_cap;     /* particles staged in shared memory per CTA (<= 0: 3072) */
-  int32_t tile_cells;    /* cells per CTA of the cell pass (<= 0: chosen from the load) */
-  int32_t cta_threads;   /* threads per CTA of the cell pass: 64, 128 or 256 (<= 0: 256) */
+  int32_t stage_cap;     /* particles per CTA the move kernel's tile of cells aims at: tile = 0.75 stage_cap /
+                            mean particles per cell (<= 0: 3072; at most 8192) */
+  int32_t tile_cells;    /* cells per CTA of the move kernel (<= 0: chosen from stage_cap and the load) */
+  int32_t cta_threads;   /* threads per CTA of the move kernel: 64, 128 or 256 (<= 0: 256) */
   int32_t closure;       /* 1: dig_couple takes the HoT from the learned closure (see closure_*) */
 } dig_config;
 

@@ -161,7 +161,8 @@ const char* dig_last_error(dig_ctx* ctx) { return ctx ? ctx->err : g_err; }
 
 int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (!cfg || !out) return DIG_ERR_ARG;
-  if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || (cfg->rot_dof != 0 && cfg->rot_dof != 2))
+  if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || (cfg->rot_dof != 0 && cfg->rot_dof != 2) ||
+      cfg->stage_cap > 8192)
     return DIG_ERR_ARG;
   dig_ctx* c = new dig_ctx();
   c->cfg = *cfg;
@@ -438,6 +439,8 @@ static size_t layout(dig_ctx* ctx, char* base) {
   P.na = A.take<int>(n);
   P.fill = A.take<int>(n);
   P.aq = A.take<int>(cap);
+  P.tq = A.take<int>(2 * cap);
+  P.src = A.take<int>(cap);
   P.cmax = A.take<float>(n);
   P.rem = A.take<double>(n);
   P.phi_inst = A.take<double>(NPHI * n);
@@ -634,8 +637,6 @@ static int check_status(dig_ctx* ctx) {
   int rc = wait_stream(ctx);
   if (rc) return rc;
   if (st[0] & ST_CAPACITY) return fail(ctx, DIG_ERR_CAPACITY, "particle count exceeded the capacity");
-  if (st[0] & ST_CELL_OVER_STAGE)
-    return fail(ctx, DIG_ERR_CAPACITY, "a cell holds more particles than the shared-memory stage (stage_cap)");
   if (cnt[C_STUCK] > 0) return fail(ctx, DIG_ERR_STUCK, "particles exceeded the face-crossing limit");
   return DIG_OK;
 }
@@ -678,7 +679,7 @@ static void pass(dig_ctx* ctx, int pass_flags, int sflags, uint32_t step_coll, u
   const int other = 1 - ctx->cur;
   if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
   launch_cell_pass(ctx->P, ctx->buf[ctx->cur], ctx->buf[other], pass_flags, sflags, step_coll, step_move,
-                   ewma_first, ctx->tile_cells, ctx->stage_cap, ctx->cta_threads, ctx->stream);
+                   ewma_first, ctx->tile_cells, ctx->cta_threads, ctx->stream);
   if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
   if (pass_flags & PASS_MOVE)
     launch_inject(ctx->P, ctx->buf[other], step_move, (sflags & S_WALLFLUX) != 0, ctx->stream);

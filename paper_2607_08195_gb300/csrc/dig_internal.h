@@ -15,7 +15,7 @@ enum : int { PASS_COLLIDE = 1, PASS_MOVE = 2 };
 // sampling flags (same bits as the public DIG_* flags)
 enum : int { S_EWMA = 1, S_WINDOW = 2, S_CUMUL = 4, S_PAIRS = 8, S_INST = 16, S_WALLFLUX = 32 };
 // device status bits
-enum : int { ST_CELL_OVER_STAGE = 1, ST_CAPACITY = 2, ST_PAIRS_FULL = 4 };
+enum : int { ST_CAPACITY = 2, ST_PAIRS_FULL = 4 };
 // counters
 enum : int { C_STEPS, C_CAND, C_COLL, C_CROSS, C_WALL, C_REMOVED, C_INJECTED, C_STUCK, C_LB };
 // random-stream purposes: key = (seed_lo, seed_hi ^ purpose << 24)
@@ -105,7 +105,9 @@ struct Params {
   double* phi_cum;
   unsigned long long* counters;  // [16]
   int* status;
-  int* state;   // [0] N, [1] extra_lo, [2] extra_hi
+  int* state;   // [0] N, [1] extra_lo, [2] extra_hi, [3] track-queue length
+  int* tq;      // [2 cap] track queue: (output slot, input slot) of each particle left to k_track
+  int* src;     // [cap] slot map of the pass: input slot of the particle at each output slot
   int* scan_part;
   int* pairs;   // [4 * pair_cap]
   unsigned char* pacc;
@@ -166,14 +168,13 @@ void launch_write(const Params& P, const Buf& out, const double* xs, const float
 void launch_scan(const Params& P, cudaStream_t s);
 void launch_scatter(const Params& P, const int* mc, cudaStream_t s);
 void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags,
-                      uint32_t step_coll, uint32_t step_move, int ewma_first, int tile_cells,
-                      int stage_cap, int threads, cudaStream_t s);
+                      uint32_t step_coll, uint32_t step_move, int ewma_first, int tile_cells, int threads,
+                      cudaStream_t s);
 void launch_inject(const Params& P, const Buf& out, uint32_t step, int wallflux, cudaStream_t s);
 void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* Is, int* cells,
                  int n, cudaStream_t s);
 void launch_moments_ex(const Params& P, const double* phi, double scale, int macro, double* out, double mass,
                        double FN, double kB, cudaStream_t s);
-size_t cell_pass_smem(int tile_cells, int stage_cap, bool diatomic);
 size_t sort_scratch_bytes(long long n, int n_cells);
 void launch_sort_by_cell(const int* cell, long long n, int n_cells, int* cell_start, int* order, char* scratch,
                          cudaStream_t s);

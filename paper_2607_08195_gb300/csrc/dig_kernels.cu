@@ -8,17 +8,24 @@
 // acceptance, wall re-emission) is a fixed sequence of IEEE operations.
 //
 // Step structure on the GPU (paper Sec. 2.1: move, then collide pairs of the
-// same cell, then sample; Sec. 4 keeps per-cell particle buckets):
-//   k_cell_pass  one CTA per tile of cells.  Gathers the tile's particles in
-//                the canonical order (stayers, then arrivals ranked by their
-//                previous slot) into shared memory, runs the NTC collisions
-//                one thread per cell, samples the moments, then moves every
-//                particle and writes it back to its canonical slot with the
-//                cell it ended in.  The move runs in two passes: all particles
-//                take the cheap path (x + v dt, FP32-proven inside test); the
-//                few that fail it are queued and tracked face by face, densely
-//                packed, so the FP64 work of crossings is not diluted by
-//                divergence (FP64 issues at 1/64 of the FP32 rate here).
+// same cell, then sample; Sec. 4 keeps per-cell particle buckets).  The
+// particles of cell c occupy slots [cs[c], cs[c+1]) of a buffer in the
+// canonical order: stayers of the last move in their previous order, then
+// arrivals in the order of their previous slot.
+//   k_order      warp per cell: the canonical order (stayers by ballot over
+//                the cell's old slot range, arrivals ranked by slot), written
+//                as the slot map src (output slot -> input slot), and the
+//                velocities (and I_r) gathered into the output buffer.
+//   k_collide    thread per cell over the whole mesh: the cell's NTC loop on
+//                its gathered velocities.  Every cell's serial candidate
+//                chain runs at once, so their latencies overlap.
+//   k_move       CTA per tile of cells: the cells' summation variables, then
+//                every particle's move x + v dt with the FP32-proven inside
+//                test, a proven one-crossing shortcut, and a queue of the rest.
+//   k_track      face-by-face tracking of the queued particles, thread per
+//                particle: the dependent mesh loads and FP64 tests of the
+//                crossings (FP64 issues at 1/64 of the FP32 rate here)
+//                overlap across many warps.
 //   k_scan_*     exclusive scans of (stayers + arrivals) and arrivals per cell.
 //   k_scatter    appends each mover to its destination cell's arrival list.
 // The counting sort of the particle loop therefore costs one 4-byte read of
@@ -566,55 +573,55 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
   P.cmax[cell] = cmax;
 }
 
-// per-cell summation variables, one warp per cell: FP32 partial sums per lane
-// (strided over the cell's particles) reduced across the warp, then FP64
-// across steps; lane q updates component q
+// per-cell summation variables of one cell, one warp: FP32 partial sums per
+// lane (strided over the cell's particles), then a reduce-scatter across the
+// warp (16 shuffles instead of one full reduction per component).  Returns
+// in lanes 2q and 2q+1 the cell's sum of component q + 1 (components 1..16:
+// v(3), vv (xx,yy,zz,xy,xz,yz), |v|^2 v(3), I, I v(3); 13..16 zero for a
+// monatomic gas).
 template <bool DIAT>
-__device__ void sample_cell_warp(const Params& P, int cell, const float* vx, const float* vy, const float* vz,
-                                 const float* I, int N, int sflags, int ewma_first, int lane) {
-  constexpr int np = DIAT ? 17 : 13;
-  float s[np];
+__device__ __forceinline__ float cell_sums_warp(const float* vx, const float* vy, const float* vz, const float* I,
+                                                int N, int lane) {
+  float s[16];
 #pragma unroll
-  for (int q = 0; q < np; ++q) s[q] = 0.0f;
+  for (int q = 0; q < 16; ++q) s[q] = 0.0f;
   for (int k = lane; k < N; k += 32) {
     const float x = vx[k], y = vy[k], z = vz[k];
     const float vv = x * x + y * y + z * z;
-    s[1] += x;
-    s[2] += y;
-    s[3] += z;
-    s[4] += x * x;
-    s[5] += y * y;
-    s[6] += z * z;
-    s[7] += x * y;
-    s[8] += x * z;
-    s[9] += y * z;
-    s[10] += vv * x;
-    s[11] += vv * y;
-    s[12] += vv * z;
+    s[0] += x;
+    s[1] += y;
+    s[2] += z;
+    s[3] += x * x;
+    s[4] += y * y;
+    s[5] += z * z;
+    s[6] += x * y;
+    s[7] += x * z;
+    s[8] += y * z;
+    s[9] += vv * x;
+    s[10] += vv * y;
+    s[11] += vv * z;
     if (DIAT) {
       const float e = I[k];
-      s[13] += e;
-      s[14] += e * x;
-      s[15] += e * y;
-      s[16] += e * z;
+      s[12] += e;
+      s[13] += e * x;
+      s[14] += e * y;
+      s[15] += e * z;
     }
   }
-  float mine = 0.0f;
+  // stage o: lanes with bit o set keep the upper half of their values, the
+  // others the lower half, each adding its partner's copy of what it keeps
 #pragma unroll
-  for (int q = 1; q < np; ++q) {
-    float v = s[q];
+  for (int st = 0; st < 4; ++st) {
+    const int o = 16 >> st, m = 8 >> st;
+    const bool up = (lane & o) != 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == q) mine = v;
+    for (int i = 0; i < m; ++i) {
+      const float send = up ? s[i] : s[i + m];
+      const float keep = up ? s[i + m] : s[i];
+      s[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
   }
-  if (lane < np) {
-    const size_t o = (size_t)lane * (size_t)P.n_cells + cell;
-    const double ph = lane == 0 ? (double)N : f2d(mine);
-    if (sflags & S_INST) P.phi_inst[o] = ph;
-    if (sflags & S_EWMA) P.phi_ewma[o] = ewma_first ? ph : __fma_rn(P.na_a, P.phi_ewma[o], P.na_b * ph);
-    if (sflags & S_WINDOW) P.phi_win[o] += ph;
-    if (sflags & S_CUMUL) P.phi_cum[o] += ph;
-  }
+  return s[0] + __shfl_xor_sync(0xffffffffu, s[0], 1);
 }
 
 __device__ __forceinline__ void flush_counters(const Params& P, const Cnt& c) {
@@ -631,266 +638,257 @@ __device__ __forceinline__ void flush_counters(const Params& P, const Cnt& c) {
 }
 
 // ---------------------------------------------------------------------------
-// the cell pass
+// the particle pass: k_order, k_collide, k_move
 // ---------------------------------------------------------------------------
 
-size_t cell_pass_smem(int TC, int CAP, bool diat) {
-  return sizeof(int) * (size_t)(5 * TC + 8) + (size_t)CAP * (2 * sizeof(int) + 3 * sizeof(float) + 1) +
-         (diat ? (size_t)CAP * sizeof(float) : 0) + 16;
-}
-
-// Layout of a particle buffer: the particles of cell c occupy slots
-// [cs[c], cs[c+1]) in canonical order (stayers of the last move first, in
-// their previous order, then arrivals in the order of their previous slot).
-// The pass writes every particle back to its canonical slot with mc[slot]
-// = the cell it is in after the move (-1: left the domain); the next pass
-// finds the stayers of cell c by mc == c over c's old range and the
-// arrivals from the lists built by k_scatter.
-// resident threads per SM the register budget of the cell pass is sized for
-#ifndef DIG_CP_RESIDENT
-#define DIG_CP_RESIDENT 768
-#endif
-
-template <bool DIAT, int CP_THREADS>
-__global__ void __launch_bounds__(CP_THREADS, DIG_CP_RESIDENT / CP_THREADS) k_cell_pass(Params P, Buf IN, Buf OUT, int pass, int sflags,
-                                                          uint32_t step_coll, uint32_t step_move,
-                                                          int ewma_first, int TC, int CAP) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  int* s_cs = (int*)smem;       // TC+1 canonical starts (global slots)
-  int* s_as = s_cs + TC + 1;    // TC+1 arrival starts
-  int* s_sb = s_as + TC + 1;    // TC old slot range start of each cell
-  int* s_no = s_sb + TC;        // TC old particle count of each cell
-  int* s_nst = s_no + TC;       // TC stayers counted in this pass
-  int* s_src = s_nst + TC;      // CAP: IN slot of each staged particle
-  int* s_q = s_src + CAP;       // CAP: slow-path queue
-  float* s_vx = (float*)(s_q + CAP);
-  float* s_vy = s_vx + CAP;
-  float* s_vz = s_vy + CAP;
-  float* s_I = s_vz + CAP;      // CAP if DIAT
-  unsigned char* s_cl = (unsigned char*)(DIAT ? s_I + CAP : s_I);  // local cell of each staged particle
-  __shared__ int s_g1, s_qn;
-
-  const int c0 = blockIdx.x * TC;
-  if (c0 >= P.n_cells) return;
-  const int nc = min(TC, P.n_cells - c0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = CP_THREADS / 32;
-  const bool do_coll = (pass & PASS_COLLIDE) != 0, do_move = (pass & PASS_MOVE) != 0;
-  const bool flux = (sflags & S_WALLFLUX) != 0;
+// Canonical order of every cell, warp per cell (grid-stride over cells).  The
+// stayers of cell c are the slots of its old range [sbase, sbase + nold) of
+// the input buffer whose mc is c (the move that wrote them left them in c),
+// in slot order; the arrivals are the aq entries of c (slots of particles
+// that moved into c, new particles included), ranked by slot.  Writes
+// src[cs[c] + k] and gathers velocities (and I_r) into the output buffer;
+// then records the new range as the cell's old range for the next pass.
+template <bool DIAT>
+__global__ void __launch_bounds__(256) k_order(Params P, Buf IN, Buf OUT) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     P.state[1] = 0;
     P.state[2] = 0;
   }
-  for (int i = threadIdx.x; i <= nc; i += CP_THREADS) {
-    s_cs[i] = P.cs[c0 + i];
-    s_as[i] = P.as[c0 + i];
-    if (i < nc) {
-      s_sb[i] = P.sbase[c0 + i];
-      s_no[i] = P.nold[c0 + i];
-      s_nst[i] = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = gw; c < P.n_cells; c += nw) {
+    const int base = P.cs[c], Nc = P.cs[c + 1] - base;
+    const int sb = P.sbase[c], no = P.nold[c];
+    int ns = 0;
+    for (int k0 = 0; k0 < no; k0 += 32) {
+      const int k = k0 + lane;
+      const bool st = k < no && IN.mc[sb + k] == c;
+      const unsigned bs = __ballot_sync(0xffffffffu, st);
+      const int pos = ns + __popc(bs & lt);
+      if (st && pos < Nc) P.src[base + pos] = sb + k;
+      ns += __popc(bs);
     }
+    const int a0 = P.as[c], na = P.as[c + 1] - a0;
+    if (na <= 32) {
+      const int key = lane < na ? P.aq[a0 + lane] : 0x7fffffff;
+      int rank = 0;
+      for (int r = 0; r < na; ++r) rank += (__shfl_sync(0xffffffffu, key, r) < key) ? 1 : 0;
+      if (lane < na && ns + rank < Nc) P.src[base + ns + rank] = key;
+    } else {
+      for (int r = lane; r < na; r += 32) {
+        const int key = P.aq[a0 + r];
+        int rank = 0;
+        for (int r2 = 0; r2 < na; ++r2) rank += (P.aq[a0 + r2] < key) ? 1 : 0;
+        if (ns + rank < Nc) P.src[base + ns + rank] = key;
+      }
+    }
+    __syncwarp();
+    for (int k = lane; k < Nc; k += 32) {
+      const int q = P.src[base + k];
+      OUT.vx[base + k] = IN.vx[q];
+      OUT.vy[base + k] = IN.vy[q];
+      OUT.vz[base + k] = IN.vz[q];
+      if (DIAT) OUT.Ir[base + k] = IN.Ir[q];
+    }
+    if (lane == 0) {
+      P.sbase[c] = base;
+      P.nold[c] = Nc;
+    }
+  }
+}
+
+// NTC collisions of every cell, thread per cell, on the gathered velocities
+template <bool DIAT>
+__global__ void __launch_bounds__(128) k_collide(Params P, Buf OUT, uint32_t step, int record) {
+  Cnt cnt;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < P.n_cells) {
+    const int base = P.cs[c], N = P.cs[c + 1] - base;
+    collide_cell<DIAT>(P, c, OUT.vx + base, OUT.vy + base, OUT.vz + base, DIAT ? OUT.Ir + base : nullptr, N, step,
+                       record != 0, cnt);
+  }
+  flush_counters(P, cnt);
+}
+
+// Sampling and move of a tile of TC cells.  Sampling: the FP32 sums of each
+// cell (warp per cell) into shared memory, then the FP64 accumulators with
+// coalesced accesses, thread per (component, cell).  Move: every particle of
+// the tile (its slots are contiguous): x' = x + v dt and the FP32 plane tests
+// of x' against its cell (plane_test32).  All four passed with the margin: it
+// stays.  Exactly one failed with the margin, the others passed and the
+// particle approaches that face: the segment x -> x' leaves through it (a
+// convex cell: the only half-space x' violates is the one the segment
+// crossed, and the margins order the FP64 hit times the same way), so if the
+// face is interior and x' passes the neighbour's other three tests, the
+// particle ends there after one crossing -- the result of the full tracking
+// rule.  Everything else (walls, several crossings, tests within the margin)
+// is queued (output slot, input slot) for k_track, its cell left in mc.
+template <bool DIAT, int NT>
+__global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass, int sflags, uint32_t step,
+                                             int ewma_first, int TC) {
+  extern __shared__ __align__(16) int smem_i[];
+  int* s_cs = smem_i;                      // TC + 1 slot starts
+  int* s_nst = s_cs + TC + 1;              // TC stayers
+  float* s_sum = (float*)(s_nst + TC);     // NPHI x TC cell sums
+  const int c0 = blockIdx.x * TC;
+  if (c0 >= P.n_cells) return;
+  const int nc = min(TC, P.n_cells - c0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = NT / 32;
+  for (int i = threadIdx.x; i <= nc; i += NT) {
+    s_cs[i] = P.cs[c0 + i];
+    if (i < nc) s_nst[i] = 0;
   }
   __syncthreads();
   Cnt cnt;
-  int g0 = 0;
-  while (g0 < nc) {
-    if (threadIdx.x == 0) {
-      int g1 = g0 + 1;
-      while (g1 < nc && s_cs[g1 + 1] - s_cs[g0] <= CAP) ++g1;
-      s_g1 = g1;
-      s_qn = 0;
+  if (pass & PASS_COLLIDE) {
+    constexpr int np = DIAT ? 17 : 13;
+    for (int c = warp; c < nc; c += nwarps) {
+      const int b = s_cs[c], N = s_cs[c + 1] - b;
+      const float t = cell_sums_warp<DIAT>(OUT.vx + b, OUT.vy + b, OUT.vz + b, DIAT ? OUT.Ir + b : nullptr, N, lane);
+      const int q = (lane >> 1) + 1;
+      if ((lane & 1) == 0 && q < np) s_sum[q * nc + c] = t;
     }
     __syncthreads();
-    const int g1 = s_g1;
-    const int gbase = s_cs[g0];
-    const int gN = s_cs[g1] - gbase;
-    if (gN > CAP) {
-      // one cell holds more particles than the stage: reported as an error;
-      // its slots are marked removed so that the buffer stays consistent
-      for (int k = threadIdx.x; k < gN; k += CP_THREADS) OUT.mc[gbase + k] = -1;
-      if (threadIdx.x == 0) atomicOr(P.status, ST_CELL_OVER_STAGE);
-      g0 = g1;
-      __syncthreads();
-      continue;
+    for (int i = threadIdx.x; i < np * nc; i += NT) {
+      const int q = i / nc, lc = i - q * nc;
+      const size_t o = (size_t)q * (size_t)P.n_cells + (size_t)(c0 + lc);
+      const double ph = q == 0 ? (double)(s_cs[lc + 1] - s_cs[lc]) : f2d(s_sum[i]);
+      if (sflags & S_INST) P.phi_inst[o] = ph;
+      if (sflags & S_EWMA) P.phi_ewma[o] = ewma_first ? ph : __fma_rn(P.na_a, P.phi_ewma[o], P.na_b * ph);
+      if (sflags & S_WINDOW) P.phi_win[o] += ph;
+      if (sflags & S_CUMUL) P.phi_cum[o] += ph;
     }
-    // 1. canonical order.  First stage, with coalesced loads by all threads, the
-    //    cell ids of the group's old slot range (contiguous: the cells' old
-    //    ranges are adjacent) and the group's arrival lists; then one warp per
-    //    cell finds the stayers by ballot and ranks the arrivals by slot.
-    {
-      const int olo = s_sb[g0], nO = s_sb[g1 - 1] + s_no[g1 - 1] - olo;
-      const bool stage_old = nO <= CAP;
-      int* s_mc = s_q;
-      int* s_aq = reinterpret_cast<int*>(s_vx);
-      const int alo = s_as[g0], nA = s_as[g1] - alo;
-      if (stage_old) {
-        for (int i0 = threadIdx.x; i0 < nO; i0 += 4 * CP_THREADS) {
-          int t[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) t[u] = i0 + u * CP_THREADS < nO ? IN.mc[olo + i0 + u * CP_THREADS] : 0;
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (i0 + u * CP_THREADS < nO) s_mc[i0 + u * CP_THREADS] = t[u];
-        }
+  }
+  const bool do_move = (pass & PASS_MOVE) != 0;
+  const int lo = s_cs[0], hi = s_cs[nc];
+  // loop bounds are warp-uniform: the ballots below see every lane
+  for (int b0 = lo + warp * 32; b0 < hi; b0 += NT) {
+    const int slot = b0 + lane;
+    const bool valid = slot < hi;
+    int lc = -1, st = -1, nb = -1;
+    if (valid) {
+      int l = 0, h = nc;  // the cell of the slot: last lc with s_cs[lc] <= slot
+      while (h - l > 1) {
+        const int m = (l + h) >> 1;
+        if (s_cs[m] <= slot)
+          l = m;
+        else
+          h = m;
       }
-      for (int i0 = threadIdx.x; i0 < nA; i0 += 4 * CP_THREADS) {
-        int t[4];
+      lc = l;
+      const int cell = c0 + lc;
+      const int q = P.src[slot];
+      double x = IN.x[q], y = IN.y[q], z = IN.z[q];
+      st = 0;
+      if (do_move) {
+        const float vx = OUT.vx[slot], vy = OUT.vy[slot], vz = OUT.vz[slot];
+        x = __fma_rn(f2d(vx), P.dt, x);
+        y = __fma_rn(f2d(vy), P.dt, y);
+        z = __fma_rn(f2d(vz), P.dt, z);
+        const float4* pf = P.plane32 + 4 * (size_t)cell;
+        const float fx = d2f_trunc(x), fy = d2f_trunc(y), fz = d2f_trunc(z);
+        int nok = 0, nout = 0, fo = 0;
+        float4 qo = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) t[u] = i0 + u * CP_THREADS < nA ? P.aq[alo + i0 + u * CP_THREADS] : 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (i0 + u * CP_THREADS < nA) s_aq[i0 + u * CP_THREADS] = t[u];
-      }
-      __syncthreads();
-      for (int c = g0 + warp; c < g1; c += nwarps) {
-        const int cell = c0 + c, cb = s_cs[c] - gbase, Nc = s_cs[c + 1] - s_cs[c];
-        const int sb = s_sb[c], no = s_no[c];
-        int ns = 0;
-        for (int k0 = 0; k0 < no; k0 += 32) {
-          const int k = k0 + lane;
-          const bool st = k < no && (stage_old ? s_mc[sb - olo + k] : IN.mc[sb + k]) == cell;
-          const unsigned bs = __ballot_sync(0xffffffffu, st);
-          if (st) s_src[cb + ns + __popc(bs & ((1u << lane) - 1u))] = sb + k;
-          ns += __popc(bs);
-        }
-        const int a0 = s_as[c] - alo, na = s_as[c + 1] - s_as[c];
-        if (na <= 32) {
-          const int key = lane < na ? s_aq[a0 + lane] : 0x7fffffff;
-          int rank = 0;
-          for (int r = 0; r < na; ++r) rank += (__shfl_sync(0xffffffffu, key, r) < key) ? 1 : 0;
-          if (lane < na) s_src[cb + ns + rank] = key;
-        } else {
-          for (int r = lane; r < na; r += 32) {
-            const int key = s_aq[a0 + r];
-            int rank = 0;
-            for (int r2 = 0; r2 < na; ++r2) rank += (s_aq[a0 + r2] < key) ? 1 : 0;
-            s_src[cb + ns + rank] = key;
+        for (int f = 0; f < 4; ++f) {
+          const float4 pq = pf[f];
+          const float t = plane_test32(pq, fx, fy, fz);
+          if (t > P.margin) {
+            ++nok;
+          } else if (t < -P.margin) {
+            ++nout;
+            fo = f;
+            qo = pq;
           }
         }
-        for (int kk = lane; kk < Nc; kk += 32) s_cl[cb + kk] = (unsigned char)(c - g0);
-      }
-    }
-    __syncthreads();
-    // 2. gather velocities (and rotational energies)
-    for (int k0 = threadIdx.x; k0 < gN; k0 += 4 * CP_THREADS) {
-      int sidx[4];
-      float ga[4], gb[4], gc[4], gd[4];
+        if (nok != 4) {
+          st = 2;
+          // the crossed face must also be approached: n.v > 0 proven in FP32
+          const float bo = __fmaf_rn(qo.z, vz, __fmaf_rn(qo.y, vy, qo.x * vx));
+          const float eb = 8.0f * 5.9604645e-08f * (fabsf(vx) + fabsf(vy) + fabsf(vz)) + 1e-30f;
+          if (nout == 1 && nok == 3 && bo > eb) {
+            nb = __ldg(P.nbr + 4 * (size_t)cell + fo);
+            if (nb >= 0) {
+              const int en = __ldg(P.nbrf + 4 * (size_t)cell + fo);
+              const float4* pn = P.plane32 + 4 * (size_t)nb;
+              bool in = true;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) sidx[u] = k0 + u * CP_THREADS < gN ? s_src[k0 + u * CP_THREADS] : -1;
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (sidx[u] >= 0) {
-          ga[u] = IN.vx[sidx[u]];
-          gb[u] = IN.vy[sidx[u]];
-          gc[u] = IN.vz[sidx[u]];
-          if (DIAT) gd[u] = IN.Ir[sidx[u]];
-        }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (sidx[u] >= 0) {
-          const int k = k0 + u * CP_THREADS;
-          s_vx[k] = ga[u];
-          s_vy[k] = gb[u];
-          s_vz[k] = gc[u];
-          if (DIAT) s_I[k] = gd[u];
-        }
-    }
-    __syncthreads();
-    // 3. collisions and sampling, one thread per cell
-    if (do_coll) {
-      const bool rec = (sflags & S_PAIRS) != 0;
-      for (int c = g0 + threadIdx.x; c < g1; c += CP_THREADS) {
-        const int cb = s_cs[c] - gbase, N = s_cs[c + 1] - s_cs[c];
-        collide_cell<DIAT>(P, c0 + c, s_vx + cb, s_vy + cb, s_vz + cb, DIAT ? s_I + cb : nullptr, N, step_coll,
-                           rec, cnt);
-      }
-      __syncthreads();
-      for (int c = g0 + warp; c < g1; c += nwarps) {
-        const int cb = s_cs[c] - gbase, N = s_cs[c + 1] - s_cs[c];
-        sample_cell_warp<DIAT>(P, c0 + c, s_vx + cb, s_vy + cb, s_vz + cb, DIAT ? s_I + cb : nullptr, N, sflags,
-                               ewma_first, lane);
-      }
-      __syncthreads();
-    }
-    // 4a. move, fast path for every particle: x' = x + v dt, proven inside by
-    //     the FP32 plane test; the others go to the queue
-    for (int k0 = threadIdx.x; k0 < gN; k0 += 4 * CP_THREADS) {
-      // positions of four particles in flight at once
-      double X[4], Y[4], Z[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int k = k0 + u * CP_THREADS;
-        if (k < gN) {
-          const int s = s_src[k];
-          X[u] = IN.x[s];
-          Y[u] = IN.y[s];
-          Z[u] = IN.z[s];
+              for (int f = 0; f < 4; ++f)
+                if (f != en && !(plane_test32(pn[f], fx, fy, fz) > P.margin)) in = false;
+              if (in) st = 1;
+            }
+          }
         }
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int k = k0 + u * CP_THREADS;
-        if (k >= gN) continue;
-        const int lc = s_cl[k], cell = c0 + g0 + lc, slot = gbase + k;
-        double x = X[u], y = Y[u], z = Z[u];
-        const float vx = s_vx[k], vy = s_vy[k], vz = s_vz[k];
-        bool done = true;
-        if (do_move) {
-          const double xn = __fma_rn(f2d(vx), P.dt, x), yn = __fma_rn(f2d(vy), P.dt, y),
-                       zn = __fma_rn(f2d(vz), P.dt, z);
-          const float4* pf = P.plane32 + 4 * (size_t)cell;
-          const float fx = d2f_trunc(xn), fy = d2f_trunc(yn), fz = d2f_trunc(zn);
-#pragma unroll
-          for (int f = 0; f < 4; ++f)
-            if (!(plane_test32(pf[f], fx, fy, fz) > P.margin)) done = false;
-          x = xn;
-          y = yn;
-          z = zn;
-        }
-        if (done) {
-          OUT.x[slot] = x;
-          OUT.y[slot] = y;
-          OUT.z[slot] = z;
-          OUT.vx[slot] = vx;
-          OUT.vy[slot] = vy;
-          OUT.vz[slot] = vz;
-          if (DIAT) OUT.Ir[slot] = s_I[k];
-          OUT.mc[slot] = cell;
-          atomicAdd(s_nst + g0 + lc, 1);
-        } else {
-          s_q[atomicAdd(&s_qn, 1)] = k;
-        }
+      if (st <= 1) {
+        OUT.x[slot] = x;
+        OUT.y[slot] = y;
+        OUT.z[slot] = z;
       }
+      OUT.mc[slot] = st == 1 ? nb : cell;
+      if (st == 1) {
+        atomicAdd(P.na + nb, 1);
+        cnt.cross++;
+      }
+      if (st == 2) lc = -1;
     }
-    __syncthreads();
-    // 4b. queued particles: full face-by-face tracking, densely packed
-    const int qn = s_qn;
-    for (int qi = threadIdx.x; qi < qn; qi += CP_THREADS) {
-      const int k = s_q[qi];
-      const int s = s_src[k], lc = s_cl[k], cell = c0 + g0 + lc, slot = gbase + k;
-      double x = IN.x[s], y = IN.y[s], z = IN.z[s];
-      float vx = s_vx[k], vy = s_vy[k], vz = s_vz[k], I = DIAT ? s_I[k] : 0.0f;
-      const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)slot, step_move, flux, cnt, P.dt, -1);
-      OUT.x[slot] = x;
-      OUT.y[slot] = y;
-      OUT.z[slot] = z;
-      OUT.vx[slot] = vx;
-      OUT.vy[slot] = vy;
-      OUT.vz[slot] = vz;
-      if (DIAT) OUT.Ir[slot] = I;
-      OUT.mc[slot] = dst;
-      if (dst == cell)
-        atomicAdd(s_nst + g0 + lc, 1);
-      else if (dst >= 0)
-        atomicAdd(P.na + dst, 1);
+    const bool queued = st == 2;
+    const unsigned qm = __ballot_sync(0xffffffffu, queued);
+    if (qm) {
+      const int leader = __ffs(qm) - 1;
+      int qbase = 0;
+      if (lane == leader) qbase = atomicAdd(P.state + 3, __popc(qm));
+      qbase = __shfl_sync(0xffffffffu, qbase, leader);
+      if (queued)
+        reinterpret_cast<int2*>(P.tq)[qbase + __popc(qm & ((1u << lane) - 1u))] = make_int2(slot, P.src[slot]);
     }
-    __syncthreads();
-    g0 = g1;
+    const bool stay = st == 0;
+    if (__ballot_sync(0xffffffffu, stay)) {
+      const unsigned peers = __match_any_sync(0xffffffffu, stay ? lc : 256 + lane);
+      if (stay && lane == __ffs(peers) - 1) atomicAdd(s_nst + lc, __popc(peers));
+    }
   }
-  // new grouping bookkeeping of this tile's cells
-  for (int c = threadIdx.x; c < nc; c += CP_THREADS) {
-    P.nst[c0 + c] = s_nst[c];
-    P.sbase[c0 + c] = s_cs[c];
-    P.nold[c0 + c] = s_cs[c + 1] - s_cs[c];
+  __syncthreads();
+  for (int c = threadIdx.x; c < nc; c += NT) P.nst[c0 + c] = s_nst[c];
+  flush_counters(P, cnt);
+}
+
+size_t move_smem(int TC) { return sizeof(int) * (size_t)(2 * TC + 1) + sizeof(float) * (size_t)NPHI * TC; }
+
+// ---------------------------------------------------------------------------
+// face-by-face tracking of the particles the cell pass queued (those whose
+// fast move it could not prove inside their cell): thread per queued
+// particle over the whole domain, so the dependent loads and FP64 tests of
+// the crossings overlap across many warps.  The cell pass left each one's
+// post-collision velocity and its cell at the output slot; the position is
+// still the input slot's.  Stayers and arrivals are counted for the sort.
+// ---------------------------------------------------------------------------
+template <bool DIAT>
+__global__ void __launch_bounds__(128) k_track(Params P, Buf IN, Buf OUT, uint32_t step, int flux) {
+  const int nq = P.state[3];
+  Cnt cnt;
+  const int2* tq = reinterpret_cast<const int2*>(P.tq);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const int2 e = tq[q];
+    const int slot = e.x, src = e.y;
+    const int cell = OUT.mc[slot];
+    double x = IN.x[src], y = IN.y[src], z = IN.z[src];
+    float vx = OUT.vx[slot], vy = OUT.vy[slot], vz = OUT.vz[slot], I = DIAT ? OUT.Ir[slot] : 0.0f;
+    const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)slot, step, flux, cnt, P.dt, -1);
+    OUT.x[slot] = x;
+    OUT.y[slot] = y;
+    OUT.z[slot] = z;
+    OUT.vx[slot] = vx;
+    OUT.vy[slot] = vy;
+    OUT.vz[slot] = vz;
+    if (DIAT) OUT.Ir[slot] = I;
+    OUT.mc[slot] = dst;
+    if (dst == cell)
+      atomicAdd(P.nst + cell, 1);
+    else if (dst >= 0)
+      atomicAdd(P.na + dst, 1);
   }
   flush_counters(P, cnt);
 }
@@ -1183,6 +1181,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_final(Params P) {
       P.cs[n] = et;
       P.as[n] = ea;
       P.state[0] = et;
+      P.state[3] = 0;  // track queue consumed
       if ((long long)et > P.cap) atomicOr(P.status, ST_CAPACITY);
     }
   }
@@ -1407,28 +1406,62 @@ void launch_scatter(const Params& P, const int* mc, cudaStream_t s) {
   ++g_launches;
 }
 
-template <bool DIAT, int NT>
-static void launch_cp(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_coll,
-                      uint32_t step_move, int ewma_first, int TC, int CAP, cudaStream_t s) {
-  const size_t sm = cell_pass_smem(TC, CAP, DIAT);
-  const int nb = blocks_for(P.n_cells, TC);
-  cudaFuncSetAttribute(k_cell_pass<DIAT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_cell_pass<DIAT, NT><<<nb, NT, sm, s>>>(P, in, out, pass, sflags, step_coll, step_move, ewma_first, TC, CAP);
+static int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
 }
 
+template <bool DIAT, int NT>
+static void launch_move_t(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_move,
+                          int ewma_first, int TC, cudaStream_t s) {
+  const size_t sm = move_smem(TC);
+  cudaFuncSetAttribute(k_move<DIAT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_move<DIAT, NT><<<blocks_for(P.n_cells, TC), NT, sm, s>>>(P, in, out, pass, sflags, step_move, ewma_first, TC);
+}
+
+// one particle pass: order, collisions (PASS_COLLIDE), sampling and move
+// (PASS_MOVE: moving, else the positions are copied), tracking of the queue
 void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_coll,
-                      uint32_t step_move, int ewma_first, int TC, int CAP, int threads, cudaStream_t s) {
+                      uint32_t step_move, int ewma_first, int TC, int threads, cudaStream_t s) {
   const bool diat = P.rot_dof > 0;
-#define DIG_CP(D, T) launch_cp<D, T>(P, in, out, pass, sflags, step_coll, step_move, ewma_first, TC, CAP, s)
-  if (threads <= 64) {
-    if (diat) DIG_CP(true, 64); else DIG_CP(false, 64);
-  } else if (threads <= 128) {
-    if (diat) DIG_CP(true, 128); else DIG_CP(false, 128);
-  } else {
-    if (diat) DIG_CP(true, 256); else DIG_CP(false, 256);
+  const int sms = sm_count();
+  if (diat)
+    k_order<true><<<sms * 16, 256, 0, s>>>(P, in, out);
+  else
+    k_order<false><<<sms * 16, 256, 0, s>>>(P, in, out);
+  g_launches += 1;
+  if (pass & PASS_COLLIDE) {
+    const int rec = (sflags & S_PAIRS) != 0;
+    if (diat)
+      k_collide<true><<<blocks_for(P.n_cells, 128), 128, 0, s>>>(P, out, step_coll, rec);
+    else
+      k_collide<false><<<blocks_for(P.n_cells, 128), 128, 0, s>>>(P, out, step_coll, rec);
+    g_launches += 1;
   }
-#undef DIG_CP
-  ++g_launches;
+#define DIG_MV(D, T) launch_move_t<D, T>(P, in, out, pass, sflags, step_move, ewma_first, TC, s)
+  if (threads <= 64) {
+    if (diat) DIG_MV(true, 64); else DIG_MV(false, 64);
+  } else if (threads <= 128) {
+    if (diat) DIG_MV(true, 128); else DIG_MV(false, 128);
+  } else {
+    if (diat) DIG_MV(true, 256); else DIG_MV(false, 256);
+  }
+#undef DIG_MV
+  g_launches += 1;
+  if (pass & PASS_MOVE) {
+    const int flux = (sflags & S_WALLFLUX) != 0;
+    if (diat)
+      k_track<true><<<sms * 16, 128, 0, s>>>(P, in, out, step_move, flux);
+    else
+      k_track<false><<<sms * 16, 128, 0, s>>>(P, in, out, step_move, flux);
+    ++g_launches;
+  }
 }
 
 void launch_inject(const Params& P, const Buf& out, uint32_t step, int wallflux, cudaStream_t s) {

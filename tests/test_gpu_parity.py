@@ -160,18 +160,51 @@ def test_edge_cases():
         assert_same_particles(g2, o2)
 
 
-def test_all_particles_in_one_cell_overflow_is_reported():
-    """A cell holding more particles than the shared-memory stage is reported
-    as DIG_ERR_CAPACITY (host check of a device status bit), not silently run."""
+@pytest.mark.parametrize("gas", [W.ARGON, W.NITROGEN])
+def test_dense_cells_take_both_collision_paths(gas):
+    """Cells with more NTC candidates than a chunk of precomputed candidate
+    records holds (about 1,000 particles per cell and a time step near the
+    mean collision time) run the per-candidate loop; cells with fewer run on
+    precomputed records; both give the oracle's pairs, acceptances and
+    velocities bit for bit, with and without rotational exchange."""
+    T, n = 273.0, 1.677e22
+    mu = gas.mu_ref() * (T / gas.T_ref) ** gas.omega
+    npart = 6000
+    s = W.Scenario(gas=gas, mesh=W.closed_box(1, 1e-3, W.BC_DIFFUSE), n_particles=npart, n_init=n, T_init=T,
+                   u_init=(0.0, 0.0, 0.0), F_N=n * 1e-9 / npart, dt=1.2 * mu / (n * W.K_B * T), seed=21, L=1e-3,
+                   Kn=0.1, capacity=2 * npart)
+    g, o = pair(s)
+    g.init()
+    o.init()
+    g.step(2, dig.EWMA | dig.RECORD_PAIRS | dig.SYNC)
+    o.step(2, orc.EWMA | orc.RECORD_PAIRS)
+    assert_same_particles(g, o)
+    pg, po = g.pairs(), o.pairs()
+    assert np.array_equal(pg, po)
+    per_cell = np.bincount(po[:, 0])
+    assert per_cell.max() > 600 and per_cell.min() > 0
+    assert g.counters()["coll"] == o.counters()["coll"]
+
+
+def test_one_cell_holding_many_particles():
+    """600 particles written into one cell (far more than a move tile aims
+    at, stage_cap = 256): the cell's NTC loop, the gather and the move give
+    the oracle's particles and pairs bit for bit over two steps."""
     s = W.config_small(seed=2)
-    g = dig.Solver(s, "cuda:0", stage_cap=256)
+    g, o = pair(s, stage_cap=256)
     n = 600
-    cen = s.mesh.nodes[s.mesh.tets[40]].mean(axis=0)
-    x = np.repeat(cen[None], n, axis=0)
-    v = np.zeros((n, 3), np.float32)
-    with pytest.raises(dig.DigError, match="CAPACITY"):
-        g.write(x, v, np.zeros(n, np.float32), np.full(n, 40, np.int32))
-        g.step(1, dig.SYNC)
+    rng = np.random.default_rng(8)
+    P = s.mesh.nodes[s.mesh.tets[40]]
+    w = rng.dirichlet(np.ones(4), size=n)
+    x = w @ P
+    v = (rng.standard_normal((n, 3)) * 300.0).astype(np.float32)
+    for h in (g, o):
+        h.write(x, v, np.zeros(n, np.float32), np.full(n, 40, np.int32))
+    g.step(2, dig.EWMA | dig.RECORD_PAIRS | dig.SYNC)
+    o.step(2, orc.EWMA | orc.RECORD_PAIRS)
+    assert_same_particles(g, o)
+    pg, po = g.pairs(), o.pairs()
+    assert len(po) > 500 and np.array_equal(pg, po)
 
 
 def test_crossing_limit_matches_oracle():
