@@ -34,12 +34,13 @@ N_S = 200  # DSMC steps per bench step (one coupling window of the benchmarked c
 
 
 def read_traffic():
-    """DRAM bytes per cell-pass launch from the committed ncu summary, if the
-    kernel source is still the one that was profiled (else None)."""
+    """DRAM bytes per particle pass (k_order + k_collide + k_move + k_track of
+    one DSMC step) from the committed ncu summary, if the kernel source is
+    still the one that was profiled (else None)."""
     import hashlib
 
     src = os.path.join(ROOT, "paper_2607_08195_gb300", "csrc", "dig_kernels.cu")
-    prof = os.path.join(ROOT, "profiles", "k_cell_pass-cavity30-Kn0.01-8M.md")
+    prof = os.path.join(ROOT, "profiles", "particle_pass-cavity30-Kn0.01-8M.md")
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         fields = dict(l.split(":", 1) for l in open(prof) if l.startswith(("kernel_source_sha256_16:", "dram_bytes")))
@@ -249,18 +250,20 @@ def main():
     psteps = N * N_S * args.steps
     value = psteps * world / (ms * 1e-3)
 
-    # dominant kernel: the cell pass; algorithmic bytes = read + write of the
+    # dominant kernel: the particle pass of one DSMC step (k_order, k_collide,
+    # k_move, k_track launched back to back, timed together with CUDA events
+    # on the library's stream); algorithmic bytes = read + write of the
     # particle state once per particle-step (x,y,z f64 + vx,vy,vz f32 = 36 B,
     # plus the 4-byte cell id) = 80 B
     alg_bytes_per_pstep = 80.0
     peak, peak_kind = read_peaks()
     cp_launch_ms = k_ms / max(k_n, 1)
-    # launches: n_steps + 1 per dsmc_step call; particle-steps per launch
+    # passes: n_steps + 1 per dsmc_step call; particle-steps per pass
     psteps_per_launch = psteps / max(k_n, 1)
     achieved = alg_bytes_per_pstep * psteps_per_launch / (cp_launch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": read_traffic(), "kernel": "k_cell_pass", "peak_kind": peak_kind,
-                "kernel_ms_per_launch": cp_launch_ms, "kernel_share_of_step": k_ms / ms}
+                "traffic": read_traffic(), "kernel": "particle pass (k_order+k_collide+k_move+k_track)",
+                "peak_kind": peak_kind, "kernel_ms_per_launch": cp_launch_ms, "kernel_share_of_step": k_ms / ms}
 
     # end to end through the C ABI with host buffers: pinned host particle
     # state in, N_S DSMC steps, moving-average sums out, every bench step

@@ -92,6 +92,7 @@ struct dig_ctx {
   std::vector<Plane64> plane;
   std::vector<float4> plane32;
   std::vector<double> vol, cumvol, fdtv, area;
+  std::vector<int> fcell, fface, cfid;  // interior faces (synthetic solver)
   std::vector<BFaceDev> bf;
   std::vector<BCDev> bc;
   std::vector<InflowDev> inflow;
@@ -392,6 +393,20 @@ int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t*
       ctx->nbrf[4 * t + f] = (signed char)f;
       ctx->bf.push_back(B);
     }
+  // interior faces, each once (from its lower-index cell), for the synthetic solver
+  ctx->fcell.clear();
+  ctx->fface.clear();
+  ctx->cfid.assign(4 * (size_t)n_tets, -1);
+  for (int64_t t = 0; t < n_tets; ++t)
+    for (int f = 0; f < 4; ++f) {
+      const int nb = ctx->nbr[4 * t + f];
+      if (nb <= t) continue;
+      const int id = (int)ctx->fcell.size();
+      ctx->fcell.push_back((int)t);
+      ctx->fface.push_back(f);
+      ctx->cfid[4 * t + f] = id;
+      ctx->cfid[4 * (size_t)nb + ctx->nbrf[4 * t + f]] = id;
+    }
   ctx->mesh_ok = true;
   return DIG_OK;
 }
@@ -476,6 +491,13 @@ static size_t layout(dig_ctx* ctx, char* base) {
   C.S = A.take<double>(12 * n);
   C.R = A.take<double>(6 * n);
   C.mu = A.take<double>(n);
+  C.snd = A.take<double>(n);
+  const size_t nif = std::max<size_t>(ctx->fcell.size(), 1);
+  C.fcell = A.take<int>(nif);
+  C.fface = A.take<int>(nif);
+  C.cfid = A.take<int>(4 * n);
+  C.Ff = A.take<double>(6 * nif);
+  C.lmf = A.take<double>(nif);
   C.part = A.take<double>(couple_part_count((int)n));
   C.avail = A.take<int>(n);
   C.avail2 = A.take<int>(n);
@@ -579,6 +601,12 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   {
     CoupleParams& C = ctx->C;
     CK(cudaMemcpyAsync((void*)C.area, ctx->area.data(), 4 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    C.n_ifaces = (int)ctx->fcell.size();
+    if (C.n_ifaces > 0) {
+      CK(cudaMemcpyAsync((void*)C.fcell, ctx->fcell.data(), C.n_ifaces * sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync((void*)C.fface, ctx->fface.data(), C.n_ifaces * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemcpyAsync((void*)C.cfid, ctx->cfid.data(), 4 * n * sizeof(int), cudaMemcpyHostToDevice, s));
     ctx->bcU.assign(3 * ctx->bc.size(), 0.0);
     ctx->bcT.assign(ctx->bc.size(), 0.0);
     ctx->bcn.assign(ctx->bc.size(), 0.0);

@@ -15,8 +15,59 @@ namespace dig {
 
 namespace {
 
+// x^a for normal x > 0 as exp(a ln x), FP64, a few ulp: ln by the exponent
+// split and ln m = 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + ...), s = (m-1)/(m+1),
+// m in [1/sqrt2, sqrt2) (|s| <= 0.1716, series to s^22); exp by Cody-Waite
+// reduction y = k ln2 + r, |r| <= ln2/2, and the Taylor series of e^r to r^13.
+// ln2 = LN2_HI + LN2_LO with LN2_HI ln2 rounded to 32 significant bits, so that
+// k LN2_HI is exact.
+__device__ __forceinline__ double pow_pos(double x, double a) {
+  constexpr double LN2_HI = 0.6931471803691238, LN2_LO = 1.9082149292705877e-10, INV_LN2 = 1.4426950408889634;
+  const long long bits = __double_as_longlong(x);
+  int e = (int)((bits >> 52) & 0x7ff) - 1023;
+  double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  if (m > 1.4142135623730951) {
+    m *= 0.5;
+    e += 1;
+  }
+  const double s = (m - 1.0) / (m + 1.0);
+  const double z = s * s;
+  double p = 1.0 / 23.0;
+  p = fma(p, z, 1.0 / 21.0);
+  p = fma(p, z, 1.0 / 19.0);
+  p = fma(p, z, 1.0 / 17.0);
+  p = fma(p, z, 1.0 / 15.0);
+  p = fma(p, z, 1.0 / 13.0);
+  p = fma(p, z, 1.0 / 11.0);
+  p = fma(p, z, 1.0 / 9.0);
+  p = fma(p, z, 1.0 / 7.0);
+  p = fma(p, z, 1.0 / 5.0);
+  p = fma(p, z, 1.0 / 3.0);
+  p = fma(p, z, 1.0);
+  const double de = (double)e;
+  const double lnx = fma(de, LN2_HI, fma(de, LN2_LO, 2.0 * s * p));
+  const double y = a * lnx;
+  const double k = rint(y * INV_LN2);
+  const double r = fma(-k, LN2_LO, fma(-k, LN2_HI, y));
+  double q = 1.0 / 6227020800.0;  // 1/13!
+  q = fma(q, r, 1.0 / 479001600.0);
+  q = fma(q, r, 1.0 / 39916800.0);
+  q = fma(q, r, 1.0 / 3628800.0);
+  q = fma(q, r, 1.0 / 362880.0);
+  q = fma(q, r, 1.0 / 40320.0);
+  q = fma(q, r, 1.0 / 5040.0);
+  q = fma(q, r, 1.0 / 720.0);
+  q = fma(q, r, 1.0 / 120.0);
+  q = fma(q, r, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  q = fma(q, r, 1.0);
+  q = fma(q, r, 1.0);
+  return q * __longlong_as_double((long long)((int)k + 1023) << 52);
+}
+
 __device__ __forceinline__ double mu_nd(const CoupleParams& C, double Tt) {
-  return C.Kn * sqrt(2.0 / M_PI) * pow(Tt > 1e-6 ? Tt : 1e-6, C.omega);
+  return C.Kn * sqrt(2.0 / M_PI) * pow_pos(Tt > 1e-6 ? Tt : 1e-6, C.omega);
 }
 
 // boundary values (walls: wall velocity and temperature; open: free stream)
@@ -87,18 +138,32 @@ __global__ void k_cp_extract(Params P, CoupleParams C, const double* __restrict_
   C.nbar[c] = N;
 }
 
-// Green-Gauss gradients of u (3), T_t, T_r from primitives prim[6][n]
-__global__ void k_cp_grad(Params P, CoupleParams C, const double* __restrict__ prim, double* __restrict__ grad) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// NSF stress and heat fluxes from the gradients G (du_i/dx_j at 3i+j, then T_t, T_r)
+__device__ void nsf_mu(const CoupleParams& C, double mu, const double* G, double* sig, double* qt, double* qr) {
+  const double div = G[0] + G[4] + G[8];
+  sig[0] = -mu * (2.0 * G[0] - 2.0 / 3.0 * div);
+  sig[1] = -mu * (2.0 * G[4] - 2.0 / 3.0 * div);
+  sig[2] = -mu * (2.0 * G[8] - 2.0 / 3.0 * div);
+  sig[3] = -mu * (G[1] + G[3]);
+  sig[4] = -mu * (G[2] + G[6]);
+  sig[5] = -mu * (G[5] + G[7]);
+  const double kt = 3.75 * mu, kr = 1.32 * mu;
+  for (int i = 0; i < 3; ++i) {
+    qt[i] = -kt * G[9 + i];
+    qr[i] = C.dr > 0 ? -kr * G[12 + i] : 0.0;
+  }
+}
+
+// Green-Gauss gradients of u (3), T_t, T_r of cell c from primitives prim[6][n]
+__device__ __forceinline__ void grad_cell(const Params& P, const CoupleParams& C, const double* __restrict__ prim,
+                                          int c, double* g) {
   const int n = P.n_cells;
-  if (c >= n) return;
-  double g[15];
   for (int q = 0; q < 15; ++q) g[q] = 0.0;
-  const double L2 = C.L0 * C.L0;
+  const double iL2 = 1.0 / (C.L0 * C.L0);
   for (int f = 0; f < 4; ++f) {
     const Plane64 pl = P.plane[4 * (size_t)c + f];
-    const double N3[3] = {pl.nx, pl.ny, pl.nz};
-    const double A = C.area[4 * (size_t)c + f] / L2;
+    const double A = C.area[4 * (size_t)c + f] * iL2;
+    const double NA[3] = {pl.nx * A, pl.ny * A, pl.nz * A};
     const int nb = P.nbr[4 * (size_t)c + f];
     double phi[5];
     if (nb >= 0) {
@@ -113,25 +178,19 @@ __global__ void k_cp_grad(Params P, CoupleParams C, const double* __restrict__ p
       phi[4] = Tb;
     }
     for (int q = 0; q < 5; ++q)
-      for (int i = 0; i < 3; ++i) g[3 * q + i] += phi[q] * N3[i] * A;
+      for (int i = 0; i < 3; ++i) g[3 * q + i] += phi[q] * NA[i];
   }
-  const double V = P.vol[c] / (L2 * C.L0);
-  for (int q = 0; q < 15; ++q) grad[(size_t)q * n + c] = g[q] / V;
+  const double iV = (C.L0 * C.L0 * C.L0) / P.vol[c];
+  for (int q = 0; q < 15; ++q) g[q] *= iV;
 }
 
-__device__ void nsf_mu(const CoupleParams& C, double mu, const double* G, double* sig, double* qt, double* qr) {
-  const double div = G[0] + G[4] + G[8];
-  sig[0] = -mu * (2.0 * G[0] - 2.0 / 3.0 * div);
-  sig[1] = -mu * (2.0 * G[4] - 2.0 / 3.0 * div);
-  sig[2] = -mu * (2.0 * G[8] - 2.0 / 3.0 * div);
-  sig[3] = -mu * (G[1] + G[3]);
-  sig[4] = -mu * (G[2] + G[6]);
-  sig[5] = -mu * (G[5] + G[7]);
-  const double kt = 3.75 * mu, kr = 1.32 * mu;
-  for (int i = 0; i < 3; ++i) {
-    qt[i] = -kt * G[9 + i];
-    qr[i] = C.dr > 0 ? -kr * G[12 + i] : 0.0;
-  }
+__global__ void k_cp_grad(Params P, CoupleParams C, const double* __restrict__ prim, double* __restrict__ grad) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n) return;
+  double g[15];
+  grad_cell(P, C, prim, c, g);
+  for (int q = 0; q < 15; ++q) grad[(size_t)q * n + c] = g[q];
 }
 
 __device__ void nsf(const CoupleParams& C, double Tt, const double* G, double* sig, double* qt, double* qr) {
@@ -305,15 +364,16 @@ __device__ __forceinline__ void cons_from_prim(const CoupleParams& C, const doub
 
 __device__ __forceinline__ void prim_from_cons(const CoupleParams& C, const double* U, double* Pp) {
   const double rho = U[0];
-  const double ux = U[1] / rho, uy = U[2] / rho, uz = U[3] / rho;
-  const double er = C.dr > 0 ? U[5] / rho : 0.0;
-  const double E = U[4] / rho;
+  const double ir = 1.0 / rho;
+  const double ux = U[1] * ir, uy = U[2] * ir, uz = U[3] * ir;
+  const double er = C.dr > 0 ? U[5] * ir : 0.0;
+  const double E = U[4] * ir;
   Pp[0] = rho;
   Pp[1] = ux;
   Pp[2] = uy;
   Pp[3] = uz;
   Pp[4] = (2.0 / 3.0) * (E - 0.5 * (ux * ux + uy * uy + uz * uz) - er);
-  Pp[5] = C.dr > 0 ? 2.0 * er / C.dr : Pp[4];
+  Pp[5] = C.dr > 0 ? (2.0 / C.dr) * er : Pp[4];
 }
 
 __global__ void k_cp_init_cons(Params P, CoupleParams C) {
@@ -344,15 +404,17 @@ __global__ void k_cp_prim(Params P, CoupleParams C, int apply) {
   prim_from_cons(C, U, Pp);
   for (int q = 0; q < 6; ++q) C.prim[(size_t)q * n + c] = Pp[q];
   C.mu[c] = mu_nd(C, Pp[4]);
+  C.snd[c] = sqrt(C.gam * Pp[4]);
 }
 
-// total stress and heat fluxes per cell: NSF of the current state + HoT
-__global__ void k_cp_stress(Params P, CoupleParams C) {
+// total stress and heat fluxes per cell: NSF of the current state (its
+// Green-Gauss gradients and viscosity) + HoT
+__global__ void k_cp_grad_stress(Params P, CoupleParams C) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
   if (c >= n || C.scal->done) return;
   double G[15];
-  for (int q = 0; q < 15; ++q) G[q] = C.grad[(size_t)q * n + c];
+  grad_cell(P, C, C.prim, c, G);
   double sig[6], qt[3], qr[3];
   nsf_mu(C, C.mu[c], G, sig, qt, qr);
   for (int q = 0; q < 6; ++q) C.S[(size_t)q * n + c] = sig[q] + C.hot[(size_t)q * n + c];
@@ -375,8 +437,69 @@ __device__ __forceinline__ void inv_flux(const double* Pp, const double* U, cons
 
 constexpr int CPT = 256;
 
-// face fluxes, residual and local stable step of every cell; per-block
-// partial (min step, sum of squared residuals)
+// Interior face flux (Rusanov inviscid flux plus the face-averaged stress and
+// heat flux) seen from cell c with outward unit normal N, and the largest
+// wave speed; from the other cell (normal -N) the flux is exactly -F.
+__device__ __forceinline__ void interior_flux(const CoupleParams& C, const double* Pc, const double* Uc,
+                                              const double* Pn, const double* Un, const double* Sc,
+                                              const double* Sn, const double* N, double cl, double cr, double* F,
+                                              double* lmo) {
+  double FL[6], FR[6];
+  inv_flux(Pc, Uc, N, FL);
+  inv_flux(Pn, Un, N, FR);
+  const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
+  const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
+  const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
+  for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
+  double sf[6], qtf[3], qrf[3], uf[3];
+  for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (Sc[q] + Sn[q]);
+  for (int q = 0; q < 3; ++q) {
+    qtf[q] = 0.5 * (Sc[6 + q] + Sn[6 + q]);
+    qrf[q] = 0.5 * (Sc[9 + q] + Sn[9 + q]);
+    uf[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
+  }
+  const double sn0 = sf[0] * N[0] + sf[3] * N[1] + sf[4] * N[2];
+  const double sn1 = sf[3] * N[0] + sf[1] * N[1] + sf[5] * N[2];
+  const double sn2 = sf[4] * N[0] + sf[5] * N[1] + sf[2] * N[2];
+  F[1] += sn0;
+  F[2] += sn1;
+  F[3] += sn2;
+  F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + (qtf[0] + qrf[0]) * N[0] + (qtf[1] + qrf[1]) * N[1] +
+          (qtf[2] + qrf[2]) * N[2];
+  F[5] += qrf[0] * N[0] + qrf[1] * N[1] + qrf[2] * N[2];
+  *lmo = lm;
+}
+
+// flux of every interior face once, seen from its lower-index cell
+__global__ void k_cp_face(Params P, CoupleParams C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C.n_ifaces || C.scal->done) return;
+  const int n = P.n_cells;
+  const int c = C.fcell[i], f = C.fface[i];
+  const int nb = P.nbr[4 * (size_t)c + f];
+  const Plane64 pl = P.plane[4 * (size_t)c + f];
+  const double N[3] = {pl.nx, pl.ny, pl.nz};
+  double Pc[6], Uc[6], Pn[6], Un[6], Sc[12], Sn[12];
+  for (int q = 0; q < 6; ++q) {
+    Pc[q] = C.prim[(size_t)q * n + c];
+    Uc[q] = C.U[(size_t)q * n + c];
+    Pn[q] = C.prim[(size_t)q * n + nb];
+    Un[q] = C.U[(size_t)q * n + nb];
+  }
+  for (int q = 0; q < 12; ++q) {
+    Sc[q] = C.S[(size_t)q * n + c];
+    Sn[q] = C.S[(size_t)q * n + nb];
+  }
+  const double cr = Pn[4] > 0 ? C.snd[nb] : sqrt(C.gam * 1e-12);
+  double F[6], lm;
+  interior_flux(C, Pc, Uc, Pn, Un, Sc, Sn, N, C.snd[c], cr, F, &lm);
+  for (int q = 0; q < 6; ++q) C.Ff[(size_t)q * C.n_ifaces + i] = F[q];
+  C.lmf[i] = lm;
+}
+
+// residual and local stable step of every cell from its face fluxes (the
+// interior ones from k_cp_face, the boundary ones here); per-block partial
+// (min step, sum of squared residuals)
 __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
@@ -388,11 +511,11 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
       Pc[q] = C.prim[(size_t)q * n + c];
       Uc[q] = C.U[(size_t)q * n + c];
     }
-    const double L2 = C.L0 * C.L0, L3 = L2 * C.L0;
-    const double V = P.vol[c] / L3;
+    const double L2 = C.L0 * C.L0, L3 = L2 * C.L0, iL2 = 1.0 / L2;
+    const double V = P.vol[c] / L3, iV = L3 / P.vol[c];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     double lam_sum = 0.0;
-    const double cc = sqrt(C.gam * Pc[4]);
+    const double cc = C.snd[c];
     const double muc = C.mu[c];
     const double nu = 2.5 * muc / Pc[0];
     const double mflux = C.rho0 * C.c0 * C.c0, eflux = mflux * C.c0;
@@ -400,18 +523,20 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
       const Plane64 pl = P.plane[4 * (size_t)c + f];
       const double N[3] = {pl.nx, pl.ny, pl.nz};
       const double Ad = C.area[4 * (size_t)c + f];
-      const double A = Ad / L2;
+      const double A = Ad * iL2;
       const int nb = P.nbr[4 * (size_t)c + f];
-      const int kind = nb >= 0 ? -1 : P.bc[P.bf[-1 - nb].bc].kind;
       double F[6];
-      if (nb >= 0 || kind >= 2) {
-        double Pn[6], Un[6];
-        if (nb >= 0) {
-          for (int q = 0; q < 6; ++q) {
-            Pn[q] = C.prim[(size_t)q * n + nb];
-            Un[q] = C.U[(size_t)q * n + nb];
-          }
-        } else {
+      if (nb >= 0) {
+        const int fi = C.cfid[4 * (size_t)c + f];
+        const double sg = C.fcell[fi] == c ? 1.0 : -1.0;
+        for (int q = 0; q < 6; ++q) F[q] = sg * C.Ff[(size_t)q * C.n_ifaces + fi];
+        lam_sum += A * (C.lmf[fi] + 2.0 * nu * A * iV);
+      } else {
+        const int kind = P.bc[P.bf[-1 - nb].bc].kind;
+        if (kind >= 2) {
+          // open boundary: Rusanov flux against the free stream (inflow) or
+          // the cell's own state (outflow), no viscous terms
+          double Pn[6], Un[6];
           const int b = P.bf[-1 - nb].bc;
           if (kind == 3) {
             for (int q = 0; q < 6; ++q) Pn[q] = Pc[q];
@@ -424,53 +549,35 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
             Pn[5] = Pn[4];
           }
           cons_from_prim(C, Pn, Un);
-        }
-        double FL[6], FR[6];
-        inv_flux(Pc, Uc, N, FL);
-        inv_flux(Pn, Un, N, FR);
-        const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
-        const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
-        const double cl = sqrt(C.gam * Pc[4]), cr = sqrt(C.gam * (Pn[4] > 0 ? Pn[4] : 1e-12));
-        const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
-        for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
-        if (nb >= 0) {
-          double sf[6], qtf[3], qrf[3], uf[3];
-          for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (C.S[(size_t)q * n + c] + C.S[(size_t)q * n + nb]);
-          for (int q = 0; q < 3; ++q) {
-            qtf[q] = 0.5 * (C.S[(size_t)(6 + q) * n + c] + C.S[(size_t)(6 + q) * n + nb]);
-            qrf[q] = 0.5 * (C.S[(size_t)(9 + q) * n + c] + C.S[(size_t)(9 + q) * n + nb]);
-            uf[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
-          }
-          const double sn0 = sf[0] * N[0] + sf[3] * N[1] + sf[4] * N[2];
-          const double sn1 = sf[3] * N[0] + sf[1] * N[1] + sf[5] * N[2];
-          const double sn2 = sf[4] * N[0] + sf[5] * N[1] + sf[2] * N[2];
-          F[1] += sn0;
-          F[2] += sn1;
-          F[3] += sn2;
-          F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + (qtf[0] + qrf[0]) * N[0] + (qtf[1] + qrf[1]) * N[1] +
-                  (qtf[2] + qrf[2]) * N[2];
-          F[5] += qrf[0] * N[0] + qrf[1] * N[1] + qrf[2] * N[2];
-        }
-        lam_sum += A * (lm + 2.0 * nu * A / V);
-      } else {
-        const int ib = -1 - nb;
-        const double* W = P.bflux + 5 * (size_t)ib;
-        F[0] = 0.0;
-        if (C.wall_t > 0.0) {
-          for (int i = 0; i < 3; ++i) F[1 + i] = W[1 + i] / (C.wall_t * Ad) / mflux;
-          F[4] = W[4] / (C.wall_t * Ad) / eflux;
+          double FL[6], FR[6];
+          inv_flux(Pc, Uc, N, FL);
+          inv_flux(Pn, Un, N, FR);
+          const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
+          const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
+          const double cl = cc, cr = sqrt(C.gam * (Pn[4] > 0 ? Pn[4] : 1e-12));
+          const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
+          for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
+          lam_sum += A * (lm + 2.0 * nu * A * iV);
         } else {
-          const double p = Pc[0] * Pc[4];
-          for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
-          F[4] = 0.0;
+          const int ib = -1 - nb;
+          const double* W = P.bflux + 5 * (size_t)ib;
+          F[0] = 0.0;
+          if (C.wall_t > 0.0) {
+            for (int i = 0; i < 3; ++i) F[1 + i] = W[1 + i] / (C.wall_t * Ad) / mflux;
+            F[4] = W[4] / (C.wall_t * Ad) / eflux;
+          } else {
+            const double p = Pc[0] * Pc[4];
+            for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
+            F[4] = 0.0;
+          }
+          F[5] = 0.0;
+          lam_sum += A * (cc + 2.0 * nu * A * iV);
         }
-        F[5] = 0.0;
-        lam_sum += A * (cc + 2.0 * nu * A / V);
       }
       for (int q = 0; q < 6; ++q) acc[q] += F[q] * A;
     }
     double Rc[6];
-    for (int q = 0; q < 6; ++q) Rc[q] = -acc[q] / V;
+    for (int q = 0; q < 6; ++q) Rc[q] = -acc[q] * iV;
     if (C.dr > 0) {
       const double T = (3.0 * Pc[4] + C.dr * Pc[5]) / (3.0 + C.dr);
       const double tau = muc / (Pc[0] * Pc[4]);
@@ -801,8 +908,8 @@ void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double e
   k_cp_init_cons<<<nb, CPT, 0, s>>>(P, C);
   for (int it = 0; it < N_m; ++it) {
     k_cp_prim<<<nb, CPT, 0, s>>>(P, C, it > 0);
-    k_cp_grad<<<nb, CPT, 0, s>>>(P, C, C.prim, C.grad);
-    k_cp_stress<<<nb, CPT, 0, s>>>(P, C);
+    k_cp_grad_stress<<<nb, CPT, 0, s>>>(P, C);
+    if (C.n_ifaces > 0) k_cp_face<<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
     k_cp_flux<<<nb, CPT, 0, s>>>(P, C);
     k_cp_reduce<<<1, 1024, 0, s>>>(C, nb, it, eps);
   }

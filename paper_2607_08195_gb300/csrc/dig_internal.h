@@ -128,8 +128,13 @@ struct CoupleParams {
   const double* bcU;   // [3 n_bcs]
   const double* bcT;   // [n_bcs]
   const double* bcn;   // [n_bcs]
-  double *own, *sd, *grad, *half, *hot, *newst, *flag, *nbar, *U, *prim, *S, *R, *part, *mu;
+  double *own, *sd, *grad, *half, *hot, *newst, *flag, *nbar, *U, *prim, *S, *R, *part, *mu, *snd;
   int *avail, *avail2;
+  int n_ifaces;          // interior faces (each once)
+  const int* fcell;      // [n_ifaces] lower-index cell of each interior face
+  const int* fface;      // [n_ifaces] its local face
+  const int* cfid;       // [4n] interior face of (cell, local face), -1 on the boundary
+  double *Ff, *lmf;      // [6][n_ifaces] face fluxes, [n_ifaces] wave speeds
   float* feat;    // [n][13] closure inputs of the coupling window
   float* ypred;   // [n][8] closure outputs
   double* wnorm;  // [2][n] window density and temperature (0: invalid row)

@@ -122,15 +122,32 @@ __device__ __forceinline__ float exp_f(float y) {
 
 __device__ __forceinline__ float pow_f(float x, float a) { return exp_f(a * ln_f(x)); }
 
-// Exact FP32 -> FP64 conversion with integer operations (keeps the FP64 pipe,
-// which issues at 1/64 of the FP32 rate, free for arithmetic).  Zero,
-// subnormal, infinite and NaN inputs take the hardware conversion.
+// Exact FP32 -> FP64 conversion with integer operations only, every input
+// (zero, subnormal, infinite and NaN included): keeps the FP64 pipe, which
+// issues at 1/64 of the FP32 rate, free for arithmetic.
 __device__ __forceinline__ double f2d(float f) {
   const unsigned b = __float_as_uint(f);
+  const unsigned s = b & 0x80000000u;
   const unsigned e = (b >> 23) & 0xffu;
-  if (e == 0u || e == 255u) return (double)f;
-  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu);
-  return __hiloint2double((int)hi, (int)(b << 29));
+  const unsigned m = b & 0x7fffffu;
+  unsigned hi, lo;
+  if (e != 0u && e != 255u) {
+    hi = s | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (e == 255u) {
+    hi = s | 0x7ff00000u | (m >> 3);
+    lo = m << 29;
+  } else if (m == 0u) {
+    hi = s;
+    lo = 0u;
+  } else {
+    // subnormal m 2^-149: leading one at bit p, exponent p - 149
+    const int p = 31 - __clz((int)m);
+    const unsigned fr = (m << (23 - p)) & 0x7fffffu;
+    hi = s | ((unsigned)(p + 874) << 20) | (fr >> 3);
+    lo = fr << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // Gaussian pair, Marsaglia's polar method; two attempts per Philox block;
@@ -754,7 +771,7 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
     for (int i = threadIdx.x; i < np * nc; i += NT) {
       const int q = i / nc, lc = i - q * nc;
       const size_t o = (size_t)q * (size_t)P.n_cells + (size_t)(c0 + lc);
-      const double ph = q == 0 ? (double)(s_cs[lc + 1] - s_cs[lc]) : f2d(s_sum[i]);
+      const double ph = f2d(q == 0 ? (float)(s_cs[lc + 1] - s_cs[lc]) : s_sum[i]);
       if (sflags & S_INST) P.phi_inst[o] = ph;
       if (sflags & S_EWMA) P.phi_ewma[o] = ewma_first ? ph : __fma_rn(P.na_a, P.phi_ewma[o], P.na_b * ph);
       if (sflags & S_WINDOW) P.phi_win[o] += ph;

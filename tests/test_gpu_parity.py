@@ -158,6 +158,23 @@ def test_edge_cases():
         g2.step(5, dig.EWMA | dig.SYNC)
         o2.step(5, orc.EWMA)
         assert_same_particles(g2, o2)
+    # velocity components that are zero, negative zero or FP32 subnormal
+    # (their exact FP64 value enters x + v dt)
+    rng = np.random.default_rng(12)
+    n = 64
+    P = s.mesh.nodes[s.mesh.tets[17]]
+    x = rng.dirichlet(np.ones(4), size=n) @ P
+    v = (rng.standard_normal((n, 3)) * 300.0).astype(np.float32)
+    v[:8, 0] = 0.0
+    v[8:16, 1] = -0.0
+    v[16:32, 2] = np.float32(1e-40) * rng.integers(1, 1000, 16).astype(np.float32)
+    v[32:40, :] = np.float32(-3e-39)
+    g3, o3 = pair(s)
+    g3.write(x, v, np.zeros(n, np.float32), np.full(n, 17, np.int32))
+    o3.write(x, v, np.zeros(n, np.float32), np.full(n, 17, np.int32))
+    g3.step(1, dig.EWMA | dig.SYNC)
+    o3.step(1, orc.EWMA)
+    assert_same_particles(g3, o3)
 
 
 @pytest.mark.parametrize("gas", [W.ARGON, W.NITROGEN])
