@@ -199,6 +199,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-couple", action="store_true", help="DSMC steps only (no DIG coupling)")
+    ap.add_argument("--workload", default="cavity30", choices=["cavity30", "cavity20"],
+                    help="cavity30: 30^3 hexes, Kn 0.01, 8M particles (the benchmark); cavity20: 20^3 hexes, "
+                         "Kn 0.001, 3M particles (smaller case for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -212,7 +215,7 @@ def main():
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    scen = W.config_c2(seed=2 + rank)
+    scen = W.config_c2(seed=2 + rank) if args.workload == "cavity30" else W.config_c3(seed=3 + rank)
     g = dig.Solver(scen, str(device))
     g.init()
     g.synchronize()

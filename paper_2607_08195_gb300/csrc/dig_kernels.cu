@@ -658,61 +658,96 @@ __device__ __forceinline__ void flush_counters(const Params& P, const Cnt& c) {
 // the particle pass: k_order, k_collide, k_move
 // ---------------------------------------------------------------------------
 
-// Canonical order of every cell, warp per cell (grid-stride over cells).  The
-// stayers of cell c are the slots of its old range [sbase, sbase + nold) of
-// the input buffer whose mc is c (the move that wrote them left them in c),
-// in slot order; the arrivals are the aq entries of c (slots of particles
-// that moved into c, new particles included), ranked by slot.  Writes
-// src[cs[c] + k] and gathers velocities (and I_r) into the output buffer;
-// then records the new range as the cell's old range for the next pass.
+// Canonical order of every cell, half a warp per cell: the two cells of a
+// warp proceed together, so their dependent loads overlap (grid-stride over
+// cell pairs).  The stayers of cell c are the slots of its old range
+// [sbase, sbase + nold) of the input buffer whose mc is c (the move that
+// wrote them left them in c), in slot order; the arrivals are the aq entries
+// of c (slots of particles that moved into c, new particles included),
+// ranked by slot.  Writes src[cs[c] + k], keeps it in shared memory for cells
+// of up to OQ particles, gathers velocities (and I_r) into the output buffer
+// and records the new range as the cell's old range for the next pass.
+constexpr int OQ = 64;
+
 template <bool DIAT>
 __global__ void __launch_bounds__(256) k_order(Params P, Buf IN, Buf OUT) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int s_src[256 / 16][OQ];
+  const int lane = threadIdx.x & 31, g = lane >> 4, gl = lane & 15;
+  int* my = s_src[threadIdx.x >> 4];
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     P.state[1] = 0;
     P.state[2] = 0;
   }
-  const unsigned lt = (1u << lane) - 1u;
-  for (int c = gw; c < P.n_cells; c += nw) {
-    const int base = P.cs[c], Nc = P.cs[c + 1] - base;
-    const int sb = P.sbase[c], no = P.nold[c];
+  const unsigned glt = (1u << gl) - 1u;
+  const int npair = (P.n_cells + 1) >> 1;
+  for (int pr = gw; pr < npair; pr += nw) {
+    const int c = 2 * pr + g;
+    const bool live = c < P.n_cells;
+    // every independent load of the cell first
+    int base = 0, Nc = 0, sb = 0, no = 0, a0 = 0, na = 0;
+    if (live) {
+      base = P.cs[c];
+      Nc = P.cs[c + 1] - base;
+      sb = P.sbase[c];
+      no = P.nold[c];
+      a0 = P.as[c];
+      na = P.as[c + 1] - a0;
+    }
+    const int key = gl < na ? P.aq[a0 + gl] : 0x7fffffff;
+    // stayers: 16 old slots per round and cell; the bounds are warp-uniform
+    const int no_max = max(no, __shfl_xor_sync(0xffffffffu, no, 16));
     int ns = 0;
-    for (int k0 = 0; k0 < no; k0 += 32) {
-      const int k = k0 + lane;
+    for (int k0 = 0; k0 < no_max; k0 += 16) {
+      const int k = k0 + gl;
       const bool st = k < no && IN.mc[sb + k] == c;
-      const unsigned bs = __ballot_sync(0xffffffffu, st);
-      const int pos = ns + __popc(bs & lt);
-      if (st && pos < Nc) P.src[base + pos] = sb + k;
+      const unsigned bs = (__ballot_sync(0xffffffffu, st) >> (16 * g)) & 0xffffu;
+      const int pos = ns + __popc(bs & glt);
+      if (st && pos < Nc) {
+        P.src[base + pos] = sb + k;
+        if (pos < OQ) my[pos] = sb + k;
+      }
       ns += __popc(bs);
     }
-    const int a0 = P.as[c], na = P.as[c + 1] - a0;
-    if (na <= 32) {
-      const int key = lane < na ? P.aq[a0 + lane] : 0x7fffffff;
+    // arrivals, ranked by slot
+    const int na_max = max(na, __shfl_xor_sync(0xffffffffu, na, 16));
+    if (na_max <= 16) {
       int rank = 0;
-      for (int r = 0; r < na; ++r) rank += (__shfl_sync(0xffffffffu, key, r) < key) ? 1 : 0;
-      if (lane < na && ns + rank < Nc) P.src[base + ns + rank] = key;
+      for (int r = 0; r < na_max; ++r) {
+        const int kr = __shfl_sync(0xffffffffu, key, 16 * g + r);
+        rank += (r < na && kr < key) ? 1 : 0;
+      }
+      const int pos = ns + rank;
+      if (gl < na && pos < Nc) {
+        P.src[base + pos] = key;
+        if (pos < OQ) my[pos] = key;
+      }
     } else {
-      for (int r = lane; r < na; r += 32) {
-        const int key = P.aq[a0 + r];
+      for (int r = gl; r < na; r += 16) {
+        const int kk = P.aq[a0 + r];
         int rank = 0;
-        for (int r2 = 0; r2 < na; ++r2) rank += (P.aq[a0 + r2] < key) ? 1 : 0;
-        if (ns + rank < Nc) P.src[base + ns + rank] = key;
+        for (int r2 = 0; r2 < na; ++r2) rank += (P.aq[a0 + r2] < kk) ? 1 : 0;
+        const int pos = ns + rank;
+        if (pos < Nc) {
+          P.src[base + pos] = kk;
+          if (pos < OQ) my[pos] = kk;
+        }
       }
     }
     __syncwarp();
-    for (int k = lane; k < Nc; k += 32) {
-      const int q = P.src[base + k];
+    for (int k = gl; k < Nc; k += 16) {
+      const int q = k < OQ ? my[k] : P.src[base + k];
       OUT.vx[base + k] = IN.vx[q];
       OUT.vy[base + k] = IN.vy[q];
       OUT.vz[base + k] = IN.vz[q];
       if (DIAT) OUT.Ir[base + k] = IN.Ir[q];
     }
-    if (lane == 0) {
+    if (live && gl == 0) {
       P.sbase[c] = base;
       P.nold[c] = Nc;
     }
+    __syncwarp();
   }
 }
 
