@@ -47,7 +47,8 @@ extern "C" {
 #define DIG_BC_OUTFLOW 3
 
 /* dsmc_step flags */
-#define DIG_EWMA 1         /* update the exponential moving average (paper Eq. exponential_average_moments) */
+#define DIG_EWMA 1         /* update the exponential moving average (paper Eq. exponential_average_moments;
+                              until n_a samples exist it is the plain mean of all samples) */
 #define DIG_WINDOW 2       /* add to the coupling-window sums */
 #define DIG_CUMUL 4        /* add to the cumulative sums (paper Eq. steady_average_moments) */
 #define DIG_RECORD_PAIRS 8 /* debug: record the candidate pairs of the last step */
@@ -228,8 +229,11 @@ int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches);
  * iterations or residual below eps_m of its first value), and the particles
  * of accepted cells recalibrated to M^{k+1} (velocities shifted and scaled,
  * rotational energies scaled, particles cloned or deleted with the density
- * ratio).  Walls use the momentum and energy given to each wall face during
- * the DSMC steps run with DIG_WALLFLUX since the last coupling.  With
+ * ratio).  Diffuse walls close the synthetic equations as isothermal no-slip
+ * walls (the wall velocity and temperature enter the gradients; the wall
+ * face carries the cell's pressure, total stress and heat flux), specular
+ * walls as slip walls (pressure only); the wall fluxes sampled with
+ * DIG_WALLFLUX remain a DSMC output (dig_wall_flux).  With
  * cfg.closure = 1 and closure parameters set, the translational HoT (sigma,
  * q_t) of each cell comes from the learned closure evaluated on the coupling
  * window's sums (DIG_WINDOW; see closure_features), except for cells whose

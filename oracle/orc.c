@@ -900,10 +900,13 @@ static void sample_cells(orc_ctx* c, int flags) {
     }
     memcpy(c->phi_inst + NPHI_MAX * t, ph, sizeof ph);
     if (flags & ORC_EWMA) {
+      /* Eq. exponential_average_moments with n_a effective samples; while
+       * fewer than n_a samples exist (m <= n_a) the plain mean of all of them */
       double* E = c->phi_ewma + NPHI_MAX * t;
-      const double na = (double)c->cfg.n_a;
-      const double a = (na - 1.0) / na, b = 1.0 / na;
-      for (int q = 0; q < np; ++q) E[q] = c->n_ewma == 0 ? ph[q] : a * E[q] + b * ph[q];
+      const double m = (double)(c->n_ewma + 1), na = (double)c->cfg.n_a;
+      const double w = m < na ? m : na;
+      const double a = (w - 1.0) / w, b = 1.0 / w;
+      for (int q = 0; q < np; ++q) E[q] = a * E[q] + b * ph[q];
     }
     if (flags & ORC_WINDOW) {
       double* W = c->phi_win + NPHI_MAX * t;
@@ -1424,10 +1427,10 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
  * sigma = sigma_NSF + HoT, q = q_NSF + HoT) by explicit pseudo-time
  * stepping with one global step (the smallest local step at CFL 0.5, so the
  * transient stays conservative): cell-centred finite volumes,
- * Rusanov inviscid flux, face-averaged stress and heat flux, walls closed by
- * the DSMC-sampled wall fluxes of the coupling window, open faces by the free
- * stream.  Stops after N_m iterations or when the residual L2 norm falls
- * below eps_m times its first value. */
+ * Rusanov inviscid flux, face-averaged stress and heat flux, diffuse walls as
+ * isothermal no-slip walls and specular walls as slip walls (see the wall
+ * faces below), open faces by the free stream.  Stops after N_m iterations or
+ * when the residual L2 norm falls below eps_m times its first value. */
 static void prim_from_cons(const nd_t* d, const double* U, double* P) {
   const double rho = U[0];
   const double ux = U[1] / rho, uy = U[2] / rho, uz = U[3] / rho;
@@ -1469,8 +1472,6 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
   double* dtl = (double*)malloc(sizeof(double) * n);
   for (int64_t t = 0; t < n; ++t) cons_from_prim(d, c->cp_half + 6 * t, U + nv * t);
   const double L2 = d->L0 * d->L0, L3 = L2 * d->L0;
-  const double mflux = d->rho0 * d->c0 * d->c0, eflux = mflux * d->c0;
-  const double wall_t = c->flux_steps > 0 ? (double)c->flux_steps * c->cfg.dt : 0.0;
   double res0 = 0.0, res = 0.0;
   int it = 0;
   for (it = 0; it < c->cfg.N_m; ++it) {
@@ -1542,22 +1543,33 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
           }
           lam_sum += A * (lm + 2.0 * nu * A / V);
         } else {
-          /* wall: no mass flux; momentum and energy given to the wall per unit
-           * area and time, as sampled by DSMC over the coupling window (if
-           * none was sampled: the cell pressure only) */
+          /* wall: no mass flux.  A diffuse wall closes the equations as an
+           * isothermal no-slip wall: the cell's pressure and total stress
+           * (NSF from gradients that take the wall velocity and temperature
+           * at the face, plus the cell's HoT), the work of that stress at the
+           * wall velocity and the cell's heat fluxes.  A specular wall carries
+           * the cell's pressure only. */
           const int32_t ib = -1 - nb;
-          const double* W = c->bflux + 5 * ib;
-          const double Ad = c->parea[4 * t + f];
+          const orc_bc* bw = c->bcs + c->bf[ib].bc;
+          const double p = Pc[0] * Pc[4];
           F[0] = 0.0;
-          if (wall_t > 0.0) {
-            for (int i = 0; i < 3; ++i) F[1 + i] = W[1 + i] / (wall_t * Ad) / mflux;
-            F[4] = W[4] / (wall_t * Ad) / eflux;
+          if (bw->kind == 0) {
+            const double* Sc = S + 12 * t;
+            const double Uw[3] = {bw->U[0] / d->c0, bw->U[1] / d->c0, bw->U[2] / d->c0};
+            const double sn0 = Sc[0] * N[0] + Sc[3] * N[1] + Sc[4] * N[2];
+            const double sn1 = Sc[3] * N[0] + Sc[1] * N[1] + Sc[5] * N[2];
+            const double sn2 = Sc[4] * N[0] + Sc[5] * N[1] + Sc[2] * N[2];
+            F[1] = p * N[0] + sn0;
+            F[2] = p * N[1] + sn1;
+            F[3] = p * N[2] + sn2;
+            F[4] = sn0 * Uw[0] + sn1 * Uw[1] + sn2 * Uw[2] + (Sc[6] + Sc[9]) * N[0] + (Sc[7] + Sc[10]) * N[1] +
+                   (Sc[8] + Sc[11]) * N[2];
+            F[5] = Sc[9] * N[0] + Sc[10] * N[1] + Sc[11] * N[2];
           } else {
-            const double p = Pc[0] * Pc[4];
             for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
             F[4] = 0.0;
+            F[5] = 0.0;
           }
-          F[5] = 0.0;
           lam_sum += A * (cc + 2.0 * nu * A / V);
         }
         for (int q = 0; q < 6; ++q) acc[q] += F[q] * A;

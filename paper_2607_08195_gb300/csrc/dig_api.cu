@@ -561,9 +561,6 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   P.T_init = (float)c.T_init;
   P.sigma_init = (float)std::sqrt(KB * c.T_init / m);
   for (int i = 0; i < 3; ++i) P.u0[i] = (float)c.u_init[i];
-  const double na = (double)c.n_a;
-  P.na_a = (na - 1.0) / na;
-  P.na_b = 1.0 / na;
   P.cap = c.capacity;
   cudaStream_t s = ctx->stream;
   CK(cudaMemcpyAsync((void*)P.nbr, ctx->nbr.data(), 4 * n * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -703,11 +700,13 @@ static cudaEvent_t timing_event(dig_ctx* ctx) {
   return ctx->tev[ctx->tev_used++];
 }
 
-static void pass(dig_ctx* ctx, int pass_flags, int sflags, uint32_t step_coll, uint32_t step_move, int ewma_first) {
+// ewa, ewb: weights of the moving average for this step, avg = ewa avg + ewb sample
+static void pass(dig_ctx* ctx, int pass_flags, int sflags, uint32_t step_coll, uint32_t step_move, double ewa,
+                 double ewb) {
   const int other = 1 - ctx->cur;
   if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
   launch_cell_pass(ctx->P, ctx->buf[ctx->cur], ctx->buf[other], pass_flags, sflags, step_coll, step_move,
-                   ewma_first, ctx->tile_cells, ctx->cta_threads, ctx->stream);
+                   ewa, ewb, ctx->tile_cells, ctx->cta_threads, ctx->stream);
   if (ctx->timing) cudaEventRecord(timing_event(ctx), ctx->stream);
   if (pass_flags & PASS_MOVE)
     launch_inject(ctx->P, ctx->buf[other], step_move, (sflags & S_WALLFLUX) != 0, ctx->stream);
@@ -723,7 +722,7 @@ static int settle_new_particles(dig_ctx* ctx, int64_t n) {
   launch_scan(ctx->P, ctx->stream);
   launch_scatter(ctx->P, ctx->buf[ctx->cur].mc, ctx->stream);
   // the first cell pass reads only arrivals (no stayers): gather into the other buffer
-  pass(ctx, 0, 0, 0, 0, 0);
+  pass(ctx, 0, 0, 0, 0, 0.0, 1.0);
   ctx->have_particles = true;
   return DIG_OK;
 }
@@ -803,7 +802,8 @@ int dsmc_step(dig_ctx* ctx, int32_t n_steps, int32_t flags) {
   const uint32_t t0 = (uint32_t)ctx->step;
   ctx->timing = (flags & DIG_TIMING) != 0;
   for (int s = 0; s <= n_steps; ++s) {
-    int pf = 0, sf = 0, first = 0;
+    int pf = 0, sf = 0;
+    double ewa = 0.0, ewb = 1.0;
     if (s > 0) {
       pf |= PASS_COLLIDE;
       sf = sflags & ~S_WALLFLUX;
@@ -811,13 +811,20 @@ int dsmc_step(dig_ctx* ctx, int32_t n_steps, int32_t flags) {
         CK(cudaMemsetAsync(ctx->P.pair_count, 0, sizeof(unsigned long long), ctx->stream));
         sf |= S_PAIRS;
       }
-      if (sflags & S_EWMA) first = ctx->n_ewma == 0;
+      if (sflags & S_EWMA) {
+        // Eq. exponential_average_moments with n_a effective samples; while
+        // fewer than n_a samples exist, the plain mean of all of them
+        const double m = (double)(ctx->n_ewma + 1), na = (double)ctx->cfg.n_a;
+        const double w = m < na ? m : na;
+        ewa = (w - 1.0) / w;
+        ewb = 1.0 / w;
+      }
     }
     if (s < n_steps) {
       pf |= PASS_MOVE;
       sf |= sflags & S_WALLFLUX;
     }
-    pass(ctx, pf, sf, t0 + (uint32_t)s, t0 + (uint32_t)s + 1, first);
+    pass(ctx, pf, sf, t0 + (uint32_t)s, t0 + (uint32_t)s + 1, ewa, ewb);
     if (s > 0) {
       if (sflags & S_EWMA) ctx->n_ewma++;
       if (sflags & S_WINDOW) ctx->n_win++;
@@ -1005,7 +1012,7 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
     launch_couple_s11(ctx->P, C, ctx->buf[ctx->cur], N, sub, ctx->P.aq, s);
     launch_scan(ctx->P, s);
     launch_scatter(ctx->P, ctx->buf[ctx->cur].mc, s);
-    pass(ctx, 0, 0, 0, 0, 0);
+    pass(ctx, 0, 0, 0, 0, 0.0, 1.0);
   }
   CK(cudaMemsetAsync(ctx->P.bflux, 0, 5 * std::max<size_t>(ctx->bf.size(), 1) * sizeof(double), s));
   ctx->flux_steps = 0;

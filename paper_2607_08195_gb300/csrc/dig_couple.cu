@@ -518,7 +518,6 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
     const double cc = C.snd[c];
     const double muc = C.mu[c];
     const double nu = 2.5 * muc / Pc[0];
-    const double mflux = C.rho0 * C.c0 * C.c0, eflux = mflux * C.c0;
     for (int f = 0; f < 4; ++f) {
       const Plane64 pl = P.plane[4 * (size_t)c + f];
       const double N[3] = {pl.nx, pl.ny, pl.nz};
@@ -559,18 +558,33 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
           for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
           lam_sum += A * (lm + 2.0 * nu * A * iV);
         } else {
-          const int ib = -1 - nb;
-          const double* W = P.bflux + 5 * (size_t)ib;
+          // wall: no mass flux.  A diffuse wall closes the equations as an
+          // isothermal no-slip wall: the cell's pressure and total stress (NSF
+          // from gradients that take the wall velocity and temperature at the
+          // face, plus the cell's HoT), the work of that stress at the wall
+          // velocity and the cell's heat fluxes.  A specular wall carries the
+          // cell's pressure only.
+          const int b = P.bf[-1 - nb].bc;
+          const double p = Pc[0] * Pc[4];
           F[0] = 0.0;
-          if (C.wall_t > 0.0) {
-            for (int i = 0; i < 3; ++i) F[1 + i] = W[1 + i] / (C.wall_t * Ad) / mflux;
-            F[4] = W[4] / (C.wall_t * Ad) / eflux;
+          if (kind == 0) {
+            double Sc[12];
+            for (int q = 0; q < 12; ++q) Sc[q] = C.S[(size_t)q * n + c];
+            const double Uw[3] = {C.bcU[3 * b + 0] / C.c0, C.bcU[3 * b + 1] / C.c0, C.bcU[3 * b + 2] / C.c0};
+            const double sn0 = Sc[0] * N[0] + Sc[3] * N[1] + Sc[4] * N[2];
+            const double sn1 = Sc[3] * N[0] + Sc[1] * N[1] + Sc[5] * N[2];
+            const double sn2 = Sc[4] * N[0] + Sc[5] * N[1] + Sc[2] * N[2];
+            F[1] = p * N[0] + sn0;
+            F[2] = p * N[1] + sn1;
+            F[3] = p * N[2] + sn2;
+            F[4] = sn0 * Uw[0] + sn1 * Uw[1] + sn2 * Uw[2] + (Sc[6] + Sc[9]) * N[0] + (Sc[7] + Sc[10]) * N[1] +
+                   (Sc[8] + Sc[11]) * N[2];
+            F[5] = Sc[9] * N[0] + Sc[10] * N[1] + Sc[11] * N[2];
           } else {
-            const double p = Pc[0] * Pc[4];
             for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
             F[4] = 0.0;
+            F[5] = 0.0;
           }
-          F[5] = 0.0;
           lam_sum += A * (cc + 2.0 * nu * A * iV);
         }
       }

@@ -87,7 +87,6 @@ struct Params {
   uint32_t seed_lo, seed_hi;
   float c_vhs, one_m_omega, p_inel, lb_exp, hmr;
   float T_init, sigma_init, u0[3];
-  double na_a, na_b;        // EWMA weights (n_a-1)/n_a and 1/n_a
   // per-cell grouping and sort state
   int* cs;      // [n+1] start of each cell in the current grouping
   int* as;      // [n+1] start of each cell's arrivals in aq
@@ -173,7 +172,8 @@ void launch_write(const Params& P, const Buf& out, const double* xs, const float
 void launch_scan(const Params& P, cudaStream_t s);
 void launch_scatter(const Params& P, const int* mc, cudaStream_t s);
 void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags,
-                      uint32_t step_coll, uint32_t step_move, int ewma_first, int tile_cells, int threads,
+                      uint32_t step_coll, uint32_t step_move, double ewma_a, double ewma_b, int tile_cells,
+                      int threads,
                       cudaStream_t s);
 void launch_inject(const Params& P, const Buf& out, uint32_t step, int wallflux, cudaStream_t s);
 void launch_read(const Params& P, const Buf& cur, double* xs, float* vs, float* Is, int* cells,

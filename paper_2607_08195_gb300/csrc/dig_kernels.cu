@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(128) k_collide(Params P, Buf OUT, uint32_t ste
 // is queued (output slot, input slot) for k_track, its cell left in mc.
 template <bool DIAT, int NT>
 __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass, int sflags, uint32_t step,
-                                             int ewma_first, int TC) {
+                                             double ewa, double ewb, int TC) {
   extern __shared__ __align__(16) int smem_i[];
   int* s_cs = smem_i;                      // TC + 1 slot starts
   int* s_nst = s_cs + TC + 1;              // TC stayers
@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
       const size_t o = (size_t)q * (size_t)P.n_cells + (size_t)(c0 + lc);
       const double ph = f2d(q == 0 ? (float)(s_cs[lc + 1] - s_cs[lc]) : s_sum[i]);
       if (sflags & S_INST) P.phi_inst[o] = ph;
-      if (sflags & S_EWMA) P.phi_ewma[o] = ewma_first ? ph : __fma_rn(P.na_a, P.phi_ewma[o], P.na_b * ph);
+      if (sflags & S_EWMA) P.phi_ewma[o] = __fma_rn(ewa, P.phi_ewma[o], ewb * ph);
       if (sflags & S_WINDOW) P.phi_win[o] += ph;
       if (sflags & S_CUMUL) P.phi_cum[o] += ph;
     }
@@ -1471,16 +1471,16 @@ static int sm_count() {
 
 template <bool DIAT, int NT>
 static void launch_move_t(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_move,
-                          int ewma_first, int TC, cudaStream_t s) {
+                          double ewa, double ewb, int TC, cudaStream_t s) {
   const size_t sm = move_smem(TC);
   cudaFuncSetAttribute(k_move<DIAT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_move<DIAT, NT><<<blocks_for(P.n_cells, TC), NT, sm, s>>>(P, in, out, pass, sflags, step_move, ewma_first, TC);
+  k_move<DIAT, NT><<<blocks_for(P.n_cells, TC), NT, sm, s>>>(P, in, out, pass, sflags, step_move, ewa, ewb, TC);
 }
 
 // one particle pass: order, collisions (PASS_COLLIDE), sampling and move
 // (PASS_MOVE: moving, else the positions are copied), tracking of the queue
 void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, int sflags, uint32_t step_coll,
-                      uint32_t step_move, int ewma_first, int TC, int threads, cudaStream_t s) {
+                      uint32_t step_move, double ewa, double ewb, int TC, int threads, cudaStream_t s) {
   const bool diat = P.rot_dof > 0;
   const int sms = sm_count();
   if (diat)
@@ -1496,7 +1496,7 @@ void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, 
       k_collide<false><<<blocks_for(P.n_cells, 128), 128, 0, s>>>(P, out, step_coll, rec);
     g_launches += 1;
   }
-#define DIG_MV(D, T) launch_move_t<D, T>(P, in, out, pass, sflags, step_move, ewma_first, TC, s)
+#define DIG_MV(D, T) launch_move_t<D, T>(P, in, out, pass, sflags, step_move, ewa, ewb, TC, s)
   if (threads <= 64) {
     if (diat) DIG_MV(true, 64); else DIG_MV(false, 64);
   } else if (threads <= 128) {

@@ -305,7 +305,7 @@ def seeded_dig_state(scen, steps=60, **over):
     return o, o.read(), o.moments(orc.PHI_EWMA), o.wall_flux()
 
 
-@pytest.mark.parametrize("nh,kn,passes,kmax", [(4, 0.1, 3, 1.0), (5, 0.05, 2, 0.4)])
+@pytest.mark.parametrize("nh,kn,passes,kmax", [(4, 0.1, 3, 0.6), (5, 0.05, 2, 0.4)])
 def test_couple_parity_from_written_state(nh, kn, passes, kmax):
     """S9-S11 from an identical written state (particles, moving-average sums,
     wall fluxes): identical filter flags, rejection/reconstruction counts,

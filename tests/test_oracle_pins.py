@@ -403,17 +403,21 @@ def test_moments_match_two_pass_central_moments():
 
 
 def test_ewma_window_cumulative_recurrences():
-    """P11: the EWMA follows Eq. exponential_average_moments (first value = first
-    sample), the window and cumulative sums are plain sums of the per-step sums."""
+    """P11: the moving average follows Eq. exponential_average_moments with n_a
+    effective samples once n_a samples exist, and is the plain mean of all
+    samples before (after m <= n_a steps it equals their mean); the window
+    and cumulative sums are plain sums of the per-step sums."""
     s = W.cavity_scenario(2, 3000, 0.1, seed=10)
     o = orc.Oracle(s, n_a=7)
     o.init()
     ph = []
-    for k in range(9):
+    for k in range(12):
         o.step(1, orc.EWMA | orc.WINDOW | (orc.CUMUL if k >= 4 else 0))
         ph.append(o.moments(orc.PHI_INST))
-    e = ph[0].copy()
-    for p in ph[1:]:
+        if k == 6:
+            assert np.allclose(o.moments(orc.PHI_EWMA), sum(ph) / 7.0, rtol=1e-12, atol=0)
+    e = sum(ph[:7]) / 7.0
+    for p in ph[7:]:
         e = (6.0 / 7.0) * e + p / 7.0
     assert np.allclose(o.moments(orc.PHI_EWMA), e, rtol=1e-12, atol=0)
     assert np.allclose(o.moments(orc.PHI_WINDOW), sum(ph), rtol=1e-12, atol=0)
@@ -613,6 +617,22 @@ def test_synthetic_solve_conserves_mass():
     vol = o.mesh_info()["vol"]
     half, new = o.read_couple(0), o.read_couple(2)
     assert abs((new[:, 0] * vol).sum() / (half[:, 0] * vol).sum() - 1) < 1e-12
+
+
+def test_coupling_stable_at_small_knudsen_number():
+    """The first coupling of a near-continuum cavity (Kn = 0.001: cells about
+    30 mean free paths, sampled stress and heat flux mostly statistical
+    noise) converges to a positive state: the isothermal no-slip wall
+    closure gives the synthetic equations a steady solution for any sampled
+    input (a closure by the sampled wall fluxes has none unless they balance)."""
+    s = W.cavity_scenario(6, 60_000, 0.001, seed=3)
+    o = orc.Oracle(s, N_m=500)
+    o.init()
+    o.step(200, orc.EWMA)
+    r = o.couple()
+    new = o.read_couple(2)
+    assert r["iters"] == 500 and r["residual"] < 0.05
+    assert new[:, 0].min() > 0.5 and new[:, 4].min() > 0.5 and np.all(np.isfinite(new))
 
 
 def test_reconstruction_layers():
