@@ -1611,10 +1611,13 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
 
 /* S11: recalibrate the particles of accepted cells to M^{k+1}:
  * v' = u_a + (v - u_b) sqrt(T_a / T_b), I' = I T_r,a / T_r,b (ratios clamped
- * to [1/4, 4]); number ratio r = rho_a / rho_b clamped to [1/2, 2]: delete
+ * to [1/4, 4]); number ratio r = rho_a / rho_N clamped to [1/2, 2]: delete
  * with probability 1 - r, or clone with probability r - 1 (the clone at a
  * uniform point of the cell with the recalibrated velocity).  b = the cell's
- * own sampled state, a = the solved state. */
+ * own sampled state (moving average), a = the solved state, rho_N = m F_N N_c
+ * / V the density of the N_c particles the cell holds now, so that the
+ * expected count after the adjustment is rho_a V / (m F_N): the particles are
+ * resampled to M^{k+1} and the mass the solve conserves is the particles'. */
 static void recalibrate(orc_ctx* c, const nd_t* d, int64_t* n_clone, int64_t* n_del) {
   const int64_t n = c->n_tets, N = c->N;
   *n_clone = 0;
@@ -1630,7 +1633,9 @@ static void recalibrate(orc_ctx* c, const nd_t* d, int64_t* n_clone, int64_t* n_
     rt = rt < 0.25 ? 0.25 : rt > 4.0 ? 4.0 : rt;
     double rr = d->dr > 0 ? a[5] / b[5] : 1.0;
     rr = rr < 0.25 ? 0.25 : rr > 4.0 ? 4.0 : rr;
-    double rn = a[0] / b[0];
+    const int64_t Nc = c->cstart[t + 1] - c->cstart[t];
+    const double rho_N = c->cfg.mass * c->cfg.F_N * (double)Nc / c->vol[t] / d->rho0;
+    double rn = Nc > 0 ? a[0] / rho_N : 1.0;
     rn = rn < 0.5 ? 0.5 : rn > 2.0 ? 2.0 : rn;
     const float sc = (float)sqrt(rt), fr = (float)rr;
     float ua[3], ub[3];

@@ -708,7 +708,10 @@ struct RecalCell {
   bool on;
 };
 
-__device__ __forceinline__ RecalCell recal_cell(const CoupleParams& C, int c, int n) {
+// b = the cell's own (moving-average) state, a = the solved state; the number
+// ratio is taken against the density of the N_c particles the cell holds now
+// (rho_N = m F_N N_c / V), so the expected count afterwards is rho_a V / (m F_N)
+__device__ __forceinline__ RecalCell recal_cell(const Params& P, const CoupleParams& C, int c, int n, int Nc) {
   RecalCell r;
   r.on = C.flag[c] == 1.0;
   const double b4 = C.own[(size_t)4 * n + c], a4 = C.newst[(size_t)4 * n + c];
@@ -716,7 +719,8 @@ __device__ __forceinline__ RecalCell recal_cell(const CoupleParams& C, int c, in
   rt = rt < 0.25 ? 0.25 : rt > 4.0 ? 4.0 : rt;
   double rr = C.dr > 0 ? C.newst[(size_t)5 * n + c] / C.own[(size_t)5 * n + c] : 1.0;
   rr = rr < 0.25 ? 0.25 : rr > 4.0 ? 4.0 : rr;
-  double rn = C.newst[c] / C.own[c];
+  const double rho_N = C.mass * C.FN * (double)Nc / P.vol[c] / C.rho0;
+  double rn = Nc > 0 ? C.newst[c] / rho_N : 1.0;
   r.rn = rn < 0.5 ? 0.5 : rn > 2.0 ? 2.0 : rn;
   r.sc = (float)sqrt(rt);
   r.fr = (float)rr;
@@ -735,7 +739,7 @@ __global__ void k_recal_decide(Params P, CoupleParams C, Buf CUR, int* __restric
   const int n = P.n_cells;
   for (int c = gw; c < n; c += nw) {
     const int lo = P.cs[c], hi = P.cs[c + 1];
-    const RecalCell r = recal_cell(C, c, n);
+    const RecalCell r = recal_cell(P, C, c, n, hi - lo);
     int stay = 0;
     for (int p = lo + lane; p < hi; p += 32) {
       int clone = 0;

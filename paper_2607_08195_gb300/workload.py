@@ -197,3 +197,17 @@ def random_particles(rng: np.random.Generator, scen: Scenario, n: int):
     v = (rng.standard_normal((n, 3)) * s).astype(np.float32)
     Ir = (rng.exponential(scen.T_init, size=n)).astype(np.float32)
     return x, v, Ir, cell
+
+
+def particles_per_cell(rng: np.random.Generator, scen: Scenario, k: int):
+    """Exactly k particles in every tet (uniform points, Maxwellian velocities
+    at T_init, zero rotational energy), cell-major order.
+
+    Returns (x f64 [n,3], v f32 [n,3], Ir f32 [n], cell i32 [n]), n = k * n_tets."""
+    m = scen.mesh
+    cell = np.repeat(np.arange(len(m.tets), dtype=np.int32), k)
+    w = rng.dirichlet(np.ones(4), size=len(cell))
+    x = np.einsum("nk,nkc->nc", w, m.nodes[m.tets[cell]])
+    s = math.sqrt(K_B * scen.T_init / scen.gas.mass)
+    v = (rng.standard_normal((len(cell), 3)) * s).astype(np.float32)
+    return x, v, np.zeros(len(cell), np.float32), cell

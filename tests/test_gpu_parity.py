@@ -336,12 +336,13 @@ def test_couple_parity_from_written_state(nh, kn, passes, kmax):
 
 def test_couple_fixed_point_identity_on_gpu():
     """Uniform equilibrium with the exact wall pressure: the GPU coupling leaves
-    the state and every particle unchanged (no clones or deletions)."""
-    s = W.Scenario(gas=W.ARGON, mesh=W.closed_box(2, 1e-3, W.BC_DIFFUSE), n_particles=4000, n_init=1.677e22,
-                   T_init=273.0, u_init=(0.0, 0.0, 0.0), F_N=1.677e22 * 1e-9 / 4000, dt=6.7e-8, seed=5, L=1e-3,
-                   Kn=0.1, capacity=8000)
+    the state and every particle unchanged (no clones or deletions); every
+    cell holds exactly the count its density stands for (48 x 100)."""
+    s = W.Scenario(gas=W.ARGON, mesh=W.closed_box(2, 1e-3, W.BC_DIFFUSE), n_particles=4800, n_init=1.677e22,
+                   T_init=273.0, u_init=(0.0, 0.0, 0.0), F_N=1.677e22 * 1e-9 / 4800, dt=6.7e-8, seed=5, L=1e-3,
+                   Kn=0.1, capacity=9600)
     g = dig.Solver(s, "cuda:0", N_m=40, KnD_max=1e9)
-    g.init()
+    g.write(*W.particles_per_cell(np.random.default_rng(5), s, 100))
     x0, v0, I0, c0 = g.read()
     vol = orc.Oracle(s).mesh_info()["vol"]
     kT_m = W.K_B * s.T_init / s.gas.mass
