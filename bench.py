@@ -190,6 +190,183 @@ def run_reference(args):
     return 0
 
 
+def centreline_map(scen):
+    """Profile point of every tet for the two centreline profiles of the
+    cavity: u_x against y (hexahedra of the central half in x and z) and u_y
+    against x (central half in y and z).  The Kuhn tets of a hexahedron are
+    consecutive (6 per hex, hex-major in i, j, k = x, y, z order).  Returns
+    (index into the u_x profile or -1, index into the u_y profile or -1, nh)."""
+    import numpy as np
+
+    nt = len(scen.mesh.tets)
+    nh = round((nt // 6) ** (1.0 / 3.0))
+    h = np.arange(nt) // 6
+    i, j, k = h // (nh * nh), (h // nh) % nh, h % nh
+    mid = lambda a: (a >= nh // 4) & (a < nh - nh // 4)
+    pu = np.where(mid(i) & mid(k), j, -1)
+    pv = np.where(mid(j) & mid(k), i, -1)
+    return pu, pv, nh
+
+
+def convergence_experiment(args):
+    """GPU time to the converged cavity field: plain DSMC vs DIG vs DIG with
+    the learned closure, on the near-continuum cavity (20^3 hexahedra, Kn =
+    0.001, 3M particles).  The reference field and the closure's training data
+    come from the solver itself (a DIG run); every timed run starts from the
+    initial equilibrium.  Returns the result object."""
+    import numpy as np
+    import torch
+
+    from paper_2607_08195_gb300 import dig
+    from paper_2607_08195_gb300 import workload as W
+
+    dev = "cuda:0"
+    scen = W.config_c3()
+    Uw = 50.0
+    pu, pv, nh = centreline_map(scen)
+    NSC = 200            # DSMC steps per coupling cycle
+    WIN = 50             # closure input window (the last WIN steps of a cycle)
+    fl = dig.EWMA | dig.WALLFLUX
+
+    def timed(f):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        r = f()
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) * 1e-3
+
+    def profiles(g, which=dig.PHI_EWMA):
+        """Mass-weighted centreline profiles (u_x(y), u_y(x)) of a moving
+        average or cumulative field: 2 nh points."""
+        m = g.moments(which | dig.MACRO)
+        w = m[:, 1] * vol
+        out = []
+        for idx, q in ((pu, 2), (pv, 3)):
+            sel = idx >= 0
+            den = np.bincount(idx[sel], w[sel], nh)
+            out.append(np.bincount(idx[sel], w[sel] * m[sel, q], nh) / np.maximum(den, 1e-300))
+        return np.concatenate(out)
+
+    def err(prof, ref):
+        return float(np.sqrt(np.mean((prof - ref) ** 2)) / Uw)
+
+    def cycle(g, closure):
+        if closure:
+            g.step(NSC - WIN, fl)
+            g.sample(dig.RESET_WINDOW)
+            g.step(WIN, fl | dig.WINDOW)
+        else:
+            g.step(NSC, fl)
+        return g.couple()
+
+    # 1. the solver's own data: a DIG run to steady state, then 50-step windows
+    #    (closure inputs) and the long-time average (targets, reference field)
+    g = dig.Solver(scen, dev, closure=0)
+    P = scen.mesh.nodes[scen.mesh.tets]  # tet volumes for the mass weights
+    vol = np.abs(np.einsum("ni,ni->n", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))) / 6.0
+    g.init()
+    warm_fields = []
+    for _ in range(args.conv_warm):
+        cycle(g, False)
+        warm_fields.append(profiles(g))
+    n = g.n_tets
+    nwin = args.conv_windows
+    X = torch.empty((nwin * n, 13), dtype=torch.float32, device=dev)
+    g.sample(dig.RESET_CUMUL)
+    w = 0
+    while w < nwin:
+        g.step(NSC - 4 * WIN, fl | dig.CUMUL)
+        for q in range(4):
+            g.sample(dig.RESET_WINDOW)
+            g.step(WIN, fl | dig.CUMUL | dig.WINDOW)
+            if w < nwin:
+                g.closure_features(dig.PHI_WINDOW, X[w * n:(w + 1) * n])
+                w += 1
+        g.couple()
+    Y = g.closure_targets(dig.PHI_CUM, X)
+    # the reference field: the cumulative average continued to conv_ref cycles
+    for _ in range(max(0, args.conv_ref - nwin // 4)):
+        g.step(NSC, fl | dig.CUMUL)
+        g.couple()
+    ref = profiles(g, dig.PHI_CUM)
+    warm_err = [round(err(u, ref), 4) for u in warm_fields][4::5]
+    # the estimator's noise floor: the moving-average block field of the
+    # converged DIG run over the following cycles (independent of the
+    # reference's samples) against the reference
+    post = []
+    for _ in range(args.conv_noise):
+        cycle(g, False)
+        post.append(err(profiles(g), ref))
+    noise = float(np.median(post))
+    # 2. training (the library's BF16 tensor-core kernels), 90/10 split
+    ntr = int(0.9 * nwin) * n
+    g.closure_init(scen.seed)
+    rng = np.random.default_rng(scen.seed)
+    epochs = args.conv_epochs
+    perm = torch.from_numpy(np.stack([rng.permutation(ntr) for _ in range(epochs)]).astype(np.int32)).to(dev)
+    losses, t_train = timed(lambda: g.closure_train(X[:ntr].contiguous(), Y[:ntr].contiguous(), epochs=epochs,
+                                                    batch=4096, lr=1e-3, perm=perm))
+    Xv, Yv = X[ntr:].contiguous(), Y[ntr:].contiguous()
+    mse_net = g.closure_loss(Xv, Yv)
+    mse_win = g.closure_loss(Xv, Yv, identity=True)
+    params = g.closure_get()
+    g.close()
+    del X, Y, perm
+    torch.cuda.empty_cache()
+
+    # 3. timed runs from the initial state
+    thr = max(args.conv_threshold, args.conv_threshold_factor * noise)
+    HOLD = 5
+
+    def run(kind, ncycles):
+        h = dig.Solver(scen, dev, closure=1 if kind == "dig_net" else 0)
+        if kind == "dig_net":
+            h.closure_set(params)
+        h.init()
+        t, hist, hit = 0.0, [], None
+        for k in range(ncycles):
+            if kind == "plain":
+                _, dt = timed(lambda: h.step(NSC, fl))
+            else:
+                _, dt = timed(lambda: cycle(h, kind == "dig_net"))
+            t += dt
+            e = err(profiles(h), ref)
+            hist.append((round(t, 3), round(e, 4), (k + 1) * NSC))
+        h.close()
+        torch.cuda.empty_cache()
+        # converged: the first checkpoint at or below the threshold whose next
+        # HOLD checkpoints also average at or below it
+        hit = None
+        for k in range(len(hist) - HOLD + 1):
+            if hist[k][1] <= thr and np.mean([x[1] for x in hist[k:k + HOLD]]) <= thr:
+                hit = hist[k]
+                break
+        return {"seconds": None if hit is None else hit[0], "steps": None if hit is None else hit[2],
+                "final_error": hist[-1][1], "mean_error_last_20": round(float(np.mean([x[1] for x in hist[-20:]])), 4),
+                "gpu_seconds_run": round(t, 3), "cycles": ncycles,
+                "error_every_5_cycles": [x[:2] for x in hist[4::5]]}
+
+    res = {"dig_net": run("dig_net", args.conv_cycles), "dig": run("dig", args.conv_cycles),
+           "plain_dsmc": run("plain", args.conv_plain_cycles)}
+    return {
+        "metric": "GPU seconds to the converged cavity field", "unit": "s", "higher_is_better": False,
+        "value": res["dig_net"]["seconds"], "workload": scen.name,
+        "error": "RMS over the centreline profiles u_x(y) and u_y(x) (moving average, central half of the "
+                 "cavity in the other two directions) against the reference profiles, over U_w",
+        "threshold": round(thr, 4), "noise_floor": round(noise, 4),
+        "reference": f"cumulative average of a DIG run over {max(args.conv_ref, nwin // 4)} coupling cycles after "
+                     f"{args.conv_warm} cycles",
+        "reference_profiles": [round(float(x) / Uw, 4) for x in ref],
+        "reference_run_error_every_5_cycles": warm_err,
+        "methods": res,
+        "closure": {"train_rows": ntr, "epochs": epochs, "train_gpu_seconds": round(t_train, 3),
+                    "loss_first_last": [float(losses[0]), float(losses[-1])],
+                    "heldout_mse_net": mse_net, "heldout_mse_window_hot": mse_win,
+                    "gain": mse_win / max(mse_net, 1e-300)},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,12 +376,30 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-couple", action="store_true", help="DSMC steps only (no DIG coupling)")
+    ap.add_argument("--convergence", action="store_true",
+                    help="only the time-to-converged-field experiment (plain DSMC vs DIG vs DIG + learned closure)")
+    ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-converged-field experiment")
+    ap.add_argument("--conv-warm", type=int, default=40)
+    ap.add_argument("--conv-windows", type=int, default=44)
+    ap.add_argument("--conv-epochs", type=int, default=20)
+    ap.add_argument("--conv-cycles", type=int, default=60)
+    ap.add_argument("--conv-plain-cycles", type=int, default=100)
+    ap.add_argument("--conv-ref", type=int, default=22)
+    ap.add_argument("--conv-noise", type=int, default=10)
+    ap.add_argument("--conv-threshold", type=float, default=0.02)
+    ap.add_argument("--conv-threshold-factor", type=float, default=1.5)
     ap.add_argument("--workload", default="cavity30", choices=["cavity30", "cavity20"],
                     help="cavity30: 30^3 hexes, Kn 0.01, 8M particles (the benchmark); cavity20: 20^3 hexes, "
                          "Kn 0.001, 3M particles (smaller case for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.convergence:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps(convergence_experiment(args)), flush=True)
+        return 0
 
     import numpy as np
     import torch
