@@ -324,27 +324,42 @@ def convergence_experiment(args):
         if kind == "dig_net":
             h.closure_set(params)
         h.init()
-        t, hist, hit = 0.0, [], None
+        t, hist, hit, tail, fields = 0.0, [], None, [], []
         for k in range(ncycles):
             if kind == "plain":
                 _, dt = timed(lambda: h.step(NSC, fl))
             else:
                 _, dt = timed(lambda: cycle(h, kind == "dig_net"))
             t += dt
-            e = err(profiles(h), ref)
+            prof = profiles(h)
+            e = err(prof, ref)
             hist.append((round(t, 3), round(e, 4), (k + 1) * NSC))
+            fields.append(prof)
+            if k >= ncycles - 20:
+                tail.append(prof)
         h.close()
         torch.cuda.empty_cache()
         # converged: the first checkpoint at or below the threshold whose next
         # HOLD checkpoints also average at or below it
-        hit = None
-        for k in range(len(hist) - HOLD + 1):
-            if hist[k][1] <= thr and np.mean([x[1] for x in hist[k:k + HOLD]]) <= thr:
-                hit = hist[k]
-                break
+        def first_hold(errs):
+            for k in range(len(errs) - HOLD + 1):
+                if errs[k] <= thr and np.mean(errs[k:k + HOLD]) <= thr:
+                    return k
+            return None
+
+        k_ref = first_hold([x[1] for x in hist])
+        hit = None if k_ref is None else hist[k_ref]
+        # the same criterion against the run's own final field (mean of its
+        # last 20 checkpoints), before those checkpoints: when the method
+        # settles, whatever field it settles on
+        own = np.mean(tail, axis=0)
+        k_own = first_hold([err(f, own) for f in fields[:len(fields) - len(tail)]])
         return {"seconds": None if hit is None else hit[0], "steps": None if hit is None else hit[2],
+                "seconds_to_own_final_field": None if k_own is None else hist[k_own][0],
+                "own_final_field_error": round(err(own, ref), 4),
                 "final_error": hist[-1][1], "mean_error_last_20": round(float(np.mean([x[1] for x in hist[-20:]])), 4),
                 "gpu_seconds_run": round(t, 3), "cycles": ncycles,
+                "final_profiles": [round(float(x) / Uw, 4) for x in np.mean(tail, axis=0)],
                 "error_every_5_cycles": [x[:2] for x in hist[4::5]]}
 
     res = {"dig_net": run("dig_net", args.conv_cycles), "dig": run("dig", args.conv_cycles),
@@ -379,12 +394,12 @@ def main():
     ap.add_argument("--convergence", action="store_true",
                     help="only the time-to-converged-field experiment (plain DSMC vs DIG vs DIG + learned closure)")
     ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-converged-field experiment")
-    ap.add_argument("--conv-warm", type=int, default=40)
+    ap.add_argument("--conv-warm", type=int, default=80)
     ap.add_argument("--conv-windows", type=int, default=44)
     ap.add_argument("--conv-epochs", type=int, default=20)
     ap.add_argument("--conv-cycles", type=int, default=60)
-    ap.add_argument("--conv-plain-cycles", type=int, default=100)
-    ap.add_argument("--conv-ref", type=int, default=22)
+    ap.add_argument("--conv-plain-cycles", type=int, default=160)
+    ap.add_argument("--conv-ref", type=int, default=40)
     ap.add_argument("--conv-noise", type=int, default=10)
     ap.add_argument("--conv-threshold", type=float, default=0.02)
     ap.add_argument("--conv-threshold-factor", type=float, default=1.5)

@@ -1426,11 +1426,12 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
 /* S10: steady synthetic equations (Eq. macro with the closure
  * sigma = sigma_NSF + HoT, q = q_NSF + HoT) by explicit pseudo-time
  * stepping with one global step (the smallest local step at CFL 0.5, so the
- * transient stays conservative): cell-centred finite volumes,
- * Rusanov inviscid flux, face-averaged stress and heat flux, diffuse walls as
- * isothermal no-slip walls and specular walls as slip walls (see the wall
- * faces below), open faces by the free stream.  Stops after N_m iterations or
- * when the residual L2 norm falls below eps_m times its first value. */
+ * transient stays conservative): cell-centred finite volumes, Rusanov
+ * inviscid flux with a low-Mach scaling of its velocity dissipation,
+ * face-averaged stress and heat flux, diffuse walls as isothermal no-slip
+ * walls and specular walls as slip walls (see the wall faces below), open
+ * faces by the free stream.  Stops after N_m iterations or when the residual
+ * L2 norm falls below eps_m times its first value. */
 static void prim_from_cons(const nd_t* d, const double* U, double* P) {
   const double rho = U[0];
   const double ux = U[1] / rho, uy = U[2] / rho, uz = U[3] / rho;
@@ -1521,7 +1522,28 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
           const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
           const double cl = sqrt(d->gam * Pc[4]), cr = sqrt(d->gam * (Pn[4] > 0 ? Pn[4] : 1e-12));
           const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
-          for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
+          if (nb >= 0) {
+            /* interior face: the dissipation acts on states whose velocity
+             * jump is scaled by z = min(1, max(M_L, M_R)) (low-Mach correction
+             * of Thornber et al. 2008), so that at low Mach it scales with the
+             * flow speed instead of the sound speed */
+            const double ml = sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cl;
+            const double mr = sqrt(Pn[1] * Pn[1] + Pn[2] * Pn[2] + Pn[3] * Pn[3]) / cr;
+            const double z = fmin(1.0, fmax(ml, mr));
+            double PL[6], PR[6], UL[6], UR[6];
+            memcpy(PL, Pc, sizeof PL);
+            memcpy(PR, Pn, sizeof PR);
+            for (int i = 1; i <= 3; ++i) {
+              const double m = 0.5 * (Pc[i] + Pn[i]), h = 0.5 * z * (Pc[i] - Pn[i]);
+              PL[i] = m + h;
+              PR[i] = m - h;
+            }
+            cons_from_prim(d, PL, UL);
+            cons_from_prim(d, PR, UR);
+            for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);
+          } else {
+            for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
+          }
           if (nb >= 0) {
             const double* Sc = S + 12 * t;
             const double* Sn = S + 12 * (int64_t)nb;
@@ -1546,9 +1568,9 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
           /* wall: no mass flux.  A diffuse wall closes the equations as an
            * isothermal no-slip wall: the cell's pressure and total stress
            * (NSF from gradients that take the wall velocity and temperature
-           * at the face, plus the cell's HoT), the work of that stress at the
-           * wall velocity and the cell's heat fluxes.  A specular wall carries
-           * the cell's pressure only. */
+           * at the face, plus the cell's HoT) plus the numerical friction
+           * below, the work of both at the wall velocity and the cell's heat
+           * fluxes.  A specular wall carries the cell's pressure only. */
           const int32_t ib = -1 - nb;
           const orc_bc* bw = c->bcs + c->bf[ib].bc;
           const double p = Pc[0] * Pc[4];
@@ -1559,11 +1581,20 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
             const double sn0 = Sc[0] * N[0] + Sc[3] * N[1] + Sc[4] * N[2];
             const double sn1 = Sc[3] * N[0] + Sc[1] * N[1] + Sc[5] * N[2];
             const double sn2 = Sc[4] * N[0] + Sc[5] * N[1] + Sc[2] * N[2];
-            F[1] = p * N[0] + sn0;
-            F[2] = p * N[1] + sn1;
-            F[3] = p * N[2] + sn2;
-            F[4] = sn0 * Uw[0] + sn1 * Uw[1] + sn2 * Uw[2] + (Sc[6] + Sc[9]) * N[0] + (Sc[7] + Sc[10]) * N[1] +
-                   (Sc[8] + Sc[11]) * N[2];
+            /* the interior faces' dissipation against the mirrored ghost
+             * state (velocity 2 U_w - u): a friction lambda z rho (U_w - u),
+             * lambda = |u.n| + c, z = min(1, max(|u|/c, |U_w|/c)), whose work
+             * is done at the wall velocity */
+            const double z = fmin(1.0, fmax(sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cc,
+                                            sqrt(Uw[0] * Uw[0] + Uw[1] * Uw[1] + Uw[2] * Uw[2]) / cc));
+            const double kw = (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc) * z * Pc[0];
+            double fw[3];
+            for (int i = 0; i < 3; ++i) fw[i] = -kw * (Uw[i] - Pc[1 + i]);
+            F[1] = p * N[0] + sn0 + fw[0];
+            F[2] = p * N[1] + sn1 + fw[1];
+            F[3] = p * N[2] + sn2 + fw[2];
+            F[4] = (sn0 + fw[0]) * Uw[0] + (sn1 + fw[1]) * Uw[1] + (sn2 + fw[2]) * Uw[2] + (Sc[6] + Sc[9]) * N[0] +
+                   (Sc[7] + Sc[10]) * N[1] + (Sc[8] + Sc[11]) * N[2];
             F[5] = Sc[9] * N[0] + Sc[10] * N[1] + Sc[11] * N[2];
           } else {
             for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];

@@ -450,7 +450,24 @@ __device__ __forceinline__ void interior_flux(const CoupleParams& C, const doubl
   const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
   const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
   const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
-  for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
+  // low-Mach correction (Thornber et al. 2008): the dissipation acts on states
+  // whose velocity jump is scaled by z = min(1, max(M_L, M_R))
+  const double ml = sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cl;
+  const double mr = sqrt(Pn[1] * Pn[1] + Pn[2] * Pn[2] + Pn[3] * Pn[3]) / cr;
+  const double z = fmin(1.0, fmax(ml, mr));
+  double PL[6], PR[6], UL[6], UR[6];
+  for (int q = 0; q < 6; ++q) {
+    PL[q] = Pc[q];
+    PR[q] = Pn[q];
+  }
+  for (int i = 1; i <= 3; ++i) {
+    const double m = 0.5 * (Pc[i] + Pn[i]), h = 0.5 * z * (Pc[i] - Pn[i]);
+    PL[i] = m + h;
+    PR[i] = m - h;
+  }
+  cons_from_prim(C, PL, UL);
+  cons_from_prim(C, PR, UR);
+  for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);
   double sf[6], qtf[3], qrf[3], uf[3];
   for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (Sc[q] + Sn[q]);
   for (int q = 0; q < 3; ++q) {
@@ -561,9 +578,9 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
           // wall: no mass flux.  A diffuse wall closes the equations as an
           // isothermal no-slip wall: the cell's pressure and total stress (NSF
           // from gradients that take the wall velocity and temperature at the
-          // face, plus the cell's HoT), the work of that stress at the wall
-          // velocity and the cell's heat fluxes.  A specular wall carries the
-          // cell's pressure only.
+          // face, plus the cell's HoT) plus the numerical friction below, the
+          // work of both at the wall velocity and the cell's heat fluxes.  A
+          // specular wall carries the cell's pressure only.
           const int b = P.bf[-1 - nb].bc;
           const double p = Pc[0] * Pc[4];
           F[0] = 0.0;
@@ -574,11 +591,19 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
             const double sn0 = Sc[0] * N[0] + Sc[3] * N[1] + Sc[4] * N[2];
             const double sn1 = Sc[3] * N[0] + Sc[1] * N[1] + Sc[5] * N[2];
             const double sn2 = Sc[4] * N[0] + Sc[5] * N[1] + Sc[2] * N[2];
-            F[1] = p * N[0] + sn0;
-            F[2] = p * N[1] + sn1;
-            F[3] = p * N[2] + sn2;
-            F[4] = sn0 * Uw[0] + sn1 * Uw[1] + sn2 * Uw[2] + (Sc[6] + Sc[9]) * N[0] + (Sc[7] + Sc[10]) * N[1] +
-                   (Sc[8] + Sc[11]) * N[2];
+            // the interior faces' dissipation against the mirrored ghost state
+            // (velocity 2 U_w - u): a friction lambda z rho (U_w - u), lambda =
+            // |u.n| + c, z = min(1, max(|u|/c, |U_w|/c)), its work done at U_w
+            const double z = fmin(1.0, fmax(sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cc,
+                                            sqrt(Uw[0] * Uw[0] + Uw[1] * Uw[1] + Uw[2] * Uw[2]) / cc));
+            const double kw = (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc) * z * Pc[0];
+            double fw[3];
+            for (int i = 0; i < 3; ++i) fw[i] = -kw * (Uw[i] - Pc[1 + i]);
+            F[1] = p * N[0] + sn0 + fw[0];
+            F[2] = p * N[1] + sn1 + fw[1];
+            F[3] = p * N[2] + sn2 + fw[2];
+            F[4] = (sn0 + fw[0]) * Uw[0] + (sn1 + fw[1]) * Uw[1] + (sn2 + fw[2]) * Uw[2] + (Sc[6] + Sc[9]) * N[0] +
+                   (Sc[7] + Sc[10]) * N[1] + (Sc[8] + Sc[11]) * N[2];
             F[5] = Sc[9] * N[0] + Sc[10] * N[1] + Sc[11] * N[2];
           } else {
             for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
