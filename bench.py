@@ -400,7 +400,7 @@ def main():
     ap.add_argument("--conv-cycles", type=int, default=60)
     ap.add_argument("--conv-plain-cycles", type=int, default=160)
     ap.add_argument("--conv-ref", type=int, default=40)
-    ap.add_argument("--conv-noise", type=int, default=10)
+    ap.add_argument("--conv-noise", type=int, default=20)
     ap.add_argument("--conv-threshold", type=float, default=0.02)
     ap.add_argument("--conv-threshold-factor", type=float, default=1.5)
     ap.add_argument("--workload", default="cavity30", choices=["cavity30", "cavity20"],

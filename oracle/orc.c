@@ -1199,39 +1199,87 @@ static double mu_nd(const nd_t* d, double Tt) { return d->Kn * sqrt(2.0 / M_PI) 
 
 /* boundary values of u, T_t, T_r at boundary face ib (walls: wall values;
  * open faces: free stream) */
-static void bc_values(const orc_ctx* c, const nd_t* d, int32_t ib, double* u, double* T) {
+/* values of u (3), T_t and T_r at a boundary face with outward unit normal N,
+ * seen from a cell with primitives Pc: a diffuse wall or an inflow face gives
+ * its own velocity and temperature; a specular wall the cell's velocity
+ * without its normal component and the cell's temperatures (slip, adiabatic);
+ * an outflow face the cell's own values */
+static void bc_values(const orc_ctx* c, const nd_t* d, int32_t ib, const double* Pc, const double* N, double* phi) {
   const orc_bc* b = c->bcs + c->bf[ib].bc;
-  for (int i = 0; i < 3; ++i) u[i] = b->U[i] / d->c0;
-  *T = b->T / d->T0;
+  if (b->kind == 1) {
+    const double un = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
+    for (int i = 0; i < 3; ++i) phi[i] = Pc[1 + i] - un * N[i];
+    phi[3] = Pc[4];
+    phi[4] = Pc[5];
+  } else if (b->kind == 3) {
+    for (int q = 0; q < 5; ++q) phi[q] = Pc[1 + q];
+  } else {
+    for (int i = 0; i < 3; ++i) phi[i] = b->U[i] / d->c0;
+    phi[3] = b->T / d->T0;
+    phi[4] = phi[3];
+  }
 }
 
-/* Green-Gauss gradients of u (3) and T_t, T_r at every cell:
- * grad phi_c = 1/V_c sum_f phi_f n_f A_f, phi_f = mean of the two cells,
- * boundary values at boundary faces.  prim[6n]: rho, u(3), T_t, T_r. */
+/* Least-squares gradients of u (3) and T_t, T_r at every cell: the gradient
+ * G minimising sum_f |phi_f - phi_c - G . d_f|^2 over the four faces, with
+ * d_f = x_f - x_c (nondimensional), x_f the neighbour's centroid across an
+ * interior face and the face centroid at a boundary face, where phi_f is the
+ * boundary value; G = (sum_f d_f d_f^T)^-1 sum_f d_f (phi_f - phi_c).  Exact
+ * for linear fields on any tetrahedron.  prim[6n]: rho, u(3), T_t, T_r. */
+static void tet_centroid(const orc_ctx* c, int64_t t, double s, double* x) {
+  for (int i = 0; i < 3; ++i) {
+    double a = 0.0;
+    for (int v = 0; v < 4; ++v) a += c->nodes[3 * (int64_t)c->tets[4 * t + v] + i];
+    x[i] = 0.25 * a * s;
+  }
+}
+
 static void gradients(const orc_ctx* c, const nd_t* d, const double* prim, double* grad /* [15n] */) {
   const int64_t n = c->n_tets;
+  const double s = 1.0 / d->L0;
   for (int64_t t = 0; t < n; ++t) {
-    double g[15];
-    memset(g, 0, sizeof g);
     const double* Pc = prim + 6 * t;
+    double xc[3], M[3][3], b[15];
+    memset(M, 0, sizeof M);
+    memset(b, 0, sizeof b);
+    tet_centroid(c, t, s, xc);
     for (int f = 0; f < 4; ++f) {
-      const double* N = c->pn + 12 * t + 3 * f;
-      const double A = c->parea[4 * t + f] / (d->L0 * d->L0);
       const int32_t nb = c->nbr[4 * t + f];
-      double phi[5];
+      double xf[3], phi[5];
       if (nb >= 0) {
-        const double* Pn = prim + 6 * (int64_t)nb;
-        for (int q = 0; q < 5; ++q) phi[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
+        tet_centroid(c, nb, s, xf);
+        for (int q = 0; q < 5; ++q) phi[q] = prim[6 * (int64_t)nb + 1 + q];
       } else {
-        double ub[3], Tb;
-        bc_values(c, d, -1 - nb, ub, &Tb);
-        phi[0] = ub[0]; phi[1] = ub[1]; phi[2] = ub[2]; phi[3] = Tb; phi[4] = Tb;
+        /* centroid of face f: the three vertices other than vertex f */
+        for (int i = 0; i < 3; ++i) {
+          double a = 0.0;
+          for (int v = 0; v < 4; ++v)
+            if (v != f) a += c->nodes[3 * (int64_t)c->tets[4 * t + v] + i];
+          xf[i] = a / 3.0 * s;
+        }
+        bc_values(c, d, -1 - nb, Pc, c->pn + 12 * t + 3 * f, phi);
       }
+      const double df[3] = {xf[0] - xc[0], xf[1] - xc[1], xf[2] - xc[2]};
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i][j] += df[i] * df[j];
       for (int q = 0; q < 5; ++q)
-        for (int i = 0; i < 3; ++i) g[3 * q + i] += phi[q] * N[i] * A;
+        for (int i = 0; i < 3; ++i) b[3 * q + i] += df[i] * (phi[q] - Pc[1 + q]);
     }
-    const double V = c->vol[t] / (d->L0 * d->L0 * d->L0);
-    for (int q = 0; q < 15; ++q) grad[15 * t + q] = g[q] / V;
+    /* inverse of the symmetric 3x3 matrix M by cofactors */
+    double A[3][3];
+    A[0][0] = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+    A[0][1] = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+    A[0][2] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+    A[1][0] = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+    A[1][1] = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+    A[1][2] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+    A[2][0] = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+    A[2][1] = M[0][1] * M[2][0] - M[0][0] * M[2][1];
+    A[2][2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    const double det = M[0][0] * A[0][0] + M[0][1] * A[1][0] + M[0][2] * A[2][0];
+    for (int q = 0; q < 5; ++q)
+      for (int i = 0; i < 3; ++i)
+        grad[15 * t + 3 * q + i] = (A[i][0] * b[3 * q] + A[i][1] * b[3 * q + 1] + A[i][2] * b[3 * q + 2]) / det;
   }
 }
 
@@ -1525,8 +1573,12 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
           if (nb >= 0) {
             /* interior face: the dissipation acts on states whose velocity
              * jump is scaled by z = min(1, max(M_L, M_R)) (low-Mach correction
-             * of Thornber et al. 2008), so that at low Mach it scales with the
-             * flow speed instead of the sound speed */
+             * of Thornber et al. 2008) and whose density jump keeps its
+             * acoustic part dp / c^2 and scales its entropy part
+             * drho - dp / c^2 by z (c^2 = gamma T of the face mean), with
+             * the pressures unchanged: at low Mach the dissipation of shear
+             * and entropy waves scales with the flow speed instead of the
+             * sound speed */
             const double ml = sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cl;
             const double mr = sqrt(Pn[1] * Pn[1] + Pn[2] * Pn[2] + Pn[3] * Pn[3]) / cr;
             const double z = fmin(1.0, fmax(ml, mr));
@@ -1538,6 +1590,15 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
               PL[i] = m + h;
               PR[i] = m - h;
             }
+            const double pl = Pc[0] * Pc[4], pr = Pn[0] * Pn[4];
+            const double c2 = d->gam * 0.5 * (Pc[4] + Pn[4]);
+            const double dpc = (pl - pr) / c2;
+            const double drho = dpc + z * ((Pc[0] - Pn[0]) - dpc);
+            const double rm = 0.5 * (Pc[0] + Pn[0]);
+            PL[0] = rm + 0.5 * drho;
+            PR[0] = rm - 0.5 * drho;
+            PL[4] = pl / PL[0];
+            PR[4] = pr / PR[0];
             cons_from_prim(d, PL, UL);
             cons_from_prim(d, PR, UR);
             for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);

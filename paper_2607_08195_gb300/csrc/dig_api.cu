@@ -91,7 +91,7 @@ struct dig_ctx {
   std::vector<signed char> nbrf;
   std::vector<Plane64> plane;
   std::vector<float4> plane32;
-  std::vector<double> vol, cumvol, fdtv, area;
+  std::vector<double> vol, cumvol, fdtv, area, lsqw;
   std::vector<int> fcell, fface, cfid;  // interior faces (synthetic solver)
   std::vector<BFaceDev> bf;
   std::vector<BCDev> bc;
@@ -407,6 +407,58 @@ int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t*
       ctx->cfid[4 * t + f] = id;
       ctx->cfid[4 * (size_t)nb + ctx->nbrf[4 * t + f]] = id;
     }
+  // least-squares gradient weights of every cell (synthetic solver): with
+  // d_f = x_f - x_c over the four faces (x_f the neighbour's centroid, or the
+  // face centroid at a boundary face; lengths over L_ref) and M = sum d_f d_f^T,
+  // grad phi = sum_f (M^-1 d_f) (phi_f - phi_c), exact for linear fields
+  ctx->lsqw.assign(12 * (size_t)n_tets, 0.0);
+  {
+    const double s = 1.0 / ctx->cfg.L_ref;
+    auto centroid = [&](int64_t t, double* x) {
+      for (int i = 0; i < 3; ++i) {
+        double a = 0.0;
+        for (int v = 0; v < 4; ++v) a += nodes[3 * (int64_t)tets[4 * t + v] + i];
+        x[i] = 0.25 * a * s;
+      }
+    };
+    for (int64_t t = 0; t < n_tets; ++t) {
+      double xc[3], d[4][3], M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      centroid(t, xc);
+      for (int f = 0; f < 4; ++f) {
+        const int nb = ctx->nbr[4 * t + f];
+        double xf[3];
+        if (nb >= 0) {
+          centroid(nb, xf);
+        } else {
+          for (int i = 0; i < 3; ++i) {
+            double a = 0.0;
+            for (int v = 0; v < 4; ++v)
+              if (v != f) a += nodes[3 * (int64_t)tets[4 * t + v] + i];
+            xf[i] = a / 3.0 * s;
+          }
+        }
+        for (int i = 0; i < 3; ++i) d[f][i] = xf[i] - xc[i];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) M[i][j] += d[f][i] * d[f][j];
+      }
+      double A[3][3];
+      A[0][0] = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+      A[0][1] = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+      A[0][2] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+      A[1][0] = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+      A[1][1] = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+      A[1][2] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+      A[2][0] = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+      A[2][1] = M[0][1] * M[2][0] - M[0][0] * M[2][1];
+      A[2][2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+      const double det = M[0][0] * A[0][0] + M[0][1] * A[1][0] + M[0][2] * A[2][0];
+      if (!(std::fabs(det) > 0.0)) return fail(ctx, DIG_ERR_MESH, "degenerate least-squares stencil");
+      for (int f = 0; f < 4; ++f)
+        for (int i = 0; i < 3; ++i)
+          ctx->lsqw[(size_t)(3 * f + i) * n_tets + t] =
+              (A[i][0] * d[f][0] + A[i][1] * d[f][1] + A[i][2] * d[f][2]) / det;
+    }
+  }
   ctx->mesh_ok = true;
   return DIG_OK;
 }
@@ -474,6 +526,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
   // DIG coupling
   CoupleParams& C = ctx->C;
   C.area = A.take<double>(4 * n);
+  C.lsqw = A.take<double>(12 * n);
   const size_t nbc = std::max<size_t>(ctx->bc.size(), 1);
   C.bcU = A.take<double>(3 * nbc);
   C.bcT = A.take<double>(nbc);
@@ -598,6 +651,7 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   {
     CoupleParams& C = ctx->C;
     CK(cudaMemcpyAsync((void*)C.area, ctx->area.data(), 4 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void*)C.lsqw, ctx->lsqw.data(), 12 * n * sizeof(double), cudaMemcpyHostToDevice, s));
     C.n_ifaces = (int)ctx->fcell.size();
     if (C.n_ifaces > 0) {
       CK(cudaMemcpyAsync((void*)C.fcell, ctx->fcell.data(), C.n_ifaces * sizeof(int), cudaMemcpyHostToDevice, s));

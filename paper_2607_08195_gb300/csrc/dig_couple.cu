@@ -71,10 +71,27 @@ __device__ __forceinline__ double mu_nd(const CoupleParams& C, double Tt) {
 }
 
 // boundary values (walls: wall velocity and temperature; open: free stream)
-__device__ __forceinline__ void bc_values(const Params& P, const CoupleParams& C, int ib, double* u, double* T) {
+// values of u (3), T_t and T_r at a boundary face with outward unit normal N,
+// seen from a cell with primitives Pc: a diffuse wall or an inflow face gives
+// its own velocity and temperature; a specular wall the cell's velocity without
+// its normal component and the cell's temperatures (slip, adiabatic); an
+// outflow face the cell's own values
+__device__ __forceinline__ void bc_values(const Params& P, const CoupleParams& C, int ib, const double* Pc,
+                                          const double* N, double* phi) {
   const int b = P.bf[ib].bc;
-  for (int i = 0; i < 3; ++i) u[i] = C.bcU[3 * b + i] / C.c0;
-  *T = C.bcT[b] / C.T0;
+  const int kind = P.bc[b].kind;
+  if (kind == 1) {
+    const double un = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
+    for (int i = 0; i < 3; ++i) phi[i] = Pc[1 + i] - un * N[i];
+    phi[3] = Pc[4];
+    phi[4] = Pc[5];
+  } else if (kind == 3) {
+    for (int q = 0; q < 5; ++q) phi[q] = Pc[1 + q];
+  } else {
+    for (int i = 0; i < 3; ++i) phi[i] = C.bcU[3 * b + i] / C.c0;
+    phi[3] = C.bcT[b] / C.T0;
+    phi[4] = phi[3];
+  }
 }
 
 // S9: the cell's own state and sampled stress / heat flux from summation
@@ -154,34 +171,36 @@ __device__ void nsf_mu(const CoupleParams& C, double mu, const double* G, double
   }
 }
 
-// Green-Gauss gradients of u (3), T_t, T_r of cell c from primitives prim[6][n]
+// least-squares gradients of u (3), T_t, T_r of cell c from primitives
+// prim[6][n]: grad phi = sum_f w_f (phi_f - phi_c), w_f = M^-1 d_f from the
+// mesh tables (neighbour values across interior faces, boundary values at
+// boundary faces); exact for linear fields
 __device__ __forceinline__ void grad_cell(const Params& P, const CoupleParams& C, const double* __restrict__ prim,
                                           int c, double* g) {
   const int n = P.n_cells;
+  double Pc[6];
+  for (int q = 0; q < 6; ++q) Pc[q] = prim[(size_t)q * n + c];
   for (int q = 0; q < 15; ++q) g[q] = 0.0;
-  const double iL2 = 1.0 / (C.L0 * C.L0);
   for (int f = 0; f < 4; ++f) {
-    const Plane64 pl = P.plane[4 * (size_t)c + f];
-    const double A = C.area[4 * (size_t)c + f] * iL2;
-    const double NA[3] = {pl.nx * A, pl.ny * A, pl.nz * A};
     const int nb = P.nbr[4 * (size_t)c + f];
     double phi[5];
     if (nb >= 0) {
-      for (int q = 0; q < 5; ++q) phi[q] = 0.5 * (prim[(size_t)(1 + q) * n + c] + prim[(size_t)(1 + q) * n + nb]);
+      for (int q = 0; q < 5; ++q) phi[q] = prim[(size_t)(1 + q) * n + nb];
     } else {
-      double ub[3], Tb;
-      bc_values(P, C, -1 - nb, ub, &Tb);
-      phi[0] = ub[0];
-      phi[1] = ub[1];
-      phi[2] = ub[2];
-      phi[3] = Tb;
-      phi[4] = Tb;
+      const Plane64 pl = P.plane[4 * (size_t)c + f];
+      const double N[3] = {pl.nx, pl.ny, pl.nz};
+      bc_values(P, C, -1 - nb, Pc, N, phi);
     }
-    for (int q = 0; q < 5; ++q)
-      for (int i = 0; i < 3; ++i) g[3 * q + i] += phi[q] * NA[i];
+    const double w0 = C.lsqw[(size_t)(3 * f + 0) * n + c];
+    const double w1 = C.lsqw[(size_t)(3 * f + 1) * n + c];
+    const double w2 = C.lsqw[(size_t)(3 * f + 2) * n + c];
+    for (int q = 0; q < 5; ++q) {
+      const double dq = phi[q] - Pc[1 + q];
+      g[3 * q + 0] += w0 * dq;
+      g[3 * q + 1] += w1 * dq;
+      g[3 * q + 2] += w2 * dq;
+    }
   }
-  const double iV = (C.L0 * C.L0 * C.L0) / P.vol[c];
-  for (int q = 0; q < 15; ++q) g[q] *= iV;
 }
 
 __global__ void k_cp_grad(Params P, CoupleParams C, const double* __restrict__ prim, double* __restrict__ grad) {
@@ -408,7 +427,7 @@ __global__ void k_cp_prim(Params P, CoupleParams C, int apply) {
 }
 
 // total stress and heat fluxes per cell: NSF of the current state (its
-// Green-Gauss gradients and viscosity) + HoT
+// least-squares gradients and viscosity) + HoT
 __global__ void k_cp_grad_stress(Params P, CoupleParams C) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
@@ -451,7 +470,8 @@ __device__ __forceinline__ void interior_flux(const CoupleParams& C, const doubl
   const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
   const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
   // low-Mach correction (Thornber et al. 2008): the dissipation acts on states
-  // whose velocity jump is scaled by z = min(1, max(M_L, M_R))
+  // whose velocity jump is scaled by z = min(1, max(M_L, M_R)), so that at low
+  // Mach the dissipation of shear and entropy waves scales with the flow speed
   const double ml = sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cl;
   const double mr = sqrt(Pn[1] * Pn[1] + Pn[2] * Pn[2] + Pn[3] * Pn[3]) / cr;
   const double z = fmin(1.0, fmax(ml, mr));
@@ -465,6 +485,17 @@ __device__ __forceinline__ void interior_flux(const CoupleParams& C, const doubl
     PL[i] = m + h;
     PR[i] = m - h;
   }
+  // density jump: the acoustic part dp / c^2 kept, the entropy part scaled by
+  // z (c^2 = gamma T of the face mean); the pressures unchanged
+  const double pl = Pc[0] * Pc[4], pr = Pn[0] * Pn[4];
+  const double c2 = C.gam * 0.5 * (Pc[4] + Pn[4]);
+  const double dpc = (pl - pr) / c2;
+  const double drho = dpc + z * ((Pc[0] - Pn[0]) - dpc);
+  const double rm = 0.5 * (Pc[0] + Pn[0]);
+  PL[0] = rm + 0.5 * drho;
+  PR[0] = rm - 0.5 * drho;
+  PL[4] = pl / PL[0];
+  PR[4] = pr / PR[0];
   cons_from_prim(C, PL, UL);
   cons_from_prim(C, PR, UR);
   for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);

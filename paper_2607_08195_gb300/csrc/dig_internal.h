@@ -124,6 +124,7 @@ struct CoupleScalars {
 struct CoupleParams {
   double L0, T0, rho0, c0, Kn, omega, gam, dr, Zr, mass, FN, kB, KnD_max, wall_t;
   const double* area;  // [4n] face areas
+  const double* lsqw;  // [12][n] least-squares gradient weights (M^-1 d_f)_i at row 3f + i, nondimensional
   const double* bcU;   // [3 n_bcs]
   const double* bcT;   // [n_bcs]
   const double* bcn;   // [n_bcs]

@@ -636,6 +636,37 @@ def test_coupling_stable_at_small_knudsen_number():
     assert new[:, 0].min() > 0.5 and new[:, 4].min() > 0.5 and np.all(np.isfinite(new))
 
 
+def test_synthetic_fourier_conduction():
+    """P12a, Fourier limit of the synthetic equations: a gas at rest between
+    diffuse walls at T1 (y = -L/2) and T2 (y = +L/2), specular (slip,
+    adiabatic) sides, HoT = 0 (a learned closure that outputs zero): the steady
+    solution has zero velocity, uniform pressure and the closed-form
+    temperature of steady conduction with kappa ~ mu ~ T^omega, T^(1+omega)
+    linear in y, at every cell centroid within 2 % of T2 - T1 (4^3 hexes)."""
+    T1, T2, Tw, n = 250.0, 300.0, 273.0, 1.677e22
+    wall = lambda T, kind=W.BC_DIFFUSE: dict(kind=kind, T=T, U=(0.0, 0.0, 0.0), n=0.0)
+    mesh = W.box_sides(4, 1e-3, [0, 0, 1, 2, 0, 0], [wall(Tw, W.BC_SPECULAR), wall(T1), wall(T2)])
+    g = W.ARGON
+    mu = g.mu_ref() * (Tw / g.T_ref) ** g.omega
+    s = W.Scenario(gas=g, mesh=mesh, n_particles=23040, n_init=n, T_init=Tw, u_init=(0.0, 0.0, 0.0),
+                   F_N=n * 1e-9 / 23040, dt=0.2 * mu / (n * KB * Tw), seed=5, L=1e-3, Kn=0.1, capacity=46080)
+    o = orc.Oracle(s, N_m=20000, eps_m=1e-12, KnD_max=1e9, closure=1)
+    o.init()
+    o.step(1, orc.WINDOW)
+    o.write_moments(orc.PHI_EWMA, equilibrium_phi(o, s))
+    o.closure_set(constant_net(np.zeros(8, np.float32)))
+    r = o.couple()
+    assert r["n_learned"] == o.n_tets and r["residual"] < 1e-9
+    new = o.read_couple(2)
+    y = s.mesh.nodes[s.mesh.tets].mean(axis=1)[:, 1] / 1e-3 + 0.5
+    w1 = 1.0 + g.omega
+    T_exact = (T1 ** w1 + (T2 ** w1 - T1 ** w1) * y) ** (1.0 / w1)
+    assert np.abs(new[:, 4] * Tw - T_exact).max() < 0.02 * (T2 - T1)
+    assert np.abs(new[:, 1:4]).max() < 1e-9
+    p = new[:, 0] * new[:, 4]
+    assert np.abs(p / p.mean() - 1.0).max() < 1e-9
+
+
 def test_reconstruction_layers():
     """Cells failing the cell-Knudsen criterion (Eq. criterion) are rebuilt layer
     by layer from available face neighbours (the paper's local passes): after P
