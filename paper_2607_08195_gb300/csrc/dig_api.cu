@@ -545,6 +545,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
   C.R = A.take<double>(6 * n);
   C.mu = A.take<double>(n);
   C.snd = A.take<double>(n);
+  C.mach = A.take<double>(n);
   const size_t nif = std::max<size_t>(ctx->fcell.size(), 1);
   C.fcell = A.take<int>(nif);
   C.fface = A.take<int>(nif);

@@ -423,7 +423,9 @@ __global__ void k_cp_prim(Params P, CoupleParams C, int apply) {
   prim_from_cons(C, U, Pp);
   for (int q = 0; q < 6; ++q) C.prim[(size_t)q * n + c] = Pp[q];
   C.mu[c] = mu_nd(C, Pp[4]);
-  C.snd[c] = sqrt(C.gam * Pp[4]);
+  const double cs = sqrt(C.gam * Pp[4]);
+  C.snd[c] = cs;
+  C.mach[c] = sqrt(Pp[1] * Pp[1] + Pp[2] * Pp[2] + Pp[3] * Pp[3]) / cs;
 }
 
 // total stress and heat fluxes per cell: NSF of the current state (its
@@ -454,15 +456,15 @@ __device__ __forceinline__ void inv_flux(const double* Pp, const double* U, cons
   F[5] = U[5] * un;
 }
 
-constexpr int CPT = 256;
+constexpr int CPT = 128;
 
 // Interior face flux (Rusanov inviscid flux plus the face-averaged stress and
 // heat flux) seen from cell c with outward unit normal N, and the largest
 // wave speed; from the other cell (normal -N) the flux is exactly -F.
 __device__ __forceinline__ void interior_flux(const CoupleParams& C, const double* Pc, const double* Uc,
                                               const double* Pn, const double* Un, const double* Sc,
-                                              const double* Sn, const double* N, double cl, double cr, double* F,
-                                              double* lmo) {
+                                              const double* Sn, const double* N, double cl, double cr, double ml,
+                                              double mr, double* F, double* lmo) {
   double FL[6], FR[6];
   inv_flux(Pc, Uc, N, FL);
   inv_flux(Pn, Un, N, FR);
@@ -472,32 +474,32 @@ __device__ __forceinline__ void interior_flux(const CoupleParams& C, const doubl
   // low-Mach correction (Thornber et al. 2008): the dissipation acts on states
   // whose velocity jump is scaled by z = min(1, max(M_L, M_R)), so that at low
   // Mach the dissipation of shear and entropy waves scales with the flow speed
-  const double ml = sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cl;
-  const double mr = sqrt(Pn[1] * Pn[1] + Pn[2] * Pn[2] + Pn[3] * Pn[3]) / cr;
   const double z = fmin(1.0, fmax(ml, mr));
-  double PL[6], PR[6], UL[6], UR[6];
-  for (int q = 0; q < 6; ++q) {
-    PL[q] = Pc[q];
-    PR[q] = Pn[q];
-  }
-  for (int i = 1; i <= 3; ++i) {
-    const double m = 0.5 * (Pc[i] + Pn[i]), h = 0.5 * z * (Pc[i] - Pn[i]);
-    PL[i] = m + h;
-    PR[i] = m - h;
-  }
   // density jump: the acoustic part dp / c^2 kept, the entropy part scaled by
-  // z (c^2 = gamma T of the face mean); the pressures unchanged
+  // z (c^2 = gamma T of the face mean); the pressures unchanged, so the
+  // conservative states follow from (rho', u', p) without T' = p / rho'
   const double pl = Pc[0] * Pc[4], pr = Pn[0] * Pn[4];
   const double c2 = C.gam * 0.5 * (Pc[4] + Pn[4]);
   const double dpc = (pl - pr) / c2;
   const double drho = dpc + z * ((Pc[0] - Pn[0]) - dpc);
   const double rm = 0.5 * (Pc[0] + Pn[0]);
-  PL[0] = rm + 0.5 * drho;
-  PR[0] = rm - 0.5 * drho;
-  PL[4] = pl / PL[0];
-  PR[4] = pr / PR[0];
-  cons_from_prim(C, PL, UL);
-  cons_from_prim(C, PR, UR);
+  const double rl = rm + 0.5 * drho, rr = rm - 0.5 * drho;
+  double UL[6], UR[6], ul2 = 0.0, ur2 = 0.0;
+  UL[0] = rl;
+  UR[0] = rr;
+  for (int i = 1; i <= 3; ++i) {
+    const double m = 0.5 * (Pc[i] + Pn[i]), h = 0.5 * z * (Pc[i] - Pn[i]);
+    const double a = m + h, b = m - h;
+    UL[i] = rl * a;
+    UR[i] = rr * b;
+    ul2 += a * a;
+    ur2 += b * b;
+  }
+  const double erl = C.dr > 0 ? 0.5 * C.dr * Pc[5] : 0.0, err = C.dr > 0 ? 0.5 * C.dr * Pn[5] : 0.0;
+  UL[4] = 1.5 * pl + rl * (0.5 * ul2 + erl);
+  UR[4] = 1.5 * pr + rr * (0.5 * ur2 + err);
+  UL[5] = rl * erl;
+  UR[5] = rr * err;
   for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);
   double sf[6], qtf[3], qrf[3], uf[3];
   for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (Sc[q] + Sn[q]);
@@ -540,7 +542,7 @@ __global__ void k_cp_face(Params P, CoupleParams C) {
   }
   const double cr = Pn[4] > 0 ? C.snd[nb] : sqrt(C.gam * 1e-12);
   double F[6], lm;
-  interior_flux(C, Pc, Uc, Pn, Un, Sc, Sn, N, C.snd[c], cr, F, &lm);
+  interior_flux(C, Pc, Uc, Pn, Un, Sc, Sn, N, C.snd[c], cr, C.mach[c], C.mach[nb], F, &lm);
   for (int q = 0; q < 6; ++q) C.Ff[(size_t)q * C.n_ifaces + i] = F[q];
   C.lmf[i] = lm;
 }
@@ -625,8 +627,7 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
             // the interior faces' dissipation against the mirrored ghost state
             // (velocity 2 U_w - u): a friction lambda z rho (U_w - u), lambda =
             // |u.n| + c, z = min(1, max(|u|/c, |U_w|/c)), its work done at U_w
-            const double z = fmin(1.0, fmax(sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cc,
-                                            sqrt(Uw[0] * Uw[0] + Uw[1] * Uw[1] + Uw[2] * Uw[2]) / cc));
+            const double z = fmin(1.0, fmax(C.mach[c], sqrt(Uw[0] * Uw[0] + Uw[1] * Uw[1] + Uw[2] * Uw[2]) / cc));
             const double kw = (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc) * z * Pc[0];
             double fw[3];
             for (int i = 0; i < 3; ++i) fw[i] = -kw * (Uw[i] - Pc[1 + i]);

@@ -129,6 +129,7 @@ struct CoupleParams {
   const double* bcT;   // [n_bcs]
   const double* bcn;   // [n_bcs]
   double *own, *sd, *grad, *half, *hot, *newst, *flag, *nbar, *U, *prim, *S, *R, *part, *mu, *snd;
+  double* mach;  // [n] |u| / c of the current state
   int *avail, *avail2;
   int n_ifaces;          // interior faces (each once)
   const int* fcell;      // [n_ifaces] lower-index cell of each interior face
