@@ -432,10 +432,21 @@ def main():
     flags = dig.EWMA | dig.WALLFLUX
     reports = []
 
+    phase_ev = []  # (start, after the DSMC steps, after the coupling) of each timed bench step
+
     def cycle(timing=0):
+        ev = None
+        if timing:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(g.stream)
         g.step(N_S, flags | timing)
+        if ev:
+            ev[1].record(g.stream)
         if not args.no_couple:
             reports.append(g.couple())
+        if ev:
+            ev[2].record(g.stream)
+            phase_ev.append(ev)
 
     # warm-up steps (untimed)
     for _ in range(args.warmup):
@@ -462,6 +473,10 @@ def main():
     N = g.count()
     psteps = N * N_S * args.steps
     value = psteps * world / (ms * 1e-3)
+    dsmc_ms = sum(a.elapsed_time(b) for a, b, _ in phase_ev)
+    couple_ms = sum(b.elapsed_time(c) for _, b, c in phase_ev)
+    phases = {"dsmc_ms_per_bench_step": dsmc_ms / args.steps, "couple_ms_per_bench_step": couple_ms / args.steps,
+              "dsmc_particle_steps_per_s": psteps / (dsmc_ms * 1e-3) if dsmc_ms > 0 else None}
 
     # dominant kernel: the particle pass of one DSMC step (k_order, k_collide,
     # k_move, k_track launched back to back, timed together with CUDA events
@@ -521,7 +536,7 @@ def main():
                        "dsmc_steps_per_step": N_S, "parallelism": f"replicas{world}",
                        "coupling": "none" if args.no_couple else f"DIG every {N_S} steps, N_m={g.cfg.N_m}",
                        "l2": "inputs larger than L2 (2 x 320 MB particle buffers)"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "phases": phases,
             "clocks": clk.summary(),
             "couple_last": reports[-1] if reports else None,
         }
