@@ -436,7 +436,9 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
         const double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
         const double beta = sqrt(c->cfg.mass / (2.0 * KB * bc->T));
         const double sn = -beta * (bc->U[0] * N[0] + bc->U[1] * N[1] + bc->U[2] * N[2]);
-        const double flux = bc->n / (2.0 * sqrt(M_PI) * beta) * (exp(-sn * sn) + sqrt(M_PI) * sn * (1.0 + erf(sn)));
+        /* 1 + erf(s) evaluated as erfc(-s): no cancellation on faces the
+         * stream leaves (s << 0) */
+        const double flux = bc->n / (2.0 * sqrt(M_PI) * beta) * (exp(-sn * sn) + sqrt(M_PI) * sn * erfc(-sn));
         B->expn = flux * area * c->cfg.dt / c->cfg.F_N;
         B->s = (float)sn;
         const double m1 = 0.5, m2 = sn > 0.0 ? sn * sqrt(M_PI) : 0.0;

@@ -377,8 +377,10 @@ int mesh_load(dig_ctx* ctx, const double* nodes, int64_t n_nodes, const int32_t*
         const double area = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
         const double beta = std::sqrt(ctx->cfg.mass / (2.0 * KB * fb.T));
         const double sn = -beta * (fb.U[0] * N3[0] + fb.U[1] * N3[1] + fb.U[2] * N3[2]);
+        // 1 + erf(s) evaluated as erfc(-s): no cancellation on faces the
+        // stream leaves (s << 0)
         const double flux = fb.n / (2.0 * std::sqrt(M_PI) * beta) *
-                            (std::exp(-sn * sn) + std::sqrt(M_PI) * sn * (1.0 + std::erf(sn)));
+                            (std::exp(-sn * sn) + std::sqrt(M_PI) * sn * std::erfc(-sn));
         F.expn = flux * area * ctx->cfg.dt / ctx->cfg.F_N;
         F.s = (float)sn;
         const double m1 = 0.5, m2 = sn > 0.0 ? sn * std::sqrt(M_PI) : 0.0;

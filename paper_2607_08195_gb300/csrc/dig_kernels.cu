@@ -963,7 +963,7 @@ __global__ void k_inj_count(Params P) {
   const double X = P.inflow[j].expn + P.inj_rem[j];
   const double fl = floor(X);
   P.inj_rem[j] = X - fl;
-  P.inj_cnt[j] = (int)fl;
+  P.inj_cnt[j] = fl > 0.0 ? (int)fl : 0;  // a rounding-negative expectation injects nothing
 }
 
 // single-CTA exclusive scan of the per-face counts (inflow faces are few

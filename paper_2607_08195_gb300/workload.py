@@ -13,6 +13,10 @@ Workloads (lid-driven cavity, paper Sec. 5.1, rescaled to a 1 mm argon cube):
   T_w; the wall y = +L/2 moves with velocity (U_w, 0, 0).
 * ``open_box(nh)``: the same mesh with every boundary face a free-stream inflow
   face (used for the injection/outflow checks).
+
+Hypersonic sphere (paper Sec. 5.2's sphere, procedural): ``sphere_mesh`` builds a
+Delaunay triangulation of seeded points on concentric shells graded toward the
+body; the far field is a free-stream face set, the body a diffuse wall.
 """
 from __future__ import annotations
 
@@ -132,6 +136,85 @@ def box_sides(nh: int, L: float, side_bc, bcs) -> Mesh:
     return Mesh(nodes, tets, face_tag, list(bcs))
 
 
+def _shell_points(n: int, r: float, rng: np.random.Generator) -> np.ndarray:
+    """n points spread evenly over the sphere of radius r (Fibonacci lattice),
+    turned by a random rotation (random unit quaternion)."""
+    i = np.arange(n) + 0.5
+    phi = np.arccos(1.0 - 2.0 * i / n)
+    th = math.pi * (1.0 + 5.0 ** 0.5) * i
+    p = np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], axis=1)
+    a, b, c, d = rng.standard_normal(4)
+    q = math.sqrt(a * a + b * b + c * c + d * d)
+    a, b, c, d = a / q, b / q, c / q, d / q
+    rot = np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                    [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                    [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+    return r * (p @ rot.T)
+
+
+def sphere_mesh(h_w: float, R: float = 0.1, R_far: float = 1.0, grading: float = 20.0, seed: int = 4,
+                T_w: float = 500.0, n_inf: float = 1e21, T_inf: float = 200.0, U_inf=(2635.0, 0.0, 0.0)) -> Mesh:
+    """Sphere of radius R in a spherical far field of radius R_far: Delaunay
+    tetrahedra of a seeded point cloud on concentric shells whose spacing grows
+    geometrically from h_w at the body to grading * h_w at the far field; the
+    tetrahedra inside the body are removed.  Boundary faces nearer the body than
+    the far field are the body wall (diffuse at T_w, bcs[0]); the others are
+    free-stream faces (n_inf, T_inf, U_inf; bcs[1])."""
+    import os
+    import tempfile
+
+    from scipy.spatial import Delaunay
+
+    bcs = [dict(kind=BC_DIFFUSE, T=T_w, U=(0.0, 0.0, 0.0), n=0.0),
+           dict(kind=BC_INFLOW, T=T_inf, U=tuple(U_inf), n=n_inf)]
+    # the triangulation of a large point cloud takes a minute: cached per parameters
+    cache = os.path.join(os.environ.get("DIG_MESH_CACHE", tempfile.gettempdir()),
+                         f"dig_sphere_{h_w:.6g}_{R:.6g}_{R_far:.6g}_{grading:.6g}_{seed}.npz")
+    if os.path.exists(cache):
+        z = np.load(cache)
+        return Mesh(z["nodes"], z["tets"], z["face_tag"], bcs)
+    rng = np.random.default_rng(seed)
+    a = math.log(grading) / math.log(R_far / R)
+    radii = [R]
+    while True:
+        h = h_w * (radii[-1] / R) ** a
+        if radii[-1] + h >= R_far - 0.3 * h:
+            break
+        radii.append(radii[-1] + h)
+    radii.append(R_far)
+    pts = []
+    for r in radii:
+        h = h_w * (r / R) ** a
+        pts.append(_shell_points(max(12, int(round(4.0 * math.pi * r * r / (0.866 * h * h)))), r, rng))
+    nodes = np.concatenate(pts).astype(np.float64)
+    tets = Delaunay(nodes).simplices.astype(np.int64)
+    tets = tets[np.linalg.norm(nodes[tets].mean(axis=1), axis=1) > R]
+    # boundary faces: the faces (opposite vertex f) that no other kept tet shares
+    nt = len(tets)
+    tri = np.stack([np.delete(tets, f, axis=1) for f in range(4)], axis=1).reshape(-1, 3)
+    tri.sort(axis=1)
+    key = (tri[:, 0] * (len(nodes) + 1) + tri[:, 1]) * (len(nodes) + 1) + tri[:, 2]
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    dup = np.zeros(len(ks), bool)
+    dup[1:] |= ks[1:] == ks[:-1]
+    dup[:-1] |= ks[:-1] == ks[1:]
+    boundary = np.empty(len(ks), bool)
+    boundary[order] = ~dup
+    boundary = boundary.reshape(nt, 4)
+    fc = np.stack([nodes[np.delete(tets, f, axis=1)].mean(axis=1) for f in range(4)], axis=1)
+    far = np.linalg.norm(fc, axis=2) > 0.5 * (R + R_far)
+    face_tag = np.where(boundary, np.where(far, 1, 0), -1).astype(np.int32)
+    tets = tets.astype(np.int32)
+    try:
+        tmp = cache + f".{os.getpid()}.npz"
+        np.savez(tmp, nodes=nodes, tets=tets, face_tag=face_tag)
+        os.replace(tmp, cache)
+    except OSError:
+        pass
+    return Mesh(nodes, tets, face_tag, bcs)
+
+
 @dataclasses.dataclass
 class Scenario:
     """Everything a run needs besides the mesh; the same values feed both sides."""
@@ -182,6 +265,31 @@ def config_c2(seed: int = 2) -> Scenario:
 def config_c3(seed: int = 3) -> Scenario:
     """Argon cavity, 20^3 hexes x 6 tets = 48,000 tets, Kn = 0.001, 3M particles."""
     return cavity_scenario(20, 3_000_000, 0.001, seed, name="cavity-20x20x20-Kn0.001-3M")
+
+
+def sphere_scenario(h_w: float, n_particles: int, seed: int = 4, gas: Gas = ARGON, R: float = 0.1,
+                    R_far: float = 1.0, n_inf: float = 1e21, T_inf: float = 200.0, U: float = 2635.0,
+                    T_w: float = 500.0, name: str = "") -> Scenario:
+    """Hypersonic argon over a sphere (Mach 10 at 200 K: U = 2635 m/s along +x,
+    n = 1e21 m^-3, diffuse wall at 500 K), initial state the free stream.
+    dt = min(0.2 tau, 0.2 h_w / (U + 3 sqrt(2 k T / m))) with tau = mu / p of
+    the free stream; L_ref = 2R and Kn from the cavity's Kn definition."""
+    mesh = sphere_mesh(h_w, R=R, R_far=R_far, seed=seed, T_w=T_w, n_inf=n_inf, T_inf=T_inf, U_inf=(U, 0.0, 0.0))
+    mu = gas.mu_ref() * (T_inf / gas.T_ref) ** gas.omega
+    p = n_inf * K_B * T_inf
+    dt = min(0.2 * mu / p, 0.2 * h_w / (U + 3.0 * math.sqrt(2.0 * K_B * T_inf / gas.mass)))
+    P = mesh.nodes[mesh.tets]
+    V = float(np.abs(np.einsum("ni,ni->n", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))).sum()) / 6.0
+    L = 2.0 * R
+    Kn = mu / (p * L) * math.sqrt(math.pi * K_B / gas.mass * T_inf / 2.0)
+    return Scenario(gas=gas, mesh=mesh, n_particles=n_particles, n_init=n_inf, T_init=T_inf, u_init=(U, 0.0, 0.0),
+                    F_N=n_inf * V / n_particles, dt=dt, seed=seed, L=L, Kn=Kn, capacity=2 * n_particles,
+                    name=name or f"sphere-{len(mesh.tets)}tets")
+
+
+def config_c4(seed: int = 4) -> Scenario:
+    """Hypersonic argon sphere: R = 0.1 m, far field 1 m, ~2M tets graded 20x toward the wall, 100M particles."""
+    return sphere_scenario(0.0036, 100_000_000, seed, name="sphere-R0.1-Ma10-2Mtets-100M")
 
 
 def random_particles(rng: np.random.Generator, scen: Scenario, n: int):

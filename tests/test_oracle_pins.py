@@ -454,6 +454,41 @@ def test_sort_by_cell_matches_stable_argsort():
 
 
 # --------------------------------------------------------------- injection (S4)
+def test_sphere_mesh_and_tracking():
+    """Procedural sphere workload: the graded Delaunay mesh of the shell
+    between the body (R = 0.1 m) and the far field (1 m) fills the region
+    between the convex hulls of the body's and the far field's points exactly
+    (no gap, no overlap; scipy's hull volumes), its boundary faces lie
+    on the two spheres and carry the body-wall and free-stream tags, and after
+    5 steps of the oracle (injection, body reflections, outflow) every particle
+    lies inside the tet it was tracked to (P7 on an unstructured mesh)."""
+    R, R_far = 0.1, 1.0
+    s = W.sphere_scenario(0.02, 8000, seed=5)
+    m = s.mesh
+    P = m.nodes[m.tets]
+    vol = np.abs(np.einsum("ni,ni->n", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))) / 6.0
+    from scipy.spatial import ConvexHull
+
+    rn = np.linalg.norm(m.nodes, axis=1)
+    hull = ConvexHull(m.nodes).volume - ConvexHull(m.nodes[rn < R * (1 + 1e-9)]).volume
+    assert vol.min() > 0 and abs(vol.sum() / hull - 1.0) < 1e-9
+    fc = np.stack([np.delete(P, f, axis=1).mean(axis=1) for f in range(4)], axis=1)
+    r = np.linalg.norm(fc, axis=2)
+    body, far = m.face_tag == 0, m.face_tag == 1
+    assert body.sum() > 100 and far.sum() > 20
+    assert np.all((r[body] > 0.9 * R) & (r[body] <= R * (1 + 1e-12)))
+    assert np.all((r[far] > 0.9 * R_far) & (r[far] <= R_far * (1 + 1e-12)))
+    o = orc.Oracle(s)
+    o.init()
+    o.step(5, orc.EWMA)
+    x, v, I, cell = o.read()
+    c = o.counters()
+    assert c["stuck"] == 0 and c["injected"] > 0 and c["removed"] > 0
+    assert len(cell) == s.n_particles + c["injected"] - c["removed"]
+    lam = barycentric(m.nodes, m.tets, cell, x)
+    assert lam.min() >= -1e-9, lam.min()
+
+
 def inflow_scenario(U, T=273.0, n=1e20, sides_inflow=(0,), dt=1e-9, F_N=None, n_particles=0, L=1e-3, seed=31):
     """One-hex box: the listed sides are free-stream inflow, the others outflow;
     collisions switched off (tiny molecular diameter)."""
