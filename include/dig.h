@@ -224,14 +224,18 @@ int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches);
  * from the moving-average sums, M^{k+1/2} and HoT = sampled stress / heat
  * flux minus their NSF values (Sec. 3.1, Eq. hot_extraction), the cell
  * Knudsen criterion Kn_Delta <= KnD_max (Sec. 3.2) with `passes` layers of
- * equal-weight neighbour reconstruction, the steady synthetic equations
+ * equal-weight neighbour reconstruction (rejected cells beyond them are
+ * filled the same way, layer by layer, up to 64 more layers, and are not
+ * recalibrated), the steady synthetic equations
  * (Eq. macro with Eq. synthetic_closure) solved for M^{k+1} (at most N_m
  * iterations or residual below eps_m of its first value), and the particles
  * of accepted cells recalibrated to M^{k+1} (velocities shifted and scaled,
  * rotational energies scaled, particles cloned or deleted with the density
- * ratio).  Diffuse walls close the synthetic equations as isothermal no-slip
- * walls (the wall velocity and temperature enter the gradients; the wall
- * face carries the cell's pressure, total stress and heat flux), specular
+ * ratio against the density of the particles the cell holds).  Diffuse walls
+ * close the synthetic equations as isothermal no-slip walls (the wall velocity
+ * and temperature enter the gradients; the wall face carries the cell's
+ * pressure, total stress and heat flux and the flux scheme's dissipation
+ * against the mirrored state), specular
  * walls as slip walls (pressure only); the wall fluxes sampled with
  * DIG_WALLFLUX remain a DSMC output (dig_wall_flux).  With
  * cfg.closure = 1 and closure parameters set, the translational HoT (sigma,
@@ -255,7 +259,8 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out);
  * (density / (m n_init), velocity / sqrt(k T_init / m), temperature / T_init):
  * which 0 = M^{k+1/2} fed to the solver (rho, u(3), T_t, T_r; k = 6),
  * 1 = HoT (sigma xx,yy,zz,xy,xz,yz, q_t(3), q_r(3); k = 12), 2 = M^{k+1}
- * (k = 6), 3 = cell flags (1 accepted, 2 reconstructed, 0 neither; k = 1),
+ * (k = 6), 3 = cell flags (1 accepted, 2 reconstructed, 3 filled beyond the
+ * reconstruction layers, 0 none of these; k = 1),
  * 4 = each cell's own sampled state (k = 6) */
 int dig_read_couple(dig_ctx* ctx, int32_t which, double* host_out, int64_t cap);
 /* overwrite summation variables (which = DIG_PHI_*) from host in[n_tets][17] */

@@ -1430,7 +1430,8 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
     /* local cell Knudsen number (Eq. cell_kn_stability) */
     const double V = c->vol[t] / (d->L0 * d->L0 * d->L0);
     const double dc = 2.0 * cbrt(3.0 * V / (4.0 * M_PI));
-    int ok = nbar[t] > 0.0 && P[0] > 0.0 && P[4] > 0.0;
+    /* a state needs at least two particles on average to have a temperature */
+    int ok = nbar[t] >= 2.0 && P[0] > 0.0 && P[4] > 0.0;
     for (int q = 0; q < 6 && ok; ++q) ok = isfinite(P[q]);
     for (int q = 0; q < 12 && ok; ++q) ok = isfinite(H[q]);
     if (ok) {
@@ -1469,6 +1470,35 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
       (*n_rec)++;
     }
     memcpy(avail, nxt, n);
+  }
+  /* fill layers: rejected cells beyond the reconstruction layers still need a
+   * state for the solve; they are filled the same way, layer by layer (flag 3,
+   * not counted as reconstructed), until a layer fills nothing or after
+   * ORC_FILL_LAYERS layers.  They are not recalibrated. */
+  for (int layer = 0; layer < ORC_FILL_LAYERS; ++layer) {
+    int64_t filled = 0;
+    memcpy(nxt, avail, n);
+    for (int64_t t = 0; t < n; ++t) {
+      if (avail[t]) continue;
+      double acc[18];
+      memset(acc, 0, sizeof acc);
+      int cnt = 0;
+      for (int f = 0; f < 4; ++f) {
+        const int32_t nb = c->nbr[4 * t + f];
+        if (nb < 0 || !avail[nb]) continue;
+        for (int q = 0; q < 6; ++q) acc[q] += c->cp_half[6 * (int64_t)nb + q];
+        for (int q = 0; q < 12; ++q) acc[6 + q] += c->cp_hot[12 * (int64_t)nb + q];
+        cnt++;
+      }
+      if (cnt == 0) continue;
+      for (int q = 0; q < 6; ++q) c->cp_half[6 * t + q] = acc[q] / cnt;
+      for (int q = 0; q < 12; ++q) c->cp_hot[12 * t + q] = acc[6 + q] / cnt;
+      nxt[t] = 1;
+      c->cp_flag[t] = 3.0;
+      filled++;
+    }
+    memcpy(avail, nxt, n);
+    if (filled == 0) break;
   }
   free(nxt); free(avail); free(nbar);
 }
@@ -1664,7 +1694,8 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
             F[4] = 0.0;
             F[5] = 0.0;
           }
-          lam_sum += A * (cc + 2.0 * nu * A / V);
+          /* wave speed of the wall face: |u.n| + c, as for the interior faces */
+          lam_sum += A * (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc + 2.0 * nu * A / V);
         }
         for (int q = 0; q < 6; ++q) acc[q] += F[q] * A;
       }

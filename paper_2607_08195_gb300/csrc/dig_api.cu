@@ -561,6 +561,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
   C.ypred = A.take<float>((size_t)MLP_NOUT * n);
   C.wnorm = A.take<double>(2 * n);
   C.stats = A.take<unsigned long long>(8);
+  C.fillcnt = A.take<int>(DIG_FILL_LAYERS);
   ctx->cl_p = A.take<float>(MLP_NPARAM);
   ctx->cl_m = A.take<float>(MLP_NPARAM);
   ctx->cl_v = A.take<float>(MLP_NPARAM);
@@ -1044,6 +1045,7 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
   CoupleParams& C = ctx->C;
   C.wall_t = ctx->flux_steps > 0 ? (double)ctx->flux_steps * ctx->cfg.dt : 0.0;
   CK(cudaMemsetAsync(C.stats, 0, 5 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(C.fillcnt, 0, DIG_FILL_LAYERS * sizeof(int), s));
   CK(cudaMemsetAsync(C.scal, 0, sizeof(CoupleScalars), s));
   CK(cudaMemsetAsync(C.clone_total, 0, sizeof(int), s));
   const bool learned = ctx->cfg.closure == 1 && ctx->cl_set;

@@ -242,7 +242,8 @@ __global__ void k_cp_hot(Params P, CoupleParams C) {
   for (int q = 0; q < 6; ++q) C.half[(size_t)q * n + c] = Pc[q];
   const double V = P.vol[c] / (C.L0 * C.L0 * C.L0);
   const double dc = 2.0 * cbrt(3.0 * V / (4.0 * M_PI));
-  bool ok = C.nbar[c] > 0.0 && Pc[0] > 0.0 && Pc[4] > 0.0;
+  // a state needs at least two particles on average to have a temperature
+  bool ok = C.nbar[c] >= 2.0 && Pc[0] > 0.0 && Pc[4] > 0.0;
   for (int q = 0; q < 6 && ok; ++q) ok = isfinite(Pc[q]);
   for (int q = 0; q < 12 && ok; ++q) ok = isfinite(H[q]);
   if (ok) {
@@ -344,10 +345,17 @@ __global__ void k_cl_apply(Params P, CoupleParams C, const float* __restrict__ Y
 
 // one reconstruction pass: a rejected cell with available face neighbours
 // takes their equal-weight mean of state and HoT
-__global__ void k_cp_recon(Params P, CoupleParams C, const int* __restrict__ av_in, int* __restrict__ av_out) {
+// one reconstruction layer: a rejected cell with available face neighbours
+// takes their equal-weight mean (state and HoT) and becomes available.  The
+// first `passes` layers are the reconstruction (flag 2); later fill layers
+// (fill >= 0: flag 3, counted in fillcnt[fill]) stop at the first layer after
+// one that filled nothing
+__global__ void k_cp_recon(Params P, CoupleParams C, const int* __restrict__ av_in, int* __restrict__ av_out,
+                           int fill) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
   if (c >= n) return;
+  if (fill > 0 && C.fillcnt[fill - 1] == 0) return;
   if (av_in[c]) {
     av_out[c] = 1;
     return;
@@ -366,8 +374,13 @@ __global__ void k_cp_recon(Params P, CoupleParams C, const int* __restrict__ av_
   if (cnt == 0) return;
   for (int q = 0; q < 6; ++q) C.half[(size_t)q * n + c] = acc[q] / cnt;
   for (int q = 0; q < 12; ++q) C.hot[(size_t)q * n + c] = acc[6 + q] / cnt;
-  C.flag[c] = 2.0;
-  atomicAdd(C.stats + 1, 1ull);
+  if (fill < 0) {
+    C.flag[c] = 2.0;
+    atomicAdd(C.stats + 1, 1ull);
+  } else {
+    C.flag[c] = 3.0;
+    atomicAdd(C.fillcnt + fill, 1);
+  }
 }
 
 __device__ __forceinline__ void cons_from_prim(const CoupleParams& C, const double* Pp, double* U) {
@@ -642,7 +655,8 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
             F[4] = 0.0;
             F[5] = 0.0;
           }
-          lam_sum += A * (cc + 2.0 * nu * A * iV);
+          // wave speed of the wall face: |u.n| + c, as for the interior faces
+          lam_sum += A * (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc + 2.0 * nu * A * iV);
         }
       }
       for (int q = 0; q < 6; ++q) acc[q] += F[q] * A;
@@ -970,12 +984,20 @@ void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const 
   int* a = C.avail;
   int* b = C.avail2;
   for (int q = 0; q < passes; ++q) {
-    k_cp_recon<<<nb, CPT, 0, s>>>(P, C, a, b);
+    k_cp_recon<<<nb, CPT, 0, s>>>(P, C, a, b, -1);
     int* t = a;
     a = b;
     b = t;
   }
-  g_launches += 3 + passes;
+  // fill layers: rejected cells beyond the reconstruction layers still need a
+  // state for the solve; they are filled the same way, layer by layer
+  for (int q = 0; q < DIG_FILL_LAYERS; ++q) {
+    k_cp_recon<<<nb, CPT, 0, s>>>(P, C, a, b, q);
+    int* t = a;
+    a = b;
+    b = t;
+  }
+  g_launches += 3 + passes + DIG_FILL_LAYERS;
 }
 
 void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double eps, cudaStream_t s) {

@@ -121,6 +121,9 @@ struct CoupleScalars {
   int iters, done, bad, pad;
 };
 
+// most fill layers after the reconstruction layers (see k_cp_recon)
+constexpr int DIG_FILL_LAYERS = 64;
+
 struct CoupleParams {
   double L0, T0, rho0, c0, Kn, omega, gam, dr, Zr, mass, FN, kB, KnD_max, wall_t;
   const double* area;  // [4n] face areas
@@ -140,6 +143,7 @@ struct CoupleParams {
   float* ypred;   // [n][8] closure outputs
   double* wnorm;  // [2][n] window density and temperature (0: invalid row)
   unsigned long long* stats;  // rejected, reconstructed, cloned, deleted, learned
+  int* fillcnt;               // [DIG_FILL_LAYERS] cells filled per fill layer
   CoupleScalars* scal;
   int* rpart;
   int* clone_total;

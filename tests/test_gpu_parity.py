@@ -413,3 +413,28 @@ def test_sphere_full_size_properties():
     bary = np.concatenate([1.0 - lam.sum(axis=1, keepdims=True), lam], axis=1)
     assert bary.min() >= -1e-9, bary.min()
     assert np.all(np.isfinite(v[k]))
+
+
+def test_couple_parity_sphere():
+    """DIG coupling on the hypersonic sphere (13,012 tets, 60,000 particles):
+    free-stream faces in the synthetic solve, cells rejected for holding
+    fewer than two particles on average, reconstruction layers and fill
+    layers beyond them; identical flags and counts, FP64 fields within 1e-9,
+    identical recalibrated particle cells."""
+    s = W.sphere_scenario(0.02, 60_000, seed=4)
+    over = dict(N_m=60, passes=3, KnD_max=1.0)
+    o, (x, v, Ir, cell), phi, wf = seeded_dig_state(s, steps=40, **over)
+    g = dig.Solver(s, "cuda:0", **over)
+    g.write(x, v, Ir, cell)
+    g.write_moments(dig.PHI_EWMA, phi)
+    rg, ro = g.couple(), o.couple()
+    for k in ("iters", "n_rejected", "n_reconstructed", "n_cloned", "n_deleted"):
+        assert rg[k] == ro[k], (k, rg[k], ro[k])
+    flags = o.read_couple(3)[:, 0]
+    assert np.array_equal(g.read_couple(3)[:, 0], flags)
+    assert (flags == 3).sum() > 0 and (flags == 2).sum() > 0 and (flags == 1).sum() > 0
+    for which in (4, 0, 1, 2):
+        a, b = g.read_couple(which), o.read_couple(which)
+        scale = np.abs(b).max(axis=0) + 1e-30
+        assert np.all(np.abs(a - b) <= 1e-9 * scale), (which, np.abs(a - b).max())
+    assert np.array_equal(g.read()[3], o.read()[3])
