@@ -741,6 +741,7 @@ __global__ void __launch_bounds__(256) k_order(Params P, Buf IN, Buf OUT) {
       OUT.vx[base + k] = IN.vx[q];
       OUT.vy[base + k] = IN.vy[q];
       OUT.vz[base + k] = IN.vz[q];
+      OUT.mc[base + k] = c;  // the slot's cell until k_move writes the destination
       if (DIAT) OUT.Ir[base + k] = IN.Ir[q];
     }
     if (live && gl == 0) {
@@ -821,16 +822,8 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
     const bool valid = slot < hi;
     int lc = -1, st = -1, nb = -1;
     if (valid) {
-      int l = 0, h = nc;  // the cell of the slot: last lc with s_cs[lc] <= slot
-      while (h - l > 1) {
-        const int m = (l + h) >> 1;
-        if (s_cs[m] <= slot)
-          l = m;
-        else
-          h = m;
-      }
-      lc = l;
-      const int cell = c0 + lc;
+      const int cell = OUT.mc[slot];  // the slot's cell, written by k_order
+      lc = cell - c0;
       const int q = P.src[slot];
       double x = IN.x[q], y = IN.y[q], z = IN.z[q];
       st = 0;
