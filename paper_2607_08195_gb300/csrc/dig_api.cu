@@ -91,7 +91,7 @@ struct dig_ctx {
   std::vector<signed char> nbrf;
   std::vector<Plane64> plane;
   std::vector<float4> plane32;
-  std::vector<double> vol, cumvol, fdtv, area, lsqw;
+  std::vector<double> vol, cumvol, fdtv, area, lsqw, vnd, ivnd;
   std::vector<int> fcell, fface, cfid;  // interior faces (synthetic solver)
   std::vector<BFaceDev> bf;
   std::vector<BCDev> bc;
@@ -529,6 +529,8 @@ static size_t layout(dig_ctx* ctx, char* base) {
   CoupleParams& C = ctx->C;
   C.area = A.take<double>(4 * n);
   C.lsqw = A.take<double>(12 * n);
+  C.vnd = A.take<double>(n);
+  C.ivnd = A.take<double>(n);
   const size_t nbc = std::max<size_t>(ctx->bc.size(), 1);
   C.bcU = A.take<double>(3 * nbc);
   C.bcT = A.take<double>(nbc);
@@ -656,6 +658,17 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
     CoupleParams& C = ctx->C;
     CK(cudaMemcpyAsync((void*)C.area, ctx->area.data(), 4 * n * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync((void*)C.lsqw, ctx->lsqw.data(), 12 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    {
+      const double L3 = c.L_ref * c.L_ref * c.L_ref;
+      ctx->vnd.resize(n);
+      ctx->ivnd.resize(n);
+      for (size_t t = 0; t < n; ++t) {
+        ctx->vnd[t] = ctx->vol[t] / L3;
+        ctx->ivnd[t] = L3 / ctx->vol[t];
+      }
+      CK(cudaMemcpyAsync((void*)C.vnd, ctx->vnd.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync((void*)C.ivnd, ctx->ivnd.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     C.n_ifaces = (int)ctx->fcell.size();
     if (C.n_ifaces > 0) {
       CK(cudaMemcpyAsync((void*)C.fcell, ctx->fcell.data(), C.n_ifaces * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -676,6 +689,7 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
       CK(cudaMemcpyAsync((void*)C.bcn, ctx->bcn.data(), ctx->bcn.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     }
     C.L0 = c.L_ref;
+    C.iL2 = 1.0 / (c.L_ref * c.L_ref);
     C.T0 = c.T_init;
     C.rho0 = c.mass * c.n_init;
     C.c0 = std::sqrt(KB / c.mass * C.T0);

@@ -175,6 +175,9 @@ __device__ void nsf_mu(const CoupleParams& C, double mu, const double* G, double
 // prim[6][n]: grad phi = sum_f w_f (phi_f - phi_c), w_f = M^-1 d_f from the
 // mesh tables (neighbour values across interior faces, boundary values at
 // boundary faces); exact for linear fields
+// (NF = 5 fields; NF = 4 leaves out T_r, whose gradient a monatomic gas does
+// not use)
+template <int NF = 5>
 __device__ __forceinline__ void grad_cell(const Params& P, const CoupleParams& C, const double* __restrict__ prim,
                                           int c, double* g) {
   const int n = P.n_cells;
@@ -185,7 +188,7 @@ __device__ __forceinline__ void grad_cell(const Params& P, const CoupleParams& C
     const int nb = P.nbr[4 * (size_t)c + f];
     double phi[5];
     if (nb >= 0) {
-      for (int q = 0; q < 5; ++q) phi[q] = prim[(size_t)(1 + q) * n + nb];
+      for (int q = 0; q < NF; ++q) phi[q] = prim[(size_t)(1 + q) * n + nb];
     } else {
       const Plane64 pl = P.plane[4 * (size_t)c + f];
       const double N[3] = {pl.nx, pl.ny, pl.nz};
@@ -194,7 +197,7 @@ __device__ __forceinline__ void grad_cell(const Params& P, const CoupleParams& C
     const double w0 = C.lsqw[(size_t)(3 * f + 0) * n + c];
     const double w1 = C.lsqw[(size_t)(3 * f + 1) * n + c];
     const double w2 = C.lsqw[(size_t)(3 * f + 2) * n + c];
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < NF; ++q) {
       const double dq = phi[q] - Pc[1 + q];
       g[3 * q + 0] += w0 * dq;
       g[3 * q + 1] += w1 * dq;
@@ -443,18 +446,21 @@ __global__ void k_cp_prim(Params P, CoupleParams C, int apply) {
 
 // total stress and heat fluxes per cell: NSF of the current state (its
 // least-squares gradients and viscosity) + HoT
+// (DI: diatomic; a monatomic gas has no rotational heat flux, whose terms are
+// then left out: they are zero)
+template <bool DI>
 __global__ void k_cp_grad_stress(Params P, CoupleParams C) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
   if (c >= n || C.scal->done) return;
   double G[15];
-  grad_cell(P, C, C.prim, c, G);
+  grad_cell<DI ? 5 : 4>(P, C, C.prim, c, G);
   double sig[6], qt[3], qr[3];
   nsf_mu(C, C.mu[c], G, sig, qt, qr);
   for (int q = 0; q < 6; ++q) C.S[(size_t)q * n + c] = sig[q] + C.hot[(size_t)q * n + c];
   for (int q = 0; q < 3; ++q) {
     C.S[(size_t)(6 + q) * n + c] = qt[q] + C.hot[(size_t)(6 + q) * n + c];
-    C.S[(size_t)(9 + q) * n + c] = qr[q] + C.hot[(size_t)(9 + q) * n + c];
+    if (DI) C.S[(size_t)(9 + q) * n + c] = qr[q] + C.hot[(size_t)(9 + q) * n + c];
   }
 }
 
@@ -474,15 +480,33 @@ constexpr int CPT = 128;
 // Interior face flux (Rusanov inviscid flux plus the face-averaged stress and
 // heat flux) seen from cell c with outward unit normal N, and the largest
 // wave speed; from the other cell (normal -N) the flux is exactly -F.
+template <bool DI>
 __device__ __forceinline__ void interior_flux(const CoupleParams& C, const double* Pc, const double* Uc,
                                               const double* Pn, const double* Un, const double* Sc,
                                               const double* Sn, const double* N, double cl, double cr, double ml,
                                               double mr, double* F, double* lmo) {
-  double FL[6], FR[6];
-  inv_flux(Pc, Uc, N, FL);
-  inv_flux(Pn, Un, N, FR);
+  constexpr int NV = DI ? 6 : 5;  // conserved variables carried (rho e_r only for a diatomic gas)
   const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
   const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
+  double FL[6], FR[6];
+  {
+    const double p = Pc[0] * Pc[4];
+    FL[0] = Uc[0] * unl;
+    FL[1] = Uc[1] * unl + p * N[0];
+    FL[2] = Uc[2] * unl + p * N[1];
+    FL[3] = Uc[3] * unl + p * N[2];
+    FL[4] = (Uc[4] + p) * unl;
+    FL[5] = DI ? Uc[5] * unl : 0.0;
+  }
+  {
+    const double p = Pn[0] * Pn[4];
+    FR[0] = Un[0] * unr;
+    FR[1] = Un[1] * unr + p * N[0];
+    FR[2] = Un[2] * unr + p * N[1];
+    FR[3] = Un[3] * unr + p * N[2];
+    FR[4] = (Un[4] + p) * unr;
+    FR[5] = DI ? Un[5] * unr : 0.0;
+  }
   const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
   // low-Mach correction (Thornber et al. 2008): the dissipation acts on states
   // whose velocity jump is scaled by z = min(1, max(M_L, M_R)), so that at low
@@ -508,17 +532,18 @@ __device__ __forceinline__ void interior_flux(const CoupleParams& C, const doubl
     ul2 += a * a;
     ur2 += b * b;
   }
-  const double erl = C.dr > 0 ? 0.5 * C.dr * Pc[5] : 0.0, err = C.dr > 0 ? 0.5 * C.dr * Pn[5] : 0.0;
+  const double erl = DI ? 0.5 * C.dr * Pc[5] : 0.0, err = DI ? 0.5 * C.dr * Pn[5] : 0.0;
   UL[4] = 1.5 * pl + rl * (0.5 * ul2 + erl);
   UR[4] = 1.5 * pr + rr * (0.5 * ur2 + err);
   UL[5] = rl * erl;
   UR[5] = rr * err;
-  for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);
-  double sf[6], qtf[3], qrf[3], uf[3];
+  for (int q = 0; q < NV; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);
+  if (!DI) F[5] = 0.0;
+  double sf[6], qtf[3], qrf[3] = {0.0, 0.0, 0.0}, uf[3];
   for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (Sc[q] + Sn[q]);
   for (int q = 0; q < 3; ++q) {
     qtf[q] = 0.5 * (Sc[6 + q] + Sn[6 + q]);
-    qrf[q] = 0.5 * (Sc[9 + q] + Sn[9 + q]);
+    if (DI) qrf[q] = 0.5 * (Sc[9 + q] + Sn[9 + q]);
     uf[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
   }
   const double sn0 = sf[0] * N[0] + sf[3] * N[1] + sf[4] * N[2];
@@ -527,13 +552,18 @@ __device__ __forceinline__ void interior_flux(const CoupleParams& C, const doubl
   F[1] += sn0;
   F[2] += sn1;
   F[3] += sn2;
-  F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + (qtf[0] + qrf[0]) * N[0] + (qtf[1] + qrf[1]) * N[1] +
-          (qtf[2] + qrf[2]) * N[2];
-  F[5] += qrf[0] * N[0] + qrf[1] * N[1] + qrf[2] * N[2];
+  if (DI) {
+    F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + (qtf[0] + qrf[0]) * N[0] + (qtf[1] + qrf[1]) * N[1] +
+            (qtf[2] + qrf[2]) * N[2];
+    F[5] += qrf[0] * N[0] + qrf[1] * N[1] + qrf[2] * N[2];
+  } else {
+    F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + qtf[0] * N[0] + qtf[1] * N[1] + qtf[2] * N[2];
+  }
   *lmo = lm;
 }
 
 // flux of every interior face once, seen from its lower-index cell
+template <bool DI>
 __global__ void k_cp_face(Params P, CoupleParams C) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C.n_ifaces || C.scal->done) return;
@@ -542,27 +572,29 @@ __global__ void k_cp_face(Params P, CoupleParams C) {
   const int nb = P.nbr[4 * (size_t)c + f];
   const Plane64 pl = P.plane[4 * (size_t)c + f];
   const double N[3] = {pl.nx, pl.ny, pl.nz};
-  double Pc[6], Uc[6], Pn[6], Un[6], Sc[12], Sn[12];
-  for (int q = 0; q < 6; ++q) {
+  constexpr int NV = DI ? 6 : 5, NS = DI ? 12 : 9;
+  double Pc[6] = {}, Uc[6] = {}, Pn[6] = {}, Un[6] = {}, Sc[12] = {}, Sn[12] = {};
+  for (int q = 0; q < NV; ++q) {
     Pc[q] = C.prim[(size_t)q * n + c];
     Uc[q] = C.U[(size_t)q * n + c];
     Pn[q] = C.prim[(size_t)q * n + nb];
     Un[q] = C.U[(size_t)q * n + nb];
   }
-  for (int q = 0; q < 12; ++q) {
+  for (int q = 0; q < NS; ++q) {
     Sc[q] = C.S[(size_t)q * n + c];
     Sn[q] = C.S[(size_t)q * n + nb];
   }
   const double cr = Pn[4] > 0 ? C.snd[nb] : sqrt(C.gam * 1e-12);
   double F[6], lm;
-  interior_flux(C, Pc, Uc, Pn, Un, Sc, Sn, N, C.snd[c], cr, C.mach[c], C.mach[nb], F, &lm);
-  for (int q = 0; q < 6; ++q) C.Ff[(size_t)q * C.n_ifaces + i] = F[q];
+  interior_flux<DI>(C, Pc, Uc, Pn, Un, Sc, Sn, N, C.snd[c], cr, C.mach[c], C.mach[nb], F, &lm);
+  for (int q = 0; q < NV; ++q) C.Ff[(size_t)q * C.n_ifaces + i] = F[q];
   C.lmf[i] = lm;
 }
 
 // residual and local stable step of every cell from its face fluxes (the
 // interior ones from k_cp_face, the boundary ones here); per-block partial
 // (min step, sum of squared residuals)
+template <bool DI>
 __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
@@ -574,8 +606,8 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
       Pc[q] = C.prim[(size_t)q * n + c];
       Uc[q] = C.U[(size_t)q * n + c];
     }
-    const double L2 = C.L0 * C.L0, L3 = L2 * C.L0, iL2 = 1.0 / L2;
-    const double V = P.vol[c] / L3, iV = L3 / P.vol[c];
+    const double iL2 = C.iL2;
+    const double V = C.vnd[c], iV = C.ivnd[c];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     double lam_sum = 0.0;
     const double cc = C.snd[c];
@@ -591,7 +623,8 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
       if (nb >= 0) {
         const int fi = C.cfid[4 * (size_t)c + f];
         const double sg = C.fcell[fi] == c ? 1.0 : -1.0;
-        for (int q = 0; q < 6; ++q) F[q] = sg * C.Ff[(size_t)q * C.n_ifaces + fi];
+        for (int q = 0; q < (DI ? 6 : 5); ++q) F[q] = sg * C.Ff[(size_t)q * C.n_ifaces + fi];
+        if (!DI) F[5] = 0.0;
         lam_sum += A * (C.lmf[fi] + 2.0 * nu * A * iV);
       } else {
         const int kind = P.bc[P.bf[-1 - nb].bc].kind;
@@ -631,8 +664,8 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
           const double p = Pc[0] * Pc[4];
           F[0] = 0.0;
           if (kind == 0) {
-            double Sc[12];
-            for (int q = 0; q < 12; ++q) Sc[q] = C.S[(size_t)q * n + c];
+            double Sc[12] = {};
+            for (int q = 0; q < (DI ? 12 : 9); ++q) Sc[q] = C.S[(size_t)q * n + c];
             const double Uw[3] = {C.bcU[3 * b + 0] / C.c0, C.bcU[3 * b + 1] / C.c0, C.bcU[3 * b + 2] / C.c0};
             const double sn0 = Sc[0] * N[0] + Sc[3] * N[1] + Sc[4] * N[2];
             const double sn1 = Sc[3] * N[0] + Sc[1] * N[1] + Sc[5] * N[2];
@@ -1005,9 +1038,15 @@ void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double e
   k_cp_init_cons<<<nb, CPT, 0, s>>>(P, C);
   for (int it = 0; it < N_m; ++it) {
     k_cp_prim<<<nb, CPT, 0, s>>>(P, C, it > 0);
-    k_cp_grad_stress<<<nb, CPT, 0, s>>>(P, C);
-    if (C.n_ifaces > 0) k_cp_face<<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
-    k_cp_flux<<<nb, CPT, 0, s>>>(P, C);
+    if (C.dr > 0) {
+      k_cp_grad_stress<true><<<nb, CPT, 0, s>>>(P, C);
+      if (C.n_ifaces > 0) k_cp_face<true><<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
+      k_cp_flux<true><<<nb, CPT, 0, s>>>(P, C);
+    } else {
+      k_cp_grad_stress<false><<<nb, CPT, 0, s>>>(P, C);
+      if (C.n_ifaces > 0) k_cp_face<false><<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
+      k_cp_flux<false><<<nb, CPT, 0, s>>>(P, C);
+    }
     k_cp_reduce<<<1, 1024, 0, s>>>(C, nb, it, eps);
   }
   if (N_m > 0) k_cp_update<<<nb, CPT, 0, s>>>(P, C);

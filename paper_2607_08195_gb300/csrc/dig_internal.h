@@ -126,6 +126,9 @@ constexpr int DIG_FILL_LAYERS = 64;
 
 struct CoupleParams {
   double L0, T0, rho0, c0, Kn, omega, gam, dr, Zr, mass, FN, kB, KnD_max, wall_t;
+  double iL2;          // 1 / L0^2
+  const double* vnd;   // [n] cell volumes / L0^3
+  const double* ivnd;  // [n] L0^3 / cell volumes
   const double* area;  // [4n] face areas
   const double* lsqw;  // [12][n] least-squares gradient weights (M^-1 d_f)_i at row 3f + i, nondimensional
   const double* bcU;   // [3 n_bcs]

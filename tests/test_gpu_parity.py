@@ -305,12 +305,14 @@ def seeded_dig_state(scen, steps=60, **over):
     return o, o.read(), o.moments(orc.PHI_EWMA), o.wall_flux()
 
 
-@pytest.mark.parametrize("nh,kn,passes,kmax", [(4, 0.1, 3, 0.6), (5, 0.05, 2, 0.4)])
-def test_couple_parity_from_written_state(nh, kn, passes, kmax):
+@pytest.mark.parametrize("nh,kn,passes,kmax,gas", [(4, 0.1, 3, 0.6, W.ARGON), (5, 0.05, 2, 0.4, W.ARGON),
+                                                   (4, 0.1, 3, 0.6, W.NITROGEN)])
+def test_couple_parity_from_written_state(nh, kn, passes, kmax, gas):
     """S9-S11 from an identical written state (particles, moving-average sums,
     wall fluxes): identical filter flags, rejection/reconstruction counts,
-    clone/delete decisions and particle cells; FP64 fields within 1e-9."""
-    s = W.cavity_scenario(nh, 30 * 6 * nh ** 3, kn, seed=17)
+    clone/delete decisions and particle cells; FP64 fields within 1e-9.
+    Nitrogen carries the rotational energy equation and heat flux."""
+    s = W.cavity_scenario(nh, 30 * 6 * nh ** 3, kn, seed=17, gas=gas)
     over = dict(N_m=60, passes=passes, KnD_max=kmax)
     o, (x, v, Ir, cell), phi, wf = seeded_dig_state(s, **over)
     g = dig.Solver(s, "cuda:0", **over)
