@@ -223,7 +223,8 @@ int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches);
  * DIG coupling -- one outer step of the paper's Alg. 1 after N_s DSMC steps:
  * from the moving-average sums, M^{k+1/2} and HoT = sampled stress / heat
  * flux minus their NSF values (Sec. 3.1, Eq. hot_extraction), the cell
- * Knudsen criterion Kn_Delta <= KnD_max (Sec. 3.2) with `passes` layers of
+ * Knudsen criterion Kn_Delta <= KnD_max (Sec. 3.2; a cell whose moving
+ * average holds fewer than two particles on average is rejected too) with `passes` layers of
  * equal-weight neighbour reconstruction (rejected cells beyond them are
  * filled the same way, layer by layer, up to 64 more layers, and are not
  * recalibrated), the steady synthetic equations
