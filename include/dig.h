@@ -271,6 +271,24 @@ int dig_write_moments(dig_ctx* ctx, int32_t which, const double* host_in);
 int dig_write_wall_flux(dig_ctx* ctx, const double* host_in, int64_t steps);
 
 /*
+ * Checkpoint / resume.  A checkpoint is the context's whole device state (the
+ * bound arena: particles, cell tables, summation variables, remainders, the
+ * collision maxima, coupling fields, closure parameters and Adam moments) and
+ * its host counters (step, sample counts, coupling count, particle count), so
+ * that a run resumed from it continues bit for bit: every random number is
+ * keyed by counters the checkpoint holds.
+ * dig_checkpoint_bytes: the size in bytes.  dig_save: write it to host memory
+ * host_out (cap >= that size; DIG_ERR_CAPACITY otherwise).  dig_load: restore
+ * it into a context created with the same configuration and mesh and bound to
+ * an arena of the same size (DIG_ERR_STATE otherwise; DIG_ERR_ARG for a buffer
+ * that is not a checkpoint or is truncated).  Both wait for the stream and
+ * need a bound arena (DIG_ERR_STATE).  The caller owns host_out / host_in.
+ */
+int dig_checkpoint_bytes(dig_ctx* ctx, int64_t* bytes);
+int dig_save(dig_ctx* ctx, void* host_out, int64_t cap);
+int dig_load(dig_ctx* ctx, const void* host_in, int64_t size);
+
+/*
  * Learned closure (not in the paper; the DIG HoT from a per-cell network):
  * an MLP 13 -> 64 -> 64 -> 64 -> 8 with GELU (z/2 (1 + erf(z / sqrt 2))) on
  * the hidden layers, BF16 weights and activations, FP32 accumulation on the

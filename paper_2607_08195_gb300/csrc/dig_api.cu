@@ -126,6 +126,9 @@ struct dig_ctx {
   int* cl_status = nullptr;
   bool cl_set = false;
   int64_t adam_t = 0;
+  // the bound arena (checkpoints copy it whole)
+  char* arena = nullptr;
+  int64_t arena_bytes = 0;
 };
 
 static int fail(dig_ctx* c, int code, const char* msg) {
@@ -594,6 +597,8 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   if (rc) return rc;
   if (bytes < need) return fail(ctx, DIG_ERR_CAPACITY, "arena smaller than dig_arena_bytes()");
   layout(ctx, (char*)dptr);
+  ctx->arena = (char*)dptr;
+  ctx->arena_bytes = need;
   Params& P = ctx->P;
   const dig_config& c = ctx->cfg;
   const size_t n = (size_t)ctx->n_tets;
@@ -1044,6 +1049,99 @@ int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches) {
   *total_ms = tot;
   *launches = (int64_t)(ctx->tev_used / 2);
   ctx->tev_used = 0;
+  return DIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint / resume: the host counters and the whole arena
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int64_t version, n_tets, capacity, arena_bytes, rot_dof;
+  double mass, dt, F_N;
+  uint64_t seed;
+  // host state
+  int64_t cur, N, have_particles, step, n_ewma, n_win, n_cum, host_steps, flux_steps, n_couple, cl_set, adam_t,
+      tile_cells;
+};
+const char kMagic[8] = {'D', 'I', 'G', 'C', 'K', 'P', 'T', '1'};
+}  // namespace
+
+int dig_checkpoint_bytes(dig_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "dig_checkpoint_bytes: no arena bound");
+  *bytes = (int64_t)sizeof(CkptHeader) + ctx->arena_bytes;
+  return DIG_OK;
+}
+
+int dig_save(dig_ctx* ctx, void* host_out, int64_t cap) {
+  if (!ctx || !host_out) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "dig_save: no arena bound");
+  if (cap < (int64_t)sizeof(CkptHeader) + ctx->arena_bytes) return fail(ctx, DIG_ERR_CAPACITY, "dig_save: buffer too small");
+  CkptHeader h{};
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.n_tets = ctx->n_tets;
+  h.capacity = ctx->cfg.capacity;
+  h.arena_bytes = ctx->arena_bytes;
+  h.rot_dof = ctx->cfg.rot_dof;
+  h.mass = ctx->cfg.mass;
+  h.dt = ctx->cfg.dt;
+  h.F_N = ctx->cfg.F_N;
+  h.seed = ctx->cfg.seed;
+  h.cur = ctx->cur;
+  h.N = ctx->N;
+  h.have_particles = ctx->have_particles;
+  h.step = ctx->step;
+  h.n_ewma = ctx->n_ewma;
+  h.n_win = ctx->n_win;
+  h.n_cum = ctx->n_cum;
+  h.host_steps = ctx->host_steps;
+  h.flux_steps = ctx->flux_steps;
+  h.n_couple = ctx->n_couple;
+  h.cl_set = ctx->cl_set;
+  h.adam_t = ctx->adam_t;
+  h.tile_cells = ctx->tile_cells;
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  std::memcpy(host_out, &h, sizeof h);
+  CK(cudaMemcpyAsync((char*)host_out + sizeof h, ctx->arena, (size_t)ctx->arena_bytes, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  return wait_stream(ctx);
+}
+
+int dig_load(dig_ctx* ctx, const void* host_in, int64_t size) {
+  if (!ctx || !host_in) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "dig_load: no arena bound");
+  if (size < (int64_t)sizeof(CkptHeader)) return fail(ctx, DIG_ERR_ARG, "dig_load: not a checkpoint");
+  CkptHeader h;
+  std::memcpy(&h, host_in, sizeof h);
+  if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(ctx, DIG_ERR_ARG, "dig_load: not a checkpoint");
+  if (h.n_tets != ctx->n_tets || h.capacity != ctx->cfg.capacity || h.arena_bytes != ctx->arena_bytes ||
+      h.rot_dof != ctx->cfg.rot_dof || h.mass != ctx->cfg.mass || h.dt != ctx->cfg.dt || h.F_N != ctx->cfg.F_N ||
+      h.seed != ctx->cfg.seed)
+    return fail(ctx, DIG_ERR_STATE, "dig_load: checkpoint of a different configuration or mesh");
+  if (size < (int64_t)sizeof h + h.arena_bytes) return fail(ctx, DIG_ERR_ARG, "dig_load: truncated checkpoint");
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(ctx->arena, (const char*)host_in + sizeof h, (size_t)h.arena_bytes, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  rc = wait_stream(ctx);
+  if (rc) return rc;
+  ctx->cur = (int)h.cur;
+  ctx->N = h.N;
+  ctx->have_particles = h.have_particles != 0;
+  ctx->step = h.step;
+  ctx->n_ewma = h.n_ewma;
+  ctx->n_win = h.n_win;
+  ctx->n_cum = h.n_cum;
+  ctx->host_steps = h.host_steps;
+  ctx->flux_steps = h.flux_steps;
+  ctx->n_couple = h.n_couple;
+  ctx->cl_set = h.cl_set != 0;
+  ctx->adam_t = h.adam_t;
+  ctx->tile_cells = (int)h.tile_cells;
   return DIG_OK;
 }
 

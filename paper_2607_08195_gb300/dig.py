@@ -73,7 +73,7 @@ EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mes
            "dig_sort_scratch_bytes", "dig_sort_by_cell", "dig_sort_by_cell_noalloc", "dig_couple",
            "dig_read_couple", "dig_write_moments", "dig_write_wall_flux", "closure_init", "closure_set",
            "closure_get", "closure_features", "closure_targets", "closure_forward", "closure_loss", "closure_grad",
-           "closure_train"]
+           "closure_train", "dig_checkpoint_bytes", "dig_save", "dig_load"]
 
 _lib = None
 
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "closure_features": [P, I32, P], "closure_targets": [P, I32, P, I64, P], "closure_forward": [P, P, I64, P],
         "closure_loss": [P, P, P, I64, I32, P], "closure_grad": [P, P, P, I64, P, P],
         "closure_train": [P, P, P, P, I64, P],
+        "dig_checkpoint_bytes": [P, P], "dig_save": [P, P, I64], "dig_load": [P, P, I64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -281,6 +282,19 @@ class Solver:
         out = np.zeros((self.n_tets, k), np.float64)
         self._check(self.L.dig_read_couple(self.h, which, _p(out), out.size))
         return out
+
+    def save(self):
+        """The context's checkpoint (numpy uint8 array): see dig_save."""
+        nb = C.c_int64(0)
+        self._check(self.L.dig_checkpoint_bytes(self.h, C.byref(nb)))
+        buf = np.empty(nb.value, np.uint8)
+        self._check(self.L.dig_save(self.h, _p(buf), buf.size))
+        return buf
+
+    def load(self, buf):
+        """Resume from a checkpoint made by save() on the same configuration and mesh."""
+        buf = np.ascontiguousarray(buf, np.uint8)
+        self._check(self.L.dig_load(self.h, _p(buf), buf.size))
 
     def write_moments(self, which, phi):
         phi = np.ascontiguousarray(phi, np.float64)
