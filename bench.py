@@ -429,9 +429,10 @@ def main():
     ap.add_argument("--conv-noise", type=int, default=20)
     ap.add_argument("--conv-threshold", type=float, default=0.02)
     ap.add_argument("--conv-threshold-factor", type=float, default=1.5)
-    ap.add_argument("--workload", default="cavity30", choices=["cavity30", "cavity20", "sphere"],
+    ap.add_argument("--workload", default="cavity30", choices=["cavity30", "cavity20", "sphere", "capsule"],
                     help="cavity30: 30^3 hexes, Kn 0.01, 8M particles (the benchmark); sphere: Mach 10 argon over a "
-                         "sphere, ~2M graded Delaunay tets, 100M particles; cavity20: 20^3 hexes, "
+                         "sphere, ~2M graded Delaunay tets, 100M particles; capsule: Mach 25 nitrogen over a capsule, "
+                         "~8M tets, 1e9 particles; cavity20: 20^3 hexes, "
                          "Kn 0.001, 3M particles (smaller case for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -454,7 +455,8 @@ def main():
     device = torch.device("cuda", local)
     scen = {"cavity30": lambda: W.config_c2(seed=replica_seed(2, rank)),
             "cavity20": lambda: W.config_c3(seed=replica_seed(3, rank)),
-            "sphere": lambda: W.config_c4(seed=replica_seed(4, rank))}[args.workload]()
+            "sphere": lambda: W.config_c4(seed=replica_seed(4, rank)),
+            "capsule": lambda: W.config_c5(seed=replica_seed(5, rank))}[args.workload]()
     g = dig.Solver(scen, str(device))
     g.init()
     g.synchronize()
@@ -513,7 +515,7 @@ def main():
     # on the library's stream); algorithmic bytes = read + write of the
     # particle state once per particle-step (x,y,z f64 + vx,vy,vz f32 = 36 B,
     # plus the 4-byte cell id) = 80 B
-    alg_bytes_per_pstep = 80.0
+    alg_bytes_per_pstep = 88.0 if scen.gas.rot_dof > 0 else 80.0  # + I_r (f32) for a diatomic gas
     peak, peak_kind = read_peaks()
     cp_launch_ms = k_ms / max(k_n, 1)
     # passes: n_steps + 1 per dsmc_step call; particle-steps per pass

@@ -215,6 +215,119 @@ def sphere_mesh(h_w: float, R: float = 0.1, R_far: float = 1.0, grading: float =
     return Mesh(nodes, tets, face_tag, bcs)
 
 
+# capsule body (the paper's Apollo case, Sec. 5.3, procedural): spherical cap
+# of radius 2 m meeting a 33-degree conical frustum at the base radius 1.95 m;
+# the frustum narrows to a flat top of radius 0.5 m.  Axis x, cap toward -x.
+CAPSULE_RC, CAPSULE_RB, CAPSULE_CONE_DEG, CAPSULE_RTOP = 2.0, 1.95, 33.0, 0.5
+
+
+def _capsule_geometry():
+    a_c = math.sqrt(CAPSULE_RC ** 2 - CAPSULE_RB ** 2)  # cap centre on the axis
+    tc = math.tan(math.radians(CAPSULE_CONE_DEG))
+    a_top = (CAPSULE_RB - CAPSULE_RTOP) / tc
+    a_min = a_c - CAPSULE_RC
+    return a_c, tc, a_top, a_min, 0.5 * (a_min + a_top)
+
+
+def capsule_inside(p: np.ndarray) -> np.ndarray:
+    """True for points inside the capsule body."""
+    a_c, tc, a_top, a_min, _ = _capsule_geometry()
+    a = p[:, 0]
+    r = np.hypot(p[:, 1], p[:, 2])
+    cap = (a <= 0.0) & (a >= a_min) & ((a - a_c) ** 2 + r ** 2 <= CAPSULE_RC ** 2)
+    cone = (a > 0.0) & (a <= a_top) & (r <= CAPSULE_RB - a * tc)
+    return cap | cone
+
+
+def _capsule_meridian(h: float, s: float) -> np.ndarray:
+    """(a, r) points along the body's meridian scaled by s about the body's
+    mid-axis point, spacing about h: cap arc, frustum line, top radius."""
+    a_c, tc, a_top, a_min, c0 = _capsule_geometry()
+    th_max = math.asin(CAPSULE_RB / CAPSULE_RC)
+    pts = []
+    n = max(2, int(math.ceil(s * CAPSULE_RC * th_max / h)))
+    pts += [(a_c - CAPSULE_RC * math.cos(th_max * i / n), CAPSULE_RC * math.sin(th_max * i / n)) for i in range(n)]
+    n = max(2, int(math.ceil(s * math.hypot(a_top, CAPSULE_RB - CAPSULE_RTOP) / h)))
+    pts += [(a_top * i / n, CAPSULE_RB - (CAPSULE_RB - CAPSULE_RTOP) * i / n) for i in range(n)]
+    n = max(2, int(math.ceil(s * CAPSULE_RTOP / h)))
+    pts += [(a_top, CAPSULE_RTOP * (1.0 - i / n)) for i in range(n + 1)]
+    m = np.array(pts)
+    m[:, 0] = c0 + s * (m[:, 0] - c0)
+    m[:, 1] *= s
+    return m
+
+
+def capsule_mesh(h_w: float, R_far: float = 15.6, grading: float = 20.0, seed: int = 5, T_w: float = 500.0,
+                 n_inf: float = 1e20, T_inf: float = 142.2, U_inf=(6000.0, 0.0, 0.0)) -> Mesh:
+    """Capsule in a spherical far field of radius R_far about the body's
+    mid-axis point: Delaunay tetrahedra of seeded points on copies of the body
+    surface scaled about that point (spacing growing from h_w at the body
+    toward grading * h_w at the far field; each surface of revolution sampled
+    along its meridian and around the axis with a random phase) and on the far
+    sphere; tetrahedra inside the body removed.  Boundary faces nearer the
+    body than half the far-field radius are the body wall (diffuse at T_w,
+    bcs[0]); the others are free-stream faces (bcs[1])."""
+    import os
+    import tempfile
+
+    from scipy.spatial import Delaunay
+
+    bcs = [dict(kind=BC_DIFFUSE, T=T_w, U=(0.0, 0.0, 0.0), n=0.0),
+           dict(kind=BC_INFLOW, T=T_inf, U=tuple(U_inf), n=n_inf)]
+    cache = os.path.join(os.environ.get("DIG_MESH_CACHE", tempfile.gettempdir()),
+                         f"dig_capsule_{h_w:.6g}_{R_far:.6g}_{grading:.6g}_{seed}.npz")
+    if os.path.exists(cache):
+        z = np.load(cache)
+        return Mesh(z["nodes"], z["tets"], z["face_tag"], bcs)
+    rng = np.random.default_rng(seed)
+    _, _, _, _, c0 = _capsule_geometry()
+    R_eq = 2.0
+    a = math.log(grading) / math.log(R_far / R_eq)
+    h_far = h_w * (R_far / R_eq) ** a
+    pts = []
+    s = 1.0
+    while True:
+        h = h_w * s ** a
+        for am, rm in _capsule_meridian(h, s):
+            n = max(1, int(round(2.0 * math.pi * rm / h))) if rm > 1e-12 else 1
+            t = rng.uniform(0.0, 2.0 * math.pi) + 2.0 * math.pi * np.arange(n) / n
+            pts.append(np.stack([np.full(n, am), rm * np.cos(t), rm * np.sin(t)], axis=1))
+        s_next = s + h / R_eq
+        if s_next * 2.4 > R_far - h_far:
+            break
+        s = s_next
+    far = _shell_points(max(12, int(round(4.0 * math.pi * R_far ** 2 / (0.866 * h_far * h_far)))), R_far, rng)
+    far[:, 0] += c0
+    pts.append(far)
+    nodes = np.concatenate(pts).astype(np.float64)
+    tets = Delaunay(nodes).simplices.astype(np.int64)
+    tets = tets[~capsule_inside(nodes[tets].mean(axis=1))]
+    nt = len(tets)
+    tri = np.stack([np.delete(tets, f, axis=1) for f in range(4)], axis=1).reshape(-1, 3)
+    tri.sort(axis=1)
+    key = (tri[:, 0] * (len(nodes) + 1) + tri[:, 1]) * (len(nodes) + 1) + tri[:, 2]
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    dup = np.zeros(len(ks), bool)
+    dup[1:] |= ks[1:] == ks[:-1]
+    dup[:-1] |= ks[:-1] == ks[1:]
+    boundary = np.empty(len(ks), bool)
+    boundary[order] = ~dup
+    boundary = boundary.reshape(nt, 4)
+    fc = np.stack([nodes[np.delete(tets, f, axis=1)].mean(axis=1) for f in range(4)], axis=1)
+    fc[..., 0] -= c0
+    far_face = np.linalg.norm(fc, axis=2) > 0.5 * R_far
+    face_tag = np.where(boundary, np.where(far_face, 1, 0), -1).astype(np.int32)
+    tets = tets.astype(np.int32)
+    try:
+        tmp = cache + f".{os.getpid()}.npz"
+        np.savez(tmp, nodes=nodes, tets=tets, face_tag=face_tag)
+        os.replace(tmp, cache)
+    except OSError:
+        pass
+    return Mesh(nodes, tets, face_tag, bcs)
+
+
 @dataclasses.dataclass
 class Scenario:
     """Everything a run needs besides the mesh; the same values feed both sides."""
@@ -290,6 +403,38 @@ def sphere_scenario(h_w: float, n_particles: int, seed: int = 4, gas: Gas = ARGO
 def config_c4(seed: int = 4) -> Scenario:
     """Hypersonic argon sphere: R = 0.1 m, far field 1 m, ~2M tets graded 20x toward the wall, 100M particles."""
     return sphere_scenario(0.0036, 100_000_000, seed, name="sphere-R0.1-Ma10-2Mtets-100M")
+
+
+def capsule_scenario(h_w: float, n_particles: int, seed: int = 5, gas: Gas = NITROGEN, Ma: float = 25.0,
+                     T_inf: float = 142.2, Kn: float = 0.01, incidence_deg: float = 20.0, T_w: float = 500.0,
+                     name: str = "") -> Scenario:
+    """Nitrogen (Borgnakke-Larsen, Z_rot = 5) at Mach 25 over the capsule at
+    20 degrees incidence: free stream at 142.2 K with the number density that
+    gives Kn = 0.01 on the diameter L = 3.9 m (the cavity's Kn definition),
+    diffuse wall at 500 K, initial state the free stream.
+    dt = min(0.2 tau, 0.2 h_w / (U + 3 sqrt(2 k T / m)))."""
+    R = K_B / gas.mass
+    gam = (5.0 + gas.rot_dof) / (3.0 + gas.rot_dof)
+    U = Ma * math.sqrt(gam * R * T_inf)
+    inc = math.radians(incidence_deg)
+    Uv = (U * math.cos(inc), U * math.sin(inc), 0.0)
+    L = 2.0 * CAPSULE_RB
+    mu = gas.mu_ref() * (T_inf / gas.T_ref) ** gas.omega
+    p = mu / (Kn * L) * math.sqrt(math.pi * R * T_inf / 2.0)
+    n_inf = p / (K_B * T_inf)
+    mesh = capsule_mesh(h_w, seed=seed, T_w=T_w, n_inf=n_inf, T_inf=T_inf, U_inf=Uv)
+    dt = min(0.2 * mu / p, 0.2 * h_w / (U + 3.0 * math.sqrt(2.0 * K_B * T_inf / gas.mass)))
+    P = mesh.nodes[mesh.tets]
+    V = float(np.abs(np.einsum("ni,ni->n", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))).sum()) / 6.0
+    return Scenario(gas=gas, mesh=mesh, n_particles=n_particles, n_init=n_inf, T_init=T_inf, u_init=Uv,
+                    F_N=n_inf * V / n_particles, dt=dt, seed=seed, L=L, Kn=Kn,
+                    capacity=int(1.25 * n_particles), name=name or f"capsule-{len(mesh.tets)}tets")
+
+
+def config_c5(seed: int = 5) -> Scenario:
+    """Nitrogen capsule at Mach 25, 20 degrees incidence: ~8M tets graded 20x
+    toward the body, 1e9 particles (44 GB of particle state per buffer set)."""
+    return capsule_scenario(0.0365, 1_000_000_000, seed, name="capsule-Ma25-8Mtets-1G")
 
 
 def random_particles(rng: np.random.Generator, scen: Scenario, n: int):

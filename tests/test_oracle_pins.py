@@ -489,6 +489,40 @@ def test_sphere_mesh_and_tracking():
     assert lam.min() >= -1e-9, lam.min()
 
 
+def test_capsule_mesh_and_tracking():
+    """Procedural capsule (nitrogen at Mach 25, 20 degrees incidence): no tet
+    lies inside the body, every body-wall face lies on the body's surface
+    (within the polyhedral approximation: its centroid is at most one wall
+    spacing inside or outside), the far-field faces on the far sphere; after 8
+    oracle steps with Borgnakke-Larsen exchange, injection, wall reflections
+    and outflow every particle lies inside the tet it was tracked to."""
+    s = W.capsule_scenario(0.3, 50_000, seed=5)
+    m = s.mesh
+    P = m.nodes[m.tets]
+    assert not W.capsule_inside(P.mean(axis=1)).any()
+    fc = np.stack([np.delete(P, f, axis=1).mean(axis=1) for f in range(4)], axis=1)
+    wall, far = fc[m.face_tag == 0], fc[m.face_tag == 1]
+    assert len(wall) > 200 and len(far) > 50
+    # a body-wall face centroid lies between the body shrunk and grown by 0.3 m
+    # about its mid-axis point (spacing at the body), the far faces near 15.6 m
+    a_c, tc, a_top, a_min, c0 = W._capsule_geometry()
+    for sc, inside in ((1.0 - 0.3 / 2.0, False), (1.0 + 0.3 / 2.0, True)):
+        q = wall.copy()
+        q[:, 0] = c0 + (q[:, 0] - c0) / sc
+        q[:, 1:] /= sc
+        assert np.all(W.capsule_inside(q) == inside)
+    rf = np.linalg.norm(far - np.array([c0, 0.0, 0.0]), axis=1)
+    assert np.all((rf > 0.9 * 15.6) & (rf <= 15.6 * (1 + 1e-12)))
+    o = orc.Oracle(s)
+    o.init()
+    o.step(8, orc.EWMA)
+    x, v, I, cell = o.read()
+    c = o.counters()
+    assert c["stuck"] == 0 and c["injected"] > 0 and c["removed"] > 0 and c["wall"] > 0 and c["lb"] > 0
+    assert len(cell) == s.n_particles + c["injected"] - c["removed"]
+    assert barycentric(m.nodes, m.tets, cell, x).min() >= -1e-9
+
+
 def inflow_scenario(U, T=273.0, n=1e20, sides_inflow=(0,), dt=1e-9, F_N=None, n_particles=0, L=1e-3, seed=31):
     """One-hex box: the listed sides are free-stream inflow, the others outflow;
     collisions switched off (tiny molecular diameter)."""
