@@ -698,17 +698,31 @@ __global__ void __launch_bounds__(256) k_order(Params P, Buf IN, Buf OUT) {
     const int key = gl < na ? P.aq[a0 + gl] : 0x7fffffff;
     // stayers: 16 old slots per round and cell; the bounds are warp-uniform
     const int no_max = max(no, __shfl_xor_sync(0xffffffffu, no, 16));
+    // the old slots' cells are loaded four rounds ahead of their ballots, and
+    // the gathered velocities four rounds ahead of their stores, so that the
+    // loads of a cell overlap
     int ns = 0;
-    for (int k0 = 0; k0 < no_max; k0 += 16) {
-      const int k = k0 + gl;
-      const bool st = k < no && IN.mc[sb + k] == c;
-      const unsigned bs = (__ballot_sync(0xffffffffu, st) >> (16 * g)) & 0xffffu;
-      const int pos = ns + __popc(bs & glt);
-      if (st && pos < Nc) {
-        P.src[base + pos] = sb + k;
-        if (pos < OQ) my[pos] = sb + k;
+    for (int k1 = 0; k1 < no_max; k1 += 64) {
+      int mv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k = k1 + 16 * r + gl;
+        mv[r] = k < no ? IN.mc[sb + k] : -2;
       }
-      ns += __popc(bs);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k0 = k1 + 16 * r;
+        if (k0 >= no_max) break;
+        const int k = k0 + gl;
+        const bool st = k < no && mv[r] == c;
+        const unsigned bs = (__ballot_sync(0xffffffffu, st) >> (16 * g)) & 0xffffu;
+        const int pos = ns + __popc(bs & glt);
+        if (st && pos < Nc) {
+          P.src[base + pos] = sb + k;
+          if (pos < OQ) my[pos] = sb + k;
+        }
+        ns += __popc(bs);
+      }
     }
     // arrivals, ranked by slot
     const int na_max = max(na, __shfl_xor_sync(0xffffffffu, na, 16));
@@ -736,13 +750,30 @@ __global__ void __launch_bounds__(256) k_order(Params P, Buf IN, Buf OUT) {
       }
     }
     __syncwarp();
-    for (int k = gl; k < Nc; k += 16) {
-      const int q = k < OQ ? my[k] : P.src[base + k];
-      OUT.vx[base + k] = IN.vx[q];
-      OUT.vy[base + k] = IN.vy[q];
-      OUT.vz[base + k] = IN.vz[q];
-      OUT.mc[base + k] = c;  // the slot's cell until k_move writes the destination
-      if (DIAT) OUT.Ir[base + k] = IN.Ir[q];
+    for (int k1 = gl; k1 < Nc; k1 += 64) {
+      float ax[4], ay[4], az[4], ai[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k = k1 + 16 * r;
+        if (k < Nc) {
+          const int q = k < OQ ? my[k] : P.src[base + k];
+          ax[r] = IN.vx[q];
+          ay[r] = IN.vy[q];
+          az[r] = IN.vz[q];
+          if (DIAT) ai[r] = IN.Ir[q];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k = k1 + 16 * r;
+        if (k < Nc) {
+          OUT.vx[base + k] = ax[r];
+          OUT.vy[base + k] = ay[r];
+          OUT.vz[base + k] = az[r];
+          OUT.mc[base + k] = c;  // the slot's cell until k_move writes the destination
+          if (DIAT) OUT.Ir[base + k] = ai[r];
+        }
+      }
     }
     if (live && gl == 0) {
       P.sbase[c] = base;
