@@ -10,10 +10,14 @@ state (2 x 352 MB) is far larger than L2, so no L2 flush is needed between
 steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload cavity30|cavity20|sphere|capsule] [--no-couple]
+  python bench.py --convergence
 
---impl reference times the CPU oracle (the reference of this build) on a
-bounded sample of the same workload.  Under torchrun every rank runs an
-independent replica (different seed) on its own GPU; value is the sum.
+--impl reference times the CPU oracle on a bounded sample of the same
+workload.  Under torchrun every rank runs an independent replica (its own
+seed) on its own GPU; value is the units of all ranks over the slowest rank's
+time.  --convergence runs the time-to-converged-field experiment (plain DSMC,
+DIG, DIG with the learned closure) on the Kn = 0.001 cavity instead.
 """
 from __future__ import annotations
 
@@ -419,7 +423,6 @@ def main():
     ap.add_argument("--no-couple", action="store_true", help="DSMC steps only (no DIG coupling)")
     ap.add_argument("--convergence", action="store_true",
                     help="only the time-to-converged-field experiment (plain DSMC vs DIG vs DIG + learned closure)")
-    ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-converged-field experiment")
     ap.add_argument("--conv-warm", type=int, default=80)
     ap.add_argument("--conv-windows", type=int, default=44)
     ap.add_argument("--conv-epochs", type=int, default=20)
