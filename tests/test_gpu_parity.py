@@ -479,3 +479,39 @@ def test_capsule_medium_size_properties():
     lam = np.linalg.solve(T, (x[k] - P[:, 0])[..., None])[..., 0]
     assert np.concatenate([1.0 - lam.sum(axis=1, keepdims=True), lam], axis=1).min() >= -1e-9
     assert np.all(np.isfinite(v[k])) and np.all(np.isfinite(I[k])) and I[k].min() >= 0.0
+
+
+def test_couple_open_boundaries_uniform_stream():
+    """A uniform drifting stream between a free-stream inflow side, an outflow
+    side and four specular walls is a fixed point of the GPU's synthetic solve
+    too (both open-boundary kinds), within 1e-12 of the written state and of
+    the oracle's result."""
+    n, T, U = 1.677e22, 273.0, 300.0
+    bcs = [dict(kind=W.BC_INFLOW, T=T, U=(U, 0.0, 0.0), n=n), dict(kind=W.BC_OUTFLOW, T=T, U=(0.0, 0.0, 0.0), n=0.0),
+           dict(kind=W.BC_SPECULAR, T=T, U=(0.0, 0.0, 0.0), n=0.0)]
+    mesh = W.box_sides(3, 1e-3, [0, 1, 2, 2, 2, 2], bcs)
+    gas = W.ARGON
+    mu = gas.mu_ref() * (T / gas.T_ref) ** gas.omega
+    s = W.Scenario(gas=gas, mesh=mesh, n_particles=16200, n_init=n, T_init=T, u_init=(U, 0.0, 0.0),
+                   F_N=n * 1e-9 / 16200, dt=0.2 * mu / (n * W.K_B * T), seed=7, L=1e-3, Kn=0.1, capacity=40000)
+    g, o = pair(s, N_m=50, KnD_max=1e9)
+    o.init()
+    g.write(*o.read())
+    vol = o.mesh_info()["vol"]
+    kT_m = W.K_B * T / gas.mass
+    N = n * vol / s.F_N
+    phi = np.zeros((len(vol), orc.NPHI))
+    phi[:, 0] = N
+    phi[:, 1] = N * U
+    phi[:, 4] = N * (kT_m + U * U)
+    phi[:, 5] = N * kT_m
+    phi[:, 6] = N * kT_m
+    phi[:, 10] = N * U * (U * U + 5.0 * kT_m)
+    g.write_moments(dig.PHI_EWMA, phi)
+    o.write_moments(orc.PHI_EWMA, phi)
+    rg, ro = g.couple(), o.couple()
+    assert rg["iters"] == ro["iters"] == 50
+    half, new = g.read_couple(0), g.read_couple(2)
+    assert np.allclose(new, half, rtol=0, atol=1e-12), np.abs(new - half).max()
+    assert np.allclose(new, o.read_couple(2), rtol=0, atol=1e-12)
+    assert np.array_equal(g.read()[3], o.read()[3])

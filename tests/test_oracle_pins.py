@@ -676,6 +676,42 @@ def test_synthetic_fixed_point_and_identity_recalibration():
     assert np.array_equal(v0, v1) and np.array_equal(x0, x1) and np.array_equal(c0, c1)
 
 
+def test_synthetic_uniform_stream_is_a_fixed_point():
+    """Open boundaries in the synthetic solve: a uniform drifting Maxwellian
+    (u = 300 m/s along x, 273 K) in a box whose x = -L/2 side is the same free
+    stream (inflow), x = +L/2 an outflow and the four other sides specular
+    walls: every flux balances (the slip walls see no normal velocity, the
+    inflow face the stream itself, the outflow face the cell), so the solve
+    leaves the state unchanged to round-off."""
+    n, T, U = 1.677e22, 273.0, 300.0
+    bcs = [dict(kind=W.BC_INFLOW, T=T, U=(U, 0.0, 0.0), n=n), dict(kind=W.BC_OUTFLOW, T=T, U=(0.0, 0.0, 0.0), n=0.0),
+           dict(kind=W.BC_SPECULAR, T=T, U=(0.0, 0.0, 0.0), n=0.0)]
+    mesh = W.box_sides(3, 1e-3, [0, 1, 2, 2, 2, 2], bcs)
+    g = W.ARGON
+    mu = g.mu_ref() * (T / g.T_ref) ** g.omega
+    s = W.Scenario(gas=g, mesh=mesh, n_particles=16200, n_init=n, T_init=T, u_init=(U, 0.0, 0.0),
+                   F_N=n * 1e-9 / 16200, dt=0.2 * mu / (n * KB * T), seed=7, L=1e-3, Kn=0.1, capacity=40000)
+    o = orc.Oracle(s, N_m=50, KnD_max=1e9)
+    o.init()
+    vol = o.mesh_info()["vol"]
+    kT_m = KB * T / g.mass
+    N = n * vol / s.F_N
+    phi = np.zeros((len(vol), orc.NPHI))
+    phi[:, 0] = N
+    phi[:, 1] = N * U
+    phi[:, 4] = N * (kT_m + U * U)
+    phi[:, 5] = N * kT_m
+    phi[:, 6] = N * kT_m
+    phi[:, 10] = N * U * (U * U + 5.0 * kT_m)  # <v_x v^2> of a drifting Maxwellian
+    o.write_moments(orc.PHI_EWMA, phi)
+    r = o.couple()
+    half, new, hot = o.read_couple(0), o.read_couple(2), o.read_couple(1)
+    assert r["iters"] == 50 and np.all(o.read_couple(3) == 1)
+    assert np.abs(hot).max() < 1e-9
+    assert np.allclose(new, half, rtol=0, atol=1e-12), np.abs(new - half).max()
+    assert abs(half[:, 1].mean() * math.sqrt(kT_m) - U) < 1e-9 * U
+
+
 def test_synthetic_solve_conserves_mass():
     """The finite-volume update is conservative: walls carry no mass, so the
     total mass sum(rho V) after the solve equals that of M^{k+1/2}."""
