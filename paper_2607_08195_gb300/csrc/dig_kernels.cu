@@ -1274,12 +1274,25 @@ __global__ void k_scatter(Params P, const int* __restrict__ mc) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int c = gw; c < P.n_cells; c += nw) {
     const int lo = P.sbase[c], hi = lo + P.nold[c];
-    for (int q = lo + lane; q < hi; q += 32) {
-      const int d = mc[q];
-      if (d != c && d >= 0 && d < P.n_cells) {
-        const int pos = P.as[d] + atomicAdd(P.fill + d, 1);
-        P.aq[pos] = q;
+    // two rounds of the range per iteration: both cells loaded, both atomics
+    // in flight, before the arrival-list stores
+    for (int q0 = lo + lane; q0 < hi; q0 += 64) {
+      const int q1 = q0 + 32;
+      const int d0 = mc[q0];
+      const int d1 = q1 < hi ? mc[q1] : c;
+      const bool m0 = d0 != c && d0 >= 0 && d0 < P.n_cells;
+      const bool m1 = d1 != c && d1 >= 0 && d1 < P.n_cells;
+      int a0 = 0, a1 = 0, f0 = 0, f1 = 0;
+      if (m0) {
+        a0 = P.as[d0];
+        f0 = atomicAdd(P.fill + d0, 1);
       }
+      if (m1) {
+        a1 = P.as[d1];
+        f1 = atomicAdd(P.fill + d1, 1);
+      }
+      if (m0) P.aq[a0 + f0] = q0;
+      if (m1) P.aq[a1 + f1] = q1;
     }
   }
   const int lo = P.state[1], hi = P.state[2];
