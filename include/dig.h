@@ -209,6 +209,14 @@ int dig_cell_state(dig_ctx* ctx, float* cmax, double* rem, int32_t write);
 /* per boundary face (in (tet, face) order): hits, momentum (3) and energy given
  * to the wall, out[n_bfaces][5]; with out NULL only *n_bfaces is set. */
 int dig_wall_flux(dig_ctx* ctx, double* out, int64_t cap, int64_t* n_bfaces);
+/* surface quantities of every boundary face (in (tet, face) order) from the
+ * wall-flux sums of the steps run with DIG_WALLFLUX since the last coupling
+ * (or dig_write_wall_flux): out[n_bfaces][6] = number flux of molecules
+ * hitting the face (1/(m^2 s)), pressure (normal momentum flux into the wall,
+ * Pa), shear stress (the tangential momentum flux vector, 3 components, Pa)
+ * and heat flux into the wall (W/m^2), per unit face area and time.  With out
+ * NULL only *n_bfaces is set; DIG_ERR_STATE if no step was sampled. */
+int dig_surface(dig_ctx* ctx, double* out, int64_t cap, int64_t* n_bfaces);
 int dig_particle_count(dig_ctx* ctx, int64_t* n);
 /* wait for all queued work; returns the first device-side error, if any */
 int dig_synchronize(dig_ctx* ctx);

@@ -1023,6 +1023,40 @@ int dig_wall_flux(dig_ctx* ctx, double* out, int64_t cap, int64_t* n_bfaces) {
   return wait_stream(ctx);
 }
 
+int dig_surface(dig_ctx* ctx, double* out, int64_t cap, int64_t* n_bfaces) {
+  if (!ctx || !n_bfaces) return DIG_ERR_ARG;
+  const size_t nb = ctx->bf.size();
+  *n_bfaces = (int64_t)nb;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "no arena");
+  if (!out) return DIG_OK;  // size query
+  if (cap < 6 * (int64_t)nb) return fail(ctx, DIG_ERR_CAPACITY, "dig_surface: buffer too small");
+  if (ctx->flux_steps <= 0) return fail(ctx, DIG_ERR_STATE, "dig_surface: no steps sampled with DIG_WALLFLUX");
+  std::vector<double> F(5 * std::max<size_t>(nb, 1));
+  CK(cudaMemcpyAsync(F.data(), ctx->P.bflux, 5 * nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  const double t = (double)ctx->flux_steps * ctx->cfg.dt;
+  for (int64_t tt = 0; tt < ctx->n_tets; ++tt)
+    for (int f = 0; f < 4; ++f) {
+      const int32_t code = ctx->nbr[4 * tt + f];
+      if (code >= 0) continue;
+      const size_t ib = (size_t)(-1 - code);
+      const Plane64 pl = ctx->plane[4 * tt + f];  // outward normal of the gas cell: into the wall
+      const double At = ctx->area[4 * tt + f] * t;
+      const double* G = F.data() + 5 * ib;
+      const double gx = G[1] / At, gy = G[2] / At, gz = G[3] / At;
+      const double p = gx * pl.nx + gy * pl.ny + gz * pl.nz;
+      double* o = out + 6 * ib;
+      o[0] = G[0] * ctx->cfg.F_N / At;
+      o[1] = p;
+      o[2] = gx - p * pl.nx;
+      o[3] = gy - p * pl.ny;
+      o[4] = gz - p * pl.nz;
+      o[5] = G[4] / At;
+    }
+  return DIG_OK;
+}
+
 int dig_particle_count(dig_ctx* ctx, int64_t* n) {
   if (!ctx || !n) return DIG_ERR_ARG;
   if (!ctx->have_particles) {

@@ -73,7 +73,7 @@ EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mes
            "dig_sort_scratch_bytes", "dig_sort_by_cell", "dig_sort_by_cell_noalloc", "dig_couple",
            "dig_read_couple", "dig_write_moments", "dig_write_wall_flux", "closure_init", "closure_set",
            "closure_get", "closure_features", "closure_targets", "closure_forward", "closure_loss", "closure_grad",
-           "closure_train", "dig_checkpoint_bytes", "dig_save", "dig_load"]
+           "closure_train", "dig_checkpoint_bytes", "dig_save", "dig_load", "dig_surface"]
 
 _lib = None
 
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "closure_loss": [P, P, P, I64, I32, P], "closure_grad": [P, P, P, I64, P, P],
         "closure_train": [P, P, P, P, I64, P],
         "dig_checkpoint_bytes": [P, P], "dig_save": [P, P, I64], "dig_load": [P, P, I64],
+        "dig_surface": [P, P, I64, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -270,6 +271,14 @@ class Solver:
         self.L.dig_wall_flux(self.h, None, 0, C.byref(n))
         out = np.zeros((n.value, 5), np.float64)
         self._check(self.L.dig_wall_flux(self.h, _p(out), out.size, C.byref(n)))
+        return out
+
+    def surface(self):
+        """[n_bfaces][6]: number flux, pressure, shear (3), heat flux per boundary face (dig_surface)."""
+        n = C.c_int64(0)
+        self.L.dig_surface(self.h, None, 0, C.byref(n))
+        out = np.zeros((n.value, 6), np.float64)
+        self._check(self.L.dig_surface(self.h, _p(out), out.size, C.byref(n)))
         return out
 
     def couple(self):

@@ -515,3 +515,46 @@ def test_couple_open_boundaries_uniform_stream():
     assert np.allclose(new, half, rtol=0, atol=1e-12), np.abs(new - half).max()
     assert np.allclose(new, o.read_couple(2), rtol=0, atol=1e-12)
     assert np.array_equal(g.read()[3], o.read()[3])
+
+
+def test_surface_quantities_of_a_gas_at_rest():
+    """dig_surface on a closed box of gas at rest at the wall temperature
+    (diffuse walls): it converts the oracle's and the GPU's (identical)
+    wall-flux sums into the number flux n c_mean / 4, the pressure n k T, zero
+    shear and zero heat flux, box-wide means within 5 % of those values (about
+    460,000 wall hits: the statistical error is near 0.2 %)."""
+    s = W.Scenario(gas=W.ARGON, mesh=W.closed_box(1, 1e-3, W.BC_DIFFUSE), n_particles=60_000, n_init=1.677e22,
+                   T_init=273.0, u_init=(0.0, 0.0, 0.0), F_N=1.677e22 * 1e-9 / 60_000, dt=6.7e-8, seed=21, L=1e-3,
+                   Kn=0.1, capacity=120_000)
+    g, o = pair(s)
+    g.init()
+    o.init()
+    g.step(200, dig.WALLFLUX | dig.SYNC)
+    o.step(200, orc.EWMA)
+    assert_same_particles(g, o)
+    surf = g.surface()
+    mi = o.mesh_info()
+    P = s.mesh.nodes[s.mesh.tets]
+    wf = g.wall_flux()
+    ib = 0
+    t = 200 * s.dt
+    for tt in range(len(s.mesh.tets)):
+        for f in range(4):
+            if mi["nbr"][tt, f] >= 0:
+                continue
+            q = [k for k in range(4) if k != f]
+            A = 0.5 * np.linalg.norm(np.cross(P[tt, q[1]] - P[tt, q[0]], P[tt, q[2]] - P[tt, q[0]]))
+            nrm = mi["normals"][tt, f]
+            G = wf[ib, 1:4] / (A * t)
+            p = G @ nrm
+            exp = [wf[ib, 0] * s.F_N / (A * t), p, *(G - p * nrm), wf[ib, 4] / (A * t)]
+            assert np.allclose(surf[ib], exp, rtol=1e-9, atol=1e-9 * np.abs(exp).max())
+            ib += 1
+    kT = W.K_B * s.T_init
+    p_exact = s.n_init * kT
+    flux_exact = s.n_init * math.sqrt(8.0 * kT / (math.pi * s.gas.mass)) / 4.0
+    # the box's 12 faces have equal areas: face means are box-wide means
+    assert abs(surf[:, 0].mean() - flux_exact) < 0.05 * flux_exact
+    assert abs(surf[:, 1].mean() - p_exact) < 0.05 * p_exact
+    assert np.abs(surf[:, 2:5].mean(axis=0)).max() < 0.05 * p_exact
+    assert abs(surf[:, 5].mean()) < 0.05 * p_exact * math.sqrt(2 * kT / s.gas.mass)
