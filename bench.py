@@ -244,7 +244,8 @@ def centreline_map(scen):
 def convergence_experiment(args):
     """GPU time to the converged cavity field: plain DSMC vs DIG vs DIG with
     the learned closure, on the near-continuum cavity (20^3 hexahedra, Kn =
-    0.001, 3M particles).  The reference field and the closure's training data
+    0.001, 3M particles; or, with --conv-workload cavity30, the 30^3-hexahedra
+    Kn = 0.01 cavity with 8M particles).  The reference field and the closure's training data
     come from the solver itself (a DIG run); every timed run starts from the
     initial equilibrium.  Returns the result object."""
     import numpy as np
@@ -254,7 +255,7 @@ def convergence_experiment(args):
     from paper_2607_08195_gb300 import workload as W
 
     dev = "cuda:0"
-    scen = W.config_c3()
+    scen = W.config_c2() if getattr(args, "conv_workload", "cavity20") == "cavity30" else W.config_c3()
     Uw = 50.0
     pu, pv, nh = centreline_map(scen)
     NSC = 200            # DSMC steps per coupling cycle
@@ -447,6 +448,9 @@ def main():
     ap.add_argument("--conv-plain-cycles", type=int, default=160)
     ap.add_argument("--conv-ref", type=int, default=40)
     ap.add_argument("--conv-noise", type=int, default=20)
+    ap.add_argument("--conv-workload", default="cavity20", choices=["cavity20", "cavity30"],
+                    help="cavity20: Kn 0.001, 50 mean free paths per cell (the experiment); cavity30: Kn 0.01, "
+                         "3.3 mean free paths per cell, where plain DSMC is nearly resolved (a check of DIG's field)")
     ap.add_argument("--conv-net-na", type=int, default=50,
                     help="moving-average length n_a of the DIG run with the learned closure")
     ap.add_argument("--conv-threshold", type=float, default=0.02)
