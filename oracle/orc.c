@@ -168,6 +168,8 @@ struct orc_ctx {
   float* bc_U;       /* [3 n_bcs] */
   /* gas constants (FP32 where the collision arithmetic uses them) */
   float c_vhs, one_m_omega, cmax0, p_inel, lb_exp, hmr, T_init_f, sigma_init, u0f[3];
+  int vss;          /* alpha != 1: VSS scattering */
+  float inv_alpha;  /* 1 / alpha */
   int nphi;
   /* particles (sorted by cell between steps) */
   int64_t N, cap;
@@ -233,6 +235,9 @@ orc_ctx* orc_create(const orc_config* cfg) {
   /* Borgnakke-Larsen probability, Eq. inelastic_probability */
   double a = cfg->alpha;
   c->p_inel = (float)(a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0) * cfg->Z_rot));
+  /* VSS scattering law (paper Sec. 2.1) for alpha != 1; alpha = 1 is VHS */
+  c->vss = a != 1.0;
+  c->inv_alpha = (float)(1.0 / a);
   c->lb_exp = (float)(1.0 / (2.5 - w));
   c->hmr = (float)(0.5 * mr / KB); /* relative translational energy in kelvin per (m/s)^2 */
   c->T_init_f = (float)cfg->T_init;
@@ -583,9 +588,70 @@ static void unit_vector(const orc_ctx* c, int purpose, uint32_t ent, uint32_t su
   e[0] = 0.0f; e[1] = 0.0f; e[2] = 1.0f;
 }
 
+/* Post-collision direction of the relative velocity under the VSS model
+ * (paper Sec. 2.1; Koura & Matsumoto 1991): the impact parameter b satisfies
+ * b/d = cos^alpha(chi/2) with (b/d)^2 uniform, so the deflection angle has
+ * cos chi = 2 R^(1/alpha) - 1 for R uniform in (0,1); the azimuth epsilon
+ * about the pre-collision direction g/|g| is uniform.  cos and sin epsilon
+ * come from a uniform point (a, b) of the unit disc: (a^2 - b^2)/s and
+ * 2ab/s with s = a^2 + b^2.  The new direction is
+ *   e = cos chi u + sin chi (sin epsilon A + cos epsilon B)
+ * with u = g/|g|, q = sqrt(u_y^2 + u_z^2), A = (q, -u_x u_y/q, -u_x u_z/q)
+ * and B = (0, u_z/q, -u_y/q), an orthonormal pair perpendicular to u; when
+ * q is below 1e-6 (g along x) A = (0, 1, 0) and B = (0, 0, 1).
+ * Random words: draw 0 of the purpose gives R (word 0) and the first disc
+ * point (words 1, 2); draws 1..31 give two points each (words 0,1 and 2,3).
+ * g2 = g_x^2 + g_y^2 + g_z^2 > 0. */
+static void vss_direction(const orc_ctx* c, int purpose, uint32_t ent, uint32_t sub, uint32_t step,
+                          const float g[3], float g2, float e[3]) {
+  uint32_t w[4];
+  rng4(c, purpose, ent, sub, step, 0, w);
+  const float ct = 2.0f * orc_powf(u01f(w[0]), c->inv_alpha) - 1.0f;
+  const float st = sqrtf((1.0f - ct) * (1.0f + ct));
+  float ce = 1.0f, se = 0.0f;
+  int found = 0;
+  for (uint32_t d = 0; d < 32 && !found; ++d) {
+    if (d > 0) rng4(c, purpose, ent, sub, step, d, w);
+    /* d == 0: the point (w1, w2); d > 0: (w0, w1) then (w2, w3) */
+    for (int k0 = d == 0 ? 1 : 0; k0 <= 2 && !found; k0 += 2) {
+      const float a1 = 2.0f * u01f(w[k0]) - 1.0f;
+      const float b1 = 2.0f * u01f(w[k0 + 1]) - 1.0f;
+      const float s = a1 * a1 + b1 * b1;
+      if (s < 1.0f && s > 0.0f) {
+        ce = (a1 * a1 - b1 * b1) / s;
+        se = 2.0f * a1 * b1 / s;
+        found = 1;
+      }
+    }
+  }
+  const float gn = sqrtf(g2);
+  const float ux = g[0] / gn, uy = g[1] / gn, uz = g[2] / gn;
+  const float qn = sqrtf(uy * uy + uz * uz);
+  if (qn > 1e-6f) {
+    e[0] = ct * ux + st * se * qn;
+    e[1] = ct * uy + st * (ce * uz - se * ux * uy) / qn;
+    e[2] = ct * uz - st * (ce * uy + se * ux * uz) / qn;
+  } else {
+    e[0] = ct * ux;
+    e[1] = ct * uy + st * se;
+    e[2] = ct * uz + st * ce;
+  }
+}
+
+int orc_vss_directions(orc_ctx* c, const float* g, int64_t n, float* e) {
+  if (!c || (n > 0 && (!g || !e))) return -1;
+  for (int64_t p = 0; p < n; ++p) {
+    const float* gp = g + 3 * p;
+    const float g2 = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
+    if (!(g2 > 0.0f)) return fail(c, -1, "orc_vss_directions: zero relative velocity");
+    vss_direction(c, RP_DIR, (uint32_t)p, 0u, 0u, gp, g2, e + 3 * p);
+  }
+  return 0;
+}
+
 /* ------------------------------------------------------------------------- */
-/* S0: initial state (paper Sec. 5.1: uniform equilibrium; Alg. 1 line       */
-/* "initialise the macroscopic state and DSMC particle state")                */
+/* S0: initial state (paper Sec. 5.1: uniform equilibrium; the               */
+/* initialisation step of Alg. 1)                                             */
 /* ------------------------------------------------------------------------- */
 int orc_particles_init(orc_ctx* c, int64_t n) {
   if (!c->vol) return fail(c, -7, "mesh not loaded");
@@ -799,7 +865,7 @@ int orc_track_one(orc_ctx* c, double* x, float* v, int32_t* cell, int64_t slot, 
 }
 
 /* ------------------------------------------------------------------------- */
-/* S5/S6: NTC collisions (Bird 1994, Sec. 11.1) with VHS cross sections and   */
+/* S5/S6: NTC collisions (Bird 1994, Sec. 11.1) with VHS/VSS collisions and   */
 /* serial Borgnakke-Larsen exchange (paper Sec. 2.1, Eq. inelastic prob.)     */
 /* ------------------------------------------------------------------------- */
 static void record_pair(orc_ctx* c, int32_t cell, int32_t k, int32_t i, int32_t j, int acc) {
@@ -836,6 +902,7 @@ static void collide_cell(orc_ctx* c, int64_t cell, uint32_t step, int record) {
     float g[3];
     for (int q = 0; q < 3; ++q) g[q] = v[3 * i + q] - v[3 * j + q];
     float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const float g2_pre = g2;
     float sc = g2 > 0.0f ? c->c_vhs * orc_powf(g2, c->one_m_omega) : 0.0f;
     if (sc > c->cmax[cell]) c->cmax[cell] = sc;
     float R = u01f(w[2]);
@@ -865,7 +932,11 @@ static void collide_cell(orc_ctx* c, int64_t cell, uint32_t step, int record) {
     }
     float cr = sqrtf(g2);
     float e[3];
-    unit_vector(c, RP_DIR, (uint32_t)cell, (uint32_t)k, step, e);
+    /* VHS: isotropic; VSS: deflected from the pre-collision g */
+    if (c->vss)
+      vss_direction(c, RP_DIR, (uint32_t)cell, (uint32_t)k, step, g, g2_pre, e);
+    else
+      unit_vector(c, RP_DIR, (uint32_t)cell, (uint32_t)k, step, e);
     float h = 0.5f * cr;
     for (int q = 0; q < 3; ++q) {
       float cm = (v[3 * i + q] + v[3 * j + q]) * 0.5f;

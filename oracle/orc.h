@@ -133,6 +133,10 @@ int orc_closure_targets(orc_ctx* c, int32_t which, const float* X, int64_t n_row
 int orc_sort_by_cell(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* cell_start, int32_t* order);
 
 /* primitives exposed for the pins */
+/* unit post-collision directions e[n][3] of the VSS model for relative
+ * velocities g[n][3] (non-zero), alpha from the context's config; entity p,
+ * sub 0, step 0 of the context's collision-direction random stream */
+int orc_vss_directions(orc_ctx* c, const float* g, int64_t n, float* e);
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 float orc_lnf(float x);
 float orc_expf(float y);

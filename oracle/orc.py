@@ -97,6 +97,7 @@ def lib():
         L.orc_track_one.argtypes = [P, P, P, P, C.c_int64, C.c_int64]
         L.orc_sort_by_cell.argtypes = [P, C.c_int64, C.c_int32, P, P]
         L.orc_couple.argtypes = [P, P]
+        L.orc_vss_directions.argtypes = [P, P, C.c_int64, P]
         L.orc_mlp_nparam.restype = C.c_int32
         L.orc_bf16.restype = C.c_double
         L.orc_bf16.argtypes = [C.c_double]
@@ -182,6 +183,14 @@ class Oracle:
             self.close()
         except Exception:
             pass
+
+    def vss_directions(self, g):
+        """Unit post-collision directions [n, 3] of the scattering law for the
+        relative velocities g [n, 3] (non-zero), with this context's alpha."""
+        g = np.ascontiguousarray(g, np.float32)
+        e = np.zeros_like(g)
+        self._check(self.L.orc_vss_directions(self.h, _p(g), len(g), _p(e)))
+        return e
 
     def init(self, n=None):
         self._check(self.L.orc_particles_init(self.h, self.scen.n_particles if n is None else n))

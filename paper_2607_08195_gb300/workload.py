@@ -43,14 +43,24 @@ class Gas:
     alpha: float = 1.0
 
     def mu_ref(self) -> float:
-        """VHS viscosity at T_ref (Bird 1994, eq. 4.62): the scenario's mu_0."""
+        """Viscosity at T_ref, the scenario's mu_0: the VHS value (Bird 1994,
+        eq. 4.62) times (alpha + 1)(alpha + 2) / (6 alpha) for a VSS gas, the
+        ratio of the VHS viscosity cross section (2/3 of the total) to the VSS
+        one (4 alpha / ((alpha + 1)(alpha + 2)) of the total)."""
         w = self.omega
-        return 15.0 * math.sqrt(math.pi * self.mass * K_B * self.T_ref) / (
+        mu = 15.0 * math.sqrt(math.pi * self.mass * K_B * self.T_ref) / (
             2.0 * math.pi * self.d_ref ** 2 * (5.0 - 2.0 * w) * (7.0 - 2.0 * w))
+        a = self.alpha
+        if a != 1.0:
+            mu *= (a + 1.0) * (a + 2.0) / (6.0 * a)
+        return mu
 
 
 ARGON = Gas(mass=6.63e-26, d_ref=4.17e-10, omega=0.81, T_ref=273.0)
 NITROGEN = Gas(mass=4.65e-26, d_ref=4.17e-10, omega=0.74, T_ref=273.0, rot_dof=2, Z_rot=5.0)
+# VSS parameters of Bird 1994, Table A1
+ARGON_VSS = Gas(mass=6.63e-26, d_ref=4.11e-10, omega=0.81, T_ref=273.0, alpha=1.40)
+NITROGEN_VSS = Gas(mass=4.65e-26, d_ref=4.11e-10, omega=0.74, T_ref=273.0, rot_dof=2, Z_rot=5.0, alpha=1.36)
 
 
 @dataclasses.dataclass

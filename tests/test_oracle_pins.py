@@ -315,6 +315,103 @@ def test_maxwell_molecule_stress_relaxation():
         assert abs(a - pred) < 4 * math.sqrt(2.0 / n) * th * 1.5 + 0.03 * abs(a0), (k, a, pred)
 
 
+def _ks_uniform(u):
+    """Kolmogorov-Smirnov distance of samples u in [0, 1] from the uniform law."""
+    x = np.sort(np.asarray(u, np.float64))
+    n = len(x)
+    return max(np.max(np.arange(1, n + 1) / n - x), np.max(x - np.arange(n) / n))
+
+
+def _vss_samples(alpha, n, seed, along_x=False):
+    gas = dataclasses.replace(W.ARGON, alpha=alpha)
+    o = orc.Oracle(box_scenario(gas=gas))
+    rng = np.random.default_rng(seed)
+    if along_x:
+        g = np.zeros((n, 3))
+        g[:, 0] = rng.choice([-1.0, 1.0], n) * rng.uniform(1.0, 900.0, n)
+    else:
+        g = rng.standard_normal((n, 3)) * rng.uniform(0.1, 900.0, (n, 1))
+    g = g.astype(np.float32)
+    e = o.vss_directions(g).astype(np.float64)
+    u = g.astype(np.float64)
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    return u, e
+
+
+def _azimuth(u, e):
+    """Angle of e about u in a frame built independently of the oracle's."""
+    r = np.where(np.abs(u[:, 2:3]) < 0.9, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+    a = r - (r * u).sum(1)[:, None] * u
+    a /= np.linalg.norm(a, axis=1)[:, None]
+    b = np.cross(u, a)
+    return np.arctan2((e * b).sum(1), (e * a).sum(1))
+
+
+@pytest.mark.parametrize("alpha", [1.0, 1.4, 3.0, 0.6])
+@pytest.mark.parametrize("along_x", [False, True])
+def test_vss_deflection_law(alpha, along_x):
+    """VSS scattering (paper Sec. 2.1; Koura & Matsumoto 1991): b/d = cos^alpha(chi/2)
+    with (b/d)^2 uniform gives P(cos chi <= x) = ((1 + x)/2)^alpha, so
+    <cos chi> = (alpha - 1)/(alpha + 1) and <sin^2 chi> = 4 alpha/((alpha + 1)(alpha + 2))
+    (2/3 for VHS); the azimuth about g is uniform and the direction a unit vector.
+    Checked on generic relative velocities and on velocities along x (the frame's
+    degenerate case)."""
+    n = 100_000
+    u, e = _vss_samples(alpha, n, seed=5 + int(10 * alpha), along_x=along_x)
+    assert np.abs(np.linalg.norm(e, axis=1) - 1.0).max() < 1e-6
+    ct = np.clip((e * u).sum(1), -1.0, 1.0)
+    # probability integral transform: F(cos chi) is uniform
+    assert _ks_uniform(((1.0 + ct) / 2.0) ** alpha) < 1.63 / math.sqrt(n)
+    m, sd = ct.mean(), ct.std() / math.sqrt(n)
+    assert abs(m - (alpha - 1.0) / (alpha + 1.0)) < 4.5 * sd
+    s2 = 1.0 - ct ** 2
+    assert abs(s2.mean() - 4.0 * alpha / ((alpha + 1.0) * (alpha + 2.0))) < 4.5 * s2.std() / math.sqrt(n)
+    phi = _azimuth(u, e)
+    assert _ks_uniform((phi + math.pi) / (2.0 * math.pi)) < 1.63 / math.sqrt(n)
+
+
+def test_vss_maxwell_molecule_stress_relaxation():
+    """For Maxwell molecules (omega = 1) the stress anisotropy relaxes as
+    exp(-p t / mu) with mu inversely proportional to the viscosity cross section:
+    VSS with alpha = 3 has 4 alpha/((alpha + 1)(alpha + 2)) = 3/5 of the total cross
+    section against 2/3 for VHS, so with the same collision rate its anisotropy
+    decays 0.9 times as fast.  Two runs from the same state and random stream."""
+    rates = {}
+    for alpha in (1.0, 3.0):
+        gas = W.Gas(mass=6.63e-26, d_ref=4.17e-10, omega=1.0, T_ref=273.0, alpha=alpha)
+        s = box_scenario(nh=1, n_particles=48000, gas=gas, dt_factor=0.02, seed=31)
+        o = orc.Oracle(s)
+        rng = np.random.default_rng(3)
+        n = s.n_particles
+        sig = math.sqrt(KB * 273.0 / gas.mass)
+        v = rng.standard_normal((n, 3)) * sig * np.array([1.3, 0.8, 0.8])
+        cell = rng.integers(0, 6, n).astype(np.int32)
+        P = s.mesh.nodes[s.mesh.tets[cell]]
+        x = np.einsum("nk,nkc->nc", rng.dirichlet(np.ones(4), n), P)
+        o.write(x, v.astype(np.float32), np.zeros(n, np.float32), cell)
+
+        def aniso():
+            _, vv, _, _ = o.read()
+            c = vv.astype(np.float64)
+            c -= c.mean(0)
+            m2 = (c * c).mean(0)
+            return m2[0] - 0.5 * (m2[1] + m2[2]), m2.sum() / 3
+
+        a0, th = aniso()
+        T = gas.mass * th / KB
+        # the VHS viscosity of the same diameter fixes the time unit of both runs
+        mu_vhs = dataclasses.replace(gas, alpha=1.0).mu_ref() * (T / gas.T_ref) ** gas.omega
+        p = s.n_init * KB * T
+        steps = 50
+        o.step(steps, 0)
+        a, _ = aniso()
+        rates[alpha] = -math.log(a / a0) / (p * steps * s.dt / mu_vhs)
+        # against the VSS viscosity itself (Gas.mu_ref carries the alpha factor)
+        mu = gas.mu_ref() * (T / gas.T_ref) ** gas.omega
+        assert abs(-math.log(a / a0) / (p * steps * s.dt / mu) - 1.0) < 0.05, (alpha, rates[alpha])
+    assert abs(rates[3.0] / rates[1.0] - 0.9) < 0.02, rates
+
+
 def test_jeans_landau_rotational_relaxation():
     """P3: homogeneous diatomic gas with T_t != T_r follows the Jeans-Landau law
     dT_r/dt = (T - T_r)/(Z_r tau), tau = mu(T_t)/p_t (paper Eq. jeans_landau),
