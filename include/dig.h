@@ -89,7 +89,8 @@ typedef struct dig_config {
   double d_ref;      /* VHS reference diameter, m */
   double omega;      /* viscosity-temperature index */
   double T_ref;      /* reference temperature of d_ref, K */
-  double alpha;      /* VSS angular parameter in P_inelastic (1 = VHS) */
+  double alpha;      /* VSS scattering parameter, > 0: 1 = VHS (isotropic); otherwise the
+                        VSS deflection law (paper Sec. 2.1); also enters P_inelastic */
   double Z_rot;      /* rotational collision number Z_r */
   int32_t rot_dof;   /* rotational degrees of freedom d_r: 0 or 2 */
   int32_t max_cross; /* face crossings allowed per particle per step (<= 0: 4096) */
@@ -127,7 +128,9 @@ typedef struct dig_bc {
 
 typedef struct dig_ctx dig_ctx;
 
-/* Create a context for one gas and time step.  No GPU work is done. */
+/* Create a context for one gas and time step.  No GPU work is done.
+ * DIG_ERR_ARG unless mass, dt, F_N and alpha are positive, rot_dof is 0 or 2
+ * and stage_cap <= 8192. */
 int dig_create(const dig_config* cfg, dig_ctx** out);
 /* Release the context (the caller then frees its arena). */
 int dig_destroy(dig_ctx* ctx);

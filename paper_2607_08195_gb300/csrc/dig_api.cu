@@ -165,7 +165,8 @@ const char* dig_last_error(dig_ctx* ctx) { return ctx ? ctx->err : g_err; }
 
 int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (!cfg || !out) return DIG_ERR_ARG;
-  if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || (cfg->rot_dof != 0 && cfg->rot_dof != 2) ||
+  if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || !(cfg->alpha > 0) ||
+      (cfg->rot_dof != 0 && cfg->rot_dof != 2) ||
       cfg->stage_cap > 8192)
     return DIG_ERR_ARG;
   dig_ctx* c = new dig_ctx();
@@ -620,6 +621,8 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   ctx->cmax0 = P.c_vhs * host_exp_f(P.one_m_omega * host_ln_f(c0sq));
   const double a = c.alpha;
   P.p_inel = (float)(a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0) * c.Z_rot));
+  P.vss = a != 1.0 ? 1 : 0;
+  P.inv_alpha = (float)(1.0 / a);
   P.lb_exp = (float)(1.0 / (2.5 - w));
   P.hmr = (float)(0.5 * mr / KB);
   P.T_init = (float)c.T_init;

@@ -86,6 +86,8 @@ struct Params {
   // gas constants in FP32
   uint32_t seed_lo, seed_hi;
   float c_vhs, one_m_omega, p_inel, lb_exp, hmr;
+  float inv_alpha;          // 1 / alpha of the VSS scattering law (alpha != 1)
+  int vss;                  // 1: VSS scattering, 0: VHS (isotropic)
   float T_init, sigma_init, u0[3];
   // per-cell grouping and sort state
   int* cs;      // [n+1] start of each cell in the current grouping

@@ -239,6 +239,62 @@ __device__ __forceinline__ void unit_vec_from(const Params& P, const uint32_t (&
   ez = 1.0f;
 }
 
+// Post-collision direction of the relative velocity under the VSS model
+// (paper Sec. 2.1; Koura & Matsumoto 1991).  The impact parameter obeys
+// b/d = cos^alpha(chi/2) with (b/d)^2 uniform, so cos chi = 2 R^(1/alpha) - 1
+// for R uniform in (0,1); the azimuth about u = g/|g| is uniform, its cosine
+// and sine taken from a uniform point (a, b) of the unit disc as
+// (a^2 - b^2)/s and 2ab/s, s = a^2 + b^2.  The direction is
+// cos chi u + sin chi (sin eps A + cos eps B) with the orthonormal pair
+// A = (q, -u_x u_y/q, -u_x u_z/q), B = (0, u_z/q, -u_y/q), q = |(u_y, u_z)|,
+// or A = (0, 1, 0), B = (0, 0, 1) when q <= 1e-6 (g along x).  Random words:
+// w0 (draw 0) gives R (word 0) and the first disc point (words 1, 2); draws
+// 1..31 two points each (words 0,1 and 2,3).  g2 = |g|^2 > 0.
+__device__ __forceinline__ void vss_dir_from(const Params& P, const uint32_t (&w0)[4], uint32_t ent, uint32_t sub,
+                                             uint32_t step, float gx, float gy, float gz, float g2, float& ex,
+                                             float& ey, float& ez) {
+  const float ct = 2.0f * pow_f(u01f(w0[0]), P.inv_alpha) - 1.0f;
+  const float st = sqrtf((1.0f - ct) * (1.0f + ct));
+  float ce = 1.0f, se = 0.0f;
+  bool found = false;
+  {
+    const float a1 = 2.0f * u01f(w0[1]) - 1.0f;
+    const float b1 = 2.0f * u01f(w0[2]) - 1.0f;
+    const float s = a1 * a1 + b1 * b1;
+    if (s < 1.0f && s > 0.0f) {
+      ce = (a1 * a1 - b1 * b1) / s;
+      se = 2.0f * a1 * b1 / s;
+      found = true;
+    }
+  }
+  for (uint32_t d = 1; d < 32 && !found; ++d) {
+    uint32_t w[4];
+    rng(P, RP_DIR, ent, sub, step, d, w);
+    for (int k0 = 0; k0 <= 2 && !found; k0 += 2) {
+      const float a1 = 2.0f * u01f(w[k0]) - 1.0f;
+      const float b1 = 2.0f * u01f(w[k0 + 1]) - 1.0f;
+      const float s = a1 * a1 + b1 * b1;
+      if (s < 1.0f && s > 0.0f) {
+        ce = (a1 * a1 - b1 * b1) / s;
+        se = 2.0f * a1 * b1 / s;
+        found = true;
+      }
+    }
+  }
+  const float gn = sqrtf(g2);
+  const float ux = gx / gn, uy = gy / gn, uz = gz / gn;
+  const float qn = sqrtf(uy * uy + uz * uz);
+  if (qn > 1e-6f) {
+    ex = ct * ux + st * se * qn;
+    ey = ct * uy + st * (ce * uz - se * ux * uy) / qn;
+    ez = ct * uz - st * (ce * uy + se * ux * uz) / qn;
+  } else {
+    ex = ct * ux;
+    ey = ct * uy + st * se;
+    ez = ct * uz + st * ce;
+  }
+}
+
 struct Cnt {
   unsigned cand = 0, coll = 0, lb = 0, cross = 0, wall = 0, removed = 0, stuck = 0;
 };
@@ -502,11 +558,12 @@ __device__ int track(const Params& P, double& x, double& y, double& z, float& vx
 }
 
 // ---------------------------------------------------------------------------
-// NTC collisions of one cell (Bird 1994 Sec. 11.1), VHS, serial
-// Borgnakke-Larsen exchange (paper Eq. inelastic_probability).  Candidates are
-// processed in order k = 0, 1, ... on the cell's shared-memory velocities.
+// NTC collisions of one cell (Bird 1994 Sec. 11.1), VHS cross sections with
+// isotropic (VHS) or VSS scattering, serial Borgnakke-Larsen exchange (paper
+// Eq. inelastic_probability).  Candidates are processed in order k = 0, 1, ...
+// on the cell's velocities in the gathered buffer.
 // ---------------------------------------------------------------------------
-template <bool DIAT>
+template <bool DIAT, bool VSS>
 __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, float* vz, float* I, int N,
                              uint32_t step, bool record, Cnt& cnt) {
   if (N < 2) return;
@@ -531,6 +588,7 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
     if (j >= i) j = j + 1;
     const float gx = vx[i] - vx[j], gy = vy[i] - vy[j], gz = vz[i] - vz[j];
     float g2 = gx * gx + gy * gy + gz * gz;
+    const float g2_pre = g2;
     const float sc = g2 > 0.0f ? P.c_vhs * pow_f(g2, P.one_m_omega) : 0.0f;
     if (sc > cmax) cmax = sc;
     const float R = u01f(w[2]);
@@ -572,7 +630,10 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
     }
     const float cr = sqrtf(g2);
     float ex, ey, ez;
-    unit_vec_from(P, wd, (uint32_t)cell, (uint32_t)k, step, ex, ey, ez);
+    if (VSS)
+      vss_dir_from(P, wd, (uint32_t)cell, (uint32_t)k, step, gx, gy, gz, g2_pre, ex, ey, ez);
+    else
+      unit_vec_from(P, wd, (uint32_t)cell, (uint32_t)k, step, ex, ey, ez);
 #pragma unroll
     for (int q = 0; q < 4; ++q) w[q] = wn[q];
     const float h = 0.5f * cr;
@@ -784,13 +845,13 @@ __global__ void __launch_bounds__(256) k_order(Params P, Buf IN, Buf OUT) {
 }
 
 // NTC collisions of every cell, thread per cell, on the gathered velocities
-template <bool DIAT>
+template <bool DIAT, bool VSS>
 __global__ void __launch_bounds__(128) k_collide(Params P, Buf OUT, uint32_t step, int record) {
   Cnt cnt;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < P.n_cells) {
     const int base = P.cs[c], N = P.cs[c + 1] - base;
-    collide_cell<DIAT>(P, c, OUT.vx + base, OUT.vy + base, OUT.vz + base, DIAT ? OUT.Ir + base : nullptr, N, step,
+    collide_cell<DIAT, VSS>(P, c, OUT.vx + base, OUT.vy + base, OUT.vz + base, DIAT ? OUT.Ir + base : nullptr, N, step,
                        record != 0, cnt);
   }
   flush_counters(P, cnt);
@@ -1527,10 +1588,15 @@ void launch_cell_pass(const Params& P, const Buf& in, const Buf& out, int pass, 
   g_launches += 1;
   if (pass & PASS_COLLIDE) {
     const int rec = (sflags & S_PAIRS) != 0;
-    if (diat)
-      k_collide<true><<<blocks_for(P.n_cells, 128), 128, 0, s>>>(P, out, step_coll, rec);
+    const int nb = blocks_for(P.n_cells, 128);
+    if (diat && P.vss)
+      k_collide<true, true><<<nb, 128, 0, s>>>(P, out, step_coll, rec);
+    else if (diat)
+      k_collide<true, false><<<nb, 128, 0, s>>>(P, out, step_coll, rec);
+    else if (P.vss)
+      k_collide<false, true><<<nb, 128, 0, s>>>(P, out, step_coll, rec);
     else
-      k_collide<false><<<blocks_for(P.n_cells, 128), 128, 0, s>>>(P, out, step_coll, rec);
+      k_collide<false, false><<<nb, 128, 0, s>>>(P, out, step_coll, rec);
     g_launches += 1;
   }
 #define DIG_MV(D, T) launch_move_t<D, T>(P, in, out, pass, sflags, step_move, ewa, ewb, TC, s)

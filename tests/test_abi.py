@@ -50,6 +50,12 @@ def test_create_rejects_bad_config(lib):
     cfg = dig.DigConfig()
     h = ctypes.c_void_p()
     assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == -1  # zero mass / dt
+    from paper_2607_08195_gb300 import workload as W
+
+    for alpha in (0.0, -1.0, float("nan")):  # the VSS exponent 1/alpha needs alpha > 0
+        cfg = dig.make_config(W.config_small())
+        cfg.alpha = alpha
+        assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == -1, alpha
 
 
 def test_mesh_load_host_validation(lib):

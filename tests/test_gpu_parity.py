@@ -126,6 +126,32 @@ def test_diatomic_bit_exact():
     assert g.counters()["lb"] == o.counters()["lb"] > 0
 
 
+@pytest.mark.parametrize("gas", [W.ARGON_VSS, W.NITROGEN_VSS, dataclasses.replace(W.ARGON, alpha=3.0)],
+                         ids=["argon-vss", "nitrogen-vss", "alpha3"])
+def test_vss_scattering_bit_exact(gas):
+    """VSS scattering (alpha != 1): one step from a written state with every
+    candidate pair, then 12 more steps, bit-identical to the oracle."""
+    s = W.cavity_scenario(4, 12_000, 0.05, seed=9, gas=gas)
+    rng = np.random.default_rng(9)
+    x, v, Ir, cell = W.random_particles(rng, s, 12_000)
+    g, o = pair(s)
+    g.write(x, v, Ir, cell)
+    o.write(x, v, Ir, cell)
+    g.step(1, dig.EWMA | dig.RECORD_PAIRS | dig.SYNC)
+    o.step(1, orc.EWMA | orc.RECORD_PAIRS)
+    assert_same_particles(g, o)
+    pg, po = g.pairs(), o.pairs()
+    assert len(pg) == len(po) > 100
+    assert np.array_equal(pg, po)
+    g.step(12, dig.EWMA | dig.SYNC)
+    o.step(12, orc.EWMA)
+    assert_same_particles(g, o)
+    cg, co = g.counters(), o.counters()
+    for k in ("cand", "coll", "lb", "cross", "wall"):
+        assert cg[k] == co[k], (k, cg[k], co[k])
+    assert co["coll"] > 1000
+
+
 @pytest.mark.parametrize("tile_cells,stage_cap,threads", [(1, 4096, 256), (7, 512, 256), (256, 8192, 256),
                                                           (0, 1024, 64), (5, 1536, 128)])
 def test_tiling_does_not_change_results(tile_cells, stage_cap, threads):
