@@ -116,6 +116,12 @@ typedef struct dig_config {
   int32_t tile_cells;    /* cells per CTA of the move kernel (<= 0: chosen from stage_cap and the load) */
   int32_t cta_threads;   /* threads per CTA of the move kernel: 64, 128 or 256 (<= 0: 256) */
   int32_t closure;       /* 1: dig_couple takes the HoT from the learned closure (see closure_*) */
+  int32_t recon;         /* mean of the neighbour reconstruction (Sec. 3.2, every neighbour with the
+                            same weight) for density and temperatures: 0 arithmetic, 1 logarithmic
+                            (exp of the mean logarithm, the log-mean reconstruction of Sec. 6; the
+                            arithmetic mean where a contributing value is not positive); velocity
+                            and HoT always arithmetic */
+  int32_t pad;           /* zero */
 } dig_config;
 
 typedef struct dig_bc {
@@ -129,8 +135,8 @@ typedef struct dig_bc {
 typedef struct dig_ctx dig_ctx;
 
 /* Create a context for one gas and time step.  No GPU work is done.
- * DIG_ERR_ARG unless mass, dt, F_N and alpha are positive, rot_dof is 0 or 2
- * and stage_cap <= 8192. */
+ * DIG_ERR_ARG unless mass, dt, F_N and alpha are positive, rot_dof is 0 or 2,
+ * recon is 0 or 1 and stage_cap <= 8192. */
 int dig_create(const dig_config* cfg, dig_ctx** out);
 /* Release the context (the caller then frees its arena). */
 int dig_destroy(dig_ctx* ctx);

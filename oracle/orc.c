@@ -1487,6 +1487,42 @@ static int64_t closure_apply(orc_ctx* c, const nd_t* d) {
   return used;
 }
 
+/* Reconstruction of cell t from its available face neighbours, every
+ * neighbour with the same weight (Sec. 3.2): the arithmetic mean of state and
+ * HoT; with recon = 1 the density and the temperatures take the logarithmic
+ * (geometric) mean exp(mean ln) instead -- the log-mean reconstruction that
+ * the paper's conclusions (Sec. 6) name -- when all contributing values are
+ * positive (the arithmetic mean otherwise).  Returns the number of
+ * contributing neighbours (0: nothing written). */
+static int neighbour_mean(orc_ctx* c, int64_t t, const uint8_t* avail) {
+  static const int lq[3] = {0, 4, 5};
+  double acc[18], lg[3] = {0.0, 0.0, 0.0};
+  int pos[3] = {1, 1, 1};
+  memset(acc, 0, sizeof acc);
+  int cnt = 0;
+  for (int f = 0; f < 4; ++f) {
+    const int32_t nb = c->nbr[4 * t + f];
+    if (nb < 0 || !avail[nb]) continue;
+    const double* h = c->cp_half + 6 * (int64_t)nb;
+    for (int q = 0; q < 6; ++q) acc[q] += h[q];
+    for (int q = 0; q < 12; ++q) acc[6 + q] += c->cp_hot[12 * (int64_t)nb + q];
+    for (int k = 0; k < 3; ++k) {
+      if (h[lq[k]] > 0.0)
+        lg[k] += log(h[lq[k]]);
+      else
+        pos[k] = 0;
+    }
+    cnt++;
+  }
+  if (cnt == 0) return 0;
+  for (int q = 0; q < 6; ++q) c->cp_half[6 * t + q] = acc[q] / cnt;
+  for (int q = 0; q < 12; ++q) c->cp_hot[12 * t + q] = acc[6 + q] / cnt;
+  if (c->cfg.recon == 1)
+    for (int k = 0; k < 3; ++k)
+      if (pos[k]) c->cp_half[6 * t + lq[k]] = exp(lg[k] / cnt);
+  return cnt;
+}
+
 /* S9: M^{k+1/2}, HoT and the reliability filter with neighbour reconstruction */
 static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_rec, int64_t* n_learned) {
   const int64_t n = c->n_tets;
@@ -1515,27 +1551,15 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
   }
   *n_learned = c->cfg.closure && c->cl_params ? closure_apply(c, d) : 0;
   /* reconstruction passes: a rejected cell with available face neighbours
-   * takes their equal-weight mean (state and HoT); it becomes available for
-   * the next pass */
+   * takes their equal-weight mean (state and HoT, neighbour_mean); it becomes
+   * available for the next pass */
   *n_rec = 0;
   uint8_t* nxt = (uint8_t*)malloc(n);
   for (int pass = 0; pass < c->cfg.passes; ++pass) {
     memcpy(nxt, avail, n);
     for (int64_t t = 0; t < n; ++t) {
       if (avail[t]) continue;
-      double acc[18];
-      memset(acc, 0, sizeof acc);
-      int cnt = 0;
-      for (int f = 0; f < 4; ++f) {
-        const int32_t nb = c->nbr[4 * t + f];
-        if (nb < 0 || !avail[nb]) continue;
-        for (int q = 0; q < 6; ++q) acc[q] += c->cp_half[6 * (int64_t)nb + q];
-        for (int q = 0; q < 12; ++q) acc[6 + q] += c->cp_hot[12 * (int64_t)nb + q];
-        cnt++;
-      }
-      if (cnt == 0) continue;
-      for (int q = 0; q < 6; ++q) c->cp_half[6 * t + q] = acc[q] / cnt;
-      for (int q = 0; q < 12; ++q) c->cp_hot[12 * t + q] = acc[6 + q] / cnt;
+      if (!neighbour_mean(c, t, avail)) continue;
       nxt[t] = 1;
       c->cp_flag[t] = 2.0;
       (*n_rec)++;
@@ -1551,19 +1575,7 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
     memcpy(nxt, avail, n);
     for (int64_t t = 0; t < n; ++t) {
       if (avail[t]) continue;
-      double acc[18];
-      memset(acc, 0, sizeof acc);
-      int cnt = 0;
-      for (int f = 0; f < 4; ++f) {
-        const int32_t nb = c->nbr[4 * t + f];
-        if (nb < 0 || !avail[nb]) continue;
-        for (int q = 0; q < 6; ++q) acc[q] += c->cp_half[6 * (int64_t)nb + q];
-        for (int q = 0; q < 12; ++q) acc[6 + q] += c->cp_hot[12 * (int64_t)nb + q];
-        cnt++;
-      }
-      if (cnt == 0) continue;
-      for (int q = 0; q < 6; ++q) c->cp_half[6 * t + q] = acc[q] / cnt;
-      for (int q = 0; q < 12; ++q) c->cp_hot[12 * t + q] = acc[6 + q] / cnt;
+      if (!neighbour_mean(c, t, avail)) continue;
       nxt[t] = 1;
       c->cp_flag[t] = 3.0;
       filled++;

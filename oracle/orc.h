@@ -50,7 +50,7 @@ typedef struct orc_config {
   double KnD_max;   /* cell Knudsen threshold of the reliability criterion */
   int64_t capacity; /* particle capacity */
   int32_t closure;  /* 1: the learned closure supplies the HoT of the coupling (S12) */
-  int32_t pad;
+  int32_t recon;    /* reconstruction mean of density and temperatures: 0 arithmetic, 1 logarithmic */
 } orc_config;
 
 typedef struct orc_bc {

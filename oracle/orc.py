@@ -29,7 +29,7 @@ class OrcConfig(C.Structure):
         ("T_init", C.c_double), ("u_init", C.c_double * 3), ("mu_ref", C.c_double), ("Kn", C.c_double),
         ("L_ref", C.c_double), ("n_a", C.c_int32), ("N_s", C.c_int32), ("N_m", C.c_int32),
         ("passes", C.c_int32), ("eps_m", C.c_double), ("KnD_max", C.c_double), ("capacity", C.c_int64),
-        ("closure", C.c_int32), ("pad", C.c_int32),
+        ("closure", C.c_int32), ("recon", C.c_int32),
     ]
 
 

@@ -166,7 +166,7 @@ const char* dig_last_error(dig_ctx* ctx) { return ctx ? ctx->err : g_err; }
 int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (!cfg || !out) return DIG_ERR_ARG;
   if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || !(cfg->alpha > 0) ||
-      (cfg->rot_dof != 0 && cfg->rot_dof != 2) ||
+      (cfg->rot_dof != 0 && cfg->rot_dof != 2) || (cfg->recon != 0 && cfg->recon != 1) ||
       cfg->stage_cap > 8192)
     return DIG_ERR_ARG;
   dig_ctx* c = new dig_ctx();
@@ -710,6 +710,7 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
     C.FN = c.F_N;
     C.kB = KB;
     C.KnD_max = c.KnD_max;
+    C.recon = c.recon;
   }
   CK(cudaStreamSynchronize(s));
   if (!ctx->ev) CK(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));

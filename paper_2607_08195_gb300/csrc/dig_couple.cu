@@ -346,13 +346,14 @@ __global__ void k_cl_apply(Params P, CoupleParams C, const float* __restrict__ Y
   atomicAdd(C.stats + 4, 1ull);
 }
 
-// one reconstruction pass: a rejected cell with available face neighbours
-// takes their equal-weight mean of state and HoT
-// one reconstruction layer: a rejected cell with available face neighbours
-// takes their equal-weight mean (state and HoT) and becomes available.  The
-// first `passes` layers are the reconstruction (flag 2); later fill layers
-// (fill >= 0: flag 3, counted in fillcnt[fill]) stop at the first layer after
-// one that filled nothing
+// one reconstruction layer (Sec. 3.2): a rejected cell with available face
+// neighbours takes their mean, every neighbour with the same weight, and
+// becomes available.  The mean is arithmetic, except that with recon = 1 the
+// density and the temperatures take the logarithmic mean exp(mean ln) (the
+// log-mean reconstruction of Sec. 6) where every contributing value is
+// positive.  The first `passes` layers are the reconstruction (flag 2); later
+// fill layers (fill >= 0: flag 3, counted in fillcnt[fill]) stop at the first
+// layer after one that filled nothing
 __global__ void k_cp_recon(Params P, CoupleParams C, const int* __restrict__ av_in, int* __restrict__ av_out,
                            int fill) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -363,7 +364,8 @@ __global__ void k_cp_recon(Params P, CoupleParams C, const int* __restrict__ av_
     av_out[c] = 1;
     return;
   }
-  double acc[18];
+  double acc[18], lg[3] = {0.0, 0.0, 0.0};
+  bool pos[3] = {true, true, true};
   for (int q = 0; q < 18; ++q) acc[q] = 0.0;
   int cnt = 0;
   for (int f = 0; f < 4; ++f) {
@@ -371,12 +373,28 @@ __global__ void k_cp_recon(Params P, CoupleParams C, const int* __restrict__ av_
     if (nb < 0 || !av_in[nb]) continue;
     for (int q = 0; q < 6; ++q) acc[q] += C.half[(size_t)q * n + nb];
     for (int q = 0; q < 12; ++q) acc[6 + q] += C.hot[(size_t)q * n + nb];
+    if (C.recon == 1) {
+      // density, translational and rotational temperature (rows 0, 4, 5)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double v = C.half[(size_t)(k == 0 ? 0 : 3 + k) * n + nb];
+        if (v > 0.0)
+          lg[k] += log(v);
+        else
+          pos[k] = false;
+      }
+    }
     cnt++;
   }
   av_out[c] = cnt > 0 ? 1 : 0;
   if (cnt == 0) return;
   for (int q = 0; q < 6; ++q) C.half[(size_t)q * n + c] = acc[q] / cnt;
   for (int q = 0; q < 12; ++q) C.hot[(size_t)q * n + c] = acc[6 + q] / cnt;
+  if (C.recon == 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (pos[k]) C.half[(size_t)(k == 0 ? 0 : 3 + k) * n + c] = exp(lg[k] / cnt);
+  }
   if (fill < 0) {
     C.flag[c] = 2.0;
     atomicAdd(C.stats + 1, 1ull);

@@ -140,6 +140,7 @@ struct CoupleParams {
   double* mach;  // [n] |u| / c of the current state
   int *avail, *avail2;
   int n_ifaces;          // interior faces (each once)
+  int recon;             // reconstruction mean of density and temperatures: 0 arithmetic, 1 logarithmic
   const int* fcell;      // [n_ifaces] lower-index cell of each interior face
   const int* fface;      // [n_ifaces] its local face
   const int* cfid;       // [4n] interior face of (cell, local face), -1 on the boundary

@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_config_struct_layout():
     # field order and sizes of dig_config as in include/dig.h (no padding surprises)
-    assert ctypes.sizeof(dig.DigConfig) == 8 * 6 + 4 * 2 + 8 * 3 + 8 + 8 + 8 * 3 + 8 * 3 + 4 * 4 + 8 * 2 + 8 + 8 + 4 * 2 + 4 * 2
+    assert ctypes.sizeof(dig.DigConfig) == 8 * 6 + 4 * 2 + 8 * 3 + 8 + 8 + 8 * 3 + 8 * 3 + 4 * 4 + 8 * 2 + 8 + 8 + 4 * 2 + 4 * 2 + 4 * 2
     assert ctypes.sizeof(dig.DigBC) == 48
 
 

@@ -331,15 +331,18 @@ def seeded_dig_state(scen, steps=60, **over):
     return o, o.read(), o.moments(orc.PHI_EWMA), o.wall_flux()
 
 
-@pytest.mark.parametrize("nh,kn,passes,kmax,gas", [(4, 0.1, 3, 0.6, W.ARGON), (5, 0.05, 2, 0.4, W.ARGON),
-                                                   (4, 0.1, 3, 0.6, W.NITROGEN)])
-def test_couple_parity_from_written_state(nh, kn, passes, kmax, gas):
+@pytest.mark.parametrize("nh,kn,passes,kmax,gas,recon", [(4, 0.1, 3, 0.6, W.ARGON, 0), (5, 0.05, 2, 0.4, W.ARGON, 0),
+                                                         (4, 0.1, 3, 0.6, W.NITROGEN, 0),
+                                                         (5, 0.05, 2, 0.4, W.ARGON, 1),
+                                                         (4, 0.1, 3, 0.6, W.NITROGEN, 1)])
+def test_couple_parity_from_written_state(nh, kn, passes, kmax, gas, recon):
     """S9-S11 from an identical written state (particles, moving-average sums,
     wall fluxes): identical filter flags, rejection/reconstruction counts,
     clone/delete decisions and particle cells; FP64 fields within 1e-9.
-    Nitrogen carries the rotational energy equation and heat flux."""
+    Nitrogen carries the rotational energy equation and heat flux; recon = 1
+    reconstructs density and temperatures by their logarithmic mean."""
     s = W.cavity_scenario(nh, 30 * 6 * nh ** 3, kn, seed=17, gas=gas)
-    over = dict(N_m=60, passes=passes, KnD_max=kmax)
+    over = dict(N_m=60, passes=passes, KnD_max=kmax, recon=recon)
     o, (x, v, Ir, cell), phi, wf = seeded_dig_state(s, **over)
     g = dig.Solver(s, "cuda:0", **over)
     g.write(x, v, Ir, cell)

@@ -909,6 +909,53 @@ def test_reconstruction_layers():
         assert np.allclose(half[t], own[nb].mean(axis=0), rtol=1e-12)
 
 
+@pytest.mark.parametrize("recon", [0, 1])
+def test_reconstruction_mean_arithmetic_or_logarithmic(recon):
+    """A layer-1 cell with accepted neighbours of different density, drift and
+    temperature: every neighbour has the same weight (Sec. 3.2); recon = 0 takes
+    the arithmetic mean of every component, recon = 1 the geometric mean
+    exp(mean ln) of density and temperatures (the log-mean reconstruction of
+    Sec. 6) and the arithmetic mean of velocity and HoT.  By the AM-GM
+    inequality the two differ wherever the neighbours differ."""
+    s = W.cavity_scenario(3, 5000, 0.1, seed=3)
+    o = orc.Oracle(s, N_m=1, KnD_max=1.5, passes=1, recon=recon)
+    o.init()
+    n = len(s.mesh.tets)
+    rng = np.random.default_rng(7)
+    acc_cell = rng.random(n) >= 0.3  # scattered rejected cells: many have several accepted neighbours
+    scale = np.where(acc_cell, rng.uniform(0.6, 1.6, n), 0.05)
+    phi = equilibrium_phi(o, s, rho_scale=scale)
+    kT_m = KB * s.T_init / s.gas.mass
+    Ts = rng.uniform(0.7, 1.4, n)
+    ux = rng.uniform(-30.0, 30.0, n)
+    N = phi[:, 0]
+    phi[:, 1] = N * ux
+    phi[:, 4] = N * (kT_m * Ts + ux * ux)
+    phi[:, 5] = N * kT_m * Ts
+    phi[:, 6] = N * kT_m * Ts
+    o.write_moments(orc.PHI_EWMA, phi)
+    o.couple()
+    flags = o.read_couple(3)[:, 0]
+    own, half, hot = o.read_couple(4), o.read_couple(0), o.read_couple(1)
+    nbr = o.mesh_info()["nbr"]
+    acc = flags == 1
+    assert np.array_equal(acc, acc_cell)
+    layer1 = [t for t in np.flatnonzero(flags == 2) if sum(1 for q in nbr[t] if q >= 0 and acc[q]) >= 2]
+    assert len(layer1) > 10
+    gap = 0.0
+    for t in layer1:
+        nb = [q for q in nbr[t] if q >= 0 and acc[q]]
+        am = own[nb].mean(axis=0)
+        want = am.copy()
+        if recon == 1:
+            for q in (0, 4, 5):
+                want[q] = math.exp(np.log(own[nb, q]).mean())
+        assert np.allclose(half[t], want, rtol=1e-12, atol=1e-15), (t, half[t], want)
+        assert np.allclose(hot[t], hot[nb].mean(axis=0), rtol=1e-12, atol=1e-15)
+        gap = max(gap, abs(am[0] - math.exp(np.log(own[nb, 0]).mean())) / am[0])
+    assert gap > 1e-3  # the neighbours differ enough to tell the two means apart
+
+
 def test_recalibration_number_statistics():
     """S11 number adjustment: each particle of an accepted cell is deleted with
     probability 1 - r or cloned with probability r - 1, r = rho^{k+1}/rho_N
