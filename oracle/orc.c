@@ -186,6 +186,7 @@ struct orc_ctx {
   double* phi_ewma;
   double* phi_win;
   double* phi_cum;
+  double* acc_w;   /* [n] local accumulation: samples the cell's average stands for (0: moving average) */
   int64_t n_ewma, n_win, n_cum;
   /* debug pairs */
   int64_t n_pairs, cap_pairs;
@@ -252,7 +253,7 @@ static void free_mesh(orc_ctx* c) {
   free(c->cl_params);
   free(c->fdtv); free(c->nodes); free(c->tets); free(c->bf); free(c->bflux); free(c->inj_rem); free(c->bcs);
   free(c->bc_sigma); free(c->bc_U); free(c->cstart); free(c->cmax); free(c->rem);
-  free(c->phi_inst); free(c->phi_ewma); free(c->phi_win); free(c->phi_cum);
+  free(c->phi_inst); free(c->phi_ewma); free(c->phi_win); free(c->phi_cum); free(c->acc_w);
 }
 
 void orc_destroy(orc_ctx* c) {
@@ -465,6 +466,7 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
   c->phi_ewma = (double*)calloc(NPHI_MAX * n, sizeof(double));
   c->phi_win = (double*)calloc(NPHI_MAX * n, sizeof(double));
   c->phi_cum = (double*)calloc(NPHI_MAX * n, sizeof(double));
+  c->acc_w = (double*)calloc(n, sizeof(double));
   c->n_ewma = c->n_win = c->n_cum = 0;
   return 0;
 }
@@ -977,7 +979,14 @@ static void sample_cells(orc_ctx* c, int flags) {
        * fewer than n_a samples exist (m <= n_a) the plain mean of all of them */
       double* E = c->phi_ewma + NPHI_MAX * t;
       const double m = (double)(c->n_ewma + 1), na = (double)c->cfg.n_a;
-      const double w = m < na ? m : na;
+      double w = m < na ? m : na;
+      /* a cell in the local accumulation state (Sec. 3.2) keeps every sample:
+       * the running mean of its average so far (worth acc_w samples) and
+       * each new step */
+      if (c->cfg.local_acc && c->acc_w[t] > 0.0) {
+        w = c->acc_w[t] + 1.0;
+        c->acc_w[t] = w;
+      }
       const double a = (w - 1.0) / w, b = 1.0 / w;
       for (int q = 0; q < np; ++q) E[q] = a * E[q] + b * ph[q];
     }
@@ -999,7 +1008,11 @@ int orc_sample(orc_ctx* c, int32_t action) {
   const int64_t m = NPHI_MAX * c->n_tets;
   if (action & ORC_RESET_WINDOW) { memset(c->phi_win, 0, sizeof(double) * m); c->n_win = 0; }
   if (action & ORC_RESET_CUMUL) { memset(c->phi_cum, 0, sizeof(double) * m); c->n_cum = 0; }
-  if (action & ORC_RESET_EWMA) { memset(c->phi_ewma, 0, sizeof(double) * m); c->n_ewma = 0; }
+  if (action & ORC_RESET_EWMA) {
+    memset(c->phi_ewma, 0, sizeof(double) * m);
+    memset(c->acc_w, 0, sizeof(double) * c->n_tets);
+    c->n_ewma = 0;
+  }
   return 0;
 }
 
@@ -1548,6 +1561,15 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
     avail[t] = (uint8_t)ok;
     c->cp_flag[t] = ok ? 1.0 : 0.0;
     if (!ok) (*n_rej)++;
+    /* local accumulation state (Sec. 3.2): a rejected cell stops forgetting;
+     * its moving average so far counts as the min(m, n_a) samples it stands
+     * for.  An accepted cell returns to the moving average. */
+    if (c->cfg.local_acc) {
+      if (ok)
+        c->acc_w[t] = 0.0;
+      else if (c->acc_w[t] == 0.0)
+        c->acc_w[t] = (double)(c->n_ewma < c->cfg.n_a ? c->n_ewma : c->cfg.n_a);
+    }
   }
   *n_learned = c->cfg.closure && c->cl_params ? closure_apply(c, d) : 0;
   /* reconstruction passes: a rejected cell with available face neighbours
@@ -1925,9 +1947,10 @@ int orc_couple(orc_ctx* c, orc_couple_report* rep) {
 
 int orc_read_couple(orc_ctx* c, int32_t which, double* out, int64_t cap) {
   const int64_t n = c->n_tets;
+  if (which < 0 || which > 5) return fail(c, -1, "bad selector");
   const double* src = which == 0 ? c->cp_half : which == 1 ? c->cp_hot : which == 2 ? c->cp_new
-                    : which == 3 ? c->cp_flag : c->cp_own;
-  const int64_t k = which == 1 ? 12 : which == 3 ? 1 : 6;
+                    : which == 3 ? c->cp_flag : which == 4 ? c->cp_own : c->acc_w;
+  const int64_t k = which == 1 ? 12 : which == 3 || which == 5 ? 1 : 6;
   if (!src) return fail(c, -7, "no coupling done");
   if (cap < k * n) return fail(c, -3, "buffer too small");
   memcpy(out, src, sizeof(double) * k * n);

@@ -51,6 +51,8 @@ typedef struct orc_config {
   int64_t capacity; /* particle capacity */
   int32_t closure;  /* 1: the learned closure supplies the HoT of the coupling (S12) */
   int32_t recon;    /* reconstruction mean of density and temperatures: 0 arithmetic, 1 logarithmic */
+  int32_t local_acc;/* 1: rejected cells enter the local accumulation state (Sec. 3.2) */
+  int32_t pad;
 } orc_config;
 
 typedef struct orc_bc {
@@ -104,7 +106,8 @@ typedef struct orc_couple_report {
   int64_t n_cloned, n_deleted;
 } orc_couple_report;
 int orc_couple(orc_ctx* c, orc_couple_report* rep);
-/* which: 0 M^{k+1/2} [n][6], 1 HoT [n][12], 2 M^{k+1} [n][6], 3 flags [n], 4 own sampled state [n][6] */
+/* which: 0 M^{k+1/2} [n][6], 1 HoT [n][12], 2 M^{k+1} [n][6], 3 flags [n], 4 own sampled state [n][6],
+ * 5 local accumulation weight [n] (0: moving average) */
 int orc_read_couple(orc_ctx* c, int32_t which, double* out, int64_t cap);
 int orc_write_moments(orc_ctx* c, int32_t which, const double* in);
 int orc_write_wall_flux(orc_ctx* c, const double* in, int64_t steps);

@@ -30,6 +30,7 @@ class OrcConfig(C.Structure):
         ("L_ref", C.c_double), ("n_a", C.c_int32), ("N_s", C.c_int32), ("N_m", C.c_int32),
         ("passes", C.c_int32), ("eps_m", C.c_double), ("KnD_max", C.c_double), ("capacity", C.c_int64),
         ("closure", C.c_int32), ("recon", C.c_int32),
+        ("local_acc", C.c_int32), ("pad", C.c_int32),
     ]
 
 
@@ -283,7 +284,7 @@ class Oracle:
         return r.as_dict()
 
     def read_couple(self, which):
-        k = {0: 6, 1: 12, 2: 6, 3: 1, 4: 6}[which]
+        k = {0: 6, 1: 12, 2: 6, 3: 1, 4: 6, 5: 1}[which]
         out = np.zeros((self.n_tets, k), np.float64)
         self._check(self.L.orc_read_couple(self.h, which, _p(out), out.size))
         return out

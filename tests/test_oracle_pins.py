@@ -956,6 +956,49 @@ def test_reconstruction_mean_arithmetic_or_logarithmic(recon):
     assert gap > 1e-3  # the neighbours differ enough to tell the two means apart
 
 
+@pytest.mark.parametrize("local_acc", [0, 1])
+def test_local_accumulation_state(local_acc):
+    """Sec. 3.2: a cell rejected by the filter enters a local accumulation state in
+    which its samples are no longer forgotten.  With n_a = 10 and 20 samples
+    before the coupling, a rejected cell's average afterwards is the running
+    mean (10 E_0 + sum of the K new steps)/(10 + K) and its weight 10 + K; an
+    accepted cell keeps the moving average E <- 0.9 E + 0.1 inst; after a
+    coupling that accepts every cell all weights return to 0.  Without the
+    state every cell keeps the moving average."""
+    s = W.cavity_scenario(3, 5000, 0.1, seed=3)
+    o = orc.Oracle(s, N_m=1, KnD_max=1.5, passes=2, n_a=10, local_acc=local_acc)
+    o.init()
+    o.step(20, orc.EWMA)
+    cen = s.mesh.nodes[s.mesh.tets].mean(axis=1)
+    dilute = cen[:, 0] < -0.1e-3
+    o.write_moments(orc.PHI_EWMA, equilibrium_phi(o, s, rho_scale=np.where(dilute, 0.05, 1.0)))
+    o.couple()
+    rej = o.read_couple(3)[:, 0] != 1
+    assert np.array_equal(rej, dilute)
+    w0 = o.read_couple(5)[:, 0]
+    assert np.array_equal(w0, np.where(rej, 10.0, 0.0) if local_acc else np.zeros(len(rej)))
+    E0 = o.moments(orc.PHI_EWMA)
+    K = 15
+    inst = []
+    for _ in range(K):
+        o.step(1, orc.EWMA)
+        inst.append(o.moments(orc.PHI_INST))
+    E = o.moments(orc.PHI_EWMA)
+    run = (10.0 * E0 + np.sum(inst, axis=0)) / (10.0 + K)
+    mov = E0.copy()
+    for ph in inst:
+        mov = 0.9 * mov + 0.1 * ph
+    want = np.where(rej[:, None], run, mov) if local_acc else mov
+    assert np.allclose(E, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    assert np.abs(run - mov)[rej].max() > 1e-3 * np.abs(mov).max()  # the two laws differ here
+    w1 = o.read_couple(5)[:, 0]
+    assert np.array_equal(w1, np.where(rej, 10.0 + K, 0.0) if local_acc else np.zeros(len(rej)))
+    o.write_moments(orc.PHI_EWMA, equilibrium_phi(o, s))
+    o.couple()
+    assert np.all(o.read_couple(3)[:, 0] == 1)
+    assert np.all(o.read_couple(5)[:, 0] == 0.0)
+
+
 def test_recalibration_number_statistics():
     """S11 number adjustment: each particle of an accepted cell is deleted with
     probability 1 - r or cloned with probability r - 1, r = rho^{k+1}/rho_N
