@@ -121,7 +121,10 @@ typedef struct dig_config {
                             (exp of the mean logarithm, the log-mean reconstruction of Sec. 6; the
                             arithmetic mean where a contributing value is not positive); velocity
                             and HoT always arithmetic */
-  int32_t pad;           /* zero */
+  int32_t local_acc;     /* 1: a cell the filter rejects enters the local accumulation state (Sec. 3.2):
+                            its moving average stops forgetting (running mean of every later step,
+                            its average so far counting as min(m, n_a) samples) until a coupling
+                            accepts it; 0: every cell keeps the moving average */
 } dig_config;
 
 typedef struct dig_bc {
@@ -136,7 +139,7 @@ typedef struct dig_ctx dig_ctx;
 
 /* Create a context for one gas and time step.  No GPU work is done.
  * DIG_ERR_ARG unless mass, dt, F_N and alpha are positive, rot_dof is 0 or 2,
- * recon is 0 or 1 and stage_cap <= 8192. */
+ * recon and local_acc are 0 or 1 and stage_cap <= 8192. */
 int dig_create(const dig_config* cfg, dig_ctx** out);
 /* Release the context (the caller then frees its arena). */
 int dig_destroy(dig_ctx* ctx);
@@ -279,7 +282,9 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out);
  * 1 = HoT (sigma xx,yy,zz,xy,xz,yz, q_t(3), q_r(3); k = 12), 2 = M^{k+1}
  * (k = 6), 3 = cell flags (1 accepted, 2 reconstructed, 3 filled beyond the
  * reconstruction layers, 0 none of these; k = 1),
- * 4 = each cell's own sampled state (k = 6) */
+ * 4 = each cell's own sampled state (k = 6), 5 = each cell's local
+ * accumulation weight (samples its moving average stands for in the local
+ * accumulation state, 0 outside it; k = 1, current value) */
 int dig_read_couple(dig_ctx* ctx, int32_t which, double* host_out, int64_t cap);
 /* overwrite summation variables (which = DIG_PHI_*) from host in[n_tets][17] */
 int dig_write_moments(dig_ctx* ctx, int32_t which, const double* host_in);

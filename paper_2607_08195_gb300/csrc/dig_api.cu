@@ -167,6 +167,7 @@ int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (!cfg || !out) return DIG_ERR_ARG;
   if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || !(cfg->alpha > 0) ||
       (cfg->rot_dof != 0 && cfg->rot_dof != 2) || (cfg->recon != 0 && cfg->recon != 1) ||
+      (cfg->local_acc != 0 && cfg->local_acc != 1) ||
       cfg->stage_cap > 8192)
     return DIG_ERR_ARG;
   dig_ctx* c = new dig_ctx();
@@ -520,6 +521,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
   P.phi_ewma = A.take<double>(NPHI * n);
   P.phi_win = A.take<double>(NPHI * n);
   P.phi_cum = A.take<double>(NPHI * n);
+  P.acc_w = A.take<double>(n);
   ctx->mom_out = A.take<double>(NMAC * n);
   P.counters = A.take<unsigned long long>(16);
   P.status = A.take<int>(4);
@@ -653,6 +655,8 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   CK(cudaMemsetAsync(P.rem, 0, n * sizeof(double), s));
   for (double* ph : {P.phi_inst, P.phi_ewma, P.phi_win, P.phi_cum})
     CK(cudaMemsetAsync(ph, 0, NPHI * n * sizeof(double), s));
+  CK(cudaMemsetAsync(P.acc_w, 0, n * sizeof(double), s));
+  P.local_acc = c.local_acc;
   CK(cudaMemsetAsync(P.counters, 0, 16 * sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(P.status, 0, 4 * sizeof(int), s));
   CK(cudaMemsetAsync(P.state, 0, 8 * sizeof(int), s));
@@ -935,6 +939,7 @@ int sample(dig_ctx* ctx, int32_t action) {
   }
   if (action & DIG_RESET_EWMA) {
     CK(cudaMemsetAsync(ctx->P.phi_ewma, 0, m, ctx->stream));
+    CK(cudaMemsetAsync(ctx->P.acc_w, 0, (size_t)ctx->n_tets * sizeof(double), ctx->stream));
     ctx->n_ewma = 0;
   }
   return DIG_OK;
@@ -1194,6 +1199,7 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
   cudaStream_t s = ctx->stream;
   CoupleParams& C = ctx->C;
   C.wall_t = ctx->flux_steps > 0 ? (double)ctx->flux_steps * ctx->cfg.dt : 0.0;
+  C.acc_w0 = (double)std::min<int64_t>(ctx->n_ewma, ctx->cfg.n_a);
   CK(cudaMemsetAsync(C.stats, 0, 5 * sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(C.fillcnt, 0, DIG_FILL_LAYERS * sizeof(int), s));
   CK(cudaMemsetAsync(C.scal, 0, sizeof(CoupleScalars), s));
@@ -1239,11 +1245,12 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
 }
 
 int dig_read_couple(dig_ctx* ctx, int32_t which, double* out, int64_t cap) {
-  if (!ctx || !out || which < 0 || which > 4) return DIG_ERR_ARG;
+  if (!ctx || !out || which < 0 || which > 5) return DIG_ERR_ARG;
   if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "dig_read_couple: no arena");
   const CoupleParams& C = ctx->C;
-  const double* src = which == 0 ? C.half : which == 1 ? C.hot : which == 2 ? C.newst : which == 3 ? C.flag : C.own;
-  const int k = which == 1 ? 12 : which == 3 ? 1 : 6;
+  const double* src = which == 0 ? C.half : which == 1 ? C.hot : which == 2 ? C.newst : which == 3 ? C.flag
+                    : which == 4 ? C.own : ctx->P.acc_w;
+  const int k = which == 1 ? 12 : which == 3 || which == 5 ? 1 : 6;
   const int64_t n = ctx->n_tets;
   if (cap < k * n) return fail(ctx, DIG_ERR_CAPACITY, "dig_read_couple: buffer too small");
   std::vector<double> tmp((size_t)k * n);

@@ -256,6 +256,15 @@ __global__ void k_cp_hot(Params P, CoupleParams C) {
   C.avail[c] = ok ? 1 : 0;
   C.flag[c] = ok ? 1.0 : 0.0;
   if (!ok) atomicAdd(C.stats + 0, 1ull);
+  // local accumulation state (Sec. 3.2): a rejected cell stops forgetting, its
+  // moving average so far counting as the acc_w0 samples it stands for; an
+  // accepted cell returns to the moving average
+  if (P.local_acc) {
+    if (ok)
+      P.acc_w[c] = 0.0;
+    else if (P.acc_w[c] == 0.0)
+      P.acc_w[c] = C.acc_w0;
+  }
 }
 
 // S12 inputs of every cell (see closure_features in dig.h): rho, u(3), T_t,

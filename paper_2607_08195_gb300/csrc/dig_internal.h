@@ -87,6 +87,8 @@ struct Params {
   uint32_t seed_lo, seed_hi;
   float c_vhs, one_m_omega, p_inel, lb_exp, hmr;
   float inv_alpha;          // 1 / alpha of the VSS scattering law (alpha != 1)
+  int local_acc;            // 1: rejected cells accumulate (acc_w)
+  double* acc_w;            // [n] samples a cell's average stands for in the local accumulation state (0: moving average)
   int vss;                  // 1: VSS scattering, 0: VHS (isotropic)
   float T_init, sigma_init, u0[3];
   // per-cell grouping and sort state
@@ -128,6 +130,7 @@ constexpr int DIG_FILL_LAYERS = 64;
 
 struct CoupleParams {
   double L0, T0, rho0, c0, Kn, omega, gam, dr, Zr, mass, FN, kB, KnD_max, wall_t;
+  double acc_w0;       // min(m, n_a): the samples a moving average stands for at this coupling
   double iL2;          // 1 / L0^2
   const double* vnd;   // [n] cell volumes / L0^3
   const double* ivnd;  // [n] L0^3 / cell volumes

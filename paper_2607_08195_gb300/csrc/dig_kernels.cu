@@ -874,16 +874,35 @@ template <bool DIAT, int NT>
 __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass, int sflags, uint32_t step,
                                              double ewa, double ewb, int TC) {
   extern __shared__ __align__(16) int smem_i[];
-  int* s_cs = smem_i;                      // TC + 1 slot starts
+  double* s_ea = (double*)smem_i;          // TC moving-average weights of old value
+  double* s_eb = s_ea + TC;                // and of the new sample
+  int* s_cs = (int*)(s_eb + TC);           // TC + 1 slot starts
   int* s_nst = s_cs + TC + 1;              // TC stayers
   float* s_sum = (float*)(s_nst + TC);     // NPHI x TC cell sums
   const int c0 = blockIdx.x * TC;
   if (c0 >= P.n_cells) return;
   const int nc = min(TC, P.n_cells - c0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = NT / 32;
+  // cells in the local accumulation state (Sec. 3.2) take the running mean:
+  // weights (w-1)/w and 1/w with w = acc_w + 1, acc_w counting the step
+  const bool accw = P.local_acc && (pass & PASS_COLLIDE) && (sflags & S_EWMA);
   for (int i = threadIdx.x; i <= nc; i += NT) {
     s_cs[i] = P.cs[c0 + i];
-    if (i < nc) s_nst[i] = 0;
+    if (i < nc) {
+      s_nst[i] = 0;
+      if (accw) {
+        double a = ewa, b = ewb;
+        const double aw = P.acc_w[c0 + i];
+        if (aw > 0.0) {
+          const double w = aw + 1.0;
+          P.acc_w[c0 + i] = w;
+          a = (w - 1.0) / w;
+          b = 1.0 / w;
+        }
+        s_ea[i] = a;
+        s_eb[i] = b;
+      }
+    }
   }
   __syncthreads();
   Cnt cnt;
@@ -901,7 +920,8 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
       const size_t o = (size_t)q * (size_t)P.n_cells + (size_t)(c0 + lc);
       const double ph = f2d(q == 0 ? (float)(s_cs[lc + 1] - s_cs[lc]) : s_sum[i]);
       if (sflags & S_INST) P.phi_inst[o] = ph;
-      if (sflags & S_EWMA) P.phi_ewma[o] = __fma_rn(ewa, P.phi_ewma[o], ewb * ph);
+      if (sflags & S_EWMA)
+        P.phi_ewma[o] = accw ? __fma_rn(s_ea[lc], P.phi_ewma[o], s_eb[lc] * ph) : __fma_rn(ewa, P.phi_ewma[o], ewb * ph);
       if (sflags & S_WINDOW) P.phi_win[o] += ph;
       if (sflags & S_CUMUL) P.phi_cum[o] += ph;
     }
@@ -992,7 +1012,9 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
   flush_counters(P, cnt);
 }
 
-size_t move_smem(int TC) { return sizeof(int) * (size_t)(2 * TC + 1) + sizeof(float) * (size_t)NPHI * TC; }
+size_t move_smem(int TC) {
+  return sizeof(double) * 2 * (size_t)TC + sizeof(int) * (size_t)(2 * TC + 1) + sizeof(float) * (size_t)NPHI * TC;
+}
 
 // ---------------------------------------------------------------------------
 // face-by-face tracking of the particles the cell pass queued (those whose

@@ -39,7 +39,7 @@ class DigConfig(C.Structure):
         ("L_ref", C.c_double), ("n_a", C.c_int32), ("N_s", C.c_int32), ("N_m", C.c_int32),
         ("passes", C.c_int32), ("eps_m", C.c_double), ("KnD_max", C.c_double), ("capacity", C.c_int64),
         ("wait_timeout_s", C.c_double), ("stage_cap", C.c_int32), ("tile_cells", C.c_int32),
-        ("cta_threads", C.c_int32), ("closure", C.c_int32), ("recon", C.c_int32), ("pad", C.c_int32),
+        ("cta_threads", C.c_int32), ("closure", C.c_int32), ("recon", C.c_int32), ("local_acc", C.c_int32),
     ]
 
 
@@ -287,7 +287,7 @@ class Solver:
         return r.as_dict()
 
     def read_couple(self, which):
-        k = {0: 6, 1: 12, 2: 6, 3: 1, 4: 6}[which]
+        k = {0: 6, 1: 12, 2: 6, 3: 1, 4: 6, 5: 1}[which]
         out = np.zeros((self.n_tets, k), np.float64)
         self._check(self.L.dig_read_couple(self.h, which, _p(out), out.size))
         return out

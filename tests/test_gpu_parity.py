@@ -365,6 +365,47 @@ def test_couple_parity_from_written_state(nh, kn, passes, kmax, gas, recon):
     assert np.allclose(vg, vo, rtol=1e-6, atol=1e-4)
 
 
+def test_local_accumulation_state_parity():
+    """Local accumulation state (Sec. 3.2, local_acc = 1): a coupling that rejects
+    the dilute part of the cavity puts the same cells into the state with the
+    same weight as the oracle; 15 more steps from identical particles (the
+    oracle's, written to both) leave identical weights and moving averages
+    within the FP32-sum tolerance, the rejected cells on the running mean."""
+    s = W.cavity_scenario(3, 5000, 0.1, seed=3)
+    over = dict(N_m=1, KnD_max=1.5, passes=2, n_a=10, local_acc=1)
+    g, o = pair(s, **over)
+    g.init()
+    o.init()
+    g.step(20, dig.EWMA | dig.SYNC)
+    o.step(20, orc.EWMA)
+    vol = o.mesh_info()["vol"]
+    cen = s.mesh.nodes[s.mesh.tets].mean(axis=1)
+    dilute = cen[:, 0] < -0.1e-3
+    kT_m = W.K_B * s.T_init / s.gas.mass
+    N = s.n_init * vol / s.F_N * np.where(dilute, 0.05, 1.0)
+    phi = np.zeros((len(vol), dig.NPHI))
+    phi[:, 0] = N
+    phi[:, 4:7] = (N * kT_m)[:, None]
+    g.write_moments(dig.PHI_EWMA, phi)
+    o.write_moments(orc.PHI_EWMA, phi)
+    g.couple()
+    o.couple()
+    assert np.array_equal(g.read_couple(3), o.read_couple(3))
+    wg, wo = g.read_couple(5), o.read_couple(5)
+    assert np.array_equal(wg, wo)
+    assert np.array_equal(wo[:, 0] > 0, dilute)
+    x, v, Ir, cell = o.read()
+    g.write(x, v, Ir, cell)
+    g.write_moments(dig.PHI_EWMA, o.moments(orc.PHI_EWMA))
+    g.step(15, dig.EWMA | dig.SYNC)
+    o.step(15, orc.EWMA)
+    assert_same_particles(g, o)
+    assert np.array_equal(g.read_couple(5), o.read_couple(5))
+    assert np.all(o.read_couple(5)[dilute, 0] == 25.0)
+    mg, mo = g.moments(dig.PHI_EWMA), o.moments(orc.PHI_EWMA)
+    assert np.all(np.abs(mg - mo) <= 30 * tol_phi(mo, 80))
+
+
 def test_couple_fixed_point_identity_on_gpu():
     """Uniform equilibrium with the exact wall pressure: the GPU coupling leaves
     the state and every particle unchanged (no clones or deletions); every
