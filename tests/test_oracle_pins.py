@@ -999,6 +999,36 @@ def test_local_accumulation_state(local_acc):
     assert np.all(o.read_couple(5)[:, 0] == 0.0)
 
 
+def test_filter_threshold_sweep_nests_rejections():
+    """A sweep of Kn_D,max (the stability study's threshold of Eq. criterion): the
+    cells rejected at a larger threshold are a subset of those rejected at a
+    smaller one, a threshold above every cell's lambda_c/d_c rejects only the
+    cells without a temperature (fewer than two particles on average), and the
+    counts follow lambda_c/d_c computed here from the sampled state."""
+    s = W.cavity_scenario(3, 5000, 0.1, seed=3)
+    cen = s.mesh.nodes[s.mesh.tets].mean(axis=1)
+    scale = np.exp(np.interp(cen[:, 0], [-0.5e-3, 0.5e-3], [math.log(0.03), 0.0]))
+    prev = None
+    for kmax in (0.3, 0.6, 1.2, 2.4, 1e9):
+        o = orc.Oracle(s, N_m=1, KnD_max=kmax, passes=1)
+        o.init()
+        o.write_moments(orc.PHI_EWMA, equilibrium_phi(o, s, rho_scale=scale))
+        r = o.couple()
+        rej = o.read_couple(3)[:, 0] != 1
+        own = o.read_couple(4)
+        vol = o.mesh_info()["vol"] / s.L ** 3
+        dc = 2.0 * np.cbrt(3.0 * vol / (4.0 * math.pi))
+        lam = s.Kn * own[:, 4] ** (s.gas.omega - 0.5) / own[:, 0]
+        nbar = equilibrium_phi(o, s, rho_scale=scale)[:, 0]
+        want = (lam / dc > kmax) | (nbar < 2.0)
+        assert np.array_equal(rej, want), kmax
+        assert r["n_rejected"] == int(want.sum())
+        if prev is not None:
+            assert np.all(rej <= prev)  # nested: rejected now => rejected at the smaller threshold
+        prev = rej
+    assert prev.sum() == int((nbar < 2.0).sum())
+
+
 def test_recalibration_number_statistics():
     """S11 number adjustment: each particle of an accepted cell is deleted with
     probability 1 - r or cloned with probability r - 1, r = rho^{k+1}/rho_N
