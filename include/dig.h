@@ -113,7 +113,8 @@ typedef struct dig_config {
   double wait_timeout_s; /* time limit of host waits (<= 0: 600 s) */
   int32_t stage_cap;     /* particles per CTA the move kernel's tile of cells aims at: tile = 0.75 stage_cap /
                             mean particles per cell (<= 0: 3072; at most 8192) */
-  int32_t tile_cells;    /* cells per CTA of the move kernel (<= 0: chosen from stage_cap and the load) */
+  int32_t tile_cells;    /* cells per CTA of the move kernel, at most 2048 (<= 0: chosen from stage_cap and
+                            the load) */
   int32_t cta_threads;   /* threads per CTA of the move kernel: 64, 128 or 256 (<= 0: 256) */
   int32_t closure;       /* 1: dig_couple takes the HoT from the learned closure (see closure_*) */
   int32_t recon;         /* mean of the neighbour reconstruction (Sec. 3.2, every neighbour with the
@@ -139,7 +140,8 @@ typedef struct dig_ctx dig_ctx;
 
 /* Create a context for one gas and time step.  No GPU work is done.
  * DIG_ERR_ARG unless mass, dt, F_N and alpha are positive, rot_dof is 0 or 2,
- * recon and local_acc are 0 or 1 and stage_cap <= 8192. */
+ * recon and local_acc are 0 or 1, stage_cap <= 8192 and tile_cells <= 2048
+ * (the move kernel's shared memory holds 92 B per cell of its tile). */
 int dig_create(const dig_config* cfg, dig_ctx** out);
 /* Release the context (the caller then frees its arena). */
 int dig_destroy(dig_ctx* ctx);

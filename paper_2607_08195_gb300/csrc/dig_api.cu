@@ -167,7 +167,7 @@ int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (!cfg || !out) return DIG_ERR_ARG;
   if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || !(cfg->alpha > 0) ||
       (cfg->rot_dof != 0 && cfg->rot_dof != 2) || (cfg->recon != 0 && cfg->recon != 1) ||
-      (cfg->local_acc != 0 && cfg->local_acc != 1) ||
+      (cfg->local_acc != 0 && cfg->local_acc != 1) || cfg->tile_cells > 2048 ||
       cfg->stage_cap > 8192)
     return DIG_ERR_ARG;
   dig_ctx* c = new dig_ctx();

@@ -56,6 +56,10 @@ def test_create_rejects_bad_config(lib):
         cfg = dig.make_config(W.config_small())
         cfg.alpha = alpha
         assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == -1, alpha
+    for field, value in (("recon", 2), ("local_acc", -1), ("tile_cells", 4096), ("rot_dof", 1)):
+        cfg = dig.make_config(W.config_small())
+        setattr(cfg, field, value)
+        assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == -1, field
 
 
 def test_mesh_load_host_validation(lib):
