@@ -114,6 +114,8 @@ struct dig_ctx {
   int tile_cells = 0, stage_cap = 3072, cta_threads = 256;
   float cmax0 = 0.0f;
   cudaEvent_t ev = nullptr;
+  cudaGraphExec_t s10_exec = nullptr;  // the synthetic solve as a CUDA graph (see run_s10)
+  long long s10_launches = 0;          // kernels in it
   std::vector<cudaEvent_t> tev;  // event pairs around timed cell passes
   CoupleParams C{};
   std::vector<double> bcU, bcT, bcn;
@@ -185,6 +187,7 @@ int dig_create(const dig_config* cfg, dig_ctx** out) {
 int dig_destroy(dig_ctx* ctx) {
   if (!ctx) return DIG_ERR_ARG;
   if (ctx->ev) cudaEventDestroy(ctx->ev);
+  if (ctx->s10_exec) cudaGraphExecDestroy(ctx->s10_exec);
   for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   delete ctx;
   return DIG_OK;
@@ -595,6 +598,10 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
   if (!ctx || !dptr) return DIG_ERR_ARG;
   if (!ctx->mesh_ok) return fail(ctx, DIG_ERR_STATE, "dig_bind_arena: no mesh loaded");
   if (((uintptr_t)dptr & 255) != 0) return fail(ctx, DIG_ERR_ARG, "arena must be 256-byte aligned");
+  if (ctx->s10_exec) {  // captured with the previous arena's pointers
+    cudaGraphExecDestroy(ctx->s10_exec);
+    ctx->s10_exec = nullptr;
+  }
   int64_t need = 0;
   int rc = dig_arena_bytes(ctx, &need);
   if (rc) return rc;
@@ -1191,6 +1198,41 @@ int dig_load(dig_ctx* ctx, const void* host_in, int64_t size) {
 // ---------------------------------------------------------------------------
 // DIG coupling (Alg. 1, one outer step)
 // ---------------------------------------------------------------------------
+// The synthetic solve (S10) is 3 + 5 N_m launches whose arguments are fixed
+// once the arena is bound (its pointers, the configuration and the mesh
+// constants; no per-coupling field of CoupleParams is read by its kernels).
+// It is captured once, on a private stream, into a CUDA graph and replayed on
+// the context's stream, which takes the per-launch overheads out of its loop.
+// If the capture is refused, the kernels are launched directly.
+static int run_s10(dig_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  if (!ctx->s10_exec) {
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+      const long long before = g_launches;
+      cudaGraph_t gr = nullptr;
+      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        launch_couple_s10(ctx->P, ctx->C, ctx->cfg.N_m, ctx->cfg.eps_m, cs);
+        if (cudaStreamEndCapture(cs, &gr) == cudaSuccess && gr) {
+          if (cudaGraphInstantiate(&ctx->s10_exec, gr, 0) != cudaSuccess) ctx->s10_exec = nullptr;
+          cudaGraphDestroy(gr);
+        }
+      }
+      ctx->s10_launches = g_launches - before;
+      g_launches = before;
+      cudaStreamDestroy(cs);
+    }
+    (void)cudaGetLastError();  // a refused capture leaves its error here
+  }
+  if (ctx->s10_exec) {
+    CK(cudaGraphLaunch(ctx->s10_exec, s));
+    g_launches += ctx->s10_launches;
+  } else {
+    launch_couple_s10(ctx->P, ctx->C, ctx->cfg.N_m, ctx->cfg.eps_m, s);
+  }
+  return DIG_OK;
+}
+
 int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
   if (!ctx || !out) return DIG_ERR_ARG;
   if (!ctx->have_particles) return fail(ctx, DIG_ERR_STATE, "dig_couple: no particles");
@@ -1211,7 +1253,8 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
     launch_mlp_forward(ctx->cl_p, C.feat, ctx->n_tets, C.ypred, s);
   }
   launch_couple_s9(ctx->P, C, ctx->cfg.passes, learned ? C.ypred : nullptr, s);
-  launch_couple_s10(ctx->P, C, ctx->cfg.N_m, ctx->cfg.eps_m, s);
+  int rs = run_s10(ctx);
+  if (rs) return rs;
   CoupleScalars sc{};
   int N = 0;
   CK(cudaMemcpyAsync(&sc, C.scal, sizeof sc, cudaMemcpyDeviceToHost, s));
