@@ -1206,6 +1206,7 @@ int dig_load(dig_ctx* ctx, const void* host_in, int64_t size) {
 // If the capture is refused, the kernels are launched directly.
 static int run_s10(dig_ctx* ctx) {
   cudaStream_t s = ctx->stream;
+  CK(cudaGetLastError());  // a launch error of the steps before, reported before any capture
   if (!ctx->s10_exec) {
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
