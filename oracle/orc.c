@@ -7,14 +7,20 @@
  *
  * Paper: "DIG-augmented DSMC on unstructured meshes" (arXiv 2607.08195).
  *   Sec. 2.1  DSMC: particle state (x, v, I_r; N_eff), move, NTC pair selection,
- *             VSS/VHS cross sections, Borgnakke-Larsen exchange (Eq. inelastic
- *             probability), sampled moments (Eq. dsmc_temperatures).
+ *             VHS cross sections with VHS or VSS scattering, Borgnakke-Larsen
+ *             exchange (Eq. inelastic probability), sampled moments
+ *             (Eq. dsmc_temperatures).
+ *   Sec. 2.2  synthetic equations (Eq. macro, Eq. synthetic_closure) and the
+ *             recalibration of the particles.
  *   Sec. 3.1  exponential moving average of the summation variables
  *             (Eq. exponential_average_moments), steady cumulative average
  *             (Eq. steady_average_moments).
+ *   Sec. 3.2  cell-Knudsen filter (Eq. criterion), equal-weight reconstruction
+ *             (arithmetic, or the logarithmic mean named in Sec. 6) and the
+ *             local accumulation state of rejected cells.
  * Where the paper names a method without giving its steps, the oracle follows
  * the published source named at that function (Bird 1994; Salmon et al. 2011;
- * Marsaglia 1972; Rocchini and Cignoni 2000).
+ * Marsaglia 1972; Rocchini and Cignoni 2000; Koura and Matsumoto 1991).
  */
 #include "orc.h"
 
