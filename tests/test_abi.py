@@ -120,4 +120,7 @@ def test_closure_host_validation(lib):
     tc.epochs, tc.beta1 = 1, 1.0
     assert lib.closure_train(h, ctypes.byref(tc), fake, fake, 10, loss.ctypes.data) == -1
     assert lib.closure_features(h, 7, fake) == -1
+    out = np.zeros(8)
+    assert lib.dig_read_couple(h, 6, out.ctypes.data, 8) == -1  # selectors are 0..5
+    assert lib.dig_read_couple(h, 5, out.ctypes.data, 8) == -7  # no arena bound yet
     assert lib.dig_destroy(h) == 0
