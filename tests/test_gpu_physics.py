@@ -55,3 +55,49 @@ def test_dig_converges_to_the_dsmc_field_where_dsmc_is_resolved():
     rms = float(np.sqrt(np.mean((prof["dig"] - prof["plain"]) ** 2)))
     assert np.abs(prof["plain"]).max() > 0.1  # a developed vortex
     assert rms < 0.02, (rms, prof)
+
+
+def test_vss_stress_relaxation_rate_on_the_gpu():
+    """VSS scattering on the CUDA path at ten times the oracle pin's size: for
+    Maxwell molecules (omega = 1) in a closed specular box, the stress anisotropy
+    decays as exp(-p t / mu), and with the same total cross section VSS with
+    alpha = 3 has 4 alpha/((alpha + 1)(alpha + 2)) = 3/5 of it as viscosity cross
+    section against 2/3 for VHS, so its decay rate is 0.9 times VHS's.  The two
+    runs share the initial state and the time step."""
+    import dataclasses
+    import math
+
+    K_B = W.K_B
+    n = 480_000
+    rates = {}
+    for alpha in (1.0, 3.0):
+        gas = W.Gas(mass=6.63e-26, d_ref=4.17e-10, omega=1.0, T_ref=273.0, alpha=alpha)
+        mesh = W.closed_box(4, L=1e-3, kind=W.BC_SPECULAR, T_w=273.0)
+        n0 = 1.677e22
+        mu_vhs = dataclasses.replace(gas, alpha=1.0).mu_ref()
+        s = W.Scenario(gas=gas, mesh=mesh, n_particles=n, n_init=n0, T_init=273.0, u_init=(0.0, 0.0, 0.0),
+                       F_N=n0 * 1e-9 / n, dt=0.02 * mu_vhs / (n0 * K_B * 273.0), seed=41, L=1e-3, Kn=0.1,
+                       capacity=2 * n)
+        rng = np.random.default_rng(5)
+        x, v, Ir, cell = W.random_particles(rng, s, n)
+        sig = math.sqrt(K_B * 273.0 / gas.mass)
+        v = (rng.standard_normal((n, 3)) * sig * np.array([1.3, 0.8, 0.8])).astype(np.float32)
+        g = dig.Solver(s, "cuda:0")
+        g.write(x, v, Ir, cell)
+
+        def aniso():
+            c = g.read()[1].astype(np.float64)
+            c -= c.mean(0)
+            m2 = (c * c).mean(0)
+            return m2[0] - 0.5 * (m2[1] + m2[2]), m2.sum() / 3
+
+        a0, th = aniso()
+        T = gas.mass * th / K_B
+        p = n0 * K_B * T
+        mu = mu_vhs * (T / gas.T_ref) ** gas.omega
+        steps = 50
+        g.step(steps, dig.SYNC)
+        a, _ = aniso()
+        rates[alpha] = -math.log(a / a0) / (p * steps * s.dt / mu)
+    assert abs(rates[1.0] - 1.0) < 0.05, rates
+    assert abs(rates[3.0] / rates[1.0] - 0.9) < 0.02, rates  # statistical error ~0.007
