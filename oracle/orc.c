@@ -1614,15 +1614,12 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
   free(nxt); free(avail); free(nbar);
 }
 
-/* S10: steady synthetic equations (Eq. macro with the closure
- * sigma = sigma_NSF + HoT, q = q_NSF + HoT) by explicit pseudo-time
- * stepping with one global step (the smallest local step at CFL 0.5, so the
- * transient stays conservative): cell-centred finite volumes, Rusanov
- * inviscid flux with a low-Mach scaling of its velocity dissipation,
+/* S10 discretisation: steady synthetic equations (Eq. macro with the closure
+ * sigma = sigma_NSF + HoT, q = q_NSF + HoT) by cell-centred finite volumes,
+ * Rusanov inviscid flux with a low-Mach scaling of its velocity dissipation,
  * face-averaged stress and heat flux, diffuse walls as isothermal no-slip
  * walls and specular walls as slip walls (see the wall faces below), open
- * faces by the free stream.  Stops after N_m iterations or when the residual
- * L2 norm falls below eps_m times its first value. */
+ * faces by the free stream.  The iteration is solve_synthetic below. */
 static void prim_from_cons(const nd_t* d, const double* U, double* P) {
   const double rho = U[0];
   const double ux = U[1] / rho, uy = U[2] / rho, uz = U[3] / rho;
@@ -1653,186 +1650,330 @@ static void inv_flux(const double* P, const double* U, const double* N, double* 
   F[5] = U[5] * un;
 }
 
-static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_out) {
+/* Residual R(U) = -(1/V) sum_f F_f A_f (+ relaxation source, + src) of every
+ * cell, and its pseudo-time step at CFL 1, dtl = V / sum_f A_f (lambda_f +
+ * 2 nu A_f / V) with the face's largest inviscid wave speed lambda_f;
+ * returns sum_c V_c |R_c|^2 over rho, rho u, rho E.  Work arrays: P [6n] primitives, G [15n] gradients, S [12n] total stress and
+ * heat fluxes. */
+static double residual(orc_ctx* c, const nd_t* d, const double* src, const double* U, double* R, double* dtl,
+                       double* P, double* G, double* S) {
   const int64_t n = c->n_tets;
   const int nv = 6;
-  double* U = (double*)malloc(sizeof(double) * nv * n);
-  double* P = (double*)calloc(6 * n, sizeof(double));
-  double* R = (double*)malloc(sizeof(double) * nv * n);
-  double* G = (double*)malloc(sizeof(double) * 15 * n);
-  double* S = (double*)malloc(sizeof(double) * 12 * n); /* total stress and heat fluxes per cell */
-  double* dtl = (double*)malloc(sizeof(double) * n);
-  for (int64_t t = 0; t < n; ++t) cons_from_prim(d, c->cp_half + 6 * t, U + nv * t);
   const double L2 = d->L0 * d->L0, L3 = L2 * d->L0;
-  double res0 = 0.0, res = 0.0;
-  int it = 0;
-  for (it = 0; it < c->cfg.N_m; ++it) {
-    for (int64_t t = 0; t < n; ++t) prim_from_cons(d, U + nv * t, P + 6 * t);
-    gradients(c, d, P, G);
-    for (int64_t t = 0; t < n; ++t) {
-      double sig[6], qt[3], qr[3];
-      nsf(d, P + 6 * t, G + 15 * t, sig, qt, qr);
-      const double* H = c->cp_hot + 12 * t;
-      for (int q = 0; q < 6; ++q) S[12 * t + q] = sig[q] + H[q];
-      for (int q = 0; q < 3; ++q) {
-        S[12 * t + 6 + q] = qt[q] + H[6 + q];
-        S[12 * t + 9 + q] = qr[q] + H[9 + q];
-      }
+  for (int64_t t = 0; t < n; ++t) prim_from_cons(d, U + nv * t, P + 6 * t);
+  gradients(c, d, P, G);
+  for (int64_t t = 0; t < n; ++t) {
+    double sig[6], qt[3], qr[3];
+    nsf(d, P + 6 * t, G + 15 * t, sig, qt, qr);
+    const double* H = c->cp_hot + 12 * t;
+    for (int q = 0; q < 6; ++q) S[12 * t + q] = sig[q] + H[q];
+    for (int q = 0; q < 3; ++q) {
+      S[12 * t + 6 + q] = qt[q] + H[6 + q];
+      S[12 * t + 9 + q] = qr[q] + H[9 + q];
     }
-    double rsum = 0.0;
-    for (int64_t t = 0; t < n; ++t) {
-      const double* Pc = P + 6 * t;
-      const double* Uc = U + nv * t;
-      const double V = c->vol[t] / L3;
-      double acc[6] = {0, 0, 0, 0, 0, 0};
-      double lam_sum = 0.0;
-      const double cc = sqrt(d->gam * Pc[4]);
-      const double nu = 2.5 * mu_nd(d, Pc[4]) / Pc[0];
-      for (int f = 0; f < 4; ++f) {
-        const double* N = c->pn + 12 * t + 3 * f;
-        const double A = c->parea[4 * t + f] / L2;
-        const int32_t nb = c->nbr[4 * t + f];
-        double F[6];
-        if (nb >= 0 || c->bcs[c->bf[-1 - nb].bc].kind >= 2) {
-          double Pn[6], Un[6];
-          if (nb >= 0) {
-            memcpy(Pn, P + 6 * (int64_t)nb, sizeof Pn);
-            memcpy(Un, U + nv * (int64_t)nb, sizeof Un);
-          } else {
-            const orc_bc* b = c->bcs + c->bf[-1 - nb].bc;
-            Pn[0] = b->kind == 2 ? b->n * c->cfg.mass / d->rho0 : Pc[0];
-            Pn[1] = b->U[0] / d->c0; Pn[2] = b->U[1] / d->c0; Pn[3] = b->U[2] / d->c0;
-            Pn[4] = b->T / d->T0; Pn[5] = Pn[4];
-            if (b->kind == 3) memcpy(Pn, Pc, sizeof Pn);
-            cons_from_prim(d, Pn, Un);
-          }
-          double FL[6], FR[6];
-          inv_flux(Pc, Uc, N, FL);
-          inv_flux(Pn, Un, N, FR);
-          const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
-          const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
-          const double cl = sqrt(d->gam * Pc[4]), cr = sqrt(d->gam * (Pn[4] > 0 ? Pn[4] : 1e-12));
-          const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
-          if (nb >= 0) {
-            /* interior face: the dissipation acts on states whose velocity
-             * jump is scaled by z = min(1, max(M_L, M_R)) (low-Mach correction
-             * of Thornber et al. 2008) and whose density jump keeps its
-             * acoustic part dp / c^2 and scales its entropy part
-             * drho - dp / c^2 by z (c^2 = gamma T of the face mean), with
-             * the pressures unchanged: at low Mach the dissipation of shear
-             * and entropy waves scales with the flow speed instead of the
-             * sound speed */
-            const double ml = sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cl;
-            const double mr = sqrt(Pn[1] * Pn[1] + Pn[2] * Pn[2] + Pn[3] * Pn[3]) / cr;
-            const double z = fmin(1.0, fmax(ml, mr));
-            double PL[6], PR[6], UL[6], UR[6];
-            memcpy(PL, Pc, sizeof PL);
-            memcpy(PR, Pn, sizeof PR);
-            for (int i = 1; i <= 3; ++i) {
-              const double m = 0.5 * (Pc[i] + Pn[i]), h = 0.5 * z * (Pc[i] - Pn[i]);
-              PL[i] = m + h;
-              PR[i] = m - h;
-            }
-            const double pl = Pc[0] * Pc[4], pr = Pn[0] * Pn[4];
-            const double c2 = d->gam * 0.5 * (Pc[4] + Pn[4]);
-            const double dpc = (pl - pr) / c2;
-            const double drho = dpc + z * ((Pc[0] - Pn[0]) - dpc);
-            const double rm = 0.5 * (Pc[0] + Pn[0]);
-            PL[0] = rm + 0.5 * drho;
-            PR[0] = rm - 0.5 * drho;
-            PL[4] = pl / PL[0];
-            PR[4] = pr / PR[0];
-            cons_from_prim(d, PL, UL);
-            cons_from_prim(d, PR, UR);
-            for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);
-          } else {
-            for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
-          }
-          if (nb >= 0) {
-            const double* Sc = S + 12 * t;
-            const double* Sn = S + 12 * (int64_t)nb;
-            double sf[6], qtf[3], qrf[3], uf[3];
-            for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (Sc[q] + Sn[q]);
-            for (int q = 0; q < 3; ++q) {
-              qtf[q] = 0.5 * (Sc[6 + q] + Sn[6 + q]);
-              qrf[q] = 0.5 * (Sc[9 + q] + Sn[9 + q]);
-              uf[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
-            }
-            /* sigma . n with sigma = [[xx,xy,xz],[xy,yy,yz],[xz,yz,zz]] */
-            const double sn0 = sf[0] * N[0] + sf[3] * N[1] + sf[4] * N[2];
-            const double sn1 = sf[3] * N[0] + sf[1] * N[1] + sf[5] * N[2];
-            const double sn2 = sf[4] * N[0] + sf[5] * N[1] + sf[2] * N[2];
-            F[1] += sn0; F[2] += sn1; F[3] += sn2;
-            F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + (qtf[0] + qrf[0]) * N[0] + (qtf[1] + qrf[1]) * N[1] +
-                    (qtf[2] + qrf[2]) * N[2];
-            F[5] += qrf[0] * N[0] + qrf[1] * N[1] + qrf[2] * N[2];
-          }
-          lam_sum += A * (lm + 2.0 * nu * A / V);
+  }
+  double rsum = 0.0;
+  for (int64_t t = 0; t < n; ++t) {
+    const double* Pc = P + 6 * t;
+    const double* Uc = U + nv * t;
+    const double V = c->vol[t] / L3;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double lam_sum = 0.0;
+    const double cc = sqrt(d->gam * Pc[4]);
+    const double nu = 2.5 * mu_nd(d, Pc[4]) / Pc[0];
+    for (int f = 0; f < 4; ++f) {
+      const double* N = c->pn + 12 * t + 3 * f;
+      const double A = c->parea[4 * t + f] / L2;
+      const int32_t nb = c->nbr[4 * t + f];
+      double F[6];
+      if (nb >= 0 || c->bcs[c->bf[-1 - nb].bc].kind >= 2) {
+        double Pn[6], Un[6];
+        if (nb >= 0) {
+          memcpy(Pn, P + 6 * (int64_t)nb, sizeof Pn);
+          memcpy(Un, U + nv * (int64_t)nb, sizeof Un);
         } else {
-          /* wall: no mass flux.  A diffuse wall closes the equations as an
-           * isothermal no-slip wall: the cell's pressure and total stress
-           * (NSF from gradients that take the wall velocity and temperature
-           * at the face, plus the cell's HoT) plus the numerical friction
-           * below, the work of both at the wall velocity and the cell's heat
-           * fluxes.  A specular wall carries the cell's pressure only. */
-          const int32_t ib = -1 - nb;
-          const orc_bc* bw = c->bcs + c->bf[ib].bc;
-          const double p = Pc[0] * Pc[4];
-          F[0] = 0.0;
-          if (bw->kind == 0) {
-            const double* Sc = S + 12 * t;
-            const double Uw[3] = {bw->U[0] / d->c0, bw->U[1] / d->c0, bw->U[2] / d->c0};
-            const double sn0 = Sc[0] * N[0] + Sc[3] * N[1] + Sc[4] * N[2];
-            const double sn1 = Sc[3] * N[0] + Sc[1] * N[1] + Sc[5] * N[2];
-            const double sn2 = Sc[4] * N[0] + Sc[5] * N[1] + Sc[2] * N[2];
-            /* the interior faces' dissipation against the mirrored ghost
-             * state (velocity 2 U_w - u): a friction lambda z rho (U_w - u),
-             * lambda = |u.n| + c, z = min(1, max(|u|/c, |U_w|/c)), whose work
-             * is done at the wall velocity */
-            const double z = fmin(1.0, fmax(sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cc,
-                                            sqrt(Uw[0] * Uw[0] + Uw[1] * Uw[1] + Uw[2] * Uw[2]) / cc));
-            const double kw = (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc) * z * Pc[0];
-            double fw[3];
-            for (int i = 0; i < 3; ++i) fw[i] = -kw * (Uw[i] - Pc[1 + i]);
-            F[1] = p * N[0] + sn0 + fw[0];
-            F[2] = p * N[1] + sn1 + fw[1];
-            F[3] = p * N[2] + sn2 + fw[2];
-            F[4] = (sn0 + fw[0]) * Uw[0] + (sn1 + fw[1]) * Uw[1] + (sn2 + fw[2]) * Uw[2] + (Sc[6] + Sc[9]) * N[0] +
-                   (Sc[7] + Sc[10]) * N[1] + (Sc[8] + Sc[11]) * N[2];
-            F[5] = Sc[9] * N[0] + Sc[10] * N[1] + Sc[11] * N[2];
-          } else {
-            for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
-            F[4] = 0.0;
-            F[5] = 0.0;
-          }
-          /* wave speed of the wall face: |u.n| + c, as for the interior faces */
-          lam_sum += A * (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc + 2.0 * nu * A / V);
+          const orc_bc* b = c->bcs + c->bf[-1 - nb].bc;
+          Pn[0] = b->kind == 2 ? b->n * c->cfg.mass / d->rho0 : Pc[0];
+          Pn[1] = b->U[0] / d->c0; Pn[2] = b->U[1] / d->c0; Pn[3] = b->U[2] / d->c0;
+          Pn[4] = b->T / d->T0; Pn[5] = Pn[4];
+          if (b->kind == 3) memcpy(Pn, Pc, sizeof Pn);
+          cons_from_prim(d, Pn, Un);
         }
-        for (int q = 0; q < 6; ++q) acc[q] += F[q] * A;
-      }
-      double* Rc = R + nv * t;
-      for (int q = 0; q < 6; ++q) Rc[q] = -acc[q] / V;
-      if (d->dr > 0) {
-        /* rotational relaxation source (Eq. macro, last line) */
-        const double T = (3.0 * Pc[4] + d->dr * Pc[5]) / (3.0 + d->dr);
-        const double tau = mu_nd(d, Pc[4]) / (Pc[0] * Pc[4]);
-        Rc[5] += 0.5 * d->dr * Pc[0] * (T - Pc[5]) / (d->Zr * tau);
+        double FL[6], FR[6];
+        inv_flux(Pc, Uc, N, FL);
+        inv_flux(Pn, Un, N, FR);
+        const double unl = Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2];
+        const double unr = Pn[1] * N[0] + Pn[2] * N[1] + Pn[3] * N[2];
+        const double cl = sqrt(d->gam * Pc[4]), cr = sqrt(d->gam * (Pn[4] > 0 ? Pn[4] : 1e-12));
+        const double lm = fmax(fabs(unl) + cl, fabs(unr) + cr);
+        if (nb >= 0) {
+          /* interior face: the dissipation acts on states whose velocity
+           * jump is scaled by z = min(1, max(M_L, M_R)) (low-Mach correction
+           * of Thornber et al. 2008) and whose density jump keeps its
+           * acoustic part dp / c^2 and scales its entropy part
+           * drho - dp / c^2 by z (c^2 = gamma T of the face mean), with
+           * the pressures unchanged: at low Mach the dissipation of shear
+           * and entropy waves scales with the flow speed instead of the
+           * sound speed */
+          const double ml = sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cl;
+          const double mr = sqrt(Pn[1] * Pn[1] + Pn[2] * Pn[2] + Pn[3] * Pn[3]) / cr;
+          const double z = fmin(1.0, fmax(ml, mr));
+          double PL[6], PR[6], UL[6], UR[6];
+          memcpy(PL, Pc, sizeof PL);
+          memcpy(PR, Pn, sizeof PR);
+          for (int i = 1; i <= 3; ++i) {
+            const double m = 0.5 * (Pc[i] + Pn[i]), h = 0.5 * z * (Pc[i] - Pn[i]);
+            PL[i] = m + h;
+            PR[i] = m - h;
+          }
+          const double pl = Pc[0] * Pc[4], pr = Pn[0] * Pn[4];
+          const double c2 = d->gam * 0.5 * (Pc[4] + Pn[4]);
+          const double dpc = (pl - pr) / c2;
+          const double drho = dpc + z * ((Pc[0] - Pn[0]) - dpc);
+          const double rm = 0.5 * (Pc[0] + Pn[0]);
+          PL[0] = rm + 0.5 * drho;
+          PR[0] = rm - 0.5 * drho;
+          PL[4] = pl / PL[0];
+          PR[4] = pr / PR[0];
+          cons_from_prim(d, PL, UL);
+          cons_from_prim(d, PR, UR);
+          for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (UR[q] - UL[q]);
+        } else {
+          for (int q = 0; q < 6; ++q) F[q] = 0.5 * (FL[q] + FR[q]) - 0.5 * lm * (Un[q] - Uc[q]);
+        }
+        if (nb >= 0) {
+          const double* Sc = S + 12 * t;
+          const double* Sn = S + 12 * (int64_t)nb;
+          double sf[6], qtf[3], qrf[3], uf[3];
+          for (int q = 0; q < 6; ++q) sf[q] = 0.5 * (Sc[q] + Sn[q]);
+          for (int q = 0; q < 3; ++q) {
+            qtf[q] = 0.5 * (Sc[6 + q] + Sn[6 + q]);
+            qrf[q] = 0.5 * (Sc[9 + q] + Sn[9 + q]);
+            uf[q] = 0.5 * (Pc[1 + q] + Pn[1 + q]);
+          }
+          /* sigma . n with sigma = [[xx,xy,xz],[xy,yy,yz],[xz,yz,zz]] */
+          const double sn0 = sf[0] * N[0] + sf[3] * N[1] + sf[4] * N[2];
+          const double sn1 = sf[3] * N[0] + sf[1] * N[1] + sf[5] * N[2];
+          const double sn2 = sf[4] * N[0] + sf[5] * N[1] + sf[2] * N[2];
+          F[1] += sn0; F[2] += sn1; F[3] += sn2;
+          F[4] += sn0 * uf[0] + sn1 * uf[1] + sn2 * uf[2] + (qtf[0] + qrf[0]) * N[0] + (qtf[1] + qrf[1]) * N[1] +
+                  (qtf[2] + qrf[2]) * N[2];
+          F[5] += qrf[0] * N[0] + qrf[1] * N[1] + qrf[2] * N[2];
+        }
+        lam_sum += A * (lm + 2.0 * nu * A / V);
       } else {
-        Rc[5] = 0.0;
+        /* wall: no mass flux.  A diffuse wall closes the equations as an
+         * isothermal no-slip wall: the cell's pressure and total stress
+         * (NSF from gradients that take the wall velocity and temperature
+         * at the face, plus the cell's HoT) plus the numerical friction
+         * below, the work of both at the wall velocity and the cell's heat
+         * fluxes.  A specular wall carries the cell's pressure only. */
+        const int32_t ib = -1 - nb;
+        const orc_bc* bw = c->bcs + c->bf[ib].bc;
+        const double p = Pc[0] * Pc[4];
+        F[0] = 0.0;
+        if (bw->kind == 0) {
+          const double* Sc = S + 12 * t;
+          const double Uw[3] = {bw->U[0] / d->c0, bw->U[1] / d->c0, bw->U[2] / d->c0};
+          const double sn0 = Sc[0] * N[0] + Sc[3] * N[1] + Sc[4] * N[2];
+          const double sn1 = Sc[3] * N[0] + Sc[1] * N[1] + Sc[5] * N[2];
+          const double sn2 = Sc[4] * N[0] + Sc[5] * N[1] + Sc[2] * N[2];
+          /* the interior faces' dissipation against the mirrored ghost
+           * state (velocity 2 U_w - u): a friction lambda z rho (U_w - u),
+           * lambda = |u.n| + c, z = min(1, max(|u|/c, |U_w|/c)), whose work
+           * is done at the wall velocity */
+          const double z = fmin(1.0, fmax(sqrt(Pc[1] * Pc[1] + Pc[2] * Pc[2] + Pc[3] * Pc[3]) / cc,
+                                          sqrt(Uw[0] * Uw[0] + Uw[1] * Uw[1] + Uw[2] * Uw[2]) / cc));
+          const double kw = (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc) * z * Pc[0];
+          double fw[3];
+          for (int i = 0; i < 3; ++i) fw[i] = -kw * (Uw[i] - Pc[1 + i]);
+          F[1] = p * N[0] + sn0 + fw[0];
+          F[2] = p * N[1] + sn1 + fw[1];
+          F[3] = p * N[2] + sn2 + fw[2];
+          F[4] = (sn0 + fw[0]) * Uw[0] + (sn1 + fw[1]) * Uw[1] + (sn2 + fw[2]) * Uw[2] + (Sc[6] + Sc[9]) * N[0] +
+                 (Sc[7] + Sc[10]) * N[1] + (Sc[8] + Sc[11]) * N[2];
+          F[5] = Sc[9] * N[0] + Sc[10] * N[1] + Sc[11] * N[2];
+        } else {
+          for (int i = 0; i < 3; ++i) F[1 + i] = p * N[i];
+          F[4] = 0.0;
+          F[5] = 0.0;
+        }
+        /* wave speed of the wall face: |u.n| + c, as for the interior faces */
+        lam_sum += A * (fabs(Pc[1] * N[0] + Pc[2] * N[1] + Pc[3] * N[2]) + cc + 2.0 * nu * A / V);
       }
-      dtl[t] = 0.5 * V / lam_sum;
-      for (int q = 0; q < 5; ++q) rsum += V * Rc[q] * Rc[q];
+      for (int q = 0; q < 6; ++q) acc[q] += F[q] * A;
     }
-    res = sqrt(rsum);
+    double* Rc = R + nv * t;
+    for (int q = 0; q < 6; ++q) Rc[q] = -acc[q] / V;
+    if (d->dr > 0) {
+      /* rotational relaxation source (Eq. macro, last line) */
+      const double T = (3.0 * Pc[4] + d->dr * Pc[5]) / (3.0 + d->dr);
+      const double tau = mu_nd(d, Pc[4]) / (Pc[0] * Pc[4]);
+      Rc[5] += 0.5 * d->dr * Pc[0] * (T - Pc[5]) / (d->Zr * tau);
+    } else {
+      Rc[5] = 0.0;
+    }
+    /* a given volume source (the manufactured-solution pin only) */
+    if (src)
+      for (int q = 0; q < 6; ++q) Rc[q] += src[6 * t + q];
+    dtl[t] = V / lam_sum;
+    for (int q = 0; q < 5; ++q) rsum += V * Rc[q] * Rc[q];
+  }
+  return rsum;
+}
+
+/* Inner product of two state vectors [n][6] weighted by the cell volumes
+ * (nondimensional), summed cell by cell in index order. */
+static double wdot(const double* a, const double* b, const double* w, int64_t n) {
+  double s = 0.0;
+  for (int64_t t = 0; t < n; ++t) {
+    double r = 0.0;
+    for (int q = 0; q < 6; ++q) r += a[6 * t + q] * b[6 * t + q];
+    s += w[t] * r;
+  }
+  return s;
+}
+
+/* The coefficients gamma minimising |f - dF gamma| (volume-weighted norm)
+ * over the k stored columns, in age order (oldest first): normal equations
+ * of the columns scaled to unit norm, with 1e-10 added to the diagonal, by
+ * Cholesky.  Returns 0 if the factorisation fails (then no column is used). */
+static int aa_coefficients(const double* dF, const int* slot, int k, int64_t len, const double* f, const double* w,
+                           int64_t n, double* gam) {
+  double H[ORC_AA_MAX][ORC_AA_MAX], b[ORC_AA_MAX], sc[ORC_AA_MAX], y[ORC_AA_MAX];
+  for (int i = 0; i < k; ++i) {
+    for (int j = 0; j <= i; ++j) H[i][j] = H[j][i] = wdot(dF + len * slot[i], dF + len * slot[j], w, n);
+    b[i] = wdot(dF + len * slot[i], f, w, n);
+  }
+  for (int i = 0; i < k; ++i) sc[i] = H[i][i] > 0 ? 1.0 / sqrt(H[i][i]) : 0.0;
+  for (int i = 0; i < k; ++i) {
+    for (int j = 0; j < k; ++j) H[i][j] *= sc[i] * sc[j];
+    H[i][i] += 1e-10;
+    b[i] *= sc[i];
+  }
+  for (int j = 0; j < k; ++j) {
+    double d = H[j][j];
+    for (int q = 0; q < j; ++q) d -= H[j][q] * H[j][q];
+    if (!(d > 0)) return 0;
+    H[j][j] = sqrt(d);
+    for (int i = j + 1; i < k; ++i) {
+      double e = H[i][j];
+      for (int q = 0; q < j; ++q) e -= H[i][q] * H[j][q];
+      H[i][j] = e / H[j][j];
+    }
+  }
+  for (int i = 0; i < k; ++i) {
+    double e = b[i];
+    for (int q = 0; q < i; ++q) e -= H[i][q] * y[q];
+    y[i] = e / H[i][i];
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double e = y[i];
+    for (int q = i + 1; q < k; ++q) e -= H[q][i] * gam[q];
+    gam[i] = e / H[i][i];
+  }
+  for (int i = 0; i < k; ++i) gam[i] *= sc[i];
+  return 1;
+}
+
+/* S10: the steady synthetic equations (Eq. macro with the closure of Eq.
+ * synthetic_closure) solved by pseudo-time iteration.  The base step is the
+ * forward-Euler step of each cell's own pseudo-time step (CFL cfg.cfl of its
+ * inviscid and viscous wave speeds), g(U) = U + cfl dtl R(U); without open
+ * boundaries it is followed by a scaling of every conserved variable that
+ * restores the initial total mass (local steps do not conserve it, and the
+ * steady equations of a closed domain leave it free).  Anderson acceleration
+ * of depth m = cfg.aa_m (Walker & Ni, SIAM J. Numer. Anal. 49, 2011) combines
+ * the last m steps: U <- g(U_k) - dG gamma, gamma minimising
+ * |f_k - dF gamma| with f = g(U) - U and dF, dG the differences of
+ * consecutive f and g(U).  A combined state with a non-positive density or
+ * temperature in some cell is replaced by g(U_k), and the history is
+ * cleared.  Stops after N_m iterations or when the residual norm falls to
+ * eps_m times its first value. */
+static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* iters, double* res_out) {
+  const int64_t n = c->n_tets;
+  const int nv = 6;
+  const int64_t len = nv * n;
+  const int m = c->cfg.aa_m < 0 ? 0 : c->cfg.aa_m > ORC_AA_MAX ? ORC_AA_MAX : c->cfg.aa_m;
+  const double cfl = c->cfg.cfl > 0 ? c->cfg.cfl : 1.5;
+  double* U = (double*)malloc(sizeof(double) * len);
+  double* P = (double*)calloc(6 * n, sizeof(double));
+  double* R = (double*)malloc(sizeof(double) * len);
+  double* G = (double*)malloc(sizeof(double) * 15 * n);
+  double* S = (double*)malloc(sizeof(double) * 12 * n);
+  double* dtl = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* Gx = (double*)malloc(sizeof(double) * len);
+  double* f = (double*)malloc(sizeof(double) * len);
+  double* fp = (double*)malloc(sizeof(double) * len);
+  double* Gp = (double*)malloc(sizeof(double) * len);
+  double* dF = (double*)malloc(sizeof(double) * len * (m > 0 ? m : 1));
+  double* dG = (double*)malloc(sizeof(double) * len * (m > 0 ? m : 1));
+  const double L3 = d->L0 * d->L0 * d->L0;
+  int closed = 1;
+  for (int32_t i = 0; i < c->n_bf; ++i)
+    if (c->bcs[c->bf[i].bc].kind >= 2) closed = 0;
+  double M0 = 0.0;
+  for (int64_t t = 0; t < n; ++t) {
+    cons_from_prim(d, c->cp_half + 6 * t, U + nv * t);
+    w[t] = c->vol[t] / L3;
+    M0 += w[t] * U[nv * t];
+  }
+  double res0 = 0.0, res = 0.0;
+  int it = 0, nh = 0, head = 0;
+  for (it = 0; it < c->cfg.N_m; ++it) {
+    res = sqrt(residual(c, d, src, U, R, dtl, P, G, S));
     if (it == 0) res0 = res > 0 ? res : 1.0;
     if (!isfinite(res)) break;
     if (res <= c->cfg.eps_m * res0) break;
-    /* one global pseudo-time step (the smallest local stable step) keeps the
-     * transient conservative */
-    double dtg = dtl[0];
-    for (int64_t t = 1; t < n; ++t) dtg = dtl[t] < dtg ? dtl[t] : dtg;
-    for (int64_t t = 0; t < n; ++t)
-      for (int q = 0; q < nv; ++q) U[nv * t + q] += dtg * R[nv * t + q];
+    /* base step */
+    for (int64_t t = 0; t < n; ++t) {
+      const double dt = cfl * dtl[t];
+      for (int q = 0; q < nv; ++q) Gx[nv * t + q] = U[nv * t + q] + dt * R[nv * t + q];
+    }
+    if (closed) {
+      double Mx = 0.0;
+      for (int64_t t = 0; t < n; ++t) Mx += w[t] * Gx[nv * t];
+      const double sc = M0 / Mx;
+      for (int64_t i = 0; i < len; ++i) Gx[i] *= sc;
+    }
+    if (m == 0) {
+      memcpy(U, Gx, sizeof(double) * len);
+      continue;
+    }
+    /* acceleration */
+    for (int64_t i = 0; i < len; ++i) f[i] = Gx[i] - U[i];
+    if (it > 0) {
+      double* a = dF + len * head;
+      double* b = dG + len * head;
+      for (int64_t i = 0; i < len; ++i) {
+        a[i] = f[i] - fp[i];
+        b[i] = Gx[i] - Gp[i];
+      }
+      head = (head + 1) % m;
+      if (nh < m) nh++;
+    }
+    memcpy(fp, f, sizeof(double) * len);
+    memcpy(Gp, Gx, sizeof(double) * len);
+    int slot[ORC_AA_MAX];
+    double gam[ORC_AA_MAX];
+    for (int i = 0; i < nh; ++i) slot[i] = ((head - nh + i) % m + m) % m;
+    const int k = nh > 0 && aa_coefficients(dF, slot, nh, len, f, w, n, gam) ? nh : 0;
+    int pos = 1;
+    for (int64_t t = 0; t < n; ++t) {
+      for (int q = 0; q < nv; ++q) {
+        double x = Gx[nv * t + q];
+        for (int j = 0; j < k; ++j) x -= gam[j] * dG[len * slot[j] + nv * t + q];
+        U[nv * t + q] = x;
+      }
+      double Pp[6];
+      prim_from_cons(d, U + nv * t, Pp);
+      if (!(Pp[0] > 0 && Pp[4] > 0)) pos = 0;
+    }
+    if (!pos) {
+      memcpy(U, Gx, sizeof(double) * len);
+      nh = 0;
+    }
   }
   int ok = isfinite(res);
   for (int64_t t = 0; t < n && ok; ++t) {
@@ -1841,7 +1982,8 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, int* iters, double* res_ou
   }
   *iters = it;
   *res_out = res / res0;
-  free(U); free(P); free(R); free(G); free(S); free(dtl);
+  free(U); free(P); free(R); free(G); free(S); free(dtl); free(w); free(Gx); free(f); free(fp); free(Gp);
+  free(dF); free(dG);
   return ok ? 0 : -5;
 }
 
@@ -1942,12 +2084,51 @@ int orc_couple(orc_ctx* c, orc_couple_report* rep) {
   int64_t n_learned = 0;
   extract_hot(c, &d, &rep->n_rejected, &rep->n_reconstructed, &n_learned);
   rep->n_learned = (int32_t)n_learned;
-  int rc = solve_synthetic(c, &d, &rep->iters, &rep->residual);
+  int rc = solve_synthetic(c, &d, NULL, &rep->iters, &rep->residual);
   /* the k-th coupling (k = 0, 1, ...) keys its random stream with sub = k */
   if (rc == 0) recalibrate(c, &d, &rep->n_cloned, &rep->n_deleted);
   c->n_couple++;
   memset(c->bflux, 0, sizeof(double) * 5 * (c->n_bf > 0 ? c->n_bf : 1));
   c->flux_steps = 0;
+  return rc == 0 ? 0 : fail(c, -5, "synthetic solve failed (non-finite or non-positive state)");
+}
+
+/* Harness exports for the pins of the synthetic equations (Sec. 2.2): the
+ * least-squares gradients, the NSF relations and the solve itself, each run
+ * on a state the caller gives (nondimensional, rows per cell). */
+int orc_gradients(orc_ctx* c, const double* prim, double* grad) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  const nd_t d = nondim(c);
+  gradients(c, &d, prim, grad);
+  return 0;
+}
+
+int orc_nsf(orc_ctx* c, const double* prim, const double* grad, double* out) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  const nd_t d = nondim(c);
+  for (int64_t t = 0; t < c->n_tets; ++t) nsf(&d, prim + 6 * t, grad + 15 * t, out + 12 * t, out + 12 * t + 6,
+                                               out + 12 * t + 9);
+  return 0;
+}
+
+int orc_synthetic_solve(orc_ctx* c, const double* half, const double* hot, const double* src, double* out,
+                        int32_t* iters, double* res) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  const int64_t n = c->n_tets;
+  if (!c->cp_half) {
+    c->cp_half = (double*)calloc(6 * n, sizeof(double));
+    c->cp_hot = (double*)calloc(12 * n, sizeof(double));
+    c->cp_new = (double*)calloc(6 * n, sizeof(double));
+    c->cp_own = (double*)calloc(6 * n, sizeof(double));
+    c->cp_flag = (double*)calloc(n, sizeof(double));
+  }
+  memcpy(c->cp_half, half, sizeof(double) * 6 * n);
+  memcpy(c->cp_hot, hot, sizeof(double) * 12 * n);
+  const nd_t d = nondim(c);
+  int it = 0;
+  const int rc = solve_synthetic(c, &d, src, &it, res);
+  *iters = it;
+  memcpy(out, c->cp_new, sizeof(double) * 6 * n);
   return rc == 0 ? 0 : fail(c, -5, "synthetic solve failed (non-finite or non-positive state)");
 }
 

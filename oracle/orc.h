@@ -52,8 +52,12 @@ typedef struct orc_config {
   int32_t closure;  /* 1: the learned closure supplies the HoT of the coupling (S12) */
   int32_t recon;    /* reconstruction mean of density and temperatures: 0 arithmetic, 1 logarithmic */
   int32_t local_acc;/* 1: rejected cells enter the local accumulation state (Sec. 3.2) */
-  int32_t pad;
+  int32_t aa_m;     /* depth of the Anderson acceleration of the synthetic solve (0: plain local steps) */
+  double cfl;       /* pseudo-time CFL number of the synthetic solve's local steps (<= 0: 1.5) */
 } orc_config;
+
+/* most Anderson-acceleration columns */
+#define ORC_AA_MAX 32
 
 typedef struct orc_bc {
   int32_t kind;     /* 0 diffuse wall, 1 specular wall, 2 free-stream inflow, 3 outflow */
@@ -109,6 +113,18 @@ int orc_couple(orc_ctx* c, orc_couple_report* rep);
 /* which: 0 M^{k+1/2} [n][6], 1 HoT [n][12], 2 M^{k+1} [n][6], 3 flags [n], 4 own sampled state [n][6],
  * 5 local accumulation weight [n] (0: moving average) */
 int orc_read_couple(orc_ctx* c, int32_t which, double* out, int64_t cap);
+/* harness for the pins of the synthetic equations (Sec. 2.2), nondimensional
+ * rows per cell: prim [n][6] = rho, u(3), T_t, T_r; grad [n][15] = d(u_x, u_y,
+ * u_z, T_t, T_r)/d(x, y, z), component-major within the row (3 q + i);
+ * NSF out [n][12] = sigma (xx, yy, zz, xy, xz, yz), q_t (3), q_r (3).
+ * orc_synthetic_solve runs the solve from M^{k+1/2} = half with the given HoT
+ * [n][12]; src [n][6] (or NULL) is a volume source added to the residual of
+ * each conserved variable (rho, rho u, rho E, rho e_r), for a manufactured
+ * solution; out [n][6] receives M^{k+1}. */
+int orc_gradients(orc_ctx* c, const double* prim, double* grad);
+int orc_nsf(orc_ctx* c, const double* prim, const double* grad, double* out);
+int orc_synthetic_solve(orc_ctx* c, const double* half, const double* hot, const double* src, double* out,
+                        int32_t* iters, double* res);
 int orc_write_moments(orc_ctx* c, int32_t which, const double* in);
 int orc_write_wall_flux(orc_ctx* c, const double* in, int64_t steps);
 

@@ -30,7 +30,7 @@ class OrcConfig(C.Structure):
         ("L_ref", C.c_double), ("n_a", C.c_int32), ("N_s", C.c_int32), ("N_m", C.c_int32),
         ("passes", C.c_int32), ("eps_m", C.c_double), ("KnD_max", C.c_double), ("capacity", C.c_int64),
         ("closure", C.c_int32), ("recon", C.c_int32),
-        ("local_acc", C.c_int32), ("pad", C.c_int32),
+        ("local_acc", C.c_int32), ("aa_m", C.c_int32), ("cfl", C.c_double),
     ]
 
 
@@ -113,6 +113,9 @@ def lib():
         L.orc_closure_set.argtypes = [P, P]
         L.orc_closure_features.argtypes = [P, C.c_int32, P]
         L.orc_closure_targets.argtypes = [P, C.c_int32, P, C.c_int64, P]
+        L.orc_gradients.argtypes = [P, P, P]
+        L.orc_nsf.argtypes = [P, P, P, P]
+        L.orc_synthetic_solve.argtypes = [P, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -143,6 +146,7 @@ def make_config(scen, **over) -> OrcConfig:
     cfg.Kn, cfg.L_ref = scen.Kn, scen.L
     cfg.n_a, cfg.N_s, cfg.N_m, cfg.passes = 1000, 100, 500, 3
     cfg.eps_m, cfg.KnD_max = 1e-6, 1.0
+    cfg.aa_m, cfg.cfl = 20, 1.5
     cfg.capacity = scen.capacity or 2 * scen.n_particles
     for k, v in over.items():
         setattr(cfg, k, v)
@@ -313,6 +317,32 @@ class Oracle:
         Y = np.zeros((len(X), 8), np.float32)
         self._check(self.L.orc_closure_targets(self.h, which, _p(X), len(X), _p(Y)))
         return Y
+
+    # harness of the synthetic-equation pins (nondimensional rows per cell)
+    def gradients(self, prim):
+        prim = np.ascontiguousarray(prim, np.float64)
+        assert prim.shape == (self.n_tets, 6)
+        g = np.zeros((self.n_tets, 15), np.float64)
+        self._check(self.L.orc_gradients(self.h, _p(prim), _p(g)))
+        return g
+
+    def nsf(self, prim, grad):
+        prim = np.ascontiguousarray(prim, np.float64)
+        grad = np.ascontiguousarray(grad, np.float64)
+        out = np.zeros((self.n_tets, 12), np.float64)
+        self._check(self.L.orc_nsf(self.h, _p(prim), _p(grad), _p(out)))
+        return out
+
+    def synthetic_solve(self, half, hot=None, src=None):
+        half = np.ascontiguousarray(half, np.float64)
+        hot = np.zeros((self.n_tets, 12)) if hot is None else np.ascontiguousarray(hot, np.float64)
+        src = None if src is None else np.ascontiguousarray(src, np.float64)
+        out = np.zeros((self.n_tets, 6), np.float64)
+        it = C.c_int32(0)
+        res = C.c_double(0.0)
+        self._check(self.L.orc_synthetic_solve(self.h, _p(half), _p(hot), _p(src), _p(out), C.byref(it),
+                                               C.byref(res)))
+        return out, it.value, res.value
 
     @property
     def step_index(self):

@@ -825,17 +825,20 @@ def test_synthetic_solve_conserves_mass():
 def test_coupling_stable_at_small_knudsen_number():
     """The first coupling of a near-continuum cavity (Kn = 0.001: cells about
     30 mean free paths, sampled stress and heat flux mostly statistical
-    noise) converges to a positive state: the isothermal no-slip wall
-    closure gives the synthetic equations a steady solution for any sampled
-    input (a closure by the sampled wall fluxes has none unless they balance)."""
+    noise) converges to eps_m = 1e-6 and to a positive state with the mass
+    it started from: the isothermal no-slip wall closure gives the synthetic
+    equations a steady solution for any sampled input (a closure by the
+    sampled wall fluxes has none unless they balance)."""
     s = W.cavity_scenario(6, 60_000, 0.001, seed=3)
-    o = orc.Oracle(s, N_m=500)
+    o = orc.Oracle(s, N_m=2000)
     o.init()
     o.step(200, orc.EWMA)
     r = o.couple()
-    new = o.read_couple(2)
-    assert r["iters"] == 500 and r["residual"] < 0.05
-    assert new[:, 0].min() > 0.5 and new[:, 4].min() > 0.5 and np.all(np.isfinite(new))
+    new, half = o.read_couple(2), o.read_couple(0)
+    vol = o.mesh_info()["vol"]
+    assert r["iters"] < 2000 and r["residual"] <= 1e-6
+    assert new[:, 0].min() > 0.3 and new[:, 4].min() > 0.3 and np.all(np.isfinite(new))
+    assert abs((new[:, 0] * vol).sum() / (half[:, 0] * vol).sum() - 1) < 1e-12
 
 
 def test_synthetic_fourier_conduction():
@@ -852,13 +855,13 @@ def test_synthetic_fourier_conduction():
     mu = g.mu_ref() * (Tw / g.T_ref) ** g.omega
     s = W.Scenario(gas=g, mesh=mesh, n_particles=23040, n_init=n, T_init=Tw, u_init=(0.0, 0.0, 0.0),
                    F_N=n * 1e-9 / 23040, dt=0.2 * mu / (n * KB * Tw), seed=5, L=1e-3, Kn=0.1, capacity=46080)
-    o = orc.Oracle(s, N_m=20000, eps_m=1e-12, KnD_max=1e9, closure=1)
+    o = orc.Oracle(s, N_m=2000, eps_m=1e-12, KnD_max=1e9, closure=1)
     o.init()
     o.step(1, orc.WINDOW)
     o.write_moments(orc.PHI_EWMA, equilibrium_phi(o, s))
     o.closure_set(constant_net(np.zeros(8, np.float32)))
     r = o.couple()
-    assert r["n_learned"] == o.n_tets and r["residual"] < 1e-9
+    assert r["n_learned"] == o.n_tets and r["residual"] <= 1e-12 and r["iters"] < 2000, r
     new = o.read_couple(2)
     y = s.mesh.nodes[s.mesh.tets].mean(axis=1)[:, 1] / 1e-3 + 0.5
     w1 = 1.0 + g.omega
