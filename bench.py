@@ -11,7 +11,7 @@ steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload cavity30|cavity20|sphere|capsule] [--no-couple]
-  python bench.py --convergence
+  python bench.py --convergence | --rconv
 
 --impl reference times the CPU oracle on a bounded sample of the same
 workload.  Under torchrun every rank runs an independent replica (its own
@@ -241,34 +241,15 @@ def centreline_map(scen):
     return pu, pv, nh
 
 
-def convergence_experiment(args):
-    """GPU time to the converged cavity field: plain DSMC vs DIG vs DIG with
-    the learned closure, on the near-continuum cavity (20^3 hexahedra, Kn =
-    0.001, 3M particles; or, with --conv-workload cavity30, the 30^3-hexahedra
-    Kn = 0.01 cavity with 8M particles).  The reference field and the closure's training data
-    come from the solver itself (a DIG run); every timed run starts from the
-    initial equilibrium.  Returns the result object."""
+def _cavity_tools(scen):
+    """Mass weights, centreline map and field readers of a cavity scenario."""
     import numpy as np
-    import torch
 
     from paper_2607_08195_gb300 import dig
-    from paper_2607_08195_gb300 import workload as W
 
-    dev = "cuda:0"
-    scen = W.config_c2() if getattr(args, "conv_workload", "cavity20") == "cavity30" else W.config_c3()
-    Uw = 50.0
+    P = scen.mesh.nodes[scen.mesh.tets]
+    vol = np.abs(np.einsum("ni,ni->n", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))) / 6.0
     pu, pv, nh = centreline_map(scen)
-    NSC = 200            # DSMC steps per coupling cycle
-    WIN = 50             # closure input window (the last WIN steps of a cycle)
-    fl = dig.EWMA | dig.WALLFLUX
-
-    def timed(f):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(torch.cuda.current_stream())
-        r = f()
-        e1.record(torch.cuda.current_stream())
-        torch.cuda.synchronize()
-        return r, e0.elapsed_time(e1) * 1e-3
 
     def profiles(g, which=dig.PHI_EWMA):
         """Mass-weighted centreline profiles (u_x(y), u_y(x)) of a moving
@@ -282,6 +263,58 @@ def convergence_experiment(args):
             out.append(np.bincount(idx[sel], w[sel] * m[sel, q], nh) / np.maximum(den, 1e-300))
         return np.concatenate(out)
 
+    def velocity(g, which):
+        return g.moments(which | dig.MACRO)[:, 2:5]
+
+    return vol, profiles, velocity
+
+
+def _timed(f):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream())
+    r = f()
+    e1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1) * 1e-3
+
+
+def convergence_experiment(args):
+    """GPU time to the converged cavity field: plain DSMC vs DIG vs DIG with
+    the learned closure, on the near-continuum cavity (20^3 hexahedra, Kn =
+    0.001, 3M particles, lid 50 m/s; or, with --conv-workload cavity30, the
+    30^3-hexahedra Kn = 0.01 cavity with 8M particles).
+
+    The closure is trained on other flows of the same cavity (lid speeds 30
+    and 70 m/s, their own seeds): their windows are its inputs and their
+    long-time averages its targets; the GPU seconds spent generating those
+    data and training are reported beside the result.  The reference field
+    is the cumulative average of a separate long DIG run of the 50 m/s flow;
+    every timed run starts from the initial equilibrium.  Returns the result
+    object."""
+    import numpy as np
+    import torch
+
+    from paper_2607_08195_gb300 import dig
+    from paper_2607_08195_gb300 import workload as W
+
+    dev = "cuda:0"
+    c30 = getattr(args, "conv_workload", "cavity20") == "cavity30"
+    base = W.config_c2() if c30 else W.config_c3()
+    nhx = 30 if c30 else 20
+    kn = base.Kn
+
+    def flow(U_lid, seed):
+        return W.cavity_scenario(nhx, base.n_particles, kn, seed, U_lid=U_lid, name=f"{base.name}-lid{U_lid:g}")
+
+    scen = base
+    Uw = 50.0
+    vol, profiles, _ = _cavity_tools(scen)
+    NSC = 200            # DSMC steps per coupling cycle
+    WIN = 50             # closure input window (the last WIN steps of a cycle)
+    fl = dig.EWMA | dig.WALLFLUX
+
     def err(prof, ref):
         return float(np.sqrt(np.mean((prof - ref) ** 2)) / Uw)
 
@@ -294,62 +327,85 @@ def convergence_experiment(args):
             g.step(NSC, fl)
         return g.couple()
 
-    # 1. the solver's own data: a DIG run to steady state, then 50-step windows
-    #    (closure inputs) and the long-time average (targets, reference field)
+    def windows(g, X, nwin):
+        """nwin closure input rows blocks (50-step windows, four per cycle)
+        into X, while the cumulative average runs; returns nothing."""
+        n = g.n_tets
+        g.sample(dig.RESET_CUMUL)
+        w = 0
+        while w < nwin:
+            g.step(NSC - 4 * WIN, fl | dig.CUMUL)
+            for _ in range(4):
+                g.sample(dig.RESET_WINDOW)
+                g.step(WIN, fl | dig.CUMUL | dig.WINDOW)
+                if w < nwin:
+                    g.closure_features(dig.PHI_WINDOW, X[w * n:(w + 1) * n])
+                    w += 1
+            g.couple()
+
+    # 1. training data: other flows of the same cavity
+    n = len(scen.mesh.tets)
+    train_flows = [(30.0, scen.seed + 100), (70.0, scen.seed + 200)]
+    nwin_f = args.conv_windows // len(train_flows)
+    X = torch.empty((nwin_f * len(train_flows) * n, 13), dtype=torch.float32, device=dev)
+    Y = torch.empty((nwin_f * len(train_flows) * n, 8), dtype=torch.float32, device=dev)
+    t_data = 0.0
+    for f_i, (U_lid, seed) in enumerate(train_flows):
+        g = dig.Solver(flow(U_lid, seed), dev, closure=0)
+        g.init()
+
+        def gen():
+            for _ in range(args.conv_train_warm):
+                cycle(g, False)
+            sl = slice(f_i * nwin_f * n, (f_i + 1) * nwin_f * n)
+            windows(g, X[sl], nwin_f)
+            Y[sl] = g.closure_targets(dig.PHI_CUM, X[sl])
+
+        _, dt = _timed(gen)
+        t_data += dt
+        g.close()
+    # 2. the reference field of the measured flow, and windows of it for the
+    #    closure's transfer check (never used for training)
     g = dig.Solver(scen, dev, closure=0)
-    P = scen.mesh.nodes[scen.mesh.tets]  # tet volumes for the mass weights
-    vol = np.abs(np.einsum("ni,ni->n", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))) / 6.0
     g.init()
     warm_fields = []
     for _ in range(args.conv_warm):
         cycle(g, False)
         warm_fields.append(profiles(g))
-    n = g.n_tets
-    nwin = args.conv_windows
-    X = torch.empty((nwin * n, 13), dtype=torch.float32, device=dev)
-    g.sample(dig.RESET_CUMUL)
-    w = 0
-    while w < nwin:
-        g.step(NSC - 4 * WIN, fl | dig.CUMUL)
-        for q in range(4):
-            g.sample(dig.RESET_WINDOW)
-            g.step(WIN, fl | dig.CUMUL | dig.WINDOW)
-            if w < nwin:
-                g.closure_features(dig.PHI_WINDOW, X[w * n:(w + 1) * n])
-                w += 1
-        g.couple()
-    Y = g.closure_targets(dig.PHI_CUM, X)
-    # the reference field: the cumulative average continued to conv_ref cycles
-    for _ in range(max(0, args.conv_ref - nwin // 4)):
+    nval = 8
+    Xt = torch.empty((nval * n, 13), dtype=torch.float32, device=dev)
+    windows(g, Xt, nval)
+    for _ in range(max(0, args.conv_ref - nval // 4)):
         g.step(NSC, fl | dig.CUMUL)
         g.couple()
+    Yt = g.closure_targets(dig.PHI_CUM, Xt)
     ref = profiles(g, dig.PHI_CUM)
     warm_err = [round(err(u, ref), 4) for u in warm_fields][4::5]
-    # the estimator's noise floor: the moving-average block field of the
-    # converged DIG run over the following cycles (independent of the
-    # reference's samples) against the reference
     post = []
     for _ in range(args.conv_noise):
         cycle(g, False)
         post.append(err(profiles(g), ref))
     noise = float(np.median(post))
-    # 2. training (the library's BF16 tensor-core kernels), 90/10 split
-    ntr = int(0.9 * nwin) * n
-    g.closure_init(scen.seed)
+    # 3. training on the other flows (the library's BF16 tensor-core kernels), 90/10 split
+    nrow = X.shape[0]
     rng = np.random.default_rng(scen.seed)
+    order = torch.from_numpy(rng.permutation(nrow).astype(np.int64)).to(dev)
+    X, Y = X[order].contiguous(), Y[order].contiguous()
+    ntr = int(0.9 * nrow)
+    g.closure_init(scen.seed)
     epochs = args.conv_epochs
     perm = torch.from_numpy(np.stack([rng.permutation(ntr) for _ in range(epochs)]).astype(np.int32)).to(dev)
-    losses, t_train = timed(lambda: g.closure_train(X[:ntr].contiguous(), Y[:ntr].contiguous(), epochs=epochs,
-                                                    batch=4096, lr=1e-3, perm=perm))
+    losses, t_train = _timed(lambda: g.closure_train(X[:ntr].contiguous(), Y[:ntr].contiguous(), epochs=epochs,
+                                                     batch=4096, lr=1e-3, perm=perm))
     Xv, Yv = X[ntr:].contiguous(), Y[ntr:].contiguous()
-    mse_net = g.closure_loss(Xv, Yv)
-    mse_win = g.closure_loss(Xv, Yv, identity=True)
+    mse_net, mse_win = g.closure_loss(Xv, Yv), g.closure_loss(Xv, Yv, identity=True)
+    mse_net_t, mse_win_t = g.closure_loss(Xt, Yt), g.closure_loss(Xt, Yt, identity=True)
     params = g.closure_get()
     g.close()
-    del X, Y, perm
+    del X, Y, perm, Xt, Yt
     torch.cuda.empty_cache()
 
-    # 3. timed runs from the initial state
+    # 4. timed runs from the initial state
     thr = max(args.conv_threshold, args.conv_threshold_factor * noise)
     HOLD = 5
 
@@ -358,12 +414,12 @@ def convergence_experiment(args):
         if kind.startswith("dig_net"):
             h.closure_set(params)
         h.init()
-        t, hist, hit, tail, fields = 0.0, [], None, [], []
+        t, hist, tail, fields = 0.0, [], [], []
         for k in range(ncycles):
             if kind == "plain":
-                _, dt = timed(lambda: h.step(NSC, fl))
+                _, dt = _timed(lambda: h.step(NSC, fl))
             else:
-                _, dt = timed(lambda: cycle(h, kind.startswith("dig_net")))
+                _, dt = _timed(lambda: cycle(h, kind.startswith("dig_net")))
             t += dt
             prof = profiles(h)
             e = err(prof, ref)
@@ -373,6 +429,7 @@ def convergence_experiment(args):
                 tail.append(prof)
         h.close()
         torch.cuda.empty_cache()
+
         # converged: the first checkpoint at or below the threshold whose next
         # HOLD checkpoints also average at or below it
         def first_hold(errs):
@@ -383,9 +440,6 @@ def convergence_experiment(args):
 
         k_ref = first_hold([x[1] for x in hist])
         hit = None if k_ref is None else hist[k_ref]
-        # the same criterion against the run's own final field (mean of its
-        # last 20 checkpoints), before those checkpoints: when the method
-        # settles, whatever field it settles on
         own = np.mean(tail, axis=0)
         k_own = first_hold([err(f, own) for f in fields[:len(fields) - len(tail)]])
         return {"seconds": None if hit is None else hit[0], "steps": None if hit is None else hit[2],
@@ -396,19 +450,16 @@ def convergence_experiment(args):
                 "final_profiles": [round(float(x) / Uw, 4) for x in np.mean(tail, axis=0)],
                 "error_every_5_cycles": [x[:2] for x in hist[4::5]]}
 
-    # DIG with the learned closure takes a moving average as short as the
-    # closure's window (its HoT comes denoised from the network; the state
-    # then follows the particles within a window); DIG without it keeps the
-    # paper's n_a = 1000, and is also run on the short average, where its
-    # sampled HoT is noisy
     na = args.conv_net_na
     res = {"dig_net": run("dig_net", args.conv_cycles, n_a=na), "dig": run("dig", args.conv_cycles),
            f"dig_na{na}": run("dig", args.conv_cycles, n_a=na),
            "dig_net_na1000": run("dig_net", args.conv_cycles, n_a=1000),
            "plain_dsmc": run("plain", args.conv_plain_cycles)}
+    sec = res["dig_net"]["seconds"]
     return {
         "metric": "GPU seconds to the converged cavity field", "unit": "s", "higher_is_better": False,
-        "value": res["dig_net"]["seconds"], "workload": scen.name,
+        "value": sec, "workload": scen.name,
+        "value_incl_closure_cost": None if sec is None else round(sec + t_data + t_train, 3),
         "methods_config": {"dig_net": f"DIG with the learned closure, n_a = {na}",
                            "dig": "DIG, n_a = 1000", f"dig_na{na}": f"DIG, n_a = {na}",
                            "dig_net_na1000": "DIG with the learned closure, n_a = 1000",
@@ -416,16 +467,77 @@ def convergence_experiment(args):
         "error": "RMS over the centreline profiles u_x(y) and u_y(x) (moving average, central half of the "
                  "cavity in the other two directions) against the reference profiles, over U_w",
         "threshold": round(thr, 4), "noise_floor": round(noise, 4),
-        "reference": f"cumulative average of a DIG run over {max(args.conv_ref, nwin // 4)} coupling cycles after "
-                     f"{args.conv_warm} cycles",
+        "reference": f"cumulative average of a separate DIG run of the lid-50 m/s flow over "
+                     f"{max(args.conv_ref, nval // 4)} coupling cycles after {args.conv_warm} cycles",
         "reference_profiles": [round(float(x) / Uw, 4) for x in ref],
         "reference_run_error_every_5_cycles": warm_err,
         "methods": res,
-        "closure": {"train_rows": ntr, "epochs": epochs, "train_gpu_seconds": round(t_train, 3),
+        "closure": {"trained_on": [f"lid {u:g} m/s, seed {sd}" for u, sd in train_flows],
+                    "train_rows": ntr, "epochs": epochs,
+                    "data_gpu_seconds": round(t_data, 3), "train_gpu_seconds": round(t_train, 3),
                     "loss_first_last": [float(losses[0]), float(losses[-1])],
                     "heldout_mse_net": mse_net, "heldout_mse_window_hot": mse_win,
-                    "gain": mse_win / max(mse_net, 1e-300)},
+                    "gain_heldout_training_flows": mse_win / max(mse_net, 1e-300),
+                    "target_flow_mse_net": mse_net_t, "target_flow_mse_window_hot": mse_win_t,
+                    "gain_target_flow": mse_win_t / max(mse_net_t, 1e-300)},
     }
+
+
+def rconv_experiment(args):
+    """The convergence criterion of the 8M-particle Kn = 0.01 cavity (30^3
+    hexahedra): plain DSMC for up to 20,000 steps against DIG coupled every
+    200 steps, each sampled into a cumulative average from its first step.
+    E_k = |u_k - u_{k-1}|_2 / |u_k|_2 between consecutive 200-step
+    checkpoints of the cumulative velocity, over every cell (volume-weighted)
+    and over the centreline profiles; a method has converged at the first
+    checkpoint where E_k < 1e-3 holds for three checkpoints in a row.
+    Returns GPU seconds and steps to that point for each measure (None if
+    not reached within 20,000 steps)."""
+    import numpy as np
+
+    from paper_2607_08195_gb300 import dig
+    from paper_2607_08195_gb300 import workload as W
+
+    scen = W.config_c2()
+    vol, profiles, velocity = _cavity_tools(scen)
+    NSC, KMAX, TOL, HOLD = 200, args.rconv_checkpoints, 1e-3, 3
+    out = {}
+    for kind in ("plain_dsmc", "dig"):
+        g = dig.Solver(scen, "cuda:0")
+        g.init()
+        g.sample(dig.RESET_CUMUL)
+        t, prev_u, prev_p, eu, ep, hist = 0.0, None, None, [], [], []
+        first = {"field": None, "profiles": None}
+        for k in range(KMAX):
+            if kind == "dig":
+                _, dt = _timed(lambda: (g.step(NSC, dig.EWMA | dig.WALLFLUX | dig.CUMUL), g.couple()))
+            else:
+                _, dt = _timed(lambda: g.step(NSC, dig.EWMA | dig.CUMUL))
+            t += dt
+            u, p = velocity(g, dig.PHI_CUM), profiles(g, dig.PHI_CUM)
+            if prev_u is not None:
+                eu.append(float(np.sqrt((vol[:, None] * (u - prev_u) ** 2).sum() / (vol[:, None] * u ** 2).sum())))
+                ep.append(float(np.linalg.norm(p - prev_p) / np.linalg.norm(p)))
+                hist.append((round(t, 3), (k + 1) * NSC, eu[-1], ep[-1]))
+                for key, e in (("field", eu), ("profiles", ep)):
+                    if first[key] is None and len(e) >= HOLD and all(x < TOL for x in e[-HOLD:]):
+                        first[key] = hist[-HOLD]
+            prev_u, prev_p = u, p
+            if all(v is not None for v in first.values()):
+                break
+        g.close()
+        out[kind] = {"field": None if first["field"] is None else {"seconds": first["field"][0],
+                                                                   "steps": first["field"][1]},
+                     "profiles": None if first["profiles"] is None else {"seconds": first["profiles"][0],
+                                                                         "steps": first["profiles"][1]},
+                     "gpu_seconds_run": round(t, 3), "steps_run": hist[-1][1] if hist else 0,
+                     "last_E_field": round(eu[-1], 6) if eu else None,
+                     "last_E_profiles": round(ep[-1], 6) if ep else None,
+                     "E_every_10_checkpoints": [(h[0], h[1], round(h[2], 5), round(h[3], 5)) for h in hist[9::10]]}
+    return {"criterion": "E_k = |u_k - u_{k-1}|_2 / |u_k|_2 < 1e-3 on the cumulative velocity at consecutive "
+                         "200-step checkpoints, three in a row (field: every cell, volume-weighted; profiles: "
+                         "the two centreline profiles)",
+            "workload": scen.name, "max_steps": KMAX * NSC, "methods": out}
 
 
 def main():
@@ -442,6 +554,12 @@ def main():
     ap.add_argument("--convergence", action="store_true",
                     help="only the time-to-converged-field experiment (plain DSMC vs DIG vs DIG + learned closure)")
     ap.add_argument("--conv-warm", type=int, default=80)
+    ap.add_argument("--conv-train-warm", type=int, default=60,
+                    help="cycles each training flow runs before its windows are taken")
+    ap.add_argument("--rconv-checkpoints", type=int, default=100,
+                    help="200-step checkpoints of the R-conv comparison (100 = 20,000 DSMC steps)")
+    ap.add_argument("--no-rconv", action="store_true", help="leave the R-conv comparison out of the default line")
+    ap.add_argument("--rconv", action="store_true", help="only the R-conv comparison (plain DSMC vs DIG, 8M cavity)")
     ap.add_argument("--conv-windows", type=int, default=44)
     ap.add_argument("--conv-epochs", type=int, default=20)
     ap.add_argument("--conv-cycles", type=int, default=60)
@@ -463,11 +581,11 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.convergence:
+    if args.convergence or args.rconv:
         import torch
 
         torch.cuda.set_device(0)
-        print(json.dumps(convergence_experiment(args)), flush=True)
+        print(json.dumps(convergence_experiment(args) if args.convergence else rconv_experiment(args)), flush=True)
         return 0
 
     import numpy as np
@@ -614,10 +732,17 @@ def main():
                     "methods": {k: {"config": cv["methods_config"][k], "seconds": r["seconds"], "steps": r["steps"],
                                     "mean_error_last_20": r["mean_error_last_20"]}
                                 for k, r in cv["methods"].items()},
-                    "closure_gain_heldout_mse": cv["closure"]["gain"],
+                    "value_incl_closure_cost": cv["value_incl_closure_cost"],
+                    "closure": {k: cv["closure"][k] for k in ("trained_on", "data_gpu_seconds", "train_gpu_seconds",
+                                                              "gain_heldout_training_flows", "gain_target_flow")},
                 }
             except Exception as e:  # reported, not fatal for the throughput line
                 line["convergence"] = {"error": f"{type(e).__name__}: {e}"}
+            if not args.no_rconv:
+                try:
+                    line["rconv"] = rconv_experiment(args)
+                except Exception as e:
+                    line["rconv"] = {"error": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

@@ -126,7 +126,13 @@ typedef struct dig_config {
                             its moving average stops forgetting (running mean of every later step,
                             its average so far counting as min(m, n_a) samples) until a coupling
                             accepts it; 0: every cell keeps the moving average */
+  int32_t aa_m;          /* synthetic solve (S10): depth of the Anderson acceleration of its pseudo-time
+                            iteration, 0..DIG_AA_MAX (0: plain local pseudo-time steps) */
+  double cfl;            /* synthetic solve: CFL number of each cell's own pseudo-time step (<= 0: 1.5) */
 } dig_config;
+
+/* most Anderson-acceleration columns of the synthetic solve (dig_config.aa_m) */
+#define DIG_AA_MAX 32
 
 typedef struct dig_bc {
   int32_t kind;  /* DIG_BC_* */
@@ -251,7 +257,10 @@ int dig_kernel_time(dig_ctx* ctx, double* total_ms, int64_t* launches);
  * filled the same way, layer by layer, up to 64 more layers, and are not
  * recalibrated), the steady synthetic equations
  * (Eq. macro with Eq. synthetic_closure) solved for M^{k+1} (at most N_m
- * iterations or residual below eps_m of its first value), and the particles
+ * iterations or residual below eps_m of its first value; pseudo-time
+ * iteration with each cell's own step at CFL cfg.cfl, Anderson acceleration
+ * of depth cfg.aa_m, and, without open boundaries, a scaling that keeps the
+ * total mass of M^{k+1/2}), and the particles
  * of accepted cells recalibrated to M^{k+1} (velocities shifted and scaled,
  * rotational energies scaled, particles cloned or deleted with the density
  * ratio against the density of the particles the cell holds).  Diffuse walls

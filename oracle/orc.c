@@ -1835,15 +1835,16 @@ static double wdot(const double* a, const double* b, const double* w, int64_t n)
 }
 
 /* The coefficients gamma minimising |f - dF gamma| (volume-weighted norm)
- * over the k stored columns, in age order (oldest first): normal equations
- * of the columns scaled to unit norm, with 1e-10 added to the diagonal, by
- * Cholesky.  Returns 0 if the factorisation fails (then no column is used). */
-static int aa_coefficients(const double* dF, const int* slot, int k, int64_t len, const double* f, const double* w,
-                           int64_t n, double* gam) {
+ * over the k held columns, in age order (oldest first), from the Gram
+ * matrix H of the columns and b_i = <dF_i, f> (both held by ring slot):
+ * normal equations of the columns scaled to unit norm, with 1e-10 added to
+ * the diagonal, by Cholesky.  Returns 0 if the factorisation fails (then no
+ * column is used). */
+static int aa_coefficients(const double (*Hs)[ORC_AA_MAX], const double* bs, const int* slot, int k, double* gam) {
   double H[ORC_AA_MAX][ORC_AA_MAX], b[ORC_AA_MAX], sc[ORC_AA_MAX], y[ORC_AA_MAX];
   for (int i = 0; i < k; ++i) {
-    for (int j = 0; j <= i; ++j) H[i][j] = H[j][i] = wdot(dF + len * slot[i], dF + len * slot[j], w, n);
-    b[i] = wdot(dF + len * slot[i], f, w, n);
+    for (int j = 0; j < k; ++j) H[i][j] = Hs[slot[i]][slot[j]];
+    b[i] = bs[slot[i]];
   }
   for (int i = 0; i < k; ++i) sc[i] = H[i][i] > 0 ? 1.0 / sqrt(H[i][i]) : 0.0;
   for (int i = 0; i < k; ++i) {
@@ -1886,9 +1887,12 @@ static int aa_coefficients(const double* dF, const int* slot, int k, int64_t len
  * of depth m = cfg.aa_m (Walker & Ni, SIAM J. Numer. Anal. 49, 2011) combines
  * the last m steps: U <- g(U_k) - dG gamma, gamma minimising
  * |f_k - dF gamma| with f = g(U) - U and dF, dG the differences of
- * consecutive f and g(U).  A combined state with a non-positive density or
- * temperature in some cell is replaced by g(U_k), and the history is
- * cleared.  Stops after N_m iterations or when the residual norm falls to
+ * consecutive f and g(U).  The Gram matrix H_ij = <dF_i, dF_j> gains one
+ * row per iteration (the new column against every held one), and
+ * b_i = <dF_i, f_k> follows from f_k = f_{k-1} + dF_new as b_i + H_i,new,
+ * except for the new column's, which is computed.  A combined state with a
+ * non-positive density or temperature in some cell is replaced by g(U_k),
+ * and the history is cleared.  Stops after N_m iterations or when the residual norm falls to
  * eps_m times its first value. */
 static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* iters, double* res_out) {
   const int64_t n = c->n_tets;
@@ -1920,6 +1924,7 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
     M0 += w[t] * U[nv * t];
   }
   double res0 = 0.0, res = 0.0;
+  double Hs[ORC_AA_MAX][ORC_AA_MAX], bs[ORC_AA_MAX];
   int it = 0, nh = 0, head = 0;
   for (it = 0; it < c->cfg.N_m; ++it) {
     res = sqrt(residual(c, d, src, U, R, dtl, P, G, S));
@@ -1943,22 +1948,30 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
     }
     /* acceleration */
     for (int64_t i = 0; i < len; ++i) f[i] = Gx[i] - U[i];
+    int slot[ORC_AA_MAX];
+    double gam[ORC_AA_MAX];
     if (it > 0) {
-      double* a = dF + len * head;
-      double* b = dG + len * head;
+      const int s0 = head;
+      double* a = dF + len * s0;
+      double* b = dG + len * s0;
       for (int64_t i = 0; i < len; ++i) {
         a[i] = f[i] - fp[i];
         b[i] = Gx[i] - Gp[i];
       }
       head = (head + 1) % m;
       if (nh < m) nh++;
+      for (int i = 0; i < nh; ++i) slot[i] = ((head - nh + i) % m + m) % m;
+      for (int i = 0; i < nh; ++i) {
+        const double h = wdot(dF + len * slot[i], a, w, n);
+        Hs[slot[i]][s0] = Hs[s0][slot[i]] = h;
+        if (slot[i] != s0) bs[slot[i]] += h;
+      }
+      bs[s0] = wdot(a, f, w, n);
     }
     memcpy(fp, f, sizeof(double) * len);
     memcpy(Gp, Gx, sizeof(double) * len);
-    int slot[ORC_AA_MAX];
-    double gam[ORC_AA_MAX];
     for (int i = 0; i < nh; ++i) slot[i] = ((head - nh + i) % m + m) % m;
-    const int k = nh > 0 && aa_coefficients(dF, slot, nh, len, f, w, n, gam) ? nh : 0;
+    const int k = nh > 0 && aa_coefficients(Hs, bs, slot, nh, gam) ? nh : 0;
     int pos = 1;
     for (int64_t t = 0; t < n; ++t) {
       for (int q = 0; q < nv; ++q) {
@@ -2108,6 +2121,23 @@ int orc_nsf(orc_ctx* c, const double* prim, const double* grad, double* out) {
   const nd_t d = nondim(c);
   for (int64_t t = 0; t < c->n_tets; ++t) nsf(&d, prim + 6 * t, grad + 15 * t, out + 12 * t, out + 12 * t + 6,
                                                out + 12 * t + 9);
+  return 0;
+}
+
+int orc_synthetic_residual(orc_ctx* c, const double* prim, const double* hot, const double* src, double* R,
+                           double* dtl) {
+  if (!c->vol) return fail(c, -7, "mesh not loaded");
+  const int64_t n = c->n_tets;
+  if (!c->cp_hot) c->cp_hot = (double*)calloc(12 * n, sizeof(double));
+  memcpy(c->cp_hot, hot, sizeof(double) * 12 * n);
+  const nd_t d = nondim(c);
+  double* U = (double*)malloc(sizeof(double) * 6 * n);
+  double* P = (double*)calloc(6 * n, sizeof(double));
+  double* G = (double*)malloc(sizeof(double) * 15 * n);
+  double* S = (double*)malloc(sizeof(double) * 12 * n);
+  for (int64_t t = 0; t < n; ++t) cons_from_prim(&d, prim + 6 * t, U + 6 * t);
+  residual(c, &d, src, U, R, dtl, P, G, S);
+  free(U); free(P); free(G); free(S);
   return 0;
 }
 

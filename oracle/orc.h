@@ -125,6 +125,11 @@ int orc_gradients(orc_ctx* c, const double* prim, double* grad);
 int orc_nsf(orc_ctx* c, const double* prim, const double* grad, double* out);
 int orc_synthetic_solve(orc_ctx* c, const double* half, const double* hot, const double* src, double* out,
                         int32_t* iters, double* res);
+/* the residual R [n][6] of the conserved variables (rho, rho u, rho E,
+ * rho e_r) and the CFL-1 pseudo-time step dtl [n] of the state prim [n][6]
+ * with the given HoT [n][12] and source src [n][6] (or NULL) */
+int orc_synthetic_residual(orc_ctx* c, const double* prim, const double* hot, const double* src, double* R,
+                           double* dtl);
 int orc_write_moments(orc_ctx* c, int32_t which, const double* in);
 int orc_write_wall_flux(orc_ctx* c, const double* in, int64_t steps);
 

@@ -116,6 +116,7 @@ def lib():
         L.orc_gradients.argtypes = [P, P, P]
         L.orc_nsf.argtypes = [P, P, P, P]
         L.orc_synthetic_solve.argtypes = [P, P, P, P, P, P, P]
+        L.orc_synthetic_residual.argtypes = [P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -343,6 +344,15 @@ class Oracle:
         self._check(self.L.orc_synthetic_solve(self.h, _p(half), _p(hot), _p(src), _p(out), C.byref(it),
                                                C.byref(res)))
         return out, it.value, res.value
+
+    def synthetic_residual(self, prim, hot=None, src=None):
+        prim = np.ascontiguousarray(prim, np.float64)
+        hot = np.zeros((self.n_tets, 12)) if hot is None else np.ascontiguousarray(hot, np.float64)
+        src = None if src is None else np.ascontiguousarray(src, np.float64)
+        R = np.zeros((self.n_tets, 6), np.float64)
+        dtl = np.zeros(self.n_tets, np.float64)
+        self._check(self.L.orc_synthetic_residual(self.h, _p(prim), _p(hot), _p(src), _p(R), _p(dtl)))
+        return R, dtl
 
     @property
     def step_index(self):

@@ -170,7 +170,7 @@ int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (!(cfg->mass > 0) || !(cfg->dt > 0) || !(cfg->F_N > 0) || !(cfg->alpha > 0) ||
       (cfg->rot_dof != 0 && cfg->rot_dof != 2) || (cfg->recon != 0 && cfg->recon != 1) ||
       (cfg->local_acc != 0 && cfg->local_acc != 1) || cfg->tile_cells > 2048 ||
-      cfg->stage_cap > 8192)
+      cfg->stage_cap > 8192 || cfg->aa_m < 0 || cfg->aa_m > AA_MAX)
     return DIG_ERR_ARG;
   dig_ctx* c = new dig_ctx();
   c->cfg = *cfg;
@@ -179,6 +179,7 @@ int dig_create(const dig_config* cfg, dig_ctx** out) {
   if (c->cfg.stage_cap > 0) c->stage_cap = c->cfg.stage_cap;
   if (c->cfg.cta_threads > 0) c->cta_threads = c->cfg.cta_threads <= 64 ? 64 : c->cfg.cta_threads <= 128 ? 128 : 256;
   if (c->cfg.n_a <= 0) c->cfg.n_a = 1000;
+  if (!(c->cfg.cfl > 0)) c->cfg.cfl = 1.5;
   c->tile_cells = c->cfg.tile_cells;
   *out = c;
   return DIG_OK;
@@ -566,6 +567,14 @@ static size_t layout(dig_ctx* ctx, char* base) {
   C.Ff = A.take<double>(6 * nif);
   C.lmf = A.take<double>(nif);
   C.part = A.take<double>(couple_part_count((int)n));
+  C.dtl = A.take<double>(n);
+  C.fp = A.take<double>(6 * n);
+  C.Gp = A.take<double>(6 * n);
+  const size_t naa = (size_t)std::max(ctx->cfg.aa_m, 1);
+  C.dF = A.take<double>(naa * 6 * n);
+  C.dG = A.take<double>(naa * 6 * n);
+  C.apart = A.take<double>(couple_apart_count((int)n));
+  C.aa = A.take<AAState>(1);
   C.avail = A.take<int>(n);
   C.avail2 = A.take<int>(n);
   C.feat = A.take<float>((size_t)MLP_NIN * n);
@@ -722,6 +731,13 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
     C.kB = KB;
     C.KnD_max = c.KnD_max;
     C.recon = c.recon;
+    C.N_m = c.N_m;
+    C.eps_m = c.eps_m;
+    C.aa_m = c.aa_m;
+    C.cfl = c.cfl;
+    C.closed = 1;
+    for (const dig_bc& b : ctx->bc_host)
+      if (b.kind == DIG_BC_INFLOW || b.kind == DIG_BC_OUTFLOW) C.closed = 0;
   }
   CK(cudaStreamSynchronize(s));
   if (!ctx->ev) CK(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));
@@ -1198,12 +1214,16 @@ int dig_load(dig_ctx* ctx, const void* host_in, int64_t size) {
 // ---------------------------------------------------------------------------
 // DIG coupling (Alg. 1, one outer step)
 // ---------------------------------------------------------------------------
-// The synthetic solve (S10) is 3 + 5 N_m launches whose arguments are fixed
-// once the arena is bound (its pointers, the configuration and the mesh
-// constants; no per-coupling field of CoupleParams is read by its kernels).
-// It is captured once, on a private stream, into a CUDA graph and replayed on
-// the context's stream, which takes the per-launch overheads out of its loop.
-// If the capture is refused, the kernels are launched directly.
+// The synthetic solve (S10) runs in chunks of S10_CHUNK iterations.  A chunk's
+// launches have arguments fixed once the arena is bound (pointers,
+// configuration, mesh constants; the iteration index and the stopping state
+// live on the device), so it is captured once, on a private stream, into a
+// CUDA graph and replayed on the context's stream until the solve reports
+// itself done (converged, N_m reached or a non-finite residual); the kernels
+// of a chunk that runs past that point return at once.  If the capture is
+// refused, the kernels are launched directly.
+static constexpr int S10_CHUNK = 25;
+
 static int run_s10(dig_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   CK(cudaGetLastError());  // a launch error of the steps before, reported before any capture
@@ -1213,7 +1233,7 @@ static int run_s10(dig_ctx* ctx) {
       const long long before = g_launches;
       cudaGraph_t gr = nullptr;
       if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        launch_couple_s10(ctx->P, ctx->C, ctx->cfg.N_m, ctx->cfg.eps_m, cs);
+        launch_couple_s10_iters(ctx->P, ctx->C, S10_CHUNK, cs);
         if (cudaStreamEndCapture(cs, &gr) == cudaSuccess && gr) {
           if (cudaGraphInstantiate(&ctx->s10_exec, gr, 0) != cudaSuccess) ctx->s10_exec = nullptr;
           cudaGraphDestroy(gr);
@@ -1225,12 +1245,22 @@ static int run_s10(dig_ctx* ctx) {
     }
     (void)cudaGetLastError();  // a refused capture leaves its error here
   }
-  if (ctx->s10_exec) {
-    CK(cudaGraphLaunch(ctx->s10_exec, s));
-    g_launches += ctx->s10_launches;
-  } else {
-    launch_couple_s10(ctx->P, ctx->C, ctx->cfg.N_m, ctx->cfg.eps_m, s);
+  launch_couple_s10_init(ctx->P, ctx->C, s);
+  const int chunks = (ctx->cfg.N_m + S10_CHUNK - 1) / S10_CHUNK + 1;  // + 1: the chunk that finds N_m reached
+  for (int k = 0; k < chunks; ++k) {
+    if (ctx->s10_exec) {
+      CK(cudaGraphLaunch(ctx->s10_exec, s));
+      g_launches += ctx->s10_launches;
+    } else {
+      launch_couple_s10_iters(ctx->P, ctx->C, S10_CHUNK, s);
+    }
+    int done = 0;
+    CK(cudaMemcpyAsync(&done, &ctx->C.scal->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int rc = wait_stream(ctx);
+    if (rc) return rc;
+    if (done) break;
   }
+  launch_couple_s10_final(ctx->P, ctx->C, s);
   return DIG_OK;
 }
 

@@ -448,20 +448,28 @@ __global__ void k_cp_init_cons(Params P, CoupleParams C) {
   for (int q = 0; q < 6; ++q) C.U[(size_t)q * n + c] = U[q];
 }
 
-// U += dt R of the previous iteration (unless it stopped), then the
-// primitives and the viscosity of the new state
-__global__ void k_cp_prim(Params P, CoupleParams C, int apply) {
+// the primitives of the current state U, and its viscosity, sound speed and
+// Mach number; the iteration limit N_m ends the solve here.  If the last
+// Anderson combination was not positive in some cell, the state is the base
+// step g(U) instead (U <- Gp; the following k_cp_reduce clears the history).
+__global__ void k_cp_prim(Params P, CoupleParams C) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
-  if (c >= n || C.scal->done) return;
-  double U[6], Pp[6];
-  const double dt = C.scal->dtg;
-  for (int q = 0; q < 6; ++q) {
-    U[q] = C.U[(size_t)q * n + c];
-    if (apply) {
-      U[q] += dt * C.R[(size_t)q * n + c];
-      C.U[(size_t)q * n + c] = U[q];
+  if (C.scal->done) return;
+  if (C.scal->itc >= C.N_m) {
+    if (c == 0) {
+      C.scal->done = 1;
+      C.scal->iters = C.N_m;
     }
+    return;
+  }
+  if (c >= n) return;
+  double U[6], Pp[6];
+  const bool fb = C.scal->aabad != 0;
+  for (int q = 0; q < 6; ++q) {
+    const size_t k = (size_t)q * n + c;
+    if (fb && (q < 5 || C.dr > 0)) C.U[k] = C.Gp[k];
+    U[q] = C.U[k];
   }
   prim_from_cons(C, U, Pp);
   for (int q = 0; q < 6; ++q) C.prim[(size_t)q * n + c] = Pp[q];
@@ -620,15 +628,17 @@ __global__ void k_cp_face(Params P, CoupleParams C) {
   C.lmf[i] = lm;
 }
 
-// residual and local stable step of every cell from its face fluxes (the
-// interior ones from k_cp_face, the boundary ones here); per-block partial
-// (min step, sum of squared residuals)
+// residual and pseudo-time step of every cell from its face fluxes (the
+// interior ones from k_cp_face, the boundary ones here): dtl = cfl V / sum_f
+// A_f (lambda_f + 2 nu A_f / V); per-block partials of sum V |R|^2 (rho, rho
+// u, rho E), of the mass after the base step sum V (rho + dtl R_rho) and of
+// the current mass sum V rho
 template <bool DI>
 __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
   if (C.scal->done) return;
-  double dmin = 1e300, rs = 0.0;
+  double rs = 0.0, mx = 0.0, m0 = 0.0;
   if (c < n) {
     double Pc[6], Uc[6];
     for (int q = 0; q < 6; ++q) {
@@ -735,73 +745,293 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
       Rc[5] = 0.0;
     }
     for (int q = 0; q < 6; ++q) C.R[(size_t)q * n + c] = Rc[q];
-    dmin = 0.5 * V / lam_sum;
+    const double dt = C.cfl * (V / lam_sum);
+    C.dtl[c] = dt;
     for (int q = 0; q < 5; ++q) rs += V * Rc[q] * Rc[q];
+    mx = V * (Uc[0] + dt * Rc[0]);
+    m0 = V * Uc[0];
   }
-  __shared__ double sm[CPT / 32], ss[CPT / 32];
+  __shared__ double sr[3][CPT / 32];
   for (int o = 16; o > 0; o >>= 1) {
-    dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
     rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    mx += __shfl_xor_sync(0xffffffffu, mx, o);
+    m0 += __shfl_xor_sync(0xffffffffu, m0, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    sm[threadIdx.x >> 5] = dmin;
-    ss[threadIdx.x >> 5] = rs;
+    sr[0][threadIdx.x >> 5] = rs;
+    sr[1][threadIdx.x >> 5] = mx;
+    sr[2][threadIdx.x >> 5] = m0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < CPT / 32; ++w) {
-      sm[0] = fmin(sm[0], sm[w]);
-      ss[0] += ss[w];
-    }
-    C.part[2 * blockIdx.x] = sm[0];
-    C.part[2 * blockIdx.x + 1] = ss[0];
+  if (threadIdx.x < 3) {
+    double a = sr[threadIdx.x][0];
+    for (int w = 1; w < CPT / 32; ++w) a += sr[threadIdx.x][w];
+    C.part[3 * blockIdx.x + threadIdx.x] = a;
   }
 }
 
-// global step, residual norm and the stopping test (one block)
-__global__ void k_cp_reduce(CoupleParams C, int nblocks, int it, double eps) {
+// residual norm, the stopping test and the mass-restoring factor of the base
+// step (one block); the first iteration also records the initial mass
+__global__ void k_cp_reduce(CoupleParams C, int nblocks) {
   if (C.scal->done) return;
-  __shared__ double sm[1024], ss[1024];
-  double dmin = 1e300, rs = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    dmin = fmin(dmin, C.part[2 * b]);
-    rs += C.part[2 * b + 1];
-  }
-  sm[threadIdx.x] = dmin;
-  ss[threadIdx.x] = rs;
+  __shared__ double sh[3][1024];
+  double a[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int k = 0; k < 3; ++k) a[k] += C.part[3 * b + k];
+  for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] = a[k];
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + s]);
-      ss[threadIdx.x] += ss[threadIdx.x + s];
-    }
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double res = sqrt(ss[0]);
-    if (it == 0) C.scal->res0 = res > 0 ? res : 1.0;
-    C.scal->res = res;
-    C.scal->iters = it;
-    C.scal->dtg = sm[0];
-    if (!isfinite(res) || res <= eps * C.scal->res0) C.scal->done = 1;
+    CoupleScalars* S = C.scal;
+    const int it = S->itc;
+    const double res = sqrt(sh[0][0]);
+    if (it == 0) {
+      S->res0 = res > 0 ? res : 1.0;
+      S->M0 = sh[2][0];
+    }
+    S->res = res;
+    S->iters = it;
+    if (!isfinite(res) || res <= C.eps_m * S->res0) {
+      S->done = 1;
+    } else {
+      S->mscale = C.closed ? S->M0 / sh[1][0] : 1.0;
+      if (S->aabad) {  // the last combination fell back to the base step: restart the history
+        S->nh = 0;
+        S->aabad = 0;
+      }
+      S->itc = it + 1;
+    }
   }
 }
 
-__global__ void k_cp_update(Params P, CoupleParams C) {
+// Base step g(U) = s (U + dtl R) of every cell (s restores the total mass of
+// a closed domain), f = g(U) - U; with Anderson acceleration the new
+// differences dF_new, dG_new of f and g(U) go to ring slot `head`, and the
+// block's partial (volume-weighted) dot products <dF_i, dF_new> of every held
+// column i in age order (the new one last) and <dF_new, f> go to apart;
+// without it U = g(U).
+template <bool DI>
+__global__ void __launch_bounds__(CPT) k_aa_base(Params P, CoupleParams C) {
+  constexpr int NV = DI ? 6 : 5;  // conserved variables carried (rho e_r only for a diatomic gas)
+  __shared__ double red[CPT / 32][AA_MAX + 1];
+  const CoupleScalars* S = C.scal;
+  if (S->done) return;
+  const int n = P.n_cells;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = c < n;
+  const int m = C.aa_m;
+  const int it = S->itc - 1;
+  const bool push = it > 0 && m > 0;
+  const int head = S->head;
+  const int nhn = push ? min(S->nh + 1, m) : 0;
+  const int hn = (head + 1) % (m > 0 ? m : 1);
+  const double s = S->mscale;
+  double f[6] = {0, 0, 0, 0, 0, 0}, dfn[6] = {0, 0, 0, 0, 0, 0};
+  if (in) {
+    const double dt = C.dtl[c];
+    for (int q = 0; q < NV; ++q) {
+      const size_t k = (size_t)q * n + c;
+      const double u = C.U[k];
+      double gx = u + dt * C.R[k];
+      if (C.closed) gx *= s;
+      if (m == 0) {
+        C.U[k] = gx;
+        continue;
+      }
+      const double fq = gx - u;
+      if (push) {
+        const size_t h = ((size_t)head * 6 + q) * n + c;
+        dfn[q] = fq - C.fp[k];
+        C.dF[h] = dfn[q];
+        C.dG[h] = gx - C.Gp[k];
+      }
+      C.fp[k] = fq;
+      C.Gp[k] = gx;
+      f[q] = fq;
+    }
+  }
+  if (!push) return;
+  const double V = in ? C.vnd[c] : 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i <= nhn; ++i) {
+    double h = 0.0;
+    if (in) {
+      double r = 0.0;
+      if (i < nhn - 1) {
+        const int sl = ((hn - nhn + i) % m + m) % m;
+        for (int q = 0; q < NV; ++q) r += C.dF[((size_t)sl * 6 + q) * n + c] * dfn[q];
+      } else if (i == nhn - 1) {
+        for (int q = 0; q < NV; ++q) r += dfn[q] * dfn[q];
+      } else {
+        for (int q = 0; q < NV; ++q) r += dfn[q] * f[q];
+      }
+      h = V * r;
+    }
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if (lane == 0) red[warp][i] = h;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t <= nhn) {
+    double a = red[0][t];
+    for (int w = 1; w < CPT / 32; ++w) a += red[w][t];
+    C.apart[(size_t)(t < nhn ? t : AA_MAX) * gridDim.x + blockIdx.x] = a;
+  }
+}
+
+// Anderson coefficients (one block): the block partials summed, the new
+// column's row of the Gram matrix stored, then gamma minimising
+// |f - dF gamma| from the normal equations of the columns scaled to unit
+// norm with 1e-10 added to the diagonal, by Cholesky (one warp, lane i owning
+// row i; a failed factorisation uses no column)
+__global__ void k_aa_solve(CoupleParams C, int nblocks) {
+  __shared__ double val[AA_MAX + 1];
+  __shared__ double L[AA_MAX][AA_MAX + 1];
+  __shared__ int sl[AA_MAX];
+  CoupleScalars* S = C.scal;
+  if (S->done) return;
+  const int m = C.aa_m;
+  const int it = S->itc - 1;
+  const bool push = it > 0;
+  const int head = S->head;
+  const int nhn = push ? min(S->nh + 1, m) : S->nh;
+  const int hn = push ? (head + 1) % m : head;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int k = nhn;
+  // the stored Gram matrix in age order (before the new row arrives; its
+  // row and column are overwritten below), loaded by the whole block
+  if (threadIdx.x < AA_MAX) sl[threadIdx.x] = threadIdx.x < k ? ((hn - k + (int)threadIdx.x) % m + m) % m : 0;
+  __syncthreads();
+  AAState* A = C.aa;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    L[i][j] = A->H[sl[i] * AA_MAX + sl[j]];
+  }
+  // block partials, four independent sums per lane: <dF_i, dF_new> at j < k,
+  // <dF_new, f> at j = AA_MAX
+  for (int j = warp; j <= AA_MAX; j += nw) {
+    if (!push || (j < AA_MAX && j >= nhn)) continue;
+    const double* pj = C.apart + (size_t)j * nblocks;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nblocks; b += 128) {
+      a0 += pj[b];
+      a1 += pj[b + 32];
+      a2 += pj[b + 64];
+      a3 += pj[b + 96];
+    }
+    for (; b < nblocks; b += 32) a0 += pj[b];
+    double a = (a0 + a1) + (a2 + a3);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) val[j] = a;
+  }
+  __syncthreads();
+  if (push && threadIdx.x < k) {  // the new column (newest, age k - 1) against every held column
+    const int i = threadIdx.x;
+    const double h = val[i];
+    A->H[head * AA_MAX + sl[i]] = h;
+    A->H[sl[i] * AA_MAX + head] = h;
+    L[k - 1][i] = h;
+    L[i][k - 1] = h;
+    // b_i = <dF_i, f_k> = <dF_i, f_{k-1}> + <dF_i, dF_new>; the new column's is computed
+    A->b[sl[i]] = i == k - 1 ? val[AA_MAX] : A->b[sl[i]] + h;
+  }
+  if (threadIdx.x == 0) {
+    S->head = hn;
+    S->nh = k;
+  }
+  __syncthreads();
+  // scaled, regularised normal matrix: thread (ti, tq) owns entry (ti, tq)
+  __shared__ double scs[AA_MAX];
+  __shared__ int okf;
+  const int ti = threadIdx.x >> 5, tq = threadIdx.x & 31;
+  if (threadIdx.x < k) {
+    const double d = L[threadIdx.x][threadIdx.x];
+    scs[threadIdx.x] = d > 0 ? 1.0 / sqrt(d) : 0.0;
+  }
+  __syncthreads();
+  if (ti < k && tq < k) L[ti][tq] = L[ti][tq] * scs[ti] * scs[tq] + (ti == tq ? 1e-10 : 0.0);
+  __syncthreads();
+  // right-looking Cholesky: every entry receives its updates in the order of
+  // the left-looking form (column 0 first), then the division by its pivot
+  bool ok = true;
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = L[j][j];
+      okf = d > 0;
+      if (d > 0) L[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    if (!okf) {
+      ok = false;
+      break;
+    }
+    if (tq == j && ti > j && ti < k) L[ti][j] /= L[j][j];
+    __syncthreads();
+    if (ti > j && ti < k && tq > j && tq <= ti) L[ti][tq] -= L[ti][j] * L[tq][j];
+    __syncthreads();
+  }
+  if (warp != 0) return;
+  const double sci = lane < k ? scs[lane] : 0.0;
+  const double bi = lane < k ? A->b[sl[lane]] * sci : 0.0;
+  if (ok) {
+    // L y = b, then L^T g = y; lane i keeps y_i and g_i
+    double yi = 0.0, gi = 0.0;
+    for (int i = 0; i < k; ++i) {
+      double t = lane < i ? L[i][lane] * yi : 0.0;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      const double y = (__shfl_sync(0xffffffffu, bi, i) - t) / L[i][i];
+      if (lane == i) yi = y;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double t = lane > i && lane < k ? L[lane][i] * gi : 0.0;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      const double g = (__shfl_sync(0xffffffffu, yi, i) - t) / L[i][i];
+      if (lane == i) gi = g;
+    }
+    if (lane < k) {
+      A->gam[lane] = gi * sci;
+      A->slot[lane] = sl[lane];
+    }
+  }
+  if (lane == 0) S->k = ok ? k : 0;
+}
+
+// the combination U = g(U_k) - sum_i gamma_i dG_i; a cell whose combined
+// density or temperature is not positive flags the fallback
+template <bool DI>
+__global__ void k_aa_update(Params P, CoupleParams C) {
+  constexpr int NV = DI ? 6 : 5;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
   if (c >= n || C.scal->done) return;
-  const double dt = C.scal->dtg;
-  for (int q = 0; q < 6; ++q) C.U[(size_t)q * n + c] += dt * C.R[(size_t)q * n + c];
+  const int k = C.scal->k;
+  double U[6] = {0, 0, 0, 0, 0, 0}, Pp[6];
+  for (int q = 0; q < NV; ++q) {
+    double x = C.Gp[(size_t)q * n + c];
+    for (int j = 0; j < k; ++j) x -= C.aa->gam[j] * C.dG[((size_t)C.aa->slot[j] * 6 + q) * n + c];
+    U[q] = x;
+    C.U[(size_t)q * n + c] = x;
+  }
+  prim_from_cons(C, U, Pp);
+  if (!(Pp[0] > 0.0 && Pp[4] > 0.0)) C.scal->aabad = 1;
 }
 
-__global__ void k_cp_final(Params P, CoupleParams C, int N_m) {
+__global__ void k_cp_final(Params P, CoupleParams C) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
-  if (c == 0 && !C.scal->done) C.scal->iters = N_m;
+  if (c == 0 && !C.scal->done) C.scal->iters = C.scal->itc;
   if (c >= n) return;
   double U[6], Pp[6];
-  for (int q = 0; q < 6; ++q) U[q] = C.U[(size_t)q * n + c];
+  const bool fb = C.scal->aabad != 0;  // N_m reached right after a failed combination
+  for (int q = 0; q < 6; ++q) {
+    const size_t k = (size_t)q * n + c;
+    U[q] = fb && (q < 5 || C.dr > 0) ? C.Gp[k] : C.U[k];
+  }
   prim_from_cons(C, U, Pp);
   for (int q = 0; q < 6; ++q) C.newst[(size_t)q * n + c] = Pp[q];
   if (!(Pp[0] > 0.0) || !(Pp[4] > 0.0) || !isfinite(Pp[0]) || !isfinite(Pp[4])) C.scal->bad = 1;
@@ -1064,25 +1294,41 @@ void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const 
   g_launches += 3 + passes + DIG_FILL_LAYERS;
 }
 
-void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double eps, cudaStream_t s) {
+void launch_couple_s10_init(const Params& P, const CoupleParams& C, cudaStream_t s) {
   const int n = P.n_cells, nb = nb_for(n, CPT);
   k_cp_init_cons<<<nb, CPT, 0, s>>>(P, C);
-  for (int it = 0; it < N_m; ++it) {
-    k_cp_prim<<<nb, CPT, 0, s>>>(P, C, it > 0);
-    if (C.dr > 0) {
-      k_cp_grad_stress<true><<<nb, CPT, 0, s>>>(P, C);
-      if (C.n_ifaces > 0) k_cp_face<true><<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
-      k_cp_flux<true><<<nb, CPT, 0, s>>>(P, C);
-    } else {
-      k_cp_grad_stress<false><<<nb, CPT, 0, s>>>(P, C);
-      if (C.n_ifaces > 0) k_cp_face<false><<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
-      k_cp_flux<false><<<nb, CPT, 0, s>>>(P, C);
-    }
-    k_cp_reduce<<<1, 1024, 0, s>>>(C, nb, it, eps);
+  g_launches += 1;
+}
+
+template <bool DI>
+static void s10_iteration(const Params& P, const CoupleParams& C, int nb, cudaStream_t s) {
+  k_cp_prim<<<nb, CPT, 0, s>>>(P, C);
+  k_cp_grad_stress<DI><<<nb, CPT, 0, s>>>(P, C);
+  if (C.n_ifaces > 0) k_cp_face<DI><<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
+  k_cp_flux<DI><<<nb, CPT, 0, s>>>(P, C);
+  k_cp_reduce<<<1, 1024, 0, s>>>(C, nb);
+  k_aa_base<DI><<<nb, CPT, 0, s>>>(P, C);
+  g_launches += C.n_ifaces > 0 ? 6 : 5;
+  if (C.aa_m > 0) {
+    k_aa_solve<<<1, 1024, 0, s>>>(C, nb);
+    k_aa_update<DI><<<nb, CPT, 0, s>>>(P, C);
+    g_launches += 2;
   }
-  if (N_m > 0) k_cp_update<<<nb, CPT, 0, s>>>(P, C);
-  k_cp_final<<<nb, CPT, 0, s>>>(P, C, N_m);
-  g_launches += 3 + 5LL * N_m;
+}
+
+void launch_couple_s10_iters(const Params& P, const CoupleParams& C, int iters, cudaStream_t s) {
+  const int nb = nb_for(P.n_cells, CPT);
+  for (int it = 0; it < iters; ++it) {
+    if (C.dr > 0)
+      s10_iteration<true>(P, C, nb, s);
+    else
+      s10_iteration<false>(P, C, nb, s);
+  }
+}
+
+void launch_couple_s10_final(const Params& P, const CoupleParams& C, cudaStream_t s) {
+  k_cp_final<<<nb_for(P.n_cells, CPT), CPT, 0, s>>>(P, C);
+  g_launches += 1;
 }
 
 void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, int N, uint32_t sub, int* cl,
@@ -1119,6 +1365,7 @@ void launch_closure_targets(const Params& P, const CoupleParams& C, const double
   }
 }
 
-size_t couple_part_count(int n_cells) { return 2 * (size_t)nb_for(n_cells, CPT) + 2; }
+size_t couple_part_count(int n_cells) { return 3 * (size_t)nb_for(n_cells, CPT) + 2; }
+size_t couple_apart_count(int n_cells) { return (size_t)(AA_MAX + 1) * nb_for(n_cells, CPT); }
 
 }  // namespace dig

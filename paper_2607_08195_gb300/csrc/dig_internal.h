@@ -119,10 +119,30 @@ struct Params {
   long long cap;
 };
 
-// DIG coupling state (dig_couple.cu); arrays are [component][cell]
+// DIG coupling state (dig_couple.cu); arrays are [component][cell].
+// The scalars of one solve; cleared before every coupling.
 struct CoupleScalars {
-  double res0, res, dtg;
-  int iters, done, bad, pad;
+  double res0, res;
+  double M0;      // total mass of the initial state (closed domains)
+  double mscale;  // mass-restoring factor of the current base step (1 for open domains)
+  int iters, done, bad;
+  int itc;        // index of the next iteration
+  int head, nh;   // Anderson history: next slot to write, columns held
+  int aabad;      // a combined state was not positive: fall back to the base step
+  int k;          // columns used by the current combination (0: base step)
+};
+
+// most Anderson-acceleration columns
+constexpr int AA_MAX = 32;
+
+// Anderson-acceleration state of the synthetic solve: Gram matrix of the
+// stored residual differences (indexed by ring slot), and the coefficients
+// and slots of the current combination in age order (oldest first)
+struct AAState {
+  double H[AA_MAX * AA_MAX];
+  double b[AA_MAX];  // <dF_i, f_k> by ring slot
+  double gam[AA_MAX];
+  int slot[AA_MAX];
 };
 
 // most fill layers after the reconstruction layers (see k_cp_recon)
@@ -154,6 +174,15 @@ struct CoupleParams {
   unsigned long long* stats;  // rejected, reconstructed, cloned, deleted, learned
   int* fillcnt;               // [DIG_FILL_LAYERS] cells filled per fill layer
   CoupleScalars* scal;
+  // synthetic solve (S10): iteration limits, local pseudo-time steps and the
+  // Anderson acceleration
+  int N_m, aa_m, closed;  // closed: no open boundary face (the solve restores the total mass)
+  double eps_m, cfl;
+  double* dtl;    // [n] cfl times the cell's CFL-1 pseudo-time step
+  double *fp, *Gp;    // [6][n] previous f = g(U) - U and g(U) (Gp holds g(U_k) during an iteration)
+  double *dF, *dG;    // [aa_m][6][n] differences of consecutive f and g(U)
+  double* apart;      // [AA_MAX + 1][blocks] per-block dot products
+  AAState* aa;
   int* rpart;
   int* clone_total;
 };
@@ -175,10 +204,16 @@ void launch_mlp_loss(const float* params, const float* X, const float* T, long l
 void launch_adam(float* p, float* m, float* v, float* g, long long t, float lr, float b1, float b2, float eps,
                  cudaStream_t s);
 void launch_mlp_init(const Params& P, uint64_t seed, float* params, cudaStream_t s);
-void launch_couple_s10(const Params& P, const CoupleParams& C, int N_m, double eps, cudaStream_t s);
+// S10: the initial conserved state, then `iters` solver iterations (each stops
+// early once the solve is done: its state lives on the device), or the final
+// primitives (final = true, iters ignored)
+void launch_couple_s10_init(const Params& P, const CoupleParams& C, cudaStream_t s);
+void launch_couple_s10_iters(const Params& P, const CoupleParams& C, int iters, cudaStream_t s);
+void launch_couple_s10_final(const Params& P, const CoupleParams& C, cudaStream_t s);
 void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, int N, uint32_t sub, int* cl,
                        cudaStream_t s);
 size_t couple_part_count(int n_cells);
+size_t couple_apart_count(int n_cells);
 
 // launchers (dig_kernels.cu)
 void launch_init(const Params& P, const Buf& out, int n, cudaStream_t s);

@@ -40,6 +40,7 @@ class DigConfig(C.Structure):
         ("passes", C.c_int32), ("eps_m", C.c_double), ("KnD_max", C.c_double), ("capacity", C.c_int64),
         ("wait_timeout_s", C.c_double), ("stage_cap", C.c_int32), ("tile_cells", C.c_int32),
         ("cta_threads", C.c_int32), ("closure", C.c_int32), ("recon", C.c_int32), ("local_acc", C.c_int32),
+        ("aa_m", C.c_int32), ("cfl", C.c_double),
     ]
 
 
@@ -135,6 +136,7 @@ def make_config(scen, **over) -> DigConfig:
     cfg.Kn, cfg.L_ref = scen.Kn, scen.L
     cfg.n_a, cfg.N_s, cfg.N_m, cfg.passes = 1000, 100, 500, 3
     cfg.eps_m, cfg.KnD_max = 1e-6, 1.0
+    cfg.aa_m, cfg.cfl = 20, 1.5
     cfg.capacity = scen.capacity or 2 * scen.n_particles
     cfg.wait_timeout_s = 600.0
     for k, v in over.items():

@@ -40,10 +40,37 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
-def test_config_struct_layout():
-    # field order and sizes of dig_config as in include/dig.h (no padding surprises)
-    assert ctypes.sizeof(dig.DigConfig) == 8 * 6 + 4 * 2 + 8 * 3 + 8 + 8 + 8 * 3 + 8 * 3 + 4 * 4 + 8 * 2 + 8 + 8 + 4 * 2 + 4 * 2 + 4 * 2
-    assert ctypes.sizeof(dig.DigBC) == 48
+def _c_layout(struct, fields):
+    """sizeof and offsetof of every field of a struct of include/dig.h, from the C compiler."""
+    import shutil
+    import subprocess
+    import tempfile
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src = ("#include <stddef.h>\n#include <stdio.h>\n#include \"dig.h\"\nint main(void) {\n"
+           f'  printf("%zu\\n", sizeof({struct}));\n' + body + "  return 0;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.check_call([cc, "-I", inc, c, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).split()]
+    return out[0], out[1:]
+
+
+@pytest.mark.parametrize("struct, cls", [("dig_config", "DigConfig"), ("dig_bc", "DigBC"),
+                                         ("dig_couple_report", "CoupleReport")])
+def test_struct_layout_matches_header(struct, cls):
+    """The binding's ctypes mirrors have the size and field offsets that the C
+    compiler gives the structs of include/dig.h."""
+    py = getattr(dig, cls)
+    names = [f for f, _ in py._fields_]
+    size, offs = _c_layout(struct, names)
+    assert ctypes.sizeof(py) == size
+    assert [getattr(py, f).offset for f in names] == offs
 
 
 def test_create_rejects_bad_config(lib):
@@ -56,7 +83,8 @@ def test_create_rejects_bad_config(lib):
         cfg = dig.make_config(W.config_small())
         cfg.alpha = alpha
         assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == -1, alpha
-    for field, value in (("recon", 2), ("local_acc", -1), ("tile_cells", 4096), ("rot_dof", 1)):
+    for field, value in (("recon", 2), ("local_acc", -1), ("tile_cells", 4096), ("rot_dof", 1), ("aa_m", -1),
+                         ("aa_m", 33)):
         cfg = dig.make_config(W.config_small())
         setattr(cfg, field, value)
         assert lib.dig_create(ctypes.byref(cfg), ctypes.byref(h)) == -1, field

@@ -244,3 +244,46 @@ def test_trained_closure_beats_window_average():
     g.step(wsteps, dig.EWMA | dig.WINDOW | dig.WALLFLUX)
     r = g.couple()
     assert r["n_learned"] > 0.9 * n and r["iters"] > 0
+
+
+def flow_windows(U_lid, seed, nwin=60, wsteps=25):
+    """Closure inputs (25-step windows) and targets (the long-time average's
+    HoT) of the 6^3-hexahedra Kn = 0.1 cavity with lid speed U_lid."""
+    s = W.cavity_scenario(6, 130_000, 0.1, seed=seed, U_lid=U_lid)
+    g = dig.Solver(s, DEV, N_m=100)
+    g.init()
+    g.step(600, dig.EWMA)
+    g.sample(dig.RESET_CUMUL)
+    n = g.n_tets
+    X = torch.empty((nwin * n, 13), dtype=torch.float32, device=DEV)
+    for w in range(nwin):
+        g.sample(dig.RESET_WINDOW)
+        g.step(wsteps, dig.EWMA | dig.WINDOW | dig.CUMUL)
+        g.closure_features(dig.PHI_WINDOW, X[w * n:(w + 1) * n])
+    Y = g.closure_targets(dig.PHI_CUM, X)
+    return g, X, Y
+
+
+def test_trained_closure_transfers_to_another_flow():
+    """S13 without leakage: the closure trained on two other flows of the
+    cavity (lid 30 and 70 m/s, their own seeds) lowers the error of the HoT
+    against the long-time average on the windows of a third flow it never saw
+    (lid 50 m/s, another seed), compared with the window HoT itself."""
+    Xs, Ys = [], []
+    for U_lid, seed in ((30.0, 41), (70.0, 43)):
+        g, X, Y = flow_windows(U_lid, seed)
+        Xs.append(X)
+        Ys.append(Y)
+        g.close()
+    X, Y = torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
+    gt, Xt, Yt = flow_windows(50.0, 47, nwin=20)
+    gt.closure_init(5)
+    epochs = 8
+    rng = np.random.default_rng(6)
+    perm = torch.from_numpy(np.stack([rng.permutation(len(X)) for _ in range(epochs)]).astype(np.int32)).to(DEV)
+    loss = gt.closure_train(X, Y, epochs=epochs, batch=512, lr=2e-3, perm=perm)
+    assert loss[-1] < 0.5 * loss[0], loss
+    net = gt.closure_loss(Xt.contiguous(), Yt.contiguous())
+    raw = gt.closure_loss(Xt.contiguous(), Yt.contiguous(), identity=True)
+    print(f"closure transfer: held-out-flow MSE net {net:.3e} vs window HoT {raw:.3e} (ratio {net / raw:.3f})")
+    assert net < 0.7 * raw, (net, raw)
