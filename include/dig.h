@@ -416,9 +416,11 @@ int dig_sort_by_cell(const int32_t* cell, int64_t n, int32_t n_cells, int32_t* c
  * n_cells <= DIG_NOALLOC_MAX_CELLS; larger sizes return DIG_ERR_CAPACITY
  * (message in dig_last_error(NULL)) without launching anything.  The call
  * allocates nothing.  All calls share the array: calls whose GPU work overlaps
- * (other streams, other threads) race and give wrong results.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make it before capturing any stream on that device.
+ * (other streams, other threads) race and give wrong results.  Every call
+ * looks up the array's device address (cudaGetSymbolAddress) for the device
+ * current at the call, so it stays right after the context is destroyed and
+ * made again; the first call on a device loads the library's module there:
+ * make it before capturing any stream on that device.
  */
 #define DIG_NOALLOC_MAX_N 4194304
 #define DIG_NOALLOC_MAX_CELLS 1048576

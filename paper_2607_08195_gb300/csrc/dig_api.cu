@@ -1130,8 +1130,24 @@ struct CkptHeader {
   // host state
   int64_t cur, N, have_particles, step, n_ewma, n_win, n_cum, host_steps, flux_steps, n_couple, cl_set, adam_t,
       tile_cells;
+  dig_config cfg;  // the configuration the state was made under (after dig_create's defaults)
 };
-const char kMagic[8] = {'D', 'I', 'G', 'C', 'K', 'P', 'T', '1'};
+const char kMagic[8] = {'D', 'I', 'G', 'C', 'K', 'P', 'T', '2'};
+
+// the first field that changes results and differs between two
+// configurations (nullptr: none); launch shapes and the host wait limit do not
+// change results and are not compared
+const char* config_mismatch(const dig_config& a, const dig_config& b) {
+#define DIG_CMP(f) \
+  if (!(a.f == b.f)) return #f;
+  DIG_CMP(mass) DIG_CMP(d_ref) DIG_CMP(omega) DIG_CMP(T_ref) DIG_CMP(alpha) DIG_CMP(Z_rot) DIG_CMP(rot_dof)
+  DIG_CMP(max_cross) DIG_CMP(F_N) DIG_CMP(dt) DIG_CMP(seed) DIG_CMP(n_init) DIG_CMP(T_init) DIG_CMP(u_init[0])
+  DIG_CMP(u_init[1]) DIG_CMP(u_init[2]) DIG_CMP(mu_ref) DIG_CMP(Kn) DIG_CMP(L_ref) DIG_CMP(n_a) DIG_CMP(N_s)
+  DIG_CMP(N_m) DIG_CMP(passes) DIG_CMP(eps_m) DIG_CMP(KnD_max) DIG_CMP(capacity) DIG_CMP(closure) DIG_CMP(recon)
+  DIG_CMP(local_acc) DIG_CMP(aa_m) DIG_CMP(cfl)
+#undef DIG_CMP
+  return nullptr;
+}
 }  // namespace
 
 int dig_checkpoint_bytes(dig_ctx* ctx, int64_t* bytes) {
@@ -1147,7 +1163,7 @@ int dig_save(dig_ctx* ctx, void* host_out, int64_t cap) {
   if (cap < (int64_t)sizeof(CkptHeader) + ctx->arena_bytes) return fail(ctx, DIG_ERR_CAPACITY, "dig_save: buffer too small");
   CkptHeader h{};
   std::memcpy(h.magic, kMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.n_tets = ctx->n_tets;
   h.capacity = ctx->cfg.capacity;
   h.arena_bytes = ctx->arena_bytes;
@@ -1169,6 +1185,7 @@ int dig_save(dig_ctx* ctx, void* host_out, int64_t cap) {
   h.cl_set = ctx->cl_set;
   h.adam_t = ctx->adam_t;
   h.tile_cells = ctx->tile_cells;
+  h.cfg = ctx->cfg;
   int rc = wait_stream(ctx);
   if (rc) return rc;
   std::memcpy(host_out, &h, sizeof h);
@@ -1183,11 +1200,16 @@ int dig_load(dig_ctx* ctx, const void* host_in, int64_t size) {
   if (size < (int64_t)sizeof(CkptHeader)) return fail(ctx, DIG_ERR_ARG, "dig_load: not a checkpoint");
   CkptHeader h;
   std::memcpy(&h, host_in, sizeof h);
-  if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(ctx, DIG_ERR_ARG, "dig_load: not a checkpoint");
+  if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 2) return fail(ctx, DIG_ERR_ARG, "dig_load: not a checkpoint");
   if (h.n_tets != ctx->n_tets || h.capacity != ctx->cfg.capacity || h.arena_bytes != ctx->arena_bytes ||
       h.rot_dof != ctx->cfg.rot_dof || h.mass != ctx->cfg.mass || h.dt != ctx->cfg.dt || h.F_N != ctx->cfg.F_N ||
       h.seed != ctx->cfg.seed)
     return fail(ctx, DIG_ERR_STATE, "dig_load: checkpoint of a different configuration or mesh");
+  if (const char* f = config_mismatch(h.cfg, ctx->cfg)) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "dig_load: checkpoint made with a different dig_config.%s", f);
+    return fail(ctx, DIG_ERR_STATE, msg);
+  }
   if (size < (int64_t)sizeof h + h.arena_bytes) return fail(ctx, DIG_ERR_ARG, "dig_load: truncated checkpoint");
   int rc = wait_stream(ctx);
   if (rc) return rc;
@@ -1206,6 +1228,7 @@ int dig_load(dig_ctx* ctx, const void* host_in, int64_t size) {
   ctx->flux_steps = h.flux_steps;
   ctx->n_couple = h.n_couple;
   ctx->cl_set = h.cl_set != 0;
+  if (ctx->have_particles) choose_tile(ctx);  // tiles sized for the restored particle count
   ctx->adam_t = h.adam_t;
   ctx->tile_cells = (int)h.tile_cells;
   return DIG_OK;
@@ -1230,17 +1253,14 @@ static int run_s10(dig_ctx* ctx) {
   if (!ctx->s10_exec) {
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
-      const long long before = g_launches;
       cudaGraph_t gr = nullptr;
       if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        launch_couple_s10_iters(ctx->P, ctx->C, S10_CHUNK, cs);
+        ctx->s10_launches = launch_couple_s10_iters(ctx->P, ctx->C, S10_CHUNK, cs);
         if (cudaStreamEndCapture(cs, &gr) == cudaSuccess && gr) {
           if (cudaGraphInstantiate(&ctx->s10_exec, gr, 0) != cudaSuccess) ctx->s10_exec = nullptr;
           cudaGraphDestroy(gr);
         }
       }
-      ctx->s10_launches = g_launches - before;
-      g_launches = before;
       cudaStreamDestroy(cs);
     }
     (void)cudaGetLastError();  // a refused capture leaves its error here
@@ -1252,7 +1272,7 @@ static int run_s10(dig_ctx* ctx) {
       CK(cudaGraphLaunch(ctx->s10_exec, s));
       g_launches += ctx->s10_launches;
     } else {
-      launch_couple_s10_iters(ctx->P, ctx->C, S10_CHUNK, s);
+      g_launches += launch_couple_s10_iters(ctx->P, ctx->C, S10_CHUNK, s);
     }
     int done = 0;
     CK(cudaMemcpyAsync(&done, &ctx->C.scal->done, sizeof(int), cudaMemcpyDeviceToHost, s));

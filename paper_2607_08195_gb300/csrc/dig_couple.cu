@@ -10,6 +10,7 @@
 // T_t^omega (the paper's Kn definition); kappa_t = 15/4 mu, kappa_r = 1.32 mu.
 // Arrays are component-major, [component][cell].
 #include "dig_internal.h"
+#include "dig_philox.cuh"
 
 namespace dig {
 
@@ -1040,32 +1041,6 @@ __global__ void k_cp_final(Params P, CoupleParams C) {
 // ---------------------------------------------------------------------------
 // S11 recalibration of the particles of accepted cells
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void philox_c(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                         uint32_t k1, uint32_t (&w)[4]) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0;
-    c1 = lo1;
-    c2 = n2;
-    c3 = lo0;
-  }
-  w[0] = c0;
-  w[1] = c1;
-  w[2] = c2;
-  w[3] = c3;
-}
-
-__device__ __forceinline__ double u01d_c(uint32_t w0, uint32_t w1) {
-  const unsigned long long k = ((unsigned long long)(w0 >> 4) << 24) | (unsigned long long)(w1 >> 8);
-  return ((double)k + 0.5) * 2.220446049250313080847e-16;
-}
 
 struct RecalCell {
   float ua[3], ub[3], sc, fr;
@@ -1116,8 +1091,8 @@ __global__ void k_recal_decide(Params P, CoupleParams C, Buf CUR, int* __restric
         CUR.vz[p] = __fadd_rn(r.ua[2], __fmul_rn(__fsub_rn(CUR.vz[p], r.ub[2]), r.sc));
         if (C.dr > 0) CUR.Ir[p] = __fmul_rn(CUR.Ir[p], r.fr);
         uint32_t w[4];
-        philox_c((uint32_t)p, sub, 0u, 0u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w);
-        const double R = u01d_c(w[0], w[1]);
+        philox((uint32_t)p, sub, 0u, 0u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w);
+        const double R = u01d(w[0], w[1]);
         if (r.rn < 1.0) {
           if (R < 1.0 - r.rn) keep = false;
         } else if (r.rn > 1.0 && R < r.rn - 1.0) {
@@ -1222,9 +1197,9 @@ __global__ void k_recal_clone(Params P, CoupleParams C, Buf CUR, const int* __re
       const long long q = (long long)N + r;
       if (q >= hi) continue;
       uint32_t w[4], w2[4];
-      philox_c((uint32_t)p, sub, 0u, 1u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w);
-      philox_c((uint32_t)p, sub, 0u, 2u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w2);
-      double s = u01d_c(w[0], w[1]), tt = u01d_c(w[2], w[3]), u = u01d_c(w2[0], w2[1]);
+      philox((uint32_t)p, sub, 0u, 1u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w);
+      philox((uint32_t)p, sub, 0u, 2u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w2);
+      double s = u01d(w[0], w[1]), tt = u01d(w[2], w[3]), u = u01d(w2[0], w2[1]);
       if (s + tt > 1.0) {
         s = 1.0 - s;
         tt = 1.0 - tt;
@@ -1301,29 +1276,27 @@ void launch_couple_s10_init(const Params& P, const CoupleParams& C, cudaStream_t
 }
 
 template <bool DI>
-static void s10_iteration(const Params& P, const CoupleParams& C, int nb, cudaStream_t s) {
+static long long s10_iteration(const Params& P, const CoupleParams& C, int nb, cudaStream_t s) {
   k_cp_prim<<<nb, CPT, 0, s>>>(P, C);
   k_cp_grad_stress<DI><<<nb, CPT, 0, s>>>(P, C);
   if (C.n_ifaces > 0) k_cp_face<DI><<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
   k_cp_flux<DI><<<nb, CPT, 0, s>>>(P, C);
   k_cp_reduce<<<1, 1024, 0, s>>>(C, nb);
   k_aa_base<DI><<<nb, CPT, 0, s>>>(P, C);
-  g_launches += C.n_ifaces > 0 ? 6 : 5;
+  long long k = C.n_ifaces > 0 ? 6 : 5;
   if (C.aa_m > 0) {
     k_aa_solve<<<1, 1024, 0, s>>>(C, nb);
     k_aa_update<DI><<<nb, CPT, 0, s>>>(P, C);
-    g_launches += 2;
+    k += 2;
   }
+  return k;
 }
 
-void launch_couple_s10_iters(const Params& P, const CoupleParams& C, int iters, cudaStream_t s) {
+long long launch_couple_s10_iters(const Params& P, const CoupleParams& C, int iters, cudaStream_t s) {
   const int nb = nb_for(P.n_cells, CPT);
-  for (int it = 0; it < iters; ++it) {
-    if (C.dr > 0)
-      s10_iteration<true>(P, C, nb, s);
-    else
-      s10_iteration<false>(P, C, nb, s);
-  }
+  long long k = 0;
+  for (int it = 0; it < iters; ++it) k += C.dr > 0 ? s10_iteration<true>(P, C, nb, s) : s10_iteration<false>(P, C, nb, s);
+  return k;
 }
 
 void launch_couple_s10_final(const Params& P, const CoupleParams& C, cudaStream_t s) {

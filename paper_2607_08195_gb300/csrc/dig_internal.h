@@ -1,6 +1,7 @@
 // dig_internal.h -- structures shared by the host API (dig_api.cu) and the
 // kernels (dig_kernels.cu).  Not part of the public ABI.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -204,11 +205,12 @@ void launch_mlp_loss(const float* params, const float* X, const float* T, long l
 void launch_adam(float* p, float* m, float* v, float* g, long long t, float lr, float b1, float b2, float eps,
                  cudaStream_t s);
 void launch_mlp_init(const Params& P, uint64_t seed, float* params, cudaStream_t s);
-// S10: the initial conserved state, then `iters` solver iterations (each stops
-// early once the solve is done: its state lives on the device), or the final
-// primitives (final = true, iters ignored)
+// S10: the initial conserved state; `iters` solver iterations (each stops
+// early once the solve is done: its state lives on the device), returning
+// the number of kernels enqueued (not added to g_launches, so that a stream
+// capture can count them); the final primitives
 void launch_couple_s10_init(const Params& P, const CoupleParams& C, cudaStream_t s);
-void launch_couple_s10_iters(const Params& P, const CoupleParams& C, int iters, cudaStream_t s);
+long long launch_couple_s10_iters(const Params& P, const CoupleParams& C, int iters, cudaStream_t s);  // kernels enqueued
 void launch_couple_s10_final(const Params& P, const CoupleParams& C, cudaStream_t s);
 void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, int N, uint32_t sub, int* cl,
                        cudaStream_t s);
@@ -236,6 +238,8 @@ void launch_sort_by_cell(const int* cell, long long n, int n_cells, int* cell_st
 int scan_blocks(int n_cells);
 // sets the calling thread's message returned by dig_last_error(NULL)
 void set_thread_error(const char* msg);
-extern long long g_launches;
+// kernels launched by the library (dig_launch_count); the context-free calls
+// may run on several host threads at once
+extern std::atomic<long long> g_launches;
 
 }  // namespace dig

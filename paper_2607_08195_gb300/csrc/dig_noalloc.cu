@@ -17,43 +17,33 @@
 // need at the start of every call; everything else in the array is
 // overwritten before it is read.
 //
-// The device address of the array is obtained once per device, on the first
-// call made while that device is current, with cudaGetSymbolAddress (host code
-// cannot use the array's name as a device address).  Make that first call
-// before capturing any stream on the device.
+// The device address of the array is looked up with cudaGetSymbolAddress on
+// every call, for the device current at the call (host code cannot use the
+// array's name as a device address).  The lookup is a cheap host call once the
+// module is loaded on that device, and it stays right if the context is
+// destroyed and made again (cudaDeviceReset), which can move the array.  The
+// first call on a device loads the module there: make it before capturing
+// any stream on that device.
 #include "../../include/dig.h"
 #include "dig_internal.h"
-
-#include <mutex>
 
 namespace dig {
 
 static __device__ __align__(256) unsigned char g_sort_scratch[DIG_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
 // failures are reported like the other context-free calls: dig_last_error(NULL)
 int noalloc_fail(int code, const char* msg) {
   set_thread_error(msg);
   return code;
 }
 
-// device address of g_sort_scratch on the current device (set up once)
+// device address of g_sort_scratch on the current device
 int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(DIG_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(DIG_ERR_ARG, "device ordinal too large");
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_sort_scratch);
-    if (e != cudaSuccess || !p) return noalloc_fail(DIG_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+  if (e != cudaSuccess || !p) return noalloc_fail(DIG_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+  *out = p;
   return DIG_OK;
 }
 }  // namespace

@@ -7,7 +7,8 @@
 //   count    histogram of cell ids (warp-aggregated atomics)
 //   scan     cell_start = exclusive scan of the counts (two kernels)
 //   place    order_tmp[cell_start[c] + atomic cursor] = i   (unordered in a cell)
-//   fix      each cell's segment ranked by index: order[...] sorted
+//   fix      each cell's segment ordered by index: warp ranking up to 32
+//            elements, a block's stable radix sort beyond (linear time)
 // Scratch (device, caller-provided): counts, cursors, scan partials, order_tmp.
 #include "dig_internal.h"
 
@@ -125,25 +126,107 @@ __global__ void k_sort_place(const int* __restrict__ cell, long long n, int n_ce
   }
 }
 
-// one warp per cell: rank each element of the segment by its index
+// one warp per cell: segments of up to 32 elements ranked by index within
+// the warp; longer segments are left to k_sort_long
 __global__ void k_sort_fix(int n_cells, const int* __restrict__ cs, SortScratch S, int* __restrict__ order) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int c = gw; c < n_cells; c += nw) {
     const int a = cs[c], len = cs[c + 1] - a;
-    if (len <= 32) {
-      const int key = lane < len ? S.tmp[a + lane] : 0x7fffffff;
-      int r = 0;
-      for (int q = 0; q < len; ++q) r += (__shfl_sync(0xffffffffu, key, q) < key) ? 1 : 0;
-      if (lane < len) order[a + r] = key;
-    } else {
-      for (int k = lane; k < len; k += 32) {
-        const int key = S.tmp[a + k];
-        int r = 0;
-        for (int q = 0; q < len; ++q) r += (S.tmp[a + q] < key) ? 1 : 0;
-        order[a + r] = key;
+    if (len > 32) continue;
+    const int key = lane < len ? S.tmp[a + lane] : 0x7fffffff;
+    int r = 0;
+    for (int q = 0; q < len; ++q) r += (__shfl_sync(0xffffffffu, key, q) < key) ? 1 : 0;
+    if (lane < len) order[a + r] = key;
+  }
+}
+
+// Segments longer than 32: one block per segment, a stable LSD radix sort of
+// its keys (distinct indices) by 8-bit digits, as many passes as the largest
+// key needs, ping-ponging between tmp and order over the segment's own range;
+// each pass counts the digits, scans them, then places the keys tile by tile
+// in index order (rank within a tile: lanes with the same digit in earlier
+// warps, then earlier lanes of the same warp).  Work O(len) per pass.
+constexpr int LT = 256, LW = LT / 32;
+
+__global__ void __launch_bounds__(LT) k_sort_long(int n_cells, const int* __restrict__ cs, SortScratch S,
+                                                 int* __restrict__ order) {
+  __shared__ int hist[256], off[256], wcnt[LW][256];
+  __shared__ int s_max;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
+    const int a = cs[c], len = cs[c + 1] - a;
+    if (len <= 32) continue;  // block-uniform
+    // the largest key fixes the number of passes
+    int mx = 0;
+    for (int k = t; k < len; k += LT) mx = max(mx, S.tmp[a + k]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (t == 0) s_max = 0;
+    __syncthreads();
+    if (lane == 0) atomicMax(&s_max, mx);
+    __syncthreads();
+    int bits = 0;
+    while (bits < 31 && (s_max >> bits) != 0) bits += 8;
+    const int passes = bits > 0 ? bits / 8 : 1;
+    int* src = S.tmp + a;
+    int* dst = order + a;
+    for (int p = 0; p < passes; ++p) {
+      const int sh = 8 * p;
+      hist[t] = 0;
+      __syncthreads();
+      for (int k = t; k < len; k += LT) atomicAdd(&hist[(src[k] >> sh) & 255], 1);
+      __syncthreads();
+      if (warp == 0) {  // exclusive scan of the 256 counts, 8 per lane
+        int v[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          v[i] = hist[8 * lane + i];
+          sum += v[i];
+        }
+        int inc = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        int e = inc - sum;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          off[8 * lane + i] = e;
+          e += v[i];
+        }
       }
+      __syncthreads();
+      for (int k0 = 0; k0 < len; k0 += LT) {
+        const int k = k0 + t;
+        const bool in = k < len;
+        const int key = in ? src[k] : 0;
+        const int d = in ? (key >> sh) & 255 : 256 + t;  // out-of-range lanes match nobody
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int below = __popc(peers & ((1u << lane) - 1u));
+        for (int i = t; i < LW * 256; i += LT) wcnt[i / 256][i % 256] = 0;
+        __syncthreads();
+        if (in && below == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (in) {
+          int r = off[d] + below;
+          for (int w = 0; w < warp; ++w) r += wcnt[w][d];
+          dst[r] = key;
+        }
+        __syncthreads();
+        // advance each digit's offset by its count in this tile
+        int tot = 0;
+        for (int w = 0; w < LW; ++w) tot += wcnt[w][t];
+        off[t] += tot;
+        __syncthreads();
+      }
+      int* x = src;
+      src = dst;
+      dst = x;
+      __syncthreads();
     }
+    if (src != order + a)  // an even number of passes left the result in tmp
+      for (int k = t; k < len; k += LT) order[a + k] = src[k];
+    __syncthreads();
   }
 }
 }  // namespace
@@ -167,8 +250,9 @@ void launch_sort_by_cell(const int* cell, long long n, int n_cells, int* cell_st
     k_sort_place<<<gridn, 256, 0, s>>>(cell, n, n_cells, cell_start, S);
     const int gw = (n_cells + 7) / 8 < 8192 ? (n_cells + 7) / 8 : 8192;
     k_sort_fix<<<gw, 256, 0, s>>>(n_cells, cell_start, S, order);
+    k_sort_long<<<n_cells < 1024 ? n_cells : 1024, LT, 0, s>>>(n_cells, cell_start, S, order);
   }
-  g_launches += n > 0 ? 6 : 4;
+  g_launches += n > 0 ? 7 : 4;
 }
 
 }  // namespace dig

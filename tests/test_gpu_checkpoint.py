@@ -2,6 +2,8 @@
 from a checkpoint continues bit for bit, across DSMC steps, moving and
 cumulative averages and a DIG coupling; a checkpoint of another
 configuration or a truncated one is refused."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -53,6 +55,16 @@ def test_load_refuses_other_configuration_and_truncation():
     other = dig.Solver(W.config_small(seed=6), "cuda:0")
     with pytest.raises(RuntimeError):
         other.load(ck)
+    # settings that change results but not the arena: refused, the field named
+    for over in (dict(alpha=1.4), dict(local_acc=1), dict(N_m=77), dict(cfl=1.0), dict(KnD_max=0.5)):
+        if "alpha" in over:
+            sc = W.config_small(seed=5)
+            sc.gas = dataclasses.replace(sc.gas, alpha=1.4)
+            h = dig.Solver(sc, "cuda:0")
+        else:
+            h = dig.Solver(s, "cuda:0", **over)
+        with pytest.raises(RuntimeError, match="different dig_config." + list(over)[0]):
+            h.load(ck)
     same = dig.Solver(s, "cuda:0")
     with pytest.raises(RuntimeError):
         same.load(ck[: len(ck) // 2])

@@ -293,6 +293,32 @@ def test_sort_by_cell_matches_oracle(n, n_cells):
     assert np.array_equal(ord_g.cpu().numpy(), ord_o)
 
 
+@pytest.mark.parametrize("n,n_cells,heavy", [(65_536, 1, 0), (65_536, 64, 0.9), (1_000_000, 4096, 0.5),
+                                             (4_000, 100, 1.0)])
+def test_sort_by_cell_heavy_segments(n, n_cells, heavy):
+    """The bucket sort on skewed input: a fraction `heavy` of the elements in
+    one cell (all of them in a single cell at n = 65,536), the rest spread:
+    cell_start and order identical to numpy's stable argsort, and the long
+    segments sorted in time linear in their length (the whole call well under
+    a second)."""
+    import time
+
+    rng = np.random.default_rng(n + n_cells)
+    cell = rng.integers(-1, n_cells, size=n).astype(np.int32)
+    cell[rng.random(n) < heavy] = n_cells // 2
+    keep = cell >= 0
+    want = np.flatnonzero(keep)[np.argsort(cell[keep], kind="stable")]
+    want_cs = np.concatenate([[0], np.cumsum(np.bincount(cell[keep], minlength=n_cells))])
+    dcell = torch.from_numpy(cell).cuda()
+    dig.sort_by_cell(dcell, n_cells)  # warm
+    t0 = time.perf_counter()
+    cs_g, ord_g = dig.sort_by_cell(dcell, n_cells)
+    dt = time.perf_counter() - t0
+    assert np.array_equal(cs_g.cpu().numpy(), want_cs)
+    assert np.array_equal(ord_g.cpu().numpy(), want)
+    assert dt < 0.5, dt
+
+
 def inflow_box(gas, U, sides_inflow, nh=2, n=1.677e22, T=273.0, n_particles=6000, seed=13):
     bcs = [dict(kind=W.BC_INFLOW, T=T, U=tuple(U), n=n), dict(kind=W.BC_OUTFLOW, T=T, U=(0.0, 0.0, 0.0), n=0.0)]
     mesh = W.box_sides(nh, 1e-3, [0 if sd in sides_inflow else 1 for sd in range(6)], bcs)
