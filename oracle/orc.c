@@ -29,6 +29,31 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Velocity precision.  By default FP32, as the method states it: velocities,
+ * rotational energies and the collision, wall and injection arithmetic in
+ * single precision, with the own FP32 ln/exp below where a transcendental
+ * decides (bit-identical to the CUDA path).  Built with -DORC_V64 the same
+ * quantities are FP64 (libm log/pow): the FP64 reference run that states the
+ * error of the FP32 path.  Positions, ray-face parameters and every sum are
+ * FP64 in both builds. */
+#ifdef ORC_V64
+typedef double vreal;
+#define VSQRT(x) sqrt(x)
+#define VLN(x) log(x)
+#define VEXP(x) exp(x)
+#define VPOW(x, a) pow(x, a)
+#define VFABS(x) fabs(x)
+#define VHALF_SQRT2 0.70710678118654752
+#else
+typedef float vreal;
+#define VSQRT(x) sqrtf(x)
+#define VLN(x) orc_lnf(x)
+#define VEXP(x) orc_expf(x)
+#define VPOW(x, a) orc_powf(x, a)
+#define VFABS(x) fabsf(x)
+#define VHALF_SQRT2 0.707106781f
+#endif
+
 #define KB 1.380649e-23
 
 /* ------------------------------------------------------------------------- */
@@ -139,11 +164,11 @@ float orc_powf(float x, float a) { return orc_expf(a * orc_lnf(x)); }
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int32_t tet, face, bc;
-  float nrm[3], t1[3], t2[3]; /* outward unit normal and tangent basis (FP32) */
+  vreal nrm[3], t1[3], t2[3]; /* outward unit normal and tangent basis (velocity precision) */
   /* free-stream inflow faces only */
   int32_t vtx[3];             /* the face's nodes (local order of the face) */
   double expn;                /* expected injections per step: F A dt / F_N */
-  float s, p1, invb, sig, ut1, ut2; /* speed ratio, mixture weight, 1/beta, sqrt(kT/m), U.t1, U.t2 */
+  vreal s, p1, invb, sig, ut1, ut2; /* speed ratio, mixture weight, 1/beta, sqrt(kT/m), U.t1, U.t2 */
 } bface_t;
 
 #define NPHI_MAX 17
@@ -170,22 +195,22 @@ struct orc_ctx {
   double* inj_rem;   /* [n_bf] carried fractional injection count of each inflow face */
   orc_bc* bcs;
   int32_t n_bcs;
-  float* bc_sigma;   /* sqrt(k T / m) per bc */
-  float* bc_U;       /* [3 n_bcs] */
-  /* gas constants (FP32 where the collision arithmetic uses them) */
-  float c_vhs, one_m_omega, cmax0, p_inel, lb_exp, hmr, T_init_f, sigma_init, u0f[3];
+  vreal* bc_sigma;   /* sqrt(k T / m) per bc */
+  vreal* bc_U;       /* [3 n_bcs] */
+  /* gas constants in the velocity precision (vreal) where the collision arithmetic uses them */
+  vreal c_vhs, one_m_omega, cmax0, p_inel, lb_exp, hmr, T_init_f, sigma_init, u0f[3];
   int vss;          /* alpha != 1: VSS scattering */
-  float inv_alpha;  /* 1 / alpha */
+  vreal inv_alpha;  /* 1 / alpha */
   int nphi;
   /* particles (sorted by cell between steps) */
   int64_t N, cap;
   double* x;
-  float* v;
-  float* Ir;
+  vreal* v;
+  vreal* Ir;
   int32_t* cell;
   int64_t* cstart; /* [n+1] */
   /* collision state per cell */
-  float* cmax;
+  vreal* cmax;
   double* rem;
   /* sampling */
   double* phi_inst;
@@ -234,22 +259,22 @@ orc_ctx* orc_create(const orc_config* cfg) {
   /* VHS: sigma_T c_r = pi d^2 (2kT_ref/(m_r c_r^2))^(w-1/2) / Gamma(5/2-w) * c_r
    *                  = C_vhs (c_r^2)^(1-w)                          (Bird 1994, eq. 4.63) */
   double cv = M_PI * cfg->d_ref * cfg->d_ref * pow(2.0 * KB * cfg->T_ref / mr, w - 0.5) / tgamma(2.5 - w);
-  c->c_vhs = (float)cv;
-  c->one_m_omega = (float)(1.0 - w);
+  c->c_vhs = (vreal)cv;
+  c->one_m_omega = (vreal)(1.0 - w);
   /* initial (sigma c_r)_max at c_0 = 2.5 sqrt(2 k T_init / m) */
-  float c0sq = (float)(6.25 * 2.0 * KB * cfg->T_init / m);
-  c->cmax0 = c->c_vhs * orc_powf(c0sq, c->one_m_omega);
+  vreal c0sq = (vreal)(6.25 * 2.0 * KB * cfg->T_init / m);
+  c->cmax0 = c->c_vhs * VPOW(c0sq, c->one_m_omega);
   /* Borgnakke-Larsen probability, Eq. inelastic_probability */
   double a = cfg->alpha;
-  c->p_inel = (float)(a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0) * cfg->Z_rot));
+  c->p_inel = (vreal)(a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0) * cfg->Z_rot));
   /* VSS scattering law (paper Sec. 2.1) for alpha != 1; alpha = 1 is VHS */
   c->vss = a != 1.0;
-  c->inv_alpha = (float)(1.0 / a);
-  c->lb_exp = (float)(1.0 / (2.5 - w));
-  c->hmr = (float)(0.5 * mr / KB); /* relative translational energy in kelvin per (m/s)^2 */
-  c->T_init_f = (float)cfg->T_init;
-  c->sigma_init = (float)sqrt(KB * cfg->T_init / m);
-  for (int i = 0; i < 3; ++i) c->u0f[i] = (float)cfg->u_init[i];
+  c->inv_alpha = (vreal)(1.0 / a);
+  c->lb_exp = (vreal)(1.0 / (2.5 - w));
+  c->hmr = (vreal)(0.5 * mr / KB); /* relative translational energy in kelvin per (m/s)^2 */
+  c->T_init_f = (vreal)cfg->T_init;
+  c->sigma_init = (vreal)sqrt(KB * cfg->T_init / m);
+  for (int i = 0; i < 3; ++i) c->u0f[i] = (vreal)cfg->u_init[i];
   return c;
 }
 
@@ -317,11 +342,11 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
   c->n_bcs = n_bcs;
   c->bcs = (orc_bc*)malloc(sizeof(orc_bc) * (n_bcs > 0 ? n_bcs : 1));
   memcpy(c->bcs, bcs, sizeof(orc_bc) * n_bcs);
-  c->bc_sigma = (float*)malloc(sizeof(float) * (n_bcs > 0 ? n_bcs : 1));
-  c->bc_U = (float*)malloc(sizeof(float) * 3 * (n_bcs > 0 ? n_bcs : 1));
+  c->bc_sigma = (vreal*)malloc(sizeof(vreal) * (n_bcs > 0 ? n_bcs : 1));
+  c->bc_U = (vreal*)malloc(sizeof(vreal) * 3 * (n_bcs > 0 ? n_bcs : 1));
   for (int b = 0; b < n_bcs; ++b) {
-    c->bc_sigma[b] = (float)sqrt(KB * bcs[b].T / c->cfg.mass);
-    for (int i = 0; i < 3; ++i) c->bc_U[3 * b + i] = (float)bcs[b].U[i];
+    c->bc_sigma[b] = (vreal)sqrt(KB * bcs[b].T / c->cfg.mass);
+    for (int i = 0; i < 3; ++i) c->bc_U[3 * b + i] = (vreal)bcs[b].U[i];
   }
 
   /* volumes: V = |det(b-a, c-a, d-a)| / 6 */
@@ -424,7 +449,7 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
       double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
       t1[0] = t1[0] / l1; t1[1] = t1[1] / l1; t1[2] = t1[2] / l1;
       double t2[3] = {N[1] * t1[2] - N[2] * t1[1], N[2] * t1[0] - N[0] * t1[2], N[0] * t1[1] - N[1] * t1[0]};
-      for (int i = 0; i < 3; ++i) { B->nrm[i] = (float)N[i]; B->t1[i] = (float)t1[i]; B->t2[i] = (float)t2[i]; }
+      for (int i = 0; i < 3; ++i) { B->nrm[i] = (vreal)N[i]; B->t1[i] = (vreal)t1[i]; B->t2[i] = (vreal)t2[i]; }
       c->nbr[4 * t + f] = -1 - ib;
       c->nbr_face[4 * t + f] = (int8_t)f;
       memset(B->vtx, 0, sizeof B->vtx);
@@ -452,20 +477,20 @@ int orc_mesh_load(orc_ctx* c, const double* nodes, int64_t n_nodes, const int32_
          * stream leaves (s << 0) */
         const double flux = bc->n / (2.0 * sqrt(M_PI) * beta) * (exp(-sn * sn) + sqrt(M_PI) * sn * erfc(-sn));
         B->expn = flux * area * c->cfg.dt / c->cfg.F_N;
-        B->s = (float)sn;
+        B->s = (vreal)sn;
         const double m1 = 0.5, m2 = sn > 0.0 ? sn * sqrt(M_PI) : 0.0;
-        B->p1 = (float)(m1 / (m1 + m2));
-        B->invb = (float)(1.0 / beta);
-        B->sig = (float)sqrt(KB * bc->T / c->cfg.mass);
-        B->ut1 = (float)(bc->U[0] * t1[0] + bc->U[1] * t1[1] + bc->U[2] * t1[2]);
-        B->ut2 = (float)(bc->U[0] * t2[0] + bc->U[1] * t2[1] + bc->U[2] * t2[2]);
+        B->p1 = (vreal)(m1 / (m1 + m2));
+        B->invb = (vreal)(1.0 / beta);
+        B->sig = (vreal)sqrt(KB * bc->T / c->cfg.mass);
+        B->ut1 = (vreal)(bc->U[0] * t1[0] + bc->U[1] * t1[1] + bc->U[2] * t1[2]);
+        B->ut2 = (vreal)(bc->U[0] * t2[0] + bc->U[1] * t2[1] + bc->U[2] * t2[2]);
       }
       ++ib;
     }
 
   /* per-cell state */
   c->cstart = (int64_t*)calloc(n + 1, sizeof(int64_t));
-  c->cmax = (float*)malloc(sizeof(float) * n);
+  c->cmax = (vreal*)malloc(sizeof(vreal) * n);
   c->rem = (double*)calloc(n, sizeof(double));
   for (int64_t t = 0; t < n; ++t) c->cmax[t] = c->cmax0;
   c->phi_inst = (double*)calloc(NPHI_MAX * n, sizeof(double));
@@ -508,8 +533,8 @@ static void ensure_cap(orc_ctx* c, int64_t n) {
   if (n <= c->cap) return;
   int64_t cap = n + n / 2 + 16;
   c->x = (double*)realloc(c->x, sizeof(double) * 3 * cap);
-  c->v = (float*)realloc(c->v, sizeof(float) * 3 * cap);
-  c->Ir = (float*)realloc(c->Ir, sizeof(float) * cap);
+  c->v = (vreal*)realloc(c->v, sizeof(vreal) * 3 * cap);
+  c->Ir = (vreal*)realloc(c->Ir, sizeof(vreal) * cap);
   c->cell = (int32_t*)realloc(c->cell, sizeof(int32_t) * cap);
   c->cap = cap;
 }
@@ -527,21 +552,21 @@ static void sort_particles(orc_ctx* c, const uint8_t* moved) {
   for (int64_t k = 0; k < 2 * n; ++k) cnt[k + 1] += cnt[k];
   int64_t M = cnt[2 * n];
   double* x = (double*)malloc(sizeof(double) * 3 * (M > 0 ? M : 1));
-  float* v = (float*)malloc(sizeof(float) * 3 * (M > 0 ? M : 1));
-  float* Ir = (float*)malloc(sizeof(float) * (M > 0 ? M : 1));
+  vreal* v = (vreal*)malloc(sizeof(vreal) * 3 * (M > 0 ? M : 1));
+  vreal* Ir = (vreal*)malloc(sizeof(vreal) * (M > 0 ? M : 1));
   int32_t* cl = (int32_t*)malloc(sizeof(int32_t) * (M > 0 ? M : 1));
   for (int64_t p = 0; p < N; ++p) {
     if (c->cell[p] < 0) continue;
     int64_t key = 2 * (int64_t)c->cell[p] + (moved ? moved[p] : 1);
     int64_t q = cnt[key]++;
     memcpy(x + 3 * q, c->x + 3 * p, 3 * sizeof(double));
-    memcpy(v + 3 * q, c->v + 3 * p, 3 * sizeof(float));
+    memcpy(v + 3 * q, c->v + 3 * p, 3 * sizeof(vreal));
     Ir[q] = c->Ir[p];
     cl[q] = c->cell[p];
   }
   memcpy(c->x, x, sizeof(double) * 3 * M);
-  memcpy(c->v, v, sizeof(float) * 3 * M);
-  memcpy(c->Ir, Ir, sizeof(float) * M);
+  memcpy(c->v, v, sizeof(vreal) * 3 * M);
+  memcpy(c->Ir, Ir, sizeof(vreal) * M);
   memcpy(c->cell, cl, sizeof(int32_t) * M);
   c->N = M;
   free(x); free(v); free(Ir); free(cl); free(cnt);
@@ -553,16 +578,16 @@ static void sort_particles(orc_ctx* c, const uint8_t* moved) {
 /* Gaussian pair by Marsaglia's polar method; attempts use successive draws,
  * two attempts per Philox block. */
 static uint32_t gauss2(const orc_ctx* c, int purpose, uint32_t ent, uint32_t sub, uint32_t step,
-                       uint32_t draw0, float* g1, float* g2) {
+                       uint32_t draw0, vreal* g1, vreal* g2) {
   for (uint32_t d = draw0; d < draw0 + 32; ++d) {
     uint32_t w[4];
     rng4(c, purpose, ent, sub, step, d, w);
     for (int a = 0; a < 2; ++a) {
-      float u1 = 2.0f * u01f(w[2 * a]) - 1.0f;
-      float u2 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
-      float s = u1 * u1 + u2 * u2;
+      vreal u1 = 2.0f * u01f(w[2 * a]) - 1.0f;
+      vreal u2 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
+      vreal s = u1 * u1 + u2 * u2;
       if (s < 1.0f && s > 0.0f) {
-        float f = sqrtf(-2.0f * orc_lnf(s) / s);
+        vreal f = VSQRT(-2.0f * VLN(s) / s);
         *g1 = u1 * f;
         *g2 = u2 * f;
         return d + 1;
@@ -576,16 +601,16 @@ static uint32_t gauss2(const orc_ctx* c, int purpose, uint32_t ent, uint32_t sub
 
 /* isotropic unit vector (Marsaglia 1972): (a,b) uniform in the unit disc,
  * e = (2a sqrt(1-s), 2b sqrt(1-s), 1-2s) with s = a^2 + b^2 */
-static void unit_vector(const orc_ctx* c, int purpose, uint32_t ent, uint32_t sub, uint32_t step, float* e) {
+static void unit_vector(const orc_ctx* c, int purpose, uint32_t ent, uint32_t sub, uint32_t step, vreal* e) {
   for (uint32_t d = 0; d < 32; ++d) {
     uint32_t w[4];
     rng4(c, purpose, ent, sub, step, d, w);
     for (int a = 0; a < 2; ++a) {
-      float a1 = 2.0f * u01f(w[2 * a]) - 1.0f;
-      float b1 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
-      float s = a1 * a1 + b1 * b1;
+      vreal a1 = 2.0f * u01f(w[2 * a]) - 1.0f;
+      vreal b1 = 2.0f * u01f(w[2 * a + 1]) - 1.0f;
+      vreal s = a1 * a1 + b1 * b1;
       if (s < 1.0f) {
-        float r = 2.0f * sqrtf(1.0f - s);
+        vreal r = 2.0f * VSQRT(1.0f - s);
         e[0] = a1 * r;
         e[1] = b1 * r;
         e[2] = 1.0f - 2.0f * s;
@@ -611,20 +636,20 @@ static void unit_vector(const orc_ctx* c, int purpose, uint32_t ent, uint32_t su
  * point (words 1, 2); draws 1..31 give two points each (words 0,1 and 2,3).
  * g2 = g_x^2 + g_y^2 + g_z^2 > 0. */
 static void vss_direction(const orc_ctx* c, int purpose, uint32_t ent, uint32_t sub, uint32_t step,
-                          const float g[3], float g2, float e[3]) {
+                          const vreal g[3], vreal g2, vreal e[3]) {
   uint32_t w[4];
   rng4(c, purpose, ent, sub, step, 0, w);
-  const float ct = 2.0f * orc_powf(u01f(w[0]), c->inv_alpha) - 1.0f;
-  const float st = sqrtf((1.0f - ct) * (1.0f + ct));
-  float ce = 1.0f, se = 0.0f;
+  const vreal ct = 2.0f * VPOW(u01f(w[0]), c->inv_alpha) - 1.0f;
+  const vreal st = VSQRT((1.0f - ct) * (1.0f + ct));
+  vreal ce = 1.0f, se = 0.0f;
   int found = 0;
   for (uint32_t d = 0; d < 32 && !found; ++d) {
     if (d > 0) rng4(c, purpose, ent, sub, step, d, w);
     /* d == 0: the point (w1, w2); d > 0: (w0, w1) then (w2, w3) */
     for (int k0 = d == 0 ? 1 : 0; k0 <= 2 && !found; k0 += 2) {
-      const float a1 = 2.0f * u01f(w[k0]) - 1.0f;
-      const float b1 = 2.0f * u01f(w[k0 + 1]) - 1.0f;
-      const float s = a1 * a1 + b1 * b1;
+      const vreal a1 = 2.0f * u01f(w[k0]) - 1.0f;
+      const vreal b1 = 2.0f * u01f(w[k0 + 1]) - 1.0f;
+      const vreal s = a1 * a1 + b1 * b1;
       if (s < 1.0f && s > 0.0f) {
         ce = (a1 * a1 - b1 * b1) / s;
         se = 2.0f * a1 * b1 / s;
@@ -632,9 +657,9 @@ static void vss_direction(const orc_ctx* c, int purpose, uint32_t ent, uint32_t 
       }
     }
   }
-  const float gn = sqrtf(g2);
-  const float ux = g[0] / gn, uy = g[1] / gn, uz = g[2] / gn;
-  const float qn = sqrtf(uy * uy + uz * uz);
+  const vreal gn = VSQRT(g2);
+  const vreal ux = g[0] / gn, uy = g[1] / gn, uz = g[2] / gn;
+  const vreal qn = VSQRT(uy * uy + uz * uz);
   if (qn > 1e-6f) {
     e[0] = ct * ux + st * se * qn;
     e[1] = ct * uy + st * (ce * uz - se * ux * uy) / qn;
@@ -646,13 +671,15 @@ static void vss_direction(const orc_ctx* c, int purpose, uint32_t ent, uint32_t 
   }
 }
 
-int orc_vss_directions(orc_ctx* c, const float* g, int64_t n, float* e) {
-  if (!c || (n > 0 && (!g || !e))) return -1;
+int orc_vss_directions(orc_ctx* c, const float* gf, int64_t n, float* ef) {
+  if (!c || (n > 0 && (!gf || !ef))) return -1;
   for (int64_t p = 0; p < n; ++p) {
-    const float* gp = g + 3 * p;
-    const float g2 = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
+    const vreal gp[3] = {gf[3 * p], gf[3 * p + 1], gf[3 * p + 2]};
+    const vreal g2 = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
     if (!(g2 > 0.0f)) return fail(c, -1, "orc_vss_directions: zero relative velocity");
-    vss_direction(c, RP_DIR, (uint32_t)p, 0u, 0u, gp, g2, e + 3 * p);
+    vreal e[3];
+    vss_direction(c, RP_DIR, (uint32_t)p, 0u, 0u, gp, g2, e);
+    for (int i = 0; i < 3; ++i) ef[3 * p + i] = (float)e[i];
   }
   return 0;
 }
@@ -696,12 +723,12 @@ int orc_particles_init(orc_ctx* c, int64_t n) {
       c->x[3 * p + i] = A[i] + s * (B[i] - A[i]) + tt * (C[i] - A[i]) + u * (D[i] - A[i]);
     /* Maxwellian velocity at T_init around u_init; rotational energy (in kelvin)
      * exponential with mean T_init (two rotational degrees of freedom) */
-    float g[4];
+    vreal g[4];
     gauss2(c, RP_INIT_VEL, (uint32_t)p, 0, 0, 0, &g[0], &g[1]);
     gauss2(c, RP_INIT_VEL, (uint32_t)p, 1, 0, 0, &g[2], &g[3]);
     for (int i = 0; i < 3; ++i) c->v[3 * p + i] = c->u0f[i] + c->sigma_init * g[i];
     rng4(c, RP_INIT_VEL, (uint32_t)p, 2, 0, 0, w);
-    c->Ir[p] = c->cfg.rot_dof > 0 ? -c->T_init_f * orc_lnf(u01f(w[0])) : 0.0f;
+    c->Ir[p] = c->cfg.rot_dof > 0 ? -c->T_init_f * VLN(u01f(w[0])) : 0.0f;
     c->cell[p] = (int32_t)t;
   }
   c->N = n;
@@ -716,9 +743,9 @@ int orc_write_particles(orc_ctx* c, const double* x, const float* v, const float
   for (int64_t p = 0; p < n; ++p)
     if (cell[p] < 0 || cell[p] >= c->n_tets) return fail(c, -1, "cell index out of range");
   memcpy(c->x, x, sizeof(double) * 3 * n);
-  memcpy(c->v, v, sizeof(float) * 3 * n);
+  for (int64_t i = 0; i < 3 * n; ++i) c->v[i] = v[i];
   /* monatomic gas carries no rotational energy: I_r is ignored and reads as 0 */
-  if (Ir && c->cfg.rot_dof > 0) memcpy(c->Ir, Ir, sizeof(float) * n); else memset(c->Ir, 0, sizeof(float) * n);
+  for (int64_t p = 0; p < n; ++p) c->Ir[p] = Ir && c->cfg.rot_dof > 0 ? Ir[p] : 0.0f;
   memcpy(c->cell, cell, sizeof(int32_t) * n);
   c->N = n;
   sort_particles(c, NULL);
@@ -729,8 +756,10 @@ int orc_read_particles(orc_ctx* c, double* x, float* v, float* Ir, int32_t* cell
   *n = c->N;
   if (cap < c->N) return fail(c, -3, "buffer too small");
   if (x) memcpy(x, c->x, sizeof(double) * 3 * c->N);
-  if (v) memcpy(v, c->v, sizeof(float) * 3 * c->N);
-  if (Ir) memcpy(Ir, c->Ir, sizeof(float) * c->N);
+  if (v)
+    for (int64_t i = 0; i < 3 * c->N; ++i) v[i] = (float)c->v[i];
+  if (Ir)
+    for (int64_t p = 0; p < c->N; ++p) Ir[p] = (float)c->Ir[p];
   if (cell) memcpy(cell, c->cell, sizeof(int32_t) * c->N);
   return 0;
 }
@@ -744,29 +773,29 @@ static double dot3(const double* n, const double* y) { return fma(n[2], y[2], fm
 
 /* wall interaction at boundary face ib; hit counts the hits of this particle in
  * this step (it keys the random stream) */
-static void wall_reflect(orc_ctx* c, int32_t ib, float* v, float* Ir, uint32_t slot, uint32_t hit, uint32_t step) {
+static void wall_reflect(orc_ctx* c, int32_t ib, vreal* v, vreal* Ir, uint32_t slot, uint32_t hit, uint32_t step) {
   const bface_t* B = c->bf + ib;
   const orc_bc* bc = c->bcs + B->bc;
-  float vin[3] = {v[0], v[1], v[2]};
-  float Iin = *Ir;
+  vreal vin[3] = {v[0], v[1], v[2]};
+  vreal Iin = *Ir;
   if (bc->kind == 1) {
     /* specular: v <- v - 2 (v.n) n */
-    float vn = v[0] * B->nrm[0] + v[1] * B->nrm[1] + v[2] * B->nrm[2];
-    float h = 2.0f * vn;
+    vreal vn = v[0] * B->nrm[0] + v[1] * B->nrm[1] + v[2] * B->nrm[2];
+    vreal h = 2.0f * vn;
     for (int i = 0; i < 3; ++i) v[i] = v[i] - h * B->nrm[i];
   } else {
     /* diffuse at T_w: normal speed from the flux-weighted half-range Maxwellian,
      * tangential Gaussian components, plus the wall velocity */
     uint32_t w[4];
     rng4(c, RP_WALL, slot, hit, step, 0, w);
-    float sg = c->bc_sigma[B->bc];
-    float vn = sg * sqrtf(-2.0f * orc_lnf(u01f(w[0])));
-    float g1, g2;
+    vreal sg = c->bc_sigma[B->bc];
+    vreal vn = sg * VSQRT(-2.0f * VLN(u01f(w[0])));
+    vreal g1, g2;
     gauss2(c, RP_WALL, slot, hit, step, 1, &g1, &g2);
-    float a = sg * g1, b = sg * g2;
-    const float* U = c->bc_U + 3 * B->bc;
+    vreal a = sg * g1, b = sg * g2;
+    const vreal* U = c->bc_U + 3 * B->bc;
     for (int i = 0; i < 3; ++i) v[i] = ((U[i] + B->t1[i] * a) + B->t2[i] * b) - B->nrm[i] * vn;
-    if (c->cfg.rot_dof > 0) *Ir = -(float)bc->T * orc_lnf(u01f(w[1]));
+    if (c->cfg.rot_dof > 0) *Ir = -(vreal)bc->T * VLN(u01f(w[1]));
   }
   /* wall flux bookkeeping (incident minus reflected), per boundary face */
   double* F = c->bflux + 5 * ib;
@@ -797,7 +826,7 @@ static void wall_reflect(orc_ctx* c, int32_t ib, float* v, float* Ir, uint32_t s
  *   hit time t_h = a_f / b_f, o <- o + v t_h, t_rem <- t_rem - t_h, new
  *   velocity, e <- o + v t_rem, entry face = the wall face; or leave the domain.
  * All dot products are fma(n2, y2, fma(n1, y1, n0 y0)) in FP64. */
-static int32_t track_ex(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, uint32_t slot, uint32_t step,
+static int32_t track_ex(orc_ctx* c, double* x, vreal* v, vreal* Ir, int32_t cell, uint32_t slot, uint32_t step,
                         double t_move, int entry0) {
   double trem = t_move;
   int entry = entry0;
@@ -862,13 +891,14 @@ static int32_t track_ex(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell
   }
 }
 
-static int32_t track(orc_ctx* c, double* x, float* v, float* Ir, int32_t cell, uint32_t slot, uint32_t step) {
+static int32_t track(orc_ctx* c, double* x, vreal* v, vreal* Ir, int32_t cell, uint32_t slot, uint32_t step) {
   return track_ex(c, x, v, Ir, cell, slot, step, c->cfg.dt, -1);
 }
 
-int orc_track_one(orc_ctx* c, double* x, float* v, int32_t* cell, int64_t slot, int64_t step) {
-  float Ir = 0.0f;
+int orc_track_one(orc_ctx* c, double* x, float* vf, int32_t* cell, int64_t slot, int64_t step) {
+  vreal Ir = 0.0f, v[3] = {vf[0], vf[1], vf[2]};
   *cell = track(c, x, v, &Ir, *cell, (uint32_t)slot, (uint32_t)step);
+  for (int i = 0; i < 3; ++i) vf[i] = (float)v[i];
   return 0;
 }
 
@@ -899,21 +929,21 @@ static void collide_cell(orc_ctx* c, int64_t cell, uint32_t step, int record) {
   double fl = floor(X);
   c->rem[cell] = X - fl;
   int64_t ncand = (int64_t)fl;
-  float* v = c->v + 3 * s0;
-  float* I = c->Ir + s0;
+  vreal* v = c->v + 3 * s0;
+  vreal* I = c->Ir + s0;
   for (int64_t k = 0; k < ncand; ++k) {
     uint32_t w[4];
     rng4(c, RP_COLL, (uint32_t)cell, (uint32_t)k, step, 0, w);
     int64_t i = (int64_t)(((uint64_t)w[0] * (uint64_t)N) >> 32);
     int64_t j = (int64_t)(((uint64_t)w[1] * (uint64_t)(N - 1)) >> 32);
     if (j >= i) j = j + 1;
-    float g[3];
+    vreal g[3];
     for (int q = 0; q < 3; ++q) g[q] = v[3 * i + q] - v[3 * j + q];
-    float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-    const float g2_pre = g2;
-    float sc = g2 > 0.0f ? c->c_vhs * orc_powf(g2, c->one_m_omega) : 0.0f;
+    vreal g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const vreal g2_pre = g2;
+    vreal sc = g2 > 0.0f ? c->c_vhs * VPOW(g2, c->one_m_omega) : 0.0f;
     if (sc > c->cmax[cell]) c->cmax[cell] = sc;
-    float R = u01f(w[2]);
+    vreal R = u01f(w[2]);
     int acc = sc > R * c->cmax[cell];
     c->counters[ORC_C_CAND]++;
     if (record) record_pair(c, (int32_t)cell, (int32_t)k, (int32_t)i, (int32_t)j, acc);
@@ -925,12 +955,12 @@ static void collide_cell(orc_ctx* c, int64_t cell, uint32_t step, int record) {
        * I'/E_c = 1 - R^(1/(5/2 - omega)) (two rotational degrees of freedom) */
       uint32_t u[4];
       rng4(c, RP_LB, (uint32_t)cell, (uint32_t)k, step, 0, u);
-      float Etr = g2 * c->hmr;
+      vreal Etr = g2 * c->hmr;
       int64_t who[2] = {i, j};
       for (int q = 0; q < 2; ++q) {
         if (u01f(u[2 * q]) < c->p_inel) {
-          float Ec = Etr + I[who[q]];
-          float In = Ec * (1.0f - orc_powf(u01f(u[2 * q + 1]), c->lb_exp));
+          vreal Ec = Etr + I[who[q]];
+          vreal In = Ec * (1.0f - VPOW(u01f(u[2 * q + 1]), c->lb_exp));
           I[who[q]] = In;
           Etr = Ec - In;
           c->counters[ORC_C_LB]++;
@@ -938,16 +968,16 @@ static void collide_cell(orc_ctx* c, int64_t cell, uint32_t step, int record) {
       }
       g2 = Etr / c->hmr;
     }
-    float cr = sqrtf(g2);
-    float e[3];
+    vreal cr = VSQRT(g2);
+    vreal e[3];
     /* VHS: isotropic; VSS: deflected from the pre-collision g */
     if (c->vss)
       vss_direction(c, RP_DIR, (uint32_t)cell, (uint32_t)k, step, g, g2_pre, e);
     else
       unit_vector(c, RP_DIR, (uint32_t)cell, (uint32_t)k, step, e);
-    float h = 0.5f * cr;
+    vreal h = 0.5f * cr;
     for (int q = 0; q < 3; ++q) {
-      float cm = (v[3 * i + q] + v[3 * j + q]) * 0.5f;
+      vreal cm = (v[3 * i + q] + v[3 * j + q]) * 0.5f;
       v[3 * i + q] = cm + h * e[q];
       v[3 * j + q] = cm - h * e[q];
     }
@@ -1039,23 +1069,23 @@ int orc_sample(orc_ctx* c, int32_t action) {
 /* fraction of dt, draws 2.. tangential Gaussian pair, then normal speed      */
 /* attempts, then (diatomic) the rotational energy.                            */
 /* ------------------------------------------------------------------------- */
-static float inflow_normal_speed(const orc_ctx* c, const bface_t* B, uint32_t ib, uint32_t k, uint32_t step,
+static vreal inflow_normal_speed(const orc_ctx* c, const bface_t* B, uint32_t ib, uint32_t k, uint32_t step,
                                  uint32_t* draw) {
-  const float s = B->s;
+  const vreal s = B->s;
   for (int att = 0; att < 64; ++att) {
     uint32_t w[4];
     rng4(c, RP_INJECT, ib, k, step, (*draw)++, w);
     if (s <= 0.0f) {
-      float z = sqrtf(-orc_lnf(u01f(w[0])));
-      if (u01f(w[1]) < orc_expf(2.0f * s * z)) return z;
+      vreal z = VSQRT(-VLN(u01f(w[0])));
+      if (u01f(w[1]) < VEXP(2.0f * s * z)) return z;
     } else if (u01f(w[0]) < B->p1) {
-      return s + sqrtf(-orc_lnf(u01f(w[1])));
+      return s + VSQRT(-VLN(u01f(w[1])));
     } else {
       /* the second component's Gaussian is drawn to completion (polar method
        * over the following draws) before the acceptance test */
-      float g1, g2;
+      vreal g1, g2;
       *draw = gauss2(c, RP_INJECT, ib, k, step, *draw, &g1, &g2);
-      float z = s + g1 * 0.707106781f;
+      vreal z = s + g1 * VHALF_SQRT2;
       if (z > 0.0f && (z >= s || u01f(w[3]) * s < z)) return z;
     }
   }
@@ -1088,16 +1118,16 @@ static void inject(orc_ctx* c, uint32_t step, uint8_t** moved, int64_t* cap_move
       for (int i = 0; i < 3; ++i) x[i] = A[i] + r1 * (P1[i] - A[i]) + r2 * (P2[i] - A[i]);
       rng4(c, RP_INJECT, (uint32_t)ib, (uint32_t)k, step, 1, w);
       const double tfrac = u01d(w[0], w[1]);
-      float g1, g2;
+      vreal g1, g2;
       uint32_t draw = gauss2(c, RP_INJECT, (uint32_t)ib, (uint32_t)k, step, 2, &g1, &g2);
-      const float vn = inflow_normal_speed(c, B, (uint32_t)ib, (uint32_t)k, step, &draw) * B->invb;
-      const float a = B->ut1 + B->sig * g1, b = B->ut2 + B->sig * g2;
-      float* v = c->v + 3 * p;
+      const vreal vn = inflow_normal_speed(c, B, (uint32_t)ib, (uint32_t)k, step, &draw) * B->invb;
+      const vreal a = B->ut1 + B->sig * g1, b = B->ut2 + B->sig * g2;
+      vreal* v = c->v + 3 * p;
       for (int i = 0; i < 3; ++i) v[i] = (B->t1[i] * a + B->t2[i] * b) - B->nrm[i] * vn;
       c->Ir[p] = 0.0f;
       if (c->cfg.rot_dof > 0) {
         rng4(c, RP_INJECT, (uint32_t)ib, (uint32_t)k, step, draw, w);
-        c->Ir[p] = -(float)c->bcs[B->bc].T * orc_lnf(u01f(w[0]));
+        c->Ir[p] = -(vreal)c->bcs[B->bc].T * VLN(u01f(w[0]));
       }
       c->N = p + 1;
       c->counters[ORC_C_INJECTED]++;
@@ -1224,10 +1254,12 @@ int orc_read_counters(orc_ctx* c, int64_t* out, int32_t n) {
 int orc_cell_state(orc_ctx* c, float* cmax, double* rem, int32_t write) {
   const int64_t n = c->n_tets;
   if (write) {
-    if (cmax) memcpy(c->cmax, cmax, sizeof(float) * n);
+    if (cmax)
+      for (int64_t t = 0; t < n; ++t) c->cmax[t] = cmax[t];
     if (rem) memcpy(c->rem, rem, sizeof(double) * n);
   } else {
-    if (cmax) memcpy(cmax, c->cmax, sizeof(float) * n);
+    if (cmax)
+      for (int64_t t = 0; t < n; ++t) cmax[t] = (float)c->cmax[t];
     if (rem) memcpy(rem, c->rem, sizeof(double) * n);
   }
   return 0;
@@ -2028,14 +2060,14 @@ static void recalibrate(orc_ctx* c, const nd_t* d, int64_t* n_clone, int64_t* n_
     const double rho_N = c->cfg.mass * c->cfg.F_N * (double)Nc / c->vol[t] / d->rho0;
     double rn = Nc > 0 ? a[0] / rho_N : 1.0;
     rn = rn < 0.5 ? 0.5 : rn > 2.0 ? 2.0 : rn;
-    const float sc = (float)sqrt(rt), fr = (float)rr;
-    float ua[3], ub[3];
+    const vreal sc = (vreal)sqrt(rt), fr = (vreal)rr;
+    vreal ua[3], ub[3];
     for (int i = 0; i < 3; ++i) {
-      ua[i] = (float)(a[1 + i] * d->c0);
-      ub[i] = (float)(b[1 + i] * d->c0);
+      ua[i] = (vreal)(a[1 + i] * d->c0);
+      ub[i] = (vreal)(b[1 + i] * d->c0);
     }
     for (int64_t p = c->cstart[t]; p < c->cstart[t + 1]; ++p) {
-      float* v = c->v + 3 * p;
+      vreal* v = c->v + 3 * p;
       for (int i = 0; i < 3; ++i) v[i] = ua[i] + (v[i] - ub[i]) * sc;
       c->Ir[p] = c->Ir[p] * fr;
       uint32_t w[4];
@@ -2069,7 +2101,7 @@ static void recalibrate(orc_ctx* c, const nd_t* d, int64_t* n_clone, int64_t* n_
         const double* D = c->nodes + 3 * c->tets[4 * t + 3];
         for (int i = 0; i < 3; ++i)
           c->x[3 * q + i] = A[i] + s * (B[i] - A[i]) + tt * (C[i] - A[i]) + u * (D[i] - A[i]);
-        memcpy(c->v + 3 * q, c->v + 3 * p, 3 * sizeof(float));
+        memcpy(c->v + 3 * q, c->v + 3 * p, 3 * sizeof(vreal));
         c->Ir[q] = c->Ir[p];
         c->cell[q] = (int32_t)t;
         moved[q] = 1;
@@ -2335,10 +2367,10 @@ void orc_mlp_init(float* params, uint64_t seed) {
     float* W = (float*)v.W[l];
     float* b = (float*)v.b[l];
     for (int i = 0; i < v.nin[l] * v.nout[l]; i += 2, idx += 2) {
-      float g1, g2;
+      vreal g1, g2;
       gauss2(&tmp, 9, (uint32_t)idx, 0, 0, 0, &g1, &g2);
-      W[i] = sd * g1;
-      if (i + 1 < v.nin[l] * v.nout[l]) W[i + 1] = sd * g2;
+      W[i] = (float)(sd * g1);
+      if (i + 1 < v.nin[l] * v.nout[l]) W[i + 1] = (float)(sd * g2);
     }
     for (int j = 0; j < v.nout[l]; ++j) b[j] = 0.0f;
   }

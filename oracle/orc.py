@@ -47,25 +47,31 @@ class OrcBC(C.Structure):
                 ("n", C.c_double)]
 
 
-def build(force: bool = False) -> str:
+LIB64 = os.path.join(HERE, "liborc64.so")
+
+
+def build(force: bool = False, v64: bool = False) -> str:
+    """liborc.so (FP32 velocities, as the method states them), or with v64
+    liborc64.so: the same oracle with FP64 velocities, rotational energies
+    and collision, wall and injection arithmetic (the FP64 reference run)."""
     src = os.path.join(HERE, "orc.c")
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
+    out = LIB64 if v64 else LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
             os.path.getmtime(src), os.path.getmtime(os.path.join(HERE, "orc.h"))):
-        tmp = LIB + f".{os.getpid()}.tmp"
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-                               "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-Wall", "-o", tmp, src, "-lm"])
-        os.replace(tmp, LIB)
-    return LIB
+                               "-D_DEFAULT_SOURCE", *(["-DORC_V64"] if v64 else []), "-fPIC", "-shared", "-Wall",
+                               "-o", tmp, src, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = C.CDLL(LIB)
+def lib(v64: bool = False):
+    if v64 not in _libs:
+        L = C.CDLL(build(v64=v64))
         P = C.c_void_p
         L.orc_create.restype = P
         L.orc_create.argtypes = [C.POINTER(OrcConfig)]
@@ -117,8 +123,8 @@ def lib():
         L.orc_nsf.argtypes = [P, P, P, P]
         L.orc_synthetic_solve.argtypes = [P, P, P, P, P, P, P]
         L.orc_synthetic_residual.argtypes = [P, P, P, P, P, P]
-        _lib = L
-    return _lib
+        _libs[v64] = L
+    return _libs[v64]
 
 
 def _p(a):
@@ -157,10 +163,11 @@ def make_config(scen, **over) -> OrcConfig:
 class Oracle:
     """One oracle simulation context on the host."""
 
-    def __init__(self, scen, **over):
+    def __init__(self, scen, v64=False, **over):
+        """v64: the FP64-velocity build (liborc64.so)."""
         self.scen = scen
         self.cfg = make_config(scen, **over)
-        self.L = lib()
+        self.L = lib(v64)
         self.h = self.L.orc_create(C.byref(self.cfg))
         m = scen.mesh
         self.n_tets = len(m.tets)
