@@ -1912,8 +1912,11 @@ static int aa_coefficients(const double (*Hs)[ORC_AA_MAX], const double* bs, con
 /* S10: the steady synthetic equations (Eq. macro with the closure of Eq.
  * synthetic_closure) solved by pseudo-time iteration.  The base step is the
  * forward-Euler step of each cell's own pseudo-time step (CFL cfg.cfl of its
- * inviscid and viscous wave speeds), g(U) = U + cfl dtl R(U); without open
- * boundaries it is followed by a scaling of every conserved variable that
+ * inviscid and viscous wave speeds), g(U) = U + cfl dtl R(U), the step of a
+ * cell halved while it would leave a non-positive density or temperature
+ * there (at most 11 times; a cell still not positive keeps its state: at a
+ * fixed point no halving occurs); without open boundaries it is followed by a
+ * scaling of every conserved variable that
  * restores the initial total mass (local steps do not conserve it, and the
  * steady equations of a closed domain leave it free).  Anderson acceleration
  * of depth m = cfg.aa_m (Walker & Ni, SIAM J. Numer. Anal. 49, 2011) combines
@@ -1963,10 +1966,17 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
     if (it == 0) res0 = res > 0 ? res : 1.0;
     if (!isfinite(res)) break;
     if (res <= c->cfg.eps_m * res0) break;
-    /* base step */
+    /* base step, each cell's own step halved until its state stays positive
+     * (at most 11 times, then the cell keeps its state) */
     for (int64_t t = 0; t < n; ++t) {
-      const double dt = cfl * dtl[t];
-      for (int q = 0; q < nv; ++q) Gx[nv * t + q] = U[nv * t + q] + dt * R[nv * t + q];
+      double dt = cfl * dtl[t];
+      for (int h = 0; h < 12; ++h) {
+        for (int q = 0; q < nv; ++q) Gx[nv * t + q] = U[nv * t + q] + dt * R[nv * t + q];
+        double Pp[6];
+        prim_from_cons(d, Gx + nv * t, Pp);
+        if (Pp[0] > 0 && Pp[4] > 0) break;
+        dt = h < 10 ? 0.5 * dt : 0.0;
+      }
     }
     if (closed) {
       double Mx = 0.0;

@@ -631,7 +631,8 @@ __global__ void k_cp_face(Params P, CoupleParams C) {
 
 // residual and pseudo-time step of every cell from its face fluxes (the
 // interior ones from k_cp_face, the boundary ones here): dtl = cfl V / sum_f
-// A_f (lambda_f + 2 nu A_f / V); per-block partials of sum V |R|^2 (rho, rho
+// A_f (lambda_f + 2 nu A_f / V), halved while the step would leave the cell
+// a non-positive density or temperature; per-block partials of sum V |R|^2 (rho, rho
 // u, rho E), of the mass after the base step sum V (rho + dtl R_rho) and of
 // the current mass sum V rho
 template <bool DI>
@@ -746,7 +747,16 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
       Rc[5] = 0.0;
     }
     for (int q = 0; q < 6; ++q) C.R[(size_t)q * n + c] = Rc[q];
-    const double dt = C.cfl * (V / lam_sum);
+    // the cell's base step, halved while it would leave a non-positive
+    // density or temperature (at most 11 times, then no step)
+    double dt = C.cfl * (V / lam_sum);
+    for (int h = 0; h < 12; ++h) {
+      double G[6], Pg[6];
+      for (int q = 0; q < 6; ++q) G[q] = Uc[q] + dt * Rc[q];
+      prim_from_cons(C, G, Pg);
+      if (Pg[0] > 0.0 && Pg[4] > 0.0) break;
+      dt = h < 10 ? 0.5 * dt : 0.0;
+    }
     C.dtl[c] = dt;
     for (int q = 0; q < 5; ++q) rs += V * Rc[q] * Rc[q];
     mx = V * (Uc[0] + dt * Rc[0]);
