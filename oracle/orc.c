@@ -1971,10 +1971,10 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
     for (int64_t t = 0; t < n; ++t) {
       double dt = cfl * dtl[t];
       for (int h = 0; h < 12; ++h) {
-        for (int q = 0; q < nv; ++q) Gx[nv * t + q] = U[nv * t + q] + dt * R[nv * t + q];
-        double Pp[6];
-        prim_from_cons(d, Gx + nv * t, Pp);
-        if (Pp[0] > 0 && Pp[4] > 0) break;
+        double* G = Gx + nv * t;
+        for (int q = 0; q < nv; ++q) G[q] = U[nv * t + q] + dt * R[nv * t + q];
+        /* rho > 0 and T_t > 0, the latter as rho (rho E) - |rho u|^2 / 2 - rho (rho e_r) > 0 */
+        if (G[0] > 0 && G[0] * G[4] - 0.5 * (G[1] * G[1] + G[2] * G[2] + G[3] * G[3]) - G[0] * G[5] > 0) break;
         dt = h < 10 ? 0.5 * dt : 0.0;
       }
     }

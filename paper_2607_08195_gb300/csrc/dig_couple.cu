@@ -749,12 +749,12 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
     for (int q = 0; q < 6; ++q) C.R[(size_t)q * n + c] = Rc[q];
     // the cell's base step, halved while it would leave a non-positive
     // density or temperature (at most 11 times, then no step)
+    // (T_t > 0 tested without division: rho (rho E) - |rho u|^2 / 2 - rho (rho e_r) > 0)
     double dt = C.cfl * (V / lam_sum);
     for (int h = 0; h < 12; ++h) {
-      double G[6], Pg[6];
+      double G[6];
       for (int q = 0; q < 6; ++q) G[q] = Uc[q] + dt * Rc[q];
-      prim_from_cons(C, G, Pg);
-      if (Pg[0] > 0.0 && Pg[4] > 0.0) break;
+      if (G[0] > 0.0 && G[0] * G[4] - 0.5 * (G[1] * G[1] + G[2] * G[2] + G[3] * G[3]) - G[0] * G[5] > 0.0) break;
       dt = h < 10 ? 0.5 * dt : 0.0;
     }
     C.dtl[c] = dt;
@@ -897,8 +897,9 @@ __global__ void __launch_bounds__(CPT) k_aa_base(Params P, CoupleParams C) {
 // Anderson coefficients (one block): the block partials summed, the new
 // column's row of the Gram matrix stored, then gamma minimising
 // |f - dF gamma| from the normal equations of the columns scaled to unit
-// norm with 1e-10 added to the diagonal, by Cholesky (one warp, lane i owning
-// row i; a failed factorisation uses no column)
+// norm with 1e-10 added to the diagonal, by a right-looking Cholesky over the
+// block (thread (i, j) owning entry (i, j)) and substitutions in one warp
+// (lane i owning row i); a failed factorisation uses no column
 __global__ void k_aa_solve(CoupleParams C, int nblocks) {
   __shared__ double val[AA_MAX + 1];
   __shared__ double L[AA_MAX][AA_MAX + 1];
@@ -957,7 +958,7 @@ __global__ void k_aa_solve(CoupleParams C, int nblocks) {
   }
   __syncthreads();
   // scaled, regularised normal matrix: thread (ti, tq) owns entry (ti, tq)
-  __shared__ double scs[AA_MAX];
+  __shared__ double scs[AA_MAX], inv[AA_MAX];
   __shared__ int okf;
   const int ti = threadIdx.x >> 5, tq = threadIdx.x & 31;
   if (threadIdx.x < k) {
@@ -969,19 +970,25 @@ __global__ void k_aa_solve(CoupleParams C, int nblocks) {
   __syncthreads();
   // right-looking Cholesky: every entry receives its updates in the order of
   // the left-looking form (column 0 first), then the division by its pivot
+  // (pivots by rsqrt, so that the column is scaled by a product: FP64
+  // division and square root are long dependent sequences on this part)
   bool ok = true;
   for (int j = 0; j < k; ++j) {
     if (threadIdx.x == 0) {
       const double d = L[j][j];
       okf = d > 0;
-      if (d > 0) L[j][j] = sqrt(d);
+      if (d > 0) {
+        const double r = rsqrt(d);
+        inv[j] = r;
+        L[j][j] = d * r;
+      }
     }
     __syncthreads();
     if (!okf) {
       ok = false;
       break;
     }
-    if (tq == j && ti > j && ti < k) L[ti][j] /= L[j][j];
+    if (tq == j && ti > j && ti < k) L[ti][j] *= inv[j];
     __syncthreads();
     if (ti > j && ti < k && tq > j && tq <= ti) L[ti][tq] -= L[ti][j] * L[tq][j];
     __syncthreads();
@@ -995,13 +1002,13 @@ __global__ void k_aa_solve(CoupleParams C, int nblocks) {
     for (int i = 0; i < k; ++i) {
       double t = lane < i ? L[i][lane] * yi : 0.0;
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      const double y = (__shfl_sync(0xffffffffu, bi, i) - t) / L[i][i];
+      const double y = (__shfl_sync(0xffffffffu, bi, i) - t) * inv[i];
       if (lane == i) yi = y;
     }
     for (int i = k - 1; i >= 0; --i) {
       double t = lane > i && lane < k ? L[lane][i] * gi : 0.0;
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      const double g = (__shfl_sync(0xffffffffu, yi, i) - t) / L[i][i];
+      const double g = (__shfl_sync(0xffffffffu, yi, i) - t) * inv[i];
       if (lane == i) gi = g;
     }
     if (lane < k) {
