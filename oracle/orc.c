@@ -1643,6 +1643,19 @@ static void extract_hot(orc_ctx* c, const nd_t* d, int64_t* n_rej, int64_t* n_re
     memcpy(avail, nxt, n);
     if (filled == 0) break;
   }
+  /* a cell still without a state (no accepted cell connected to it within
+   * the layers) starts the solve from the configuration's initial state
+   * (density m n_init, velocity u_init, temperatures T_init: for an open
+   * domain the free stream) with zero HoT; flag 0, not recalibrated */
+  for (int64_t t = 0; t < n; ++t) {
+    if (avail[t]) continue;
+    double* h = c->cp_half + 6 * t;
+    h[0] = 1.0;
+    for (int i = 0; i < 3; ++i) h[1 + i] = c->cfg.u_init[i] / d->c0;
+    h[4] = 1.0;
+    h[5] = 1.0;
+    memset(c->cp_hot + 12 * t, 0, 12 * sizeof(double));
+  }
   free(nxt); free(avail); free(nbar);
 }
 
@@ -1927,15 +1940,21 @@ static int aa_coefficients(const double (*Hs)[ORC_AA_MAX], const double* bs, con
  * b_i = <dF_i, f_k> follows from f_k = f_{k-1} + dF_new as b_i + H_i,new,
  * except for the new column's, which is computed.  A combined state with a
  * non-positive density or temperature in some cell is replaced by g(U_k),
- * and the history is cleared.  Stops after N_m iterations or when the residual norm falls to
- * eps_m times its first value. */
+ * and the history is cleared.  A non-finite residual, or one above 100 times
+ * the best so far, sends the iteration back to the best iterate with half
+ * the CFL number (at most six times) and no history.  Stops after N_m
+ * iterations or when the residual norm falls to eps_m times its first
+ * value; the result is the last iterate, or the best one if the last is
+ * worse. */
 static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* iters, double* res_out) {
   const int64_t n = c->n_tets;
   const int nv = 6;
   const int64_t len = nv * n;
   const int m = c->cfg.aa_m < 0 ? 0 : c->cfg.aa_m > ORC_AA_MAX ? ORC_AA_MAX : c->cfg.aa_m;
-  const double cfl = c->cfg.cfl > 0 ? c->cfg.cfl : 1.5;
+  double cfl = c->cfg.cfl > 0 ? c->cfg.cfl : 1.5;
+  const double cfl_min = cfl / 64.0;
   double* U = (double*)malloc(sizeof(double) * len);
+  double* Ub = (double*)malloc(sizeof(double) * len); /* the best iterate so far */
   double* P = (double*)calloc(6 * n, sizeof(double));
   double* R = (double*)malloc(sizeof(double) * len);
   double* G = (double*)malloc(sizeof(double) * 15 * n);
@@ -1958,14 +1977,32 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
     w[t] = c->vol[t] / L3;
     M0 += w[t] * U[nv * t];
   }
-  double res0 = 0.0, res = 0.0;
+  double res0 = 0.0, res = 0.0, resb = 0.0;
   double Hs[ORC_AA_MAX][ORC_AA_MAX], bs[ORC_AA_MAX];
-  int it = 0, nh = 0, head = 0;
+  int it = 0, nh = 0, head = 0, fresh = 1; /* fresh: no previous f to difference with */
   for (it = 0; it < c->cfg.N_m; ++it) {
     res = sqrt(residual(c, d, src, U, R, dtl, P, G, S));
-    if (it == 0) res0 = res > 0 ? res : 1.0;
-    if (!isfinite(res)) break;
+    if (it == 0) {
+      res0 = res > 0 ? res : 1.0;
+      resb = res;
+      memcpy(Ub, U, sizeof(double) * len);
+    }
     if (res <= c->cfg.eps_m * res0) break;
+    /* divergence (a non-finite residual or one 100 times the best): back to
+     * the best iterate with half the CFL number (down to 1/64 of the
+     * configured one) and no history; the next iteration starts there */
+    if (!(res <= 100.0 * resb)) {
+      if (cfl <= cfl_min) break;
+      memcpy(U, Ub, sizeof(double) * len);
+      cfl = 0.5 * cfl;
+      nh = 0;
+      fresh = 1;
+      continue;
+    }
+    if (res < resb) {
+      resb = res;
+      memcpy(Ub, U, sizeof(double) * len);
+    }
     /* base step, each cell's own step halved until its state stays positive
      * (at most 11 times, then the cell keeps its state) */
     for (int64_t t = 0; t < n; ++t) {
@@ -1992,7 +2029,7 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
     for (int64_t i = 0; i < len; ++i) f[i] = Gx[i] - U[i];
     int slot[ORC_AA_MAX];
     double gam[ORC_AA_MAX];
-    if (it > 0) {
+    if (!fresh) {
       const int s0 = head;
       double* a = dF + len * s0;
       double* b = dG + len * s0;
@@ -2010,6 +2047,7 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
       }
       bs[s0] = wdot(a, f, w, n);
     }
+    fresh = 0;
     memcpy(fp, f, sizeof(double) * len);
     memcpy(Gp, Gx, sizeof(double) * len);
     for (int i = 0; i < nh; ++i) slot[i] = ((head - nh + i) % m + m) % m;
@@ -2030,6 +2068,12 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
       nh = 0;
     }
   }
+  /* the result: the last iterate, or the best one if the last is worse (a
+   * stop at N_m after a rise of the residual, or a divergence) */
+  if (!(res <= resb)) {
+    memcpy(U, Ub, sizeof(double) * len);
+    res = resb;
+  }
   int ok = isfinite(res);
   for (int64_t t = 0; t < n && ok; ++t) {
     prim_from_cons(d, U + nv * t, c->cp_new + 6 * t);
@@ -2037,7 +2081,7 @@ static int solve_synthetic(orc_ctx* c, const nd_t* d, const double* src, int* it
   }
   *iters = it;
   *res_out = res / res0;
-  free(U); free(P); free(R); free(G); free(S); free(dtl); free(w); free(Gx); free(f); free(fp); free(Gp);
+  free(U); free(Ub); free(P); free(R); free(G); free(S); free(dtl); free(w); free(Gx); free(f); free(fp); free(Gp);
   free(dF); free(dG);
   return ok ? 0 : -5;
 }

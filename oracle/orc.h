@@ -146,7 +146,7 @@ void orc_adam(float* params, double* m, double* v, const double* g, int64_t t, d
 #define ORC_CLOSURE_YMAX 4.0
 
 /* most fill layers after the reconstruction layers of a coupling */
-#define ORC_FILL_LAYERS 64
+#define ORC_FILL_LAYERS 1024
 int orc_closure_set(orc_ctx* c, const float* params);
 int orc_closure_features(orc_ctx* c, int32_t which, float* X);
 int orc_closure_targets(orc_ctx* c, int32_t which, const float* X, int64_t n_rows, float* Y);

@@ -570,6 +570,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
   C.dtl = A.take<double>(n);
   C.fp = A.take<double>(6 * n);
   C.Gp = A.take<double>(6 * n);
+  C.Ub = A.take<double>(6 * n);
   const size_t naa = (size_t)std::max(ctx->cfg.aa_m, 1);
   C.dF = A.take<double>(naa * 6 * n);
   C.dG = A.take<double>(naa * 6 * n);
@@ -721,6 +722,7 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
     C.T0 = c.T_init;
     C.rho0 = c.mass * c.n_init;
     C.c0 = std::sqrt(KB / c.mass * C.T0);
+    for (int i = 0; i < 3; ++i) C.u_ref[i] = c.u_init[i] / C.c0;
     C.Kn = c.Kn;
     C.omega = c.omega;
     C.dr = (double)c.rot_dof;
@@ -1303,7 +1305,18 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
     launch_closure_features(ctx->P, C, ctx->P.phi_win, (double)ctx->n_win, C.feat, s);
     launch_mlp_forward(ctx->cl_p, C.feat, ctx->n_tets, C.ypred, s);
   }
-  launch_couple_s9(ctx->P, C, ctx->cfg.passes, learned ? C.ypred : nullptr, s);
+  int* av = nullptr;
+  launch_couple_s9(ctx->P, C, ctx->cfg.passes, learned ? C.ypred : nullptr, &av, s);
+  // further chunks of fill layers while the last layer of a chunk still filled cells
+  for (int q = DIG_FILL_CHUNK; q < DIG_FILL_LAYERS; q += DIG_FILL_CHUNK) {
+    int last = 0;
+    CK(cudaMemcpyAsync(&last, C.fillcnt + q - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int rw = wait_stream(ctx);
+    if (rw) return rw;
+    if (last == 0) break;
+    launch_couple_fill(ctx->P, C, q, q + DIG_FILL_CHUNK, &av, s);
+  }
+  launch_couple_unreached(ctx->P, C, av, s);
   int rs = run_s10(ctx);
   if (rs) return rs;
   CoupleScalars sc{};
@@ -1313,10 +1326,12 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
   int rc = wait_stream(ctx);
   if (rc) return rc;
   out->iters = sc.iters;
-  out->residual = sc.res / (sc.res0 > 0 ? sc.res0 : 1.0);
+  // the result is the best iterate when the last one is worse (k_cp_final)
+  const double res = sc.res <= sc.res_best ? sc.res : sc.res_best;
+  out->residual = res / (sc.res0 > 0 ? sc.res0 : 1.0);
   const uint32_t sub = (uint32_t)ctx->n_couple;
   ctx->n_couple++;
-  bool solved = !sc.bad && std::isfinite(sc.res);
+  bool solved = !sc.bad && std::isfinite(res);
   if (solved) {
     launch_couple_s11(ctx->P, C, ctx->buf[ctx->cur], N, sub, ctx->P.aq, s);
     launch_scan(ctx->P, s);

@@ -414,6 +414,22 @@ __global__ void k_cp_recon(Params P, CoupleParams C, const int* __restrict__ av_
   }
 }
 
+// a cell that no accepted cell reaches within the reconstruction and fill
+// layers (a region disconnected from every reliable cell) starts the solve
+// from the configuration's initial state: density rho0, drift u_init,
+// temperatures T0 (for an open domain the free stream), with zero HoT.  It
+// keeps flag 0 and is not recalibrated.
+__global__ void k_cp_unreached(Params P, CoupleParams C, const int* __restrict__ av) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_cells;
+  if (c >= n || av[c]) return;
+  C.half[c] = 1.0;
+  for (int i = 0; i < 3; ++i) C.half[(size_t)(1 + i) * n + c] = C.u_ref[i];
+  C.half[(size_t)4 * n + c] = 1.0;
+  C.half[(size_t)5 * n + c] = 1.0;
+  for (int q = 0; q < 12; ++q) C.hot[(size_t)q * n + c] = 0.0;
+}
+
 __device__ __forceinline__ void cons_from_prim(const CoupleParams& C, const double* Pp, double* U) {
   const double rho = Pp[0], uu = Pp[1] * Pp[1] + Pp[2] * Pp[2] + Pp[3] * Pp[3];
   const double er = C.dr > 0 ? 0.5 * C.dr * Pp[5] : 0.0;
@@ -750,7 +766,7 @@ __global__ void __launch_bounds__(CPT) k_cp_flux(Params P, CoupleParams C) {
     // the cell's base step, halved while it would leave a non-positive
     // density or temperature (at most 11 times, then no step)
     // (T_t > 0 tested without division: rho (rho E) - |rho u|^2 / 2 - rho (rho e_r) > 0)
-    double dt = C.cfl * (V / lam_sum);
+    double dt = C.cfl * ldexp(1.0, -C.scal->halvings) * (V / lam_sum);
     for (int h = 0; h < 12; ++h) {
       double G[6];
       for (int q = 0; q < 6; ++q) G[q] = Uc[q] + dt * Rc[q];
@@ -800,15 +816,37 @@ __global__ void k_cp_reduce(CoupleParams C, int nblocks) {
     CoupleScalars* S = C.scal;
     const int it = S->itc;
     const double res = sqrt(sh[0][0]);
+    S->save = 0;
+    S->revert = 0;
     if (it == 0) {
       S->res0 = res > 0 ? res : 1.0;
       S->M0 = sh[2][0];
+      S->res_best = res;
+      S->save = 1;
     }
     S->res = res;
     S->iters = it;
-    if (!isfinite(res) || res <= C.eps_m * S->res0) {
+    if (res <= C.eps_m * S->res0) {
       S->done = 1;
+    } else if (!(res <= 100.0 * S->res_best)) {
+      // divergence (a non-finite residual or one 100 times the best): back to
+      // the best iterate with half the CFL number (at most six times) and no
+      // history; the next iteration starts there
+      if (S->halvings >= 6) {
+        S->done = 1;
+      } else {
+        S->revert = 1;
+        S->halvings += 1;
+        S->nh = 0;
+        S->fresh = 1;
+        S->aabad = 0;
+        S->itc = it + 1;
+      }
     } else {
+      if (res < S->res_best) {
+        S->res_best = res;
+        S->save = 1;
+      }
       S->mscale = C.closed ? S->M0 / sh[1][0] : 1.0;
       if (S->aabad) {  // the last combination fell back to the base step: restart the history
         S->nh = 0;
@@ -834,9 +872,16 @@ __global__ void __launch_bounds__(CPT) k_aa_base(Params P, CoupleParams C) {
   const int n = P.n_cells;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = c < n;
+  if (S->revert) {  // divergence: back to the best iterate, no step this iteration
+    if (in)
+      for (int q = 0; q < NV; ++q) C.U[(size_t)q * n + c] = C.Ub[(size_t)q * n + c];
+    return;
+  }
+  if (S->save && in)
+    for (int q = 0; q < NV; ++q) C.Ub[(size_t)q * n + c] = C.U[(size_t)q * n + c];
   const int m = C.aa_m;
   const int it = S->itc - 1;
-  const bool push = it > 0 && m > 0;
+  const bool push = it > 0 && m > 0 && !S->fresh;
   const int head = S->head;
   const int nhn = push ? min(S->nh + 1, m) : 0;
   const int hn = (head + 1) % (m > 0 ? m : 1);
@@ -905,10 +950,10 @@ __global__ void k_aa_solve(CoupleParams C, int nblocks) {
   __shared__ double L[AA_MAX][AA_MAX + 1];
   __shared__ int sl[AA_MAX];
   CoupleScalars* S = C.scal;
-  if (S->done) return;
+  if (S->done || S->revert) return;
   const int m = C.aa_m;
   const int it = S->itc - 1;
-  const bool push = it > 0;
+  const bool push = it > 0 && !S->fresh;
   const int head = S->head;
   const int nhn = push ? min(S->nh + 1, m) : S->nh;
   const int hn = push ? (head + 1) % m : head;
@@ -955,6 +1000,7 @@ __global__ void k_aa_solve(CoupleParams C, int nblocks) {
   if (threadIdx.x == 0) {
     S->head = hn;
     S->nh = k;
+    S->fresh = 0;
   }
   __syncthreads();
   // scaled, regularised normal matrix: thread (ti, tq) owns entry (ti, tq)
@@ -1026,7 +1072,7 @@ __global__ void k_aa_update(Params P, CoupleParams C) {
   constexpr int NV = DI ? 6 : 5;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
-  if (c >= n || C.scal->done) return;
+  if (c >= n || C.scal->done || C.scal->revert) return;
   const int k = C.scal->k;
   double U[6] = {0, 0, 0, 0, 0, 0}, Pp[6];
   for (int q = 0; q < NV; ++q) {
@@ -1045,10 +1091,15 @@ __global__ void k_cp_final(Params P, CoupleParams C) {
   if (c == 0 && !C.scal->done) C.scal->iters = C.scal->itc;
   if (c >= n) return;
   double U[6], Pp[6];
-  const bool fb = C.scal->aabad != 0;  // N_m reached right after a failed combination
+  // the best iterate if the last one is worse (a stop at N_m after a rise
+  // of the residual, or a divergence); else a pending fallback (N_m reached
+  // right after a failed combination) or the last iterate
+  const bool best = !(C.scal->res <= C.scal->res_best);
+  const bool fb = C.scal->aabad != 0;
   for (int q = 0; q < 6; ++q) {
     const size_t k = (size_t)q * n + c;
-    U[q] = fb && (q < 5 || C.dr > 0) ? C.Gp[k] : C.U[k];
+    const bool carried = q < 5 || C.dr > 0;
+    U[q] = best && carried ? C.Ub[k] : fb && carried ? C.Gp[k] : C.U[k];
   }
   prim_from_cons(C, U, Pp);
   for (int q = 0; q < 6; ++q) C.newst[(size_t)q * n + c] = Pp[q];
@@ -1258,7 +1309,8 @@ __global__ void k_recal_clone(Params P, CoupleParams C, Buf CUR, const int* __re
 int nb_for(int n, int t) { return (n + t - 1) / t; }
 }  // namespace
 
-void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const float* ypred, cudaStream_t s) {
+void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const float* ypred, int** av,
+                      cudaStream_t s) {
   const int n = P.n_cells, nb = nb_for(n, CPT);
   k_cp_extract<<<nb, CPT, 0, s>>>(P, C, P.phi_ewma, 1.0);
   k_cp_grad<<<nb, CPT, 0, s>>>(P, C, C.own, C.grad);
@@ -1275,15 +1327,35 @@ void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const 
     a = b;
     b = t;
   }
+  g_launches += 3 + passes;
+  *av = a;
   // fill layers: rejected cells beyond the reconstruction layers still need a
   // state for the solve; they are filled the same way, layer by layer
-  for (int q = 0; q < DIG_FILL_LAYERS; ++q) {
+  launch_couple_fill(P, C, 0, DIG_FILL_CHUNK, av, s);
+}
+
+// A layer that returns early (the previous one filled nothing) leaves its
+// output array as it was; both arrays then already hold the same
+// availability, since a layer that fills nothing copies it unchanged, so the
+// alternation below stays exact.
+void launch_couple_fill(const Params& P, const CoupleParams& C, int q0, int q1, int** av, cudaStream_t s) {
+  const int n = P.n_cells, nb = nb_for(n, CPT);
+  int* a = *av;
+  int* b = a == C.avail ? C.avail2 : C.avail;
+  for (int q = q0; q < q1; ++q) {
     k_cp_recon<<<nb, CPT, 0, s>>>(P, C, a, b, q);
     int* t = a;
     a = b;
     b = t;
   }
-  g_launches += 3 + passes + DIG_FILL_LAYERS;
+  g_launches += q1 - q0;
+  *av = a;
+}
+
+void launch_couple_unreached(const Params& P, const CoupleParams& C, const int* av, cudaStream_t s) {
+  const int n = P.n_cells, nb = nb_for(n, CPT);
+  k_cp_unreached<<<nb, CPT, 0, s>>>(P, C, av);
+  g_launches += 1;
 }
 
 void launch_couple_s10_init(const Params& P, const CoupleParams& C, cudaStream_t s) {

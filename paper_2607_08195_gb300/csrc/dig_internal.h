@@ -124,6 +124,7 @@ struct Params {
 // The scalars of one solve; cleared before every coupling.
 struct CoupleScalars {
   double res0, res;
+  double res_best;  // the smallest residual so far (its state in CoupleParams::Ub)
   double M0;      // total mass of the initial state (closed domains)
   double mscale;  // mass-restoring factor of the current base step (1 for open domains)
   int iters, done, bad;
@@ -131,6 +132,10 @@ struct CoupleScalars {
   int head, nh;   // Anderson history: next slot to write, columns held
   int aabad;      // a combined state was not positive: fall back to the base step
   int k;          // columns used by the current combination (0: base step)
+  int halvings;   // of the CFL number after divergences (the step scale is 2^-halvings)
+  int save;       // this iteration's state is the best so far: copy it to Ub
+  int revert;     // divergence: this iteration returns to Ub instead of stepping
+  int fresh;      // no previous f to difference with (after a return to Ub)
 };
 
 // most Anderson-acceleration columns
@@ -146,12 +151,16 @@ struct AAState {
   int slot[AA_MAX];
 };
 
-// most fill layers after the reconstruction layers (see k_cp_recon)
-constexpr int DIG_FILL_LAYERS = 64;
+// most fill layers after the reconstruction layers (see k_cp_recon), issued
+// in chunks of DIG_FILL_CHUNK; the host stops after a chunk whose last layer
+// filled nothing
+constexpr int DIG_FILL_LAYERS = 1024;
+constexpr int DIG_FILL_CHUNK = 64;
 
 struct CoupleParams {
   double L0, T0, rho0, c0, Kn, omega, gam, dr, Zr, mass, FN, kB, KnD_max, wall_t;
   double acc_w0;       // min(m, n_a): the samples a moving average stands for at this coupling
+  double u_ref[3];     // initial drift / c0: velocity of the state of unreached cells
   double iL2;          // 1 / L0^2
   const double* vnd;   // [n] cell volumes / L0^3
   const double* ivnd;  // [n] L0^3 / cell volumes
@@ -181,6 +190,7 @@ struct CoupleParams {
   double eps_m, cfl;
   double* dtl;    // [n] cfl times the cell's CFL-1 pseudo-time step
   double *fp, *Gp;    // [6][n] previous f = g(U) - U and g(U) (Gp holds g(U_k) during an iteration)
+  double* Ub;         // [6][n] the best iterate so far
   double *dF, *dG;    // [aa_m][6][n] differences of consecutive f and g(U)
   double* apart;      // [AA_MAX + 1][blocks] per-block dot products
   AAState* aa;
@@ -188,8 +198,15 @@ struct CoupleParams {
   int* clone_total;
 };
 
-// S9; with ypred non-null the learned closure's outputs replace the HoT
-void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const float* ypred, cudaStream_t s);
+// S9; with ypred non-null the learned closure's outputs replace the HoT.  It
+// runs extraction, the reconstruction passes and the first chunk of fill
+// layers and leaves in *av the availability array that holds the result.
+void launch_couple_s9(const Params& P, const CoupleParams& C, int passes, const float* ypred, int** av,
+                      cudaStream_t s);
+// fill layers [q0, q1) continuing from availability *av (updated)
+void launch_couple_fill(const Params& P, const CoupleParams& C, int q0, int q1, int** av, cudaStream_t s);
+// cells still unavailable after the fill layers take the initial state with zero HoT
+void launch_couple_unreached(const Params& P, const CoupleParams& C, const int* av, cudaStream_t s);
 // closure inputs X[n][13] from sums phi over cnt steps (also fills C.wnorm)
 void launch_closure_features(const Params& P, const CoupleParams& C, const double* phi, double cnt, float* X,
                              cudaStream_t s);

@@ -525,6 +525,72 @@ def test_couple_fixed_point_identity_on_gpu():
     assert np.array_equal(v0, v1) and np.array_equal(x0, x1) and np.array_equal(c0, c1)
 
 
+def uniform_phi(vol, scen, scale):
+    """Summation variables of a Maxwellian at rest at T_init, n_init * scale."""
+    kT_m = W.K_B * scen.T_init / scen.gas.mass
+    N = scen.n_init * vol / scen.F_N * scale
+    phi = np.zeros((len(vol), dig.NPHI))
+    phi[:, 0] = N
+    phi[:, 4:7] = (N * kT_m)[:, None]
+    return phi
+
+
+def test_deep_fill_layers_match_oracle():
+    """One accepted corner of the 48,000-tet cavity, every other cell dilute
+    (rejected): after 3 reconstruction passes the rest of the mesh is reached
+    only by fill layers, about 75 of them, so the GPU's fill runs past its
+    first chunk of 64 layers.  Flags and counts agree exactly, M^{k+1/2} and
+    HoT within the tolerance of the other coupling tests (the fill is a chain
+    of neighbour means, summed in the same order on both sides)."""
+    s = W.cavity_scenario(20, 480_000, 0.1, seed=3)
+    over = dict(N_m=5, passes=3, KnD_max=5.0)
+    o = orc.Oracle(s, **over)
+    o.init()
+    g = dig.Solver(s, "cuda:0", **over)
+    g.write(*o.read())
+    vol = o.mesh_info()["vol"]
+    cen = s.mesh.nodes[s.mesh.tets].mean(axis=1) / s.L
+    scale = np.where((cen < -0.45).all(axis=1), 1.0, 0.05)
+    phi = uniform_phi(vol, s, scale)
+    phi[:, 1] = phi[:, 0] * 20.0 * cen[:, 1]  # a drift that varies, so the means carry information
+    phi[:, 4] += phi[:, 1] ** 2 / np.maximum(phi[:, 0], 1e-300)
+    g.write_moments(dig.PHI_EWMA, phi)
+    o.write_moments(orc.PHI_EWMA, phi)
+    rg, ro = g.couple(), o.couple()
+    fl = o.read_couple(3)[:, 0]
+    assert np.array_equal(g.read_couple(3)[:, 0], fl)
+    assert (fl == 1).sum() == int((scale == 1.0).sum()) and (fl == 0).sum() == 0
+    assert (fl == 3).sum() > 0.9 * len(fl)
+    for k in ("n_rejected", "n_reconstructed"):
+        assert rg[k] == ro[k], (k, rg[k], ro[k])
+    # the accepted cells' own states differ by the rounding of their moments
+    # (relative 1e-9 as in the other coupling tests; the HoT of a gas at rest
+    # is round-off itself, hence the absolute 1e-12 in nondimensional units)
+    for which in (0, 1):
+        a, b = g.read_couple(which), o.read_couple(which)
+        sc = np.abs(b).max(axis=0)
+        assert np.all(np.abs(a - b) <= 1e-9 * sc + 1e-12), (which, np.abs(a - b).max())
+
+
+def test_unreached_cells_take_initial_state_on_gpu():
+    """No accepted cell anywhere: every cell keeps flag 0 and starts the solve
+    from the configuration's initial state with zero HoT, as in the oracle."""
+    s = dataclasses.replace(W.cavity_scenario(3, 5000, 0.1, seed=3), u_init=(40.0, -15.0, 0.0))
+    over = dict(N_m=1, passes=2, KnD_max=1.5)
+    o = orc.Oracle(s, **over)
+    o.init()
+    g = dig.Solver(s, "cuda:0", **over)
+    g.write(*o.read())
+    phi = uniform_phi(o.mesh_info()["vol"], s, 0.05)
+    g.write_moments(dig.PHI_EWMA, phi)
+    o.write_moments(orc.PHI_EWMA, phi)
+    rg, ro = g.couple(), o.couple()
+    assert rg["n_rejected"] == ro["n_rejected"] == o.n_tets and rg["n_reconstructed"] == 0
+    assert np.all(g.read_couple(3) == 0)
+    assert np.array_equal(g.read_couple(0), o.read_couple(0))
+    assert np.all(g.read_couple(1) == 0.0)
+
+
 # ----------------------------------------------------------- hypersonic sphere
 def test_sphere_bit_exact():
     """Hypersonic argon sphere (Mach 10 free stream, diffuse body at 500 K) on

@@ -907,9 +907,30 @@ def test_reconstruction_layers():
                 dq.append(nb)
     assert np.array_equal(flags == 2, (dist >= 1) & (dist <= passes))
     assert r["n_reconstructed"] == int(((dist >= 1) & (dist <= passes)).sum()) > 0
+    # the rest of the (connected) mesh is reached by the fill layers
+    assert np.array_equal(flags == 3, dist > passes) and (dist > passes).any()
     for t in np.flatnonzero(dist == 1)[:20]:
         nb = [q for q in nbr[t] if q >= 0 and acc[q]]
         assert np.allclose(half[t], own[nb].mean(axis=0), rtol=1e-12)
+
+
+def test_unreached_cells_take_initial_state():
+    """With no accepted cell anywhere, no layer can fill a cell: every cell
+    keeps flag 0 and starts the solve from the configuration's initial state
+    (density n_init m, drift u_init, temperatures T_init; nondimensional 1,
+    u_init / sqrt(k T_init / m), 1, 1) with zero HoT."""
+    s = dataclasses.replace(W.cavity_scenario(3, 5000, 0.1, seed=3), u_init=(40.0, -15.0, 0.0))
+    o = orc.Oracle(s, N_m=1, KnD_max=1.5, passes=2)
+    o.init()
+    o.write_moments(orc.PHI_EWMA, equilibrium_phi(o, s, rho_scale=0.05))
+    r = o.couple()
+    n = o.n_tets
+    assert r["n_rejected"] == n and r["n_reconstructed"] == 0
+    assert np.all(o.read_couple(3) == 0)
+    c0 = math.sqrt(KB * s.T_init / s.gas.mass)
+    want = np.array([1.0, 40.0 / c0, -15.0 / c0, 0.0, 1.0, 1.0])
+    assert np.array_equal(o.read_couple(0), np.broadcast_to(want, (n, 6)))
+    assert np.all(o.read_couple(1) == 0.0)
 
 
 @pytest.mark.parametrize("recon", [0, 1])
