@@ -575,6 +575,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
   C.dF = A.take<double>(naa * 6 * n);
   C.dG = A.take<double>(naa * 6 * n);
   C.apart = A.take<double>(couple_apart_count((int)n));
+  C.aab = couple_aa_blocks((int)n);
   C.aa = A.take<AAState>(1);
   C.avail = A.take<int>(n);
   C.avail2 = A.take<int>(n);

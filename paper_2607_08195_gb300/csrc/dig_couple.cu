@@ -862,23 +862,26 @@ __global__ void k_cp_reduce(CoupleParams C, int nblocks) {
 // differences dF_new, dG_new of f and g(U) go to ring slot `head`, and the
 // block's partial (volume-weighted) dot products <dF_i, dF_new> of every held
 // column i in age order (the new one last) and <dF_new, f> go to apart;
-// without it U = g(U).
+// without it U = g(U).  C.aab blocks loop over the cells, each thread
+// accumulating its dot products in its own column of shared memory, so that
+// the FP64 reduction across threads happens once per block and not once per
+// cell.
 template <bool DI>
 __global__ void __launch_bounds__(CPT) k_aa_base(Params P, CoupleParams C) {
   constexpr int NV = DI ? 6 : 5;  // conserved variables carried (rho e_r only for a diatomic gas)
-  __shared__ double red[CPT / 32][AA_MAX + 1];
+  __shared__ double red[AA_MAX + 1][CPT];
+  __shared__ int sl[AA_MAX];
   const CoupleScalars* S = C.scal;
   if (S->done) return;
   const int n = P.n_cells;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = c < n;
+  const int t = threadIdx.x;
+  const int stride = gridDim.x * CPT;
   if (S->revert) {  // divergence: back to the best iterate, no step this iteration
-    if (in)
+    for (int c = blockIdx.x * CPT + t; c < n; c += stride)
       for (int q = 0; q < NV; ++q) C.U[(size_t)q * n + c] = C.Ub[(size_t)q * n + c];
     return;
   }
-  if (S->save && in)
-    for (int q = 0; q < NV; ++q) C.Ub[(size_t)q * n + c] = C.U[(size_t)q * n + c];
+  const bool save = S->save;
   const int m = C.aa_m;
   const int it = S->itc - 1;
   const bool push = it > 0 && m > 0 && !S->fresh;
@@ -886,12 +889,19 @@ __global__ void __launch_bounds__(CPT) k_aa_base(Params P, CoupleParams C) {
   const int nhn = push ? min(S->nh + 1, m) : 0;
   const int hn = (head + 1) % (m > 0 ? m : 1);
   const double s = S->mscale;
-  double f[6] = {0, 0, 0, 0, 0, 0}, dfn[6] = {0, 0, 0, 0, 0, 0};
-  if (in) {
+  if (push) {
+    // slots of the held columns in age order; the new one (slot head) is last
+    if (t < nhn - 1) sl[t] = ((hn - nhn + t) % m + m) % m;
+    for (int i = 0; i <= nhn; ++i) red[i][t] = 0.0;
+  }
+  __syncthreads();
+  for (int c = blockIdx.x * CPT + t; c < n; c += stride) {
+    double f[6] = {0, 0, 0, 0, 0, 0}, dfn[6] = {0, 0, 0, 0, 0, 0};
     const double dt = C.dtl[c];
     for (int q = 0; q < NV; ++q) {
       const size_t k = (size_t)q * n + c;
       const double u = C.U[k];
+      if (save) C.Ub[k] = u;
       double gx = u + dt * C.R[k];
       if (C.closed) gx *= s;
       if (m == 0) {
@@ -909,33 +919,39 @@ __global__ void __launch_bounds__(CPT) k_aa_base(Params P, CoupleParams C) {
       C.Gp[k] = gx;
       f[q] = fq;
     }
+    if (!push) continue;
+    const double V = C.vnd[c];
+    double dv[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) dv[q] = V * dfn[q];
+    // the held columns are not written by this kernel (the new one goes to
+    // slot head, which is not among them)
+#pragma unroll 4
+    for (int i = 0; i < nhn - 1; ++i) {
+      const double* col = C.dF + (size_t)sl[i] * 6 * n + c;
+      double a = red[i][t];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) a = fma(__ldg(col + (size_t)q * n), dv[q], a);
+      red[i][t] = a;
+    }
+    double a = red[nhn - 1][t], b = red[nhn][t];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      a = fma(dfn[q], dv[q], a);
+      b = fma(dv[q], f[q], b);
+    }
+    red[nhn - 1][t] = a;
+    red[nhn][t] = b;
   }
   if (!push) return;
-  const double V = in ? C.vnd[c] : 0.0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i <= nhn; ++i) {
-    double h = 0.0;
-    if (in) {
-      double r = 0.0;
-      if (i < nhn - 1) {
-        const int sl = ((hn - nhn + i) % m + m) % m;
-        for (int q = 0; q < NV; ++q) r += C.dF[((size_t)sl * 6 + q) * n + c] * dfn[q];
-      } else if (i == nhn - 1) {
-        for (int q = 0; q < NV; ++q) r += dfn[q] * dfn[q];
-      } else {
-        for (int q = 0; q < NV; ++q) r += dfn[q] * f[q];
-      }
-      h = V * r;
-    }
-    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
-    if (lane == 0) red[warp][i] = h;
-  }
   __syncthreads();
-  const int t = threadIdx.x;
-  if (t <= nhn) {
-    double a = red[0][t];
-    for (int w = 1; w < CPT / 32; ++w) a += red[w][t];
-    C.apart[(size_t)(t < nhn ? t : AA_MAX) * gridDim.x + blockIdx.x] = a;
+  const int lane = t & 31, warp = t >> 5;
+  for (int i = warp; i <= nhn; i += CPT / 32) {
+    double a = 0.0;
+#pragma unroll
+    for (int r = 0; r < CPT; r += 32) a += red[i][r + lane];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) C.apart[(size_t)(i < nhn ? i : AA_MAX) * gridDim.x + blockIdx.x] = a;
   }
 }
 
@@ -1009,7 +1025,7 @@ __global__ void k_aa_solve(CoupleParams C, int nblocks) {
   const int ti = threadIdx.x >> 5, tq = threadIdx.x & 31;
   if (threadIdx.x < k) {
     const double d = L[threadIdx.x][threadIdx.x];
-    scs[threadIdx.x] = d > 0 ? 1.0 / sqrt(d) : 0.0;
+    scs[threadIdx.x] = d > 0 ? rsqrt(d) : 0.0;
   }
   __syncthreads();
   if (ti < k && tq < k) L[ti][tq] = L[ti][tq] * scs[ti] * scs[tq] + (ti == tq ? 1e-10 : 0.0);
@@ -1043,22 +1059,22 @@ __global__ void k_aa_solve(CoupleParams C, int nblocks) {
   const double sci = lane < k ? scs[lane] : 0.0;
   const double bi = lane < k ? A->b[sl[lane]] * sci : 0.0;
   if (ok) {
-    // L y = b, then L^T g = y; lane i keeps y_i and g_i
-    double yi = 0.0, gi = 0.0;
-    for (int i = 0; i < k; ++i) {
-      double t = lane < i ? L[i][lane] * yi : 0.0;
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      const double y = (__shfl_sync(0xffffffffu, bi, i) - t) * inv[i];
-      if (lane == i) yi = y;
+    // L y = b, then L^T g = y, column-oriented: lane i holds entry i of the
+    // right-hand side; once y_j (g_j) is known every later lane subtracts its
+    // multiple, so each step is one broadcast and one multiply-add
+    double r = bi;
+    for (int j = 0; j < k; ++j) {
+      const double y = __shfl_sync(0xffffffffu, r, j) * inv[j];
+      if (lane == j) r = y;
+      else if (lane > j && lane < k) r = fma(-L[lane][j], y, r);
     }
-    for (int i = k - 1; i >= 0; --i) {
-      double t = lane > i && lane < k ? L[lane][i] * gi : 0.0;
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      const double g = (__shfl_sync(0xffffffffu, yi, i) - t) * inv[i];
-      if (lane == i) gi = g;
+    for (int j = k - 1; j >= 0; --j) {
+      const double g = __shfl_sync(0xffffffffu, r, j) * inv[j];
+      if (lane == j) r = g;
+      else if (lane < j) r = fma(-L[j][lane], g, r);
     }
     if (lane < k) {
-      A->gam[lane] = gi * sci;
+      A->gam[lane] = r * sci;
       A->slot[lane] = sl[lane];
     }
   }
@@ -1068,19 +1084,33 @@ __global__ void k_aa_solve(CoupleParams C, int nblocks) {
 // the combination U = g(U_k) - sum_i gamma_i dG_i; a cell whose combined
 // density or temperature is not positive flags the fallback
 template <bool DI>
-__global__ void k_aa_update(Params P, CoupleParams C) {
+__global__ void __launch_bounds__(CPT) k_aa_update(Params P, CoupleParams C) {
   constexpr int NV = DI ? 6 : 5;
+  __shared__ double gam[AA_MAX];
+  __shared__ int sl[AA_MAX];
+  if (C.scal->done || C.scal->revert) return;
+  const int k = C.scal->k;
+  if (threadIdx.x < k) {
+    gam[threadIdx.x] = C.aa->gam[threadIdx.x];
+    sl[threadIdx.x] = C.aa->slot[threadIdx.x];
+  }
+  __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n_cells;
-  if (c >= n || C.scal->done || C.scal->revert) return;
-  const int k = C.scal->k;
+  if (c >= n) return;
   double U[6] = {0, 0, 0, 0, 0, 0}, Pp[6];
-  for (int q = 0; q < NV; ++q) {
-    double x = C.Gp[(size_t)q * n + c];
-    for (int j = 0; j < k; ++j) x -= C.aa->gam[j] * C.dG[((size_t)C.aa->slot[j] * 6 + q) * n + c];
-    U[q] = x;
-    C.U[(size_t)q * n + c] = x;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) U[q] = C.Gp[(size_t)q * n + c];
+  // column by column, every component's sum in the order j = 0, 1, ...
+#pragma unroll 2
+  for (int j = 0; j < k; ++j) {
+    const double* col = C.dG + (size_t)sl[j] * 6 * n + c;
+    const double g = gam[j];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) U[q] -= g * __ldg(col + (size_t)q * n);
   }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) C.U[(size_t)q * n + c] = U[q];
   prim_from_cons(C, U, Pp);
   if (!(Pp[0] > 0.0 && Pp[4] > 0.0)) C.scal->aabad = 1;
 }
@@ -1371,10 +1401,10 @@ static long long s10_iteration(const Params& P, const CoupleParams& C, int nb, c
   if (C.n_ifaces > 0) k_cp_face<DI><<<nb_for(C.n_ifaces, CPT), CPT, 0, s>>>(P, C);
   k_cp_flux<DI><<<nb, CPT, 0, s>>>(P, C);
   k_cp_reduce<<<1, 1024, 0, s>>>(C, nb);
-  k_aa_base<DI><<<nb, CPT, 0, s>>>(P, C);
+  k_aa_base<DI><<<C.aab, CPT, 0, s>>>(P, C);
   long long k = C.n_ifaces > 0 ? 6 : 5;
   if (C.aa_m > 0) {
-    k_aa_solve<<<1, 1024, 0, s>>>(C, nb);
+    k_aa_solve<<<1, 1024, 0, s>>>(C, C.aab);
     k_aa_update<DI><<<nb, CPT, 0, s>>>(P, C);
     k += 2;
   }
@@ -1429,5 +1459,12 @@ void launch_closure_targets(const Params& P, const CoupleParams& C, const double
 
 size_t couple_part_count(int n_cells) { return 3 * (size_t)nb_for(n_cells, CPT) + 2; }
 size_t couple_apart_count(int n_cells) { return (size_t)(AA_MAX + 1) * nb_for(n_cells, CPT); }
+
+int couple_aa_blocks(int n_cells) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, std::min(nb_for(n_cells, CPT), 4 * sms));
+}
 
 }  // namespace dig

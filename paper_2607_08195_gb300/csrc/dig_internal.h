@@ -192,7 +192,8 @@ struct CoupleParams {
   double *fp, *Gp;    // [6][n] previous f = g(U) - U and g(U) (Gp holds g(U_k) during an iteration)
   double* Ub;         // [6][n] the best iterate so far
   double *dF, *dG;    // [aa_m][6][n] differences of consecutive f and g(U)
-  double* apart;      // [AA_MAX + 1][blocks] per-block dot products
+  double* apart;      // [AA_MAX + 1][aab] per-block dot products
+  int aab;            // blocks of the Anderson base step (a few per SM, at most one per CPT cells)
   AAState* aa;
   int* rpart;
   int* clone_total;
@@ -233,6 +234,8 @@ void launch_couple_s11(const Params& P, const CoupleParams& C, const Buf& cur, i
                        cudaStream_t s);
 size_t couple_part_count(int n_cells);
 size_t couple_apart_count(int n_cells);
+// blocks of the Anderson base step: four per SM, at most one per 128 cells
+int couple_aa_blocks(int n_cells);
 
 // launchers (dig_kernels.cu)
 void launch_init(const Params& P, const Buf& out, int n, cudaStream_t s);
