@@ -357,7 +357,10 @@ int closure_features(dig_ctx* ctx, int32_t which, float* X);
  * outputs); zero for rows with zero density or temperature or an empty cell.
  * Asynchronous. */
 int closure_targets(dig_ctx* ctx, int32_t which, const float* X, int64_t n_rows, float* Y);
-/* Y[n][8] = network(X[n][13]) (DEVICE).  Asynchronous. */
+/* Y[n][8] = network(X[n][13]) (DEVICE), on the tcgen05 tensor cores (BF16
+ * operands, FP32 accumulators in tensor memory, 128 rows per tile).
+ * Synchronous; DIG_ERR_TIMEOUT if a wait on the tensor cores gave up (about
+ * a second). */
 int closure_forward(dig_ctx* ctx, const float* X, int64_t n, float* Y);
 /* mean-square error L = 1/(8 n) sum (pred - Y)^2 over n rows (DEVICE X, Y):
  * pred = network(X), or with identity = 1 the inputs' own HoT X[:, 5:13]

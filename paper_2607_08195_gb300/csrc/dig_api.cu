@@ -126,6 +126,7 @@ struct dig_ctx {
   float *cl_p = nullptr, *cl_m = nullptr, *cl_v = nullptr, *cl_g = nullptr;
   double* cl_acc = nullptr;  // [2] loss accumulators
   int* cl_status = nullptr;
+  int* fw_status = nullptr;  // set by the tensor-core forward when a wait gave up
   bool cl_set = false;
   int64_t adam_t = 0;
   // the bound arena (checkpoints copy it whole)
@@ -590,6 +591,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
   ctx->cl_g = A.take<float>(MLP_NPARAM);
   ctx->cl_acc = A.take<double>(2);
   ctx->cl_status = A.take<int>(2);
+  ctx->fw_status = A.take<int>(1);
   C.scal = A.take<CoupleScalars>(1);
   C.rpart = A.take<int>(cap / 4096 + 2);
   C.clone_total = A.take<int>(1);
@@ -751,6 +753,8 @@ int dig_bind_arena(dig_ctx* ctx, void* dptr, int64_t bytes) {
 // ---------------------------------------------------------------------------
 // waits and status
 // ---------------------------------------------------------------------------
+static int check_forward(dig_ctx* ctx);
+
 static int wait_stream(dig_ctx* ctx) {
   CK(cudaEventRecord(ctx->ev, ctx->stream));
   const auto t0 = std::chrono::steady_clock::now();
@@ -1304,7 +1308,10 @@ int dig_couple(dig_ctx* ctx, dig_couple_report* out) {
   if (learned) {
     // S12: the closure's inputs from the coupling window, then its outputs
     launch_closure_features(ctx->P, C, ctx->P.phi_win, (double)ctx->n_win, C.feat, s);
-    launch_mlp_forward(ctx->cl_p, C.feat, ctx->n_tets, C.ypred, s);
+    CK(cudaMemsetAsync(ctx->fw_status, 0, sizeof(int), s));
+    launch_mlp_forward(ctx->cl_p, C.feat, ctx->n_tets, C.ypred, ctx->fw_status, s);
+    int rf = check_forward(ctx);
+    if (rf) return rf;
   }
   int* av = nullptr;
   launch_couple_s9(ctx->P, C, ctx->cfg.passes, learned ? C.ypred : nullptr, &av, s);
@@ -1490,12 +1497,25 @@ int closure_targets(dig_ctx* ctx, int32_t which, const float* X, int64_t n_rows,
   return DIG_OK;
 }
 
+// the status of the closure's tensor-core forward pass just launched (its
+// flag is cleared before every launch); synchronous: DIG_ERR_TIMEOUT if one
+// of its waits gave up
+static int check_forward(dig_ctx* ctx) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->fw_status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  if (st) return fail(ctx, DIG_ERR_TIMEOUT, "closure forward: a wait on the tensor cores gave up");
+  return DIG_OK;
+}
+
 int closure_forward(dig_ctx* ctx, const float* X, int64_t n, float* Y) {
   if (!ctx || n < 0 || (n > 0 && (!X || !Y))) return DIG_ERR_ARG;
   if (!ctx->cl_set) return fail(ctx, DIG_ERR_STATE, "closure_forward: no parameters set");
-  launch_mlp_forward(ctx->cl_p, X, n, Y, ctx->stream);
+  CK(cudaMemsetAsync(ctx->fw_status, 0, sizeof(int), ctx->stream));
+  launch_mlp_forward(ctx->cl_p, X, n, Y, ctx->fw_status, ctx->stream);
   CK(cudaGetLastError());
-  return DIG_OK;
+  return check_forward(ctx);
 }
 
 int closure_loss(dig_ctx* ctx, const float* X, const float* Y, int64_t n, int32_t identity, double* loss) {

@@ -149,9 +149,11 @@ def test_init_is_bit_exact(solver):
         assert np.array_equal(solver.closure_get(), orc.mlp_init(seed))
 
 
-@pytest.mark.parametrize("n", [1, 64, 1000, 4096 + 37])
+@pytest.mark.parametrize("n", [1, 64, 1000, 4096 + 37, 200_003])
 def test_forward_parity(solver, n):
-    """Forward pass on rows spanning several 64-row tiles and a ragged tail."""
+    """Forward pass (the tcgen05 inference kernel) on rows spanning several
+    128-row tiles and a ragged tail; 200,003 rows give every CTA of the
+    persistent grid several tiles."""
     p = random_net(n)
     solver.closure_set(p)
     rng = np.random.default_rng(n + 1)
