@@ -540,6 +540,48 @@ def rconv_experiment(args):
             "workload": scen.name, "max_steps": KMAX * NSC, "methods": out}
 
 
+def closure_timing(args):
+    """Learned-closure inference (closure_forward: the tcgen05 kernel) against
+    the training kernels' WMMA forward (closure_loss, which adds the loss
+    reduction) on n random rows of a freshly initialised network; CUDA events
+    around 10 launches after 3 warm-up launches.  Returns one object per n."""
+    import torch
+
+    from paper_2607_08195_gb300 import dig
+    from paper_2607_08195_gb300 import workload as W
+
+    g = dig.Solver(W.config_small(), "cuda:0")
+    g.closure_init(3)
+    out = []
+    flops_row = 2.0 * (13 * 64 + 64 * 64 * 2 + 64 * 8)
+    for n in (48_000, 2_000_000, 8_000_000):
+        X = torch.randn((n, 13), device="cuda:0")
+        Y = torch.empty((n, 8), device="cuda:0")
+        T = torch.zeros((n, 8), device="cuda:0")
+        for _ in range(3):
+            g.closure_forward(X, Y)
+            g.closure_loss(X, T)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(10):
+            g.closure_forward(X, Y)
+        b.record()
+        torch.cuda.synchronize()
+        tf = a.elapsed_time(b) / 10
+        a.record()
+        for _ in range(10):
+            g.closure_loss(X, T)
+        b.record()
+        torch.cuda.synchronize()
+        tl = a.elapsed_time(b) / 10
+        out.append({"rows": n, "tcgen05_forward_ms": round(tf, 4), "wmma_forward_and_loss_ms": round(tl, 4),
+                    "tcgen05_tflops": round(flops_row * n / tf / 1e9, 2),
+                    "wmma_tflops": round(flops_row * n / tl / 1e9, 2)})
+    g.close()
+    return {"closure_timing": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -560,6 +602,8 @@ def main():
                     help="200-step checkpoints of the R-conv comparison (100 = 20,000 DSMC steps)")
     ap.add_argument("--no-rconv", action="store_true", help="leave the R-conv comparison out of the default line")
     ap.add_argument("--rconv", action="store_true", help="only the R-conv comparison (plain DSMC vs DIG, 8M cavity)")
+    ap.add_argument("--closure-timing", action="store_true",
+                    help="only the learned closure's inference (tcgen05) and training-kernel forward timings")
     ap.add_argument("--conv-windows", type=int, default=44)
     ap.add_argument("--conv-epochs", type=int, default=20)
     ap.add_argument("--conv-cycles", type=int, default=60)
@@ -581,11 +625,12 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.convergence or args.rconv:
+    if args.convergence or args.rconv or args.closure_timing:
         import torch
 
         torch.cuda.set_device(0)
-        print(json.dumps(convergence_experiment(args) if args.convergence else rconv_experiment(args)), flush=True)
+        fn = convergence_experiment if args.convergence else rconv_experiment if args.rconv else closure_timing
+        print(json.dumps(fn(args)), flush=True)
         return 0
 
     import numpy as np
