@@ -403,6 +403,33 @@ def test_couple_parity_from_written_state(nh, kn, passes, kmax, gas, recon):
     assert np.allclose(vg, vo, rtol=1e-6, atol=1e-4)
 
 
+@pytest.mark.parametrize("N_m", [20, 4000])
+def test_couple_safeguard_parity(N_m):
+    """The synthetic solve's best-iterate safeguard on the GPU (CFL 48 without
+    acceleration: explicit local steps are stable only near CFL 1).  With
+    N_m = 20 every iterate is worse than the initial state, so M^{k+1} is
+    M^{k+1/2} itself and the residual 1, on both sides; with N_m = 4000 the
+    CFL halvings on divergence let both converge to 1e-12, to the same fixed
+    point within 1e-9."""
+    s = W.cavity_scenario(6, 60_000, 0.01, seed=23)
+    over = dict(N_m=N_m, eps_m=1e-12, passes=3, KnD_max=1.0, cfl=48.0, aa_m=0)
+    o, (x, v, Ir, cell), phi, wf = seeded_dig_state(s, steps=40, **over)
+    g = dig.Solver(s, "cuda:0", **over)
+    g.write(x, v, Ir, cell)
+    g.write_moments(dig.PHI_EWMA, phi)
+    g.write_wall_flux(wf, 40)
+    rg, ro = g.couple(), o.couple()
+    assert np.array_equal(g.read_couple(3), o.read_couple(3))
+    if N_m == 20:
+        assert rg["iters"] == ro["iters"] == 20 and rg["residual"] == ro["residual"] == 1.0, (rg, ro)
+        for side in (g, o):
+            assert np.allclose(side.read_couple(2), side.read_couple(0), rtol=1e-13, atol=1e-15)
+    else:
+        converged_pair(rg, ro, N_m, 1e-12)
+        a, b = g.read_couple(2), o.read_couple(2)
+        assert np.all(np.abs(a - b) <= 1e-9 * np.abs(b).max(axis=0)), np.abs(a - b).max(axis=0)
+
+
 def test_couple_parity_benchmarked_solve():
     """The coupling at the synthetic-solve configuration the bench runs (N_m =
     500, eps_m = 1e-6, Anderson depth 20, CFL 1.5) on the 48,000-tet cavity at

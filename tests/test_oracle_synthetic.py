@@ -241,6 +241,37 @@ def test_manufactured_solution_converges():
     assert tot[-1] < 0.02
 
 
+# ------------------------------------------------------------ safeguard
+def _seeded_cavity_inputs():
+    s = W.cavity_scenario(6, 60_000, 0.01, seed=23)
+    o = orc.Oracle(s, N_m=1, passes=3, KnD_max=1.0)
+    o.init()
+    o.step(40, orc.EWMA)
+    o.couple()
+    return s, o.read_couple(0), o.read_couple(1)
+
+
+def test_safeguard_returns_best_iterate_and_recovers():
+    """An unstable pseudo-time step (CFL 48, no acceleration: explicit local
+    steps are stable only near CFL 1): every iterate of the first 20 is worse
+    than the initial state, so the solve returns M^{k+1/2} itself with
+    residual 1; given iterations, the CFL halvings on divergence make it
+    converge to the same fixed point as the stable step (a steady solution does
+    not depend on the pseudo-time step), and the accelerated solve at CFL 12
+    as well."""
+    s, half, hot = _seeded_cavity_inputs()
+    out, it, res = orc.Oracle(s, N_m=20, eps_m=1e-12, cfl=48.0, aa_m=0).synthetic_solve(half, hot=hot)
+    assert it == 20 and res == 1.0
+    assert np.allclose(out, half, rtol=1e-13, atol=1e-15)
+    ref, it0, r0 = orc.Oracle(s, N_m=4000, eps_m=1e-12).synthetic_solve(half, hot=hot)
+    assert r0 <= 1e-12 and it0 < 4000
+    sc = np.abs(ref).max(axis=0)
+    for cfl, m in ((48.0, 0), (12.0, 20)):
+        new, it, res = orc.Oracle(s, N_m=4000, eps_m=1e-12, cfl=cfl, aa_m=m).synthetic_solve(half, hot=hot)
+        assert res <= 1e-12 and it < 4000, (cfl, m, it, res)
+        assert np.all(np.abs(new - ref) <= 1e-9 * sc), (cfl, m, np.abs(new - ref).max(axis=0))
+
+
 # -------------------------------------------------------------- mean free path
 def test_vhs_mean_free_path():
     """P2: in an equilibrium VHS gas the mean distance a molecule flies between
