@@ -362,6 +362,13 @@ int closure_targets(dig_ctx* ctx, int32_t which, const float* X, int64_t n_rows,
  * Synchronous; DIG_ERR_TIMEOUT if a wait on the tensor cores gave up (about
  * a second). */
 int closure_forward(dig_ctx* ctx, const float* X, int64_t n, float* Y);
+/* Test of the failure path of the closure's tensor-core forward: runs it on
+ * up to 128 rows of the context's own buffers with its MMAs withheld, so that
+ * its first mbarrier wait gives up after about a second (a flag that nothing
+ * sets); the kernel then frees its tensor memory and returns.  Returns what
+ * closure_forward returns in that case, DIG_ERR_TIMEOUT; the context stays
+ * usable.  Synchronous (about two seconds). */
+int dig_test_forward_timeout(dig_ctx* ctx);
 /* mean-square error L = 1/(8 n) sum (pred - Y)^2 over n rows (DEVICE X, Y):
  * pred = network(X), or with identity = 1 the inputs' own HoT X[:, 5:13]
  * (the closure without the network).  Synchronous. */

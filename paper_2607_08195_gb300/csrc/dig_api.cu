@@ -1509,6 +1509,16 @@ static int check_forward(dig_ctx* ctx) {
   return DIG_OK;
 }
 
+int dig_test_forward_timeout(dig_ctx* ctx) {
+  if (!ctx) return DIG_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, DIG_ERR_STATE, "dig_test_forward_timeout: no arena bound");
+  const long long n = std::min<long long>(128, ctx->n_tets);
+  CK(cudaMemsetAsync(ctx->fw_status, 0, sizeof(int), ctx->stream));
+  launch_mlp_forward(ctx->cl_p, ctx->C.feat, n, ctx->C.ypred, ctx->fw_status, ctx->stream, 1);
+  CK(cudaGetLastError());
+  return check_forward(ctx);
+}
+
 int closure_forward(dig_ctx* ctx, const float* X, int64_t n, float* Y) {
   if (!ctx || n < 0 || (n > 0 && (!X || !Y))) return DIG_ERR_ARG;
   if (!ctx->cl_set) return fail(ctx, DIG_ERR_STATE, "closure_forward: no parameters set");

@@ -216,8 +216,10 @@ void launch_closure_targets(const Params& P, const CoupleParams& C, const double
                             long long n_rows, float* Y, cudaStream_t s);
 // learned closure (dig_mlp.cu); params are the FP32 master parameters
 // Y[n][8] = network(X[n][13]) on tcgen05; *status |= 1 if a wait on the
-// tensor cores gave up (about a second)
-void launch_mlp_forward(const float* params, const float* X, long long n, float* Y, int* status, cudaStream_t s);
+// tensor cores gave up (about a second); hold != 0 withholds the MMAs (a
+// test of that path)
+void launch_mlp_forward(const float* params, const float* X, long long n, float* Y, int* status, cudaStream_t s,
+                        int hold = 0);
 void launch_mlp_train_step(const float* params, const float* X, const float* T, const int* perm, long long n_total,
                            long long b0, long long nb, float* grad, double* loss, int* status, cudaStream_t s);
 void launch_mlp_loss(const float* params, const float* X, const float* T, long long n, int identity, double* acc,

@@ -181,7 +181,9 @@ __device__ void forward(Smem& S, const float* __restrict__ X, long long row0, lo
 // Layers 1-3 accumulate into TMEM columns 0..63 (N = 64), layer 4 into
 // columns 64..79 (N = 16: the 8 outputs and 8 zero rows of padding).
 // Every wait on the mbarrier gives up after about a second: the CTA then
-// records the failure in *status, frees its TMEM and returns.
+// records the failure in *status, frees its TMEM and returns.  With hold != 0
+// (a test of that path) no MMA is issued or committed, so the first wait
+// runs out.
 // ---------------------------------------------------------------------------
 constexpr int TROWS = 128;          // rows per tile (MMA M)
 constexpr int TCT = 128;            // threads per CTA
@@ -303,7 +305,8 @@ __device__ __forceinline__ void tc_hidden(TcSmem& S, uint32_t tl, const float* b
 }
 
 __global__ void __launch_bounds__(TCT) k_mlp_forward_tc(const float* __restrict__ p, const float* __restrict__ X,
-                                                       long long n, float* __restrict__ Y, int* __restrict__ status) {
+                                                       long long n, float* __restrict__ Y, int* __restrict__ status,
+                                                       int hold) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(TCT) k_mlp_forward_tc(const float* __restrict_
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !hold) {
       tc_fence_after();
       for (int kk = 0; kk < ksteps; ++kk)
         tc_mma(tmem + dcol, da + (uint64_t)(16 * kk), db + (uint64_t)(16 * kk), id, kk > 0 ? 1u : 0u);
@@ -609,7 +612,8 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
 }
 }  // namespace
 
-void launch_mlp_forward(const float* params, const float* X, long long n, float* Y, int* status, cudaStream_t s) {
+void launch_mlp_forward(const float* params, const float* X, long long n, float* Y, int* status, cudaStream_t s,
+                        int hold) {
   if (n <= 0) return;
   static int sms = 0;
   if (sms == 0) {
@@ -621,7 +625,7 @@ void launch_mlp_forward(const float* params, const float* X, long long n, float*
   cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   long long nb = (n + TROWS - 1) / TROWS;
   if (nb > 4LL * sms) nb = 4LL * sms;
-  k_mlp_forward_tc<<<(int)nb, TCT, TC_SMEM, s>>>(params, X, n, Y, status);
+  k_mlp_forward_tc<<<(int)nb, TCT, TC_SMEM, s>>>(params, X, n, Y, status, hold);
   ++g_launches;
 }
 

@@ -74,7 +74,8 @@ EXPORTS = ["dig_create", "dig_destroy", "dig_last_error", "dig_set_stream", "mes
            "dig_sort_scratch_bytes", "dig_sort_by_cell", "dig_sort_by_cell_noalloc", "dig_couple",
            "dig_read_couple", "dig_write_moments", "dig_write_wall_flux", "closure_init", "closure_set",
            "closure_get", "closure_features", "closure_targets", "closure_forward", "closure_loss", "closure_grad",
-           "closure_train", "dig_checkpoint_bytes", "dig_save", "dig_load", "dig_surface"]
+           "closure_train", "dig_checkpoint_bytes", "dig_save", "dig_load", "dig_surface",
+           "dig_test_forward_timeout"]
 
 _lib = None
 
@@ -106,7 +107,7 @@ def load_library(path: str = LIB_PATH):
         "closure_loss": [P, P, P, I64, I32, P], "closure_grad": [P, P, P, I64, P, P],
         "closure_train": [P, P, P, P, I64, P],
         "dig_checkpoint_bytes": [P, P], "dig_save": [P, P, I64], "dig_load": [P, P, I64],
-        "dig_surface": [P, P, I64, P],
+        "dig_surface": [P, P, I64, P], "dig_test_forward_timeout": [P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -365,6 +366,11 @@ class Solver:
         self._check(self.L.closure_targets(self.h, which, self._dev(X, torch.float32, MLP_NIN), X.shape[0],
                                            self._dev(Y, torch.float32, MLP_NOUT)))
         return Y
+
+    def test_forward_timeout(self):
+        """The failure path of the tensor-core forward (its MMAs withheld, so
+        its first wait gives up); returns the library's status code."""
+        return self.L.dig_test_forward_timeout(self.h)
 
     def closure_forward(self, X, Y=None):
         import torch

@@ -169,6 +169,27 @@ def test_forward_parity(solver, n):
     assert np.abs(Yg - Yo).mean() < np.abs(Yg - Y64).mean()
 
 
+def test_forward_wait_gives_up_and_context_survives(solver):
+    """Failure detection of the tensor-core forward without a GPU fault: with
+    its MMAs withheld the first mbarrier wait runs out after about a second,
+    the kernel frees its tensor memory and returns, and the library reports
+    DIG_ERR_TIMEOUT; a normal forward on the same context then still matches
+    the oracle."""
+    import time
+
+    p = random_net(5)
+    solver.closure_set(p)
+    t0 = time.time()
+    assert solver.test_forward_timeout() == -8  # DIG_ERR_TIMEOUT
+    assert 0.5 < time.time() - t0 < 30.0
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((300, 13)).astype(np.float32)
+    Yg = solver.closure_forward(torch.from_numpy(X).to(DEV)).cpu().numpy().astype(np.float64)
+    Yo = orc.mlp_forward(p, X, bf16=True)
+    tol = NSIG * forward_sd(p, X)[0] + 1e-7
+    assert np.all(np.abs(Yg - Yo) <= tol)
+
+
 def test_gradient_parity(solver):
     """Backward pass: gradient of the mean-square loss over 777 rows, layer by
     layer within 1e-2 relative L2; the loss within 1e-3."""
