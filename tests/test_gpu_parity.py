@@ -713,6 +713,34 @@ def test_capsule_bit_exact():
     assert cg["lb"] > 0 and cg["wall"] > 0 and cg["stuck"] == 0
 
 
+def test_couple_parity_capsule():
+    """DIG coupling on the nitrogen capsule at Mach 25 (14,381 tets, 50,000
+    particles after 40 steps), the solve converged to eps_m = 1e-12 (about
+    5,900 iterations): rotational energy equation and heat flux, free-stream
+    and outflow faces, a wall at 500 K; most cells filled (few particles per
+    cell this early).  Identical flags and counts, the solve's inputs within
+    1e-9 and its converged state within 1e-8 (as on the sphere), identical
+    recalibrated particle cells."""
+    s = W.capsule_scenario(0.3, 50_000, seed=5)
+    over = dict(N_m=12000, eps_m=1e-12, passes=3, KnD_max=1.0)
+    o, (x, v, Ir, cell), phi, wf = seeded_dig_state(s, steps=40, **over)
+    g = dig.Solver(s, "cuda:0", **over)
+    g.write(x, v, Ir, cell)
+    g.write_moments(dig.PHI_EWMA, phi)
+    rg, ro = g.couple(), o.couple()
+    converged_pair(rg, ro, 12000, 1e-12)
+    for k in ("n_rejected", "n_reconstructed", "n_cloned", "n_deleted"):
+        assert rg[k] == ro[k], (k, rg[k], ro[k])
+    flags = o.read_couple(3)[:, 0]
+    assert np.array_equal(g.read_couple(3)[:, 0], flags)
+    assert (flags == 3).sum() > 0 and (flags == 2).sum() > 0 and (flags == 1).sum() > 0
+    for which, tol in ((4, 1e-9), (0, 1e-9), (1, 1e-9), (2, 1e-8)):
+        a, b = g.read_couple(which), o.read_couple(which)
+        scale = np.abs(b).max(axis=0) + 1e-30
+        assert np.all(np.abs(a - b) <= tol * scale), (which, np.abs(a - b).max(axis=0))
+    assert np.array_equal(g.read()[3], o.read()[3])
+
+
 def test_capsule_medium_size_properties():
     """The capsule at a medium size (about 0.4M tets, 20M particles), three
     steps: count bookkeeping, no particle over the crossing limit, sampled
