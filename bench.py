@@ -58,6 +58,30 @@ def read_traffic():
     return None
 
 
+def read_solve_flops():
+    """Executed FP64 FLOPs (DADD + DMUL + 2 DFMA thread instructions, ncu) per
+    cell and synthetic-solver iteration, from the committed summary, if the
+    coupling kernels' source is still the one that was counted (else None)."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2607_08195_gb300", "csrc", "dig_couple.cu")
+    prof = os.path.join(ROOT, "profiles", "synthetic_solver-cavity30-Kn0.01.md")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = dict(l.split(":", 1) for l in open(prof)
+                      if l.startswith(("kernel_source_sha256_16:", "fp64_flops_per_cell_iteration:")))
+        if fields["kernel_source_sha256_16"].strip() == h:
+            return float(fields["fp64_flops_per_cell_iteration"])
+    except Exception:
+        pass
+    return None
+
+
+# FP64 peak of the part: ncu's sm__sass_thread_inst_executed_op_dfma_pred_on
+# peak_sustained is 2 per SM and cycle; 152 SMs x 2 FMA x 2 FLOP x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -721,6 +745,23 @@ def main():
                 "kernel": "particle pass (k_order+k_collide+k_move+k_track)",
                 "peak_kind": peak_kind, "kernel_ms_per_launch": cp_launch_ms, "kernel_share_of_step": k_ms / ms}
 
+    # the coupling: its synthetic solve is bound by the FP64 pipe; executed
+    # FP64 FLOPs per cell-iteration (ncu count, committed summary) x cells x
+    # the timed couplings' iterations / the couplings' CUDA-event time (S9
+    # and S11 included, so slightly low)
+    roofline_solve = None
+    timed = reports[len(reports) - args.steps:] if reports else []
+    fpc = read_solve_flops()
+    if timed and couple_ms > 0:
+        iters = sum(r["iters"] for r in timed)
+        ach = None if fpc is None else fpc * len(scen.mesh.tets) * iters / (couple_ms * 1e-3) / 1e9
+        roofline_solve = {"bound": "fp64", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                          "frac": None if ach is None else ach / FP64_PEAK_GFLOPS,
+                          "peak_kind": "derived: 2 FP64 FMA per SM and cycle x 152 SMs x 2.07 GHz",
+                          "flops_per_cell_iteration": fpc, "iterations": iters,
+                          "ms_per_iteration": couple_ms / iters if iters else None,
+                          "kernel": "synthetic solve (k_cp_*, k_aa_*)"}
+
     # end to end through the C ABI with host buffers: pinned host particle
     # state in, N_S DSMC steps, moving-average sums out, every bench step
     e2e = None
@@ -764,7 +805,8 @@ def main():
                        "dsmc_steps_per_step": N_S, "parallelism": f"replicas{world}",
                        "coupling": "none" if args.no_couple else f"DIG every {N_S} steps, N_m={g.cfg.N_m}",
                        "l2": f"inputs larger than L2 (2 x {40 * scen.n_particles / 1e6:.0f} MB particle buffers)"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "phases": phases,
+            "roofline": roofline, "roofline_solve": roofline_solve, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "phases": phases,
             "clocks": clk.summary(),
             "couple_last": reports[-1] if reports else None,
         }
