@@ -1322,9 +1322,9 @@ __global__ void k_recal_clone(Params P, CoupleParams C, Buf CUR, const int* __re
         xs[i] = __dadd_rn(__dadd_rn(__dadd_rn(A[i], __dmul_rn(s, __dsub_rn(B[i], A[i]))),
                                     __dmul_rn(tt, __dsub_rn(Cc[i], A[i]))),
                           __dmul_rn(u, __dsub_rn(D[i], A[i])));
-      CUR.x[q] = xs[0];
-      CUR.y[q] = xs[1];
-      CUR.z[q] = xs[2];
+      CUR.pos[3 * (size_t)q] = xs[0];
+      CUR.pos[3 * (size_t)q + 1] = xs[1];
+      CUR.pos[3 * (size_t)q + 2] = xs[2];
       CUR.vx[q] = CUR.vx[p];
       CUR.vy[q] = CUR.vy[p];
       CUR.vz[q] = CUR.vz[p];

@@ -55,7 +55,7 @@ struct InflowDev {
 // one particle buffer, structure of arrays; x,y,z and vx,vy,vz are contiguous
 // blocks of `cap` elements each
 struct Buf {
-  double *x, *y, *z;
+  double* pos;  // [cap][3] positions x, y, z of each slot, one 24-byte record per particle
   float *vx, *vy, *vz, *Ir;
   int* mc;  // cell of the particle at each slot after the move that wrote it (-1: removed)
 };

@@ -22,6 +22,8 @@
 //   k_move       CTA per tile of cells: the cells' summation variables, then
 //                every particle's move x + v dt with the FP32-proven inside
 //                test, a proven one-crossing shortcut, and a queue of the rest.
+//                A particle's position is one 24-byte record (x, y, z), so
+//                gathering it through the slot map touches one or two sectors.
 //   k_track      face-by-face tracking of the queued particles, thread per
 //                particle: the dependent mesh loads and FP64 tests of the
 //                crossings (FP64 issues at 1/64 of the FP32 rate here)
@@ -904,7 +906,8 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
       const int cell = OUT.mc[slot];  // the slot's cell, written by k_order
       lc = cell - c0;
       const int q = P.src[slot];
-      double x = IN.x[q], y = IN.y[q], z = IN.z[q];
+      const double* pq = IN.pos + 3 * (size_t)q;
+      double x = pq[0], y = pq[1], z = pq[2];
       st = 0;
       if (do_move) {
         const float vx = OUT.vx[slot], vy = OUT.vy[slot], vz = OUT.vz[slot];
@@ -947,9 +950,10 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
         }
       }
       if (st <= 1) {
-        OUT.x[slot] = x;
-        OUT.y[slot] = y;
-        OUT.z[slot] = z;
+        double* po = OUT.pos + 3 * (size_t)slot;
+        po[0] = x;
+        po[1] = y;
+        po[2] = z;
       }
       OUT.mc[slot] = st == 1 ? nb : cell;
       if (st == 1) {
@@ -1000,12 +1004,13 @@ __global__ void __launch_bounds__(128) k_track(Params P, Buf IN, Buf OUT, uint32
     const int2 e = tq[q];
     const int slot = e.x, src = e.y;
     const int cell = OUT.mc[slot];
-    double x = IN.x[src], y = IN.y[src], z = IN.z[src];
+    const double* ps = IN.pos + 3 * (size_t)src;
+    double x = ps[0], y = ps[1], z = ps[2];
     float vx = OUT.vx[slot], vy = OUT.vy[slot], vz = OUT.vz[slot], I = DIAT ? OUT.Ir[slot] : 0.0f;
     const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)slot, step, flux, cnt, P.dt, -1);
-    OUT.x[slot] = x;
-    OUT.y[slot] = y;
-    OUT.z[slot] = z;
+    OUT.pos[3 * (size_t)slot] = x;
+    OUT.pos[3 * (size_t)slot + 1] = y;
+    OUT.pos[3 * (size_t)slot + 2] = z;
     OUT.vx[slot] = vx;
     OUT.vy[slot] = vy;
     OUT.vz[slot] = vz;
@@ -1154,9 +1159,9 @@ __global__ void k_inj_gen(Params P, Buf OUT, uint32_t step, int wallflux) {
     }
     const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, F.tet, (uint32_t)slot, step, wallflux != 0, cnt,
                                 tfrac * P.dt, F.face);
-    OUT.x[slot] = x;
-    OUT.y[slot] = y;
-    OUT.z[slot] = z;
+    OUT.pos[3 * (size_t)slot] = x;
+    OUT.pos[3 * (size_t)slot + 1] = y;
+    OUT.pos[3 * (size_t)slot + 2] = z;
     OUT.vx[slot] = vx;
     OUT.vy[slot] = vy;
     OUT.vz[slot] = vz;
@@ -1403,9 +1408,9 @@ __global__ void k_init(Params P, Buf OUT, int n) {
   float g[4];
   gauss2(P, RP_INIT_VEL, (uint32_t)p, 0, 0, 0, g[0], g[1]);
   gauss2(P, RP_INIT_VEL, (uint32_t)p, 1, 0, 0, g[2], g[3]);
-  OUT.x[p] = xs[0];
-  OUT.y[p] = xs[1];
-  OUT.z[p] = xs[2];
+  OUT.pos[3 * (size_t)p] = xs[0];
+  OUT.pos[3 * (size_t)p + 1] = xs[1];
+  OUT.pos[3 * (size_t)p + 2] = xs[2];
   OUT.vx[p] = P.u0[0] + P.sigma_init * g[0];
   OUT.vy[p] = P.u0[1] + P.sigma_init * g[1];
   OUT.vz[p] = P.u0[2] + P.sigma_init * g[2];
@@ -1422,9 +1427,9 @@ __global__ void k_write(Params P, Buf OUT, const double* xs, const float* vs, co
                         int n, int diat) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  OUT.x[p] = xs[3 * (size_t)p];
-  OUT.y[p] = xs[3 * (size_t)p + 1];
-  OUT.z[p] = xs[3 * (size_t)p + 2];
+  OUT.pos[3 * (size_t)p] = xs[3 * (size_t)p];
+  OUT.pos[3 * (size_t)p + 1] = xs[3 * (size_t)p + 1];
+  OUT.pos[3 * (size_t)p + 2] = xs[3 * (size_t)p + 2];
   OUT.vx[p] = vs[3 * (size_t)p];
   OUT.vy[p] = vs[3 * (size_t)p + 1];
   OUT.vz[p] = vs[3 * (size_t)p + 2];
@@ -1438,9 +1443,9 @@ __global__ void k_write(Params P, Buf OUT, const double* xs, const float* vs, co
 __global__ void k_read(Params P, Buf CUR, double* xs, float* vs, float* Is, int* cells, int n, int diat) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
   for (int p = gt; p < n; p += nt) {
-    xs[3 * (size_t)p] = CUR.x[p];
-    xs[3 * (size_t)p + 1] = CUR.y[p];
-    xs[3 * (size_t)p + 2] = CUR.z[p];
+    xs[3 * (size_t)p] = CUR.pos[3 * (size_t)p];
+    xs[3 * (size_t)p + 1] = CUR.pos[3 * (size_t)p + 1];
+    xs[3 * (size_t)p + 2] = CUR.pos[3 * (size_t)p + 2];
     vs[3 * (size_t)p] = CUR.vx[p];
     vs[3 * (size_t)p + 1] = CUR.vy[p];
     vs[3 * (size_t)p + 2] = CUR.vz[p];
