@@ -507,7 +507,7 @@ static size_t layout(dig_ctx* ctx, char* base) {
     float* vs = A.take<float>(3 * cap);
     float* Is = A.take<float>(cap);
     int* mc = A.take<int>(cap);
-    ctx->buf[b] = Buf{xs, vs, vs ? vs + cap : nullptr, vs ? vs + 2 * cap : nullptr, Is, mc};
+    ctx->buf[b] = Buf{xs, vs, Is, mc};
   }
   P.cs = A.take<int>(n + 1);
   P.as = A.take<int>(n + 1);
@@ -875,11 +875,11 @@ int write_particles(dig_ctx* ctx, const double* x, const float* v, const float* 
   cudaStream_t s = ctx->stream;
   if (n > 0) {
     CK(cudaMemcpyAsync(st.pos, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(st.vx, v, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(st.vel, v, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s));
     if (Ir) CK(cudaMemcpyAsync(st.Ir, Ir, n * sizeof(float), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->P.aq, cell, n * sizeof(int), cudaMemcpyHostToDevice, s));
   }
-  launch_write(ctx->P, ctx->buf[ctx->cur], st.pos, st.vx, Ir ? st.Ir : nullptr, ctx->P.aq, (int)n, s);
+  launch_write(ctx->P, ctx->buf[ctx->cur], st.pos, st.vel, Ir ? st.Ir : nullptr, ctx->P.aq, (int)n, s);
   return settle_new_particles(ctx, n);
 }
 
@@ -898,10 +898,10 @@ int read_particles(dig_ctx* ctx, double* x, float* v, float* Ir, int32_t* cell, 
   if (cap < N) return fail(ctx, DIG_ERR_CAPACITY, "read_particles: buffer too small");
   const Buf& st = ctx->buf[1 - ctx->cur];
   cudaStream_t s = ctx->stream;
-  launch_read(ctx->P, ctx->buf[ctx->cur], st.pos, st.vx, st.Ir, ctx->P.aq, N, s);
+  launch_read(ctx->P, ctx->buf[ctx->cur], st.pos, st.vel, st.Ir, ctx->P.aq, N, s);
   if (N > 0) {
     if (x) CK(cudaMemcpyAsync(x, st.pos, 3 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (v) CK(cudaMemcpyAsync(v, st.vx, 3 * (size_t)N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (v) CK(cudaMemcpyAsync(v, st.vel, 3 * (size_t)N * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (Ir) CK(cudaMemcpyAsync(Ir, st.Ir, (size_t)N * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (cell) CK(cudaMemcpyAsync(cell, ctx->P.aq, (size_t)N * sizeof(int), cudaMemcpyDeviceToHost, s));
   }

@@ -1184,9 +1184,8 @@ __global__ void k_recal_decide(Params P, CoupleParams C, Buf CUR, int* __restric
       bool keep = true;
       if (r.on) {
         // v' = u_a + (v - u_b) sc, evaluated as written (no fused multiply-add)
-        CUR.vx[p] = __fadd_rn(r.ua[0], __fmul_rn(__fsub_rn(CUR.vx[p], r.ub[0]), r.sc));
-        CUR.vy[p] = __fadd_rn(r.ua[1], __fmul_rn(__fsub_rn(CUR.vy[p], r.ub[1]), r.sc));
-        CUR.vz[p] = __fadd_rn(r.ua[2], __fmul_rn(__fsub_rn(CUR.vz[p], r.ub[2]), r.sc));
+        float* vp = CUR.vel + 3 * (size_t)p;
+        for (int i = 0; i < 3; ++i) vp[i] = __fadd_rn(r.ua[i], __fmul_rn(__fsub_rn(vp[i], r.ub[i]), r.sc));
         if (C.dr > 0) CUR.Ir[p] = __fmul_rn(CUR.Ir[p], r.fr);
         uint32_t w[4];
         philox((uint32_t)p, sub, 0u, 0u, P.seed_lo, P.seed_hi ^ (RP_RECAL << 24), w);
@@ -1325,9 +1324,7 @@ __global__ void k_recal_clone(Params P, CoupleParams C, Buf CUR, const int* __re
       CUR.pos[3 * (size_t)q] = xs[0];
       CUR.pos[3 * (size_t)q + 1] = xs[1];
       CUR.pos[3 * (size_t)q + 2] = xs[2];
-      CUR.vx[q] = CUR.vx[p];
-      CUR.vy[q] = CUR.vy[p];
-      CUR.vz[q] = CUR.vz[p];
+      for (int i = 0; i < 3; ++i) CUR.vel[3 * (size_t)q + i] = CUR.vel[3 * (size_t)p + i];
       if (C.dr > 0) CUR.Ir[q] = CUR.Ir[p];
       CUR.mc[q] = c;
       atomicAdd(P.na + c, 1);

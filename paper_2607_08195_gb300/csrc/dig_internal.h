@@ -56,7 +56,8 @@ struct InflowDev {
 // blocks of `cap` elements each
 struct Buf {
   double* pos;  // [cap][3] positions x, y, z of each slot, one 24-byte record per particle
-  float *vx, *vy, *vz, *Ir;
+  float* vel;   // [cap][3] velocities vx, vy, vz, one 12-byte record per particle
+  float* Ir;
   int* mc;  // cell of the particle at each slot after the move that wrote it (-1: removed)
 };
 

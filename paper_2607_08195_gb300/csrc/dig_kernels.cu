@@ -22,8 +22,9 @@
 //   k_move       CTA per tile of cells: the cells' summation variables, then
 //                every particle's move x + v dt with the FP32-proven inside
 //                test, a proven one-crossing shortcut, and a queue of the rest.
-//                A particle's position is one 24-byte record (x, y, z), so
-//                gathering it through the slot map touches one or two sectors.
+//                A particle's position is one 24-byte record (x, y, z) and
+//                its velocity one 12-byte record, so gathering either through
+//                the slot map touches one or two sectors.
 //   k_track      face-by-face tracking of the queued particles, thread per
 //                particle: the dependent mesh loads and FP64 tests of the
 //                crossings (FP64 issues at 1/64 of the FP32 rate here)
@@ -533,9 +534,13 @@ __device__ int track(const Params& P, double& x, double& y, double& z, float& vx
 // on the cell's velocities in the gathered buffer.
 // ---------------------------------------------------------------------------
 template <bool DIAT, bool VSS>
-__device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, float* vz, float* I, int N,
-                             uint32_t step, bool record, Cnt& cnt) {
+__device__ void collide_cell(const Params& P, int cell, float* v, float* I, int N, uint32_t step, bool record,
+                             Cnt& cnt) {
   if (N < 2) return;
+  // the cell's velocity records: particle k's components at v[3k], v[3k+1], v[3k+2]
+  auto vx = [v](int k) -> float& { return v[3 * k]; };
+  auto vy = [v](int k) -> float& { return v[3 * k + 1]; };
+  auto vz = [v](int k) -> float& { return v[3 * k + 2]; };
   float cmax = P.cmax[cell];
   const double X = (double)N * (double)(N - 1) * 0.5 * (double)cmax * P.fdtv[cell] + P.rem[cell];
   const double fl = floor(X);
@@ -555,7 +560,7 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
     const int i = (int)(((unsigned long long)w[0] * (unsigned long long)N) >> 32);
     int j = (int)(((unsigned long long)w[1] * (unsigned long long)(N - 1)) >> 32);
     if (j >= i) j = j + 1;
-    const float gx = vx[i] - vx[j], gy = vy[i] - vy[j], gz = vz[i] - vz[j];
+    const float gx = vx(i) - vx(j), gy = vy(i) - vy(j), gz = vz(i) - vz(j);
     float g2 = gx * gx + gy * gy + gz * gz;
     const float g2_pre = g2;
     const float sc = g2 > 0.0f ? P.c_vhs * pow_f(g2, P.one_m_omega) : 0.0f;
@@ -607,15 +612,15 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
     for (int q = 0; q < 4; ++q) w[q] = wn[q];
     const float h = 0.5f * cr;
     float cm;
-    cm = (vx[i] + vx[j]) * 0.5f;
-    vx[i] = cm + h * ex;
-    vx[j] = cm - h * ex;
-    cm = (vy[i] + vy[j]) * 0.5f;
-    vy[i] = cm + h * ey;
-    vy[j] = cm - h * ey;
-    cm = (vz[i] + vz[j]) * 0.5f;
-    vz[i] = cm + h * ez;
-    vz[j] = cm - h * ez;
+    cm = (vx(i) + vx(j)) * 0.5f;
+    vx(i) = cm + h * ex;
+    vx(j) = cm - h * ex;
+    cm = (vy(i) + vy(j)) * 0.5f;
+    vy(i) = cm + h * ey;
+    vy(j) = cm - h * ey;
+    cm = (vz(i) + vz(j)) * 0.5f;
+    vz(i) = cm + h * ez;
+    vz(j) = cm - h * ez;
   }
   P.cmax[cell] = cmax;
 }
@@ -627,13 +632,12 @@ __device__ void collide_cell(const Params& P, int cell, float* vx, float* vy, fl
 // v(3), vv (xx,yy,zz,xy,xz,yz), |v|^2 v(3), I, I v(3); 13..16 zero for a
 // monatomic gas).
 template <bool DIAT>
-__device__ __forceinline__ float cell_sums_warp(const float* vx, const float* vy, const float* vz, const float* I,
-                                                int N, int lane) {
+__device__ __forceinline__ float cell_sums_warp(const float* v, const float* I, int N, int lane) {
   float s[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) s[q] = 0.0f;
   for (int k = lane; k < N; k += 32) {
-    const float x = vx[k], y = vy[k], z = vz[k];
+    const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
     const float vv = x * x + y * y + z * z;
     s[0] += x;
     s[1] += y;
@@ -787,9 +791,9 @@ __global__ void __launch_bounds__(256) k_order(Params P, Buf IN, Buf OUT) {
         const int k = k1 + 16 * r;
         if (k < Nc) {
           const int q = k < OQ ? my[k] : P.src[base + k];
-          ax[r] = IN.vx[q];
-          ay[r] = IN.vy[q];
-          az[r] = IN.vz[q];
+          ax[r] = IN.vel[3 * (size_t)q];
+          ay[r] = IN.vel[3 * (size_t)q + 1];
+          az[r] = IN.vel[3 * (size_t)q + 2];
           if (DIAT) ai[r] = IN.Ir[q];
         }
       }
@@ -797,9 +801,10 @@ __global__ void __launch_bounds__(256) k_order(Params P, Buf IN, Buf OUT) {
       for (int r = 0; r < 4; ++r) {
         const int k = k1 + 16 * r;
         if (k < Nc) {
-          OUT.vx[base + k] = ax[r];
-          OUT.vy[base + k] = ay[r];
-          OUT.vz[base + k] = az[r];
+          float* vo = OUT.vel + 3 * (size_t)(base + k);
+          vo[0] = ax[r];
+          vo[1] = ay[r];
+          vo[2] = az[r];
           OUT.mc[base + k] = c;  // the slot's cell until k_move writes the destination
           if (DIAT) OUT.Ir[base + k] = ai[r];
         }
@@ -820,8 +825,8 @@ __global__ void __launch_bounds__(128) k_collide(Params P, Buf OUT, uint32_t ste
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < P.n_cells) {
     const int base = P.cs[c], N = P.cs[c + 1] - base;
-    collide_cell<DIAT, VSS>(P, c, OUT.vx + base, OUT.vy + base, OUT.vz + base, DIAT ? OUT.Ir + base : nullptr, N, step,
-                       record != 0, cnt);
+    collide_cell<DIAT, VSS>(P, c, OUT.vel + 3 * (size_t)base, DIAT ? OUT.Ir + base : nullptr, N, step, record != 0,
+                            cnt);
   }
   flush_counters(P, cnt);
 }
@@ -879,7 +884,7 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
     constexpr int np = DIAT ? 17 : 13;
     for (int c = warp; c < nc; c += nwarps) {
       const int b = s_cs[c], N = s_cs[c + 1] - b;
-      const float t = cell_sums_warp<DIAT>(OUT.vx + b, OUT.vy + b, OUT.vz + b, DIAT ? OUT.Ir + b : nullptr, N, lane);
+      const float t = cell_sums_warp<DIAT>(OUT.vel + 3 * (size_t)b, DIAT ? OUT.Ir + b : nullptr, N, lane);
       const int q = (lane >> 1) + 1;
       if ((lane & 1) == 0 && q < np) s_sum[q * nc + c] = t;
     }
@@ -910,7 +915,8 @@ __global__ void __launch_bounds__(NT) k_move(Params P, Buf IN, Buf OUT, int pass
       double x = pq[0], y = pq[1], z = pq[2];
       st = 0;
       if (do_move) {
-        const float vx = OUT.vx[slot], vy = OUT.vy[slot], vz = OUT.vz[slot];
+        const float* vs = OUT.vel + 3 * (size_t)slot;
+        const float vx = vs[0], vy = vs[1], vz = vs[2];
         x = __fma_rn(f2d(vx), P.dt, x);
         y = __fma_rn(f2d(vy), P.dt, y);
         z = __fma_rn(f2d(vz), P.dt, z);
@@ -1006,14 +1012,15 @@ __global__ void __launch_bounds__(128) k_track(Params P, Buf IN, Buf OUT, uint32
     const int cell = OUT.mc[slot];
     const double* ps = IN.pos + 3 * (size_t)src;
     double x = ps[0], y = ps[1], z = ps[2];
-    float vx = OUT.vx[slot], vy = OUT.vy[slot], vz = OUT.vz[slot], I = DIAT ? OUT.Ir[slot] : 0.0f;
+    const float* vs = OUT.vel + 3 * (size_t)slot;
+    float vx = vs[0], vy = vs[1], vz = vs[2], I = DIAT ? OUT.Ir[slot] : 0.0f;
     const int dst = track<DIAT>(P, x, y, z, vx, vy, vz, I, cell, (uint32_t)slot, step, flux, cnt, P.dt, -1);
     OUT.pos[3 * (size_t)slot] = x;
     OUT.pos[3 * (size_t)slot + 1] = y;
     OUT.pos[3 * (size_t)slot + 2] = z;
-    OUT.vx[slot] = vx;
-    OUT.vy[slot] = vy;
-    OUT.vz[slot] = vz;
+    OUT.vel[3 * (size_t)slot] = vx;
+    OUT.vel[3 * (size_t)slot + 1] = vy;
+    OUT.vel[3 * (size_t)slot + 2] = vz;
     if (DIAT) OUT.Ir[slot] = I;
     OUT.mc[slot] = dst;
     if (dst == cell)
@@ -1162,9 +1169,9 @@ __global__ void k_inj_gen(Params P, Buf OUT, uint32_t step, int wallflux) {
     OUT.pos[3 * (size_t)slot] = x;
     OUT.pos[3 * (size_t)slot + 1] = y;
     OUT.pos[3 * (size_t)slot + 2] = z;
-    OUT.vx[slot] = vx;
-    OUT.vy[slot] = vy;
-    OUT.vz[slot] = vz;
+    OUT.vel[3 * (size_t)slot] = vx;
+    OUT.vel[3 * (size_t)slot + 1] = vy;
+    OUT.vel[3 * (size_t)slot + 2] = vz;
     if (DIAT) OUT.Ir[slot] = I;
     OUT.mc[slot] = dst;
     if (dst >= 0) atomicAdd(P.na + dst, 1);
@@ -1411,9 +1418,9 @@ __global__ void k_init(Params P, Buf OUT, int n) {
   OUT.pos[3 * (size_t)p] = xs[0];
   OUT.pos[3 * (size_t)p + 1] = xs[1];
   OUT.pos[3 * (size_t)p + 2] = xs[2];
-  OUT.vx[p] = P.u0[0] + P.sigma_init * g[0];
-  OUT.vy[p] = P.u0[1] + P.sigma_init * g[1];
-  OUT.vz[p] = P.u0[2] + P.sigma_init * g[2];
+  OUT.vel[3 * (size_t)p] = P.u0[0] + P.sigma_init * g[0];
+  OUT.vel[3 * (size_t)p + 1] = P.u0[1] + P.sigma_init * g[1];
+  OUT.vel[3 * (size_t)p + 2] = P.u0[2] + P.sigma_init * g[2];
   if (DIAT) {
     rng(P, RP_INIT_VEL, (uint32_t)p, 2, 0, 0, w);
     OUT.Ir[p] = -P.T_init * ln_f(u01f(w[0]));
@@ -1430,9 +1437,9 @@ __global__ void k_write(Params P, Buf OUT, const double* xs, const float* vs, co
   OUT.pos[3 * (size_t)p] = xs[3 * (size_t)p];
   OUT.pos[3 * (size_t)p + 1] = xs[3 * (size_t)p + 1];
   OUT.pos[3 * (size_t)p + 2] = xs[3 * (size_t)p + 2];
-  OUT.vx[p] = vs[3 * (size_t)p];
-  OUT.vy[p] = vs[3 * (size_t)p + 1];
-  OUT.vz[p] = vs[3 * (size_t)p + 2];
+  OUT.vel[3 * (size_t)p] = vs[3 * (size_t)p];
+  OUT.vel[3 * (size_t)p + 1] = vs[3 * (size_t)p + 1];
+  OUT.vel[3 * (size_t)p + 2] = vs[3 * (size_t)p + 2];
   if (diat) OUT.Ir[p] = Is ? Is[p] : 0.0f;
   const int c = cells[p];
   OUT.mc[p] = c;
@@ -1446,9 +1453,9 @@ __global__ void k_read(Params P, Buf CUR, double* xs, float* vs, float* Is, int*
     xs[3 * (size_t)p] = CUR.pos[3 * (size_t)p];
     xs[3 * (size_t)p + 1] = CUR.pos[3 * (size_t)p + 1];
     xs[3 * (size_t)p + 2] = CUR.pos[3 * (size_t)p + 2];
-    vs[3 * (size_t)p] = CUR.vx[p];
-    vs[3 * (size_t)p + 1] = CUR.vy[p];
-    vs[3 * (size_t)p + 2] = CUR.vz[p];
+    vs[3 * (size_t)p] = CUR.vel[3 * (size_t)p];
+    vs[3 * (size_t)p + 1] = CUR.vel[3 * (size_t)p + 1];
+    vs[3 * (size_t)p + 2] = CUR.vel[3 * (size_t)p + 2];
     Is[p] = diat ? CUR.Ir[p] : 0.0f;
   }
   for (int c = gt; c < P.n_cells; c += nt)
