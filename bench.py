@@ -571,10 +571,15 @@ def rconv_experiment(args):
 
 
 def closure_timing(args):
-    """Learned-closure inference (closure_forward: the tcgen05 kernel) against
-    the training kernels' WMMA forward (closure_loss, which adds the loss
-    reduction) on n random rows of a freshly initialised network; CUDA events
-    around 10 launches after 3 warm-up launches.  Returns one object per n."""
+    """The learned closure's tensor-core kernels on random rows of a freshly
+    initialised network: inference (closure_forward) on n rows, CUDA events
+    around 10 launches after 3 warm-up launches; and a training run (20
+    epochs of Adam over 2.1M rows, batches of 4096, the convergence
+    experiment's shape), timed on the host around the synchronous call.
+    Returns the timings."""
+    import time
+
+    import numpy as np
     import torch
 
     from paper_2607_08195_gb300 import dig
@@ -587,10 +592,8 @@ def closure_timing(args):
     for n in (48_000, 2_000_000, 8_000_000):
         X = torch.randn((n, 13), device="cuda:0")
         Y = torch.empty((n, 8), device="cuda:0")
-        T = torch.zeros((n, 8), device="cuda:0")
         for _ in range(3):
             g.closure_forward(X, Y)
-            g.closure_loss(X, T)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
@@ -599,17 +602,22 @@ def closure_timing(args):
         b.record()
         torch.cuda.synchronize()
         tf = a.elapsed_time(b) / 10
-        a.record()
-        for _ in range(10):
-            g.closure_loss(X, T)
-        b.record()
-        torch.cuda.synchronize()
-        tl = a.elapsed_time(b) / 10
-        out.append({"rows": n, "tcgen05_forward_ms": round(tf, 4), "wmma_forward_and_loss_ms": round(tl, 4),
-                    "tcgen05_tflops": round(flops_row * n / tf / 1e9, 2),
-                    "wmma_tflops": round(flops_row * n / tl / 1e9, 2)})
+        out.append({"rows": n, "forward_ms": round(tf, 4), "forward_tflops": round(flops_row * n / tf / 1e9, 2)})
+    n, ep = 2_100_000, 20
+    X = torch.randn((n, 13), device="cuda:0") * 0.5
+    Y = torch.randn((n, 8), device="cuda:0") * 0.1
+    rng = np.random.default_rng(1)
+    perm = torch.from_numpy(np.stack([rng.permutation(n) for _ in range(ep)]).astype(np.int32)).cuda()
+    g.closure_train(X, Y, epochs=1, batch=4096, lr=1e-3, perm=perm[:1].contiguous())
+    torch.cuda.synchronize()
+    t0 = time.time()
+    g.closure_train(X, Y, epochs=ep, batch=4096, lr=1e-3, perm=perm)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
     g.close()
-    return {"closure_timing": out}
+    return {"closure_forward": out,
+            "closure_train": {"rows": n, "epochs": ep, "batch": 4096, "seconds": round(dt, 3),
+                              "ns_per_row_epoch": round(dt / (n * ep) * 1e9, 2)}}
 
 
 def main():
@@ -633,7 +641,7 @@ def main():
     ap.add_argument("--no-rconv", action="store_true", help="leave the R-conv comparison out of the default line")
     ap.add_argument("--rconv", action="store_true", help="only the R-conv comparison (plain DSMC vs DIG, 8M cavity)")
     ap.add_argument("--closure-timing", action="store_true",
-                    help="only the learned closure's inference (tcgen05) and training-kernel forward timings")
+                    help="only the learned closure's tensor-core inference and training timings")
     ap.add_argument("--conv-windows", type=int, default=44)
     ap.add_argument("--conv-epochs", type=int, default=20)
     ap.add_argument("--conv-cycles", type=int, default=60)

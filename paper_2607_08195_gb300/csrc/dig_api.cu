@@ -1532,11 +1532,12 @@ int closure_loss(dig_ctx* ctx, const float* X, const float* Y, int64_t n, int32_
   if (!identity && !ctx->cl_set) return fail(ctx, DIG_ERR_STATE, "closure_loss: no parameters set");
   cudaStream_t s = ctx->stream;
   CK(cudaMemsetAsync(ctx->cl_acc, 0, 2 * sizeof(double), s));
-  launch_mlp_loss(ctx->cl_p, X, Y, n, identity ? 1 : 0, ctx->cl_acc, s);
+  CK(cudaMemsetAsync(ctx->fw_status, 0, sizeof(int), s));
+  launch_mlp_loss(ctx->cl_p, X, Y, n, identity ? 1 : 0, ctx->cl_acc, ctx->fw_status, s);
   CK(cudaGetLastError());
   double acc = 0.0;
   CK(cudaMemcpyAsync(&acc, ctx->cl_acc, sizeof acc, cudaMemcpyDeviceToHost, s));
-  int rc = wait_stream(ctx);
+  int rc = check_forward(ctx);
   if (rc) return rc;
   *loss = acc / (double)(MLP_NOUT * n);
   return DIG_OK;
@@ -1552,11 +1553,14 @@ int closure_grad(dig_ctx* ctx, const float* X, const float* Y, int64_t n, float*
   launch_mlp_train_step(ctx->cl_p, X, Y, nullptr, n, 0, n, ctx->cl_g, ctx->cl_acc, ctx->cl_status, s);
   CK(cudaGetLastError());
   double acc = 0.0;
+  int st = 0;
   CK(cudaMemcpyAsync(grad, ctx->cl_g, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&acc, ctx->cl_acc, sizeof acc, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&st, ctx->cl_status, sizeof st, cudaMemcpyDeviceToHost, s));
   CK(cudaMemsetAsync(ctx->cl_g, 0, MLP_NPARAM * sizeof(float), s));
   int rc = wait_stream(ctx);
   if (rc) return rc;
+  if (st & 2) return fail(ctx, DIG_ERR_TIMEOUT, "closure_grad: a wait on the tensor cores gave up");
   *loss = acc / (double)(MLP_NOUT * n);
   return DIG_OK;
 }
@@ -1587,6 +1591,7 @@ int closure_train(dig_ctx* ctx, const dig_train_cfg* cfg, const float* X, const 
     CK(cudaMemcpyAsync(&st, ctx->cl_status, sizeof st, cudaMemcpyDeviceToHost, s));
     int rc = wait_stream(ctx);
     if (rc) return rc;
+    if (st & 2) return fail(ctx, DIG_ERR_TIMEOUT, "closure_train: a wait on the tensor cores gave up");
     if (st) return fail(ctx, DIG_ERR_ARG, "closure_train: a perm entry is outside [0, n)");
     loss[e] = acc / (double)(MLP_NOUT * n);
   }

@@ -220,11 +220,11 @@ void launch_closure_targets(const Params& P, const CoupleParams& C, const double
 // tensor cores gave up (about a second); hold != 0 withholds the MMAs (a
 // test of that path)
 void launch_mlp_forward(const float* params, const float* X, long long n, float* Y, int* status, cudaStream_t s,
-                        int hold = 0);
+                        int hold = 0, const float* T = nullptr, double* acc = nullptr);
 void launch_mlp_train_step(const float* params, const float* X, const float* T, const int* perm, long long n_total,
                            long long b0, long long nb, float* grad, double* loss, int* status, cudaStream_t s);
 void launch_mlp_loss(const float* params, const float* X, const float* T, long long n, int identity, double* acc,
-                     cudaStream_t s);
+                     int* status, cudaStream_t s);
 void launch_adam(float* p, float* m, float* v, float* g, long long t, float lr, float b1, float b2, float eps,
                  cudaStream_t s);
 void launch_mlp_init(const Params& P, uint64_t seed, float* params, cudaStream_t s);
