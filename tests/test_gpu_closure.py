@@ -190,14 +190,18 @@ def test_forward_wait_gives_up_and_context_survives(solver):
     assert np.all(np.abs(Yg - Yo) <= tol)
 
 
-def test_gradient_parity(solver):
-    """Backward pass: gradient of the mean-square loss over 777 rows, layer by
-    layer within 1e-2 relative L2; the loss within 1e-3."""
+@pytest.mark.parametrize("n", [777, 45_001])
+def test_gradient_parity(solver, n):
+    """Backward pass: every component of the gradient of the mean-square loss
+    within its element-wise tolerance, the loss within 1e-3.  777 rows are
+    seven 128-row tiles, one per CTA; 45,001 rows give every CTA of the
+    one-per-SM grid two or three tiles, whose weight gradients accumulate in
+    tensor memory before they are added to the global gradient."""
     p = random_net(9)
     solver.closure_set(p)
     rng = np.random.default_rng(10)
-    X = rng.standard_normal((777, 13)).astype(np.float32)
-    T = (0.5 * rng.standard_normal((777, 8))).astype(np.float32)
+    X = rng.standard_normal((n, 13)).astype(np.float32)
+    T = (0.5 * rng.standard_normal((n, 8))).astype(np.float32)
     lg, gg = solver.closure_grad(torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV))
     lo, go = orc.mlp_grad(p, X, T, bf16=True)
     assert abs(lg - lo) <= 1e-3 * lo
