@@ -325,7 +325,10 @@ int dig_load(dig_ctx* ctx, const void* host_in, int64_t size);
  * Learned closure (not in the paper; the DIG HoT from a per-cell network):
  * an MLP 13 -> 64 -> 64 -> 64 -> 8 with GELU (z/2 (1 + erf(z / sqrt 2))) on
  * the hidden layers, BF16 weights and activations, FP32 accumulation on the
- * tensor cores.  Parameters (FP32 master copy, [out][in] per layer):
+ * tcgen05 tensor cores (accumulators in tensor memory, 128 rows per tile) in
+ * the forward pass, the loss and the training step.  Every wait on the
+ * tensor cores gives up after about a second; the calls below then return
+ * DIG_ERR_TIMEOUT.  Parameters (FP32 master copy, [out][in] per layer):
  * W1[64][13] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[8][64] b4[8],
  * DIG_MLP_NPARAM floats; the biases are not rounded to BF16.
  * Inputs (closure_features), per cell, nondimensional as in dig_read_couple:
@@ -371,10 +374,11 @@ int closure_forward(dig_ctx* ctx, const float* X, int64_t n, float* Y);
 int dig_test_forward_timeout(dig_ctx* ctx);
 /* mean-square error L = 1/(8 n) sum (pred - Y)^2 over n rows (DEVICE X, Y):
  * pred = network(X), or with identity = 1 the inputs' own HoT X[:, 5:13]
- * (the closure without the network).  Synchronous. */
+ * (the closure without the network).  Synchronous; DIG_ERR_TIMEOUT as above. */
 int closure_loss(dig_ctx* ctx, const float* X, const float* Y, int64_t n, int32_t identity, double* loss);
 /* gradient of L over all n rows with respect to every parameter, to HOST
- * grad[DIG_MLP_NPARAM] (FP32); *loss = L.  No update.  Synchronous. */
+ * grad[DIG_MLP_NPARAM] (FP32); *loss = L.  No update.  Synchronous;
+ * DIG_ERR_TIMEOUT as above. */
 int closure_grad(dig_ctx* ctx, const float* X, const float* Y, int64_t n, float* grad, double* loss);
 typedef struct dig_train_cfg {
   int32_t epochs;        /* passes over the rows (>= 1) */
@@ -387,7 +391,7 @@ typedef struct dig_train_cfg {
  * Y[n][8] (DEVICE); loss[epochs] (HOST) receives each epoch's mean training
  * loss.  The Adam step count carries over between calls.  DIG_ERR_ARG for a
  * bad cfg or a perm entry outside [0, n) (found on the device: the epoch's
- * rows with such entries are skipped).  Synchronous. */
+ * rows with such entries are skipped); DIG_ERR_TIMEOUT as above.  Synchronous. */
 int closure_train(dig_ctx* ctx, const dig_train_cfg* cfg, const float* X, const float* Y, int64_t n,
                   double* loss);
 
